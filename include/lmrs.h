@@ -1,0 +1,215 @@
+/*
+ * lmrs.h -- C ABI of the GB300 (sm_103a) matrix-free Levenberg-Marquardt
+ * hot path for 3D Gaussian splatting with residual sampling
+ * ("Matrix-free Second-order Optimization of Gaussian Splats with Residual
+ * Sampling", Sec. 4 and App. A).
+ *
+ * The library computes, on one GPU, the pieces of one LM step (Alg. 1):
+ * per-tile pixel sampling (Sec. 4.4), projection and tile binning with a
+ * radix sort on (tile, depth) (Sec. 3), the alpha-composited render and its
+ * residuals (Eq. 4, Eq. 7), the Jacobian-vector product J v by forward mode
+ * (Alg. 3), the back-scatter J^T u, diag(J^T W J), the damped operator
+ * (J^T W J + lambda D) v of the normal equation (Eq. 8), the preconditioned
+ * CG solve (Alg. 1) and the parameter update with the step-size rule of
+ * Sec. 4.5 / App. D.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Parameter vectors ("P-vectors": parameters, v, J^T u, D, x, b) hold P =
+ *   G * P_g floats, P_g = 11 + 3 (d+1)^2 for SH degree d, group-major:
+ *     [ means G x 3 | log-scales G x 3 | quaternions G x 4 (w,x,y,z) |
+ *       opacity logits G | SH coefficients G x (d+1)^2 x 3 ]
+ *   scale = exp(log-scale), rotation from the normalised quaternion, opacity
+ *   = sigmoid(logit), colour = sum_k sh_k Y_k(view direction) + 0.5,
+ *   clamped at 0 (real SH basis without Condon-Shortley phase).
+ * - Sampled-pixel vectors (residuals, J v, the u of J^T u) hold S x 3
+ *   floats, one RGB triple per sampled pixel, ordered by view slot, then
+ *   tile (row-major), then the sample order inside the tile.
+ * - Pointers named *_dev are device pointers on the scene's device.  Entry
+ *   points documented as "host or device" accept either (CUDA unified
+ *   addressing decides).  The library never frees caller memory.
+ * - Every call is asynchronous on the scene's stream unless it returns data
+ *   to host memory or takes a non-NULL stats pointer; those synchronise the
+ *   stream before returning.
+ * - Errors are returned as lmrs_status; nothing is thrown across the ABI.
+ *   After LMRS_ERR_CUDA the scene should be destroyed; after any other error
+ *   the scene stays usable.  lmrs_last_error() describes the last failure.
+ * - A scene is not thread-safe: one host thread at a time.
+ */
+#ifndef LMRS_H
+#define LMRS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lmrs_scene lmrs_scene;
+
+typedef enum {
+    LMRS_OK = 0,
+    LMRS_ERR_INVALID_ARG = 1,      /* bad pointer, size, view id or config value */
+    LMRS_ERR_OOM = 2,              /* a device allocation failed */
+    LMRS_ERR_CUDA = 3,             /* a CUDA call or kernel launch failed */
+    LMRS_ERR_NOT_PREPROCESSED = 4, /* a prerequisite call (preprocess, render, diag) is missing */
+    LMRS_ERR_NUMERIC = 5,          /* non-finite or non-positive CG curvature */
+    LMRS_ERR_TIMEOUT = 6,          /* a bounded device-side wait gave up */
+    LMRS_ERR_BUDGET = 7            /* a size limit of the library was exceeded */
+} lmrs_status;
+
+/* Pinhole camera, OpenCV axes (x right, y down, z forward).  Pixel (x, y)
+ * covers [x, x+1) x [y, y+1) with its centre at (x + 0.5, y + 0.5); a point
+ * t in camera space projects to (fx t_x / t_z + cx, fy t_y / t_z + cy). */
+typedef struct {
+    int32_t width, height;
+    float fx, fy, cx, cy;
+    float world_to_cam[12]; /* row-major 3x4 [R | t] */
+    float znear;            /* Gaussians with camera-space depth <= znear are culled */
+} lmrs_camera;
+
+typedef struct {
+    int32_t sh_degree;        /* 0..3 */
+    int32_t tile_w, tile_h;   /* tile shape in pixels, tile_w * tile_h <= 256 (16 x 16 in the paper, Sec. 4.4) */
+    double  sample_frac;      /* K_t = clamp(floor(frac * n_valid + 0.5), 1, n_valid) samples per tile */
+    int32_t samples_per_tile; /* > 0 overrides sample_frac: K_t = min(n_valid, samples_per_tile) */
+    int32_t weight_mode;      /* 0: w = 1; 1: w = n_valid / K_t (the 1/q weight of Eq. 13 per tile) */
+    double  lambda;           /* damping of Eq. 8 */
+    int32_t damping_mode;     /* 0: + lambda * I (Eq. 8); 1: + lambda * diag(J^T W J) */
+    int32_t cg_iters;         /* PCG iterations per LM step (Alg. 1), each one operator application */
+    double  lr_warm;          /* step size of the first warm_iters LM steps (App. D: 0.05 for 10) */
+    double  lr_cap;           /* upper bound of the step size (App. D: 0.2) */
+    double  color_bound;      /* largest SH degree-0 change per step (Sec. 4.5: 1) */
+    int32_t warm_iters;
+    int32_t cache_bf16;       /* 1: per-sample render caches (final colour, transmittance) in BF16 */
+    uint64_t seed;            /* key of the per-tile pixel sampler */
+} lmrs_config;
+
+typedef struct {
+    double rz0;        /* r_0^T z_0 */
+    double rz_final;   /* r_n^T z_n */
+    double res_norm;   /* |r_n| */
+    double alpha[64];  /* per-iteration alpha (first 64 iterations) */
+    double beta[64];
+    int32_t iters;
+} lmrs_cg_stats;
+
+typedef struct {
+    double loss;          /* sum_i w_i |r_i|^2 / (3 sum_i w_i) over the sampled pixels, before the update */
+    double eta;           /* step size used */
+    double max_dc;        /* max |x| over the SH degree-0 entries of the solution */
+    double rz0, rz_final; /* PCG diagnostics */
+    int64_t n_samples;    /* S */
+    int64_t n_pairs;      /* (view, tile, Gaussian) entries in the sorted tile lists */
+} lmrs_step_stats;
+
+/* Fills *cfg with the defaults: SH degree 0, 16x16 tiles, sample_frac 1,
+ * weight_mode 0, lambda 0.1, damping_mode 1, 8 CG iterations, lr_warm 0.05,
+ * lr_cap 0.2, color_bound 1, warm_iters 10, FP32 caches, seed 0. */
+lmrs_status lmrs_config_default(lmrs_config* cfg);
+
+/* Creates a scene on the current CUDA device.
+ *   params     : P floats (host or device), copied.
+ *   cams_host  : n_cams cameras in host memory, copied; all of one size.
+ *   targets_dev: n_cams x height x width x 3 floats (device), borrowed: must
+ *                outlive the scene; may be NULL (then residuals are renders).
+ *   cuda_stream: cudaStream_t used for every launch (NULL = legacy stream).
+ * The scene owns every internal device buffer (parameters, CG vectors,
+ * per-pair records, sort buffers, per-sample caches). */
+lmrs_status lmrs_scene_create(const lmrs_config* cfg, int64_t n_gauss, const float* params,
+                              const lmrs_camera* cams_host, int32_t n_cams,
+                              const float* targets_dev, void* cuda_stream, lmrs_scene** out);
+lmrs_status lmrs_scene_destroy(lmrs_scene* scene);
+
+/* Copies P floats in or out of the scene's parameters (host or device
+ * pointer).  set_params invalidates a previous preprocess. */
+lmrs_status lmrs_set_params(lmrs_scene* scene, const float* src);
+lmrs_status lmrs_get_params(lmrs_scene* scene, float* dst);
+
+/* Steps (a1-a3) of one LM step for the views view_ids_host[0..n_views)
+ * (camera indices, host memory): per-tile pixel sampling keyed by
+ * (seed, lm_step, camera index, tile) (Sec. 4.4), projection of every
+ * Gaussian into every view, tile binning and the radix sort by (tile,
+ * depth, Gaussian index).  Synchronises once (to size the sort). */
+lmrs_status lmrs_preprocess(lmrs_scene* scene, const int32_t* view_ids_host, int32_t n_views,
+                            int64_t lm_step);
+
+/* Alpha-composited render (Eq. 4, Alg. 2) of the preprocessed views.
+ *   images_dev   : n_views x height x width x 3 floats or NULL; full frames.
+ *   residuals_dev: S x 3 floats or NULL; r = render - target at the sampled
+ *                  pixels (Eq. 7).
+ * Always fills the per-sample caches (final colour, final transmittance,
+ * list position of the termination) used by vjp, rhs, diag and lm_step.
+ * Requires lmrs_preprocess. */
+lmrs_status lmrs_render(lmrs_scene* scene, float* images_dev, float* residuals_dev);
+
+/* u = J v at the sampled pixels: forward mode through preprocessing and
+ * compositing (Alg. 3).  v_dev: P floats; u_dev: S x 3 floats.
+ * Requires lmrs_preprocess. */
+lmrs_status lmrs_jvp(lmrs_scene* scene, const float* v_dev, float* u_dev);
+
+/* g = J^T u (no weights): reverse mode, compositing then preprocessing
+ * (App. A).  u_dev: S x 3 floats; g_dev: P floats, overwritten.
+ * Requires lmrs_render. */
+lmrs_status lmrs_vjp(lmrs_scene* scene, const float* u_dev, float* g_dev);
+
+/* b = J^T W r, the right-hand side of Eq. 8 (Eq. 14 up to its constant),
+ * from the cached residuals.  b_dev: P floats.  Requires lmrs_render. */
+lmrs_status lmrs_rhs(lmrs_scene* scene, float* b_dev);
+
+/* D = diag(J^T W J) (App. A, "Diag kernel"), also kept by the scene for the
+ * damping and the Jacobi preconditioner.  d_dev: P floats or NULL.
+ * Requires lmrs_render. */
+lmrs_status lmrs_jtj_diag(lmrs_scene* scene, float* d_dev);
+
+/* out = (J^T W J + lambda * (I or D)) v, the operator of Eq. 8 (Alg. 1,
+ * line "u = ..."), fused JVP + VJP rasterisation.  v, out: P floats (host or
+ * device; host pointers are staged through the scene and the call
+ * synchronises).  Requires lmrs_preprocess, and lmrs_jtj_diag when
+ * damping_mode = 1. */
+lmrs_status lmrs_jtjv(lmrs_scene* scene, const float* v, float* out);
+
+/* Preconditioned CG of Alg. 1 on A x = b with the Jacobi preconditioner
+ * 1 / diag(A) (Sec. 4.2): x_0 = 0, exactly `iters` operator applications,
+ * FP64 inner products and scalars on the device.  b_dev, x_dev: P floats.
+ * st may be NULL.  Requires lmrs_jtj_diag. */
+lmrs_status lmrs_cg_solve(lmrs_scene* scene, const float* b_dev, float* x_dev, int32_t iters,
+                          lmrs_cg_stats* st);
+
+/* Step size of Sec. 4.5 / App. D for a solution x (device, P floats):
+ * lr_warm while lm_step < warm_iters, else min(lr_cap, color_bound /
+ * max |x_dc|) (lr_cap when that maximum is 0); returned in *eta_host. */
+lmrs_status lmrs_step_size(lmrs_scene* scene, const float* x_dev, int64_t lm_step, double* eta_host);
+
+/* One LM step (Alg. 1): preprocess, render, b = J^T W r, D, PCG with
+ * cfg.cg_iters iterations, step size, and the update beta <- beta - eta x
+ * (the descent reading of Eq. 8 with r = render - target).  st may be NULL
+ * (then nothing synchronises).  The solution x stays readable through
+ * lmrs_get_solution. */
+lmrs_status lmrs_lm_step(lmrs_scene* scene, const int32_t* view_ids_host, int32_t n_views,
+                         int64_t lm_step, lmrs_step_stats* st);
+lmrs_status lmrs_get_solution(lmrs_scene* scene, float* x_dst);
+
+/* Introspection (host memory; synchronising).  Sample layout: off[S] is the
+ * offset of each sample inside the valid part of its tile (row-major over
+ * min(tile_w, remaining width) columns), tile_off[n_views*T + 1] the prefix
+ * over tiles.  Tile lists: ranges[n_views*T][2] = [begin, end) into ids[]. */
+int64_t lmrs_num_params(const lmrs_scene* scene);
+int64_t lmrs_num_samples(const lmrs_scene* scene);
+int64_t lmrs_num_pairs(const lmrs_scene* scene);
+lmrs_status lmrs_get_samples(lmrs_scene* scene, uint8_t* off_host, int32_t* tile_off_host);
+lmrs_status lmrs_get_tile_lists(lmrs_scene* scene, int32_t* ranges_host, int32_t* ids_host);
+
+/* Waits for the scene's stream. */
+lmrs_status lmrs_synchronize(lmrs_scene* scene);
+
+const char* lmrs_status_str(lmrs_status s);
+const char* lmrs_last_error(const lmrs_scene* scene);
+
+/* Number of kernels this library has launched in the process so far. */
+int64_t lmrs_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LMRS_H */

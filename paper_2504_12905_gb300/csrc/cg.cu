@@ -1,0 +1,138 @@
+// Vector kernels of the preconditioned CG solve (Alg. 1) and the LM update
+// with the step-size rule (Sec. 4.5, App. D).  Inner products and scalars are
+// FP64 on the device: products of FP32 entries are exact in FP64 and the sums
+// run in FP64 with a fixed-order grid reduction, so no step of the solve goes
+// through the host.
+#include <cstddef>
+
+#include "common.cuh"
+#include "reduce.cuh"
+
+namespace lmrs {
+
+constexpr int kVecBlock = 256;
+
+static int vec_grid(long long n) {
+    long long g = (n + kVecBlock - 1) / kVecBlock;
+    if (g > 1216) g = 1216;  // 8 blocks per SM on 152 SMs; grid-stride beyond
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+// Jacobi preconditioner 1 / diag(A) (Sec. 4.2): 1 / (D + lambda) for the
+// identity damping, 1 / ((1 + lambda) D) for the diagonal damping (0 where
+// D = 0: such a parameter touches no sampled pixel, its right-hand side is 0).
+__global__ void k_precond(Ctx c, const float* D, float* minv) {
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < c.P; j += (long long)gridDim.x * blockDim.x) {
+        const float d = c.damping_mode == 1 ? (1.f + c.lambda) * D[j] : D[j] + c.lambda;
+        minv[j] = d > 0.f ? 1.f / d : 0.f;
+    }
+}
+
+// x0 = 0, r0 = b, z0 = M^-1 r0, p = 0 (the first p-update forms p0 = z0),
+// rz = r0^T z0.
+__global__ void __launch_bounds__(kVecBlock) k_cg_init(Ctx c, const float* b, const float* minv, float* x, float* r,
+                                                      float* z, float* p) {
+    double dot = 0.0;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < c.P; j += (long long)gridDim.x * blockDim.x) {
+        const float bj = b[j];
+        const float zj = minv[j] * bj;
+        x[j] = 0.f;
+        r[j] = bj;
+        z[j] = zj;
+        p[j] = 0.f;
+        dot += (double)bj * (double)zj;
+    }
+    double tot;
+    if (grid_sum_last<kVecBlock>(dot, c.partials, c.counter, &tot) && threadIdx.x == 0) {
+        Scalars* s = c.sc;
+        s->rz = tot;
+        s->rz0 = tot;
+        s->beta = 0.0;
+        if (!isfinite(tot) || tot < 0.0) s->numeric_error = 1u;
+    }
+}
+
+// x += alpha p, r -= alpha A p, z = M^-1 r, beta = r'^T z' / r^T z.
+__global__ void __launch_bounds__(kVecBlock) k_cg_update(Ctx c, int iter, const float* p, const float* Ap,
+                                                        const float* minv, float* x, float* r, float* z) {
+    const float alpha = (float)c.sc->alpha;
+    double dot = 0.0;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < c.P; j += (long long)gridDim.x * blockDim.x) {
+        x[j] += alpha * p[j];
+        const float rj = r[j] - alpha * Ap[j];
+        r[j] = rj;
+        const float zj = minv[j] * rj;
+        z[j] = zj;
+        dot += (double)rj * (double)zj;
+    }
+    double tot;
+    if (grid_sum_last<kVecBlock>(dot, c.partials, c.counter, &tot) && threadIdx.x == 0) {
+        Scalars* s = c.sc;
+        s->rz_new = tot;
+        s->beta = s->rz != 0.0 ? tot / s->rz : 0.0;
+        if (iter < 64) {
+            s->alpha_hist[iter] = s->alpha;
+            s->beta_hist[iter] = s->beta;
+        }
+        s->rz = tot;
+        if (!isfinite(tot)) s->numeric_error = 1u;
+    }
+}
+
+// max |x| over the SH degree-0 entries (the colour parameters of Sec. 4.5).
+__global__ void __launch_bounds__(kVecBlock) k_max_dc(Ctx c, const float* x) {
+    float m = 0.f;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < c.G; g += gridDim.x * blockDim.x) {
+        const float* e = x + 11ll * c.G + (long long)g * c.K * 3;
+        m = fmaxf(m, fmaxf(fabsf(e[0]), fmaxf(fabsf(e[1]), fabsf(e[2]))));
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(&c.sc->max_dc_bits, __float_as_uint(m));
+}
+
+__device__ __forceinline__ double step_size(long long lm_step, double lr_warm, double lr_cap, double color_bound,
+                                            int warm_iters, unsigned int max_bits) {
+    if (lm_step < warm_iters) return lr_warm;
+    const double m = (double)__uint_as_float(max_bits);
+    if (m == 0.0) return lr_cap;
+    return fmin(lr_cap, color_bound / m);
+}
+
+// beta <- beta - eta x
+__global__ void __launch_bounds__(kVecBlock) k_lm_update(Ctx c, long long lm_step, double lr_warm, double lr_cap,
+                                                        double color_bound, int warm_iters, const float* x,
+                                                        float* params) {
+    const double eta = step_size(lm_step, lr_warm, lr_cap, color_bound, warm_iters, c.sc->max_dc_bits);
+    if (blockIdx.x == 0 && threadIdx.x == 0) c.sc->eta = eta;
+    const float e = (float)eta;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < c.P; j += (long long)gridDim.x * blockDim.x)
+        params[j] -= e * x[j];
+}
+
+void launch_precond(const Ctx& c, const float* D, float* minv, cudaStream_t st) {
+    LMRS_LAUNCH(k_precond, vec_grid(c.P), kVecBlock, 0, st, c, D, minv);
+}
+void launch_cg_init(const Ctx& c, const float* b, const float* minv, float* x, float* r, float* z, float* p,
+                    cudaStream_t st) {
+    LMRS_LAUNCH(k_cg_init, vec_grid(c.P), kVecBlock, 0, st, c, b, minv, x, r, z, p);
+}
+void launch_cg_update(const Ctx& c, int iter, const float* p, const float* Ap, const float* minv, float* x, float* r,
+                      float* z, cudaStream_t st) {
+    LMRS_LAUNCH(k_cg_update, vec_grid(c.P), kVecBlock, 0, st, c, iter, p, Ap, minv, x, r, z);
+}
+void launch_cg_finish(const Ctx&, const float*, float*, cudaStream_t) {}
+void launch_max_dc(const Ctx& c, const float* x, cudaStream_t st) {
+    LMRS_LAUNCH(k_max_dc, vec_grid(c.G), kVecBlock, 0, st, c, x);
+}
+void launch_lm_update(const Ctx& c, long long lm_step, double lr_warm, double lr_cap, double color_bound,
+                      int warm_iters, const float* x, float* params, cudaStream_t st) {
+    LMRS_LAUNCH(k_lm_update, vec_grid(c.P), kVecBlock, 0, st, c, lm_step, lr_warm, lr_cap, color_bound, warm_iters, x,
+                params);
+}
+void launch_zero_scalars(const Ctx& c, cudaStream_t st) {
+    cudaMemsetAsync(c.sc, 0, offsetof(Scalars, loss_num), st);
+}
+
+}  // namespace lmrs

@@ -1,0 +1,158 @@
+// Internal declarations shared by the CUDA translation units of liblmrs.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "lmrs.h"
+
+namespace lmrs {
+
+constexpr int kWarp = 32;
+constexpr int kMaxShCoeffs = 16;
+constexpr float kAlphaMin = 1.0f / 255.0f;  // skip threshold
+constexpr float kAlphaMax = 0.99f;          // alpha clamp
+constexpr float kTMin = 1e-4f;              // termination threshold
+constexpr int kRecF4 = 6;                   // float4 per (view, Gaussian) record
+constexpr int kCotF = 12;                   // floats per (view, Gaussian) cotangent slot (9 used)
+constexpr int kGramF = 40;                  // floats per (view, Gaussian) Gram slot
+constexpr int kMaxPartials = 4096;          // block partials of the FP64 reductions
+
+// Camera as the kernels read it.  R, t, fx, fy, cx, cy, limx, limy, znear are
+// the FP32 values the list decisions use.
+struct CamDev {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    float limx, limy;
+    float znear;
+    float centre[3];
+    int W, H;
+};
+
+// Device scalars of the solver (FP64), one block in device memory.  The CG
+// part (up to loss_num) is reset by every solve; the LM part by its users.
+struct Scalars {
+    double rz;       // r^T z of the current iterate
+    double rz_new;
+    double pAp;
+    double alpha;
+    double beta;
+    double rz0;
+    unsigned int numeric_error;
+    unsigned int pad0;
+    double alpha_hist[64];
+    double beta_hist[64];
+    // LM step
+    double loss_num;  // sum w |r|^2
+    double loss_den;  // sum 3 w
+    double eta;
+    unsigned int max_dc_bits;  // bits of max |x_dc| (non-negative float)
+    unsigned int pad1;
+};
+
+// Everything a kernel needs to know about the scene and the current step.
+struct Ctx {
+    int G, deg, K, Pg;
+    long long P;
+    int nv, W, H, tiles_x, tiles_y, T, tile_w, tile_h;
+    int cache_bf16;
+    int damping_mode;
+    float lambda;
+    const float* params;
+    const CamDev* cams;     // indexed by camera id
+    const int* views;       // camera id per slot
+    const float* targets;   // [n_cams][H][W][3] or null
+    // per (slot, Gaussian) pair, index slot * G + g
+    float4* rec;            // kRecF4 float4: primal (3) then tangent (3)
+    int4* rect;             // inclusive tile rectangle, x0 > x1 when culled
+    unsigned int* depth;    // FP32 depth bits
+    unsigned long long* cnt;  // tiles touched (then exclusive prefix)
+    float* cot;             // kCotF floats
+    float* gram;            // kGramF floats
+    // binning
+    unsigned long long* keys;
+    unsigned int* ids;
+    long long npairs;
+    int2* ranges;           // [nv * T] begin, end
+    // sampling
+    const int* tile_off;    // [nv * T + 1]
+    unsigned char* off;     // [S]
+    const float* wtile;     // [nv * T]
+    long long S;
+    const int2* work;       // (slot * T + tile, first sample in tile) per warp item
+    int nwork;
+    // per-sample caches
+    float* resid;           // [S][3]
+    float* cacheC;          // [S][3] FP32 (or BF16 in cacheCh)
+    float* cacheT;          // [S]
+    __nv_bfloat16* cacheCh; // [S][3]
+    __nv_bfloat16* cacheTh; // [S]
+    int* cacheN;            // [S] list position where compositing stopped
+    Scalars* sc;
+    double* partials;
+    unsigned int* counter;
+};
+
+// ---- launch count (every kernel launch goes through note_launch) --------
+void note_launch();
+
+// ---- preprocess.cu --------------------------------------------------------
+void set_sh_constants();
+void launch_sample(const Ctx& c, long long lm_step, unsigned long long seed, cudaStream_t st);
+void launch_prep_fwd(const Ctx& c, cudaStream_t st);
+// tangent v (P floats). With p_update, the tangent is p = z + beta p (beta
+// from the device scalars), written back to p.
+void launch_prep_jvp(const Ctx& c, const float* v, float* p_update, const float* z, cudaStream_t st);
+// g = J^T u chained from the cotangent slots (+ lambda damping of v if v).
+// With dot, pAp = v^T g in FP64 and alpha = rz / pAp on the device.
+void launch_prep_vjp(const Ctx& c, float* g, const float* v, const float* D, bool dot, cudaStream_t st);
+void launch_prep_diag(const Ctx& c, float* D, cudaStream_t st);
+
+// ---- binning.cu -----------------------------------------------------------
+// Exclusive prefix sum of n 64-bit counts in place; returns the total via a
+// device word (total_dev) the caller reads.
+void scan_u64(unsigned long long* data, long long n, unsigned long long* total_dev, void* tmp, size_t tmp_bytes,
+              cudaStream_t st);
+size_t scan_u64_tmp_bytes(long long n);
+void launch_emit(const Ctx& c, cudaStream_t st);
+size_t radix_tmp_bytes(long long n);
+// Stable LSD radix sort of (keys, vals) on the low `bits` key bits.
+// Result ends in keys/vals (the alternate buffers are scratch).
+void radix_sort(unsigned long long* keys, unsigned int* vals, unsigned long long* keys_alt, unsigned int* vals_alt,
+                long long n, int bits, void* tmp, size_t tmp_bytes, cudaStream_t st);
+void launch_ranges(const Ctx& c, cudaStream_t st);
+
+// ---- raster.cu ------------------------------------------------------------
+// Forward render of the sampled pixels: residuals and caches; loss sums.
+void launch_raster_fwd_samples(const Ctx& c, cudaStream_t st);
+// Full frames of every slot into images [nv][H][W][3].
+void launch_raster_full(const Ctx& c, float* images, cudaStream_t st);
+void launch_raster_jvp(const Ctx& c, float* u, cudaStream_t st);
+// Back-scatter of the per-sample cotangent (u, or w * residual when u is
+// null) into the cotangent slots; needs the caches.
+void launch_raster_vjp(const Ctx& c, const float* u, cudaStream_t st);
+// Fused J^T W J: JVP pass then VJP pass per warp item.
+void launch_raster_jtj(const Ctx& c, cudaStream_t st);
+void launch_raster_gram(const Ctx& c, cudaStream_t st);
+
+// ---- cg.cu ----------------------------------------------------------------
+void launch_precond(const Ctx& c, const float* D, float* minv, cudaStream_t st);
+void launch_cg_init(const Ctx& c, const float* b, const float* minv, float* x, float* r, float* z, float* p,
+                    cudaStream_t st);
+void launch_cg_update(const Ctx& c, int iter, const float* p, const float* Ap, const float* minv, float* x, float* r,
+                      float* z, cudaStream_t st);
+void launch_cg_finish(const Ctx& c, const float* p, float* x, cudaStream_t st);
+void launch_max_dc(const Ctx& c, const float* x, cudaStream_t st);
+void launch_lm_update(const Ctx& c, long long lm_step, double lr_warm, double lr_cap, double color_bound,
+                      int warm_iters, const float* x, float* params, cudaStream_t st);
+void launch_zero_scalars(const Ctx& c, cudaStream_t st);
+
+}  // namespace lmrs
+
+#define LMRS_LAUNCH(kernel, grid, block, smem, stream, ...)              \
+    do {                                                                 \
+        ::lmrs::note_launch();                                           \
+        kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);     \
+    } while (0)

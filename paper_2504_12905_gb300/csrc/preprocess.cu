@@ -1,0 +1,763 @@
+// Per-(view, Gaussian) preprocessing of the LM-RS hot path.
+//
+//   k_sample     per-tile stratified pixel sampling (Sec. 4.4)
+//   k_prep_fwd   projection (Sec. 3, Eqs. 2-4): list decisions in FP32 with a
+//                fixed operation order, 2D features, tile counts
+//   k_prep_jvp   forward-mode tangents of the 2D features (Alg. 3, the
+//                "preprocessing" half of the Jv kernel, App. A)
+//   k_prep_vjp   reverse mode from the per-pair 2D cotangents to the 3D
+//                parameters (second launch of the J^T v kernel, App. A), plus
+//                the damping of Eq. 8 and p^T A p in FP64
+//   k_prep_diag  diag(J^T W J) from per-pair 9x9 Gram blocks (App. A "Diag")
+#include <cmath>
+
+#include "common.cuh"
+#include "reduce.cuh"
+
+namespace lmrs {
+
+// Real SH normalisation constants (degree <= 3), computed on the host from
+// K_l^m = sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!), times sqrt(2) for m != 0.
+__constant__ float c_sh[10];
+
+void set_sh_constants() {
+    const double pi = 3.14159265358979323846;
+    float h[10] = {
+        (float)std::sqrt(1.0 / (4.0 * pi)),     // 0: l=0
+        (float)std::sqrt(3.0 / (4.0 * pi)),     // 1: l=1
+        (float)std::sqrt(15.0 / (4.0 * pi)),    // 2: xy, yz, xz
+        (float)std::sqrt(5.0 / (16.0 * pi)),    // 3: 3z^2 - 1
+        (float)std::sqrt(15.0 / (16.0 * pi)),   // 4: x^2 - y^2
+        (float)std::sqrt(35.0 / (32.0 * pi)),   // 5: l=3, |m|=3
+        (float)std::sqrt(105.0 / (4.0 * pi)),   // 6: xyz
+        (float)std::sqrt(21.0 / (32.0 * pi)),   // 7: l=3, |m|=1
+        (float)std::sqrt(7.0 / (16.0 * pi)),    // 8: l=3, m=0
+        (float)std::sqrt(105.0 / (16.0 * pi)),  // 9: z (x^2 - y^2)
+    };
+    cudaMemcpyToSymbol(c_sh, h, sizeof(h));
+}
+
+// Basis values, index l^2 + l + m.
+__device__ __forceinline__ void sh_eval(int deg, float x, float y, float z, float* Y) {
+    Y[0] = c_sh[0];
+    if (deg < 1) return;
+    Y[1] = c_sh[1] * y;
+    Y[2] = c_sh[1] * z;
+    Y[3] = c_sh[1] * x;
+    if (deg < 2) return;
+    Y[4] = c_sh[2] * x * y;
+    Y[5] = c_sh[2] * y * z;
+    Y[6] = c_sh[3] * (3.f * z * z - 1.f);
+    Y[7] = c_sh[2] * x * z;
+    Y[8] = c_sh[4] * (x * x - y * y);
+    if (deg < 3) return;
+    Y[9] = c_sh[5] * y * (3.f * x * x - y * y);
+    Y[10] = c_sh[6] * x * y * z;
+    Y[11] = c_sh[7] * y * (5.f * z * z - 1.f);
+    Y[12] = c_sh[8] * z * (5.f * z * z - 3.f);
+    Y[13] = c_sh[7] * x * (5.f * z * z - 1.f);
+    Y[14] = c_sh[9] * z * (x * x - y * y);
+    Y[15] = c_sh[5] * x * (x * x - 3.f * y * y);
+}
+
+// g = sum_{k>=1} w[k] grad Y_k(x, y, z)  (gradient in R^3 of the polynomial).
+__device__ __forceinline__ void sh_weighted_grad(int deg, float x, float y, float z, const float* w, float g[3]) {
+    g[0] = g[1] = g[2] = 0.f;
+    if (deg < 1) return;
+    const float k1 = c_sh[1];
+    g[1] += w[1] * k1;
+    g[2] += w[2] * k1;
+    g[0] += w[3] * k1;
+    if (deg < 2) return;
+    const float k2 = c_sh[2], k20 = c_sh[3], k22 = c_sh[4];
+    g[0] += w[4] * k2 * y;  g[1] += w[4] * k2 * x;
+    g[1] += w[5] * k2 * z;  g[2] += w[5] * k2 * y;
+    g[2] += w[6] * 6.f * k20 * z;
+    g[0] += w[7] * k2 * z;  g[2] += w[7] * k2 * x;
+    g[0] += w[8] * 2.f * k22 * x;  g[1] -= w[8] * 2.f * k22 * y;
+    if (deg < 3) return;
+    const float k33 = c_sh[5], k32a = c_sh[6], k31 = c_sh[7], k30 = c_sh[8], k32 = c_sh[9];
+    g[0] += w[9] * 6.f * k33 * x * y;
+    g[1] += w[9] * 3.f * k33 * (x * x - y * y);
+    g[0] += w[10] * k32a * y * z;  g[1] += w[10] * k32a * x * z;  g[2] += w[10] * k32a * x * y;
+    g[1] += w[11] * k31 * (5.f * z * z - 1.f);  g[2] += w[11] * 10.f * k31 * y * z;
+    g[2] += w[12] * k30 * (15.f * z * z - 3.f);
+    g[0] += w[13] * k31 * (5.f * z * z - 1.f);  g[2] += w[13] * 10.f * k31 * x * z;
+    g[0] += w[14] * 2.f * k32 * x * z;  g[1] -= w[14] * 2.f * k32 * y * z;  g[2] += w[14] * k32 * (x * x - y * y);
+    g[0] += w[15] * 3.f * k33 * (x * x - y * y);  g[1] -= w[15] * 6.f * k33 * x * y;
+}
+
+// ---------------------------------------------------------------------------
+// Primal quantities of one (view, Gaussian) pair.
+// ---------------------------------------------------------------------------
+struct GParams {
+    float X[3], ls[3], q[4], th;
+};
+
+__device__ __forceinline__ GParams load_gparams(const float* p, int G, int g) {
+    GParams r;
+    const long long G3 = 3ll * G;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        r.X[k] = p[3ll * g + k];
+        r.ls[k] = p[G3 + 3ll * g + k];
+    }
+    // the quaternion block starts at float 6G: not 16-byte aligned for odd G
+#pragma unroll
+    for (int k = 0; k < 4; ++k) r.q[k] = p[6ll * G + 4ll * g + k];
+    r.th = p[10ll * G + g];
+    return r;
+}
+
+struct Prim {
+    float t[3], s[3], qn, qh[4];
+    float R[9], M[9], S[9];
+    float ux, uy;
+    bool clx, cly;
+    float j00, j02, j11, j12;
+    float T[6], V[6];
+    float a, b, c, det;
+    float mux, muy;
+    float A, B, C, o;
+    float dir[3], dn;
+    float col[3];
+    bool clamped[3];
+};
+
+__device__ __forceinline__ float rm(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float ra(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float rs(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float rd(float a, float b) { return __fdiv_rn(a, b); }
+
+// Geometry with the list decisions.  Every operation is one binary32
+// operation in the written order (no contraction), the scale exponential is
+// the binary32 rounding of the FP64 exponential; the same sequence as the
+// reference definition of the decisions, so visibility, depth key and tile
+// rectangle are reproducible bit for bit.  Returns false when culled.
+__device__ __forceinline__ bool prim_geometry(const GParams& gp, const CamDev& cam, int tiles_x, int tiles_y,
+                                              int tw, int th, Prim& P, int4* rect_out, float* depth_out) {
+    const float* R = cam.R;
+    const float* X = gp.X;
+    P.t[0] = ra(ra(ra(rm(R[0], X[0]), rm(R[1], X[1])), rm(R[2], X[2])), cam.t[0]);
+    P.t[1] = ra(ra(ra(rm(R[3], X[0]), rm(R[4], X[1])), rm(R[5], X[2])), cam.t[1]);
+    P.t[2] = ra(ra(ra(rm(R[6], X[0]), rm(R[7], X[1])), rm(R[8], X[2])), cam.t[2]);
+    if (!(P.t[2] > cam.znear)) return false;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) P.s[j] = (float)exp((double)gp.ls[j]);
+    const float* q = gp.q;
+    float qq = ra(ra(ra(rm(q[0], q[0]), rm(q[1], q[1])), rm(q[2], q[2])), rm(q[3], q[3]));
+    if (!(qq > 0.f)) return false;
+    P.qn = __fsqrt_rn(qq);
+    const float w = rd(q[0], P.qn), x = rd(q[1], P.qn), y = rd(q[2], P.qn), z = rd(q[3], P.qn);
+    P.qh[0] = w; P.qh[1] = x; P.qh[2] = y; P.qh[3] = z;
+    float* r = P.R;
+    r[0] = rs(1.f, rm(2.f, ra(rm(y, y), rm(z, z))));
+    r[1] = rm(2.f, rs(rm(x, y), rm(w, z)));
+    r[2] = rm(2.f, ra(rm(x, z), rm(w, y)));
+    r[3] = rm(2.f, ra(rm(x, y), rm(w, z)));
+    r[4] = rs(1.f, rm(2.f, ra(rm(x, x), rm(z, z))));
+    r[5] = rm(2.f, rs(rm(y, z), rm(w, x)));
+    r[6] = rm(2.f, rs(rm(x, z), rm(w, y)));
+    r[7] = rm(2.f, ra(rm(y, z), rm(w, x)));
+    r[8] = rs(1.f, rm(2.f, ra(rm(x, x), rm(y, y))));
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) P.M[3 * i + j] = rm(r[3 * i + j], P.s[j]);
+    const float* m = P.M;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j < 3; ++j) {
+            float v = ra(ra(rm(m[3 * i], m[3 * j]), rm(m[3 * i + 1], m[3 * j + 1])), rm(m[3 * i + 2], m[3 * j + 2]));
+            P.S[3 * i + j] = v;
+            P.S[3 * j + i] = v;
+        }
+    P.ux = rd(P.t[0], P.t[2]);
+    P.uy = rd(P.t[1], P.t[2]);
+    const float cux = fminf(fmaxf(P.ux, -cam.limx), cam.limx);
+    const float cuy = fminf(fmaxf(P.uy, -cam.limy), cam.limy);
+    P.clx = cux != P.ux;
+    P.cly = cuy != P.uy;
+    P.j00 = rd(cam.fx, P.t[2]);
+    P.j02 = -rd(rm(cam.fx, cux), P.t[2]);
+    P.j11 = rd(cam.fy, P.t[2]);
+    P.j12 = -rd(rm(cam.fy, cuy), P.t[2]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        P.T[k] = ra(rm(P.j00, R[k]), rm(P.j02, R[6 + k]));
+        P.T[3 + k] = ra(rm(P.j11, R[3 + k]), rm(P.j12, R[6 + k]));
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            P.V[3 * i + k] = ra(ra(rm(P.T[3 * i], P.S[k]), rm(P.T[3 * i + 1], P.S[3 + k])), rm(P.T[3 * i + 2], P.S[6 + k]));
+    P.a = ra(ra(ra(rm(P.V[0], P.T[0]), rm(P.V[1], P.T[1])), rm(P.V[2], P.T[2])), 0.3f);
+    P.b = ra(ra(rm(P.V[0], P.T[3]), rm(P.V[1], P.T[4])), rm(P.V[2], P.T[5]));
+    P.c = ra(ra(ra(rm(P.V[3], P.T[3]), rm(P.V[4], P.T[4])), rm(P.V[5], P.T[5])), 0.3f);
+    P.det = rs(rm(P.a, P.c), rm(P.b, P.b));
+    if (!(P.det > 0.f)) return false;
+    const float mid = rm(0.5f, ra(P.a, P.c));
+    const float disc = fmaxf(rs(rm(mid, mid), P.det), 0.1f);
+    const float lam = ra(mid, __fsqrt_rn(disc));
+    const float rad = ceilf(rm(3.0f, __fsqrt_rn(lam)));
+    P.mux = ra(rm(cam.fx, P.ux), cam.cx);
+    P.muy = ra(rm(cam.fy, P.uy), cam.cy);
+    const float fx0 = floorf(rd(rs(P.mux, rad), (float)tw));
+    const float fx1 = floorf(rd(ra(P.mux, rad), (float)tw));
+    const float fy0 = floorf(rd(rs(P.muy, rad), (float)th));
+    const float fy1 = floorf(rd(ra(P.muy, rad), (float)th));
+    if (fx1 < 0.f || fx0 > (float)(tiles_x - 1) || fy1 < 0.f || fy0 > (float)(tiles_y - 1)) return false;
+    if (rect_out) {
+        rect_out->x = (int)fmaxf(fx0, 0.f);
+        rect_out->y = (int)fminf(fx1, (float)(tiles_x - 1));
+        rect_out->z = (int)fmaxf(fy0, 0.f);
+        rect_out->w = (int)fminf(fy1, (float)(tiles_y - 1));
+    }
+    if (depth_out) *depth_out = P.t[2];
+    return true;
+}
+
+// 2D features used by the rasterizer: conic, opacity and view-dependent colour.
+__device__ __forceinline__ void prim_features(const GParams& gp, const float* sh, int deg, const CamDev& cam, Prim& P) {
+    const float inv = 1.f / P.det;
+    P.A = P.c * inv;
+    P.B = -P.b * inv;
+    P.C = P.a * inv;
+    P.o = 1.f / (1.f + expf(-gp.th));
+    float d[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) d[k] = gp.X[k] - cam.centre[k];
+    P.dn = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    const float idn = 1.f / P.dn;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) P.dir[k] = d[k] * idn;
+    float Y[kMaxShCoeffs];
+    sh_eval(deg, P.dir[0], P.dir[1], P.dir[2], Y);
+    const int K = (deg + 1) * (deg + 1);
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        float acc = 0.5f;
+        for (int k = 0; k < K; ++k) acc += sh[3 * k + ch] * Y[k];
+        P.clamped[ch] = acc < 0.f;
+        P.col[ch] = P.clamped[ch] ? 0.f : acc;
+    }
+}
+
+__device__ __forceinline__ void load_sh(const float* p, int G, int K, int g, float* sh) {
+    const float* src = p + 11ll * G + (long long)g * K * 3;
+    for (int i = 0; i < 3 * K; ++i) sh[i] = src[i];
+}
+
+// ---------------------------------------------------------------------------
+// Forward-mode tangent of the 9 features (mu_x, mu_y, A, B, C, o, r, g, b)
+// along (dX, dls, dq, dth, dsh); dsh may be null (no SH tangent).
+// ---------------------------------------------------------------------------
+struct GTan {
+    float X[3], ls[3], q[4], th;
+};
+
+__device__ __forceinline__ void prim_tangent(const Prim& P, const CamDev& cam, const GTan& d, const float* sh,
+                                             const float* dsh, int deg, float out[9]) {
+    const float* W = cam.R;
+    float dt[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) dt[k] = W[3 * k] * d.X[0] + W[3 * k + 1] * d.X[1] + W[3 * k + 2] * d.X[2];
+    float ds[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) ds[j] = P.s[j] * d.ls[j];
+    // normalised quaternion: dqh = (dq - qh (qh . dq)) / |q|
+    const float* qh = P.qh;
+    const float proj = qh[0] * d.q[0] + qh[1] * d.q[1] + qh[2] * d.q[2] + qh[3] * d.q[3];
+    const float iqn = 1.f / P.qn;
+    const float dw = (d.q[0] - qh[0] * proj) * iqn, dx = (d.q[1] - qh[1] * proj) * iqn;
+    const float dy = (d.q[2] - qh[2] * proj) * iqn, dz = (d.q[3] - qh[3] * proj) * iqn;
+    const float w = qh[0], x = qh[1], y = qh[2], z = qh[3];
+    float dR[9];
+    dR[0] = -4.f * (y * dy + z * dz);
+    dR[1] = 2.f * (dx * y + x * dy - dw * z - w * dz);
+    dR[2] = 2.f * (dx * z + x * dz + dw * y + w * dy);
+    dR[3] = 2.f * (dx * y + x * dy + dw * z + w * dz);
+    dR[4] = -4.f * (x * dx + z * dz);
+    dR[5] = 2.f * (dy * z + y * dz - dw * x - w * dx);
+    dR[6] = 2.f * (dx * z + x * dz - dw * y - w * dy);
+    dR[7] = 2.f * (dy * z + y * dz + dw * x + w * dx);
+    dR[8] = -4.f * (x * dx + y * dy);
+    float dM[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) dM[3 * i + j] = dR[3 * i + j] * P.s[j] + P.R[3 * i + j] * ds[j];
+    // dSigma = dM M^T + M dM^T
+    float dS[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            float v = 0.f;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) v += dM[3 * i + k] * P.M[3 * j + k] + P.M[3 * i + k] * dM[3 * j + k];
+            dS[3 * i + j] = v;
+        }
+    const float it2 = 1.f / P.t[2];
+    const float dux = (dt[0] - P.ux * dt[2]) * it2;
+    const float duy = (dt[1] - P.uy * dt[2]) * it2;
+    const float dcux = P.clx ? 0.f : dux, dcuy = P.cly ? 0.f : duy;
+    const float dj00 = -P.j00 * dt[2] * it2;
+    const float dj02 = -cam.fx * dcux * it2 - P.j02 * dt[2] * it2;
+    const float dj11 = -P.j11 * dt[2] * it2;
+    const float dj12 = -cam.fy * dcuy * it2 - P.j12 * dt[2] * it2;
+    float dT[6];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        dT[k] = dj00 * W[k] + dj02 * W[6 + k];
+        dT[3 + k] = dj11 * W[3 + k] + dj12 * W[6 + k];
+    }
+    // d(T Sigma T^T) = dT V^T + V dT^T + T dSigma T^T  with V = T Sigma
+    float TdS[6];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            TdS[3 * i + k] = P.T[3 * i] * dS[k] + P.T[3 * i + 1] * dS[3 + k] + P.T[3 * i + 2] * dS[6 + k];
+    const float* V = P.V;
+    const float* T = P.T;
+    const float da = 2.f * (dT[0] * V[0] + dT[1] * V[1] + dT[2] * V[2]) + TdS[0] * T[0] + TdS[1] * T[1] + TdS[2] * T[2];
+    const float db = dT[0] * V[3] + dT[1] * V[4] + dT[2] * V[5] + V[0] * dT[3] + V[1] * dT[4] + V[2] * dT[5] +
+                     TdS[0] * T[3] + TdS[1] * T[4] + TdS[2] * T[5];
+    const float dc = 2.f * (dT[3] * V[3] + dT[4] * V[4] + dT[5] * V[5]) + TdS[3] * T[3] + TdS[4] * T[4] + TdS[5] * T[5];
+    const float ddet = da * P.c + P.a * dc - 2.f * P.b * db;
+    const float idet = 1.f / P.det;
+    out[0] = cam.fx * dux;
+    out[1] = cam.fy * duy;
+    out[2] = (dc - P.A * ddet) * idet;
+    out[3] = (-db - P.B * ddet) * idet;
+    out[4] = (da - P.C * ddet) * idet;
+    out[5] = P.o * (1.f - P.o) * d.th;
+    // colour: SH coefficients and the view direction (through the mean)
+    const float idn = 1.f / P.dn;
+    const float pd = P.dir[0] * d.X[0] + P.dir[1] * d.X[1] + P.dir[2] * d.X[2];
+    float ddir[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) ddir[k] = (d.X[k] - P.dir[k] * pd) * idn;
+    float Y[kMaxShCoeffs];
+    if (dsh) sh_eval(deg, P.dir[0], P.dir[1], P.dir[2], Y);
+    const int K = (deg + 1) * (deg + 1);
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        float v = 0.f;
+        if (deg > 0) {
+            float wk[kMaxShCoeffs];
+            for (int k = 0; k < K; ++k) wk[k] = sh[3 * k + ch];
+            float gr[3];
+            sh_weighted_grad(deg, P.dir[0], P.dir[1], P.dir[2], wk, gr);
+            v = gr[0] * ddir[0] + gr[1] * ddir[1] + gr[2] * ddir[2];
+        }
+        if (dsh)
+            for (int k = 0; k < K; ++k) v += dsh[3 * k + ch] * Y[k];
+        out[6 + ch] = P.clamped[ch] ? 0.f : v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Reverse mode: cotangent of the 9 features -> cotangents of the 3D
+// parameters (accumulated into gX, gls, gq, gth, gsh).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void prim_adjoint(const Prim& P, const CamDev& cam, const float* cot, const float* sh,
+                                             int deg, float gX[3], float gls[3], float gq[4], float* gth, float* gsh) {
+    const float* W = cam.R;
+    // colour -> SH coefficients and view direction
+    const int K = (deg + 1) * (deg + 1);
+    float ccol[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) ccol[ch] = P.clamped[ch] ? 0.f : cot[6 + ch];
+    float Y[kMaxShCoeffs];
+    sh_eval(deg, P.dir[0], P.dir[1], P.dir[2], Y);
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) gsh[3 * k + ch] += ccol[ch] * Y[k];
+    if (deg > 0) {
+        float wk[kMaxShCoeffs];
+        for (int k = 0; k < K; ++k) wk[k] = ccol[0] * sh[3 * k] + ccol[1] * sh[3 * k + 1] + ccol[2] * sh[3 * k + 2];
+        float gd[3];
+        sh_weighted_grad(deg, P.dir[0], P.dir[1], P.dir[2], wk, gd);
+        const float pd = P.dir[0] * gd[0] + P.dir[1] * gd[1] + P.dir[2] * gd[2];
+        const float idn = 1.f / P.dn;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) gX[k] += (gd[k] - P.dir[k] * pd) * idn;
+    }
+    // opacity
+    *gth += cot[5] * P.o * (1.f - P.o);
+    // conic -> 2D covariance (a, b, c)
+    const float idet = 1.f / P.det;
+    const float gdet = -(cot[2] * P.A + cot[3] * P.B + cot[4] * P.C) * idet;
+    const float ga = cot[4] * idet + gdet * P.c;
+    const float gb = -cot[3] * idet - 2.f * P.b * gdet;
+    const float gc = cot[2] * idet + gdet * P.a;
+    // 2D covariance -> T and Sigma:  a = T0 S T0^T, b = T0 S T1^T, c = T1 S T1^T
+    const float* T = P.T;
+    const float* V = P.V;
+    float gT[6];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        gT[k] = 2.f * ga * V[k] + gb * V[3 + k];
+        gT[3 + k] = gb * V[k] + 2.f * gc * V[3 + k];
+    }
+    float gS[9];  // full (non-symmetrised) cotangent of Sigma
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+#pragma unroll
+        for (int n = 0; n < 3; ++n) gS[3 * m + n] = ga * T[m] * T[n] + gb * T[m] * T[3 + n] + gc * T[3 + m] * T[3 + n];
+    // T = J W
+    float gj00 = 0.f, gj02 = 0.f, gj11 = 0.f, gj12 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        gj00 += gT[k] * W[k];
+        gj02 += gT[k] * W[6 + k];
+        gj11 += gT[3 + k] * W[3 + k];
+        gj12 += gT[3 + k] * W[6 + k];
+    }
+    const float it2 = 1.f / P.t[2];
+    float gt[3] = {0.f, 0.f, 0.f};
+    gt[2] += -(gj00 * P.j00 + gj02 * P.j02 + gj11 * P.j11 + gj12 * P.j12) * it2;
+    float gux = cot[0] * cam.fx, guy = cot[1] * cam.fy;
+    if (!P.clx) gux += -gj02 * cam.fx * it2;
+    if (!P.cly) guy += -gj12 * cam.fy * it2;
+    gt[0] += gux * it2;
+    gt[1] += guy * it2;
+    gt[2] += -(gux * P.ux + guy * P.uy) * it2;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) gX[k] += W[k] * gt[0] + W[3 + k] * gt[1] + W[6 + k] * gt[2];
+    // Sigma = M M^T -> gM = (gS + gS^T) M
+    float gM[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            float v = 0.f;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) v += (gS[3 * i + k] + gS[3 * k + i]) * P.M[3 * k + j];
+            gM[3 * i + j] = v;
+        }
+    // M = R diag(s)
+    float gR[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) gR[3 * i + j] = gM[3 * i + j] * P.s[j];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const float gs = gM[j] * P.R[j] + gM[3 + j] * P.R[3 + j] + gM[6 + j] * P.R[6 + j];
+        gls[j] += gs * P.s[j];
+    }
+    // R(qh)
+    const float w = P.qh[0], x = P.qh[1], y = P.qh[2], z = P.qh[3];
+    const float gw = 2.f * (-z * gR[1] + y * gR[2] + z * gR[3] - x * gR[5] - y * gR[6] + x * gR[7]);
+    const float gx = 2.f * (y * gR[1] + z * gR[2] + y * gR[3] - w * gR[5] + z * gR[6] + w * gR[7]) - 4.f * x * (gR[4] + gR[8]);
+    const float gy = 2.f * (x * gR[1] + w * gR[2] + x * gR[3] + z * gR[5] - w * gR[6] + z * gR[7]) - 4.f * y * (gR[0] + gR[8]);
+    const float gz = 2.f * (-w * gR[1] + x * gR[2] + w * gR[3] + y * gR[5] + x * gR[6] + y * gR[7]) - 4.f * z * (gR[0] + gR[4]);
+    // qh = q / |q|
+    const float pr = w * gw + x * gx + y * gy + z * gz;
+    const float iqn = 1.f / P.qn;
+    gq[0] += (gw - w * pr) * iqn;
+    gq[1] += (gx - x * pr) * iqn;
+    gq[2] += (gy - y * pr) * iqn;
+    gq[3] += (gz - z * pr) * iqn;
+}
+
+// ---------------------------------------------------------------------------
+// Kernels
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long sm64_mix(unsigned long long z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// One thread per (slot, tile): partial Fisher-Yates over the tile's valid
+// pixels driven by SplitMix64 keyed by (seed, LM step, camera id, tile id).
+__global__ void k_sample(Ctx c, long long lm_step, unsigned long long seed) {
+    const int vt = blockIdx.x * blockDim.x + threadIdx.x;
+    if (vt >= c.nv * c.T) return;
+    const int slot = vt / c.T, tile = vt % c.T;
+    const int tx = tile % c.tiles_x, ty = tile / c.tiles_x;
+    const int vw = min(c.tile_w, c.W - tx * c.tile_w), vh = min(c.tile_h, c.H - ty * c.tile_h);
+    const int n = vw * vh;
+    const int b = c.tile_off[vt], k = c.tile_off[vt + 1] - b;
+    unsigned char a[256];
+    for (int i = 0; i < n; ++i) a[i] = (unsigned char)i;
+    unsigned long long h = sm64_mix(seed ^ 0x5851F42D4C957F2Dull);
+    h = sm64_mix(h ^ (unsigned long long)lm_step);
+    h = sm64_mix(h ^ (unsigned long long)(unsigned int)c.views[slot]);
+    h = sm64_mix(h ^ (unsigned long long)(unsigned int)tile);
+    for (int i = 0; i < k; ++i) {
+        h += 0x9E3779B97F4A7C15ull;
+        const unsigned long long r = sm64_mix(h);
+        const int j = i + (int)(r % (unsigned long long)(n - i));
+        const unsigned char t = a[i];
+        a[i] = a[j];
+        a[j] = t;
+        c.off[b + i] = a[i];
+    }
+}
+
+__global__ void k_prep_fwd(Ctx c) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)c.nv * c.G) return;
+    const int slot = (int)(i / c.G), g = (int)(i % c.G);
+    const CamDev& cam = c.cams[c.views[slot]];
+    const GParams gp = load_gparams(c.params, c.G, g);
+    Prim P;
+    int4 rect;
+    float depth;
+    if (!prim_geometry(gp, cam, c.tiles_x, c.tiles_y, c.tile_w, c.tile_h, P, &rect, &depth)) {
+        c.rect[i] = make_int4(1, 0, 1, 0);
+        c.cnt[i] = 0ull;
+        return;
+    }
+    float sh[3 * kMaxShCoeffs];
+    load_sh(c.params, c.G, c.K, g, sh);
+    prim_features(gp, sh, c.deg, cam, P);
+    float4* r = c.rec + i * kRecF4;
+    r[0] = make_float4(P.mux, P.muy, P.A, P.B);
+    r[1] = make_float4(P.C, P.o, P.col[0], P.col[1]);
+    r[2] = make_float4(P.col[2], 0.f, 0.f, 0.f);
+    c.rect[i] = rect;
+    c.depth[i] = __float_as_uint(depth);
+    c.cnt[i] = (unsigned long long)(rect.y - rect.x + 1) * (unsigned long long)(rect.w - rect.z + 1);
+}
+
+__device__ __forceinline__ void load_tangent(const float* v, int G, int K, int g, GTan& d, float* dsh) {
+    const GParams t = load_gparams(v, G, g);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        d.X[k] = t.X[k];
+        d.ls[k] = t.ls[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) d.q[k] = t.q[k];
+    d.th = t.th;
+    load_sh(v, G, K, g, dsh);
+}
+
+// Writes p = z + beta p for Gaussian g's entries (beta from the device
+// scalars) and returns the new entries in d/dsh.
+__device__ __forceinline__ void update_p(const Ctx& c, float* p, const float* z, int g, GTan& d, float* dsh) {
+    const float beta = (float)c.sc->beta;
+    const long long G = c.G;
+    auto upd = [&](long long idx) {
+        const float v = z[idx] + beta * p[idx];
+        p[idx] = v;
+        return v;
+    };
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        d.X[k] = upd(3 * g + k);
+        d.ls[k] = upd(3 * G + 3 * g + k);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) d.q[k] = upd(6 * G + 4 * g + k);
+    d.th = upd(10 * G + g);
+    for (int k = 0; k < 3 * c.K; ++k) dsh[k] = upd(11 * G + (long long)g * c.K * 3 + k);
+}
+
+__global__ void k_prep_jvp(Ctx c, const float* v, float* p, const float* z) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= c.G) return;
+    GTan d;
+    float dsh[3 * kMaxShCoeffs];
+    if (p) update_p(c, p, z, g, d, dsh);
+    else load_tangent(v, c.G, c.K, g, d, dsh);
+    const GParams gp = load_gparams(c.params, c.G, g);
+    float sh[3 * kMaxShCoeffs];
+    load_sh(c.params, c.G, c.K, g, sh);
+    for (int slot = 0; slot < c.nv; ++slot) {
+        const long long i = (long long)slot * c.G + g;
+        const int4 rc = c.rect[i];
+        if (rc.x > rc.y) continue;
+        const CamDev& cam = c.cams[c.views[slot]];
+        Prim P;
+        prim_geometry(gp, cam, c.tiles_x, c.tiles_y, c.tile_w, c.tile_h, P, nullptr, nullptr);
+        prim_features(gp, sh, c.deg, cam, P);
+        float o[9];
+        prim_tangent(P, cam, d, sh, dsh, c.deg, o);
+        float4* r = c.rec + i * kRecF4;
+        r[3] = make_float4(o[0], o[1], o[2], o[3]);
+        r[4] = make_float4(o[4], o[5], o[6], o[7]);
+        r[5] = make_float4(o[8], 0.f, 0.f, 0.f);
+        float4* ct = reinterpret_cast<float4*>(c.cot + i * kCotF);
+        ct[0] = ct[1] = ct[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+constexpr int kPrepBlock = 128;
+
+template <bool kDot>
+__global__ void __launch_bounds__(kPrepBlock) k_prep_vjp(Ctx c, float* out, const float* v, const float* D) {
+    double dot = 0.0;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < c.G; g += gridDim.x * blockDim.x) {
+        const GParams gp = load_gparams(c.params, c.G, g);
+        float sh[3 * kMaxShCoeffs];
+        load_sh(c.params, c.G, c.K, g, sh);
+        float gX[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, gth = 0.f;
+        float gsh[3 * kMaxShCoeffs];
+        for (int k = 0; k < 3 * c.K; ++k) gsh[k] = 0.f;
+        for (int slot = 0; slot < c.nv; ++slot) {
+            const long long i = (long long)slot * c.G + g;
+            const int4 rc = c.rect[i];
+            if (rc.x > rc.y) continue;
+            const CamDev& cam = c.cams[c.views[slot]];
+            Prim P;
+            prim_geometry(gp, cam, c.tiles_x, c.tiles_y, c.tile_w, c.tile_h, P, nullptr, nullptr);
+            prim_features(gp, sh, c.deg, cam, P);
+            const float4* ct = reinterpret_cast<const float4*>(c.cot + i * kCotF);
+            const float4 c0 = ct[0], c1 = ct[1], c2 = ct[2];
+            const float cot[9] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, c2.x};
+            prim_adjoint(P, cam, cot, sh, c.deg, gX, gls, gq, &gth, gsh);
+        }
+        const long long G = c.G;
+        auto put = [&](long long idx, float val) {
+            if (v) {
+                const float damp = c.damping_mode == 1 ? c.lambda * D[idx] : c.lambda;
+                val += damp * v[idx];
+                if (kDot) dot += (double)v[idx] * (double)val;
+            }
+            out[idx] = val;
+        };
+#pragma unroll
+        for (int k = 0; k < 3; ++k) put(3 * g + k, gX[k]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) put(3 * G + 3 * g + k, gls[k]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) put(6 * G + 4 * g + k, gq[k]);
+        put(10 * G + g, gth);
+        for (int k = 0; k < 3 * c.K; ++k) put(11 * G + (long long)g * c.K * 3 + k, gsh[k]);
+    }
+    if (kDot) {
+        double tot;
+        if (grid_sum_last<kPrepBlock>(dot, c.partials, c.counter, &tot) && threadIdx.x == 0) {
+            Scalars* s = c.sc;
+            s->pAp = tot;
+            if (!(tot > 0.0) || !isfinite(tot)) {
+                s->numeric_error = 1u;
+                s->alpha = 0.0;
+            } else {
+                s->alpha = s->rz / tot;
+            }
+        }
+    }
+}
+
+// diag(J^T W J) for Gaussian g from the Gram blocks of its visible views.
+// Gram layout (40 floats): [0,21) upper triangle of the 6x6 geometric block
+// (mu_x, mu_y, A, B, C, o) row-major; [21,39) geometric x colour, index
+// 21 + 3 f + ch; [39] the colour diagonal (same for the three channels).
+__device__ __forceinline__ float gram_quad(const float* gm, const float a[9]) {
+    float v = 0.f;
+    int idx = 0;
+#pragma unroll
+    for (int f = 0; f < 6; ++f)
+#pragma unroll
+        for (int h = f; h < 6; ++h) {
+            const float m = gm[idx++];
+            v += (f == h ? 1.f : 2.f) * m * a[f] * a[h];
+        }
+#pragma unroll
+    for (int f = 0; f < 6; ++f)
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) v += 2.f * gm[21 + 3 * f + ch] * a[f] * a[6 + ch];
+    v += gm[39] * (a[6] * a[6] + a[7] * a[7] + a[8] * a[8]);
+    return v;
+}
+
+__global__ void __launch_bounds__(kPrepBlock) k_prep_diag(Ctx c, float* D) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= c.G) return;
+    const GParams gp = load_gparams(c.params, c.G, g);
+    float sh[3 * kMaxShCoeffs];
+    load_sh(c.params, c.G, c.K, g, sh);
+    float dgeo[11];
+#pragma unroll
+    for (int j = 0; j < 11; ++j) dgeo[j] = 0.f;
+    float dsh[3 * kMaxShCoeffs];
+    for (int k = 0; k < 3 * c.K; ++k) dsh[k] = 0.f;
+    for (int slot = 0; slot < c.nv; ++slot) {
+        const long long i = (long long)slot * c.G + g;
+        const int4 rc = c.rect[i];
+        if (rc.x > rc.y) continue;
+        const CamDev& cam = c.cams[c.views[slot]];
+        Prim P;
+        prim_geometry(gp, cam, c.tiles_x, c.tiles_y, c.tile_w, c.tile_h, P, nullptr, nullptr);
+        prim_features(gp, sh, c.deg, cam, P);
+        float gm[kGramF];
+        const float4* gsrc = reinterpret_cast<const float4*>(c.gram + i * kGramF);
+#pragma unroll
+        for (int k = 0; k < kGramF / 4; ++k) {
+            const float4 q = gsrc[k];
+            gm[4 * k] = q.x; gm[4 * k + 1] = q.y; gm[4 * k + 2] = q.z; gm[4 * k + 3] = q.w;
+        }
+        // geometric parameters: one unit tangent each
+#pragma unroll 1
+        for (int j = 0; j < 11; ++j) {
+            GTan d;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) { d.X[k] = j == k ? 1.f : 0.f; d.ls[k] = j == 3 + k ? 1.f : 0.f; }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) d.q[k] = j == 6 + k ? 1.f : 0.f;
+            d.th = j == 10 ? 1.f : 0.f;
+            float a[9];
+            prim_tangent(P, cam, d, sh, nullptr, c.deg, a);
+            dgeo[j] += gram_quad(gm, a);
+        }
+        // SH coefficient (k, ch) moves only colour ch, by Y_k
+        float Y[kMaxShCoeffs];
+        sh_eval(c.deg, P.dir[0], P.dir[1], P.dir[2], Y);
+        for (int k = 0; k < c.K; ++k)
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch)
+                if (!P.clamped[ch]) dsh[3 * k + ch] += gm[39] * Y[k] * Y[k];
+    }
+    const long long G = c.G;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) D[3 * g + k] = dgeo[k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) D[3 * G + 3 * g + k] = dgeo[3 + k];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) D[6 * G + 4 * g + k] = dgeo[6 + k];
+    D[10 * G + g] = dgeo[10];
+    for (int k = 0; k < 3 * c.K; ++k) D[11 * G + (long long)g * c.K * 3 + k] = dsh[k];
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+void launch_sample(const Ctx& c, long long lm_step, unsigned long long seed, cudaStream_t st) {
+    const int n = c.nv * c.T;
+    LMRS_LAUNCH(k_sample, (n + 127) / 128, 128, 0, st, c, lm_step, seed);
+}
+
+void launch_prep_fwd(const Ctx& c, cudaStream_t st) {
+    const long long n = (long long)c.nv * c.G;
+    LMRS_LAUNCH(k_prep_fwd, (unsigned)((n + 127) / 128), 128, 0, st, c);
+}
+
+void launch_prep_jvp(const Ctx& c, const float* v, float* p_update, const float* z, cudaStream_t st) {
+    LMRS_LAUNCH(k_prep_jvp, (c.G + 127) / 128, 128, 0, st, c, v, p_update, z);
+}
+
+void launch_prep_vjp(const Ctx& c, float* g, const float* v, const float* D, bool dot, cudaStream_t st) {
+    int grid = (c.G + kPrepBlock - 1) / kPrepBlock;
+    if (dot) {
+        if (grid > kMaxPartials) grid = kMaxPartials;
+        LMRS_LAUNCH(k_prep_vjp<true>, grid, kPrepBlock, 0, st, c, g, v, D);
+    } else {
+        LMRS_LAUNCH(k_prep_vjp<false>, grid, kPrepBlock, 0, st, c, g, v, D);
+    }
+}
+
+void launch_prep_diag(const Ctx& c, float* D, cudaStream_t st) {
+    LMRS_LAUNCH(k_prep_diag, (c.G + kPrepBlock - 1) / kPrepBlock, kPrepBlock, 0, st, c, D);
+}
+
+}  // namespace lmrs

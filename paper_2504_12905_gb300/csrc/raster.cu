@@ -1,0 +1,423 @@
+// Rasterisation kernels of the LM-RS hot path.  One warp handles one work
+// item: up to 32 sampled pixels of one (view, tile) (Sec. 4.4: per-tile
+// stratified samples), front to back over the tile's depth-sorted list
+// (Eq. 4, Alg. 2).  Gaussian records are staged 32 at a time into the warp's
+// shared-memory slice with coalesced id loads and 16-byte record loads.
+//
+//   k_fwd_samples  render + residual (Eq. 7) + per-sample caches
+//   k_full         full frames (all pixels)
+//   k_jvp          u = J v, dual-number style tangent compositing (Alg. 3)
+//   k_vjp          back-scatter of a per-sample cotangent (App. A, J^T v
+//                  kernel, first launch) using the cached final colour and
+//                  termination position
+//   k_jtj          fused: JVP pass then VJP pass of w * (J v) per work item
+//   k_gram         per-pair Gram blocks of the per-sample feature gradients
+//                  (App. A, Diag kernel; completed by k_prep_diag)
+// Back-scatter: per Gaussian, the 32 lanes' contributions are summed with a
+// warp reduce-scatter and one lane per value issues a single atomic add into
+// the per-(view, Gaussian) slot.
+#include "common.cuh"
+#include "reduce.cuh"
+
+namespace lmrs {
+
+constexpr int kRasterWarps = 4;
+constexpr int kRasterBlock = kRasterWarps * kWarp;
+
+struct Pix {
+    int vt, slot, tile;
+    long long si;
+    bool active;
+    float pcx, pcy;
+    int px, py;
+    float w;
+};
+
+__device__ __forceinline__ void setup_item(const Ctx& c, int item, Pix& p) {
+    const int lane = threadIdx.x & 31;
+    const int2 wk = c.work[item];
+    p.vt = wk.x;
+    p.slot = p.vt / c.T;
+    p.tile = p.vt - p.slot * c.T;
+    const int tx = p.tile % c.tiles_x, ty = p.tile / c.tiles_x;
+    const int vw = min(c.tile_w, c.W - tx * c.tile_w);
+    const int s0 = c.tile_off[p.vt], s1 = c.tile_off[p.vt + 1];
+    p.si = (long long)s0 + wk.y + lane;
+    p.active = p.si < s1;
+    const int o = p.active ? c.off[p.si] : 0;
+    p.px = tx * c.tile_w + o % vw;
+    p.py = ty * c.tile_h + o / vw;
+    p.pcx = p.px + 0.5f;
+    p.pcy = p.py + 0.5f;
+    p.w = c.wtile[p.vt];
+}
+
+template <int NF4>
+__device__ __forceinline__ int stage_batch(const Ctx& c, int slot, int b, int end, float4 (*s_rec)[kRecF4],
+                                           unsigned* s_id) {
+    const int lane = threadIdx.x & 31;
+    const int k = b + lane;
+    if (k < end) {
+        const unsigned id = c.ids[k];
+        const float4* r = c.rec + ((long long)slot * c.G + id) * kRecF4;
+#pragma unroll
+        for (int q = 0; q < NF4; ++q) s_rec[lane][q] = r[q];
+        s_id[lane] = id;
+    }
+    __syncwarp();
+    return min(32, end - b);
+}
+
+// Front-to-back pass.  With kTan also the tangent of the colour (Alg. 3).
+// ncons = list entries consumed before termination (the whole list if none).
+template <bool kTan>
+__device__ __forceinline__ void forward_pass(const Ctx& c, const Pix& p, int2 rg, float4 (*s_rec)[kRecF4],
+                                             unsigned* s_id, float C[3], float& T, float dC[3], int& ncons) {
+    T = 1.f;
+    float dT = 0.f;
+    C[0] = C[1] = C[2] = 0.f;
+    dC[0] = dC[1] = dC[2] = 0.f;
+    bool done = !p.active;
+    ncons = rg.y - rg.x;
+    for (int b = rg.x; b < rg.y; b += 32) {
+        if (__all_sync(kFull, done)) break;
+        const int n = stage_batch<kTan ? 6 : 3>(c, p.slot, b, rg.y, s_rec, s_id);
+        for (int j = 0; j < n; ++j) {
+            if (done) continue;
+            const float4 r0 = s_rec[j][0], r1 = s_rec[j][1];
+            const float dx = r0.x - p.pcx, dy = r0.y - p.pcy;
+            const float power = -0.5f * (r0.z * dx * dx + r1.x * dy * dy) - r0.w * dx * dy;
+            const float gval = __expf(power);
+            const float raw = r1.y * gval;
+            const float alpha = fminf(kAlphaMax, raw);
+            if (alpha < kAlphaMin) continue;
+            const float Tn = T * (1.f - alpha);
+            if (Tn < kTMin) {
+                done = true;
+                ncons = b + j - rg.x;
+                continue;
+            }
+            const float col2 = s_rec[j][2].x;
+            const float wgt = alpha * T;
+            if (kTan) {
+                const float4 t0 = s_rec[j][3], t1 = s_rec[j][4];
+                const float dcol2 = s_rec[j][5].x;
+                float dalpha = 0.f;
+                if (raw <= kAlphaMax) {
+                    const float dpow = -0.5f * (t0.z * dx * dx + t1.x * dy * dy) - t0.w * dx * dy -
+                                       (r0.z * dx + r0.w * dy) * t0.x - (r0.w * dx + r1.x * dy) * t0.y;
+                    dalpha = t1.y * gval + raw * dpow;
+                }
+                const float dw = dalpha * T + alpha * dT;
+                dC[0] += t1.z * wgt + r1.z * dw;
+                dC[1] += t1.w * wgt + r1.w * dw;
+                dC[2] += dcol2 * wgt + col2 * dw;
+                dT = dT * (1.f - alpha) - T * dalpha;
+            }
+            C[0] += r1.z * wgt;
+            C[1] += r1.w * wgt;
+            C[2] += col2 * wgt;
+            T = Tn;
+        }
+        __syncwarp();
+    }
+}
+
+// Back-scatter of the cotangent ub of each lane's colour into the 9 feature
+// cotangents of every contributing Gaussian (reverse mode through Eq. 4 with
+// the final colour Cf known: dC/dalpha_n = T_n c_n - (Cf - C_<=n)/(1 - alpha_n)).
+__device__ __forceinline__ void backward_pass(const Ctx& c, const Pix& p, int2 rg, float4 (*s_rec)[kRecF4],
+                                              unsigned* s_id, const float ub[3], const float Cf[3], int ncons) {
+    const int lane = threadIdx.x & 31;
+    const float S_tot = ub[0] * Cf[0] + ub[1] * Cf[1] + ub[2] * Cf[2];
+    float s = 0.f, T = 1.f;
+    const int lane_end = p.active ? rg.x + ncons : rg.x;
+    int warp_end = lane_end;
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) warp_end = max(warp_end, __shfl_xor_sync(kFull, warp_end, m));
+    float* cot_base = c.cot + (long long)p.slot * c.G * kCotF;
+    for (int b = rg.x; b < warp_end; b += 32) {
+        const int n = stage_batch<3>(c, p.slot, b, warp_end, s_rec, s_id);
+        for (int j = 0; j < n; ++j) {
+            float v[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) v[q] = 0.f;
+            bool contrib = false;
+            if (b + j < lane_end) {
+                const float4 r0 = s_rec[j][0], r1 = s_rec[j][1];
+                const float dx = r0.x - p.pcx, dy = r0.y - p.pcy;
+                const float power = -0.5f * (r0.z * dx * dx + r1.x * dy * dy) - r0.w * dx * dy;
+                const float gval = __expf(power);
+                const float raw = r1.y * gval;
+                const float alpha = fminf(kAlphaMax, raw);
+                if (alpha >= kAlphaMin) {
+                    contrib = true;
+                    const float col2 = s_rec[j][2].x;
+                    const float ucol = ub[0] * r1.z + ub[1] * r1.w + ub[2] * col2;
+                    const float wgt = alpha * T;
+                    s += ucol * wgt;
+                    const float abar = T * ucol - (S_tot - s) / (1.f - alpha);
+                    v[6] = ub[0] * wgt;
+                    v[7] = ub[1] * wgt;
+                    v[8] = ub[2] * wgt;
+                    if (raw <= kAlphaMax) {
+                        const float pbar = abar * raw;
+                        v[0] = -pbar * (r0.z * dx + r0.w * dy);
+                        v[1] = -pbar * (r0.w * dx + r1.x * dy);
+                        v[2] = -0.5f * pbar * dx * dx;
+                        v[3] = -pbar * dx * dy;
+                        v[4] = -0.5f * pbar * dy * dy;
+                        v[5] = abar * gval;
+                    }
+                    T *= 1.f - alpha;
+                }
+            }
+            if (__any_sync(kFull, contrib)) {
+                warp_reduce_scatter<16>(v);
+                const int idx = lane >> 1;
+                if (!(lane & 1) && idx < 9) atomicAdd(cot_base + (long long)s_id[j] * kCotF + idx, v[0]);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+__device__ __forceinline__ void load_cache(const Ctx& c, long long si, float Cf[3], int& ncons) {
+    if (c.cache_bf16) {
+        Cf[0] = __bfloat162float(c.cacheCh[3 * si]);
+        Cf[1] = __bfloat162float(c.cacheCh[3 * si + 1]);
+        Cf[2] = __bfloat162float(c.cacheCh[3 * si + 2]);
+    } else {
+        Cf[0] = c.cacheC[3 * si];
+        Cf[1] = c.cacheC[3 * si + 1];
+        Cf[2] = c.cacheC[3 * si + 2];
+    }
+    ncons = c.cacheN[si];
+}
+
+#define LMRS_RASTER_PROLOGUE                                                    \
+    __shared__ float4 s_rec_all[kRasterWarps][32][kRecF4];                      \
+    __shared__ unsigned s_id_all[kRasterWarps][32];                             \
+    const int wid = threadIdx.x >> 5;                                           \
+    const int item = blockIdx.x * kRasterWarps + wid;                           \
+    if (item >= c.nwork) return;                                                \
+    float4(*s_rec)[kRecF4] = s_rec_all[wid];                                    \
+    unsigned* s_id = s_id_all[wid];                                             \
+    Pix p;                                                                      \
+    setup_item(c, item, p);                                                     \
+    const int2 rg = c.ranges[p.vt];
+
+__global__ void __launch_bounds__(kRasterBlock) k_fwd_samples(Ctx c) {
+    LMRS_RASTER_PROLOGUE
+    float C[3], T, dC[3];
+    int ncons;
+    forward_pass<false>(c, p, rg, s_rec, s_id, C, T, dC, ncons);
+    double num = 0.0, den = 0.0;
+    if (p.active) {
+        const long long si = p.si;
+        float r[3];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            float tgt = 0.f;
+            if (c.targets) {
+                const int cam = c.views[p.slot];
+                tgt = c.targets[(((long long)cam * c.H + p.py) * c.W + p.px) * 3 + ch];
+            }
+            r[ch] = C[ch] - tgt;
+            c.resid[3 * si + ch] = r[ch];
+        }
+        if (c.cache_bf16) {
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) c.cacheCh[3 * si + ch] = __float2bfloat16_rn(C[ch]);
+            c.cacheTh[si] = __float2bfloat16_rn(T);
+        } else {
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) c.cacheC[3 * si + ch] = C[ch];
+            c.cacheT[si] = T;
+        }
+        c.cacheN[si] = ncons;
+        num = (double)p.w * ((double)r[0] * r[0] + (double)r[1] * r[1] + (double)r[2] * r[2]);
+        den = 3.0 * p.w;
+    }
+    num = warp_sum(num);
+    den = warp_sum(den);
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&c.sc->loss_num, num);
+        atomicAdd(&c.sc->loss_den, den);
+    }
+}
+
+__global__ void __launch_bounds__(kRasterBlock) k_jvp(Ctx c, float* u) {
+    LMRS_RASTER_PROLOGUE
+    float C[3], T, dC[3];
+    int ncons;
+    forward_pass<true>(c, p, rg, s_rec, s_id, C, T, dC, ncons);
+    if (p.active) {
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) u[3 * p.si + ch] = dC[ch];
+    }
+}
+
+__global__ void __launch_bounds__(kRasterBlock) k_vjp(Ctx c, const float* u) {
+    LMRS_RASTER_PROLOGUE
+    float ub[3] = {0.f, 0.f, 0.f}, Cf[3] = {0.f, 0.f, 0.f};
+    int ncons = 0;
+    if (p.active) {
+        load_cache(c, p.si, Cf, ncons);
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) ub[ch] = u ? u[3 * p.si + ch] : p.w * c.resid[3 * p.si + ch];
+    }
+    backward_pass(c, p, rg, s_rec, s_id, ub, Cf, ncons);
+}
+
+__global__ void __launch_bounds__(kRasterBlock) k_jtj(Ctx c) {
+    LMRS_RASTER_PROLOGUE
+    float C[3], T, dC[3];
+    int ncons;
+    forward_pass<true>(c, p, rg, s_rec, s_id, C, T, dC, ncons);
+    const float ub[3] = {p.w * dC[0], p.w * dC[1], p.w * dC[2]};
+    backward_pass(c, p, rg, s_rec, s_id, ub, C, ncons);
+}
+
+// Gram blocks: per contributing (sample, Gaussian), with e = d alpha /
+// d(mu_x, mu_y, A, B, C, o), h_ch = d C_ch / d alpha and q = alpha T:
+//   [0,21)   w (sum_ch h_ch^2) e e^T   (upper triangle, row-major)
+//   [21,39)  w q h_ch e_f              (index 21 + 3 f + ch)
+//   [39]     w q^2
+__global__ void __launch_bounds__(kRasterBlock) k_gram(Ctx c) {
+    LMRS_RASTER_PROLOGUE
+    const int lane = threadIdx.x & 31;
+    float Cf[3] = {0.f, 0.f, 0.f};
+    int ncons = 0;
+    if (p.active) load_cache(c, p.si, Cf, ncons);
+    const int lane_end = p.active ? rg.x + ncons : rg.x;
+    int warp_end = lane_end;
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) warp_end = max(warp_end, __shfl_xor_sync(kFull, warp_end, m));
+    float acc[3] = {0.f, 0.f, 0.f}, T = 1.f;
+    float* gbase = c.gram + (long long)p.slot * c.G * kGramF;
+    for (int b = rg.x; b < warp_end; b += 32) {
+        const int n = stage_batch<3>(c, p.slot, b, warp_end, s_rec, s_id);
+        for (int j = 0; j < n; ++j) {
+            float v[32], v2[16];
+#pragma unroll
+            for (int q = 0; q < 32; ++q) v[q] = 0.f;
+#pragma unroll
+            for (int q = 0; q < 16; ++q) v2[q] = 0.f;
+            bool contrib = false;
+            if (b + j < lane_end) {
+                const float4 r0 = s_rec[j][0], r1 = s_rec[j][1];
+                const float dx = r0.x - p.pcx, dy = r0.y - p.pcy;
+                const float power = -0.5f * (r0.z * dx * dx + r1.x * dy * dy) - r0.w * dx * dy;
+                const float gval = __expf(power);
+                const float raw = r1.y * gval;
+                const float alpha = fminf(kAlphaMax, raw);
+                if (alpha >= kAlphaMin) {
+                    contrib = true;
+                    const float col[3] = {r1.z, r1.w, s_rec[j][2].x};
+                    const float q = alpha * T;
+                    float h[3];
+#pragma unroll
+                    for (int ch = 0; ch < 3; ++ch) {
+                        acc[ch] += col[ch] * q;
+                        h[ch] = T * col[ch] - (Cf[ch] - acc[ch]) / (1.f - alpha);
+                    }
+                    float e[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                    if (raw <= kAlphaMax) {
+                        e[0] = -raw * (r0.z * dx + r0.w * dy);
+                        e[1] = -raw * (r0.w * dx + r1.x * dy);
+                        e[2] = -0.5f * raw * dx * dx;
+                        e[3] = -raw * dx * dy;
+                        e[4] = -0.5f * raw * dy * dy;
+                        e[5] = gval;
+                    }
+                    const float H2 = p.w * (h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
+                    float vals[40];
+                    int idx = 0;
+#pragma unroll
+                    for (int f = 0; f < 6; ++f)
+#pragma unroll
+                        for (int g = f; g < 6; ++g) vals[idx++] = H2 * e[f] * e[g];
+#pragma unroll
+                    for (int f = 0; f < 6; ++f)
+#pragma unroll
+                        for (int ch = 0; ch < 3; ++ch) vals[21 + 3 * f + ch] = p.w * q * h[ch] * e[f];
+                    vals[39] = p.w * q * q;
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) v[k] = vals[k];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) v2[k] = vals[32 + k];
+                    T *= 1.f - alpha;
+                }
+            }
+            if (__any_sync(kFull, contrib)) {
+                float* dst = gbase + (long long)s_id[j] * kGramF;
+                warp_reduce_scatter<32>(v);
+                atomicAdd(dst + lane, v[0]);
+                warp_reduce_scatter<16>(v2);
+                const int idx = lane >> 1;
+                if (!(lane & 1) && idx < 8) atomicAdd(dst + 32 + idx, v2[0]);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Full frames: one block per (slot, tile), one warp per 32 pixels.
+__global__ void __launch_bounds__(256) k_full(Ctx c, float* images) {
+    __shared__ float4 s_rec_all[8][32][kRecF4];
+    __shared__ unsigned s_id_all[8][32];
+    const int vt = blockIdx.x;
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int slot = vt / c.T, tile = vt - slot * c.T;
+    const int tx = tile % c.tiles_x, ty = tile / c.tiles_x;
+    const int vw = min(c.tile_w, c.W - tx * c.tile_w), vh = min(c.tile_h, c.H - ty * c.tile_h);
+    const int nvalid = vw * vh;
+    const int first = wid * 32;
+    if (first >= nvalid) return;
+    Pix p;
+    p.vt = vt;
+    p.slot = slot;
+    p.tile = tile;
+    const int o = first + lane;
+    p.active = o < nvalid;
+    p.si = 0;
+    p.px = tx * c.tile_w + (p.active ? o % vw : 0);
+    p.py = ty * c.tile_h + (p.active ? o / vw : 0);
+    p.pcx = p.px + 0.5f;
+    p.pcy = p.py + 0.5f;
+    p.w = 1.f;
+    const int2 rg = c.ranges[vt];
+    float C[3], T, dC[3];
+    int ncons;
+    forward_pass<false>(c, p, rg, s_rec_all[wid], s_id_all[wid], C, T, dC, ncons);
+    if (p.active) {
+        float* dst = images + (((long long)slot * c.H + p.py) * c.W + p.px) * 3;
+        dst[0] = C[0];
+        dst[1] = C[1];
+        dst[2] = C[2];
+    }
+}
+
+static unsigned raster_grid(const Ctx& c) { return (unsigned)((c.nwork + kRasterWarps - 1) / kRasterWarps); }
+
+void launch_raster_fwd_samples(const Ctx& c, cudaStream_t st) {
+    if (c.nwork > 0) LMRS_LAUNCH(k_fwd_samples, raster_grid(c), kRasterBlock, 0, st, c);
+}
+void launch_raster_full(const Ctx& c, float* images, cudaStream_t st) {
+    LMRS_LAUNCH(k_full, (unsigned)(c.nv * c.T), 256, 0, st, c, images);
+}
+void launch_raster_jvp(const Ctx& c, float* u, cudaStream_t st) {
+    if (c.nwork > 0) LMRS_LAUNCH(k_jvp, raster_grid(c), kRasterBlock, 0, st, c, u);
+}
+void launch_raster_vjp(const Ctx& c, const float* u, cudaStream_t st) {
+    if (c.nwork > 0) LMRS_LAUNCH(k_vjp, raster_grid(c), kRasterBlock, 0, st, c, u);
+}
+void launch_raster_jtj(const Ctx& c, cudaStream_t st) {
+    if (c.nwork > 0) LMRS_LAUNCH(k_jtj, raster_grid(c), kRasterBlock, 0, st, c);
+}
+void launch_raster_gram(const Ctx& c, cudaStream_t st) {
+    if (c.nwork > 0) LMRS_LAUNCH(k_gram, raster_grid(c), kRasterBlock, 0, st, c);
+}
+
+}  // namespace lmrs

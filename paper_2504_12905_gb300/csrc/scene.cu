@@ -1,0 +1,665 @@
+// C-ABI of liblmrs (include/lmrs.h): scene state, buffer management and the
+// orchestration of the kernels of one LM step (Alg. 1).
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace lmrs {
+static std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace lmrs
+
+using namespace lmrs;
+
+namespace {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+    template <class T>
+    T* as() const { return static_cast<T*>(p); }
+};
+
+}  // namespace
+
+struct lmrs_scene {
+    lmrs_config cfg;
+    int G = 0, deg = 0, K = 0, Pg = 0;
+    long long P = 0;
+    int n_cams = 0, W = 0, H = 0, tiles_x = 0, tiles_y = 0, T = 0;
+    cudaStream_t st = nullptr;
+    std::string err;
+    const float* targets = nullptr;
+    // device state
+    DevBuf params, cams, views;
+    DevBuf rec, rect, depth, cnt, cot, gram;
+    DevBuf keys, ids, keys_alt, ids_alt, ranges, scan_tmp, radix_tmp, total;
+    DevBuf tile_off, off, wtile, work;
+    DevBuf resid, cacheC, cacheT, cacheCh, cacheTh, cacheN;
+    DevBuf x, r, z, p, Ap, minv, D, b, stage_a, stage_b;
+    DevBuf sc, partials, counter;
+    // host state of the current step
+    std::vector<int> views_h;
+    int nv = 0;
+    long long step = 0, S = 0, npairs = 0;
+    int nwork = 0;
+    int layout_nv = -1;
+    std::vector<int> tile_off_h;
+    bool preprocessed = false, rendered = false, have_D = false;
+
+    Ctx ctx() const {
+        Ctx c;
+        std::memset(&c, 0, sizeof(c));
+        c.G = G; c.deg = deg; c.K = K; c.Pg = Pg; c.P = P;
+        c.nv = nv; c.W = W; c.H = H; c.tiles_x = tiles_x; c.tiles_y = tiles_y; c.T = T;
+        c.tile_w = cfg.tile_w; c.tile_h = cfg.tile_h;
+        c.cache_bf16 = cfg.cache_bf16;
+        c.damping_mode = cfg.damping_mode;
+        c.lambda = (float)cfg.lambda;
+        c.params = params.as<float>();
+        c.cams = cams.as<CamDev>();
+        c.views = views.as<int>();
+        c.targets = targets;
+        c.rec = rec.as<float4>();
+        c.rect = rect.as<int4>();
+        c.depth = depth.as<unsigned int>();
+        c.cnt = cnt.as<unsigned long long>();
+        c.cot = cot.as<float>();
+        c.gram = gram.as<float>();
+        c.keys = keys.as<unsigned long long>();
+        c.ids = ids.as<unsigned int>();
+        c.npairs = npairs;
+        c.ranges = ranges.as<int2>();
+        c.tile_off = tile_off.as<int>();
+        c.off = off.as<unsigned char>();
+        c.wtile = wtile.as<float>();
+        c.S = S;
+        c.work = work.as<int2>();
+        c.nwork = nwork;
+        c.resid = resid.as<float>();
+        c.cacheC = cacheC.as<float>();
+        c.cacheT = cacheT.as<float>();
+        c.cacheCh = cacheCh.as<__nv_bfloat16>();
+        c.cacheTh = cacheTh.as<__nv_bfloat16>();
+        c.cacheN = cacheN.as<int>();
+        c.sc = sc.as<Scalars>();
+        c.partials = partials.as<double>();
+        c.counter = counter.as<unsigned int>();
+        return c;
+    }
+};
+
+namespace {
+
+const char* kStatusStr[] = {"LMRS_OK", "LMRS_ERR_INVALID_ARG", "LMRS_ERR_OOM", "LMRS_ERR_CUDA",
+                            "LMRS_ERR_NOT_PREPROCESSED", "LMRS_ERR_NUMERIC", "LMRS_ERR_TIMEOUT", "LMRS_ERR_BUDGET"};
+
+lmrs_status fail(lmrs_scene* s, lmrs_status code, const std::string& msg) {
+    if (s) s->err = msg;
+    return code;
+}
+
+lmrs_status cuda_fail(lmrs_scene* s, cudaError_t e, const char* what) {
+    return fail(s, e == cudaErrorMemoryAllocation ? LMRS_ERR_OOM : LMRS_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(s, call)                                          \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail((s), e_, #call); \
+    } while (0)
+
+#define CHECK_LAUNCH(s)                                               \
+    do {                                                              \
+        cudaError_t e_ = cudaGetLastError();                          \
+        if (e_ != cudaSuccess) return cuda_fail((s), e_, "kernel launch"); \
+    } while (0)
+
+#define TRY(expr)                        \
+    do {                                 \
+        lmrs_status st_ = (expr);        \
+        if (st_ != LMRS_OK) return st_;  \
+    } while (0)
+
+lmrs_status ensure(lmrs_scene* s, DevBuf& b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (b.cap >= bytes) return LMRS_OK;
+    if (b.p) {
+        cudaError_t e = cudaFree(b.p);
+        b.p = nullptr;
+        b.cap = 0;
+        if (e != cudaSuccess) return cuda_fail(s, e, "cudaFree");
+    }
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        cudaGetLastError();
+        return cuda_fail(s, e, "cudaMalloc");
+    }
+    b.cap = bytes;
+    return LMRS_OK;
+}
+
+void release(DevBuf& b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+}
+
+bool is_device_ptr(const void* ptr) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+CamDev make_cam(const lmrs_camera& c) {
+    CamDev d;
+    std::memset(&d, 0, sizeof(d));
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) d.R[3 * i + j] = c.world_to_cam[4 * i + j];
+        d.t[i] = c.world_to_cam[4 * i + 3];
+    }
+    d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy; d.znear = c.znear;
+    // FP32 list decisions: the clamp limits in this exact operation order
+    d.limx = 1.3f * ((0.5f * (float)c.width) / c.fx);
+    d.limy = 1.3f * ((0.5f * (float)c.height) / c.fy);
+    for (int j = 0; j < 3; ++j) {
+        double v = 0.0;
+        for (int k = 0; k < 3; ++k) v -= (double)c.world_to_cam[4 * k + j] * (double)c.world_to_cam[4 * k + 3];
+        d.centre[j] = (float)v;  // camera centre -R^T t
+    }
+    d.W = c.width;
+    d.H = c.height;
+    return d;
+}
+
+int samples_in_tile(const lmrs_config& cfg, int n_valid) {
+    int k = cfg.samples_per_tile > 0 ? cfg.samples_per_tile : (int)std::floor(cfg.sample_frac * n_valid + 0.5);
+    return std::max(1, std::min(k, n_valid));
+}
+
+// Sample layout for nv slots (depends on the image size and config only).
+lmrs_status build_layout(lmrs_scene* s) {
+    if (s->layout_nv == s->nv) return LMRS_OK;
+    const int nT = s->nv * s->T;
+    std::vector<int> toff(nT + 1, 0);
+    std::vector<float> w(nT);
+    std::vector<int2> work;
+    for (int slot = 0; slot < s->nv; ++slot)
+        for (int t = 0; t < s->T; ++t) {
+            const int tx = t % s->tiles_x, ty = t / s->tiles_x;
+            const int vw = std::min(s->cfg.tile_w, s->W - tx * s->cfg.tile_w);
+            const int vh = std::min(s->cfg.tile_h, s->H - ty * s->cfg.tile_h);
+            const int n = vw * vh;
+            const int k = samples_in_tile(s->cfg, n);
+            const int vt = slot * s->T + t;
+            toff[vt + 1] = toff[vt] + k;
+            w[vt] = s->cfg.weight_mode == 1 ? (float)((double)n / (double)k) : 1.f;
+            for (int j = 0; j < k; j += 32) work.push_back(make_int2(vt, j));
+        }
+    s->S = toff[nT];
+    s->nwork = (int)work.size();
+    TRY(ensure(s, s->tile_off, sizeof(int) * (nT + 1)));
+    TRY(ensure(s, s->wtile, sizeof(float) * nT));
+    TRY(ensure(s, s->work, sizeof(int2) * std::max<size_t>(work.size(), 1)));
+    TRY(ensure(s, s->off, (size_t)s->S));
+    TRY(ensure(s, s->resid, sizeof(float) * 3 * s->S));
+    TRY(ensure(s, s->cacheC, sizeof(float) * 3 * s->S));
+    TRY(ensure(s, s->cacheT, sizeof(float) * s->S));
+    TRY(ensure(s, s->cacheCh, sizeof(__nv_bfloat16) * 3 * s->S));
+    TRY(ensure(s, s->cacheTh, sizeof(__nv_bfloat16) * s->S));
+    TRY(ensure(s, s->cacheN, sizeof(int) * s->S));
+    // pageable sources: the copies are staged before the calls return
+    CK(s, cudaMemcpyAsync(s->tile_off.p, toff.data(), sizeof(int) * (nT + 1), cudaMemcpyHostToDevice, s->st));
+    CK(s, cudaMemcpyAsync(s->wtile.p, w.data(), sizeof(float) * nT, cudaMemcpyHostToDevice, s->st));
+    if (!work.empty())
+        CK(s, cudaMemcpyAsync(s->work.p, work.data(), sizeof(int2) * work.size(), cudaMemcpyHostToDevice, s->st));
+    CK(s, cudaStreamSynchronize(s->st));
+    s->tile_off_h = toff;
+    s->layout_nv = s->nv;
+    return LMRS_OK;
+}
+
+lmrs_status check_scene(lmrs_scene* s) { return s ? LMRS_OK : LMRS_ERR_INVALID_ARG; }
+
+lmrs_status need_pre(lmrs_scene* s) {
+    if (!s->preprocessed) return fail(s, LMRS_ERR_NOT_PREPROCESSED, "lmrs_preprocess has not been called");
+    return LMRS_OK;
+}
+lmrs_status need_render(lmrs_scene* s) {
+    TRY(need_pre(s));
+    if (!s->rendered) return fail(s, LMRS_ERR_NOT_PREPROCESSED, "lmrs_render has not been called");
+    return LMRS_OK;
+}
+
+lmrs_status do_jtj_diag(lmrs_scene* s) {
+    const size_t pairs = (size_t)s->nv * s->G;
+    TRY(ensure(s, s->gram, sizeof(float) * kGramF * pairs));
+    CK(s, cudaMemsetAsync(s->gram.p, 0, sizeof(float) * kGramF * pairs, s->st));
+    Ctx c = s->ctx();
+    launch_raster_gram(c, s->st);
+    launch_prep_diag(c, s->D.as<float>(), s->st);
+    CHECK_LAUNCH(s);
+    s->have_D = true;
+    return LMRS_OK;
+}
+
+// (J^T W J + lambda damp) v -> out, device pointers.
+lmrs_status do_jtjv(lmrs_scene* s, const float* v, float* out) {
+    Ctx c = s->ctx();
+    launch_prep_jvp(c, v, nullptr, nullptr, s->st);
+    launch_raster_jtj(c, s->st);
+    launch_prep_vjp(c, out, v, s->D.as<float>(), false, s->st);
+    CHECK_LAUNCH(s);
+    return LMRS_OK;
+}
+
+lmrs_status do_cg(lmrs_scene* s, const float* b, float* x, int iters) {
+    Ctx c = s->ctx();
+    float* r = s->r.as<float>();
+    float* z = s->z.as<float>();
+    float* p = s->p.as<float>();
+    float* Ap = s->Ap.as<float>();
+    float* minv = s->minv.as<float>();
+    const float* D = s->D.as<float>();
+    launch_zero_scalars(c, s->st);
+    launch_precond(c, D, minv, s->st);
+    launch_cg_init(c, b, minv, x, r, z, p, s->st);
+    for (int it = 0; it < iters; ++it) {
+        launch_prep_jvp(c, nullptr, p, z, s->st);        // p = z + beta p; tangents of p
+        launch_raster_jtj(c, s->st);                     // J^T W J p into the cotangent slots
+        launch_prep_vjp(c, Ap, p, D, true, s->st);       // Ap (+ damping), p^T A p, alpha
+        launch_cg_update(c, it, p, Ap, minv, x, r, z, s->st);  // x, r, z, beta
+    }
+    CHECK_LAUNCH(s);
+    return LMRS_OK;
+}
+
+lmrs_status read_scalars(lmrs_scene* s, Scalars* h) {
+    CK(s, cudaMemcpyAsync(h, s->sc.p, sizeof(Scalars), cudaMemcpyDeviceToHost, s->st));
+    CK(s, cudaStreamSynchronize(s->st));
+    return LMRS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lmrs_status lmrs_config_default(lmrs_config* cfg) {
+    if (!cfg) return LMRS_ERR_INVALID_ARG;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->sh_degree = 0;
+    cfg->tile_w = 16;
+    cfg->tile_h = 16;
+    cfg->sample_frac = 1.0;
+    cfg->samples_per_tile = 0;
+    cfg->weight_mode = 0;
+    cfg->lambda = 0.1;
+    cfg->damping_mode = 1;
+    cfg->cg_iters = 8;
+    cfg->lr_warm = 0.05;
+    cfg->lr_cap = 0.2;
+    cfg->color_bound = 1.0;
+    cfg->warm_iters = 10;
+    cfg->cache_bf16 = 0;
+    cfg->seed = 0;
+    return LMRS_OK;
+}
+
+lmrs_status lmrs_scene_create(const lmrs_config* cfg, int64_t n_gauss, const float* params,
+                              const lmrs_camera* cams_host, int32_t n_cams, const float* targets_dev,
+                              void* cuda_stream, lmrs_scene** out) {
+    if (!out) return LMRS_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!cfg || !params || !cams_host || n_cams <= 0 || n_gauss <= 0 || n_gauss > (1ll << 30))
+        return LMRS_ERR_INVALID_ARG;
+    if (cfg->sh_degree < 0 || cfg->sh_degree > 3 || cfg->tile_w <= 0 || cfg->tile_h <= 0 ||
+        cfg->tile_w * cfg->tile_h > 256 || !(cfg->sample_frac > 0.0) || cfg->cg_iters < 0 ||
+        (cfg->damping_mode != 0 && cfg->damping_mode != 1) || (cfg->weight_mode != 0 && cfg->weight_mode != 1) ||
+        !(cfg->lambda >= 0.0))
+        return LMRS_ERR_INVALID_ARG;
+    for (int i = 0; i < n_cams; ++i)
+        if (cams_host[i].width != cams_host[0].width || cams_host[i].height != cams_host[0].height ||
+            cams_host[i].width <= 0 || cams_host[i].height <= 0 || !(cams_host[i].fx > 0.f) || !(cams_host[i].fy > 0.f))
+            return LMRS_ERR_INVALID_ARG;
+    lmrs_scene* s = new lmrs_scene();
+    s->cfg = *cfg;
+    s->G = (int)n_gauss;
+    s->deg = cfg->sh_degree;
+    s->K = (s->deg + 1) * (s->deg + 1);
+    s->Pg = 11 + 3 * s->K;
+    s->P = (long long)s->G * s->Pg;
+    s->n_cams = n_cams;
+    s->W = cams_host[0].width;
+    s->H = cams_host[0].height;
+    s->tiles_x = (s->W + cfg->tile_w - 1) / cfg->tile_w;
+    s->tiles_y = (s->H + cfg->tile_h - 1) / cfg->tile_h;
+    s->T = s->tiles_x * s->tiles_y;
+    s->st = static_cast<cudaStream_t>(cuda_stream);
+    s->targets = targets_dev;
+    set_sh_constants();
+    lmrs_status rc = LMRS_OK;
+    auto take = [&](DevBuf& b, size_t bytes) {
+        if (rc == LMRS_OK) rc = ensure(s, b, bytes);
+    };
+    const size_t pv = sizeof(float) * (size_t)s->P;
+    take(s->params, pv);
+    for (DevBuf* b : {&s->x, &s->r, &s->z, &s->p, &s->Ap, &s->minv, &s->D, &s->b}) take(*b, pv);
+    take(s->cams, sizeof(CamDev) * n_cams);
+    take(s->sc, sizeof(Scalars));
+    take(s->partials, sizeof(double) * kMaxPartials);
+    take(s->counter, sizeof(unsigned int) * 4);
+    take(s->total, sizeof(unsigned long long) * 2);
+    if (rc != LMRS_OK) {
+        lmrs_scene_destroy(s);
+        return rc;
+    }
+    std::vector<CamDev> cd(n_cams);
+    for (int i = 0; i < n_cams; ++i) cd[i] = make_cam(cams_host[i]);
+    cudaError_t e = cudaMemcpy(s->cams.p, cd.data(), sizeof(CamDev) * n_cams, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(s->params.p, params, pv, cudaMemcpyDefault);
+    if (e == cudaSuccess) e = cudaMemset(s->counter.p, 0, sizeof(unsigned int) * 4);
+    if (e == cudaSuccess) e = cudaMemset(s->sc.p, 0, sizeof(Scalars));
+    if (e == cudaSuccess) e = cudaMemset(s->D.p, 0, pv);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        lmrs_scene_destroy(s);
+        return e == cudaErrorMemoryAllocation ? LMRS_ERR_OOM : LMRS_ERR_CUDA;
+    }
+    *out = s;
+    return LMRS_OK;
+}
+
+lmrs_status lmrs_scene_destroy(lmrs_scene* s) {
+    if (!s) return LMRS_ERR_INVALID_ARG;
+    if (s->st) cudaStreamSynchronize(s->st);
+    for (DevBuf* b : {&s->params, &s->cams, &s->views, &s->rec, &s->rect, &s->depth, &s->cnt, &s->cot, &s->gram,
+                      &s->keys, &s->ids, &s->keys_alt, &s->ids_alt, &s->ranges, &s->scan_tmp, &s->radix_tmp,
+                      &s->total, &s->tile_off, &s->off, &s->wtile, &s->work, &s->resid, &s->cacheC, &s->cacheT,
+                      &s->cacheCh, &s->cacheTh, &s->cacheN, &s->x, &s->r, &s->z, &s->p, &s->Ap, &s->minv, &s->D,
+                      &s->b, &s->stage_a, &s->stage_b, &s->sc, &s->partials, &s->counter})
+        release(*b);
+    delete s;
+    return LMRS_OK;
+}
+
+lmrs_status lmrs_set_params(lmrs_scene* s, const float* src) {
+    TRY(check_scene(s));
+    if (!src) return fail(s, LMRS_ERR_INVALID_ARG, "null source");
+    CK(s, cudaMemcpyAsync(s->params.p, src, sizeof(float) * s->P, cudaMemcpyDefault, s->st));
+    s->preprocessed = s->rendered = s->have_D = false;
+    return LMRS_OK;
+}
+
+lmrs_status lmrs_get_params(lmrs_scene* s, float* dst) {
+    TRY(check_scene(s));
+    if (!dst) return fail(s, LMRS_ERR_INVALID_ARG, "null destination");
+    CK(s, cudaMemcpyAsync(dst, s->params.p, sizeof(float) * s->P, cudaMemcpyDefault, s->st));
+    if (!is_device_ptr(dst)) CK(s, cudaStreamSynchronize(s->st));
+    return LMRS_OK;
+}
+
+lmrs_status lmrs_get_solution(lmrs_scene* s, float* dst) {
+    TRY(check_scene(s));
+    if (!dst) return fail(s, LMRS_ERR_INVALID_ARG, "null destination");
+    CK(s, cudaMemcpyAsync(dst, s->x.p, sizeof(float) * s->P, cudaMemcpyDefault, s->st));
+    if (!is_device_ptr(dst)) CK(s, cudaStreamSynchronize(s->st));
+    return LMRS_OK;
+}
+
+lmrs_status lmrs_preprocess(lmrs_scene* s, const int32_t* view_ids, int32_t n_views, int64_t lm_step) {
+    TRY(check_scene(s));
+    if (!view_ids || n_views <= 0) return fail(s, LMRS_ERR_INVALID_ARG, "no views");
+    for (int i = 0; i < n_views; ++i)
+        if (view_ids[i] < 0 || view_ids[i] >= s->n_cams) return fail(s, LMRS_ERR_INVALID_ARG, "view id out of range");
+    if ((long long)n_views * s->T >= (1ll << 31) || (long long)n_views * s->G >= (1ll << 31))
+        return fail(s, LMRS_ERR_BUDGET, "too many (view, tile) or (view, Gaussian) pairs");
+    s->preprocessed = s->rendered = s->have_D = false;
+    s->views_h.assign(view_ids, view_ids + n_views);
+    s->nv = n_views;
+    s->step = lm_step;
+    const size_t pairs = (size_t)s->nv * s->G;
+    TRY(ensure(s, s->views, sizeof(int) * n_views));
+    TRY(ensure(s, s->rec, sizeof(float4) * kRecF4 * pairs));
+    TRY(ensure(s, s->rect, sizeof(int4) * pairs));
+    TRY(ensure(s, s->depth, sizeof(unsigned int) * pairs));
+    TRY(ensure(s, s->cnt, sizeof(unsigned long long) * pairs));
+    TRY(ensure(s, s->cot, sizeof(float) * kCotF * pairs));
+    TRY(ensure(s, s->ranges, sizeof(int2) * (size_t)s->nv * s->T));
+    TRY(ensure(s, s->scan_tmp, scan_u64_tmp_bytes((long long)pairs)));
+    TRY(build_layout(s));
+    CK(s, cudaMemcpyAsync(s->views.p, s->views_h.data(), sizeof(int) * n_views, cudaMemcpyHostToDevice, s->st));
+    Ctx c = s->ctx();
+    launch_sample(c, lm_step, s->cfg.seed, s->st);
+    launch_prep_fwd(c, s->st);
+    scan_u64(c.cnt, (long long)pairs, s->total.as<unsigned long long>(), s->scan_tmp.p, s->scan_tmp.cap, s->st);
+    CHECK_LAUNCH(s);
+    unsigned long long total = 0;
+    CK(s, cudaMemcpyAsync(&total, s->total.p, sizeof(total), cudaMemcpyDeviceToHost, s->st));
+    CK(s, cudaStreamSynchronize(s->st));
+    if (total >= (1ull << 31)) return fail(s, LMRS_ERR_BUDGET, "more than 2^31 (view, tile, Gaussian) pairs");
+    s->npairs = (long long)total;
+    const size_t np = std::max<size_t>((size_t)total, 1);
+    TRY(ensure(s, s->keys, sizeof(unsigned long long) * np));
+    TRY(ensure(s, s->keys_alt, sizeof(unsigned long long) * np));
+    TRY(ensure(s, s->ids, sizeof(unsigned int) * np));
+    TRY(ensure(s, s->ids_alt, sizeof(unsigned int) * np));
+    TRY(ensure(s, s->radix_tmp, radix_tmp_bytes((long long)np)));
+    c = s->ctx();
+    launch_emit(c, s->st);
+    int vbits = 0;
+    while ((1ll << vbits) < (long long)s->nv * s->T) ++vbits;
+    radix_sort(c.keys, c.ids, s->keys_alt.as<unsigned long long>(), s->ids_alt.as<unsigned int>(), s->npairs,
+               32 + vbits, s->radix_tmp.p, s->radix_tmp.cap, s->st);
+    CK(s, cudaMemsetAsync(s->ranges.p, 0, sizeof(int2) * (size_t)s->nv * s->T, s->st));
+    launch_ranges(c, s->st);
+    CHECK_LAUNCH(s);
+    s->preprocessed = true;
+    return LMRS_OK;
+}
+
+lmrs_status lmrs_render(lmrs_scene* s, float* images_dev, float* residuals_dev) {
+    TRY(check_scene(s));
+    TRY(need_pre(s));
+    Ctx c = s->ctx();
+    CK(s, cudaMemsetAsync(&c.sc->loss_num, 0, 2 * sizeof(double), s->st));
+    launch_raster_fwd_samples(c, s->st);
+    if (images_dev) launch_raster_full(c, images_dev, s->st);
+    CHECK_LAUNCH(s);
+    if (residuals_dev)
+        CK(s, cudaMemcpyAsync(residuals_dev, s->resid.p, sizeof(float) * 3 * s->S, cudaMemcpyDeviceToDevice, s->st));
+    s->rendered = true;
+    return LMRS_OK;
+}
+
+lmrs_status lmrs_jvp(lmrs_scene* s, const float* v, float* u) {
+    TRY(check_scene(s));
+    if (!v || !u) return fail(s, LMRS_ERR_INVALID_ARG, "null vector");
+    TRY(need_pre(s));
+    Ctx c = s->ctx();
+    launch_prep_jvp(c, v, nullptr, nullptr, s->st);
+    launch_raster_jvp(c, u, s->st);
+    CHECK_LAUNCH(s);
+    return LMRS_OK;
+}
+
+lmrs_status lmrs_vjp(lmrs_scene* s, const float* u, float* g) {
+    TRY(check_scene(s));
+    if (!u || !g) return fail(s, LMRS_ERR_INVALID_ARG, "null vector");
+    TRY(need_render(s));
+    Ctx c = s->ctx();
+    CK(s, cudaMemsetAsync(s->cot.p, 0, sizeof(float) * kCotF * (size_t)s->nv * s->G, s->st));
+    launch_raster_vjp(c, u, s->st);
+    launch_prep_vjp(c, g, nullptr, nullptr, false, s->st);
+    CHECK_LAUNCH(s);
+    return LMRS_OK;
+}
+
+lmrs_status lmrs_rhs(lmrs_scene* s, float* b) {
+    TRY(check_scene(s));
+    if (!b) return fail(s, LMRS_ERR_INVALID_ARG, "null vector");
+    TRY(need_render(s));
+    Ctx c = s->ctx();
+    CK(s, cudaMemsetAsync(s->cot.p, 0, sizeof(float) * kCotF * (size_t)s->nv * s->G, s->st));
+    launch_raster_vjp(c, nullptr, s->st);
+    launch_prep_vjp(c, b, nullptr, nullptr, false, s->st);
+    CHECK_LAUNCH(s);
+    return LMRS_OK;
+}
+
+lmrs_status lmrs_jtj_diag(lmrs_scene* s, float* d) {
+    TRY(check_scene(s));
+    TRY(need_render(s));
+    TRY(do_jtj_diag(s));
+    if (d) CK(s, cudaMemcpyAsync(d, s->D.p, sizeof(float) * s->P, cudaMemcpyDeviceToDevice, s->st));
+    return LMRS_OK;
+}
+
+lmrs_status lmrs_jtjv(lmrs_scene* s, const float* v, float* out) {
+    TRY(check_scene(s));
+    if (!v || !out) return fail(s, LMRS_ERR_INVALID_ARG, "null vector");
+    TRY(need_pre(s));
+    if (s->cfg.damping_mode == 1 && !s->have_D)
+        return fail(s, LMRS_ERR_NOT_PREPROCESSED, "diagonal damping needs lmrs_jtj_diag first");
+    const size_t pv = sizeof(float) * s->P;
+    const bool vdev = is_device_ptr(v), odev = is_device_ptr(out);
+    const float* vin = v;
+    float* o = out;
+    if (!vdev) {
+        TRY(ensure(s, s->stage_a, pv));
+        CK(s, cudaMemcpyAsync(s->stage_a.p, v, pv, cudaMemcpyHostToDevice, s->st));
+        vin = s->stage_a.as<float>();
+    }
+    if (!odev) {
+        TRY(ensure(s, s->stage_b, pv));
+        o = s->stage_b.as<float>();
+    }
+    TRY(do_jtjv(s, vin, o));
+    if (!odev) {
+        CK(s, cudaMemcpyAsync(out, o, pv, cudaMemcpyDeviceToHost, s->st));
+        CK(s, cudaStreamSynchronize(s->st));
+    }
+    return LMRS_OK;
+}
+
+lmrs_status lmrs_cg_solve(lmrs_scene* s, const float* b, float* x, int32_t iters, lmrs_cg_stats* st) {
+    TRY(check_scene(s));
+    if (!b || !x || iters < 0) return fail(s, LMRS_ERR_INVALID_ARG, "bad CG arguments");
+    TRY(need_pre(s));
+    if (!s->have_D) return fail(s, LMRS_ERR_NOT_PREPROCESSED, "CG needs lmrs_jtj_diag (preconditioner) first");
+    TRY(do_cg(s, b, x, iters));
+    if (st) {
+        Scalars h;
+        TRY(read_scalars(s, &h));
+        std::memset(st, 0, sizeof(*st));
+        st->rz0 = h.rz0;
+        st->rz_final = h.rz;
+        st->iters = iters;
+        for (int i = 0; i < std::min(iters, 64); ++i) {
+            st->alpha[i] = h.alpha_hist[i];
+            st->beta[i] = h.beta_hist[i];
+        }
+        if (h.numeric_error) return fail(s, LMRS_ERR_NUMERIC, "non-finite or non-positive CG curvature");
+    }
+    return LMRS_OK;
+}
+
+lmrs_status lmrs_step_size(lmrs_scene* s, const float* x, int64_t lm_step, double* eta) {
+    TRY(check_scene(s));
+    if (!x || !eta) return fail(s, LMRS_ERR_INVALID_ARG, "null argument");
+    Ctx c = s->ctx();
+    CK(s, cudaMemsetAsync(&c.sc->max_dc_bits, 0, sizeof(unsigned int), s->st));
+    launch_max_dc(c, x, s->st);
+    CHECK_LAUNCH(s);
+    Scalars h;
+    TRY(read_scalars(s, &h));
+    float m;
+    std::memcpy(&m, &h.max_dc_bits, sizeof(m));
+    if (lm_step < s->cfg.warm_iters) *eta = s->cfg.lr_warm;
+    else if (m == 0.f) *eta = s->cfg.lr_cap;
+    else *eta = std::fmin(s->cfg.lr_cap, s->cfg.color_bound / (double)m);
+    return LMRS_OK;
+}
+
+lmrs_status lmrs_lm_step(lmrs_scene* s, const int32_t* view_ids, int32_t n_views, int64_t lm_step,
+                         lmrs_step_stats* st) {
+    TRY(check_scene(s));
+    TRY(lmrs_preprocess(s, view_ids, n_views, lm_step));
+    TRY(lmrs_render(s, nullptr, nullptr));
+    TRY(lmrs_rhs(s, s->b.as<float>()));
+    TRY(do_jtj_diag(s));
+    TRY(do_cg(s, s->b.as<float>(), s->x.as<float>(), s->cfg.cg_iters));
+    Ctx c = s->ctx();
+    CK(s, cudaMemsetAsync(&c.sc->max_dc_bits, 0, sizeof(unsigned int), s->st));
+    launch_max_dc(c, s->x.as<float>(), s->st);
+    launch_lm_update(c, lm_step, s->cfg.lr_warm, s->cfg.lr_cap, s->cfg.color_bound, s->cfg.warm_iters,
+                     s->x.as<float>(), s->params.as<float>(), s->st);
+    CHECK_LAUNCH(s);
+    // the parameters changed: the per-step state no longer describes them
+    s->preprocessed = s->rendered = s->have_D = false;
+    if (st) {
+        Scalars h;
+        TRY(read_scalars(s, &h));
+        float m;
+        std::memcpy(&m, &h.max_dc_bits, sizeof(m));
+        st->loss = h.loss_den > 0.0 ? h.loss_num / h.loss_den : 0.0;
+        st->eta = h.eta;
+        st->max_dc = m;
+        st->rz0 = h.rz0;
+        st->rz_final = h.rz;
+        st->n_samples = s->S;
+        st->n_pairs = s->npairs;
+        if (h.numeric_error) return fail(s, LMRS_ERR_NUMERIC, "non-finite or non-positive CG curvature");
+    }
+    return LMRS_OK;
+}
+
+int64_t lmrs_num_params(const lmrs_scene* s) { return s ? s->P : -1; }
+int64_t lmrs_num_samples(const lmrs_scene* s) { return s && s->layout_nv >= 0 ? s->S : -1; }
+int64_t lmrs_num_pairs(const lmrs_scene* s) { return s && s->preprocessed ? s->npairs : -1; }
+
+lmrs_status lmrs_get_samples(lmrs_scene* s, uint8_t* off, int32_t* tile_off) {
+    TRY(check_scene(s));
+    TRY(need_pre(s));
+    if (off) CK(s, cudaMemcpyAsync(off, s->off.p, (size_t)s->S, cudaMemcpyDeviceToHost, s->st));
+    CK(s, cudaStreamSynchronize(s->st));
+    if (tile_off) std::copy(s->tile_off_h.begin(), s->tile_off_h.end(), tile_off);
+    return LMRS_OK;
+}
+
+lmrs_status lmrs_get_tile_lists(lmrs_scene* s, int32_t* ranges, int32_t* ids) {
+    TRY(check_scene(s));
+    TRY(need_pre(s));
+    if (ranges)
+        CK(s, cudaMemcpyAsync(ranges, s->ranges.p, sizeof(int2) * (size_t)s->nv * s->T, cudaMemcpyDeviceToHost, s->st));
+    if (ids && s->npairs > 0)
+        CK(s, cudaMemcpyAsync(ids, s->ids.p, sizeof(unsigned int) * s->npairs, cudaMemcpyDeviceToHost, s->st));
+    CK(s, cudaStreamSynchronize(s->st));
+    return LMRS_OK;
+}
+
+lmrs_status lmrs_synchronize(lmrs_scene* s) {
+    TRY(check_scene(s));
+    CK(s, cudaStreamSynchronize(s->st));
+    return LMRS_OK;
+}
+
+const char* lmrs_status_str(lmrs_status st) {
+    const int i = (int)st;
+    return (i >= 0 && i < (int)(sizeof(kStatusStr) / sizeof(kStatusStr[0]))) ? kStatusStr[i] : "LMRS_ERR_UNKNOWN";
+}
+
+const char* lmrs_last_error(const lmrs_scene* s) { return s ? s->err.c_str() : "null scene"; }
+
+int64_t lmrs_launch_count(void) { return lmrs::g_launches.load(std::memory_order_relaxed); }
+
+}  // extern "C"

@@ -1,0 +1,312 @@
+"""Thin ctypes binding of include/lmrs.h (argument marshalling only).
+
+Every function has the name and argument order of its C entry point.  Vector
+arguments may be torch tensors (their ``data_ptr()`` is passed), integers
+(raw pointers) or None where the C API accepts NULL.  All arithmetic runs in
+liblmrs.so; if the library is missing the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_LIB = None
+
+LMRS_OK = 0
+STATUS = ["LMRS_OK", "LMRS_ERR_INVALID_ARG", "LMRS_ERR_OOM", "LMRS_ERR_CUDA", "LMRS_ERR_NOT_PREPROCESSED",
+          "LMRS_ERR_NUMERIC", "LMRS_ERR_TIMEOUT", "LMRS_ERR_BUDGET"]
+
+
+class LmrsError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        name = STATUS[status] if 0 <= status < len(STATUS) else str(status)
+        super().__init__(f"{name}: {msg}" if msg else name)
+
+
+class Camera(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("world_to_cam", C.c_float * 12), ("znear", C.c_float)]
+
+
+class Config(C.Structure):
+    _fields_ = [("sh_degree", C.c_int32), ("tile_w", C.c_int32), ("tile_h", C.c_int32),
+                ("sample_frac", C.c_double), ("samples_per_tile", C.c_int32), ("weight_mode", C.c_int32),
+                ("lambda_", C.c_double), ("damping_mode", C.c_int32), ("cg_iters", C.c_int32),
+                ("lr_warm", C.c_double), ("lr_cap", C.c_double), ("color_bound", C.c_double),
+                ("warm_iters", C.c_int32), ("cache_bf16", C.c_int32), ("seed", C.c_uint64)]
+
+
+class CgStats(C.Structure):
+    _fields_ = [("rz0", C.c_double), ("rz_final", C.c_double), ("res_norm", C.c_double),
+                ("alpha", C.c_double * 64), ("beta", C.c_double * 64), ("iters", C.c_int32)]
+
+
+class StepStats(C.Structure):
+    _fields_ = [("loss", C.c_double), ("eta", C.c_double), ("max_dc", C.c_double), ("rz0", C.c_double),
+                ("rz_final", C.c_double), ("n_samples", C.c_int64), ("n_pairs", C.c_int64)]
+
+
+_P = C.c_void_p
+_S = C.c_int
+_SIGS = {
+    "lmrs_config_default": (_S, [C.POINTER(Config)]),
+    "lmrs_scene_create": (_S, [C.POINTER(Config), C.c_int64, _P, _P, C.c_int32, _P, _P, C.POINTER(_P)]),
+    "lmrs_scene_destroy": (_S, [_P]),
+    "lmrs_set_params": (_S, [_P, _P]),
+    "lmrs_get_params": (_S, [_P, _P]),
+    "lmrs_preprocess": (_S, [_P, _P, C.c_int32, C.c_int64]),
+    "lmrs_render": (_S, [_P, _P, _P]),
+    "lmrs_jvp": (_S, [_P, _P, _P]),
+    "lmrs_vjp": (_S, [_P, _P, _P]),
+    "lmrs_rhs": (_S, [_P, _P]),
+    "lmrs_jtj_diag": (_S, [_P, _P]),
+    "lmrs_jtjv": (_S, [_P, _P, _P]),
+    "lmrs_cg_solve": (_S, [_P, _P, _P, C.c_int32, C.POINTER(CgStats)]),
+    "lmrs_step_size": (_S, [_P, _P, C.c_int64, C.POINTER(C.c_double)]),
+    "lmrs_lm_step": (_S, [_P, _P, C.c_int32, C.c_int64, C.POINTER(StepStats)]),
+    "lmrs_get_solution": (_S, [_P, _P]),
+    "lmrs_num_params": (C.c_int64, [_P]),
+    "lmrs_num_samples": (C.c_int64, [_P]),
+    "lmrs_num_pairs": (C.c_int64, [_P]),
+    "lmrs_get_samples": (_S, [_P, _P, _P]),
+    "lmrs_get_tile_lists": (_S, [_P, _P, _P]),
+    "lmrs_synchronize": (_S, [_P]),
+    "lmrs_status_str": (C.c_char_p, [_S]),
+    "lmrs_last_error": (C.c_char_p, [_P]),
+    "lmrs_launch_count": (C.c_int64, []),
+}
+EXPORTS = tuple(_SIGS)
+
+
+def library_path() -> str:
+    return _build.library_path()
+
+
+def lib():
+    """Load liblmrs.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with paper_2504_12905_gb300.build.build() "
+                               "(there is no fallback implementation)")
+        L = C.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot pass {type(x)} as a pointer")
+
+
+def _check(status, scene=None):
+    if status != LMRS_OK:
+        msg = ""
+        if scene:
+            m = lib().lmrs_last_error(scene)
+            msg = m.decode() if m else ""
+        raise LmrsError(status, msg)
+
+
+def cameras(cams):
+    """numpy records (synthetic.CAMERA_DTYPE) -> ctypes array."""
+    arr = (Camera * len(cams))()
+    for i, c in enumerate(cams):
+        arr[i].width = int(c["width"])
+        arr[i].height = int(c["height"])
+        arr[i].fx = float(c["fx"])
+        arr[i].fy = float(c["fy"])
+        arr[i].cx = float(c["cx"])
+        arr[i].cy = float(c["cy"])
+        for k in range(12):
+            arr[i].world_to_cam[k] = float(c["world_to_cam"][k])
+        arr[i].znear = float(c["znear"])
+    return arr
+
+
+def lmrs_config_default(**overrides) -> Config:
+    cfg = Config()
+    _check(lib().lmrs_config_default(C.byref(cfg)))
+    for k, v in overrides.items():
+        setattr(cfg, "lambda_" if k == "lambda" else k, v)
+    return cfg
+
+
+def lmrs_scene_create(cfg, n_gauss, params, cams, targets=None, stream=None):
+    h = _P()
+    cam_arr = cams if isinstance(cams, C.Array) else cameras(cams)
+    _check(lib().lmrs_scene_create(C.byref(cfg), int(n_gauss), _ptr(params), C.cast(cam_arr, _P), len(cam_arr),
+                                   _ptr(targets), _ptr(stream) if stream is not None else None, C.byref(h)))
+    return h.value
+
+
+def lmrs_scene_destroy(scene):
+    _check(lib().lmrs_scene_destroy(scene))
+
+
+def lmrs_set_params(scene, src):
+    _check(lib().lmrs_set_params(scene, _ptr(src)), scene)
+
+
+def lmrs_get_params(scene, dst):
+    _check(lib().lmrs_get_params(scene, _ptr(dst)), scene)
+
+
+def lmrs_preprocess(scene, view_ids, lm_step=0):
+    v = np.ascontiguousarray(view_ids, dtype=np.int32)
+    _check(lib().lmrs_preprocess(scene, v.ctypes.data, len(v), int(lm_step)), scene)
+
+
+def lmrs_render(scene, images=None, residuals=None):
+    _check(lib().lmrs_render(scene, _ptr(images), _ptr(residuals)), scene)
+
+
+def lmrs_jvp(scene, v, u):
+    _check(lib().lmrs_jvp(scene, _ptr(v), _ptr(u)), scene)
+
+
+def lmrs_vjp(scene, u, g):
+    _check(lib().lmrs_vjp(scene, _ptr(u), _ptr(g)), scene)
+
+
+def lmrs_rhs(scene, b):
+    _check(lib().lmrs_rhs(scene, _ptr(b)), scene)
+
+
+def lmrs_jtj_diag(scene, d=None):
+    _check(lib().lmrs_jtj_diag(scene, _ptr(d)), scene)
+
+
+def lmrs_jtjv(scene, v, out):
+    _check(lib().lmrs_jtjv(scene, _ptr(v), _ptr(out)), scene)
+
+
+def lmrs_cg_solve(scene, b, x, iters, stats=True):
+    st = CgStats() if stats else None
+    _check(lib().lmrs_cg_solve(scene, _ptr(b), _ptr(x), int(iters), C.byref(st) if st is not None else None), scene)
+    return st
+
+
+def lmrs_step_size(scene, x, lm_step):
+    eta = C.c_double()
+    _check(lib().lmrs_step_size(scene, _ptr(x), int(lm_step), C.byref(eta)), scene)
+    return eta.value
+
+
+def lmrs_lm_step(scene, view_ids, lm_step, stats=True):
+    v = np.ascontiguousarray(view_ids, dtype=np.int32)
+    st = StepStats() if stats else None
+    _check(lib().lmrs_lm_step(scene, v.ctypes.data, len(v), int(lm_step), C.byref(st) if st is not None else None),
+           scene)
+    return st
+
+
+def lmrs_get_solution(scene, dst):
+    _check(lib().lmrs_get_solution(scene, _ptr(dst)), scene)
+
+
+def lmrs_num_params(scene):
+    return int(lib().lmrs_num_params(scene))
+
+
+def lmrs_num_samples(scene):
+    return int(lib().lmrs_num_samples(scene))
+
+
+def lmrs_num_pairs(scene):
+    return int(lib().lmrs_num_pairs(scene))
+
+
+def lmrs_get_samples(scene, n_views, n_tiles):
+    S = lmrs_num_samples(scene)
+    off = np.empty(S, np.uint8)
+    tile_off = np.empty(n_views * n_tiles + 1, np.int32)
+    _check(lib().lmrs_get_samples(scene, off.ctypes.data, tile_off.ctypes.data), scene)
+    return off, tile_off
+
+
+def lmrs_get_tile_lists(scene, n_views, n_tiles):
+    n = lmrs_num_pairs(scene)
+    ranges = np.empty((n_views * n_tiles, 2), np.int32)
+    ids = np.empty(max(n, 1), np.int32)
+    _check(lib().lmrs_get_tile_lists(scene, ranges.ctypes.data, ids.ctypes.data), scene)
+    return ranges, ids[:n]
+
+
+def lmrs_synchronize(scene):
+    _check(lib().lmrs_synchronize(scene), scene)
+
+
+def lmrs_status_str(status):
+    return lib().lmrs_status_str(status).decode()
+
+
+def lmrs_last_error(scene):
+    m = lib().lmrs_last_error(scene)
+    return m.decode() if m else ""
+
+
+def lmrs_launch_count():
+    return int(lib().lmrs_launch_count())
+
+
+class Scene:
+    """Owner of one lmrs_scene plus the torch tensors it borrows."""
+
+    def __init__(self, params, cams, n_gauss, sh_degree=0, targets=None, stream=None, **cfg):
+        import torch
+        c = lmrs_config_default(sh_degree=sh_degree, **cfg)
+        self.cfg = c
+        self.n_gauss = int(n_gauss)
+        self.sh_degree = sh_degree
+        self.cams = cams
+        self.width = int(cams[0]["width"])
+        self.height = int(cams[0]["height"])
+        self.tiles_x = (self.width + c.tile_w - 1) // c.tile_w
+        self.tiles_y = (self.height + c.tile_h - 1) // c.tile_h
+        self.n_tiles = self.tiles_x * self.tiles_y
+        self.targets = targets  # kept alive: the scene borrows it
+        p = params if hasattr(params, "data_ptr") else torch.as_tensor(np.ascontiguousarray(params, np.float32))
+        self.h = lmrs_scene_create(c, n_gauss, p.contiguous() if p.is_cuda else p.contiguous(), cams, targets, stream)
+        self.n_params = lmrs_num_params(self.h)
+        self.n_views = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            lmrs_scene_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def preprocess(self, views, step=0):
+        lmrs_preprocess(self.h, views, step)
+        self.n_views = len(views)
+
+    @property
+    def n_samples(self):
+        return lmrs_num_samples(self.h)
+
+    @property
+    def n_pairs(self):
+        return lmrs_num_pairs(self.h)

@@ -1,0 +1,240 @@
+"""CUDA path (through the C-ABI) against the FP64 oracle on the same seeded
+inputs: the tiny configuration (1,000 Gaussians, 4 views of 64x64, all
+pixels), ragged images, sampling, SH degrees 0/1/3 and both damping modes.
+
+Tolerances: sample offsets, tile lists and sort order bit-exact; pixels
+1e-5 absolute; J v, J^T u, D, b and the damped operator 1e-4 normwise
+relative (overall and per parameter group); CG and the LM update 1e-3."""
+import numpy as np
+import pytest
+
+from paper_2504_12905_gb300 import synthetic as syn
+
+from gpu_common import GROUPS, Pair, assert_pvec_close, group_errors, oracle_targets
+from helpers import normwise_rel, small_scene
+
+pytestmark = pytest.mark.gpu
+
+PIX_TOL = 1e-5
+OP_TOL = 1e-4
+CG_TOL = 1e-3
+
+
+def _tiny(sh_degree=0, **cfg):
+    sc = syn.tiny_scene(sh_degree=sh_degree)
+    rng = np.random.default_rng(3)
+    tgt = oracle_targets(sc, syn.perturb(rng, sc.params))
+    return Pair(sc, tgt, **cfg), [0, 1, 2, 3]
+
+
+def _ragged(sh_degree=1, frac=0.1, **cfg):
+    rng = np.random.default_rng(17)
+    sc = syn.tiny_scene(seed=99, n_gauss=1500, width=100, height=70, sh_degree=sh_degree)
+    tgt = syn.noise_targets(rng, len(sc.cams), 70, 100)
+    return Pair(sc, tgt, sample_frac=frac, **cfg), [3, 1]
+
+
+CASES = {
+    "tiny": lambda: _tiny(0, lambda_=1e-2),
+    "ragged_sh1_frac": lambda: _ragged(1, 0.1, weight_mode=1),
+    "ragged_sh3": lambda: _ragged(3, 0.25),
+}
+
+
+@pytest.fixture(params=list(CASES))
+def case(request):
+    pair, views = CASES[request.param]()
+    pair.begin(views, step=2)
+    return pair
+
+
+def test_samples_bit_exact(case):
+    off, tile_off = case.lmrs.lmrs_get_samples(case.gpu.h, case.gpu.n_views, case.gpu.n_tiles)
+    ref = case.orc.samples()
+    np.testing.assert_array_equal(tile_off, ref["tile_off"])
+    np.testing.assert_array_equal(off, ref["off"])
+
+
+def test_tile_lists_bit_exact(case):
+    ranges, ids = case.lmrs.lmrs_get_tile_lists(case.gpu.h, case.gpu.n_views, case.gpu.n_tiles)
+    r_ref, ids_ref = case.orc.lists()
+    assert case.gpu.n_pairs == len(ids_ref)
+    np.testing.assert_array_equal(ranges, r_ref)
+    np.testing.assert_array_equal(ids, ids_ref)
+
+
+def test_render_and_residuals(case):
+    images = case.zeros(case.gpu.n_views * case.scene.height * case.scene.width * 3)
+    resid = case.zeros(case.S * 3)
+    case.lmrs.lmrs_render(case.gpu.h, images, resid)
+    rgb, r_ref, flags = case.orc.render_samples()
+    r = case.host(resid).reshape(-1, 3)
+    keep = flags == 0
+    assert keep.mean() > 0.995
+    np.testing.assert_allclose(r[keep], r_ref[keep], atol=PIX_TOL, rtol=0)
+    img = case.host(images).reshape(case.gpu.n_views, case.scene.height, case.scene.width, 3)
+    for slot in range(case.gpu.n_views):
+        ref, fl = case.orc.render_full(slot)
+        k = fl == 0
+        assert k.mean() > 0.995
+        np.testing.assert_allclose(img[slot][k], ref[k], atol=PIX_TOL, rtol=0)
+
+
+def test_jvp(case):
+    rng = np.random.default_rng(1)
+    v = rng.standard_normal(case.P).astype(np.float32)
+    u = case.zeros(case.S * 3)
+    case.lmrs.lmrs_jvp(case.gpu.h, case.cuda(v), u)
+    u_ref = case.orc.jvp(v.astype(np.float64))
+    _, _, flags = case.orc.render_samples()
+    keep = flags == 0
+    got = case.host(u).reshape(-1, 3)
+    assert normwise_rel(got[keep], u_ref[keep]) <= OP_TOL
+
+
+def test_vjp_and_rhs(case):
+    rng = np.random.default_rng(2)
+    case.lmrs.lmrs_render(case.gpu.h)
+    u = rng.standard_normal((case.S, 3)).astype(np.float32)
+    g = case.zeros(case.P)
+    case.lmrs.lmrs_vjp(case.gpu.h, case.cuda(u), g)
+    g_ref = case.orc.vjp(u.astype(np.float64))
+    got = case.host(g)
+    assert_pvec_close(got, g_ref, OP_TOL, "J^T u")
+    errs = group_errors(case, got, g_ref)
+    assert max(errs.values()) <= OP_TOL, errs
+    b = case.zeros(case.P)
+    case.lmrs.lmrs_rhs(case.gpu.h, b)
+    assert_pvec_close(case.host(b), case.orc.rhs(), OP_TOL, "J^T W r")
+
+
+def test_diag(case):
+    case.lmrs.lmrs_render(case.gpu.h)
+    d = case.zeros(case.P)
+    case.lmrs.lmrs_jtj_diag(case.gpu.h, d)
+    d_ref = case.orc.diag()
+    got = case.host(d)
+    assert_pvec_close(got, d_ref, OP_TOL, "diag")
+    errs = group_errors(case, got, d_ref)
+    assert max(errs.values()) <= OP_TOL, errs
+    assert np.all(got >= 0)
+
+
+@pytest.mark.parametrize("damping_mode", [0, 1])
+def test_jtjv(case, damping_mode):
+    case.gpu.close()
+    cfg = dict(case.cfg)
+    cfg["damping_mode"] = damping_mode
+    cfg.setdefault("lambda_", 0.1)
+    pair = Pair(case.scene, case.targets_np, **cfg)
+    pair.begin(case.views, step=2)
+    pair.lmrs.lmrs_render(pair.gpu.h)
+    pair.lmrs.lmrs_jtj_diag(pair.gpu.h)
+    D_ref = pair.orc.diag()
+    rng = np.random.default_rng(4)
+    v = rng.standard_normal(pair.P).astype(np.float32)
+    out = pair.zeros(pair.P)
+    pair.lmrs.lmrs_jtjv(pair.gpu.h, pair.cuda(v), out)
+    ref = pair.orc.apply(v.astype(np.float64), D_ref)
+    got = pair.host(out)
+    assert_pvec_close(got, ref, OP_TOL, "(J^T W J + lambda D) v")
+    errs = group_errors(pair, got, ref)
+    assert max(errs.values()) <= OP_TOL, errs
+    # host buffers through the same entry point
+    out_h = np.zeros(pair.P, np.float32)
+    pair.lmrs.lmrs_jtjv(pair.gpu.h, np.ascontiguousarray(v), out_h)
+    np.testing.assert_allclose(out_h, got, rtol=1e-5, atol=1e-6 * np.abs(got).max())
+
+
+def test_cg_solve(case):
+    case.lmrs.lmrs_render(case.gpu.h)
+    case.lmrs.lmrs_jtj_diag(case.gpu.h)
+    b = case.zeros(case.P)
+    case.lmrs.lmrs_rhs(case.gpu.h, b)
+    x = case.zeros(case.P)
+    st = case.lmrs.lmrs_cg_solve(case.gpu.h, b, x, 10)
+    D_ref = case.orc.diag()
+    x_ref, st_ref = case.orc.cg(case.orc.rhs(), D_ref, 10)
+    assert normwise_rel(case.host(x), x_ref) <= CG_TOL
+    assert abs(st.rz0 - st_ref[0]) <= 1e-4 * abs(st_ref[0])
+
+
+def test_lm_step_and_step_size(case):
+    for step in (0, 10):
+        cfg = dict(case.cfg)
+        cfg["cg_iters"] = 10
+        pair = Pair(case.scene, case.targets_np, **cfg)
+        p0 = pair.scene.params.astype(np.float64)
+        st = pair.lmrs.lmrs_lm_step(pair.gpu.h, case.views, step)
+        x_ref, st_ref = pair.orc.lm_step(case.views, step)
+        x = np.zeros(pair.P, np.float32)
+        pair.lmrs.lmrs_get_solution(pair.gpu.h, x)
+        assert normwise_rel(x, x_ref) <= CG_TOL
+        # the step size is exact given x (Sec. 4.5, App. D)
+        eta_gpu_rule = pair.orc.step_size(x.astype(np.float64), step)
+        assert st.eta == pytest.approx(eta_gpu_rule, rel=1e-12)
+        assert st.eta == pytest.approx(st_ref[1], rel=CG_TOL)
+        assert st.loss == pytest.approx(st_ref[0], rel=1e-5)
+        p1 = np.zeros(pair.P, np.float32)
+        pair.lmrs.lmrs_get_params(pair.gpu.h, p1)
+        assert normwise_rel(p1 - p0, pair.orc.get_params() - p0) <= CG_TOL
+        assert pair.lmrs.lmrs_step_size(pair.gpu.h, pair.cuda(x), step) == pytest.approx(eta_gpu_rule, rel=1e-12)
+        pair.gpu.close()
+
+
+def test_cache_bf16_error_is_reported():
+    pair, views = _tiny(0, lambda_=1e-2)
+    pair16, _ = _tiny(0, lambda_=1e-2, cache_bf16=1)
+    for p in (pair, pair16):
+        p.begin(views, step=0)
+        p.lmrs.lmrs_render(p.gpu.h)
+    b_ref = pair.orc.rhs()
+    errs = []
+    for p in (pair, pair16):
+        b = p.zeros(p.P)
+        p.lmrs.lmrs_rhs(p.gpu.h, b)
+        errs.append(normwise_rel(p.host(b), b_ref))
+    assert errs[0] <= OP_TOL
+    assert errs[1] <= 2e-2  # BF16 keeps 8 bits of the cached final colour
+    print(f"RHS normwise error: FP32 caches {errs[0]:.2e}, BF16 caches {errs[1]:.2e}")
+
+
+def test_edge_cases_empty_and_single():
+    # views that see nothing: no pairs, zero residual derivative
+    sc = small_scene(5, n_gauss=3)
+    far = sc.params.copy()
+    far[:9] = np.tile([0.0, 0.0, 50.0], 3)  # high above: behind both cameras
+    sc_far = syn.Scene(3, 0, far, sc.cams, 5)
+    pair = Pair(sc_far, None, lambda_=0.1)
+    pair.begin([0, 1])
+    assert pair.gpu.n_pairs == 0 == len(pair.orc.lists()[1])
+    resid = pair.zeros(pair.S * 3)
+    pair.lmrs.lmrs_render(pair.gpu.h, None, resid)
+    assert float(pair.host(resid).max()) == 0.0
+    pair.lmrs.lmrs_jtj_diag(pair.gpu.h)
+    out = pair.zeros(pair.P)
+    pair.lmrs.lmrs_jtjv(pair.gpu.h, pair.cuda(np.ones(pair.P)), out)
+    np.testing.assert_allclose(pair.host(out), 0.0)
+    # a single Gaussian, odd G, all pixels
+    one = small_scene(6, n_gauss=1, sh_degree=3)
+    p1 = Pair(one, None, lambda_=0.1)
+    p1.begin([0, 1])
+    p1.lmrs.lmrs_render(p1.gpu.h)
+    d = p1.zeros(p1.P)
+    p1.lmrs.lmrs_jtj_diag(p1.gpu.h, d)
+    assert_pvec_close(p1.host(d), p1.orc.diag(), OP_TOL, "diag, one Gaussian")
+
+
+def test_errors_are_status_codes():
+    from paper_2504_12905_gb300 import lmrs
+    pair, views = _tiny(0)
+    with pytest.raises(lmrs.LmrsError) as e:
+        lmrs.lmrs_render(pair.gpu.h)
+    assert e.value.status == 4  # not preprocessed
+    with pytest.raises(lmrs.LmrsError) as e:
+        lmrs.lmrs_preprocess(pair.gpu.h, [0, 7])
+    assert e.value.status == 1
+    pair.begin(views)
+    with pytest.raises(lmrs.LmrsError) as e:
+        lmrs.lmrs_vjp(pair.gpu.h, pair.zeros(pair.S * 3), pair.zeros(pair.P))
+    assert e.value.status == 4  # render first
