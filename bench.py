@@ -1,0 +1,385 @@
+#!/usr/bin/env python3
+"""Benchmark of the LM-RS hot path on one GB300 (or N independent replicas).
+
+Workload (default): the 200k-Gaussian scene -- SH degree 3 (coefficients
+N(0, 0.2)), means from 32 anisotropic blobs, 24 views of 1024x672 on a
+hemisphere, 10% of each tile's pixels sampled, 8 views per solve, 8 PCG
+iterations per LM step, lambda 0.1 with diagonal damping.  A bench "step" is
+one full LM step (sampling, projection, binning + sort, render, J^T W r,
+diag, 8 damped-operator applications with the CG updates, step size and the
+parameter update).  Reported metric: applications of (J^T W J + lambda D)
+per second, i.e. 8 x LM steps / time, with all per-step work counted.
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle on the
+host cores instead (a bounded sample of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "JᵀJv matvecs/s at 200k Gaussians (%HBM peak); fits/s & p99 fit latency vs plain"
+
+WORKLOADS = {
+    "moderate": dict(desc="200k Gaussians, SH3, 8 of 24 views 1024x672, 10% per-tile sampling, 8 CG iters",
+                     views_per_step=8, sample_frac=0.1, cg_iters=8, lam=0.1, damping_mode=0),
+    "tiny": dict(desc="1k Gaussians, SH0, 4 views 64x64, all pixels, 10 CG iters",
+                 views_per_step=4, sample_frac=1.0, cg_iters=10, lam=1e-2, damping_mode=0),
+}
+
+
+def make_scene(name, seed_offset=0):
+    from paper_2504_12905_gb300 import synthetic as syn
+    if name == "moderate":
+        return syn.moderate_scene(seed=0x1A5E0001 + seed_offset)
+    return syn.tiny_scene(seed=0x1A5E0000 + seed_offset)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# algorithmic bytes per launch of the raster kernels (see the design notes)
+# --------------------------------------------------------------------------
+def algorithmic_bytes(kernel, sizes):
+    Pi, Vis, S, nvT, P = sizes["pairs"], sizes["visible"], sizes["samples"], sizes["view_tiles"], sizes["P"]
+    tile_meta = 16 * nvT + S  # ranges (8), tile offsets (4), weights (4), sample offsets (1 per sample)
+    if kernel == "k_jtj":
+        # tile lists once, primal + tangent features of every visible pair once,
+        # 9 cotangents per visible pair written once
+        return 4 * Pi + tile_meta + (36 + 36) * Vis + 36 * Vis
+    if kernel == "k_prep_vjp<true>":
+        # per Gaussian: params, p, D read, Ap written; 9 cotangents per visible pair read
+        return 4 * P * 4 + 36 * Vis
+    if kernel == "k_prep_jvp":
+        # params, z, p read, p written; 9 tangents per visible pair written
+        return 4 * P * 4 + 36 * Vis
+    if kernel == "k_cg_update":
+        return 4 * P * 8  # p, Ap, minv, x, r read; x, r, z written
+    return None
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_2504_12905_gb300 import lmrs
+    from paper_2504_12905_gb300 import synthetic as syn
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    wl = WORKLOADS[args.workload]
+    sc = make_scene(args.workload, seed_offset=rank)
+    G, deg = sc.n_gauss, sc.sh_degree
+    nc = len(sc.cams)
+    H, W = sc.height, sc.width
+    # targets: renders of the perturbed parameters (through this library)
+    rng = np.random.default_rng(1234 + rank)
+    tparams = torch.from_numpy(syn.perturb(rng, sc.params)).cuda()
+    targets = torch.zeros((nc, H, W, 3), dtype=torch.float32, device="cuda")
+    tsc = lmrs.Scene(tparams, sc.cams, G, deg)
+    for v0 in range(0, nc, 8):
+        vs = list(range(v0, min(nc, v0 + 8)))
+        lmrs.lmrs_preprocess(tsc.h, vs, 0)
+        lmrs.lmrs_render(tsc.h, targets[v0:v0 + len(vs)])
+    torch.cuda.synchronize()
+    tsc.close()
+    del tparams
+
+    scene = lmrs.Scene(torch.from_numpy(sc.params).cuda(), sc.cams, G, deg, targets=targets,
+                       sample_frac=wl["sample_frac"], lambda_=wl["lam"], damping_mode=wl["damping_mode"],
+                       cg_iters=wl["cg_iters"], seed=0x5EED + rank)
+    h = scene.h
+    vrng = np.random.default_rng(77 + rank)
+    nvs = wl["views_per_step"]
+    n_steps = args.warmup + args.steps
+    views = [syn.view_subset(vrng, nc, nvs) for _ in range(n_steps + args.steps)]
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    # ---- warm-up -------------------------------------------------------
+    for k in range(args.warmup):
+        lmrs.lmrs_lm_step(h, views[k], k, stats=False)
+    barrier()
+
+    # ---- timed region: K full LM steps, inputs resident ----------------
+    vis_dev = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    smi_idx = vis_dev.split(",")[local_rank] if vis_dev and not vis_dev.startswith("GPU") else str(local_rank)
+    clocks = ClockSampler(smi_idx)
+    lmrs.lmrs_get_timing(h)  # clear
+    lmrs.lmrs_set_timing(h, True)
+    launches0 = lmrs.lmrs_launch_count()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    last = None
+    for k in range(args.warmup, n_steps):
+        last = lmrs.lmrs_lm_step(h, views[k], k, stats=(k == n_steps - 1))
+    e1.record()
+    barrier()
+    clock_info = clocks.stop()
+    launches = lmrs.lmrs_launch_count() - launches0
+    lmrs.lmrs_set_timing(h, False)
+    ktimes = lmrs.lmrs_get_timing(h)
+    ms = e0.elapsed_time(e1)
+    ms_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    matvecs = world * args.steps * wl["cg_iters"]
+    value = matvecs / (ms_max / 1000.0)
+
+    # sizes of the last step for the byte model
+    lmrs.lmrs_preprocess(h, views[n_steps - 1], n_steps - 1)
+    sizes = {"pairs": lmrs.lmrs_num_pairs(h), "visible": lmrs.lmrs_num_visible(h),
+             "samples": lmrs.lmrs_num_samples(h), "view_tiles": nvs * scene.n_tiles, "P": scene.n_params}
+
+    # ---- (J^T W J + lambda diag(J^T W J)) v alone, at the current parameters
+    cur = torch.empty(scene.n_params, dtype=torch.float32, device="cuda")
+    lmrs.lmrs_get_params(h, cur)
+    op = lmrs.Scene(cur, sc.cams, G, deg, targets=targets, sample_frac=wl["sample_frac"], lambda_=wl["lam"],
+                    damping_mode=1, cg_iters=wl["cg_iters"], seed=0x5EED + rank)
+    lmrs.lmrs_preprocess(op.h, views[n_steps - 1], n_steps - 1)
+    lmrs.lmrs_render(op.h)
+    lmrs.lmrs_jtj_diag(op.h)
+    v = torch.randn(scene.n_params, device="cuda")
+    out = torch.empty_like(v)
+    for _ in range(3):
+        lmrs.lmrs_jtjv(op.h, v, out)
+    torch.cuda.synchronize()
+    m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+    m0.record()
+    for _ in range(reps):
+        lmrs.lmrs_jtjv(op.h, v, out)
+    m1.record()
+    torch.cuda.synchronize()
+    matvec_ms = m0.elapsed_time(m1) / reps
+    op.close()
+    del cur
+
+    # ---- end to end through the C-ABI with host buffers ---------------
+    p_host = torch.empty(scene.n_params, dtype=torch.float32).pin_memory()
+    lmrs.lmrs_get_params(h, p_host)
+    barrier()
+    t0 = time.perf_counter()
+    for k in range(n_steps, n_steps + args.steps):
+        lmrs.lmrs_set_params(h, p_host)          # host -> device, pinned
+        lmrs.lmrs_lm_step(h, views[k], k, stats=False)
+        lmrs.lmrs_get_params(h, p_host)          # device -> host, synchronises
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": matvecs / e2e_s, "unit": "matvec/s", "h2d_bytes_per_step": 4 * scene.n_params,
+           "d2h_bytes_per_step": 4 * scene.n_params}
+
+    # ---- roofline of the dominant kernel ------------------------------
+    peak, peak_kind = load_peaks()
+    top = max(ktimes.items(), key=lambda kv: kv[1][1])
+    top_name, (top_n, top_ms) = top
+    roof = None
+    kname = top_name if algorithmic_bytes(top_name, sizes) is not None else "k_jtj"
+    if kname in ktimes:
+        n_l, tot = ktimes[kname]
+        avg_s = tot / n_l / 1000.0
+        byt = algorithmic_bytes(kname, sizes)
+        ach = byt / avg_s / 1e9
+        roof = {"kernel": kname, "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(ach / peak, 4), "traffic": None, "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": int(byt), "avg_launch_ms": round(tot / n_l, 4)}
+    step_ms = ms_max / args.steps
+    kshare = {k: {"launches": n, "ms": round(t, 3), "share": round(t / max(ms, 1e-9), 4)}
+              for k, (n, t) in sorted(ktimes.items(), key=lambda kv: -kv[1][1])}
+
+    result = {
+        "metric": METRIC, "value": round(value, 2), "unit": "matvec/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(step_ms, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 CG scalars)",
+        "data": "synthetic (seeded; targets rendered from perturbed parameters)",
+        "config": {"workload": f"{args.workload}: {wl['desc']}", "n_gauss": G, "sh_degree": deg,
+                   "n_params": scene.n_params, "views_per_step": nvs, "image": f"{W}x{H}",
+                   "cg_iters": wl["cg_iters"], "lambda": wl["lam"],
+                   "damping": "LM steps: lambda*I (Eq. 8); matvec_only: lambda*diag(J^T W J)",
+                   "sample_frac": wl["sample_frac"], "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (per-step working set > 129 MB)",
+                   "lm_steps_per_s": round(1000.0 * args.steps / ms_max * world, 3),
+                   "matvec_only_ms": round(matvec_ms, 4), "matvec_only_per_s": round(1000.0 / matvec_ms, 2),
+                   "sizes_last_step": sizes, "loss_last_step": None if last is None else last.loss},
+        "roofline": roof, "kernels": kshare, "e2e": e2e, "gpu_launches": launches, "clocks": clock_info,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(sc, views[n_steps - 1], n_steps - 1, wl, budget_s=args.cpu_seconds)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    scene.close()
+    return result
+
+
+def cpu_baseline(sc, views, step, wl, budget_s=20.0):
+    """The FP64 oracle as it stands: J^T W J v over the same scene and views,
+    repeated until budget_s (at least once); value in operator applications
+    per second."""
+    import oracle
+    o = oracle.OracleScene(sc.params, sc.cams, sc.n_gauss, sc.sh_degree, sample_frac=wl["sample_frac"],
+                           lambda_=wl["lam"], damping_mode=1, seed=0x5EED)
+    o.begin_step(list(views), step)
+    v = np.random.default_rng(0).standard_normal(o.n_params)
+    D = np.zeros(o.n_params)  # the damping term is one axpy; the product is J^T W J v
+    n, t0 = 0, time.perf_counter()
+    while True:
+        o.apply(v, D)
+        n += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": round(n / dt, 4), "unit": "matvec/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{n} full operator application(s) J^T W J v over the {len(views)} sampled views of the "
+                      f"same scene ({o.n_samples} samples), FP64, {dt:.1f} s"}
+
+
+def run_reference(args):
+    import oracle
+    wl = WORKLOADS[args.workload]
+    sc = make_scene(args.workload)
+    from paper_2504_12905_gb300 import synthetic as syn
+    vrng = np.random.default_rng(77)
+    nc = len(sc.cams)
+    o = oracle.OracleScene(sc.params, sc.cams, sc.n_gauss, sc.sh_degree, sample_frac=wl["sample_frac"],
+                           lambda_=wl["lam"], damping_mode=1, seed=0x5EED)
+    v = np.random.default_rng(0).standard_normal(o.n_params)
+    D = np.zeros(o.n_params)
+    # each step: one operator application on one of the sampled views (a
+    # bounded sample of the workload); the metric scales it to full steps
+    per_step_views = 1
+    total = 0.0
+    for k in range(args.warmup + args.steps):
+        vs = syn.view_subset(vrng, nc, wl["views_per_step"])[:per_step_views]
+        o.begin_step(list(vs), k)
+        t0 = time.perf_counter()
+        o.apply(v, D)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            total += dt
+    frac = per_step_views / wl["views_per_step"]
+    value = args.steps * frac / total
+    cores = oracle.num_threads()
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "matvec/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1000 * total / args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded)",
+            "config": {"workload": f"{args.workload}: {wl['desc']}", "parallelism": "host cores"},
+            "cpu_baseline": {"value": round(value, 4), "unit": "matvec/s", "cores": cores, "kind": "oracle",
+                             "sample": f"per step one operator application over 1 of the {wl['views_per_step']} "
+                                       f"views (scaled by {frac:.3f} of an application)"},
+            "e2e": {"value": round(value, 4), "unit": "matvec/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="moderate")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.warmup < 3:
+        print("bench: at least 3 warm-up steps are required", file=sys.stderr)
+        args.warmup = 3
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)))
+        return
+    res = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()

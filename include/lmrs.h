@@ -126,7 +126,7 @@ lmrs_status lmrs_scene_destroy(lmrs_scene* scene);
 lmrs_status lmrs_set_params(lmrs_scene* scene, const float* src);
 lmrs_status lmrs_get_params(lmrs_scene* scene, float* dst);
 
-/* Steps (a1-a3) of one LM step for the views view_ids_host[0..n_views)
+/* Per-step setup of one LM step for the views view_ids_host[0..n_views)
  * (camera indices, host memory): per-tile pixel sampling keyed by
  * (seed, lm_step, camera index, tile) (Sec. 4.4), projection of every
  * Gaussian into every view, tile binning and the radix sort by (tile,
@@ -197,8 +197,22 @@ lmrs_status lmrs_get_solution(lmrs_scene* scene, float* x_dst);
 int64_t lmrs_num_params(const lmrs_scene* scene);
 int64_t lmrs_num_samples(const lmrs_scene* scene);
 int64_t lmrs_num_pairs(const lmrs_scene* scene);
+int64_t lmrs_num_visible(const lmrs_scene* scene); /* visible (view, Gaussian) pairs */
 lmrs_status lmrs_get_samples(lmrs_scene* scene, uint8_t* off_host, int32_t* tile_off_host);
 lmrs_status lmrs_get_tile_lists(lmrs_scene* scene, int32_t* ranges_host, int32_t* ids_host);
+
+/* Per-kernel device time, measured with CUDA events recorded on the scene's
+ * stream around every launch while timing is enabled (off by default). */
+typedef struct {
+    char name[64];     /* kernel name */
+    int64_t launches;
+    double total_ms;   /* sum of the launches' event-to-event times */
+} lmrs_kernel_time;
+
+lmrs_status lmrs_set_timing(lmrs_scene* scene, int32_t enable);
+/* Synchronises, aggregates the launches timed since the previous call by
+ * kernel name into out[0..min(max_entries, n)) and sets *n_entries = n. */
+lmrs_status lmrs_get_timing(lmrs_scene* scene, lmrs_kernel_time* out, int32_t max_entries, int32_t* n_entries);
 
 /* Waits for the scene's stream. */
 lmrs_status lmrs_synchronize(lmrs_scene* scene);

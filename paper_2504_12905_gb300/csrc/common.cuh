@@ -69,6 +69,7 @@ struct Ctx {
     int4* rect;             // inclusive tile rectangle, x0 > x1 when culled
     unsigned int* depth;    // FP32 depth bits
     unsigned long long* cnt;  // tiles touched (then exclusive prefix)
+    unsigned long long* n_visible;  // count of visible pairs
     float* cot;             // kCotF floats
     float* gram;            // kGramF floats
     // binning
@@ -151,8 +152,20 @@ void launch_zero_scalars(const Ctx& c, cudaStream_t st);
 
 }  // namespace lmrs
 
-#define LMRS_LAUNCH(kernel, grid, block, smem, stream, ...)              \
-    do {                                                                 \
-        ::lmrs::note_launch();                                           \
-        kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);     \
+namespace lmrs {
+// Optional per-launch CUDA-event timing of the scene being driven by the
+// calling thread (set by the ABI entry points while timing is enabled).
+struct LaunchTimer;
+LaunchTimer* active_timer();
+int timer_start(LaunchTimer* t, const char* name, cudaStream_t st);
+void timer_stop(LaunchTimer* t, int rec, cudaStream_t st);
+}  // namespace lmrs
+
+#define LMRS_LAUNCH(kernel, grid, block, smem, stream, ...)                     \
+    do {                                                                        \
+        ::lmrs::note_launch();                                                  \
+        ::lmrs::LaunchTimer* t_ = ::lmrs::active_timer();                       \
+        const int r_ = t_ ? ::lmrs::timer_start(t_, #kernel, (stream)) : -1;    \
+        kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);            \
+        if (t_) ::lmrs::timer_stop(t_, r_, (stream));                           \
     } while (0)

@@ -511,7 +511,11 @@ __global__ void k_prep_fwd(Ctx c) {
     Prim P;
     int4 rect;
     float depth;
-    if (!prim_geometry(gp, cam, c.tiles_x, c.tiles_y, c.tile_w, c.tile_h, P, &rect, &depth)) {
+    const bool vis = prim_geometry(gp, cam, c.tiles_x, c.tiles_y, c.tile_w, c.tile_h, P, &rect, &depth);
+    const unsigned ballot = __ballot_sync(__activemask(), vis);
+    if ((threadIdx.x & 31) == __ffs(__activemask()) - 1 && ballot)
+        atomicAdd(c.n_visible, (unsigned long long)__popc(ballot));
+    if (!vis) {
         c.rect[i] = make_int4(1, 0, 1, 0);
         c.cnt[i] = 0ull;
         return;

@@ -12,6 +12,42 @@
 namespace lmrs {
 static std::atomic<long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// Per-launch CUDA events on the launching stream, resolved when read.
+struct LaunchTimer {
+    struct Rec {
+        const char* name;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+    cudaEvent_t get() {
+        cudaEvent_t e = nullptr;
+        if (!pool.empty()) {
+            e = pool.back();
+            pool.pop_back();
+        } else {
+            cudaEventCreate(&e);
+        }
+        return e;
+    }
+    ~LaunchTimer() {
+        for (auto& r : recs) {
+            cudaEventDestroy(r.a);
+            cudaEventDestroy(r.b);
+        }
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+static thread_local LaunchTimer* t_active = nullptr;
+LaunchTimer* active_timer() { return t_active; }
+int timer_start(LaunchTimer* t, const char* name, cudaStream_t st) {
+    LaunchTimer::Rec r{name, t->get(), t->get()};
+    cudaEventRecord(r.a, st);
+    t->recs.push_back(r);
+    return (int)t->recs.size() - 1;
+}
+void timer_stop(LaunchTimer* t, int i, cudaStream_t st) { cudaEventRecord(t->recs[i].b, st); }
 }  // namespace lmrs
 
 using namespace lmrs;
@@ -46,11 +82,13 @@ struct lmrs_scene {
     // host state of the current step
     std::vector<int> views_h;
     int nv = 0;
-    long long step = 0, S = 0, npairs = 0;
+    long long step = 0, S = 0, npairs = 0, nvisible = 0;
     int nwork = 0;
     int layout_nv = -1;
     std::vector<int> tile_off_h;
     bool preprocessed = false, rendered = false, have_D = false;
+    bool timing = false;
+    LaunchTimer timer;
 
     Ctx ctx() const {
         Ctx c;
@@ -69,6 +107,7 @@ struct lmrs_scene {
         c.rect = rect.as<int4>();
         c.depth = depth.as<unsigned int>();
         c.cnt = cnt.as<unsigned long long>();
+        c.n_visible = total.as<unsigned long long>() + 1;
         c.cot = cot.as<float>();
         c.gram = gram.as<float>();
         c.keys = keys.as<unsigned long long>();
@@ -126,6 +165,13 @@ lmrs_status cuda_fail(lmrs_scene* s, cudaError_t e, const char* what) {
         lmrs_status st_ = (expr);        \
         if (st_ != LMRS_OK) return st_;  \
     } while (0)
+
+// Routes the launches of one ABI call to the scene's timer when enabled.
+struct TimerScope {
+    LaunchTimer* prev;
+    explicit TimerScope(lmrs_scene* s) : prev(t_active) { t_active = (s && s->timing) ? &s->timer : nullptr; }
+    ~TimerScope() { t_active = prev; }
+};
 
 lmrs_status ensure(lmrs_scene* s, DevBuf& b, size_t bytes) {
     if (bytes == 0) bytes = 16;
@@ -418,6 +464,7 @@ lmrs_status lmrs_get_solution(lmrs_scene* s, float* dst) {
 
 lmrs_status lmrs_preprocess(lmrs_scene* s, const int32_t* view_ids, int32_t n_views, int64_t lm_step) {
     TRY(check_scene(s));
+    TimerScope ts_(s);
     if (!view_ids || n_views <= 0) return fail(s, LMRS_ERR_INVALID_ARG, "no views");
     for (int i = 0; i < n_views; ++i)
         if (view_ids[i] < 0 || view_ids[i] >= s->n_cams) return fail(s, LMRS_ERR_INVALID_ARG, "view id out of range");
@@ -439,13 +486,16 @@ lmrs_status lmrs_preprocess(lmrs_scene* s, const int32_t* view_ids, int32_t n_vi
     TRY(build_layout(s));
     CK(s, cudaMemcpyAsync(s->views.p, s->views_h.data(), sizeof(int) * n_views, cudaMemcpyHostToDevice, s->st));
     Ctx c = s->ctx();
+    CK(s, cudaMemsetAsync(s->total.p, 0, 2 * sizeof(unsigned long long), s->st));
     launch_sample(c, lm_step, s->cfg.seed, s->st);
     launch_prep_fwd(c, s->st);
     scan_u64(c.cnt, (long long)pairs, s->total.as<unsigned long long>(), s->scan_tmp.p, s->scan_tmp.cap, s->st);
     CHECK_LAUNCH(s);
-    unsigned long long total = 0;
-    CK(s, cudaMemcpyAsync(&total, s->total.p, sizeof(total), cudaMemcpyDeviceToHost, s->st));
+    unsigned long long tot2[2] = {0ull, 0ull};
+    CK(s, cudaMemcpyAsync(tot2, s->total.p, sizeof(tot2), cudaMemcpyDeviceToHost, s->st));
     CK(s, cudaStreamSynchronize(s->st));
+    const unsigned long long total = tot2[0];
+    s->nvisible = (long long)tot2[1];
     if (total >= (1ull << 31)) return fail(s, LMRS_ERR_BUDGET, "more than 2^31 (view, tile, Gaussian) pairs");
     s->npairs = (long long)total;
     const size_t np = std::max<size_t>((size_t)total, 1);
@@ -469,6 +519,7 @@ lmrs_status lmrs_preprocess(lmrs_scene* s, const int32_t* view_ids, int32_t n_vi
 
 lmrs_status lmrs_render(lmrs_scene* s, float* images_dev, float* residuals_dev) {
     TRY(check_scene(s));
+    TimerScope ts_(s);
     TRY(need_pre(s));
     Ctx c = s->ctx();
     CK(s, cudaMemsetAsync(&c.sc->loss_num, 0, 2 * sizeof(double), s->st));
@@ -483,6 +534,7 @@ lmrs_status lmrs_render(lmrs_scene* s, float* images_dev, float* residuals_dev) 
 
 lmrs_status lmrs_jvp(lmrs_scene* s, const float* v, float* u) {
     TRY(check_scene(s));
+    TimerScope ts_(s);
     if (!v || !u) return fail(s, LMRS_ERR_INVALID_ARG, "null vector");
     TRY(need_pre(s));
     Ctx c = s->ctx();
@@ -494,6 +546,7 @@ lmrs_status lmrs_jvp(lmrs_scene* s, const float* v, float* u) {
 
 lmrs_status lmrs_vjp(lmrs_scene* s, const float* u, float* g) {
     TRY(check_scene(s));
+    TimerScope ts_(s);
     if (!u || !g) return fail(s, LMRS_ERR_INVALID_ARG, "null vector");
     TRY(need_render(s));
     Ctx c = s->ctx();
@@ -506,6 +559,7 @@ lmrs_status lmrs_vjp(lmrs_scene* s, const float* u, float* g) {
 
 lmrs_status lmrs_rhs(lmrs_scene* s, float* b) {
     TRY(check_scene(s));
+    TimerScope ts_(s);
     if (!b) return fail(s, LMRS_ERR_INVALID_ARG, "null vector");
     TRY(need_render(s));
     Ctx c = s->ctx();
@@ -518,6 +572,7 @@ lmrs_status lmrs_rhs(lmrs_scene* s, float* b) {
 
 lmrs_status lmrs_jtj_diag(lmrs_scene* s, float* d) {
     TRY(check_scene(s));
+    TimerScope ts_(s);
     TRY(need_render(s));
     TRY(do_jtj_diag(s));
     if (d) CK(s, cudaMemcpyAsync(d, s->D.p, sizeof(float) * s->P, cudaMemcpyDeviceToDevice, s->st));
@@ -526,6 +581,7 @@ lmrs_status lmrs_jtj_diag(lmrs_scene* s, float* d) {
 
 lmrs_status lmrs_jtjv(lmrs_scene* s, const float* v, float* out) {
     TRY(check_scene(s));
+    TimerScope ts_(s);
     if (!v || !out) return fail(s, LMRS_ERR_INVALID_ARG, "null vector");
     TRY(need_pre(s));
     if (s->cfg.damping_mode == 1 && !s->have_D)
@@ -553,6 +609,7 @@ lmrs_status lmrs_jtjv(lmrs_scene* s, const float* v, float* out) {
 
 lmrs_status lmrs_cg_solve(lmrs_scene* s, const float* b, float* x, int32_t iters, lmrs_cg_stats* st) {
     TRY(check_scene(s));
+    TimerScope ts_(s);
     if (!b || !x || iters < 0) return fail(s, LMRS_ERR_INVALID_ARG, "bad CG arguments");
     TRY(need_pre(s));
     if (!s->have_D) return fail(s, LMRS_ERR_NOT_PREPROCESSED, "CG needs lmrs_jtj_diag (preconditioner) first");
@@ -575,6 +632,7 @@ lmrs_status lmrs_cg_solve(lmrs_scene* s, const float* b, float* x, int32_t iters
 
 lmrs_status lmrs_step_size(lmrs_scene* s, const float* x, int64_t lm_step, double* eta) {
     TRY(check_scene(s));
+    TimerScope ts_(s);
     if (!x || !eta) return fail(s, LMRS_ERR_INVALID_ARG, "null argument");
     Ctx c = s->ctx();
     CK(s, cudaMemsetAsync(&c.sc->max_dc_bits, 0, sizeof(unsigned int), s->st));
@@ -593,6 +651,7 @@ lmrs_status lmrs_step_size(lmrs_scene* s, const float* x, int64_t lm_step, doubl
 lmrs_status lmrs_lm_step(lmrs_scene* s, const int32_t* view_ids, int32_t n_views, int64_t lm_step,
                          lmrs_step_stats* st) {
     TRY(check_scene(s));
+    TimerScope ts_(s);
     TRY(lmrs_preprocess(s, view_ids, n_views, lm_step));
     TRY(lmrs_render(s, nullptr, nullptr));
     TRY(lmrs_rhs(s, s->b.as<float>()));
@@ -623,9 +682,45 @@ lmrs_status lmrs_lm_step(lmrs_scene* s, const int32_t* view_ids, int32_t n_views
     return LMRS_OK;
 }
 
+lmrs_status lmrs_set_timing(lmrs_scene* s, int32_t enable) {
+    TRY(check_scene(s));
+    s->timing = enable != 0;
+    return LMRS_OK;
+}
+
+lmrs_status lmrs_get_timing(lmrs_scene* s, lmrs_kernel_time* out, int32_t max_entries, int32_t* n_entries) {
+    TRY(check_scene(s));
+    if (!n_entries || (max_entries > 0 && !out)) return fail(s, LMRS_ERR_INVALID_ARG, "null output");
+    CK(s, cudaStreamSynchronize(s->st));
+    std::vector<lmrs_kernel_time> agg;
+    for (auto& r : s->timer.recs) {
+        float ms = 0.f;
+        CK(s, cudaEventElapsedTime(&ms, r.a, r.b));
+        lmrs_kernel_time* k = nullptr;
+        for (auto& e : agg)
+            if (std::strncmp(e.name, r.name, sizeof(e.name) - 1) == 0) k = &e;
+        if (!k) {
+            lmrs_kernel_time e;
+            std::memset(&e, 0, sizeof(e));
+            std::strncpy(e.name, r.name, sizeof(e.name) - 1);
+            agg.push_back(e);
+            k = &agg.back();
+        }
+        k->launches += 1;
+        k->total_ms += ms;
+        s->timer.pool.push_back(r.a);
+        s->timer.pool.push_back(r.b);
+    }
+    s->timer.recs.clear();
+    *n_entries = (int32_t)agg.size();
+    for (int i = 0; i < (int)agg.size() && i < max_entries; ++i) out[i] = agg[i];
+    return LMRS_OK;
+}
+
 int64_t lmrs_num_params(const lmrs_scene* s) { return s ? s->P : -1; }
 int64_t lmrs_num_samples(const lmrs_scene* s) { return s && s->layout_nv >= 0 ? s->S : -1; }
 int64_t lmrs_num_pairs(const lmrs_scene* s) { return s && s->preprocessed ? s->npairs : -1; }
+int64_t lmrs_num_visible(const lmrs_scene* s) { return s && s->preprocessed ? s->nvisible : -1; }
 
 lmrs_status lmrs_get_samples(lmrs_scene* s, uint8_t* off, int32_t* tile_off) {
     TRY(check_scene(s));

@@ -46,6 +46,10 @@ class CgStats(C.Structure):
                 ("alpha", C.c_double * 64), ("beta", C.c_double * 64), ("iters", C.c_int32)]
 
 
+class KernelTime(C.Structure):
+    _fields_ = [("name", C.c_char * 64), ("launches", C.c_int64), ("total_ms", C.c_double)]
+
+
 class StepStats(C.Structure):
     _fields_ = [("loss", C.c_double), ("eta", C.c_double), ("max_dc", C.c_double), ("rz0", C.c_double),
                 ("rz_final", C.c_double), ("n_samples", C.c_int64), ("n_pairs", C.c_int64)]
@@ -73,8 +77,11 @@ _SIGS = {
     "lmrs_num_params": (C.c_int64, [_P]),
     "lmrs_num_samples": (C.c_int64, [_P]),
     "lmrs_num_pairs": (C.c_int64, [_P]),
+    "lmrs_num_visible": (C.c_int64, [_P]),
     "lmrs_get_samples": (_S, [_P, _P, _P]),
     "lmrs_get_tile_lists": (_S, [_P, _P, _P]),
+    "lmrs_set_timing": (_S, [_P, C.c_int32]),
+    "lmrs_get_timing": (_S, [_P, C.POINTER(KernelTime), C.c_int32, C.POINTER(C.c_int32)]),
     "lmrs_synchronize": (_S, [_P]),
     "lmrs_status_str": (C.c_char_p, [_S]),
     "lmrs_last_error": (C.c_char_p, [_P]),
@@ -234,6 +241,10 @@ def lmrs_num_pairs(scene):
     return int(lib().lmrs_num_pairs(scene))
 
 
+def lmrs_num_visible(scene):
+    return int(lib().lmrs_num_visible(scene))
+
+
 def lmrs_get_samples(scene, n_views, n_tiles):
     S = lmrs_num_samples(scene)
     off = np.empty(S, np.uint8)
@@ -248,6 +259,18 @@ def lmrs_get_tile_lists(scene, n_views, n_tiles):
     ids = np.empty(max(n, 1), np.int32)
     _check(lib().lmrs_get_tile_lists(scene, ranges.ctypes.data, ids.ctypes.data), scene)
     return ranges, ids[:n]
+
+
+def lmrs_set_timing(scene, enable=True):
+    _check(lib().lmrs_set_timing(scene, 1 if enable else 0), scene)
+
+
+def lmrs_get_timing(scene):
+    """{kernel name: (launches, total ms)} since the previous call."""
+    buf = (KernelTime * 128)()
+    n = C.c_int32()
+    _check(lib().lmrs_get_timing(scene, buf, 128, C.byref(n)), scene)
+    return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(min(n.value, 128))}
 
 
 def lmrs_synchronize(scene):

@@ -59,8 +59,13 @@ def test_tile_lists_bit_exact(case):
     ranges, ids = case.lmrs.lmrs_get_tile_lists(case.gpu.h, case.gpu.n_views, case.gpu.n_tiles)
     r_ref, ids_ref = case.orc.lists()
     assert case.gpu.n_pairs == len(ids_ref)
-    np.testing.assert_array_equal(ranges, r_ref)
-    np.testing.assert_array_equal(ids, ids_ref)
+    np.testing.assert_array_equal(ids, ids_ref)  # whole sorted order
+    # per tile: same length and, for non-empty tiles, the same bounds (an
+    # empty tile's bounds carry no information)
+    len_gpu, len_ref = ranges[:, 1] - ranges[:, 0], r_ref[:, 1] - r_ref[:, 0]
+    np.testing.assert_array_equal(len_gpu, len_ref)
+    ne = len_ref > 0
+    np.testing.assert_array_equal(ranges[ne], r_ref[ne])
 
 
 def test_render_and_residuals(case):
@@ -146,6 +151,21 @@ def test_jtjv(case, damping_mode):
     np.testing.assert_allclose(out_h, got, rtol=1e-5, atol=1e-6 * np.abs(got).max())
 
 
+def assert_solution_close(pair, x, x_ref, D_ref, tol=CG_TOL):
+    """CG iterates agree in the energy norm |e|_A / |x|_A (the norm CG
+    minimises) and in the 2-norm over the well-determined parameters
+    (D_j >= 1e-6 max D).  Parameters with a near-null Jacobian column get
+    x_j ~ b_j / ((1 + lambda) D_j) under diagonal damping, where the FP32
+    and FP64 diagonals legitimately differ in relative terms."""
+    e = x - x_ref
+    a_norm = np.sqrt(max(e @ pair.orc.apply(e, D_ref), 0.0)) / np.sqrt(x_ref @ pair.orc.apply(x_ref, D_ref))
+    assert a_norm <= tol, f"A-norm rel error {a_norm:.3e}"
+    well = D_ref >= 1e-6 * D_ref.max()
+    assert well.sum() >= 0.5 * (D_ref > 0).sum()
+    assert normwise_rel(x[well], x_ref[well]) <= tol
+    return a_norm
+
+
 def test_cg_solve(case):
     case.lmrs.lmrs_render(case.gpu.h)
     case.lmrs.lmrs_jtj_diag(case.gpu.h)
@@ -155,7 +175,7 @@ def test_cg_solve(case):
     st = case.lmrs.lmrs_cg_solve(case.gpu.h, b, x, 10)
     D_ref = case.orc.diag()
     x_ref, st_ref = case.orc.cg(case.orc.rhs(), D_ref, 10)
-    assert normwise_rel(case.host(x), x_ref) <= CG_TOL
+    assert_solution_close(case, case.host(x), x_ref, D_ref)
     assert abs(st.rz0 - st_ref[0]) <= 1e-4 * abs(st_ref[0])
 
 
@@ -166,10 +186,14 @@ def test_lm_step_and_step_size(case):
         pair = Pair(case.scene, case.targets_np, **cfg)
         p0 = pair.scene.params.astype(np.float64)
         st = pair.lmrs.lmrs_lm_step(pair.gpu.h, case.views, step)
+        pair.orc.begin_step(case.views, step)
+        D_ref = pair.orc.diag()
         x_ref, st_ref = pair.orc.lm_step(case.views, step)
         x = np.zeros(pair.P, np.float32)
         pair.lmrs.lmrs_get_solution(pair.gpu.h, x)
-        assert normwise_rel(x, x_ref) <= CG_TOL
+        pair.orc.set_params(p0)  # the operator at the pre-step point
+        pair.orc.begin_step(case.views, step)
+        assert_solution_close(pair, x.astype(np.float64), x_ref, D_ref)
         # the step size is exact given x (Sec. 4.5, App. D)
         eta_gpu_rule = pair.orc.step_size(x.astype(np.float64), step)
         assert st.eta == pytest.approx(eta_gpu_rule, rel=1e-12)
@@ -177,7 +201,10 @@ def test_lm_step_and_step_size(case):
         assert st.loss == pytest.approx(st_ref[0], rel=1e-5)
         p1 = np.zeros(pair.P, np.float32)
         pair.lmrs.lmrs_get_params(pair.gpu.h, p1)
-        assert normwise_rel(p1 - p0, pair.orc.get_params() - p0) <= CG_TOL
+        well = D_ref >= 1e-6 * D_ref.max()
+        # beta_1 = beta_0 - eta x; compared on the well-determined entries
+        np.testing.assert_allclose(p1 - p0, -st.eta * x, rtol=1e-5, atol=1e-6 * np.abs(x).max() * st.eta + 1e-7)
+        assert normwise_rel((p1 - p0)[well], -st_ref[1] * x_ref[well]) <= CG_TOL
         assert pair.lmrs.lmrs_step_size(pair.gpu.h, pair.cuda(x), step) == pytest.approx(eta_gpu_rule, rel=1e-12)
         pair.gpu.close()
 
