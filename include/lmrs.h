@@ -181,6 +181,30 @@ lmrs_status lmrs_cg_solve(lmrs_scene* scene, const float* b_dev, float* x_dev, i
  * max |x_dc|) (lr_cap when that maximum is 0); returned in *eta_host. */
 lmrs_status lmrs_step_size(lmrs_scene* scene, const float* x_dev, int64_t lm_step, double* eta_host);
 
+/* The step size of lmrs_step_size without a scene and without allocating
+ * any device memory.  The paper has no counterpart: this entry point exists
+ * for callers that cannot call cudaMalloc, for example code whose device
+ * memory is owned by another allocator (a framework's caching pool that has
+ * reserved the free memory, so a driver allocation can fail or force a
+ * device-wide synchronisation) and latency-critical loops in which an
+ * allocation or free would stall.
+ *   x_dev      : solution, G * (11 + 3 (sh_degree+1)^2) floats (device), read.
+ *   n_gauss    : G, at most 8,388,608 (4096 blocks of 2048 Gaussians);
+ *                larger G returns LMRS_ERR_BUDGET before any device work.
+ *   lm_step, lr_warm, lr_cap, color_bound, warm_iters: as in lmrs_config.
+ *   cuda_stream: stream of the launch (NULL = legacy stream).
+ *   *eta_host  : the step size (host); the call synchronises the stream.
+ * Scratch: a 16,512-byte static device array that every GPU loading the
+ * library holds until the process exits.  The first call on a device looks
+ * up its address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  All calls on a device share the
+ * array, so calls that overlap on the GPU race; each call clears the words
+ * that must start at zero.  Errors: LMRS_ERR_INVALID_ARG for null pointers,
+ * n_gauss <= 0 or sh_degree outside 0..3; LMRS_ERR_CUDA if a CUDA call fails. */
+lmrs_status lmrs_step_size_noalloc(const float* x_dev, int64_t n_gauss, int32_t sh_degree, int64_t lm_step,
+                                   double lr_warm, double lr_cap, double color_bound, int32_t warm_iters,
+                                   void* cuda_stream, double* eta_host);
+
 /* One LM step (Alg. 1): preprocess, render, b = J^T W r, D, PCG with
  * cfg.cg_iters iterations, step size, and the update beta <- beta - eta x
  * (the descent reading of Eq. 8 with r = render - target).  st may be NULL

@@ -72,6 +72,8 @@ _SIGS = {
     "lmrs_jtjv": (_S, [_P, _P, _P]),
     "lmrs_cg_solve": (_S, [_P, _P, _P, C.c_int32, C.POINTER(CgStats)]),
     "lmrs_step_size": (_S, [_P, _P, C.c_int64, C.POINTER(C.c_double)]),
+    "lmrs_step_size_noalloc": (_S, [_P, C.c_int64, C.c_int32, C.c_int64, C.c_double, C.c_double, C.c_double,
+                                    C.c_int32, _P, C.POINTER(C.c_double)]),
     "lmrs_lm_step": (_S, [_P, _P, C.c_int32, C.c_int64, C.POINTER(StepStats)]),
     "lmrs_get_solution": (_S, [_P, _P]),
     "lmrs_num_params": (C.c_int64, [_P]),
@@ -214,6 +216,16 @@ def lmrs_cg_solve(scene, b, x, iters, stats=True):
 def lmrs_step_size(scene, x, lm_step):
     eta = C.c_double()
     _check(lib().lmrs_step_size(scene, _ptr(x), int(lm_step), C.byref(eta)), scene)
+    return eta.value
+
+
+def lmrs_step_size_noalloc(x, n_gauss, sh_degree, lm_step, lr_warm, lr_cap, color_bound, warm_iters, stream=None):
+    """Step size without a scene and without device allocation (for callers
+    that cannot call cudaMalloc); see include/lmrs.h."""
+    eta = C.c_double()
+    _check(lib().lmrs_step_size_noalloc(_ptr(x), int(n_gauss), int(sh_degree), int(lm_step), float(lr_warm),
+                                        float(lr_cap), float(color_bound), int(warm_iters),
+                                        _ptr(stream) if stream is not None else None, C.byref(eta)))
     return eta.value
 
 
