@@ -80,6 +80,27 @@ __global__ void __launch_bounds__(kVecBlock) k_cg_update(Ctx c, int iter, const 
     }
 }
 
+// p = z + beta p (beta = r_{i+1}^T z_{i+1} / r_i^T z_i, 0 before the first
+// iteration so that p_0 = z_0).  float4 over the body, scalars for the tail.
+__global__ void __launch_bounds__(kVecBlock) k_cg_direction(Ctx c, const float* z, float* p) {
+    const float beta = (float)c.sc->beta;
+    const long long n4 = c.P / 4;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const float4* z4 = reinterpret_cast<const float4*>(z);
+    float4* p4 = reinterpret_cast<float4*>(p);
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n4; j += stride) {
+        const float4 a = z4[j];
+        float4 b = p4[j];
+        b.x = a.x + beta * b.x;
+        b.y = a.y + beta * b.y;
+        b.z = a.z + beta * b.z;
+        b.w = a.w + beta * b.w;
+        p4[j] = b;
+    }
+    for (long long j = 4 * n4 + (long long)blockIdx.x * blockDim.x + threadIdx.x; j < c.P; j += stride)
+        p[j] = z[j] + beta * p[j];
+}
+
 // max |x| over the SH degree-0 entries (the colour parameters of Sec. 4.5).
 __global__ void __launch_bounds__(kVecBlock) k_max_dc(Ctx c, const float* x) {
     float m = 0.f;
@@ -122,7 +143,9 @@ void launch_cg_update(const Ctx& c, int iter, const float* p, const float* Ap, c
                       float* z, cudaStream_t st) {
     LMRS_LAUNCH(k_cg_update, vec_grid(c.P), kVecBlock, 0, st, c, iter, p, Ap, minv, x, r, z);
 }
-void launch_cg_finish(const Ctx&, const float*, float*, cudaStream_t) {}
+void launch_cg_direction(const Ctx& c, const float* z, float* p, cudaStream_t st) {
+    LMRS_LAUNCH(k_cg_direction, vec_grid(c.P / 4 + 1), kVecBlock, 0, st, c, z, p);
+}
 void launch_max_dc(const Ctx& c, const float* x, cudaStream_t st) {
     LMRS_LAUNCH(k_max_dc, vec_grid(c.G), kVecBlock, 0, st, c, x);
 }

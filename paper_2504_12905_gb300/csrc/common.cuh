@@ -18,6 +18,7 @@ constexpr int kRecF4 = 6;                   // float4 per (view, Gaussian) recor
 constexpr int kCotF = 12;                   // floats per (view, Gaussian) cotangent slot (9 used)
 constexpr int kGramF = 40;                  // floats per (view, Gaussian) Gram slot
 constexpr int kMaxPartials = 4096;          // block partials of the FP64 reductions
+constexpr int kGaussF4 = 9;                 // float4 planes of the per-Gaussian cache
 
 // Camera as the kernels read it.  R, t, fx, fy, cx, cy, limx, limy, znear are
 // the FP32 values the list decisions use.
@@ -65,6 +66,7 @@ struct Ctx {
     const int* views;       // camera id per slot
     const float* targets;   // [n_cams][H][W][3] or null
     // per (slot, Gaussian) pair, index slot * G + g
+    float4* gcache;         // per Gaussian, kGaussF4 planes of G float4 (view-independent 3D state)
     float4* rec;            // kRecF4 float4: primal (3) then tangent (3)
     int4* rect;             // inclusive tile rectangle, x0 > x1 when culled
     unsigned int* depth;    // FP32 depth bits
@@ -84,6 +86,7 @@ struct Ctx {
     long long S;
     const int2* work;       // (slot * T + tile, first sample in tile) per warp item
     int nwork;
+    int* item_cost;         // [nwork] list entries a work item traverses (from the forward render)
     // per-sample caches
     float* resid;           // [S][3]
     float* cacheC;          // [S][3] FP32 (or BF16 in cacheCh)
@@ -102,10 +105,13 @@ void note_launch();
 // ---- preprocess.cu --------------------------------------------------------
 void set_sh_constants();
 void launch_sample(const Ctx& c, long long lm_step, unsigned long long seed, cudaStream_t st);
+// per-Gaussian view-independent cache (scale, rotation, 3D covariance,
+// opacity); valid until the parameters change
+void launch_prep_gauss(const Ctx& c, cudaStream_t st);
 void launch_prep_fwd(const Ctx& c, cudaStream_t st);
-// tangent v (P floats). With p_update, the tangent is p = z + beta p (beta
-// from the device scalars), written back to p.
-void launch_prep_jvp(const Ctx& c, const float* v, float* p_update, const float* z, cudaStream_t st);
+// tangent features of v (P floats) for every visible pair; clears the
+// pairs' cotangent slots
+void launch_prep_jvp(const Ctx& c, const float* v, cudaStream_t st);
 // g = J^T u chained from the cotangent slots (+ lambda damping of v if v).
 // With dot, pAp = v^T g in FP64 and alpha = rz / pAp on the device.
 void launch_prep_vjp(const Ctx& c, float* g, const float* v, const float* D, bool dot, cudaStream_t st);
@@ -137,6 +143,11 @@ void launch_raster_vjp(const Ctx& c, const float* u, cudaStream_t st);
 // Fused J^T W J: JVP pass then VJP pass per warp item.
 void launch_raster_jtj(const Ctx& c, cudaStream_t st);
 void launch_raster_gram(const Ctx& c, cudaStream_t st);
+// Longest-first order of the work items by the traversal lengths the forward
+// render recorded: sorted[k] = work[order[k]].  Scratch: keys/vals and their
+// alternates (nwork each) and radix_tmp_bytes(nwork).
+void launch_order_work(const Ctx& c, unsigned long long* keys, unsigned int* vals, unsigned long long* keys_alt,
+                       unsigned int* vals_alt, void* tmp, size_t tmp_bytes, int2* sorted, cudaStream_t st);
 
 // ---- cg.cu ----------------------------------------------------------------
 void launch_precond(const Ctx& c, const float* D, float* minv, cudaStream_t st);
@@ -144,7 +155,8 @@ void launch_cg_init(const Ctx& c, const float* b, const float* minv, float* x, f
                     cudaStream_t st);
 void launch_cg_update(const Ctx& c, int iter, const float* p, const float* Ap, const float* minv, float* x, float* r,
                       float* z, cudaStream_t st);
-void launch_cg_finish(const Ctx& c, const float* p, float* x, cudaStream_t st);
+// p = z + beta p with beta from the device scalars (Alg. 1, last loop line)
+void launch_cg_direction(const Ctx& c, const float* z, float* p, cudaStream_t st);
 void launch_max_dc(const Ctx& c, const float* x, cudaStream_t st);
 void launch_lm_update(const Ctx& c, long long lm_step, double lr_warm, double lr_cap, double color_bound,
                       int warm_iters, const float* x, float* params, cudaStream_t st);
@@ -167,5 +179,16 @@ void timer_stop(LaunchTimer* t, int rec, cudaStream_t st);
         ::lmrs::LaunchTimer* t_ = ::lmrs::active_timer();                       \
         const int r_ = t_ ? ::lmrs::timer_start(t_, #kernel, (stream)) : -1;    \
         kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);            \
+        if (t_) ::lmrs::timer_stop(t_, r_, (stream));                           \
+    } while (0)
+
+// The same for a kernel given as a function pointer with an explicit name
+// (template kernels whose argument lists contain commas).
+#define LMRS_LAUNCH_AS(name, kptr, grid, block, smem, stream, ...)              \
+    do {                                                                        \
+        ::lmrs::note_launch();                                                  \
+        ::lmrs::LaunchTimer* t_ = ::lmrs::active_timer();                       \
+        const int r_ = t_ ? ::lmrs::timer_start(t_, (name), (stream)) : -1;     \
+        (kptr)<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);            \
         if (t_) ::lmrs::timer_stop(t_, r_, (stream));                           \
     } while (0)

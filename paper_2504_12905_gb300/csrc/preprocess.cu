@@ -1,14 +1,19 @@
 // Per-(view, Gaussian) preprocessing of the LM-RS hot path.
 //
-//   k_sample     per-tile stratified pixel sampling (Sec. 4.4)
-//   k_prep_fwd   projection (Sec. 3, Eqs. 2-4): list decisions in FP32 with a
-//                fixed operation order, 2D features, tile counts
-//   k_prep_jvp   forward-mode tangents of the 2D features (Alg. 3, the
-//                "preprocessing" half of the Jv kernel, App. A)
-//   k_prep_vjp   reverse mode from the per-pair 2D cotangents to the 3D
-//                parameters (second launch of the J^T v kernel, App. A), plus
-//                the damping of Eq. 8 and p^T A p in FP64
-//   k_prep_diag  diag(J^T W J) from per-pair 9x9 Gram blocks (App. A "Diag")
+//   k_sample        per-tile stratified pixel sampling (Sec. 4.4)
+//   k_prep_gauss    view-independent 3D state per Gaussian (scale, normalised
+//                   quaternion, R, M = R S, Sigma = M M^T, opacity), once per
+//                   LM step (Sec. 3, Eq. 3)
+//   k_prep_fwd      projection (Sec. 3, Eqs. 2-4): list decisions in FP32 with
+//                   a fixed operation order, 2D features, tile counts
+//   k_prep_jvp      forward-mode tangents of the 2D features (Alg. 3, the
+//                   "preprocessing" half of the Jv kernel, App. A)
+//   k_prep_vjp      reverse mode from the per-pair 2D cotangents to the 3D
+//                   parameters (second launch of the J^T v kernel, App. A),
+//                   plus the damping of Eq. 8 and p^T A p in FP64
+//   k_prep_diag     diag(J^T W J) from per-pair 9x9 Gram blocks (App. A "Diag")
+// Kernels are instantiated per SH degree (0..3) so coefficient arrays live
+// in registers.
 #include <cmath>
 
 #include "common.cuh"
@@ -37,20 +42,26 @@ void set_sh_constants() {
     cudaMemcpyToSymbol(c_sh, h, sizeof(h));
 }
 
+template <int DEG>
+struct Sh {
+    static constexpr int K = (DEG + 1) * (DEG + 1);
+};
+
 // Basis values, index l^2 + l + m.
-__device__ __forceinline__ void sh_eval(int deg, float x, float y, float z, float* Y) {
+template <int DEG>
+__device__ __forceinline__ void sh_eval(float x, float y, float z, float* Y) {
     Y[0] = c_sh[0];
-    if (deg < 1) return;
+    if (DEG < 1) return;
     Y[1] = c_sh[1] * y;
     Y[2] = c_sh[1] * z;
     Y[3] = c_sh[1] * x;
-    if (deg < 2) return;
+    if (DEG < 2) return;
     Y[4] = c_sh[2] * x * y;
     Y[5] = c_sh[2] * y * z;
     Y[6] = c_sh[3] * (3.f * z * z - 1.f);
     Y[7] = c_sh[2] * x * z;
     Y[8] = c_sh[4] * (x * x - y * y);
-    if (deg < 3) return;
+    if (DEG < 3) return;
     Y[9] = c_sh[5] * y * (3.f * x * x - y * y);
     Y[10] = c_sh[6] * x * y * z;
     Y[11] = c_sh[7] * y * (5.f * z * z - 1.f);
@@ -61,21 +72,22 @@ __device__ __forceinline__ void sh_eval(int deg, float x, float y, float z, floa
 }
 
 // g = sum_{k>=1} w[k] grad Y_k(x, y, z)  (gradient in R^3 of the polynomial).
-__device__ __forceinline__ void sh_weighted_grad(int deg, float x, float y, float z, const float* w, float g[3]) {
+template <int DEG>
+__device__ __forceinline__ void sh_weighted_grad(float x, float y, float z, const float* w, float g[3]) {
     g[0] = g[1] = g[2] = 0.f;
-    if (deg < 1) return;
+    if (DEG < 1) return;
     const float k1 = c_sh[1];
     g[1] += w[1] * k1;
     g[2] += w[2] * k1;
     g[0] += w[3] * k1;
-    if (deg < 2) return;
+    if (DEG < 2) return;
     const float k2 = c_sh[2], k20 = c_sh[3], k22 = c_sh[4];
     g[0] += w[4] * k2 * y;  g[1] += w[4] * k2 * x;
     g[1] += w[5] * k2 * z;  g[2] += w[5] * k2 * y;
     g[2] += w[6] * 6.f * k20 * z;
     g[0] += w[7] * k2 * z;  g[2] += w[7] * k2 * x;
     g[0] += w[8] * 2.f * k22 * x;  g[1] -= w[8] * 2.f * k22 * y;
-    if (deg < 3) return;
+    if (DEG < 3) return;
     const float k33 = c_sh[5], k32a = c_sh[6], k31 = c_sh[7], k30 = c_sh[8], k32 = c_sh[9];
     g[0] += w[9] * 6.f * k33 * x * y;
     g[1] += w[9] * 3.f * k33 * (x * x - y * y);
@@ -87,38 +99,51 @@ __device__ __forceinline__ void sh_weighted_grad(int deg, float x, float y, floa
     g[0] += w[15] * 3.f * k33 * (x * x - y * y);  g[1] -= w[15] * 6.f * k33 * x * y;
 }
 
-// ---------------------------------------------------------------------------
-// Primal quantities of one (view, Gaussian) pair.
-// ---------------------------------------------------------------------------
-struct GParams {
-    float X[3], ls[3], q[4], th;
-};
-
-__device__ __forceinline__ GParams load_gparams(const float* p, int G, int g) {
-    GParams r;
-    const long long G3 = 3ll * G;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        r.X[k] = p[3ll * g + k];
-        r.ls[k] = p[G3 + 3ll * g + k];
-    }
-    // the quaternion block starts at float 6G: not 16-byte aligned for odd G
-#pragma unroll
-    for (int k = 0; k < 4; ++k) r.q[k] = p[6ll * G + 4ll * g + k];
-    r.th = p[10ll * G + g];
-    return r;
+// gY[k] = grad Y_k(x, y, z) . d  (directional derivative of each basis function).
+template <int DEG>
+__device__ __forceinline__ void sh_dir_deriv(float x, float y, float z, const float d[3], float* gY) {
+    gY[0] = 0.f;
+    if (DEG < 1) return;
+    const float k1 = c_sh[1];
+    gY[1] = k1 * d[1];
+    gY[2] = k1 * d[2];
+    gY[3] = k1 * d[0];
+    if (DEG < 2) return;
+    const float k2 = c_sh[2], k20 = c_sh[3], k22 = c_sh[4];
+    gY[4] = k2 * (d[0] * y + x * d[1]);
+    gY[5] = k2 * (d[1] * z + y * d[2]);
+    gY[6] = 6.f * k20 * z * d[2];
+    gY[7] = k2 * (d[0] * z + x * d[2]);
+    gY[8] = 2.f * k22 * (x * d[0] - y * d[1]);
+    if (DEG < 3) return;
+    const float k33 = c_sh[5], k32a = c_sh[6], k31 = c_sh[7], k30 = c_sh[8], k32 = c_sh[9];
+    gY[9] = k33 * (6.f * x * y * d[0] + 3.f * (x * x - y * y) * d[1]);
+    gY[10] = k32a * (y * z * d[0] + x * z * d[1] + x * y * d[2]);
+    gY[11] = k31 * ((5.f * z * z - 1.f) * d[1] + 10.f * y * z * d[2]);
+    gY[12] = k30 * (15.f * z * z - 3.f) * d[2];
+    gY[13] = k31 * ((5.f * z * z - 1.f) * d[0] + 10.f * x * z * d[2]);
+    gY[14] = k32 * (2.f * x * z * d[0] - 2.f * y * z * d[1] + (x * x - y * y) * d[2]);
+    gY[15] = k33 * (3.f * (x * x - y * y) * d[0] - 6.f * x * y * d[1]);
 }
 
+// ---------------------------------------------------------------------------
+// Primal quantities.
+// ---------------------------------------------------------------------------
 struct Prim {
-    float t[3], s[3], qn, qh[4];
+    // per Gaussian (cache)
+    float s[3], qn, qh[4];
     float R[9], M[9], S[9];
+    float o;
+    bool valid;
+    // per (view, Gaussian)
+    float t[3];
     float ux, uy;
     bool clx, cly;
     float j00, j02, j11, j12;
     float T[6], V[6];
     float a, b, c, det;
     float mux, muy;
-    float A, B, C, o;
+    float A, B, C;
     float dir[3], dn;
     float col[3];
     bool clamped[3];
@@ -129,28 +154,37 @@ __device__ __forceinline__ float ra(float a, float b) { return __fadd_rn(a, b); 
 __device__ __forceinline__ float rs(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ float rd(float a, float b) { return __fdiv_rn(a, b); }
 
-// Geometry with the list decisions.  Every operation is one binary32
-// operation in the written order (no contraction), the scale exponential is
-// the binary32 rounding of the FP64 exponential; the same sequence as the
-// reference definition of the decisions, so visibility, depth key and tile
-// rectangle are reproducible bit for bit.  Returns false when culled.
-__device__ __forceinline__ bool prim_geometry(const GParams& gp, const CamDev& cam, int tiles_x, int tiles_y,
-                                              int tw, int th, Prim& P, int4* rect_out, float* depth_out) {
-    const float* R = cam.R;
-    const float* X = gp.X;
-    P.t[0] = ra(ra(ra(rm(R[0], X[0]), rm(R[1], X[1])), rm(R[2], X[2])), cam.t[0]);
-    P.t[1] = ra(ra(ra(rm(R[3], X[0]), rm(R[4], X[1])), rm(R[5], X[2])), cam.t[1]);
-    P.t[2] = ra(ra(ra(rm(R[6], X[0]), rm(R[7], X[1])), rm(R[8], X[2])), cam.t[2]);
-    if (!(P.t[2] > cam.znear)) return false;
+__device__ __forceinline__ void load_mean(const float* p, int g, float X[3]) {
 #pragma unroll
-    for (int j = 0; j < 3; ++j) P.s[j] = (float)exp((double)gp.ls[j]);
-    const float* q = gp.q;
-    float qq = ra(ra(ra(rm(q[0], q[0]), rm(q[1], q[1])), rm(q[2], q[2])), rm(q[3], q[3]));
-    if (!(qq > 0.f)) return false;
-    P.qn = __fsqrt_rn(qq);
-    const float w = rd(q[0], P.qn), x = rd(q[1], P.qn), y = rd(q[2], P.qn), z = rd(q[3], P.qn);
-    P.qh[0] = w; P.qh[1] = x; P.qh[2] = y; P.qh[3] = z;
-    float* r = P.R;
+    for (int k = 0; k < 3; ++k) X[k] = p[3ll * g + k];
+}
+
+template <int DEG>
+__device__ __forceinline__ void load_sh(const float* p, int G, int g, float* sh) {
+    constexpr int K3 = 3 * Sh<DEG>::K;
+    const float* src = p + 11ll * G + (long long)g * K3;
+#pragma unroll
+    for (int i = 0; i < K3; ++i) sh[i] = src[i];
+}
+
+// View-independent 3D state in the fixed FP32 operation order of the list
+// decisions: s = binary32(exp_fp64(log-scale)), q / |q|, R(q), M = R S,
+// Sigma = M M^T; every operation rounded on its own.
+__global__ void k_prep_gauss(Ctx c) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= c.G) return;
+    const float* p = c.params;
+    const long long G = c.G;
+    float s[3], q[4];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) s[j] = (float)exp((double)p[3 * G + 3ll * g + j]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) q[k] = p[6 * G + 4ll * g + k];
+    const float qq = ra(ra(ra(rm(q[0], q[0]), rm(q[1], q[1])), rm(q[2], q[2])), rm(q[3], q[3]));
+    const bool valid = qq > 0.f;
+    const float qn = valid ? __fsqrt_rn(qq) : 1.f;
+    const float w = rd(q[0], qn), x = rd(q[1], qn), y = rd(q[2], qn), z = rd(q[3], qn);
+    float r[9];
     r[0] = rs(1.f, rm(2.f, ra(rm(y, y), rm(z, z))));
     r[1] = rm(2.f, rs(rm(x, y), rm(w, z)));
     r[2] = rm(2.f, ra(rm(x, z), rm(w, y)));
@@ -160,19 +194,67 @@ __device__ __forceinline__ bool prim_geometry(const GParams& gp, const CamDev& c
     r[6] = rm(2.f, rs(rm(x, z), rm(w, y)));
     r[7] = rm(2.f, ra(rm(y, z), rm(w, x)));
     r[8] = rs(1.f, rm(2.f, ra(rm(x, x), rm(y, y))));
+    float m[9];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) P.M[3 * i + j] = rm(r[3 * i + j], P.s[j]);
-    const float* m = P.M;
+        for (int j = 0; j < 3; ++j) m[3 * i + j] = rm(r[3 * i + j], s[j]);
+    float S[6];  // S00 S01 S02 S11 S12 S22
+    int k = 0;
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int j = i; j < 3; ++j) {
-            float v = ra(ra(rm(m[3 * i], m[3 * j]), rm(m[3 * i + 1], m[3 * j + 1])), rm(m[3 * i + 2], m[3 * j + 2]));
-            P.S[3 * i + j] = v;
-            P.S[3 * j + i] = v;
-        }
+        for (int j = i; j < 3; ++j)
+            S[k++] = ra(ra(rm(m[3 * i], m[3 * j]), rm(m[3 * i + 1], m[3 * j + 1])), rm(m[3 * i + 2], m[3 * j + 2]));
+    const float o = 1.f / (1.f + expf(-p[10 * G + g]));
+    float4* gc = c.gcache;
+    gc[0 * G + g] = make_float4(s[0], s[1], s[2], qn);
+    gc[1 * G + g] = make_float4(w, x, y, z);
+    gc[2 * G + g] = make_float4(r[0], r[1], r[2], r[3]);
+    gc[3 * G + g] = make_float4(r[4], r[5], r[6], r[7]);
+    gc[4 * G + g] = make_float4(r[8], m[0], m[1], m[2]);
+    gc[5 * G + g] = make_float4(m[3], m[4], m[5], m[6]);
+    gc[6 * G + g] = make_float4(m[7], m[8], S[0], S[1]);
+    gc[7 * G + g] = make_float4(S[2], S[3], S[4], S[5]);
+    gc[8 * G + g] = make_float4(o, valid ? 1.f : 0.f, 0.f, 0.f);
+}
+
+__device__ __forceinline__ void load_gauss(const Ctx& c, int g, Prim& P) {
+    const long long G = c.G;
+    const float4* gc = c.gcache;
+    float4 v = gc[0 * G + g];
+    P.s[0] = v.x; P.s[1] = v.y; P.s[2] = v.z; P.qn = v.w;
+    v = gc[1 * G + g];
+    P.qh[0] = v.x; P.qh[1] = v.y; P.qh[2] = v.z; P.qh[3] = v.w;
+    v = gc[2 * G + g];
+    P.R[0] = v.x; P.R[1] = v.y; P.R[2] = v.z; P.R[3] = v.w;
+    v = gc[3 * G + g];
+    P.R[4] = v.x; P.R[5] = v.y; P.R[6] = v.z; P.R[7] = v.w;
+    v = gc[4 * G + g];
+    P.R[8] = v.x; P.M[0] = v.y; P.M[1] = v.z; P.M[2] = v.w;
+    v = gc[5 * G + g];
+    P.M[3] = v.x; P.M[4] = v.y; P.M[5] = v.z; P.M[6] = v.w;
+    v = gc[6 * G + g];
+    P.M[7] = v.x; P.M[8] = v.y; P.S[0] = v.z; P.S[1] = v.w;
+    v = gc[7 * G + g];
+    P.S[2] = v.x; P.S[4] = v.y; P.S[5] = v.z; P.S[8] = v.w;
+    P.S[3] = P.S[1]; P.S[6] = P.S[2]; P.S[7] = P.S[5];
+    v = gc[8 * G + g];
+    P.o = v.x;
+    P.valid = v.y != 0.f;
+}
+
+// Per-(view, Gaussian) projection with the list decisions, continuing the
+// fixed FP32 operation order of k_prep_gauss (so visibility, depth key and
+// tile rectangle are reproducible bit for bit).  Returns false when culled.
+__device__ __forceinline__ bool prim_project(const float X[3], const CamDev& cam, int tiles_x, int tiles_y, int tw,
+                                             int th, Prim& P, int4* rect_out, float* depth_out) {
+    const float* R = cam.R;
+    P.t[0] = ra(ra(ra(rm(R[0], X[0]), rm(R[1], X[1])), rm(R[2], X[2])), cam.t[0]);
+    P.t[1] = ra(ra(ra(rm(R[3], X[0]), rm(R[4], X[1])), rm(R[5], X[2])), cam.t[1]);
+    P.t[2] = ra(ra(ra(rm(R[6], X[0]), rm(R[7], X[1])), rm(R[8], X[2])), cam.t[2]);
+    if (!(P.t[2] > cam.znear)) return false;
+    if (!P.valid) return false;
     P.ux = rd(P.t[0], P.t[2]);
     P.uy = rd(P.t[1], P.t[2]);
     const float cux = fminf(fmaxf(P.ux, -cam.limx), cam.limx);
@@ -198,68 +280,65 @@ __device__ __forceinline__ bool prim_geometry(const GParams& gp, const CamDev& c
     P.c = ra(ra(ra(rm(P.V[3], P.T[3]), rm(P.V[4], P.T[4])), rm(P.V[5], P.T[5])), 0.3f);
     P.det = rs(rm(P.a, P.c), rm(P.b, P.b));
     if (!(P.det > 0.f)) return false;
-    const float mid = rm(0.5f, ra(P.a, P.c));
-    const float disc = fmaxf(rs(rm(mid, mid), P.det), 0.1f);
-    const float lam = ra(mid, __fsqrt_rn(disc));
-    const float rad = ceilf(rm(3.0f, __fsqrt_rn(lam)));
     P.mux = ra(rm(cam.fx, P.ux), cam.cx);
     P.muy = ra(rm(cam.fy, P.uy), cam.cy);
-    const float fx0 = floorf(rd(rs(P.mux, rad), (float)tw));
-    const float fx1 = floorf(rd(ra(P.mux, rad), (float)tw));
-    const float fy0 = floorf(rd(rs(P.muy, rad), (float)th));
-    const float fy1 = floorf(rd(ra(P.muy, rad), (float)th));
-    if (fx1 < 0.f || fx0 > (float)(tiles_x - 1) || fy1 < 0.f || fy0 > (float)(tiles_y - 1)) return false;
     if (rect_out) {
+        const float mid = rm(0.5f, ra(P.a, P.c));
+        const float disc = fmaxf(rs(rm(mid, mid), P.det), 0.1f);
+        const float lam = ra(mid, __fsqrt_rn(disc));
+        const float rad = ceilf(rm(3.0f, __fsqrt_rn(lam)));
+        const float fx0 = floorf(rd(rs(P.mux, rad), (float)tw));
+        const float fx1 = floorf(rd(ra(P.mux, rad), (float)tw));
+        const float fy0 = floorf(rd(rs(P.muy, rad), (float)th));
+        const float fy1 = floorf(rd(ra(P.muy, rad), (float)th));
+        if (fx1 < 0.f || fx0 > (float)(tiles_x - 1) || fy1 < 0.f || fy0 > (float)(tiles_y - 1)) return false;
         rect_out->x = (int)fmaxf(fx0, 0.f);
         rect_out->y = (int)fminf(fx1, (float)(tiles_x - 1));
         rect_out->z = (int)fmaxf(fy0, 0.f);
         rect_out->w = (int)fminf(fy1, (float)(tiles_y - 1));
+        *depth_out = P.t[2];
     }
-    if (depth_out) *depth_out = P.t[2];
     return true;
 }
 
-// 2D features used by the rasterizer: conic, opacity and view-dependent colour.
-__device__ __forceinline__ void prim_features(const GParams& gp, const float* sh, int deg, const CamDev& cam, Prim& P) {
+// 2D conic and view-dependent colour.
+template <int DEG>
+__device__ __forceinline__ void prim_features(const float X[3], const float* sh, const CamDev& cam, Prim& P) {
     const float inv = 1.f / P.det;
     P.A = P.c * inv;
     P.B = -P.b * inv;
     P.C = P.a * inv;
-    P.o = 1.f / (1.f + expf(-gp.th));
     float d[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) d[k] = gp.X[k] - cam.centre[k];
+    for (int k = 0; k < 3; ++k) d[k] = X[k] - cam.centre[k];
     P.dn = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
     const float idn = 1.f / P.dn;
 #pragma unroll
     for (int k = 0; k < 3; ++k) P.dir[k] = d[k] * idn;
-    float Y[kMaxShCoeffs];
-    sh_eval(deg, P.dir[0], P.dir[1], P.dir[2], Y);
-    const int K = (deg + 1) * (deg + 1);
+    constexpr int K = Sh<DEG>::K;
+    float Y[K];
+    sh_eval<DEG>(P.dir[0], P.dir[1], P.dir[2], Y);
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
         float acc = 0.5f;
+#pragma unroll
         for (int k = 0; k < K; ++k) acc += sh[3 * k + ch] * Y[k];
         P.clamped[ch] = acc < 0.f;
         P.col[ch] = P.clamped[ch] ? 0.f : acc;
     }
 }
 
-__device__ __forceinline__ void load_sh(const float* p, int G, int K, int g, float* sh) {
-    const float* src = p + 11ll * G + (long long)g * K * 3;
-    for (int i = 0; i < 3 * K; ++i) sh[i] = src[i];
-}
-
 // ---------------------------------------------------------------------------
 // Forward-mode tangent of the 9 features (mu_x, mu_y, A, B, C, o, r, g, b)
-// along (dX, dls, dq, dth, dsh); dsh may be null (no SH tangent).
+// along (dX, dls, dq, dth, dsh); kSh = false means a zero SH tangent.
 // ---------------------------------------------------------------------------
 struct GTan {
     float X[3], ls[3], q[4], th;
 };
 
+template <int DEG, bool kSh>
 __device__ __forceinline__ void prim_tangent(const Prim& P, const CamDev& cam, const GTan& d, const float* sh,
-                                             const float* dsh, int deg, float out[9]) {
+                                             const float* dsh, float out[9]) {
     const float* W = cam.R;
     float dt[3];
 #pragma unroll
@@ -335,53 +414,61 @@ __device__ __forceinline__ void prim_tangent(const Prim& P, const CamDev& cam, c
     out[3] = (-db - P.B * ddet) * idet;
     out[4] = (da - P.C * ddet) * idet;
     out[5] = P.o * (1.f - P.o) * d.th;
-    // colour: SH coefficients and the view direction (through the mean)
-    const float idn = 1.f / P.dn;
-    const float pd = P.dir[0] * d.X[0] + P.dir[1] * d.X[1] + P.dir[2] * d.X[2];
-    float ddir[3];
+    // colour: SH coefficients and the view direction (through the mean);
+    // dc_ch = sum_k dsh_k,ch Y_k + sh_k,ch (grad Y_k . ddir), coefficients
+    // streamed from memory
+    constexpr int K = Sh<DEG>::K;
+    float v3[3] = {0.f, 0.f, 0.f};
+    if (DEG > 0) {
+        const float idn = 1.f / P.dn;
+        const float pd = P.dir[0] * d.X[0] + P.dir[1] * d.X[1] + P.dir[2] * d.X[2];
+        float ddir[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) ddir[k] = (d.X[k] - P.dir[k] * pd) * idn;
-    float Y[kMaxShCoeffs];
-    if (dsh) sh_eval(deg, P.dir[0], P.dir[1], P.dir[2], Y);
-    const int K = (deg + 1) * (deg + 1);
+        for (int k = 0; k < 3; ++k) ddir[k] = (d.X[k] - P.dir[k] * pd) * idn;
+        float gY[K];
+        sh_dir_deriv<DEG>(P.dir[0], P.dir[1], P.dir[2], ddir, gY);
 #pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-        float v = 0.f;
-        if (deg > 0) {
-            float wk[kMaxShCoeffs];
-            for (int k = 0; k < K; ++k) wk[k] = sh[3 * k + ch];
-            float gr[3];
-            sh_weighted_grad(deg, P.dir[0], P.dir[1], P.dir[2], wk, gr);
-            v = gr[0] * ddir[0] + gr[1] * ddir[1] + gr[2] * ddir[2];
-        }
-        if (dsh)
-            for (int k = 0; k < K; ++k) v += dsh[3 * k + ch] * Y[k];
-        out[6 + ch] = P.clamped[ch] ? 0.f : v;
+        for (int k = 1; k < K; ++k)
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) v3[ch] += sh[3 * k + ch] * gY[k];
     }
+    if (kSh) {
+        float Y[K];
+        sh_eval<DEG>(P.dir[0], P.dir[1], P.dir[2], Y);
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) v3[ch] += dsh[3 * k + ch] * Y[k];
+    }
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) out[6 + ch] = P.clamped[ch] ? 0.f : v3[ch];
 }
 
 // ---------------------------------------------------------------------------
 // Reverse mode: cotangent of the 9 features -> cotangents of the 3D
 // parameters (accumulated into gX, gls, gq, gth, gsh).
 // ---------------------------------------------------------------------------
+template <int DEG>
 __device__ __forceinline__ void prim_adjoint(const Prim& P, const CamDev& cam, const float* cot, const float* sh,
-                                             int deg, float gX[3], float gls[3], float gq[4], float* gth, float* gsh) {
+                                             float gX[3], float gls[3], float gq[4], float* gth, float* gsh) {
     const float* W = cam.R;
     // colour -> SH coefficients and view direction
-    const int K = (deg + 1) * (deg + 1);
+    constexpr int K = Sh<DEG>::K;
     float ccol[3];
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) ccol[ch] = P.clamped[ch] ? 0.f : cot[6 + ch];
-    float Y[kMaxShCoeffs];
-    sh_eval(deg, P.dir[0], P.dir[1], P.dir[2], Y);
+    float Y[K];
+    sh_eval<DEG>(P.dir[0], P.dir[1], P.dir[2], Y);
+#pragma unroll
     for (int k = 0; k < K; ++k)
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) gsh[3 * k + ch] += ccol[ch] * Y[k];
-    if (deg > 0) {
-        float wk[kMaxShCoeffs];
+    if (DEG > 0) {
+        float wk[K];
+#pragma unroll
         for (int k = 0; k < K; ++k) wk[k] = ccol[0] * sh[3 * k] + ccol[1] * sh[3 * k + 1] + ccol[2] * sh[3 * k + 2];
         float gd[3];
-        sh_weighted_grad(deg, P.dir[0], P.dir[1], P.dir[2], wk, gd);
+        sh_weighted_grad<DEG>(P.dir[0], P.dir[1], P.dir[2], wk, gd);
         const float pd = P.dir[0] * gd[0] + P.dir[1] * gd[1] + P.dir[2] * gd[2];
         const float idn = 1.f / P.dn;
 #pragma unroll
@@ -502,16 +589,19 @@ __global__ void k_sample(Ctx c, long long lm_step, unsigned long long seed) {
     }
 }
 
+template <int DEG>
 __global__ void k_prep_fwd(Ctx c) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (long long)c.nv * c.G) return;
     const int slot = (int)(i / c.G), g = (int)(i % c.G);
     const CamDev& cam = c.cams[c.views[slot]];
-    const GParams gp = load_gparams(c.params, c.G, g);
+    float X[3];
+    load_mean(c.params, g, X);
     Prim P;
+    load_gauss(c, g, P);
     int4 rect;
     float depth;
-    const bool vis = prim_geometry(gp, cam, c.tiles_x, c.tiles_y, c.tile_w, c.tile_h, P, &rect, &depth);
+    const bool vis = prim_project(X, cam, c.tiles_x, c.tiles_y, c.tile_w, c.tile_h, P, &rect, &depth);
     const unsigned ballot = __ballot_sync(__activemask(), vis);
     if ((threadIdx.x & 31) == __ffs(__activemask()) - 1 && ballot)
         atomicAdd(c.n_visible, (unsigned long long)__popc(ballot));
@@ -520,9 +610,8 @@ __global__ void k_prep_fwd(Ctx c) {
         c.cnt[i] = 0ull;
         return;
     }
-    float sh[3 * kMaxShCoeffs];
-    load_sh(c.params, c.G, c.K, g, sh);
-    prim_features(gp, sh, c.deg, cam, P);
+    const float* sh = c.params + 11ll * c.G + (long long)g * 3 * Sh<DEG>::K;
+    prim_features<DEG>(X, sh, cam, P);
     float4* r = c.rec + i * kRecF4;
     r[0] = make_float4(P.mux, P.muy, P.A, P.B);
     r[1] = make_float4(P.C, P.o, P.col[0], P.col[1]);
@@ -532,93 +621,86 @@ __global__ void k_prep_fwd(Ctx c) {
     c.cnt[i] = (unsigned long long)(rect.y - rect.x + 1) * (unsigned long long)(rect.w - rect.z + 1);
 }
 
-__device__ __forceinline__ void load_tangent(const float* v, int G, int K, int g, GTan& d, float* dsh) {
-    const GParams t = load_gparams(v, G, g);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        d.X[k] = t.X[k];
-        d.ls[k] = t.ls[k];
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) d.q[k] = t.q[k];
-    d.th = t.th;
-    load_sh(v, G, K, g, dsh);
+// Primal state of a visible pair for the derivative kernels.
+template <int DEG>
+__device__ __forceinline__ void pair_primal(const Ctx& c, const CamDev& cam, const float X[3], const float* sh,
+                                            Prim& P) {
+    prim_project(X, cam, c.tiles_x, c.tiles_y, c.tile_w, c.tile_h, P, nullptr, nullptr);
+    prim_features<DEG>(X, sh, cam, P);
 }
 
-// Writes p = z + beta p for Gaussian g's entries (beta from the device
-// scalars) and returns the new entries in d/dsh.
-__device__ __forceinline__ void update_p(const Ctx& c, float* p, const float* z, int g, GTan& d, float* dsh) {
-    const float beta = (float)c.sc->beta;
-    const long long G = c.G;
-    auto upd = [&](long long idx) {
-        const float v = z[idx] + beta * p[idx];
-        p[idx] = v;
-        return v;
-    };
+// tangent of the 11 geometric parameters of Gaussian g
+__device__ __forceinline__ void load_geo_tangent(const float* v, int G, int g, GTan& d) {
+    const long long GG = G;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        d.X[k] = upd(3 * g + k);
-        d.ls[k] = upd(3 * G + 3 * g + k);
+        d.X[k] = v[3ll * g + k];
+        d.ls[k] = v[3 * GG + 3ll * g + k];
     }
 #pragma unroll
-    for (int k = 0; k < 4; ++k) d.q[k] = upd(6 * G + 4 * g + k);
-    d.th = upd(10 * G + g);
-    for (int k = 0; k < 3 * c.K; ++k) dsh[k] = upd(11 * G + (long long)g * c.K * 3 + k);
+    for (int k = 0; k < 4; ++k) d.q[k] = v[6 * GG + 4ll * g + k];
+    d.th = v[10 * GG + g];
 }
 
-__global__ void k_prep_jvp(Ctx c, const float* v, float* p, const float* z) {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= c.G) return;
+// One thread per (Gaussian, view) pair, Gaussian-major (consecutive threads
+// are the views of one Gaussian, so its parameters and tangent are loaded
+// once per warp through L1).  Writes the tangent half of the pair record and
+// clears the pair's cotangent slot.
+template <int DEG>
+__global__ void k_prep_jvp(Ctx c, const float* v) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)c.nv * c.G) return;
+    const int g = (int)(i / c.nv), slot = (int)(i - (long long)g * c.nv);
+    const long long pair = (long long)slot * c.G + g;
+    const int4 rc = c.rect[pair];
+    if (rc.x > rc.y) return;
+    constexpr int K3 = 3 * Sh<DEG>::K;
     GTan d;
-    float dsh[3 * kMaxShCoeffs];
-    if (p) update_p(c, p, z, g, d, dsh);
-    else load_tangent(v, c.G, c.K, g, d, dsh);
-    const GParams gp = load_gparams(c.params, c.G, g);
-    float sh[3 * kMaxShCoeffs];
-    load_sh(c.params, c.G, c.K, g, sh);
-    for (int slot = 0; slot < c.nv; ++slot) {
-        const long long i = (long long)slot * c.G + g;
-        const int4 rc = c.rect[i];
-        if (rc.x > rc.y) continue;
-        const CamDev& cam = c.cams[c.views[slot]];
-        Prim P;
-        prim_geometry(gp, cam, c.tiles_x, c.tiles_y, c.tile_w, c.tile_h, P, nullptr, nullptr);
-        prim_features(gp, sh, c.deg, cam, P);
-        float o[9];
-        prim_tangent(P, cam, d, sh, dsh, c.deg, o);
-        float4* r = c.rec + i * kRecF4;
-        r[3] = make_float4(o[0], o[1], o[2], o[3]);
-        r[4] = make_float4(o[4], o[5], o[6], o[7]);
-        r[5] = make_float4(o[8], 0.f, 0.f, 0.f);
-        float4* ct = reinterpret_cast<float4*>(c.cot + i * kCotF);
-        ct[0] = ct[1] = ct[2] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
+    load_geo_tangent(v, c.G, g, d);
+    const float* dsh = v + 11ll * c.G + (long long)g * K3;
+    const float* sh = c.params + 11ll * c.G + (long long)g * K3;
+    float X[3];
+    load_mean(c.params, g, X);
+    Prim P;
+    load_gauss(c, g, P);
+    const CamDev& cam = c.cams[c.views[slot]];
+    pair_primal<DEG>(c, cam, X, sh, P);
+    float o[9];
+    prim_tangent<DEG, true>(P, cam, d, sh, dsh, o);
+    float4* r = c.rec + pair * kRecF4;
+    r[3] = make_float4(o[0], o[1], o[2], o[3]);
+    r[4] = make_float4(o[4], o[5], o[6], o[7]);
+    r[5] = make_float4(o[8], 0.f, 0.f, 0.f);
+    float4* ct = reinterpret_cast<float4*>(c.cot + pair * kCotF);
+    ct[0] = ct[1] = ct[2] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 constexpr int kPrepBlock = 128;
 
-template <bool kDot>
+template <int DEG, bool kDot>
 __global__ void __launch_bounds__(kPrepBlock) k_prep_vjp(Ctx c, float* out, const float* v, const float* D) {
+    constexpr int K3 = 3 * Sh<DEG>::K;
     double dot = 0.0;
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < c.G; g += gridDim.x * blockDim.x) {
-        const GParams gp = load_gparams(c.params, c.G, g);
-        float sh[3 * kMaxShCoeffs];
-        load_sh(c.params, c.G, c.K, g, sh);
+        float X[3], sh[K3];  // held in registers across the view loop
+        load_mean(c.params, g, X);
+        load_sh<DEG>(c.params, c.G, g, sh);
+        Prim P;
+        load_gauss(c, g, P);
         float gX[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, gth = 0.f;
-        float gsh[3 * kMaxShCoeffs];
-        for (int k = 0; k < 3 * c.K; ++k) gsh[k] = 0.f;
+        float gsh[K3];
+#pragma unroll
+        for (int k = 0; k < K3; ++k) gsh[k] = 0.f;
         for (int slot = 0; slot < c.nv; ++slot) {
             const long long i = (long long)slot * c.G + g;
             const int4 rc = c.rect[i];
             if (rc.x > rc.y) continue;
             const CamDev& cam = c.cams[c.views[slot]];
-            Prim P;
-            prim_geometry(gp, cam, c.tiles_x, c.tiles_y, c.tile_w, c.tile_h, P, nullptr, nullptr);
-            prim_features(gp, sh, c.deg, cam, P);
+            pair_primal<DEG>(c, cam, X, sh, P);
             const float4* ct = reinterpret_cast<const float4*>(c.cot + i * kCotF);
             const float4 c0 = ct[0], c1 = ct[1], c2 = ct[2];
             const float cot[9] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, c2.x};
-            prim_adjoint(P, cam, cot, sh, c.deg, gX, gls, gq, &gth, gsh);
+            prim_adjoint<DEG>(P, cam, cot, sh, gX, gls, gq, &gth, gsh);
         }
         const long long G = c.G;
         auto put = [&](long long idx, float val) {
@@ -630,20 +712,23 @@ __global__ void __launch_bounds__(kPrepBlock) k_prep_vjp(Ctx c, float* out, cons
             out[idx] = val;
         };
 #pragma unroll
-        for (int k = 0; k < 3; ++k) put(3 * g + k, gX[k]);
+        for (int k = 0; k < 3; ++k) put(3ll * g + k, gX[k]);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) put(3 * G + 3 * g + k, gls[k]);
+        for (int k = 0; k < 3; ++k) put(3 * G + 3ll * g + k, gls[k]);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) put(6 * G + 4 * g + k, gq[k]);
+        for (int k = 0; k < 4; ++k) put(6 * G + 4ll * g + k, gq[k]);
         put(10 * G + g, gth);
-        for (int k = 0; k < 3 * c.K; ++k) put(11 * G + (long long)g * c.K * 3 + k, gsh[k]);
+#pragma unroll
+        for (int k = 0; k < K3; ++k) put(11 * G + (long long)g * K3 + k, gsh[k]);
     }
     if (kDot) {
         double tot;
         if (grid_sum_last<kPrepBlock>(dot, c.partials, c.counter, &tot) && threadIdx.x == 0) {
             Scalars* s = c.sc;
             s->pAp = tot;
-            if (!(tot > 0.0) || !isfinite(tot)) {
+            if (s->rz == 0.0) {
+                s->alpha = 0.0;
+            } else if (!(tot > 0.0) || !isfinite(tot)) {
                 s->numeric_error = 1u;
                 s->alpha = 0.0;
             } else {
@@ -675,25 +760,29 @@ __device__ __forceinline__ float gram_quad(const float* gm, const float a[9]) {
     return v;
 }
 
+template <int DEG>
 __global__ void __launch_bounds__(kPrepBlock) k_prep_diag(Ctx c, float* D) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= c.G) return;
-    const GParams gp = load_gparams(c.params, c.G, g);
-    float sh[3 * kMaxShCoeffs];
-    load_sh(c.params, c.G, c.K, g, sh);
+    constexpr int K = Sh<DEG>::K;
+    constexpr int K3 = 3 * K;
+    float X[3];
+    load_mean(c.params, g, X);
+    const float* sh = c.params + 11ll * c.G + (long long)g * K3;
+    Prim P;
+    load_gauss(c, g, P);
     float dgeo[11];
 #pragma unroll
     for (int j = 0; j < 11; ++j) dgeo[j] = 0.f;
-    float dsh[3 * kMaxShCoeffs];
-    for (int k = 0; k < 3 * c.K; ++k) dsh[k] = 0.f;
+    float dsh[K3];
+#pragma unroll
+    for (int k = 0; k < K3; ++k) dsh[k] = 0.f;
     for (int slot = 0; slot < c.nv; ++slot) {
         const long long i = (long long)slot * c.G + g;
         const int4 rc = c.rect[i];
         if (rc.x > rc.y) continue;
         const CamDev& cam = c.cams[c.views[slot]];
-        Prim P;
-        prim_geometry(gp, cam, c.tiles_x, c.tiles_y, c.tile_w, c.tile_h, P, nullptr, nullptr);
-        prim_features(gp, sh, c.deg, cam, P);
+        pair_primal<DEG>(c, cam, X, sh, P);
         float gm[kGramF];
         const float4* gsrc = reinterpret_cast<const float4*>(c.gram + i * kGramF);
 #pragma unroll
@@ -711,57 +800,101 @@ __global__ void __launch_bounds__(kPrepBlock) k_prep_diag(Ctx c, float* D) {
             for (int k = 0; k < 4; ++k) d.q[k] = j == 6 + k ? 1.f : 0.f;
             d.th = j == 10 ? 1.f : 0.f;
             float a[9];
-            prim_tangent(P, cam, d, sh, nullptr, c.deg, a);
+            prim_tangent<DEG, false>(P, cam, d, sh, nullptr, a);
             dgeo[j] += gram_quad(gm, a);
         }
         // SH coefficient (k, ch) moves only colour ch, by Y_k
-        float Y[kMaxShCoeffs];
-        sh_eval(c.deg, P.dir[0], P.dir[1], P.dir[2], Y);
-        for (int k = 0; k < c.K; ++k)
+        float Y[K];
+        sh_eval<DEG>(P.dir[0], P.dir[1], P.dir[2], Y);
+#pragma unroll
+        for (int k = 0; k < K; ++k)
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch)
                 if (!P.clamped[ch]) dsh[3 * k + ch] += gm[39] * Y[k] * Y[k];
     }
     const long long G = c.G;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) D[3 * g + k] = dgeo[k];
+    for (int k = 0; k < 3; ++k) D[3ll * g + k] = dgeo[k];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) D[3 * G + 3 * g + k] = dgeo[3 + k];
+    for (int k = 0; k < 3; ++k) D[3 * G + 3ll * g + k] = dgeo[3 + k];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) D[6 * G + 4 * g + k] = dgeo[6 + k];
+    for (int k = 0; k < 4; ++k) D[6 * G + 4ll * g + k] = dgeo[6 + k];
     D[10 * G + g] = dgeo[10];
-    for (int k = 0; k < 3 * c.K; ++k) D[11 * G + (long long)g * c.K * 3 + k] = dsh[k];
+#pragma unroll
+    for (int k = 0; k < K3; ++k) D[11 * G + (long long)g * K3 + k] = dsh[k];
 }
 
 // ---------------------------------------------------------------------------
-// Launchers
+// Launchers (dispatch on the SH degree)
 // ---------------------------------------------------------------------------
 void launch_sample(const Ctx& c, long long lm_step, unsigned long long seed, cudaStream_t st) {
     const int n = c.nv * c.T;
     LMRS_LAUNCH(k_sample, (n + 127) / 128, 128, 0, st, c, lm_step, seed);
 }
 
-void launch_prep_fwd(const Ctx& c, cudaStream_t st) {
+void launch_prep_gauss(const Ctx& c, cudaStream_t st) {
+    LMRS_LAUNCH(k_prep_gauss, (c.G + 255) / 256, 256, 0, st, c);
+}
+
+template <int DEG>
+static void prep_fwd_deg(const Ctx& c, cudaStream_t st) {
     const long long n = (long long)c.nv * c.G;
-    LMRS_LAUNCH(k_prep_fwd, (unsigned)((n + 127) / 128), 128, 0, st, c);
+    LMRS_LAUNCH_AS("k_prep_fwd", k_prep_fwd<DEG>, (unsigned)((n + 127) / 128), 128, 0, st, c);
 }
-
-void launch_prep_jvp(const Ctx& c, const float* v, float* p_update, const float* z, cudaStream_t st) {
-    LMRS_LAUNCH(k_prep_jvp, (c.G + 127) / 128, 128, 0, st, c, v, p_update, z);
+template <int DEG>
+static void prep_jvp_deg(const Ctx& c, const float* v, cudaStream_t st) {
+    const long long n = (long long)c.nv * c.G;
+    LMRS_LAUNCH_AS("k_prep_jvp", k_prep_jvp<DEG>, (unsigned)((n + 127) / 128), 128, 0, st, c, v);
 }
-
-void launch_prep_vjp(const Ctx& c, float* g, const float* v, const float* D, bool dot, cudaStream_t st) {
+template <int DEG>
+static void prep_vjp_deg(const Ctx& c, float* g, const float* v, const float* D, bool dot, cudaStream_t st) {
     int grid = (c.G + kPrepBlock - 1) / kPrepBlock;
     if (dot) {
         if (grid > kMaxPartials) grid = kMaxPartials;
-        LMRS_LAUNCH(k_prep_vjp<true>, grid, kPrepBlock, 0, st, c, g, v, D);
+        LMRS_LAUNCH_AS("k_prep_vjp<dot>", (k_prep_vjp<DEG, true>), grid, kPrepBlock, 0, st, c, g, v, D);
     } else {
-        LMRS_LAUNCH(k_prep_vjp<false>, grid, kPrepBlock, 0, st, c, g, v, D);
+        LMRS_LAUNCH_AS("k_prep_vjp", (k_prep_vjp<DEG, false>), grid, kPrepBlock, 0, st, c, g, v, D);
+    }
+}
+template <int DEG>
+static void prep_diag_deg(const Ctx& c, float* D, cudaStream_t st) {
+    LMRS_LAUNCH_AS("k_prep_diag", k_prep_diag<DEG>, (c.G + kPrepBlock - 1) / kPrepBlock, kPrepBlock, 0, st, c, D);
+}
+
+void launch_prep_fwd(const Ctx& c, cudaStream_t st) {
+    switch (c.deg) {
+        case 0: prep_fwd_deg<0>(c, st); break;
+        case 1: prep_fwd_deg<1>(c, st); break;
+        case 2: prep_fwd_deg<2>(c, st); break;
+        default: prep_fwd_deg<3>(c, st); break;
+    }
+}
+
+void launch_prep_jvp(const Ctx& c, const float* v, cudaStream_t st) {
+    switch (c.deg) {
+        case 0: prep_jvp_deg<0>(c, v, st); break;
+        case 1: prep_jvp_deg<1>(c, v, st); break;
+        case 2: prep_jvp_deg<2>(c, v, st); break;
+        default: prep_jvp_deg<3>(c, v, st); break;
+    }
+}
+
+void launch_prep_vjp(const Ctx& c, float* g, const float* v, const float* D, bool dot, cudaStream_t st) {
+    switch (c.deg) {
+        case 0: prep_vjp_deg<0>(c, g, v, D, dot, st); break;
+        case 1: prep_vjp_deg<1>(c, g, v, D, dot, st); break;
+        case 2: prep_vjp_deg<2>(c, g, v, D, dot, st); break;
+        default: prep_vjp_deg<3>(c, g, v, D, dot, st); break;
     }
 }
 
 void launch_prep_diag(const Ctx& c, float* D, cudaStream_t st) {
-    LMRS_LAUNCH(k_prep_diag, (c.G + kPrepBlock - 1) / kPrepBlock, kPrepBlock, 0, st, c, D);
+    switch (c.deg) {
+        case 0: prep_diag_deg<0>(c, D, st); break;
+        case 1: prep_diag_deg<1>(c, D, st); break;
+        case 2: prep_diag_deg<2>(c, D, st); break;
+        default: prep_diag_deg<3>(c, D, st); break;
+    }
 }
 
 }  // namespace lmrs

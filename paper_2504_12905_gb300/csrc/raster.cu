@@ -239,6 +239,11 @@ __global__ void __launch_bounds__(kRasterBlock) k_fwd_samples(Ctx c) {
         num = (double)p.w * ((double)r[0] * r[0] + (double)r[1] * r[1] + (double)r[2] * r[2]);
         den = 3.0 * p.w;
     }
+    // traversal length of this work item (the longest-lived lane)
+    int len = p.active ? ncons : 0;
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) len = max(len, __shfl_xor_sync(kFull, len, m));
+    if ((threadIdx.x & 31) == 0 && c.item_cost) c.item_cost[item] = len;
     num = warp_sum(num);
     den = warp_sum(den);
     if ((threadIdx.x & 31) == 0) {
@@ -400,6 +405,27 @@ __global__ void __launch_bounds__(256) k_full(Ctx c, float* images) {
 }
 
 static unsigned raster_grid(const Ctx& c) { return (unsigned)((c.nwork + kRasterWarps - 1) / kRasterWarps); }
+
+__global__ void k_order_keys(const int* cost, int n, unsigned long long* keys, unsigned int* vals) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    keys[k] = 0xFFFFFFFFull - (unsigned long long)(unsigned int)cost[k];  // ascending key = descending cost
+    vals[k] = (unsigned int)k;
+}
+
+__global__ void k_gather_work(const int2* work, const unsigned int* order, int n, int2* sorted) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) sorted[k] = work[order[k]];
+}
+
+void launch_order_work(const Ctx& c, unsigned long long* keys, unsigned int* vals, unsigned long long* keys_alt,
+                       unsigned int* vals_alt, void* tmp, size_t tmp_bytes, int2* sorted, cudaStream_t st) {
+    if (c.nwork <= 0) return;
+    const unsigned grid = (unsigned)((c.nwork + 255) / 256);
+    LMRS_LAUNCH(k_order_keys, grid, 256, 0, st, c.item_cost, c.nwork, keys, vals);
+    radix_sort(keys, vals, keys_alt, vals_alt, c.nwork, 32, tmp, tmp_bytes, st);
+    LMRS_LAUNCH(k_gather_work, grid, 256, 0, st, c.work, vals, c.nwork, sorted);
+}
 
 void launch_raster_fwd_samples(const Ctx& c, cudaStream_t st) {
     if (c.nwork > 0) LMRS_LAUNCH(k_fwd_samples, raster_grid(c), kRasterBlock, 0, st, c);

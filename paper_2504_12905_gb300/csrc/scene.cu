@@ -72,10 +72,11 @@ struct lmrs_scene {
     std::string err;
     const float* targets = nullptr;
     // device state
-    DevBuf params, cams, views;
+    DevBuf params, cams, views, gcache;
     DevBuf rec, rect, depth, cnt, cot, gram;
     DevBuf keys, ids, keys_alt, ids_alt, ranges, scan_tmp, radix_tmp, total;
     DevBuf tile_off, off, wtile, work;
+    DevBuf item_cost, work_sorted, okeys, ovals, okeys_alt, ovals_alt, otmp;
     DevBuf resid, cacheC, cacheT, cacheCh, cacheTh, cacheN;
     DevBuf x, r, z, p, Ap, minv, D, b, stage_a, stage_b;
     DevBuf sc, partials, counter;
@@ -87,6 +88,7 @@ struct lmrs_scene {
     int layout_nv = -1;
     std::vector<int> tile_off_h;
     bool preprocessed = false, rendered = false, have_D = false;
+    bool ordered = false;  // work items in longest-first order (after a render)
     bool timing = false;
     LaunchTimer timer;
 
@@ -103,6 +105,7 @@ struct lmrs_scene {
         c.cams = cams.as<CamDev>();
         c.views = views.as<int>();
         c.targets = targets;
+        c.gcache = gcache.as<float4>();
         c.rec = rec.as<float4>();
         c.rect = rect.as<int4>();
         c.depth = depth.as<unsigned int>();
@@ -118,7 +121,8 @@ struct lmrs_scene {
         c.off = off.as<unsigned char>();
         c.wtile = wtile.as<float>();
         c.S = S;
-        c.work = work.as<int2>();
+        c.work = ordered ? work_sorted.as<int2>() : work.as<int2>();
+        c.item_cost = item_cost.as<int>();
         c.nwork = nwork;
         c.resid = resid.as<float>();
         c.cacheC = cacheC.as<float>();
@@ -264,6 +268,14 @@ lmrs_status build_layout(lmrs_scene* s) {
     TRY(ensure(s, s->cacheCh, sizeof(__nv_bfloat16) * 3 * s->S));
     TRY(ensure(s, s->cacheTh, sizeof(__nv_bfloat16) * s->S));
     TRY(ensure(s, s->cacheN, sizeof(int) * s->S));
+    const size_t nw = std::max<size_t>(work.size(), 1);
+    TRY(ensure(s, s->item_cost, sizeof(int) * nw));
+    TRY(ensure(s, s->work_sorted, sizeof(int2) * nw));
+    TRY(ensure(s, s->okeys, sizeof(unsigned long long) * nw));
+    TRY(ensure(s, s->okeys_alt, sizeof(unsigned long long) * nw));
+    TRY(ensure(s, s->ovals, sizeof(unsigned int) * nw));
+    TRY(ensure(s, s->ovals_alt, sizeof(unsigned int) * nw));
+    TRY(ensure(s, s->otmp, radix_tmp_bytes((long long)nw)));
     // pageable sources: the copies are staged before the calls return
     CK(s, cudaMemcpyAsync(s->tile_off.p, toff.data(), sizeof(int) * (nT + 1), cudaMemcpyHostToDevice, s->st));
     CK(s, cudaMemcpyAsync(s->wtile.p, w.data(), sizeof(float) * nT, cudaMemcpyHostToDevice, s->st));
@@ -302,7 +314,7 @@ lmrs_status do_jtj_diag(lmrs_scene* s) {
 // (J^T W J + lambda damp) v -> out, device pointers.
 lmrs_status do_jtjv(lmrs_scene* s, const float* v, float* out) {
     Ctx c = s->ctx();
-    launch_prep_jvp(c, v, nullptr, nullptr, s->st);
+    launch_prep_jvp(c, v, s->st);
     launch_raster_jtj(c, s->st);
     launch_prep_vjp(c, out, v, s->D.as<float>(), false, s->st);
     CHECK_LAUNCH(s);
@@ -321,7 +333,8 @@ lmrs_status do_cg(lmrs_scene* s, const float* b, float* x, int iters) {
     launch_precond(c, D, minv, s->st);
     launch_cg_init(c, b, minv, x, r, z, p, s->st);
     for (int it = 0; it < iters; ++it) {
-        launch_prep_jvp(c, nullptr, p, z, s->st);        // p = z + beta p; tangents of p
+        launch_cg_direction(c, z, p, s->st);             // p = z + beta p
+        launch_prep_jvp(c, p, s->st);                    // tangent features of p
         launch_raster_jtj(c, s->st);                     // J^T W J p into the cotangent slots
         launch_prep_vjp(c, Ap, p, D, true, s->st);       // Ap (+ damping), p^T A p, alpha
         launch_cg_update(c, it, p, Ap, minv, x, r, z, s->st);  // x, r, z, beta
@@ -401,6 +414,7 @@ lmrs_status lmrs_scene_create(const lmrs_config* cfg, int64_t n_gauss, const flo
     take(s->params, pv);
     for (DevBuf* b : {&s->x, &s->r, &s->z, &s->p, &s->Ap, &s->minv, &s->D, &s->b}) take(*b, pv);
     take(s->cams, sizeof(CamDev) * n_cams);
+    take(s->gcache, sizeof(float4) * kGaussF4 * (size_t)s->G);
     take(s->sc, sizeof(Scalars));
     take(s->partials, sizeof(double) * kMaxPartials);
     take(s->counter, sizeof(unsigned int) * 4);
@@ -428,9 +442,10 @@ lmrs_status lmrs_scene_create(const lmrs_config* cfg, int64_t n_gauss, const flo
 lmrs_status lmrs_scene_destroy(lmrs_scene* s) {
     if (!s) return LMRS_ERR_INVALID_ARG;
     if (s->st) cudaStreamSynchronize(s->st);
-    for (DevBuf* b : {&s->params, &s->cams, &s->views, &s->rec, &s->rect, &s->depth, &s->cnt, &s->cot, &s->gram,
+    for (DevBuf* b : {&s->params, &s->cams, &s->views, &s->gcache, &s->rec, &s->rect, &s->depth, &s->cnt, &s->cot, &s->gram,
                       &s->keys, &s->ids, &s->keys_alt, &s->ids_alt, &s->ranges, &s->scan_tmp, &s->radix_tmp,
-                      &s->total, &s->tile_off, &s->off, &s->wtile, &s->work, &s->resid, &s->cacheC, &s->cacheT,
+                      &s->total, &s->tile_off, &s->off, &s->wtile, &s->work, &s->item_cost,
+                      &s->work_sorted, &s->okeys, &s->ovals, &s->okeys_alt, &s->ovals_alt, &s->otmp, &s->resid, &s->cacheC, &s->cacheT,
                       &s->cacheCh, &s->cacheTh, &s->cacheN, &s->x, &s->r, &s->z, &s->p, &s->Ap, &s->minv, &s->D,
                       &s->b, &s->stage_a, &s->stage_b, &s->sc, &s->partials, &s->counter})
         release(*b);
@@ -442,7 +457,7 @@ lmrs_status lmrs_set_params(lmrs_scene* s, const float* src) {
     TRY(check_scene(s));
     if (!src) return fail(s, LMRS_ERR_INVALID_ARG, "null source");
     CK(s, cudaMemcpyAsync(s->params.p, src, sizeof(float) * s->P, cudaMemcpyDefault, s->st));
-    s->preprocessed = s->rendered = s->have_D = false;
+    s->preprocessed = s->rendered = s->have_D = s->ordered = false;
     return LMRS_OK;
 }
 
@@ -470,7 +485,7 @@ lmrs_status lmrs_preprocess(lmrs_scene* s, const int32_t* view_ids, int32_t n_vi
         if (view_ids[i] < 0 || view_ids[i] >= s->n_cams) return fail(s, LMRS_ERR_INVALID_ARG, "view id out of range");
     if ((long long)n_views * s->T >= (1ll << 31) || (long long)n_views * s->G >= (1ll << 31))
         return fail(s, LMRS_ERR_BUDGET, "too many (view, tile) or (view, Gaussian) pairs");
-    s->preprocessed = s->rendered = s->have_D = false;
+    s->preprocessed = s->rendered = s->have_D = s->ordered = false;
     s->views_h.assign(view_ids, view_ids + n_views);
     s->nv = n_views;
     s->step = lm_step;
@@ -488,6 +503,7 @@ lmrs_status lmrs_preprocess(lmrs_scene* s, const int32_t* view_ids, int32_t n_vi
     Ctx c = s->ctx();
     CK(s, cudaMemsetAsync(s->total.p, 0, 2 * sizeof(unsigned long long), s->st));
     launch_sample(c, lm_step, s->cfg.seed, s->st);
+    launch_prep_gauss(c, s->st);
     launch_prep_fwd(c, s->st);
     scan_u64(c.cnt, (long long)pairs, s->total.as<unsigned long long>(), s->scan_tmp.p, s->scan_tmp.cap, s->st);
     CHECK_LAUNCH(s);
@@ -521,11 +537,16 @@ lmrs_status lmrs_render(lmrs_scene* s, float* images_dev, float* residuals_dev) 
     TRY(check_scene(s));
     TimerScope ts_(s);
     TRY(need_pre(s));
+    s->ordered = false;  // the forward render indexes the work items in their natural order
     Ctx c = s->ctx();
     CK(s, cudaMemsetAsync(&c.sc->loss_num, 0, 2 * sizeof(double), s->st));
     launch_raster_fwd_samples(c, s->st);
     if (images_dev) launch_raster_full(c, images_dev, s->st);
+    launch_order_work(c, s->okeys.as<unsigned long long>(), s->ovals.as<unsigned int>(),
+                      s->okeys_alt.as<unsigned long long>(), s->ovals_alt.as<unsigned int>(), s->otmp.p, s->otmp.cap,
+                      s->work_sorted.as<int2>(), s->st);
     CHECK_LAUNCH(s);
+    s->ordered = true;
     if (residuals_dev)
         CK(s, cudaMemcpyAsync(residuals_dev, s->resid.p, sizeof(float) * 3 * s->S, cudaMemcpyDeviceToDevice, s->st));
     s->rendered = true;
@@ -538,7 +559,7 @@ lmrs_status lmrs_jvp(lmrs_scene* s, const float* v, float* u) {
     if (!v || !u) return fail(s, LMRS_ERR_INVALID_ARG, "null vector");
     TRY(need_pre(s));
     Ctx c = s->ctx();
-    launch_prep_jvp(c, v, nullptr, nullptr, s->st);
+    launch_prep_jvp(c, v, s->st);
     launch_raster_jvp(c, u, s->st);
     CHECK_LAUNCH(s);
     return LMRS_OK;
@@ -664,7 +685,7 @@ lmrs_status lmrs_lm_step(lmrs_scene* s, const int32_t* view_ids, int32_t n_views
                      s->x.as<float>(), s->params.as<float>(), s->st);
     CHECK_LAUNCH(s);
     // the parameters changed: the per-step state no longer describes them
-    s->preprocessed = s->rendered = s->have_D = false;
+    s->preprocessed = s->rendered = s->have_D = s->ordered = false;
     if (st) {
         Scalars h;
         TRY(read_scalars(s, &h));
