@@ -1,13 +1,20 @@
-// Tile binning: emission of (view-tile, depth) keys, a hand-written stable
-// LSD radix sort, and per-tile ranges.  The sort order is (view slot, tile,
-// FP32 depth bits, Gaussian index): keys are emitted in Gaussian-index order
-// and every radix pass is stable, so equal depths keep the lower index first.
+// Tile binning with a hand-written stable LSD radix sort.
+//
+// Two levels, so the long (view, tile, Gaussian) list is sorted on the tile
+// bits only:
+//   1. the (view, Gaussian) pairs are sorted by (view, FP32 depth bits); they
+//      are emitted in Gaussian-index order and every pass is stable, so equal
+//      depths keep the lower index first;
+//   2. each visible pair, in that order, emits one entry per overlapped tile;
+//   3. the entries are stable-sorted by (view, tile).
+// The result is ordered by (view, tile, depth, Gaussian index), the list
+// order of the rendering equation (Sec. 3: Gaussians sorted by depth).
 #include "common.cuh"
 
 namespace lmrs {
 
 // ---------------------------------------------------------------------------
-// Exclusive prefix sum (two-level recursive, 2048 elements per block).
+// Exclusive prefix sum (recursive, 2048 elements per block).
 // ---------------------------------------------------------------------------
 constexpr int kScanBlock = 256;
 constexpr int kScanItems = 8;
@@ -95,43 +102,20 @@ void scan_u64(unsigned long long* data, long long n, unsigned long long* total_d
 }
 
 // ---------------------------------------------------------------------------
-// Key emission: one thread per (slot, Gaussian), keys in index order.
-// ---------------------------------------------------------------------------
-__global__ void k_emit(Ctx c) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long long)c.nv * c.G) return;
-    const int4 rc = c.rect[i];
-    if (rc.x > rc.y) return;
-    const int slot = (int)(i / c.G), g = (int)(i % c.G);
-    unsigned long long o = c.cnt[i];
-    const unsigned long long dbits = c.depth[i];
-    for (int ty = rc.z; ty <= rc.w; ++ty)
-        for (int tx = rc.x; tx <= rc.y; ++tx) {
-            const unsigned long long vt = (unsigned long long)slot * c.T + (unsigned long long)(ty * c.tiles_x + tx);
-            c.keys[o] = (vt << 32) | dbits;
-            c.ids[o] = (unsigned int)g;
-            ++o;
-        }
-}
-
-void launch_emit(const Ctx& c, cudaStream_t st) {
-    const long long n = (long long)c.nv * c.G;
-    LMRS_LAUNCH(k_emit, (unsigned)((n + 127) / 128), 128, 0, st, c);
-}
-
-// ---------------------------------------------------------------------------
-// Stable LSD radix sort, 8-bit digits.  Per pass: a per-block digit
-// histogram (digit-major, so one exclusive scan gives every block's output
-// base per digit), then a stable scatter that ranks equal digits in element
-// order with warp match masks and per-warp counters.
+// Stable LSD radix sort, 8-bit digits, 32- or 64-bit keys and 32-bit values.
+// Per pass: a per-block digit histogram (digit-major, so one exclusive scan
+// gives every block's output base per digit), then a stable scatter that
+// ranks equal digits in element order with warp match masks and per-warp
+// counters.
 // ---------------------------------------------------------------------------
 constexpr int kRadixBlock = 256;
 constexpr int kRadixItems = 8;
 constexpr int kRadixTile = kRadixBlock * kRadixItems;
 constexpr int kRadixWarps = kRadixBlock / kWarp;
 
-__global__ void __launch_bounds__(kRadixBlock) k_radix_hist(const unsigned long long* keys, long long n, int shift,
-                                                           unsigned int* hist, int nblocks) {
+template <typename K>
+__global__ void __launch_bounds__(kRadixBlock) k_radix_hist(const K* keys, long long n, int shift, unsigned int* hist,
+                                                           int nblocks) {
     __shared__ unsigned int s[256];
     s[threadIdx.x] = 0u;
     __syncthreads();
@@ -145,9 +129,10 @@ __global__ void __launch_bounds__(kRadixBlock) k_radix_hist(const unsigned long 
     hist[(long long)threadIdx.x * nblocks + blockIdx.x] = s[threadIdx.x];
 }
 
-__global__ void __launch_bounds__(kRadixBlock) k_radix_scatter(const unsigned long long* kin, const unsigned int* vin,
-                                                              unsigned long long* kout, unsigned int* vout, long long n,
-                                                              int shift, const unsigned int* hist, int nblocks) {
+template <typename K>
+__global__ void __launch_bounds__(kRadixBlock) k_radix_scatter(const K* kin, const unsigned int* vin, K* kout,
+                                                              unsigned int* vout, long long n, int shift,
+                                                              const unsigned int* hist, int nblocks) {
     __shared__ unsigned int s_base[256];
     __shared__ unsigned int s_wc[kRadixWarps][256];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -160,7 +145,7 @@ __global__ void __launch_bounds__(kRadixBlock) k_radix_scatter(const unsigned lo
     for (int r = 0; r < kRadixItems; ++r) {
         const long long idx = base + r * kRadixBlock + tid;
         const bool valid = idx < n;
-        unsigned long long key = 0ull;
+        K key = 0;
         unsigned int val = 0u;
         if (valid) {
             key = kin[idx];
@@ -196,27 +181,80 @@ size_t radix_tmp_bytes(long long n) {
     return (size_t)hist * sizeof(unsigned int) + scan_tmp_elems<unsigned int>(hist) * sizeof(unsigned int);
 }
 
-void radix_sort(unsigned long long* keys, unsigned int* vals, unsigned long long* keys_alt, unsigned int* vals_alt,
-                long long n, int bits, void* tmp, size_t, cudaStream_t st) {
+template <typename K>
+static void radix_sort_impl(K* keys, unsigned int* vals, K* keys_alt, unsigned int* vals_alt, long long n, int bits,
+                            void* tmp, cudaStream_t st) {
     if (n <= 1) return;
     const int nb = (int)((n + kRadixTile - 1) / kRadixTile);
     unsigned int* hist = static_cast<unsigned int*>(tmp);
     unsigned int* stmp = hist + 256ll * nb;
-    unsigned long long *ki = keys, *ko = keys_alt;
+    K *ki = keys, *ko = keys_alt;
     unsigned int *vi = vals, *vo = vals_alt;
     const int passes = (bits + 7) / 8;
     for (int p = 0; p < passes; ++p) {
         const int shift = 8 * p;
-        LMRS_LAUNCH(k_radix_hist, nb, kRadixBlock, 0, st, ki, n, shift, hist, nb);
+        LMRS_LAUNCH(k_radix_hist<K>, nb, kRadixBlock, 0, st, ki, n, shift, hist, nb);
         scan_rec<unsigned int>(hist, 256ll * nb, nullptr, stmp, st);
-        LMRS_LAUNCH(k_radix_scatter, nb, kRadixBlock, 0, st, ki, vi, ko, vo, n, shift, hist, nb);
-        unsigned long long* tk = ki; ki = ko; ko = tk;
+        LMRS_LAUNCH(k_radix_scatter<K>, nb, kRadixBlock, 0, st, ki, vi, ko, vo, n, shift, hist, nb);
+        K* tk = ki; ki = ko; ko = tk;
         unsigned int* tv = vi; vi = vo; vo = tv;
     }
     if (ki != keys) {
-        cudaMemcpyAsync(keys, ki, (size_t)n * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(keys, ki, (size_t)n * sizeof(K), cudaMemcpyDeviceToDevice, st);
         cudaMemcpyAsync(vals, vi, (size_t)n * sizeof(unsigned int), cudaMemcpyDeviceToDevice, st);
     }
+}
+
+void radix_sort(unsigned long long* keys, unsigned int* vals, unsigned long long* keys_alt, unsigned int* vals_alt,
+                long long n, int bits, void* tmp, size_t, cudaStream_t st) {
+    radix_sort_impl<unsigned long long>(keys, vals, keys_alt, vals_alt, n, bits, tmp, st);
+}
+
+void radix_sort32(unsigned int* keys, unsigned int* vals, unsigned int* keys_alt, unsigned int* vals_alt, long long n,
+                  int bits, void* tmp, size_t, cudaStream_t st) {
+    radix_sort_impl<unsigned int>(keys, vals, keys_alt, vals_alt, n, bits, tmp, st);
+}
+
+// ---------------------------------------------------------------------------
+// Level 2: tile counts of the depth-sorted pairs and entry emission.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long rect_area(int4 rc) {
+    return rc.x > rc.y ? 0ull : (unsigned long long)(rc.y - rc.x + 1) * (unsigned long long)(rc.w - rc.z + 1);
+}
+
+__global__ void k_sorted_counts(Ctx c) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (long long)c.nv * c.G) return;
+    const long long slot = (long long)(c.dkeys[k] >> 32);
+    c.cnt[k] = rect_area(c.rect[slot * c.G + c.dvals[k]]);
+}
+
+// One thread per depth-sorted pair; its entries are (view-tile key, Gaussian).
+__global__ void k_emit(Ctx c) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (long long)c.nv * c.G) return;
+    const unsigned slot = (unsigned)(c.dkeys[k] >> 32);
+    const unsigned g = c.dvals[k];
+    const int4 rc = c.rect[(long long)slot * c.G + g];
+    if (rc.x > rc.y) return;
+    unsigned long long o = c.cnt[k];
+    const unsigned base = slot * (unsigned)c.T;
+    for (int ty = rc.z; ty <= rc.w; ++ty)
+        for (int tx = rc.x; tx <= rc.y; ++tx) {
+            c.keys[o] = base + (unsigned)(ty * c.tiles_x + tx);
+            c.ids[o] = g;
+            ++o;
+        }
+}
+
+void launch_sorted_counts(const Ctx& c, cudaStream_t st) {
+    const long long n = (long long)c.nv * c.G;
+    LMRS_LAUNCH(k_sorted_counts, (unsigned)((n + 255) / 256), 256, 0, st, c);
+}
+
+void launch_emit(const Ctx& c, cudaStream_t st) {
+    const long long n = (long long)c.nv * c.G;
+    LMRS_LAUNCH(k_emit, (unsigned)((n + 127) / 128), 128, 0, st, c);
 }
 
 // ---------------------------------------------------------------------------
@@ -225,9 +263,9 @@ void radix_sort(unsigned long long* keys, unsigned int* vals, unsigned long long
 __global__ void k_ranges(Ctx c) {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= c.npairs) return;
-    const unsigned vt = (unsigned)(c.keys[k] >> 32);
-    if (k == 0 || (unsigned)(c.keys[k - 1] >> 32) != vt) c.ranges[vt].x = (int)k;
-    if (k == c.npairs - 1 || (unsigned)(c.keys[k + 1] >> 32) != vt) c.ranges[vt].y = (int)(k + 1);
+    const unsigned vt = c.keys[k];
+    if (k == 0 || c.keys[k - 1] != vt) c.ranges[vt].x = (int)k;
+    if (k == c.npairs - 1 || c.keys[k + 1] != vt) c.ranges[vt].y = (int)(k + 1);
 }
 
 void launch_ranges(const Ctx& c, cudaStream_t st) {

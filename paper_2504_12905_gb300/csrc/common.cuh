@@ -69,13 +69,14 @@ struct Ctx {
     float4* gcache;         // per Gaussian, kGaussF4 planes of G float4 (view-independent 3D state)
     float4* rec;            // kRecF4 float4: primal (3) then tangent (3)
     int4* rect;             // inclusive tile rectangle, x0 > x1 when culled
-    unsigned int* depth;    // FP32 depth bits
-    unsigned long long* cnt;  // tiles touched (then exclusive prefix)
+    unsigned long long* dkeys;  // (slot << 32 | depth bits, or all ones when culled), sorted in place
+    unsigned int* dvals;        // Gaussian index of each depth key
+    unsigned long long* cnt;  // tiles touched per depth-sorted pair (then exclusive prefix)
     unsigned long long* n_visible;  // count of visible pairs
     float* cot;             // kCotF floats
     float* gram;            // kGramF floats
     // binning
-    unsigned long long* keys;
+    unsigned int* keys;     // slot * T + tile of each list entry
     unsigned int* ids;
     long long npairs;
     int2* ranges;           // [nv * T] begin, end
@@ -123,12 +124,17 @@ void launch_prep_diag(const Ctx& c, float* D, cudaStream_t st);
 void scan_u64(unsigned long long* data, long long n, unsigned long long* total_dev, void* tmp, size_t tmp_bytes,
               cudaStream_t st);
 size_t scan_u64_tmp_bytes(long long n);
+// tile counts of the depth-sorted pairs into cnt (then scanned in place)
+void launch_sorted_counts(const Ctx& c, cudaStream_t st);
+// one (slot * T + tile, Gaussian) entry per overlapped tile, in depth order
 void launch_emit(const Ctx& c, cudaStream_t st);
 size_t radix_tmp_bytes(long long n);
 // Stable LSD radix sort of (keys, vals) on the low `bits` key bits.
 // Result ends in keys/vals (the alternate buffers are scratch).
 void radix_sort(unsigned long long* keys, unsigned int* vals, unsigned long long* keys_alt, unsigned int* vals_alt,
                 long long n, int bits, void* tmp, size_t tmp_bytes, cudaStream_t st);
+void radix_sort32(unsigned int* keys, unsigned int* vals, unsigned int* keys_alt, unsigned int* vals_alt, long long n,
+                  int bits, void* tmp, size_t tmp_bytes, cudaStream_t st);
 void launch_ranges(const Ctx& c, cudaStream_t st);
 
 // ---- raster.cu ------------------------------------------------------------

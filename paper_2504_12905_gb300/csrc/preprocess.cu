@@ -605,9 +605,11 @@ __global__ void k_prep_fwd(Ctx c) {
     const unsigned ballot = __ballot_sync(__activemask(), vis);
     if ((threadIdx.x & 31) == __ffs(__activemask()) - 1 && ballot)
         atomicAdd(c.n_visible, (unsigned long long)__popc(ballot));
+    // depth key in (slot, Gaussian) order: the stable depth sort keeps index order on ties
+    c.dvals[i] = (unsigned int)g;
     if (!vis) {
         c.rect[i] = make_int4(1, 0, 1, 0);
-        c.cnt[i] = 0ull;
+        c.dkeys[i] = ((unsigned long long)slot << 32) | 0xFFFFFFFFull;
         return;
     }
     const float* sh = c.params + 11ll * c.G + (long long)g * 3 * Sh<DEG>::K;
@@ -617,8 +619,7 @@ __global__ void k_prep_fwd(Ctx c) {
     r[1] = make_float4(P.C, P.o, P.col[0], P.col[1]);
     r[2] = make_float4(P.col[2], 0.f, 0.f, 0.f);
     c.rect[i] = rect;
-    c.depth[i] = __float_as_uint(depth);
-    c.cnt[i] = (unsigned long long)(rect.y - rect.x + 1) * (unsigned long long)(rect.w - rect.z + 1);
+    c.dkeys[i] = ((unsigned long long)slot << 32) | __float_as_uint(depth);
 }
 
 // Primal state of a visible pair for the derivative kernels.

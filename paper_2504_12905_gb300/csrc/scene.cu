@@ -73,7 +73,7 @@ struct lmrs_scene {
     const float* targets = nullptr;
     // device state
     DevBuf params, cams, views, gcache;
-    DevBuf rec, rect, depth, cnt, cot, gram;
+    DevBuf rec, rect, dkeys, dvals, dkeys_alt, dvals_alt, dtmp, cnt, cot, gram;
     DevBuf keys, ids, keys_alt, ids_alt, ranges, scan_tmp, radix_tmp, total;
     DevBuf tile_off, off, wtile, work;
     DevBuf item_cost, work_sorted, okeys, ovals, okeys_alt, ovals_alt, otmp;
@@ -108,12 +108,13 @@ struct lmrs_scene {
         c.gcache = gcache.as<float4>();
         c.rec = rec.as<float4>();
         c.rect = rect.as<int4>();
-        c.depth = depth.as<unsigned int>();
+        c.dkeys = dkeys.as<unsigned long long>();
+        c.dvals = dvals.as<unsigned int>();
         c.cnt = cnt.as<unsigned long long>();
         c.n_visible = total.as<unsigned long long>() + 1;
         c.cot = cot.as<float>();
         c.gram = gram.as<float>();
-        c.keys = keys.as<unsigned long long>();
+        c.keys = keys.as<unsigned int>();
         c.ids = ids.as<unsigned int>();
         c.npairs = npairs;
         c.ranges = ranges.as<int2>();
@@ -442,7 +443,8 @@ lmrs_status lmrs_scene_create(const lmrs_config* cfg, int64_t n_gauss, const flo
 lmrs_status lmrs_scene_destroy(lmrs_scene* s) {
     if (!s) return LMRS_ERR_INVALID_ARG;
     if (s->st) cudaStreamSynchronize(s->st);
-    for (DevBuf* b : {&s->params, &s->cams, &s->views, &s->gcache, &s->rec, &s->rect, &s->depth, &s->cnt, &s->cot, &s->gram,
+    for (DevBuf* b : {&s->params, &s->cams, &s->views, &s->gcache, &s->rec, &s->rect, &s->dkeys, &s->dvals,
+                      &s->dkeys_alt, &s->dvals_alt, &s->dtmp, &s->cnt, &s->cot, &s->gram,
                       &s->keys, &s->ids, &s->keys_alt, &s->ids_alt, &s->ranges, &s->scan_tmp, &s->radix_tmp,
                       &s->total, &s->tile_off, &s->off, &s->wtile, &s->work, &s->item_cost,
                       &s->work_sorted, &s->okeys, &s->ovals, &s->okeys_alt, &s->ovals_alt, &s->otmp, &s->resid, &s->cacheC, &s->cacheT,
@@ -493,7 +495,11 @@ lmrs_status lmrs_preprocess(lmrs_scene* s, const int32_t* view_ids, int32_t n_vi
     TRY(ensure(s, s->views, sizeof(int) * n_views));
     TRY(ensure(s, s->rec, sizeof(float4) * kRecF4 * pairs));
     TRY(ensure(s, s->rect, sizeof(int4) * pairs));
-    TRY(ensure(s, s->depth, sizeof(unsigned int) * pairs));
+    TRY(ensure(s, s->dkeys, sizeof(unsigned long long) * pairs));
+    TRY(ensure(s, s->dkeys_alt, sizeof(unsigned long long) * pairs));
+    TRY(ensure(s, s->dvals, sizeof(unsigned int) * pairs));
+    TRY(ensure(s, s->dvals_alt, sizeof(unsigned int) * pairs));
+    TRY(ensure(s, s->dtmp, radix_tmp_bytes((long long)pairs)));
     TRY(ensure(s, s->cnt, sizeof(unsigned long long) * pairs));
     TRY(ensure(s, s->cot, sizeof(float) * kCotF * pairs));
     TRY(ensure(s, s->ranges, sizeof(int2) * (size_t)s->nv * s->T));
@@ -505,6 +511,12 @@ lmrs_status lmrs_preprocess(lmrs_scene* s, const int32_t* view_ids, int32_t n_vi
     launch_sample(c, lm_step, s->cfg.seed, s->st);
     launch_prep_gauss(c, s->st);
     launch_prep_fwd(c, s->st);
+    // level 1: (slot, depth, index) order of the pairs
+    int sbits = 0;
+    while ((1 << sbits) < s->nv) ++sbits;
+    radix_sort(c.dkeys, c.dvals, s->dkeys_alt.as<unsigned long long>(), s->dvals_alt.as<unsigned int>(),
+               (long long)pairs, 32 + sbits, s->dtmp.p, s->dtmp.cap, s->st);
+    launch_sorted_counts(c, s->st);
     scan_u64(c.cnt, (long long)pairs, s->total.as<unsigned long long>(), s->scan_tmp.p, s->scan_tmp.cap, s->st);
     CHECK_LAUNCH(s);
     unsigned long long tot2[2] = {0ull, 0ull};
@@ -515,17 +527,18 @@ lmrs_status lmrs_preprocess(lmrs_scene* s, const int32_t* view_ids, int32_t n_vi
     if (total >= (1ull << 31)) return fail(s, LMRS_ERR_BUDGET, "more than 2^31 (view, tile, Gaussian) pairs");
     s->npairs = (long long)total;
     const size_t np = std::max<size_t>((size_t)total, 1);
-    TRY(ensure(s, s->keys, sizeof(unsigned long long) * np));
-    TRY(ensure(s, s->keys_alt, sizeof(unsigned long long) * np));
+    TRY(ensure(s, s->keys, sizeof(unsigned int) * np));
+    TRY(ensure(s, s->keys_alt, sizeof(unsigned int) * np));
     TRY(ensure(s, s->ids, sizeof(unsigned int) * np));
     TRY(ensure(s, s->ids_alt, sizeof(unsigned int) * np));
     TRY(ensure(s, s->radix_tmp, radix_tmp_bytes((long long)np)));
     c = s->ctx();
+    // level 2: entries in depth order, then a stable sort on the (slot, tile) bits
     launch_emit(c, s->st);
     int vbits = 0;
     while ((1ll << vbits) < (long long)s->nv * s->T) ++vbits;
-    radix_sort(c.keys, c.ids, s->keys_alt.as<unsigned long long>(), s->ids_alt.as<unsigned int>(), s->npairs,
-               32 + vbits, s->radix_tmp.p, s->radix_tmp.cap, s->st);
+    radix_sort32(c.keys, c.ids, s->keys_alt.as<unsigned int>(), s->ids_alt.as<unsigned int>(), s->npairs, vbits,
+                 s->radix_tmp.p, s->radix_tmp.cap, s->st);
     CK(s, cudaMemsetAsync(s->ranges.p, 0, sizeof(int2) * (size_t)s->nv * s->T, s->st));
     launch_ranges(c, s->st);
     CHECK_LAUNCH(s);
