@@ -88,6 +88,11 @@ struct Ctx {
     const int2* work;       // (slot * T + tile, first sample in tile) per warp item
     int nwork;
     int* item_cost;         // [nwork] list entries a work item traverses (from the forward render)
+    // compact lists (written by the forward render): the entries a work item's
+    // pixels need; chunk q of tile vt at max_items * begin(vt) + q * len(vt)
+    unsigned int* cids;     // [max_items * npairs]
+    int* clen;              // [nv * T * max_items]
+    int max_items;          // largest number of 32-sample chunks in a tile
     // per-sample caches
     float* resid;           // [S][3]
     float* cacheC;          // [S][3] FP32 (or BF16 in cacheCh)

@@ -4,18 +4,23 @@
 // (Eq. 4, Alg. 2).  Gaussian records are staged 32 at a time into the warp's
 // shared-memory slice with coalesced id loads and 16-byte record loads.
 //
-//   k_fwd_samples  render + residual (Eq. 7) + per-sample caches
+//   k_fwd_samples  render + residual (Eq. 7) + per-sample caches; also the
+//                  work item's compact list: the entries at which at least
+//                  one of its live pixels has alpha >= 1/255 (every other
+//                  entry is skipped by all of them, so dropping it changes no
+//                  pixel), and each pixel's stopping position in it
 //   k_full         full frames (all pixels)
 //   k_jvp          u = J v, dual-number style tangent compositing (Alg. 3)
 //   k_vjp          back-scatter of a per-sample cotangent (App. A, J^T v
 //                  kernel, first launch) using the cached final colour and
-//                  termination position
+//                  stopping position
 //   k_jtj          fused: JVP pass then VJP pass of w * (J v) per work item
 //   k_gram         per-pair Gram blocks of the per-sample feature gradients
 //                  (App. A, Diag kernel; completed by k_prep_diag)
-// Back-scatter: per Gaussian, the 32 lanes' contributions are summed with a
-// warp reduce-scatter and one lane per value issues a single atomic add into
-// the per-(view, Gaussian) slot.
+// k_vjp, k_jtj and k_gram walk the compact lists.  Back-scatter: per
+// Gaussian, the lanes' contributions are summed with a warp reduce-scatter
+// and one lane per value issues a single atomic add into the per-(view,
+// Gaussian) slot.
 #include "common.cuh"
 #include "reduce.cuh"
 
@@ -25,7 +30,7 @@ constexpr int kRasterWarps = 4;
 constexpr int kRasterBlock = kRasterWarps * kWarp;
 
 struct Pix {
-    int vt, slot, tile;
+    int vt, slot, tile, chunk;
     long long si;
     bool active;
     float pcx, pcy;
@@ -37,6 +42,7 @@ __device__ __forceinline__ void setup_item(const Ctx& c, int item, Pix& p) {
     const int lane = threadIdx.x & 31;
     const int2 wk = c.work[item];
     p.vt = wk.x;
+    p.chunk = wk.y >> 5;
     p.slot = p.vt / c.T;
     p.tile = p.vt - p.slot * c.T;
     const int tx = p.tile % c.tiles_x, ty = p.tile / c.tiles_x;
@@ -52,13 +58,43 @@ __device__ __forceinline__ void setup_item(const Ctx& c, int item, Pix& p) {
     p.w = c.wtile[p.vt];
 }
 
+// The list a kernel walks: ids[b, e).
+struct List {
+    const unsigned* ids;
+    int b, e;
+};
+
+// Compact list of a work item: capacity max_items * (tile list length) per
+// tile, chunk q at offset max_items * begin + q * length.
+__device__ __forceinline__ long long compact_base(const Ctx& c, const Pix& p, int2 rg) {
+    return (long long)c.max_items * rg.x + (long long)p.chunk * (rg.y - rg.x);
+}
+
+__device__ __forceinline__ List compact_list(const Ctx& c, const Pix& p) {
+    const int2 rg = c.ranges[p.vt];
+    List L;
+    L.ids = c.cids + compact_base(c, p, rg);
+    L.b = 0;
+    L.e = c.clen[(long long)p.vt * c.max_items + p.chunk];
+    return L;
+}
+
+__device__ __forceinline__ List tile_list(const Ctx& c, const Pix& p) {
+    const int2 rg = c.ranges[p.vt];
+    List L;
+    L.ids = c.ids;
+    L.b = rg.x;
+    L.e = rg.y;
+    return L;
+}
+
 template <int NF4>
-__device__ __forceinline__ int stage_batch(const Ctx& c, int slot, int b, int end, float4 (*s_rec)[kRecF4],
-                                           unsigned* s_id) {
+__device__ __forceinline__ int stage_batch(const Ctx& c, int slot, const unsigned* ids, int b, int end,
+                                           float4 (*s_rec)[kRecF4], unsigned* s_id) {
     const int lane = threadIdx.x & 31;
     const int k = b + lane;
     if (k < end) {
-        const unsigned id = c.ids[k];
+        const unsigned id = ids[k];
         const float4* r = c.rec + ((long long)slot * c.G + id) * kRecF4;
 #pragma unroll
         for (int q = 0; q < NF4; ++q) s_rec[lane][q] = r[q];
@@ -69,32 +105,64 @@ __device__ __forceinline__ int stage_batch(const Ctx& c, int slot, int b, int en
 }
 
 // Front-to-back pass.  With kTan also the tangent of the colour (Alg. 3).
-// ncons = list entries consumed before termination (the whole list if none).
-template <bool kTan>
-__device__ __forceinline__ void forward_pass(const Ctx& c, const Pix& p, int2 rg, float4 (*s_rec)[kRecF4],
-                                             unsigned* s_id, float C[3], float& T, float dC[3], int& ncons) {
+// ncons = entries of the walked list consumed before termination (all of
+// them if none).  With kCompact the needed entries are appended to out_ids
+// and ncons counts them instead; *out_len receives their number.
+template <bool kTan, bool kCompact>
+__device__ __forceinline__ void forward_pass(const Ctx& c, const Pix& p, List L, float4 (*s_rec)[kRecF4],
+                                             unsigned* s_id, float C[3], float& T, float dC[3], int& ncons,
+                                             unsigned* out_ids = nullptr, int* out_len = nullptr) {
+    const int lane = threadIdx.x & 31;
     T = 1.f;
     float dT = 0.f;
     C[0] = C[1] = C[2] = 0.f;
     dC[0] = dC[1] = dC[2] = 0.f;
     bool done = !p.active;
-    ncons = rg.y - rg.x;
-    for (int b = rg.x; b < rg.y; b += 32) {
+    ncons = L.e - L.b;
+    int kept = 0;
+    for (int b = L.b; b < L.e; b += 32) {
         if (__all_sync(kFull, done)) break;
-        const int n = stage_batch<kTan ? 6 : 3>(c, p.slot, b, rg.y, s_rec, s_id);
+        const int n = stage_batch<kTan ? 6 : 3>(c, p.slot, L.ids, b, L.e, s_rec, s_id);
         for (int j = 0; j < n; ++j) {
-            if (done) continue;
-            const float4 r0 = s_rec[j][0], r1 = s_rec[j][1];
-            const float dx = r0.x - p.pcx, dy = r0.y - p.pcy;
-            const float power = -0.5f * (r0.z * dx * dx + r1.x * dy * dy) - r0.w * dx * dy;
-            const float gval = __expf(power);
-            const float raw = r1.y * gval;
-            const float alpha = fminf(kAlphaMax, raw);
-            if (alpha < kAlphaMin) continue;
+            bool need = false;
+            float alpha = 0.f, raw = 0.f, gval = 0.f, dx = 0.f, dy = 0.f;
+            float4 r0, r1;
+            if (!done) {
+                r0 = s_rec[j][0];
+                r1 = s_rec[j][1];
+                dx = r0.x - p.pcx;
+                dy = r0.y - p.pcy;
+                const float power = -0.5f * (r0.z * dx * dx + r1.x * dy * dy) - r0.w * dx * dy;
+                gval = __expf(power);
+                raw = r1.y * gval;
+                alpha = fminf(kAlphaMax, raw);
+                need = alpha >= kAlphaMin;
+            }
+            if (kCompact) {
+                const bool any = __any_sync(kFull, need);
+                if (any && lane == 0) out_ids[kept] = s_id[j];
+                if (need) {
+                    const float Tn = T * (1.f - alpha);
+                    if (Tn < kTMin) {
+                        done = true;
+                        ncons = kept;
+                    } else {
+                        const float col2 = s_rec[j][2].x;
+                        const float wgt = alpha * T;
+                        C[0] += r1.z * wgt;
+                        C[1] += r1.w * wgt;
+                        C[2] += col2 * wgt;
+                        T = Tn;
+                    }
+                }
+                if (any) ++kept;
+                continue;
+            }
+            if (!need) continue;
             const float Tn = T * (1.f - alpha);
             if (Tn < kTMin) {
                 done = true;
-                ncons = b + j - rg.x;
+                ncons = b + j - L.b;
                 continue;
             }
             const float col2 = s_rec[j][2].x;
@@ -121,23 +189,28 @@ __device__ __forceinline__ void forward_pass(const Ctx& c, const Pix& p, int2 rg
         }
         __syncwarp();
     }
+    if (kCompact) {
+        if (!done) ncons = kept;
+        if (out_len && lane == 0) *out_len = kept;
+    }
 }
 
 // Back-scatter of the cotangent ub of each lane's colour into the 9 feature
 // cotangents of every contributing Gaussian (reverse mode through Eq. 4 with
 // the final colour Cf known: dC/dalpha_n = T_n c_n - (Cf - C_<=n)/(1 - alpha_n)).
-__device__ __forceinline__ void backward_pass(const Ctx& c, const Pix& p, int2 rg, float4 (*s_rec)[kRecF4],
+// Lane stops after its first ncons entries of the list.
+__device__ __forceinline__ void backward_pass(const Ctx& c, const Pix& p, List L, float4 (*s_rec)[kRecF4],
                                               unsigned* s_id, const float ub[3], const float Cf[3], int ncons) {
     const int lane = threadIdx.x & 31;
     const float S_tot = ub[0] * Cf[0] + ub[1] * Cf[1] + ub[2] * Cf[2];
     float s = 0.f, T = 1.f;
-    const int lane_end = p.active ? rg.x + ncons : rg.x;
+    const int lane_end = p.active ? L.b + ncons : L.b;
     int warp_end = lane_end;
 #pragma unroll
     for (int m = 16; m >= 1; m >>= 1) warp_end = max(warp_end, __shfl_xor_sync(kFull, warp_end, m));
     float* cot_base = c.cot + (long long)p.slot * c.G * kCotF;
-    for (int b = rg.x; b < warp_end; b += 32) {
-        const int n = stage_batch<3>(c, p.slot, b, warp_end, s_rec, s_id);
+    for (int b = L.b; b < warp_end; b += 32) {
+        const int n = stage_batch<3>(c, p.slot, L.ids, b, warp_end, s_rec, s_id);
         for (int j = 0; j < n; ++j) {
             float v[16];
 #pragma unroll
@@ -204,14 +277,16 @@ __device__ __forceinline__ void load_cache(const Ctx& c, long long si, float Cf[
     float4(*s_rec)[kRecF4] = s_rec_all[wid];                                    \
     unsigned* s_id = s_id_all[wid];                                             \
     Pix p;                                                                      \
-    setup_item(c, item, p);                                                     \
-    const int2 rg = c.ranges[p.vt];
+    setup_item(c, item, p);
 
 __global__ void __launch_bounds__(kRasterBlock) k_fwd_samples(Ctx c) {
     LMRS_RASTER_PROLOGUE
+    const int2 rg = c.ranges[p.vt];
     float C[3], T, dC[3];
     int ncons;
-    forward_pass<false>(c, p, rg, s_rec, s_id, C, T, dC, ncons);
+    int* len_out = c.clen + (long long)p.vt * c.max_items + p.chunk;
+    forward_pass<false, true>(c, p, tile_list(c, p), s_rec, s_id, C, T, dC, ncons,
+                              c.cids + compact_base(c, p, rg), len_out);
     double num = 0.0, den = 0.0;
     if (p.active) {
         const long long si = p.si;
@@ -239,11 +314,8 @@ __global__ void __launch_bounds__(kRasterBlock) k_fwd_samples(Ctx c) {
         num = (double)p.w * ((double)r[0] * r[0] + (double)r[1] * r[1] + (double)r[2] * r[2]);
         den = 3.0 * p.w;
     }
-    // traversal length of this work item (the longest-lived lane)
-    int len = p.active ? ncons : 0;
-#pragma unroll
-    for (int m = 16; m >= 1; m >>= 1) len = max(len, __shfl_xor_sync(kFull, len, m));
-    if ((threadIdx.x & 31) == 0 && c.item_cost) c.item_cost[item] = len;
+    // traversal length of this work item in the kernels that walk the compact list
+    if ((threadIdx.x & 31) == 0 && c.item_cost) c.item_cost[item] = *len_out;
     num = warp_sum(num);
     den = warp_sum(den);
     if ((threadIdx.x & 31) == 0) {
@@ -256,7 +328,7 @@ __global__ void __launch_bounds__(kRasterBlock) k_jvp(Ctx c, float* u) {
     LMRS_RASTER_PROLOGUE
     float C[3], T, dC[3];
     int ncons;
-    forward_pass<true>(c, p, rg, s_rec, s_id, C, T, dC, ncons);
+    forward_pass<true, false>(c, p, tile_list(c, p), s_rec, s_id, C, T, dC, ncons);
     if (p.active) {
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) u[3 * p.si + ch] = dC[ch];
@@ -272,16 +344,17 @@ __global__ void __launch_bounds__(kRasterBlock) k_vjp(Ctx c, const float* u) {
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) ub[ch] = u ? u[3 * p.si + ch] : p.w * c.resid[3 * p.si + ch];
     }
-    backward_pass(c, p, rg, s_rec, s_id, ub, Cf, ncons);
+    backward_pass(c, p, compact_list(c, p), s_rec, s_id, ub, Cf, ncons);
 }
 
 __global__ void __launch_bounds__(kRasterBlock) k_jtj(Ctx c) {
     LMRS_RASTER_PROLOGUE
+    const List L = compact_list(c, p);
     float C[3], T, dC[3];
     int ncons;
-    forward_pass<true>(c, p, rg, s_rec, s_id, C, T, dC, ncons);
+    forward_pass<true, false>(c, p, L, s_rec, s_id, C, T, dC, ncons);
     const float ub[3] = {p.w * dC[0], p.w * dC[1], p.w * dC[2]};
-    backward_pass(c, p, rg, s_rec, s_id, ub, C, ncons);
+    backward_pass(c, p, L, s_rec, s_id, ub, C, ncons);
 }
 
 // Gram blocks: per contributing (sample, Gaussian), with e = d alpha /
@@ -291,18 +364,19 @@ __global__ void __launch_bounds__(kRasterBlock) k_jtj(Ctx c) {
 //   [39]     w q^2
 __global__ void __launch_bounds__(kRasterBlock) k_gram(Ctx c) {
     LMRS_RASTER_PROLOGUE
+    const List L = compact_list(c, p);
     const int lane = threadIdx.x & 31;
     float Cf[3] = {0.f, 0.f, 0.f};
     int ncons = 0;
     if (p.active) load_cache(c, p.si, Cf, ncons);
-    const int lane_end = p.active ? rg.x + ncons : rg.x;
+    const int lane_end = p.active ? L.b + ncons : L.b;
     int warp_end = lane_end;
 #pragma unroll
     for (int m = 16; m >= 1; m >>= 1) warp_end = max(warp_end, __shfl_xor_sync(kFull, warp_end, m));
     float acc[3] = {0.f, 0.f, 0.f}, T = 1.f;
     float* gbase = c.gram + (long long)p.slot * c.G * kGramF;
-    for (int b = rg.x; b < warp_end; b += 32) {
-        const int n = stage_batch<3>(c, p.slot, b, warp_end, s_rec, s_id);
+    for (int b = L.b; b < warp_end; b += 32) {
+        const int n = stage_batch<3>(c, p.slot, L.ids, b, warp_end, s_rec, s_id);
         for (int j = 0; j < n; ++j) {
             float v[32], v2[16];
 #pragma unroll
@@ -384,6 +458,7 @@ __global__ void __launch_bounds__(256) k_full(Ctx c, float* images) {
     p.vt = vt;
     p.slot = slot;
     p.tile = tile;
+    p.chunk = 0;
     const int o = first + lane;
     p.active = o < nvalid;
     p.si = 0;
@@ -392,10 +467,9 @@ __global__ void __launch_bounds__(256) k_full(Ctx c, float* images) {
     p.pcx = p.px + 0.5f;
     p.pcy = p.py + 0.5f;
     p.w = 1.f;
-    const int2 rg = c.ranges[vt];
     float C[3], T, dC[3];
     int ncons;
-    forward_pass<false>(c, p, rg, s_rec_all[wid], s_id_all[wid], C, T, dC, ncons);
+    forward_pass<false, false>(c, p, tile_list(c, p), s_rec_all[wid], s_id_all[wid], C, T, dC, ncons);
     if (p.active) {
         float* dst = images + (((long long)slot * c.H + p.py) * c.W + p.px) * 3;
         dst[0] = C[0];

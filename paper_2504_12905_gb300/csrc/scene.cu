@@ -77,6 +77,8 @@ struct lmrs_scene {
     DevBuf keys, ids, keys_alt, ids_alt, ranges, scan_tmp, radix_tmp, total;
     DevBuf tile_off, off, wtile, work;
     DevBuf item_cost, work_sorted, okeys, ovals, okeys_alt, ovals_alt, otmp;
+    DevBuf cids, clen;
+    int max_items = 1;
     DevBuf resid, cacheC, cacheT, cacheCh, cacheTh, cacheN;
     DevBuf x, r, z, p, Ap, minv, D, b, stage_a, stage_b;
     DevBuf sc, partials, counter;
@@ -124,6 +126,9 @@ struct lmrs_scene {
         c.S = S;
         c.work = ordered ? work_sorted.as<int2>() : work.as<int2>();
         c.item_cost = item_cost.as<int>();
+        c.cids = cids.as<unsigned int>();
+        c.clen = clen.as<int>();
+        c.max_items = max_items;
         c.nwork = nwork;
         c.resid = resid.as<float>();
         c.cacheC = cacheC.as<float>();
@@ -242,6 +247,7 @@ int samples_in_tile(const lmrs_config& cfg, int n_valid) {
 lmrs_status build_layout(lmrs_scene* s) {
     if (s->layout_nv == s->nv) return LMRS_OK;
     const int nT = s->nv * s->T;
+    s->max_items = 1;
     std::vector<int> toff(nT + 1, 0);
     std::vector<float> w(nT);
     std::vector<int2> work;
@@ -256,6 +262,7 @@ lmrs_status build_layout(lmrs_scene* s) {
             toff[vt + 1] = toff[vt] + k;
             w[vt] = s->cfg.weight_mode == 1 ? (float)((double)n / (double)k) : 1.f;
             for (int j = 0; j < k; j += 32) work.push_back(make_int2(vt, j));
+            s->max_items = std::max(s->max_items, (k + 31) / 32);
         }
     s->S = toff[nT];
     s->nwork = (int)work.size();
@@ -277,6 +284,7 @@ lmrs_status build_layout(lmrs_scene* s) {
     TRY(ensure(s, s->ovals, sizeof(unsigned int) * nw));
     TRY(ensure(s, s->ovals_alt, sizeof(unsigned int) * nw));
     TRY(ensure(s, s->otmp, radix_tmp_bytes((long long)nw)));
+    TRY(ensure(s, s->clen, sizeof(int) * (size_t)nT * s->max_items));
     // pageable sources: the copies are staged before the calls return
     CK(s, cudaMemcpyAsync(s->tile_off.p, toff.data(), sizeof(int) * (nT + 1), cudaMemcpyHostToDevice, s->st));
     CK(s, cudaMemcpyAsync(s->wtile.p, w.data(), sizeof(float) * nT, cudaMemcpyHostToDevice, s->st));
@@ -447,7 +455,7 @@ lmrs_status lmrs_scene_destroy(lmrs_scene* s) {
                       &s->dkeys_alt, &s->dvals_alt, &s->dtmp, &s->cnt, &s->cot, &s->gram,
                       &s->keys, &s->ids, &s->keys_alt, &s->ids_alt, &s->ranges, &s->scan_tmp, &s->radix_tmp,
                       &s->total, &s->tile_off, &s->off, &s->wtile, &s->work, &s->item_cost,
-                      &s->work_sorted, &s->okeys, &s->ovals, &s->okeys_alt, &s->ovals_alt, &s->otmp, &s->resid, &s->cacheC, &s->cacheT,
+                      &s->work_sorted, &s->okeys, &s->ovals, &s->okeys_alt, &s->ovals_alt, &s->otmp, &s->cids, &s->clen, &s->resid, &s->cacheC, &s->cacheT,
                       &s->cacheCh, &s->cacheTh, &s->cacheN, &s->x, &s->r, &s->z, &s->p, &s->Ap, &s->minv, &s->D,
                       &s->b, &s->stage_a, &s->stage_b, &s->sc, &s->partials, &s->counter})
         release(*b);
@@ -532,6 +540,7 @@ lmrs_status lmrs_preprocess(lmrs_scene* s, const int32_t* view_ids, int32_t n_vi
     TRY(ensure(s, s->ids, sizeof(unsigned int) * np));
     TRY(ensure(s, s->ids_alt, sizeof(unsigned int) * np));
     TRY(ensure(s, s->radix_tmp, radix_tmp_bytes((long long)np)));
+    TRY(ensure(s, s->cids, sizeof(unsigned int) * np * (size_t)s->max_items));
     c = s->ctx();
     // level 2: entries in depth order, then a stable sort on the (slot, tile) bits
     launch_emit(c, s->st);
