@@ -229,22 +229,36 @@ __global__ void k_sorted_counts(Ctx c) {
     c.cnt[k] = rect_area(c.rect[slot * c.G + c.dvals[k]]);
 }
 
-// One thread per depth-sorted pair; its entries are (view-tile key, Gaussian).
+// Entries (view-tile key, Gaussian) of the depth-sorted pairs.  Each warp
+// takes 32 consecutive pairs and writes them one pair at a time with all
+// lanes, so the stores are contiguous and large rectangles do not serialise
+// on one thread.
 __global__ void k_emit(Ctx c) {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= (long long)c.nv * c.G) return;
-    const unsigned slot = (unsigned)(c.dkeys[k] >> 32);
-    const unsigned g = c.dvals[k];
-    const int4 rc = c.rect[(long long)slot * c.G + g];
-    if (rc.x > rc.y) return;
-    unsigned long long o = c.cnt[k];
-    const unsigned base = slot * (unsigned)c.T;
-    for (int ty = rc.z; ty <= rc.w; ++ty)
-        for (int tx = rc.x; tx <= rc.y; ++tx) {
-            c.keys[o] = base + (unsigned)(ty * c.tiles_x + tx);
-            c.ids[o] = g;
-            ++o;
+    const int lane = threadIdx.x & 31;
+    unsigned slot = 0u, g = 0u;
+    int4 rc = make_int4(1, 0, 1, 0);
+    unsigned long long o = 0ull;
+    if (k < (long long)c.nv * c.G) {
+        slot = (unsigned)(c.dkeys[k] >> 32);
+        g = c.dvals[k];
+        rc = c.rect[(long long)slot * c.G + g];
+        o = c.cnt[k];
+    }
+    for (int j = 0; j < 32; ++j) {
+        const int x0 = __shfl_sync(0xffffffffu, rc.x, j), x1 = __shfl_sync(0xffffffffu, rc.y, j);
+        const int y0 = __shfl_sync(0xffffffffu, rc.z, j), y1 = __shfl_sync(0xffffffffu, rc.w, j);
+        const unsigned long long oj = __shfl_sync(0xffffffffu, o, j);
+        const unsigned gj = __shfl_sync(0xffffffffu, g, j);
+        const unsigned base = __shfl_sync(0xffffffffu, slot, j) * (unsigned)c.T;
+        if (x0 > x1) continue;
+        const int w = x1 - x0 + 1, area = w * (y1 - y0 + 1);
+        for (int e = lane; e < area; e += 32) {
+            const int ty = y0 + e / w, tx = x0 + e - (e / w) * w;
+            c.keys[oj + e] = base + (unsigned)(ty * c.tiles_x + tx);
+            c.ids[oj + e] = gj;
         }
+    }
 }
 
 void launch_sorted_counts(const Ctx& c, cudaStream_t st) {

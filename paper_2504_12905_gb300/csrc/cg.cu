@@ -1,9 +1,12 @@
 // Vector kernels of the preconditioned CG solve (Alg. 1) and the LM update
-// with the step-size rule (Sec. 4.5, App. D).  Inner products and scalars are
-// FP64 on the device: products of FP32 entries are exact in FP64 and the sums
-// run in FP64 with a fixed-order grid reduction, so no step of the solve goes
-// through the host.
+// with the step-size rule (Sec. 4.5, App. D).  Inner products: per-thread
+// partials in compensated FP32 (Dot2, twice-working-precision accuracy),
+// combined across threads in FP64 by a fixed-order grid reduction whose last
+// block also forms alpha or beta; no step of the solve goes through the host.
+// The streaming kernels use 16-byte accesses when every vector is 16-byte
+// aligned.
 #include <cstddef>
+#include <cstdint>
 
 #include "common.cuh"
 #include "reduce.cuh"
@@ -19,6 +22,8 @@ static int vec_grid(long long n) {
     return (int)g;
 }
 
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
 // Jacobi preconditioner 1 / diag(A) (Sec. 4.2): 1 / (D + lambda) for the
 // identity damping, 1 / ((1 + lambda) D) for the diagonal damping (0 where
 // D = 0: such a parameter touches no sampled pixel, its right-hand side is 0).
@@ -29,66 +34,119 @@ __global__ void k_precond(Ctx c, const float* D, float* minv) {
     }
 }
 
-// x0 = 0, r0 = b, z0 = M^-1 r0, p = 0 (the first p-update forms p0 = z0),
-// rz = r0^T z0.
+// Element range [lo, hi) of the scalar tail after the float4 body.
+struct Span {
+    long long n4, lo, hi, stride, first;
+};
+__device__ __forceinline__ Span span(long long P, bool vec) {
+    Span s;
+    s.stride = (long long)gridDim.x * blockDim.x;
+    s.first = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    s.n4 = vec ? P / 4 : 0;
+    s.lo = 4 * s.n4;
+    s.hi = P;
+    return s;
+}
+
+// x0 = 0, r0 = b, z0 = M^-1 r0, p = 0 (the first direction update forms
+// p0 = z0), rz = r0^T z0.
+template <bool kVec>
 __global__ void __launch_bounds__(kVecBlock) k_cg_init(Ctx c, const float* b, const float* minv, float* x, float* r,
                                                       float* z, float* p) {
-    double dot = 0.0;
-    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < c.P; j += (long long)gridDim.x * blockDim.x) {
+    Dot2 dot;
+    const Span s = span(c.P, kVec);
+    if (kVec) {
+        const float4* b4 = reinterpret_cast<const float4*>(b);
+        const float4* m4 = reinterpret_cast<const float4*>(minv);
+        const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (long long j = s.first; j < s.n4; j += s.stride) {
+            const float4 bj = b4[j], mj = m4[j];
+            const float4 zj = make_float4(mj.x * bj.x, mj.y * bj.y, mj.z * bj.z, mj.w * bj.w);
+            reinterpret_cast<float4*>(x)[j] = zero;
+            reinterpret_cast<float4*>(r)[j] = bj;
+            reinterpret_cast<float4*>(z)[j] = zj;
+            reinterpret_cast<float4*>(p)[j] = zero;
+            dot.add(bj.x, zj.x);
+            dot.add(bj.y, zj.y);
+            dot.add(bj.z, zj.z);
+            dot.add(bj.w, zj.w);
+        }
+    }
+    for (long long j = s.lo + s.first; j < s.hi; j += s.stride) {
         const float bj = b[j];
         const float zj = minv[j] * bj;
         x[j] = 0.f;
         r[j] = bj;
         z[j] = zj;
         p[j] = 0.f;
-        dot += (double)bj * (double)zj;
+        dot.add(bj, zj);
     }
     double tot;
-    if (grid_sum_last<kVecBlock>(dot, c.partials, c.counter, &tot) && threadIdx.x == 0) {
-        Scalars* s = c.sc;
-        s->rz = tot;
-        s->rz0 = tot;
-        s->beta = 0.0;
-        if (!isfinite(tot) || tot < 0.0) s->numeric_error = 1u;
+    if (grid_sum_last<kVecBlock>(dot.value(), c.partials, c.counter, &tot) && threadIdx.x == 0) {
+        Scalars* sc = c.sc;
+        sc->rz = tot;
+        sc->rz0 = tot;
+        sc->beta = 0.0;
+        if (!isfinite(tot) || tot < 0.0) sc->numeric_error = 1u;
     }
 }
 
 // x += alpha p, r -= alpha A p, z = M^-1 r, beta = r'^T z' / r^T z.
+template <bool kVec>
 __global__ void __launch_bounds__(kVecBlock) k_cg_update(Ctx c, int iter, const float* p, const float* Ap,
                                                         const float* minv, float* x, float* r, float* z) {
     const float alpha = (float)c.sc->alpha;
-    double dot = 0.0;
-    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < c.P; j += (long long)gridDim.x * blockDim.x) {
+    Dot2 dot;
+    const Span s = span(c.P, kVec);
+    if (kVec) {
+        for (long long j = s.first; j < s.n4; j += s.stride) {
+            const float4 pj = reinterpret_cast<const float4*>(p)[j];
+            const float4 aj = reinterpret_cast<const float4*>(Ap)[j];
+            const float4 mj = reinterpret_cast<const float4*>(minv)[j];
+            float4 xj = reinterpret_cast<float4*>(x)[j];
+            float4 rj = reinterpret_cast<float4*>(r)[j];
+            xj.x += alpha * pj.x; xj.y += alpha * pj.y; xj.z += alpha * pj.z; xj.w += alpha * pj.w;
+            rj.x -= alpha * aj.x; rj.y -= alpha * aj.y; rj.z -= alpha * aj.z; rj.w -= alpha * aj.w;
+            const float4 zj = make_float4(mj.x * rj.x, mj.y * rj.y, mj.z * rj.z, mj.w * rj.w);
+            reinterpret_cast<float4*>(x)[j] = xj;
+            reinterpret_cast<float4*>(r)[j] = rj;
+            reinterpret_cast<float4*>(z)[j] = zj;
+            dot.add(rj.x, zj.x);
+            dot.add(rj.y, zj.y);
+            dot.add(rj.z, zj.z);
+            dot.add(rj.w, zj.w);
+        }
+    }
+    for (long long j = s.lo + s.first; j < s.hi; j += s.stride) {
         x[j] += alpha * p[j];
         const float rj = r[j] - alpha * Ap[j];
         r[j] = rj;
         const float zj = minv[j] * rj;
         z[j] = zj;
-        dot += (double)rj * (double)zj;
+        dot.add(rj, zj);
     }
     double tot;
-    if (grid_sum_last<kVecBlock>(dot, c.partials, c.counter, &tot) && threadIdx.x == 0) {
-        Scalars* s = c.sc;
-        s->rz_new = tot;
-        s->beta = s->rz != 0.0 ? tot / s->rz : 0.0;
+    if (grid_sum_last<kVecBlock>(dot.value(), c.partials, c.counter, &tot) && threadIdx.x == 0) {
+        Scalars* sc = c.sc;
+        sc->rz_new = tot;
+        sc->beta = sc->rz != 0.0 ? tot / sc->rz : 0.0;
         if (iter < 64) {
-            s->alpha_hist[iter] = s->alpha;
-            s->beta_hist[iter] = s->beta;
+            sc->alpha_hist[iter] = sc->alpha;
+            sc->beta_hist[iter] = sc->beta;
         }
-        s->rz = tot;
-        if (!isfinite(tot)) s->numeric_error = 1u;
+        sc->rz = tot;
+        if (!isfinite(tot)) sc->numeric_error = 1u;
     }
 }
 
 // p = z + beta p (beta = r_{i+1}^T z_{i+1} / r_i^T z_i, 0 before the first
-// iteration so that p_0 = z_0).  float4 over the body, scalars for the tail.
+// iteration so that p_0 = z_0).
 __global__ void __launch_bounds__(kVecBlock) k_cg_direction(Ctx c, const float* z, float* p) {
     const float beta = (float)c.sc->beta;
-    const long long n4 = c.P / 4;
-    const long long stride = (long long)gridDim.x * blockDim.x;
+    const Span s = span(c.P, true);
     const float4* z4 = reinterpret_cast<const float4*>(z);
     float4* p4 = reinterpret_cast<float4*>(p);
-    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n4; j += stride) {
+    for (long long j = s.first; j < s.n4; j += s.stride) {
         const float4 a = z4[j];
         float4 b = p4[j];
         b.x = a.x + beta * b.x;
@@ -97,8 +155,7 @@ __global__ void __launch_bounds__(kVecBlock) k_cg_direction(Ctx c, const float* 
         b.w = a.w + beta * b.w;
         p4[j] = b;
     }
-    for (long long j = 4 * n4 + (long long)blockIdx.x * blockDim.x + threadIdx.x; j < c.P; j += stride)
-        p[j] = z[j] + beta * p[j];
+    for (long long j = s.lo + s.first; j < s.hi; j += s.stride) p[j] = z[j] + beta * p[j];
 }
 
 // max |x| over the SH degree-0 entries (the colour parameters of Sec. 4.5).
@@ -137,11 +194,15 @@ void launch_precond(const Ctx& c, const float* D, float* minv, cudaStream_t st) 
 }
 void launch_cg_init(const Ctx& c, const float* b, const float* minv, float* x, float* r, float* z, float* p,
                     cudaStream_t st) {
-    LMRS_LAUNCH(k_cg_init, vec_grid(c.P), kVecBlock, 0, st, c, b, minv, x, r, z, p);
+    const bool vec = aligned16(b) && aligned16(minv) && aligned16(x) && aligned16(r) && aligned16(z) && aligned16(p);
+    if (vec) LMRS_LAUNCH(k_cg_init<true>, vec_grid(c.P / 4 + 1), kVecBlock, 0, st, c, b, minv, x, r, z, p);
+    else LMRS_LAUNCH(k_cg_init<false>, vec_grid(c.P), kVecBlock, 0, st, c, b, minv, x, r, z, p);
 }
 void launch_cg_update(const Ctx& c, int iter, const float* p, const float* Ap, const float* minv, float* x, float* r,
                       float* z, cudaStream_t st) {
-    LMRS_LAUNCH(k_cg_update, vec_grid(c.P), kVecBlock, 0, st, c, iter, p, Ap, minv, x, r, z);
+    const bool vec = aligned16(p) && aligned16(Ap) && aligned16(minv) && aligned16(x) && aligned16(r) && aligned16(z);
+    if (vec) LMRS_LAUNCH(k_cg_update<true>, vec_grid(c.P / 4 + 1), kVecBlock, 0, st, c, iter, p, Ap, minv, x, r, z);
+    else LMRS_LAUNCH(k_cg_update<false>, vec_grid(c.P), kVecBlock, 0, st, c, iter, p, Ap, minv, x, r, z);
 }
 void launch_cg_direction(const Ctx& c, const float* z, float* p, cudaStream_t st) {
     LMRS_LAUNCH(k_cg_direction, vec_grid(c.P / 4 + 1), kVecBlock, 0, st, c, z, p);

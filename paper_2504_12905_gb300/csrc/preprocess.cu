@@ -681,7 +681,7 @@ constexpr int kPrepBlock = 128;
 template <int DEG, bool kDot>
 __global__ void __launch_bounds__(kPrepBlock) k_prep_vjp(Ctx c, float* out, const float* v, const float* D) {
     constexpr int K3 = 3 * Sh<DEG>::K;
-    double dot = 0.0;
+    Dot2 dot;
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < c.G; g += gridDim.x * blockDim.x) {
         float X[3], sh[K3];  // held in registers across the view loop
         load_mean(c.params, g, X);
@@ -708,7 +708,7 @@ __global__ void __launch_bounds__(kPrepBlock) k_prep_vjp(Ctx c, float* out, cons
             if (v) {
                 const float damp = c.damping_mode == 1 ? c.lambda * D[idx] : c.lambda;
                 val += damp * v[idx];
-                if (kDot) dot += (double)v[idx] * (double)val;
+                if (kDot) dot.add(v[idx], val);
             }
             out[idx] = val;
         };
@@ -724,7 +724,7 @@ __global__ void __launch_bounds__(kPrepBlock) k_prep_vjp(Ctx c, float* out, cons
     }
     if (kDot) {
         double tot;
-        if (grid_sum_last<kPrepBlock>(dot, c.partials, c.counter, &tot) && threadIdx.x == 0) {
+        if (grid_sum_last<kPrepBlock>(dot.value(), c.partials, c.counter, &tot) && threadIdx.x == 0) {
             Scalars* s = c.sc;
             s->pAp = tot;
             if (s->rz == 0.0) {
@@ -824,6 +824,8 @@ __global__ void __launch_bounds__(kPrepBlock) k_prep_diag(Ctx c, float* D) {
 #pragma unroll
     for (int k = 0; k < K3; ++k) D[11 * G + (long long)g * K3 + k] = dsh[k];
 }
+
+
 
 // ---------------------------------------------------------------------------
 // Launchers (dispatch on the SH degree)

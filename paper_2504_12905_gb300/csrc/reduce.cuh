@@ -19,6 +19,27 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
+// Compensated FP32 dot product, Dot2 of Ogita, Rump and Oishi ("Accurate Sum
+// and Dot Product", SIAM J. Sci. Comput. 26(6), 2005): TwoProduct through an
+// FMA and Knuth's TwoSum, so a thread's partial sum is as accurate as if it
+// were computed in twice the working precision.  FP64 arithmetic runs at a
+// small fraction of the FP32 rate on this GPU; per-thread partials are
+// formed this way and only the cross-thread combination is FP64.  Every
+// operation of the error-free transformations is rounded on its own.
+struct Dot2 {
+    float p = 0.f, s = 0.f;
+    __device__ __forceinline__ void add(float x, float y) {
+        const float h = __fmul_rn(x, y);
+        const float r = __fmaf_rn(x, y, -h);  // x * y = h + r exactly
+        const float t = __fadd_rn(p, h);
+        const float z = __fsub_rn(t, p);
+        const float q = __fadd_rn(__fsub_rn(p, __fsub_rn(t, z)), __fsub_rn(h, z));  // p + h = t + q exactly
+        p = t;
+        s += q + r;
+    }
+    __device__ __forceinline__ double value() const { return (double)p + (double)s; }
+};
+
 // Sum over the block, returned to every thread.
 template <int BLOCK>
 __device__ __forceinline__ double block_sum(double v) {
