@@ -214,6 +214,36 @@ lmrs_status lmrs_lm_step(lmrs_scene* scene, const int32_t* view_ids_host, int32_
                          int64_t lm_step, lmrs_step_stats* st);
 lmrs_status lmrs_get_solution(lmrs_scene* scene, float* x_dst);
 
+/* ---- Batches: many small fits stepping together ------------------------
+ * A batch groups scenes (same SH degree, same cg_iters <= 64) whose LM steps
+ * run together.  The paper steps one scene at a time; this is the batched
+ * form of Alg. 1.  Per LM step:
+ *   1. each scene's per-step setup (sampling, binning, render, J^T W r,
+ *      diag) runs on its own stream, n_threads scenes at a time on host
+ *      threads (give the scenes distinct streams for overlap);
+ *   2. the PCG iterations of all scenes run as one launch per phase
+ *      (direction, preprocess-JVP, fused raster, preprocess-VJP + p^T A p,
+ *      vector update) over segment tables, with per-scene FP64 scalars;
+ *      the whole loop is a CUDA graph captured at the first step and
+ *      replayed (re-captured when the tables outgrow their buffers);
+ *   3. the per-scene step sizes and updates run in two more launches.
+ * Each scene's result equals its own lmrs_lm_step up to the summation
+ * order of the inner products.  The scenes stay owned by the caller, must
+ * outlive the batch and must not be used by other calls during a step.
+ * cuda_stream: stream of the batched launches; NULL makes the batch create
+ * its own (graph capture needs a non-legacy stream). */
+typedef struct lmrs_batch lmrs_batch;
+lmrs_status lmrs_batch_create(lmrs_scene* const* scenes, int32_t n_scenes, int32_t n_threads, void* cuda_stream,
+                              lmrs_batch** out);
+lmrs_status lmrs_batch_destroy(lmrs_batch* batch);
+/* One LM step of every scene.  view_ids: the views of scene 0, then of
+ * scene 1, ... (camera indices of each scene, host); n_views[i], lm_steps[i]
+ * per scene (host).  stats: n_scenes entries or NULL (then nothing
+ * synchronises).  Scene errors are returned as the first failing status. */
+lmrs_status lmrs_batch_lm_step(lmrs_batch* batch, const int32_t* view_ids, const int32_t* n_views,
+                               const int64_t* lm_steps, lmrs_step_stats* stats);
+const char* lmrs_batch_last_error(const lmrs_batch* batch);
+
 /* Introspection (host memory; synchronising).  Sample layout: off[S] is the
  * offset of each sample inside the valid part of its tile (row-major over
  * min(tile_w, remaining width) columns), tile_off[n_views*T + 1] the prefix

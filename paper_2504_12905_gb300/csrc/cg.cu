@@ -189,6 +189,126 @@ __global__ void __launch_bounds__(kVecBlock) k_lm_update(Ctx c, long long lm_ste
         params[j] -= e * x[j];
 }
 
+// ---------------------------------------------------------------------------
+// Batched CG: every scene of a batch in one launch per phase.  Chunks never
+// cross a scene; the per-scene scalars of iteration i are
+//   rz[i] = r_i^T z_i (accumulated by init / the previous update),
+//   pAp[i] = p_i^T A p_i (accumulated by kb_prep_vjp),
+// so alpha_i = rz[i] / pAp[i] and beta_i = rz[i+1] / rz[i] are formed where
+// they are used.  The history arrays start at zero.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBatchBlock) kb_precond_init(BatchTables t) {
+    const int n = t.counts[2];
+    for (int k = blockIdx.x; k < n; k += gridDim.x) {
+        const int4 ch = t.vchunks[k];
+        const Ctx& c = t.ctxs[ch.x];
+        const BatchVec& bv = t.vecs[ch.x];
+        if (ch.y == 0 && threadIdx.x == 0) {
+            c.sc->max_dc_bits = 0u;
+            c.sc->numeric_error = 0u;
+        }
+        const int mode = c.damping_mode;
+        const float lam = c.lambda;
+        Dot2 dot;
+        for (long long j = ch.y + threadIdx.x; j < ch.z; j += kBatchBlock) {
+            const float d = mode == 1 ? (1.f + lam) * bv.D[j] : bv.D[j] + lam;
+            const float m = d > 0.f ? 1.f / d : 0.f;
+            const float bj = bv.b[j];
+            const float zj = m * bj;
+            bv.minv[j] = m;
+            bv.x[j] = 0.f;
+            bv.r[j] = bj;
+            bv.z[j] = zj;
+            bv.p[j] = 0.f;
+            dot.add(bj, zj);
+        }
+        const double tot = block_sum<kBatchBlock>(dot.value());
+        if (threadIdx.x == 0) atomicAdd(&bv.rz[0], tot);
+    }
+}
+
+__global__ void __launch_bounds__(kBatchBlock) kb_direction(BatchTables t, int iter) {
+    const int n = t.counts[2];
+    for (int k = blockIdx.x; k < n; k += gridDim.x) {
+        const int4 ch = t.vchunks[k];
+        const BatchVec& bv = t.vecs[ch.x];
+        const double prev = iter > 0 ? bv.rz[iter - 1] : 0.0;
+        const float beta = prev != 0.0 ? (float)(bv.rz[iter] / prev) : 0.f;
+        for (long long j = ch.y + threadIdx.x; j < ch.z; j += kBatchBlock) bv.p[j] = bv.z[j] + beta * bv.p[j];
+    }
+}
+
+__global__ void __launch_bounds__(kBatchBlock) kb_update(BatchTables t, int iter) {
+    const int n = t.counts[2];
+    for (int k = blockIdx.x; k < n; k += gridDim.x) {
+        const int4 ch = t.vchunks[k];
+        const Ctx& c = t.ctxs[ch.x];
+        const BatchVec& bv = t.vecs[ch.x];
+        const double rz = bv.rz[iter], pap = bv.pAp[iter];
+        float alpha = 0.f;
+        if (rz != 0.0) {
+            if (pap > 0.0 && isfinite(pap)) alpha = (float)(rz / pap);
+            else if (threadIdx.x == 0) c.sc->numeric_error = 1u;
+        }
+        Dot2 dot;
+        for (long long j = ch.y + threadIdx.x; j < ch.z; j += kBatchBlock) {
+            bv.x[j] += alpha * bv.p[j];
+            const float rj = bv.r[j] - alpha * bv.Ap[j];
+            bv.r[j] = rj;
+            const float zj = bv.minv[j] * rj;
+            bv.z[j] = zj;
+            dot.add(rj, zj);
+        }
+        const double tot = block_sum<kBatchBlock>(dot.value());
+        if (threadIdx.x == 0) atomicAdd(&bv.rz[iter + 1], tot);
+    }
+}
+
+__global__ void __launch_bounds__(kBatchBlock) kb_max_dc(BatchTables t) {
+    const int n = t.counts[0];
+    for (int k = blockIdx.x; k < n; k += gridDim.x) {
+        const int4 ch = t.gchunks[k];
+        const Ctx& c = t.ctxs[ch.x];
+        const int g = ch.y + threadIdx.x;
+        float m = 0.f;
+        if (g < ch.z) {
+            const float* e = t.vecs[ch.x].x + 11ll * c.G + (long long)g * c.K * 3;
+            m = fmaxf(fabsf(e[0]), fmaxf(fabsf(e[1]), fabsf(e[2])));
+        }
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, o));
+        if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(&c.sc->max_dc_bits, __float_as_uint(m));
+    }
+}
+
+__global__ void __launch_bounds__(kBatchBlock) kb_lm_update(BatchTables t) {
+    const int n = t.counts[2];
+    for (int k = blockIdx.x; k < n; k += gridDim.x) {
+        const int4 ch = t.vchunks[k];
+        const Ctx& c = t.ctxs[ch.x];
+        const BatchVec& bv = t.vecs[ch.x];
+        const double eta = step_size(bv.lm_step, bv.lr_warm, bv.lr_cap, bv.color_bound, bv.warm_iters,
+                                     c.sc->max_dc_bits);
+        if (ch.y == 0 && threadIdx.x == 0) c.sc->eta = eta;
+        const float e = (float)eta;
+        for (long long j = ch.y + threadIdx.x; j < ch.z; j += kBatchBlock) bv.params[j] -= e * bv.x[j];
+    }
+}
+
+void launch_b_precond_init(const BatchTables& t, int grid, cudaStream_t st) {
+    LMRS_LAUNCH(kb_precond_init, grid, kBatchBlock, 0, st, t);
+}
+void launch_b_direction(const BatchTables& t, int iter, int grid, cudaStream_t st) {
+    LMRS_LAUNCH(kb_direction, grid, kBatchBlock, 0, st, t, iter);
+}
+void launch_b_update(const BatchTables& t, int iter, int grid, cudaStream_t st) {
+    LMRS_LAUNCH(kb_update, grid, kBatchBlock, 0, st, t, iter);
+}
+void launch_b_lm_update(const BatchTables& t, int, int grid, cudaStream_t st) {
+    LMRS_LAUNCH(kb_max_dc, grid, kBatchBlock, 0, st, t);
+    LMRS_LAUNCH(kb_lm_update, grid, kBatchBlock, 0, st, t);
+}
+
 void launch_precond(const Ctx& c, const float* D, float* minv, cudaStream_t st) {
     LMRS_LAUNCH(k_precond, vec_grid(c.P), kVecBlock, 0, st, c, D, minv);
 }

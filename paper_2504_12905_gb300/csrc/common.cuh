@@ -105,6 +105,35 @@ struct Ctx {
     unsigned int* counter;
 };
 
+// ---- batches of scenes ----------------------------------------------------
+constexpr int kMaxBatchIters = 64;  // CG iterations a batch step can run
+constexpr int kBatchBlock = 128;    // block size of the batched kernels
+constexpr int kVecChunk = 2048;     // vector entries per chunk
+
+// Per-scene vectors, solver history and step-size settings of a batch.
+struct BatchVec {
+    float *b, *x, *r, *z, *p, *Ap, *minv, *D, *params;
+    double* rz;   // [kMaxBatchIters + 1]: r_i^T z_i
+    double* pAp;  // [kMaxBatchIters]: p_i^T A p_i
+    long long P;
+    long long lm_step;
+    double lr_warm, lr_cap, color_bound;
+    int warm_iters;
+};
+
+// Segment tables of a batch: chunks (scene, begin, end) that never cross a
+// scene, one chunk per block iteration; counts live in device memory so a
+// captured graph replays with new contents.
+struct BatchTables {
+    const Ctx* ctxs;
+    const BatchVec* vecs;
+    const int4* gchunks;  // Gaussians, <= kBatchBlock per chunk
+    const int4* pchunks;  // (Gaussian, view) pairs, Gaussian-major, <= kBatchBlock
+    const int4* vchunks;  // P-vector entries, <= kVecChunk
+    const int4* wchunks;  // raster work items, <= kBatchBlock / 32
+    const int* counts;    // [4]: number of g, p, v, w chunks
+};
+
 // ---- launch count (every kernel launch goes through note_launch) --------
 void note_launch();
 
@@ -172,6 +201,16 @@ void launch_max_dc(const Ctx& c, const float* x, cudaStream_t st);
 void launch_lm_update(const Ctx& c, long long lm_step, double lr_warm, double lr_cap, double color_bound,
                       int warm_iters, const float* x, float* params, cudaStream_t st);
 void launch_zero_scalars(const Ctx& c, cudaStream_t st);
+
+// ---- batched CG (all scenes of a batch in one launch per phase) ----------
+// grid: blocks of a batched launch (grid-stride over the chunks)
+void launch_b_precond_init(const BatchTables& t, int grid, cudaStream_t st);
+void launch_b_direction(const BatchTables& t, int iter, int grid, cudaStream_t st);
+void launch_b_prep_jvp(const BatchTables& t, int deg, int grid, cudaStream_t st);
+void launch_b_jtj(const BatchTables& t, int grid, cudaStream_t st);
+void launch_b_prep_vjp(const BatchTables& t, int deg, int iter, int grid, cudaStream_t st);
+void launch_b_update(const BatchTables& t, int iter, int grid, cudaStream_t st);
+void launch_b_lm_update(const BatchTables& t, int iters, int grid, cudaStream_t st);
 
 }  // namespace lmrs
 

@@ -648,9 +648,7 @@ __device__ __forceinline__ void load_geo_tangent(const float* v, int G, int g, G
 // once per warp through L1).  Writes the tangent half of the pair record and
 // clears the pair's cotangent slot.
 template <int DEG>
-__global__ void k_prep_jvp(Ctx c, const float* v) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long long)c.nv * c.G) return;
+__device__ __forceinline__ void prep_jvp_pair(const Ctx& c, const float* v, long long i) {
     const int g = (int)(i / c.nv), slot = (int)(i - (long long)g * c.nv);
     const long long pair = (long long)slot * c.G + g;
     const int4 rc = c.rect[pair];
@@ -676,13 +674,32 @@ __global__ void k_prep_jvp(Ctx c, const float* v) {
     ct[0] = ct[1] = ct[2] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
+template <int DEG>
+__global__ void k_prep_jvp(Ctx c, const float* v) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < (long long)c.nv * c.G) prep_jvp_pair<DEG>(c, v, i);
+}
+
+// The same for every scene of a batch: chunks of pairs, tangent = the scene's p.
+template <int DEG>
+__global__ void __launch_bounds__(kBatchBlock) kb_prep_jvp(BatchTables t) {
+    const int n = t.counts[1];
+    for (int k = blockIdx.x; k < n; k += gridDim.x) {
+        const int4 ch = t.pchunks[k];
+        const long long i = (long long)ch.y + threadIdx.x;
+        if (i < ch.z) prep_jvp_pair<DEG>(t.ctxs[ch.x], t.vecs[ch.x].p, i);
+    }
+}
+
 constexpr int kPrepBlock = 128;
 
+// J^T of Gaussian g's cotangent slots over its visible views, written to out
+// (+ lambda damping of v when v is given; v^T out accumulated into dot).
 template <int DEG, bool kDot>
-__global__ void __launch_bounds__(kPrepBlock) k_prep_vjp(Ctx c, float* out, const float* v, const float* D) {
+__device__ __forceinline__ void prep_vjp_gauss(const Ctx& c, int g, float* out, const float* v, const float* D,
+                                               Dot2& dot) {
     constexpr int K3 = 3 * Sh<DEG>::K;
-    Dot2 dot;
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < c.G; g += gridDim.x * blockDim.x) {
+    {
         float X[3], sh[K3];  // held in registers across the view loop
         load_mean(c.params, g, X);
         load_sh<DEG>(c.params, c.G, g, sh);
@@ -722,6 +739,13 @@ __global__ void __launch_bounds__(kPrepBlock) k_prep_vjp(Ctx c, float* out, cons
 #pragma unroll
         for (int k = 0; k < K3; ++k) put(11 * G + (long long)g * K3 + k, gsh[k]);
     }
+}
+
+template <int DEG, bool kDot>
+__global__ void __launch_bounds__(kPrepBlock) k_prep_vjp(Ctx c, float* out, const float* v, const float* D) {
+    Dot2 dot;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < c.G; g += gridDim.x * blockDim.x)
+        prep_vjp_gauss<DEG, kDot>(c, g, out, v, D, dot);
     if (kDot) {
         double tot;
         if (grid_sum_last<kPrepBlock>(dot.value(), c.partials, c.counter, &tot) && threadIdx.x == 0) {
@@ -736,6 +760,24 @@ __global__ void __launch_bounds__(kPrepBlock) k_prep_vjp(Ctx c, float* out, cons
                 s->alpha = s->rz / tot;
             }
         }
+    }
+}
+
+// The same for every scene of a batch: Ap = J^T W J p + damping, and
+// p^T A p of iteration `iter` accumulated into the scene's history (the
+// per-thread Dot2 partials of one chunk are summed in FP64 over the block).
+template <int DEG>
+__global__ void __launch_bounds__(kBatchBlock) kb_prep_vjp(BatchTables t, int iter) {
+    const int n = t.counts[0];
+    for (int k = blockIdx.x; k < n; k += gridDim.x) {
+        const int4 ch = t.gchunks[k];
+        const Ctx& c = t.ctxs[ch.x];
+        const BatchVec& bv = t.vecs[ch.x];
+        Dot2 dot;
+        const int g = ch.y + threadIdx.x;
+        if (g < ch.z) prep_vjp_gauss<DEG, true>(c, g, bv.Ap, bv.p, bv.D, dot);
+        const double tot = block_sum<kBatchBlock>(dot.value());
+        if (threadIdx.x == 0) atomicAdd(&bv.pAp[iter], tot);
     }
 }
 
@@ -888,6 +930,24 @@ void launch_prep_vjp(const Ctx& c, float* g, const float* v, const float* D, boo
         case 1: prep_vjp_deg<1>(c, g, v, D, dot, st); break;
         case 2: prep_vjp_deg<2>(c, g, v, D, dot, st); break;
         default: prep_vjp_deg<3>(c, g, v, D, dot, st); break;
+    }
+}
+
+void launch_b_prep_jvp(const BatchTables& t, int deg, int grid, cudaStream_t st) {
+    switch (deg) {
+        case 0: LMRS_LAUNCH(kb_prep_jvp<0>, grid, kBatchBlock, 0, st, t); break;
+        case 1: LMRS_LAUNCH(kb_prep_jvp<1>, grid, kBatchBlock, 0, st, t); break;
+        case 2: LMRS_LAUNCH(kb_prep_jvp<2>, grid, kBatchBlock, 0, st, t); break;
+        default: LMRS_LAUNCH(kb_prep_jvp<3>, grid, kBatchBlock, 0, st, t); break;
+    }
+}
+
+void launch_b_prep_vjp(const BatchTables& t, int deg, int iter, int grid, cudaStream_t st) {
+    switch (deg) {
+        case 0: LMRS_LAUNCH(kb_prep_vjp<0>, grid, kBatchBlock, 0, st, t, iter); break;
+        case 1: LMRS_LAUNCH(kb_prep_vjp<1>, grid, kBatchBlock, 0, st, t, iter); break;
+        case 2: LMRS_LAUNCH(kb_prep_vjp<2>, grid, kBatchBlock, 0, st, t, iter); break;
+        default: LMRS_LAUNCH(kb_prep_vjp<3>, grid, kBatchBlock, 0, st, t, iter); break;
     }
 }
 

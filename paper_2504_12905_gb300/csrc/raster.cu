@@ -347,14 +347,43 @@ __global__ void __launch_bounds__(kRasterBlock) k_vjp(Ctx c, const float* u) {
     backward_pass(c, p, compact_list(c, p), s_rec, s_id, ub, Cf, ncons);
 }
 
-__global__ void __launch_bounds__(kRasterBlock) k_jtj(Ctx c) {
-    LMRS_RASTER_PROLOGUE
+__device__ __forceinline__ void jtj_item(const Ctx& c, int item, float4 (*s_rec)[kRecF4], unsigned* s_id) {
+    Pix p;
+    setup_item(c, item, p);
     const List L = compact_list(c, p);
     float C[3], T, dC[3];
     int ncons;
     forward_pass<true, false>(c, p, L, s_rec, s_id, C, T, dC, ncons);
     const float ub[3] = {p.w * dC[0], p.w * dC[1], p.w * dC[2]};
     backward_pass(c, p, L, s_rec, s_id, ub, C, ncons);
+}
+
+__global__ void __launch_bounds__(kRasterBlock) k_jtj(Ctx c) {
+    __shared__ float4 s_rec_all[kRasterWarps][32][kRecF4];
+    __shared__ unsigned s_id_all[kRasterWarps][32];
+    const int wid = threadIdx.x >> 5;
+    const int item = blockIdx.x * kRasterWarps + wid;
+    if (item < c.nwork) jtj_item(c, item, s_rec_all[wid], s_id_all[wid]);
+}
+
+// The same for every scene of a batch: chunks of at most kRasterWarps work
+// items of one scene, one item per warp.
+__global__ void __launch_bounds__(kRasterBlock) kb_jtj(BatchTables t) {
+    static_assert(kRasterBlock == kBatchBlock, "one warp per work item of a chunk");
+    __shared__ float4 s_rec_all[kRasterWarps][32][kRecF4];
+    __shared__ unsigned s_id_all[kRasterWarps][32];
+    const int wid = threadIdx.x >> 5;
+    const int n = t.counts[3];
+    for (int k = blockIdx.x; k < n; k += gridDim.x) {
+        const int4 ch = t.wchunks[k];
+        const int item = ch.y + wid;
+        if (item < ch.z) jtj_item(t.ctxs[ch.x], item, s_rec_all[wid], s_id_all[wid]);
+        __syncwarp();
+    }
+}
+
+void launch_b_jtj(const BatchTables& t, int grid, cudaStream_t st) {
+    LMRS_LAUNCH(kb_jtj, grid, kRasterBlock, 0, st, t);
 }
 
 // Gram blocks: per contributing (sample, Gaussian), with e = d alpha /

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -799,5 +800,300 @@ const char* lmrs_status_str(lmrs_status st) {
 const char* lmrs_last_error(const lmrs_scene* s) { return s ? s->err.c_str() : "null scene"; }
 
 int64_t lmrs_launch_count(void) { return lmrs::g_launches.load(std::memory_order_relaxed); }
+
+}  // extern "C"
+
+// ===========================================================================
+// Batches
+// ===========================================================================
+struct lmrs_batch {
+    std::vector<lmrs_scene*> scenes;
+    int n = 0, deg = 0, iters = 0, nthreads = 1;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    std::string err;
+    // device tables
+    DevBuf ctxs, vecs, gch, pch, vch, wch, counts, hist;
+    // host copies (kept alive while the asynchronous uploads are staged)
+    std::vector<Ctx> hctx;
+    std::vector<BatchVec> hvec;
+    std::vector<int4> hg, hp, hv, hw;
+    int hcounts[4] = {0, 0, 0, 0};
+    // the captured CG loop
+    cudaGraphExec_t exec = nullptr;
+    long long graph_kernels = 0;
+    void* graph_key[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    std::vector<cudaEvent_t> ev_scene;
+    cudaEvent_t ev_batch = nullptr;
+};
+
+namespace {
+
+constexpr int kBatchGrid = 1216;  // blocks of the batched launches (8 per SM), grid-stride over chunks
+
+lmrs_status bfail(lmrs_batch* b, lmrs_status code, const std::string& msg) {
+    if (b) b->err = msg;
+    return code;
+}
+
+void add_chunks(std::vector<int4>& out, int scene, long long n, int step) {
+    for (long long b0 = 0; b0 < n; b0 += step) out.push_back(make_int4(scene, (int)b0, (int)std::min(n, b0 + step), 0));
+}
+
+// Per-step setup of scene i: everything of its LM step before the PCG loop.
+lmrs_status scene_setup(lmrs_scene* s, const int32_t* views, int nv, long long step) {
+    TRY(lmrs_preprocess(s, views, nv, step));
+    TRY(lmrs_render(s, nullptr, nullptr));
+    TRY(lmrs_rhs(s, s->b.as<float>()));
+    TimerScope ts_(s);
+    TRY(do_jtj_diag(s));
+    return LMRS_OK;
+}
+
+lmrs_status batch_tables(lmrs_batch* B, const int64_t* steps) {
+    B->hctx.resize(B->n);
+    B->hvec.resize(B->n);
+    B->hg.clear();
+    B->hp.clear();
+    B->hv.clear();
+    B->hw.clear();
+    double* hist = B->hist.as<double>();
+    for (int i = 0; i < B->n; ++i) {
+        lmrs_scene* s = B->scenes[i];
+        if (s->P >= (1ll << 31)) return bfail(B, LMRS_ERR_BUDGET, "scene too large for a batch");
+        B->hctx[i] = s->ctx();
+        BatchVec& v = B->hvec[i];
+        v.b = s->b.as<float>();
+        v.x = s->x.as<float>();
+        v.r = s->r.as<float>();
+        v.z = s->z.as<float>();
+        v.p = s->p.as<float>();
+        v.Ap = s->Ap.as<float>();
+        v.minv = s->minv.as<float>();
+        v.D = s->D.as<float>();
+        v.params = s->params.as<float>();
+        v.rz = hist + (size_t)i * 2 * (kMaxBatchIters + 1);
+        v.pAp = v.rz + kMaxBatchIters + 1;
+        v.P = s->P;
+        v.lm_step = steps[i];
+        v.lr_warm = s->cfg.lr_warm;
+        v.lr_cap = s->cfg.lr_cap;
+        v.color_bound = s->cfg.color_bound;
+        v.warm_iters = s->cfg.warm_iters;
+        add_chunks(B->hg, i, s->G, kBatchBlock);
+        add_chunks(B->hp, i, (long long)s->nv * s->G, kBatchBlock);
+        add_chunks(B->hv, i, s->P, kVecChunk);
+        add_chunks(B->hw, i, s->nwork, kBatchBlock / kWarp);
+    }
+    B->hcounts[0] = (int)B->hg.size();
+    B->hcounts[1] = (int)B->hp.size();
+    B->hcounts[2] = (int)B->hv.size();
+    B->hcounts[3] = (int)B->hw.size();
+    TRY(ensure(nullptr, B->gch, sizeof(int4) * B->hg.size()));
+    TRY(ensure(nullptr, B->pch, sizeof(int4) * B->hp.size()));
+    TRY(ensure(nullptr, B->vch, sizeof(int4) * B->hv.size()));
+    TRY(ensure(nullptr, B->wch, sizeof(int4) * std::max<size_t>(B->hw.size(), 1)));
+    auto up = [&](DevBuf& d, const void* h, size_t bytes) {
+        return bytes ? cudaMemcpyAsync(d.p, h, bytes, cudaMemcpyHostToDevice, B->st) : cudaSuccess;
+    };
+    cudaError_t e = up(B->ctxs, B->hctx.data(), sizeof(Ctx) * B->n);
+    if (e == cudaSuccess) e = up(B->vecs, B->hvec.data(), sizeof(BatchVec) * B->n);
+    if (e == cudaSuccess) e = up(B->gch, B->hg.data(), sizeof(int4) * B->hg.size());
+    if (e == cudaSuccess) e = up(B->pch, B->hp.data(), sizeof(int4) * B->hp.size());
+    if (e == cudaSuccess) e = up(B->vch, B->hv.data(), sizeof(int4) * B->hv.size());
+    if (e == cudaSuccess) e = up(B->wch, B->hw.data(), sizeof(int4) * B->hw.size());
+    if (e == cudaSuccess) e = up(B->counts, B->hcounts, sizeof(B->hcounts));
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(B->hist.p, 0, sizeof(double) * (size_t)B->n * 2 * (kMaxBatchIters + 1), B->st);
+    if (e != cudaSuccess) return bfail(B, LMRS_ERR_CUDA, std::string("batch upload: ") + cudaGetErrorString(e));
+    return LMRS_OK;
+}
+
+BatchTables batch_view(const lmrs_batch* B) {
+    BatchTables t;
+    t.ctxs = B->ctxs.as<Ctx>();
+    t.vecs = B->vecs.as<BatchVec>();
+    t.gchunks = B->gch.as<int4>();
+    t.pchunks = B->pch.as<int4>();
+    t.vchunks = B->vch.as<int4>();
+    t.wchunks = B->wch.as<int4>();
+    t.counts = B->counts.as<int>();
+    return t;
+}
+
+// Capture the PCG loop and the updates of all scenes as one graph (again
+// whenever a table buffer moved).
+lmrs_status batch_graph(lmrs_batch* B) {
+    void* key[6] = {B->ctxs.p, B->vecs.p, B->gch.p, B->pch.p, B->vch.p, B->wch.p};
+    if (B->exec && std::equal(key, key + 6, B->graph_key)) return LMRS_OK;
+    if (B->exec) {
+        cudaGraphExecDestroy(B->exec);
+        B->exec = nullptr;
+    }
+    LaunchTimer* saved = t_active;
+    t_active = nullptr;  // no event records inside the captured graph
+    const long long before = lmrs_launch_count();
+    cudaError_t e = cudaStreamBeginCapture(B->st, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        const BatchTables t = batch_view(B);
+        launch_b_precond_init(t, kBatchGrid, B->st);
+        for (int it = 0; it < B->iters; ++it) {
+            launch_b_direction(t, it, kBatchGrid, B->st);
+            launch_b_prep_jvp(t, B->deg, kBatchGrid, B->st);
+            launch_b_jtj(t, kBatchGrid, B->st);
+            launch_b_prep_vjp(t, B->deg, it, kBatchGrid, B->st);
+            launch_b_update(t, it, kBatchGrid, B->st);
+        }
+        launch_b_lm_update(t, B->iters, kBatchGrid, B->st);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(B->st, &g);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&B->exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+    }
+    t_active = saved;
+    // captured launches run at every replay, not now
+    B->graph_kernels = lmrs_launch_count() - before;
+    g_launches.fetch_sub(B->graph_kernels, std::memory_order_relaxed);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        B->exec = nullptr;
+        return bfail(B, LMRS_ERR_CUDA, std::string("batch graph: ") + cudaGetErrorString(e));
+    }
+    std::copy(key, key + 6, B->graph_key);
+    return LMRS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lmrs_status lmrs_batch_create(lmrs_scene* const* scenes, int32_t n_scenes, int32_t n_threads, void* cuda_stream,
+                              lmrs_batch** out) {
+    if (!out) return LMRS_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!scenes || n_scenes <= 0) return LMRS_ERR_INVALID_ARG;
+    for (int i = 0; i < n_scenes; ++i) {
+        if (!scenes[i]) return LMRS_ERR_INVALID_ARG;
+        if (scenes[i]->deg != scenes[0]->deg || scenes[i]->cfg.cg_iters != scenes[0]->cfg.cg_iters)
+            return LMRS_ERR_INVALID_ARG;
+        for (int j = 0; j < i; ++j)
+            if (scenes[j] == scenes[i]) return LMRS_ERR_INVALID_ARG;
+    }
+    if (scenes[0]->cfg.cg_iters > kMaxBatchIters) return LMRS_ERR_BUDGET;
+    lmrs_batch* B = new lmrs_batch();
+    B->scenes.assign(scenes, scenes + n_scenes);
+    B->n = n_scenes;
+    B->deg = scenes[0]->deg;
+    B->iters = scenes[0]->cfg.cg_iters;
+    B->nthreads = std::max(1, std::min<int>(n_threads, n_scenes));
+    lmrs_status rc = LMRS_OK;
+    if (cuda_stream) {
+        B->st = static_cast<cudaStream_t>(cuda_stream);
+    } else if (cudaStreamCreateWithFlags(&B->st, cudaStreamNonBlocking) != cudaSuccess) {
+        rc = LMRS_ERR_CUDA;
+    } else {
+        B->own_stream = true;
+    }
+    if (rc == LMRS_OK) rc = ensure(nullptr, B->ctxs, sizeof(Ctx) * n_scenes);
+    if (rc == LMRS_OK) rc = ensure(nullptr, B->vecs, sizeof(BatchVec) * n_scenes);
+    if (rc == LMRS_OK) rc = ensure(nullptr, B->counts, sizeof(int) * 4);
+    if (rc == LMRS_OK) rc = ensure(nullptr, B->hist, sizeof(double) * n_scenes * 2 * (kMaxBatchIters + 1));
+    B->ev_scene.assign(n_scenes, nullptr);
+    for (int i = 0; rc == LMRS_OK && i < n_scenes; ++i)
+        if (cudaEventCreateWithFlags(&B->ev_scene[i], cudaEventDisableTiming) != cudaSuccess) rc = LMRS_ERR_CUDA;
+    if (rc == LMRS_OK && cudaEventCreateWithFlags(&B->ev_batch, cudaEventDisableTiming) != cudaSuccess)
+        rc = LMRS_ERR_CUDA;
+    if (rc != LMRS_OK) {
+        cudaGetLastError();
+        lmrs_batch_destroy(B);
+        return rc;
+    }
+    *out = B;
+    return LMRS_OK;
+}
+
+lmrs_status lmrs_batch_destroy(lmrs_batch* B) {
+    if (!B) return LMRS_ERR_INVALID_ARG;
+    if (B->st) cudaStreamSynchronize(B->st);
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    for (auto e : B->ev_scene)
+        if (e) cudaEventDestroy(e);
+    if (B->ev_batch) cudaEventDestroy(B->ev_batch);
+    for (DevBuf* d : {&B->ctxs, &B->vecs, &B->gch, &B->pch, &B->vch, &B->wch, &B->counts, &B->hist}) release(*d);
+    if (B->own_stream) cudaStreamDestroy(B->st);
+    delete B;
+    return LMRS_OK;
+}
+
+lmrs_status lmrs_batch_lm_step(lmrs_batch* B, const int32_t* view_ids, const int32_t* n_views, const int64_t* lm_steps,
+                               lmrs_step_stats* stats) {
+    if (!B) return LMRS_ERR_INVALID_ARG;
+    if (!view_ids || !n_views || !lm_steps) return bfail(B, LMRS_ERR_INVALID_ARG, "null argument");
+    std::vector<long long> voff(B->n + 1, 0);
+    for (int i = 0; i < B->n; ++i) {
+        if (n_views[i] <= 0) return bfail(B, LMRS_ERR_INVALID_ARG, "scene without views");
+        voff[i + 1] = voff[i] + n_views[i];
+    }
+    // 1. per-scene setup, n threads at a time, each scene on its own stream
+    std::vector<lmrs_status> rc(B->n, LMRS_OK);
+    auto work = [&](int w) {
+        for (int i = w; i < B->n; i += B->nthreads) {
+            lmrs_scene* s = B->scenes[i];
+            rc[i] = scene_setup(s, view_ids + voff[i], n_views[i], lm_steps[i]);
+            if (rc[i] == LMRS_OK && cudaEventRecord(B->ev_scene[i], s->st) != cudaSuccess) rc[i] = LMRS_ERR_CUDA;
+        }
+    };
+    if (B->nthreads == 1) {
+        work(0);
+    } else {
+        std::vector<std::thread> pool;
+        for (int w = 0; w < B->nthreads; ++w) pool.emplace_back(work, w);
+        for (auto& th : pool) th.join();
+    }
+    for (int i = 0; i < B->n; ++i)
+        if (rc[i] != LMRS_OK)
+            return bfail(B, rc[i], "scene " + std::to_string(i) + ": " + B->scenes[i]->err);
+    // 2. tables, then the batched PCG loop and updates (one graph)
+    for (int i = 0; i < B->n; ++i)
+        if (cudaStreamWaitEvent(B->st, B->ev_scene[i], 0) != cudaSuccess)
+            return bfail(B, LMRS_ERR_CUDA, "stream wait");
+    TRY(batch_tables(B, lm_steps));
+    TRY(batch_graph(B));
+    cudaError_t e = cudaGraphLaunch(B->exec, B->st);
+    if (e != cudaSuccess) return bfail(B, LMRS_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+    g_launches.fetch_add(B->graph_kernels, std::memory_order_relaxed);
+    // 3. the scenes' next work waits for the batch
+    if (cudaEventRecord(B->ev_batch, B->st) != cudaSuccess) return bfail(B, LMRS_ERR_CUDA, "event record");
+    for (lmrs_scene* s : B->scenes) {
+        if (cudaStreamWaitEvent(s->st, B->ev_batch, 0) != cudaSuccess) return bfail(B, LMRS_ERR_CUDA, "stream wait");
+        s->preprocessed = s->rendered = s->have_D = s->ordered = false;
+    }
+    if (!stats) return LMRS_OK;
+    if (cudaStreamSynchronize(B->st) != cudaSuccess) return bfail(B, LMRS_ERR_CUDA, "synchronise");
+    std::vector<double> hist((size_t)B->n * 2 * (kMaxBatchIters + 1));
+    if (cudaMemcpy(hist.data(), B->hist.p, sizeof(double) * hist.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return bfail(B, LMRS_ERR_CUDA, "read history");
+    lmrs_status out = LMRS_OK;
+    for (int i = 0; i < B->n; ++i) {
+        lmrs_scene* s = B->scenes[i];
+        Scalars h;
+        if (cudaMemcpy(&h, s->sc.p, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return bfail(B, LMRS_ERR_CUDA, "read scalars");
+        float m;
+        std::memcpy(&m, &h.max_dc_bits, sizeof(m));
+        const double* rz = hist.data() + (size_t)i * 2 * (kMaxBatchIters + 1);
+        stats[i].loss = h.loss_den > 0.0 ? h.loss_num / h.loss_den : 0.0;
+        stats[i].eta = h.eta;
+        stats[i].max_dc = m;
+        stats[i].rz0 = rz[0];
+        stats[i].rz_final = rz[B->iters];
+        stats[i].n_samples = s->S;
+        stats[i].n_pairs = s->npairs;
+        if (h.numeric_error && out == LMRS_OK) out = bfail(B, LMRS_ERR_NUMERIC, "scene " + std::to_string(i));
+    }
+    return out;
+}
+
+const char* lmrs_batch_last_error(const lmrs_batch* B) { return B ? B->err.c_str() : "null batch"; }
 
 }  // extern "C"

@@ -84,6 +84,10 @@ _SIGS = {
     "lmrs_get_tile_lists": (_S, [_P, _P, _P]),
     "lmrs_set_timing": (_S, [_P, C.c_int32]),
     "lmrs_get_timing": (_S, [_P, C.POINTER(KernelTime), C.c_int32, C.POINTER(C.c_int32)]),
+    "lmrs_batch_create": (_S, [_P, C.c_int32, C.c_int32, _P, C.POINTER(_P)]),
+    "lmrs_batch_destroy": (_S, [_P]),
+    "lmrs_batch_lm_step": (_S, [_P, _P, _P, _P, _P]),
+    "lmrs_batch_last_error": (C.c_char_p, [_P]),
     "lmrs_synchronize": (_S, [_P]),
     "lmrs_status_str": (C.c_char_p, [_S]),
     "lmrs_last_error": (C.c_char_p, [_P]),
@@ -283,6 +287,39 @@ def lmrs_get_timing(scene):
     n = C.c_int32()
     _check(lib().lmrs_get_timing(scene, buf, 128, C.byref(n)), scene)
     return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(min(n.value, 128))}
+
+
+def lmrs_batch_create(scenes, n_threads=8, stream=None):
+    """scenes: scene handles (ints).  Returns the batch handle."""
+    arr = (_P * len(scenes))(*scenes)
+    h = _P()
+    _check(lib().lmrs_batch_create(arr, len(scenes), int(n_threads), _ptr(stream) if stream is not None else None,
+                                   C.byref(h)))
+    return h.value
+
+
+def lmrs_batch_destroy(batch):
+    _check(lib().lmrs_batch_destroy(batch))
+
+
+def lmrs_batch_last_error(batch):
+    m = lib().lmrs_batch_last_error(batch)
+    return m.decode() if m else ""
+
+
+def lmrs_batch_lm_step(batch, views, lm_steps, stats=True):
+    """views: one sequence of camera indices per scene; lm_steps: one step
+    index per scene.  Returns the per-scene StepStats (or None)."""
+    n = len(views)
+    flat = np.ascontiguousarray(np.concatenate([np.asarray(v, np.int32) for v in views]), np.int32)
+    nv = np.ascontiguousarray([len(v) for v in views], np.int32)
+    steps = np.ascontiguousarray(lm_steps, np.int64)
+    st = (StepStats * n)() if stats else None
+    status = lib().lmrs_batch_lm_step(batch, flat.ctypes.data, nv.ctypes.data, steps.ctypes.data,
+                                      C.cast(st, _P) if st is not None else None)
+    if status != LMRS_OK:
+        raise LmrsError(status, lmrs_batch_last_error(batch))
+    return list(st) if st is not None else None
 
 
 def lmrs_synchronize(scene):

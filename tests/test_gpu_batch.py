@@ -1,0 +1,98 @@
+"""Batched LM steps (all scenes' PCG iterations in one launch per phase,
+replayed as a CUDA graph) against solo LM steps of the same scenes and
+against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2504_12905_gb300 import synthetic as syn
+
+from helpers import normwise_rel
+
+pytestmark = pytest.mark.gpu
+
+
+def _scenes(n=5, seed=23):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        G = int(rng.integers(300, 2500))
+        nv = int(rng.integers(2, 6))
+        size = int(rng.choice([48, 64, 80]))
+        sub = np.random.default_rng([seed, i])
+        params = syn.draw_gaussians(sub, G, 0, means=syn.blob_means(sub, G, n_blobs=4))
+        cams = syn.hemisphere_cameras(nv, 3.0, size, size)
+        tgt = syn.noise_targets(sub, nv, size, size)
+        out.append((syn.Scene(G, 0, params, cams, i), tgt))
+    return out
+
+
+def _make(torch, lmrs, sc, tgt, stream):
+    t = torch.from_numpy(tgt).cuda()
+    s = lmrs.Scene(torch.from_numpy(sc.params).cuda(), sc.cams, sc.n_gauss, 0, targets=t, stream=stream,
+                   samples_per_tile=32, lambda_=0.1, damping_mode=0, cg_iters=8, seed=0x5EED)
+    s._t = t
+    return s
+
+
+def test_batch_matches_solo_steps_and_oracle():
+    import torch
+
+    from paper_2504_12905_gb300 import lmrs
+
+    scenes = _scenes()
+    streams = [torch.cuda.Stream() for _ in scenes]
+    batch_sc = [_make(torch, lmrs, sc, tgt, streams[i].cuda_stream) for i, (sc, tgt) in enumerate(scenes)]
+    solo_sc = [_make(torch, lmrs, sc, tgt, None) for sc, tgt in scenes]
+    b = lmrs.lmrs_batch_create([s.h for s in batch_sc], n_threads=3)
+    views = [list(range(len(sc.cams))) for sc, _ in scenes]
+    for step in (10, 11):  # two steps: the second replays the captured graph
+        st_b = lmrs.lmrs_batch_lm_step(b, views, [step] * len(scenes))
+        for i, s in enumerate(solo_sc):
+            st = lmrs.lmrs_lm_step(s.h, views[i], step)
+            xs = np.zeros(s.n_params, np.float32)
+            xb = np.zeros(s.n_params, np.float32)
+            lmrs.lmrs_get_solution(s.h, xs)
+            lmrs.lmrs_get_solution(batch_sc[i].h, xb)
+            assert normwise_rel(xb, xs) <= 1e-3, (step, i)
+            assert st_b[i].eta == pytest.approx(st.eta, rel=1e-4)
+            assert st_b[i].loss == pytest.approx(st.loss, rel=1e-6)
+            assert st_b[i].rz0 == pytest.approx(st.rz0, rel=1e-5)
+            pb = np.zeros(s.n_params, np.float32)
+            ps = np.zeros(s.n_params, np.float32)
+            lmrs.lmrs_get_params(batch_sc[i].h, pb)
+            lmrs.lmrs_get_params(s.h, ps)
+            assert normwise_rel(pb - scenes[i][0].params, ps - scenes[i][0].params) <= 1e-3
+    # the first batch step of scene 0 against the FP64 oracle (A-norm, as for solo steps)
+    sc, tgt = scenes[0]
+    fresh = _make(torch, lmrs, sc, tgt, streams[0].cuda_stream)
+    b1 = lmrs.lmrs_batch_create([fresh.h], n_threads=1)
+    lmrs.lmrs_batch_lm_step(b1, [views[0]], [10])
+    x = np.zeros(fresh.n_params, np.float32)
+    lmrs.lmrs_get_solution(fresh.h, x)
+    o = oracle.OracleScene(sc.params, sc.cams, sc.n_gauss, 0, targets=tgt, samples_per_tile=32, lambda_=0.1,
+                           damping_mode=0, cg_iters=8, seed=0x5EED)
+    o.begin_step(views[0], 10)
+    D = o.diag()
+    x_ref, _ = o.lm_step(views[0], 10)
+    o.set_params(sc.params.astype(np.float64))
+    o.begin_step(views[0], 10)
+    e = x.astype(np.float64) - x_ref
+    a_norm = np.sqrt(max(e @ o.apply(e, D), 0.0)) / np.sqrt(x_ref @ o.apply(x_ref, D))
+    assert a_norm <= 1e-3
+    lmrs.lmrs_batch_destroy(b1)
+    lmrs.lmrs_batch_destroy(b)
+
+
+def test_batch_rejects_mixed_configs():
+    import torch
+
+    from paper_2504_12905_gb300 import lmrs
+
+    (sc, tgt), = _scenes(1)
+    a = _make(torch, lmrs, sc, tgt, None)
+    b = lmrs.Scene(torch.from_numpy(sc.params).cuda(), sc.cams, sc.n_gauss, 0, cg_iters=5)
+    with pytest.raises(lmrs.LmrsError):
+        lmrs.lmrs_batch_create([a.h, b.h])
+    with pytest.raises(lmrs.LmrsError):
+        lmrs.lmrs_batch_create([a.h, a.h])
