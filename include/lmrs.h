@@ -244,6 +244,28 @@ lmrs_status lmrs_batch_lm_step(lmrs_batch* batch, const int32_t* view_ids, const
                                const int64_t* lm_steps, lmrs_step_stats* stats);
 const char* lmrs_batch_last_error(const lmrs_batch* batch);
 
+/* Tile-shape autotuner.  The tile shape groups pixels for the per-tile
+ * residual sampling (Sec. 4.4) and for the tile lists of every raster pass;
+ * the fastest shape depends on the scene.  For each candidate shape
+ * (shapes[2i], shapes[2i+1]) = (tile_w, tile_h), tile_w * tile_h <= 256,
+ * the tuner builds a private copy of the scene with that shape (cfg
+ * otherwise unchanged, except that a fixed samples_per_tile is scaled by
+ * the tile area so the sampled fraction stays the same) and times `reps`
+ * full LM steps (after one untimed step), each from params_dev, with CUDA
+ * events on cuda_stream (NULL: a private stream).  The candidates are
+ * different but equally valid samplings of the same objective.
+ *   params_dev / targets_dev: as lmrs_scene_create (device, borrowed);
+ *   view_ids_host[n_views]: the views of each timed step;
+ *   best: index of the shape with the lowest median step time;
+ *   ms_per_step[n_shapes]: the medians, or NULL.
+ * Returns LMRS_ERR_INVALID_ARG for a bad shape or argument (best = -1);
+ * scene-creation and step errors are passed through. */
+lmrs_status lmrs_autotune_tile(const lmrs_config* cfg, int64_t n_gauss, const float* params_dev,
+                               const lmrs_camera* cams_host, int32_t n_cams, const float* targets_dev,
+                               const int32_t* view_ids_host, int32_t n_views, const int32_t* shapes,
+                               int32_t n_shapes, int32_t reps, void* cuda_stream, int32_t* best,
+                               float* ms_per_step);
+
 /* Introspection (host memory; synchronising).  Sample layout: off[S] is the
  * offset of each sample inside the valid part of its tile (row-major over
  * min(tile_w, remaining width) columns), tile_off[n_views*T + 1] the prefix

@@ -3,7 +3,9 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -184,29 +186,87 @@ struct TimerScope {
     ~TimerScope() { t_active = prev; }
 };
 
-lmrs_status ensure(lmrs_scene* s, DevBuf& b, size_t bytes) {
+// Device memory comes from one stream-ordered pool per device owned by the
+// library: allocations and frees are ordered on the owner's stream (no
+// device-wide synchronisation, so scenes on different streams keep
+// running concurrently when a buffer grows), freed blocks stay in the pool
+// for reuse, and the pool never adds hidden cross-stream dependencies.
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[kMaxDevices] = {};
+
+cudaError_t lib_pool(cudaMemPool_t* out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        e = cudaMemPoolCreate(&p, &props);
+        if (e != cudaSuccess) return e;
+        uint64_t keep = UINT64_MAX;
+        int no = 0;
+        e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e == cudaSuccess) e = cudaMemPoolSetAttribute(p, cudaMemPoolReuseAllowInternalDependencies, &no);
+        if (e != cudaSuccess) {
+            cudaMemPoolDestroy(p);
+            return e;
+        }
+        g_pools[dev] = p;
+    }
+    *out = g_pools[dev];
+    return cudaSuccess;
+}
+
+// Grows b to at least `bytes` on stream st (contents are not kept).  A
+// buffer that has to grow again gets 25% headroom: per-step sizes (pairs,
+// samples) drift as the parameters move.
+cudaError_t ensure_on(DevBuf& b, size_t bytes, cudaStream_t st) {
     if (bytes == 0) bytes = 16;
-    if (b.cap >= bytes) return LMRS_OK;
+    if (b.cap >= bytes) return cudaSuccess;
+    const size_t want = b.cap ? bytes + bytes / 4 : bytes;
     if (b.p) {
-        cudaError_t e = cudaFree(b.p);
+        cudaError_t e = cudaFreeAsync(b.p, st);
         b.p = nullptr;
         b.cap = 0;
-        if (e != cudaSuccess) return cuda_fail(s, e, "cudaFree");
+        if (e != cudaSuccess) return e;
     }
-    cudaError_t e = cudaMalloc(&b.p, bytes);
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = lib_pool(&pool);
+    if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&b.p, want, pool, st);
     if (e != cudaSuccess) {
         b.p = nullptr;
-        cudaGetLastError();
-        return cuda_fail(s, e, "cudaMalloc");
+        return e;
     }
-    b.cap = bytes;
+    b.cap = want;
+    return cudaSuccess;
+}
+
+lmrs_status ensure(lmrs_scene* s, DevBuf& b, size_t bytes) {
+    const cudaError_t e = ensure_on(b, bytes, s->st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail(s, e, "device allocation");
+    }
     return LMRS_OK;
 }
 
-void release(DevBuf& b) {
-    if (b.p) cudaFree(b.p);
+void release(DevBuf& b, cudaStream_t st) {
+    if (b.p) cudaFreeAsync(b.p, st);
     b.p = nullptr;
     b.cap = 0;
+}
+
+// Returns the pool's unused blocks to the device (after scenes or batches
+// are destroyed).
+void trim_pool() {
+    cudaMemPool_t pool = nullptr;
+    if (lib_pool(&pool) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
 }
 
 bool is_device_ptr(const void* ptr) {
@@ -435,7 +495,10 @@ lmrs_status lmrs_scene_create(const lmrs_config* cfg, int64_t n_gauss, const flo
     }
     std::vector<CamDev> cd(n_cams);
     for (int i = 0; i < n_cams; ++i) cd[i] = make_cam(cams_host[i]);
-    cudaError_t e = cudaMemcpy(s->cams.p, cd.data(), sizeof(CamDev) * n_cams, cudaMemcpyHostToDevice);
+    // the stream-ordered allocations are complete before the synchronous
+    // copies below (which keep the legacy-stream ordering with the caller)
+    cudaError_t e = cudaStreamSynchronize(s->st);
+    if (e == cudaSuccess) e = cudaMemcpy(s->cams.p, cd.data(), sizeof(CamDev) * n_cams, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(s->params.p, params, pv, cudaMemcpyDefault);
     if (e == cudaSuccess) e = cudaMemset(s->counter.p, 0, sizeof(unsigned int) * 4);
     if (e == cudaSuccess) e = cudaMemset(s->sc.p, 0, sizeof(Scalars));
@@ -459,7 +522,9 @@ lmrs_status lmrs_scene_destroy(lmrs_scene* s) {
                       &s->work_sorted, &s->okeys, &s->ovals, &s->okeys_alt, &s->ovals_alt, &s->otmp, &s->cids, &s->clen, &s->resid, &s->cacheC, &s->cacheT,
                       &s->cacheCh, &s->cacheTh, &s->cacheN, &s->x, &s->r, &s->z, &s->p, &s->Ap, &s->minv, &s->D,
                       &s->b, &s->stage_a, &s->stage_b, &s->sc, &s->partials, &s->counter})
-        release(*b);
+        release(*b, s->st);
+    cudaStreamSynchronize(s->st);
+    trim_pool();
     delete s;
     return LMRS_OK;
 }
@@ -889,10 +954,14 @@ lmrs_status batch_tables(lmrs_batch* B, const int64_t* steps) {
     B->hcounts[1] = (int)B->hp.size();
     B->hcounts[2] = (int)B->hv.size();
     B->hcounts[3] = (int)B->hw.size();
-    TRY(ensure(nullptr, B->gch, sizeof(int4) * B->hg.size()));
-    TRY(ensure(nullptr, B->pch, sizeof(int4) * B->hp.size()));
-    TRY(ensure(nullptr, B->vch, sizeof(int4) * B->hv.size()));
-    TRY(ensure(nullptr, B->wch, sizeof(int4) * std::max<size_t>(B->hw.size(), 1)));
+    cudaError_t ea = ensure_on(B->gch, sizeof(int4) * B->hg.size(), B->st);
+    if (ea == cudaSuccess) ea = ensure_on(B->pch, sizeof(int4) * B->hp.size(), B->st);
+    if (ea == cudaSuccess) ea = ensure_on(B->vch, sizeof(int4) * B->hv.size(), B->st);
+    if (ea == cudaSuccess) ea = ensure_on(B->wch, sizeof(int4) * std::max<size_t>(B->hw.size(), 1), B->st);
+    if (ea != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(B, ea == cudaErrorMemoryAllocation ? LMRS_ERR_OOM : LMRS_ERR_CUDA, "batch tables");
+    }
     auto up = [&](DevBuf& d, const void* h, size_t bytes) {
         return bytes ? cudaMemcpyAsync(d.p, h, bytes, cudaMemcpyHostToDevice, B->st) : cudaSuccess;
     };
@@ -994,10 +1063,10 @@ lmrs_status lmrs_batch_create(lmrs_scene* const* scenes, int32_t n_scenes, int32
     } else {
         B->own_stream = true;
     }
-    if (rc == LMRS_OK) rc = ensure(nullptr, B->ctxs, sizeof(Ctx) * n_scenes);
-    if (rc == LMRS_OK) rc = ensure(nullptr, B->vecs, sizeof(BatchVec) * n_scenes);
-    if (rc == LMRS_OK) rc = ensure(nullptr, B->counts, sizeof(int) * 4);
-    if (rc == LMRS_OK) rc = ensure(nullptr, B->hist, sizeof(double) * n_scenes * 2 * (kMaxBatchIters + 1));
+    if (rc == LMRS_OK && ensure_on(B->ctxs, sizeof(Ctx) * n_scenes, B->st) != cudaSuccess) rc = LMRS_ERR_OOM;
+    if (rc == LMRS_OK && ensure_on(B->vecs, sizeof(BatchVec) * n_scenes, B->st) != cudaSuccess) rc = LMRS_ERR_OOM;
+    if (rc == LMRS_OK && ensure_on(B->counts, sizeof(int) * 4, B->st) != cudaSuccess) rc = LMRS_ERR_OOM;
+    if (rc == LMRS_OK && ensure_on(B->hist, sizeof(double) * n_scenes * 2 * (kMaxBatchIters + 1), B->st) != cudaSuccess) rc = LMRS_ERR_OOM;
     B->ev_scene.assign(n_scenes, nullptr);
     for (int i = 0; rc == LMRS_OK && i < n_scenes; ++i)
         if (cudaEventCreateWithFlags(&B->ev_scene[i], cudaEventDisableTiming) != cudaSuccess) rc = LMRS_ERR_CUDA;
@@ -1019,8 +1088,11 @@ lmrs_status lmrs_batch_destroy(lmrs_batch* B) {
     for (auto e : B->ev_scene)
         if (e) cudaEventDestroy(e);
     if (B->ev_batch) cudaEventDestroy(B->ev_batch);
-    for (DevBuf* d : {&B->ctxs, &B->vecs, &B->gch, &B->pch, &B->vch, &B->wch, &B->counts, &B->hist}) release(*d);
+    for (DevBuf* d : {&B->ctxs, &B->vecs, &B->gch, &B->pch, &B->vch, &B->wch, &B->counts, &B->hist})
+        release(*d, B->st);
+    if (B->st) cudaStreamSynchronize(B->st);
     if (B->own_stream) cudaStreamDestroy(B->st);
+    trim_pool();
     delete B;
     return LMRS_OK;
 }

@@ -88,6 +88,8 @@ _SIGS = {
     "lmrs_batch_destroy": (_S, [_P]),
     "lmrs_batch_lm_step": (_S, [_P, _P, _P, _P, _P]),
     "lmrs_batch_last_error": (C.c_char_p, [_P]),
+    "lmrs_autotune_tile": (_S, [C.POINTER(Config), C.c_int64, _P, _P, C.c_int32, _P, _P, C.c_int32, _P, C.c_int32,
+                                C.c_int32, _P, C.POINTER(C.c_int32), _P]),
     "lmrs_synchronize": (_S, [_P]),
     "lmrs_status_str": (C.c_char_p, [_S]),
     "lmrs_last_error": (C.c_char_p, [_P]),
@@ -320,6 +322,20 @@ def lmrs_batch_lm_step(batch, views, lm_steps, stats=True):
     if status != LMRS_OK:
         raise LmrsError(status, lmrs_batch_last_error(batch))
     return list(st) if st is not None else None
+
+
+def lmrs_autotune_tile(cfg, n_gauss, params, cams, targets, views, shapes, reps=3, stream=None):
+    """Times each (tile_w, tile_h) in ``shapes`` on a private copy of the
+    scene; returns (index of the fastest, per-shape median ms per LM step)."""
+    cam_arr = cams if isinstance(cams, C.Array) else cameras(cams)
+    v = np.ascontiguousarray(views, dtype=np.int32)
+    sh = np.ascontiguousarray(shapes, dtype=np.int32).reshape(-1, 2)
+    ms = np.zeros(len(sh), np.float32)
+    best = C.c_int32(-1)
+    _check(lib().lmrs_autotune_tile(C.byref(cfg), int(n_gauss), _ptr(params), C.cast(cam_arr, _P), len(cam_arr),
+                                    _ptr(targets), v.ctypes.data, len(v), sh.ctypes.data, len(sh), int(reps),
+                                    _ptr(stream) if stream is not None else None, C.byref(best), ms.ctypes.data))
+    return best.value, ms
 
 
 def lmrs_synchronize(scene):

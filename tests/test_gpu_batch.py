@@ -96,3 +96,23 @@ def test_batch_rejects_mixed_configs():
         lmrs.lmrs_batch_create([a.h, b.h])
     with pytest.raises(lmrs.LmrsError):
         lmrs.lmrs_batch_create([a.h, a.h])
+
+
+def test_autotune_tile_times_every_shape():
+    import torch
+
+    from paper_2504_12905_gb300 import lmrs
+
+    (sc, tgt), = _scenes(1, seed=5)
+    params = torch.from_numpy(sc.params).cuda()
+    t = torch.from_numpy(tgt).cuda()
+    cfg = lmrs.lmrs_config_default(sh_degree=0, samples_per_tile=32, lambda_=0.1, damping_mode=0, cg_iters=4)
+    shapes = [(16, 16), (32, 8), (8, 32), (8, 8)]
+    views = list(range(len(sc.cams)))
+    best, ms = lmrs.lmrs_autotune_tile(cfg, sc.n_gauss, params, sc.cams, t, views, shapes, reps=2)
+    assert 0 <= best < len(shapes)
+    assert (ms > 0).all() and ms[best] == ms.min()
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(params.cpu().numpy(), sc.params)  # the caller's parameters are untouched
+    with pytest.raises(lmrs.LmrsError):
+        lmrs.lmrs_autotune_tile(cfg, sc.n_gauss, params, sc.cams, t, views, [(32, 16)], reps=1)

@@ -38,6 +38,9 @@ CASES = {
     "tiny": lambda: _tiny(0, lambda_=1e-2),
     "ragged_sh1_frac": lambda: _ragged(1, 0.1, weight_mode=1),
     "ragged_sh3": lambda: _ragged(3, 0.25),
+    # non-square tiles of the autotuner's candidate set
+    "ragged_tile32x8": lambda: _ragged(1, 0.3, tile_w=32, tile_h=8),
+    "ragged_tile8x32_spt": lambda: _ragged(0, 1.0, tile_w=8, tile_h=32, samples_per_tile=40, weight_mode=1),
 }
 
 
