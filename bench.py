@@ -41,6 +41,12 @@ WORKLOADS = {
                          "32 samples per 256-pixel tile, all views every step, 8 CG iters, 20 LM steps per fit",
                     samples_per_tile=32, cg_iters=8, lam=0.1, damping_mode=0, fit_steps=20,
                     tile_shapes=((16, 16), (32, 8), (8, 32))),
+    "serving": dict(desc="fit requests with Poisson arrivals (mean 20/s): 2k-300k Gaussians (log-uniform), SH1, "
+                         "8-32 views 512x512, all views every step, 32 samples per 256-pixel tile, 8 CG iters; each "
+                         "fit runs until its sampled loss is within 0.1 dB of its ground truth's (at most 60 steps); "
+                         "120 GB admission budget",
+                    samples_per_tile=32, cg_iters=8, lam=0.1, damping_mode=0, rate=20.0, requests=100,
+                    max_steps=60, noise_sigma=0.02, psnr_slack_db=0.1, budget_bytes=120 << 30, max_active=64),
 }
 
 
@@ -486,6 +492,183 @@ def run_batched(args, rank, world, local_rank):
     return result
 
 
+def _serving_inputs(lmrs, torch, syn, reqs, wl, rank):
+    """Per request: ground-truth render + N(0, noise_sigma) noise as the
+    targets (host), the stop loss (the ground truth's MSE against the
+    targets, scaled by the PSNR slack) and the perturbed start (host)."""
+    out = []
+    for i, (t_arr, sc) in enumerate(reqs):
+        nc = len(sc.cams)
+        clean = torch.zeros((nc, sc.height, sc.width, 3), dtype=torch.float32, device="cuda")
+        gt = lmrs.Scene(torch.from_numpy(sc.params).cuda(), sc.cams, sc.n_gauss, sc.sh_degree)
+        for v0 in range(0, nc, 8):
+            vs = list(range(v0, min(nc, v0 + 8)))
+            lmrs.lmrs_preprocess(gt.h, vs, 0)
+            lmrs.lmrs_render(gt.h, clean[v0:v0 + len(vs)])
+        lmrs.lmrs_synchronize(gt.h)
+        gt.close()
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(1000 * rank + i)
+        tgt = clean + wl["noise_sigma"] * torch.randn(clean.shape, device="cuda", generator=gen)
+        mse_gt = float(((tgt - clean) ** 2).mean().item())
+        start = syn.perturb_appearance(np.random.default_rng([rank, i]), sc.params, sc.n_gauss, sc.sh_degree)
+        out.append(dict(t=t_arr, sc=sc, targets=tgt.cpu().numpy(), start=start,
+                        stop_loss=mse_gt * 10.0 ** (wl["psnr_slack_db"] / 10.0)))
+        del clean, tgt
+    torch.cuda.synchronize()
+    return out
+
+
+def _pct(x, q):
+    return round(float(np.percentile(np.asarray(x), q)), 4) if len(x) else None
+
+
+def run_serving(args, rank, world, local_rank):
+    """Fit requests through the server (admission against the budget,
+    continuous batching) and the same stream served one fit at a time with
+    lmrs_lm_step; latency = finish - arrival."""
+    import torch
+
+    from paper_2504_12905_gb300 import lmrs
+    from paper_2504_12905_gb300 import synthetic as syn
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    wl = WORKLOADS["serving"]
+    n_req = args.requests or wl["requests"]
+    reqs = syn.serving_requests(seed=0x1A5E0004 + rank, n_requests=n_req + args.warmup, rate=wl["rate"])
+    jobs = _serving_inputs(lmrs, torch, syn, reqs, wl, rank)
+    warm, jobs = jobs[:args.warmup], jobs[args.warmup:]
+    t_first = jobs[0]["t"]
+    for j in jobs:
+        j["t"] -= t_first
+    cfgd = dict(samples_per_tile=wl["samples_per_tile"], lambda_=wl["lam"], damping_mode=wl["damping_mode"],
+                cg_iters=wl["cg_iters"])
+
+    def cfg_of(k, sc):
+        return lmrs.lmrs_config_default(sh_degree=sc.sh_degree, seed=0x5EED + k, **cfgd)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    # ---- server arm ---------------------------------------------------------
+    srv = lmrs.lmrs_server_create(wl["budget_bytes"], max_active=wl["max_active"], setup_threads=8)
+    wid = [lmrs.lmrs_server_submit(srv, cfg_of(k, j["sc"]), j["sc"].n_gauss, j["start"], j["sc"].cams, j["targets"],
+                                   0, j["stop_loss"], wl["max_steps"]) for k, j in enumerate(warm)]
+    for w in wid:
+        lmrs.lmrs_server_wait(srv, w, 600.0)
+    barrier()
+    vis_dev = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    smi_idx = vis_dev.split(",")[local_rank] if vis_dev and not vis_dev.startswith("GPU") else str(local_rank)
+    clocks = ClockSampler(smi_idx)
+    launches0 = lmrs.lmrs_launch_count()
+    clocks.start()
+    t0 = time.perf_counter()
+    ids = []
+    for k, j in enumerate(jobs):
+        delay = t0 + j["t"] - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        ids.append(lmrs.lmrs_server_submit(srv, cfg_of(k, j["sc"]), j["sc"].n_gauss, j["start"], j["sc"].cams,
+                                           j["targets"], 0, j["stop_loss"], wl["max_steps"]))
+    infos = []
+    for jid in ids:
+        status, info = lmrs.lmrs_server_wait(srv, jid, 1800.0)
+        infos.append(info)
+    wall_srv = time.perf_counter() - t0
+    clock_info = clocks.stop()
+    launches = lmrs.lmrs_launch_count() - launches0
+    sstats = lmrs.lmrs_server_get_stats(srv)
+    lmrs.lmrs_server_destroy(srv)
+    ok = [i for i in infos if i.state == lmrs.JOB_DONE]
+    lat_srv = [i.t_done - i.t_submit for i in ok]
+    span_srv = max(i.t_done for i in infos) - min(i.t_submit for i in infos)
+
+    # ---- plain arm: one fit at a time, in arrival order ----------------------
+    sstream = torch.cuda.Stream()
+    lat_plain, conv_plain, steps_plain = [], 0, []
+    t0 = time.perf_counter()
+    for k, j in enumerate(jobs):
+        delay = t0 + j["t"] - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        sc = j["sc"]
+        tg = torch.from_numpy(j["targets"]).to("cuda", non_blocking=False)
+        scene = lmrs.Scene(j["start"], sc.cams, sc.n_gauss, sc.sh_degree, targets=tg, stream=sstream.cuda_stream,
+                           seed=0x5EED + k, **cfgd)
+        views = list(range(len(sc.cams)))
+        conv = False
+        for step in range(wl["max_steps"]):
+            st = lmrs.lmrs_lm_step(scene.h, views, step)
+            if st.loss <= j["stop_loss"]:
+                conv = True
+                break
+        out = np.empty(scene.n_params, np.float32)
+        lmrs.lmrs_get_params(scene.h, out)
+        scene.close()
+        del tg
+        lat_plain.append(time.perf_counter() - t0 - j["t"])
+        conv_plain += int(conv)
+        steps_plain.append(step + 1)
+    wall_plain = time.perf_counter() - t0
+    barrier()
+
+    n = len(jobs)
+    fits_srv = world * len(ok) / span_srv
+    fits_plain = world * n / wall_plain
+    h2d = int(np.mean([j["targets"].nbytes + j["start"].nbytes for j in jobs]))
+    d2h = int(np.mean([j["start"].nbytes for j in jobs]))
+    est = np.array([i.footprint_est for i in ok], np.float64)
+    peak = np.array([i.footprint_peak for i in ok], np.float64)
+    result = {
+        "metric": METRIC, "value": round(fits_srv, 3), "unit": "fits/s", "n_gpus": world, "steps": n,
+        "warmup": len(warm), "ms_per_step": round(1000.0 * span_srv / max(len(ok), 1), 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 CG scalars)",
+        "data": "synthetic (seeded; targets = ground-truth renders + N(0, 0.02^2) noise)",
+        "config": {"workload": f"serving: {wl['desc']}", "requests": n, "rate_per_s": wl["rate"],
+                   "step": "one fit request (a bench step = one request)",
+                   "n_gauss_mean": int(np.mean([j["sc"].n_gauss for j in jobs])),
+                   "views_mean": round(float(np.mean([len(j["sc"].cams) for j in jobs])), 2),
+                   "budget_gb": wl["budget_bytes"] / 2**30, "max_active": wl["max_active"],
+                   "bytes_peak_gb": round(sstats.bytes_peak / 2**30, 3),
+                   "footprint_peak_over_estimate": {"max": round(float((peak / est).max()), 3),
+                                                    "mean": round(float((peak / est).mean()), 3)} if len(ok) else None,
+                   "latency_s": {"p50": _pct(lat_srv, 50), "p99": _pct(lat_srv, 99), "max": _pct(lat_srv, 100)},
+                   "converged": sum(i.converged for i in ok), "failed": n - len(ok),
+                   "steps_mean": round(float(np.mean([i.steps for i in ok])), 2) if ok else None,
+                   "scheduler_iterations": sstats.iterations,
+                   "plain": {"fits_per_s": round(fits_plain, 3),
+                             "latency_s": {"p50": _pct(lat_plain, 50), "p99": _pct(lat_plain, 99)},
+                             "converged": conv_plain, "steps_mean": round(float(np.mean(steps_plain)), 2)},
+                   "server_over_plain": round(fits_srv / fits_plain, 3),
+                   "parallelism": f"replicas x{world}", "l2": "no flush: per-step working set > 129 MB",
+                   "wall_s": {"server": round(wall_srv, 2), "plain": round(wall_plain, 2)}},
+        "roofline": None,
+        "e2e": {"value": round(fits_srv, 3), "unit": "fits/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches, "clocks": clock_info,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        t, m, dt = _oracle_fit_step_time([j["sc"] for j in jobs], [j["start"] for j in jobs],
+                                         [j["targets"] for j in jobs], [list(range(len(j["sc"].cams))) for j in jobs],
+                                         {**cfgd, "seed": 0x5EED}, {"fit_steps": 0}, args.cpu_seconds)
+        spf = float(np.mean([i.steps for i in ok])) if ok else wl["max_steps"]
+        result["cpu_baseline"] = {
+            "value": round(1.0 / (spf * t), 6), "unit": "fits/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"one FP64 LM step on each of the first {m} requests ({dt:.1f} s); fits/s = 1 / "
+                      f"({spf:.1f} steps per fit, the server's mean, x mean seconds per step)"}
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return result
+
+
 def _oracle_fit_step_time(scenes, starts, targets, views, cfg, wl, budget_s):
     """The FP64 oracle's LM step on scenes 0, 1, ... until budget_s; returns
     (mean seconds per scene-step, scenes done, seconds)."""
@@ -620,6 +803,7 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="moderate")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--requests", type=int, default=0, help="serving workload: number of timed requests")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -631,7 +815,7 @@ def main():
         if rank == 0:
             print(json.dumps(run_reference(args)))
         return
-    run = run_batched if args.workload == "batched" else run_ours
+    run = {"batched": run_batched, "serving": run_serving}.get(args.workload, run_ours)
     res = run(args, rank, world, local_rank)
     if rank == 0:
         print(json.dumps(res))

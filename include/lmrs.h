@@ -243,6 +243,98 @@ lmrs_status lmrs_batch_destroy(lmrs_batch* batch);
 lmrs_status lmrs_batch_lm_step(lmrs_batch* batch, const int32_t* view_ids, const int32_t* n_views,
                                const int64_t* lm_steps, lmrs_step_stats* stats);
 const char* lmrs_batch_last_error(const lmrs_batch* batch);
+/* Outcome of the last lmrs_batch_lm_step for scene i: LMRS_OK (stepped),
+ * the scene's own error (its setup failed; LMRS_ERR_NUMERIC when its CG hit
+ * p^T A p <= 0, detected only when stats were requested), or
+ * LMRS_ERR_NOT_PREPROCESSED (not stepped because another scene failed
+ * before the batched loop). */
+lmrs_status lmrs_batch_scene_status(const lmrs_batch* batch, int32_t i);
+
+/* ---- Serving: a queue of fit jobs on one device --------------------------
+ * The paper fits one scene at a time; the server keeps many fits resident
+ * and steps them together with the batched LM step above.
+ *   - lmrs_server_submit copies a job (parameters, cameras, targets: host
+ *     memory) and queues it; it does not wait for the device.
+ *   - a scheduler thread admits queued jobs in FIFO order while fewer than
+ *     max_active jobs are resident and the device bytes of the resident jobs
+ *     (for each, the larger of its admission estimate and what it holds)
+ *     plus the next job's estimate (lmrs_footprint_bytes) stay within
+ *     budget_bytes.  An admitted job's parameters, CG vectors, raster
+ *     caches and targets stay on the device until it finishes.
+ *   - every scheduler iteration runs one LM step of each resident job (one
+ *     batch per group of equal SH degree and cg_iters), then retires the
+ *     jobs whose sampled loss (Eq. 11 at the step's samples, before the
+ *     update) is <= target_loss or that have run max_steps steps; the freed
+ *     memory admits the next jobs (continuous batching).
+ *   - the views of step k: views_per_step camera indices drawn without
+ *     replacement (partial Fisher-Yates driven by SplitMix64 seeded with
+ *     cfg.seed and k), or every camera when views_per_step <= 0 or >=
+ *     n_cams.  A job's steps therefore do not depend on the other jobs: its
+ *     result alone and in any mix agree up to the summation order.
+ * Jobs stay owned by the server; their records are kept until forgotten. */
+typedef struct lmrs_server lmrs_server;
+typedef struct {
+    int64_t budget_bytes;   /* device bytes the resident jobs may hold */
+    int32_t max_active;     /* resident jobs at most (1..1024) */
+    int32_t setup_threads;  /* host threads for the per-scene step setup (>= 1) */
+    double tiles_per_pair;  /* footprint model: tile entries per visible (view, Gaussian) pair; <= 0: 10 */
+} lmrs_server_config;
+
+typedef enum { LMRS_JOB_QUEUED = 0, LMRS_JOB_RUNNING = 1, LMRS_JOB_DONE = 2, LMRS_JOB_FAILED = 3 } lmrs_job_state;
+
+typedef struct {
+    int32_t state;           /* lmrs_job_state */
+    int32_t status;          /* lmrs_status of a failed job, else LMRS_OK */
+    int32_t converged;       /* 1: target_loss reached; 0: stopped at max_steps (or not finished) */
+    int32_t steps;           /* LM steps run so far */
+    double loss;             /* sampled loss of the last step */
+    double t_submit;         /* seconds since the server was created */
+    double t_admit;          /* -1 while queued */
+    double t_done;           /* -1 until finished */
+    int64_t footprint_est;   /* the admission estimate (bytes) */
+    int64_t footprint_peak;  /* device bytes the job held at most */
+} lmrs_job_info;
+
+typedef struct {
+    int32_t queued, active;
+    int64_t finished;        /* jobs done or failed */
+    int64_t bytes_in_use;    /* device bytes held by the resident jobs */
+    int64_t bytes_peak;
+    int64_t iterations;      /* scheduler iterations (batched steps) run */
+} lmrs_server_stats;
+
+/* Starts the scheduler thread on the current device. */
+lmrs_status lmrs_server_create(const lmrs_server_config* cfg, lmrs_server** out);
+/* Queues a fit: cfg as for lmrs_scene_create; params_host[P],
+ * cams_host[n_cams], targets_host[n_cams][H][W][3] are copied.  Invalid
+ * configurations are rejected here; a job whose estimate alone exceeds the
+ * budget is rejected with LMRS_ERR_BUDGET. */
+lmrs_status lmrs_server_submit(lmrs_server* srv, const lmrs_config* cfg, int64_t n_gauss, const float* params_host,
+                               const lmrs_camera* cams_host, int32_t n_cams, const float* targets_host,
+                               int32_t views_per_step, double target_loss, int32_t max_steps, int64_t* job_id);
+lmrs_status lmrs_server_poll(lmrs_server* srv, int64_t job_id, lmrs_job_info* info);
+/* Waits until the job is done or failed; LMRS_ERR_TIMEOUT after timeout_s
+ * seconds (info then holds the current state). */
+lmrs_status lmrs_server_wait(lmrs_server* srv, int64_t job_id, double timeout_s, lmrs_job_info* info);
+/* Final parameters of a done job (P floats, host). */
+lmrs_status lmrs_server_result(lmrs_server* srv, int64_t job_id, float* params_host);
+/* Drops the record of a finished job. */
+lmrs_status lmrs_server_forget(lmrs_server* srv, int64_t job_id);
+lmrs_status lmrs_server_get_stats(lmrs_server* srv, lmrs_server_stats* out);
+/* Stops the scheduler after its current iteration and waits for it;
+ * unfinished jobs end as failed with LMRS_ERR_TIMEOUT. */
+lmrs_status lmrs_server_destroy(lmrs_server* srv);
+
+/* Footprint model of the admission test: device bytes of a scene during an
+ * LM step with views_per_step views (all when <= 0): 9 P-vectors, the
+ * per-Gaussian cache, 352 B per (view, Gaussian) pair, the tile entries
+ * (tiles_per_pair per pair, keys, ids, their sort buffers and the compact
+ * lists), 41 B per sample, the per-tile tables, the targets, and 25%
+ * headroom on the per-step parts. */
+int64_t lmrs_footprint_bytes(const lmrs_config* cfg, int64_t n_gauss, int32_t n_cams, int32_t width, int32_t height,
+                             int32_t views_per_step, double tiles_per_pair);
+/* Device bytes the scene holds now. */
+int64_t lmrs_scene_device_bytes(const lmrs_scene* scene);
 
 /* Tile-shape autotuner.  The tile shape groups pixels for the per-tile
  * residual sampling (Sec. 4.4) and for the tile lists of every raster pass;

@@ -18,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB_NAME = "liblmrs.so"
-SOURCES = ["scene.cu", "preprocess.cu", "binning.cu", "raster.cu", "cg.cu", "noalloc.cu", "autotune.cu"]
+SOURCES = ["scene.cu", "preprocess.cu", "binning.cu", "raster.cu", "cg.cu", "noalloc.cu", "autotune.cu",
+           "server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -212,6 +212,11 @@ void launch_b_prep_vjp(const BatchTables& t, int deg, int iter, int grid, cudaSt
 void launch_b_update(const BatchTables& t, int iter, int grid, cudaStream_t st);
 void launch_b_lm_update(const BatchTables& t, int iters, int grid, cudaStream_t st);
 
+// ---- device memory from the library's stream-ordered pool -----------------
+cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t st);
+void pool_free(void* p, cudaStream_t st);
+void pool_trim();
+
 }  // namespace lmrs
 
 namespace lmrs {

@@ -97,6 +97,15 @@ struct lmrs_scene {
     bool timing = false;
     LaunchTimer timer;
 
+    // every device buffer the scene owns
+    std::vector<DevBuf*> bufs() {
+        return {&params, &cams, &views, &gcache, &rec, &rect, &dkeys, &dvals, &dkeys_alt, &dvals_alt, &dtmp, &cnt,
+                &cot, &gram, &keys, &ids, &keys_alt, &ids_alt, &ranges, &scan_tmp, &radix_tmp, &total, &tile_off,
+                &off, &wtile, &work, &item_cost, &work_sorted, &okeys, &ovals, &okeys_alt, &ovals_alt, &otmp,
+                &cids, &clen, &resid, &cacheC, &cacheT, &cacheCh, &cacheTh, &cacheN, &x, &r, &z, &p, &Ap,
+                &minv, &D, &b, &stage_a, &stage_b, &sc, &partials, &counter};
+    }
+
     Ctx ctx() const {
         Ctx c;
         std::memset(&c, 0, sizeof(c));
@@ -268,6 +277,23 @@ void trim_pool() {
     cudaMemPool_t pool = nullptr;
     if (lib_pool(&pool) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
 }
+
+}  // namespace
+
+namespace lmrs {
+cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t st) {
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = lib_pool(&pool);
+    if (e == cudaSuccess) e = cudaMallocFromPoolAsync(p, bytes ? bytes : 16, pool, st);
+    return e;
+}
+void pool_free(void* p, cudaStream_t st) {
+    if (p) cudaFreeAsync(p, st);
+}
+void pool_trim() { trim_pool(); }
+}  // namespace lmrs
+
+namespace {
 
 bool is_device_ptr(const void* ptr) {
     cudaPointerAttributes a;
@@ -515,13 +541,7 @@ lmrs_status lmrs_scene_create(const lmrs_config* cfg, int64_t n_gauss, const flo
 lmrs_status lmrs_scene_destroy(lmrs_scene* s) {
     if (!s) return LMRS_ERR_INVALID_ARG;
     if (s->st) cudaStreamSynchronize(s->st);
-    for (DevBuf* b : {&s->params, &s->cams, &s->views, &s->gcache, &s->rec, &s->rect, &s->dkeys, &s->dvals,
-                      &s->dkeys_alt, &s->dvals_alt, &s->dtmp, &s->cnt, &s->cot, &s->gram,
-                      &s->keys, &s->ids, &s->keys_alt, &s->ids_alt, &s->ranges, &s->scan_tmp, &s->radix_tmp,
-                      &s->total, &s->tile_off, &s->off, &s->wtile, &s->work, &s->item_cost,
-                      &s->work_sorted, &s->okeys, &s->ovals, &s->okeys_alt, &s->ovals_alt, &s->otmp, &s->cids, &s->clen, &s->resid, &s->cacheC, &s->cacheT,
-                      &s->cacheCh, &s->cacheTh, &s->cacheN, &s->x, &s->r, &s->z, &s->p, &s->Ap, &s->minv, &s->D,
-                      &s->b, &s->stage_a, &s->stage_b, &s->sc, &s->partials, &s->counter})
+    for (DevBuf* b : s->bufs())
         release(*b, s->st);
     cudaStreamSynchronize(s->st);
     trim_pool();
@@ -866,6 +886,53 @@ const char* lmrs_last_error(const lmrs_scene* s) { return s ? s->err.c_str() : "
 
 int64_t lmrs_launch_count(void) { return lmrs::g_launches.load(std::memory_order_relaxed); }
 
+int64_t lmrs_footprint_bytes(const lmrs_config* cfg, int64_t n_gauss, int32_t n_cams, int32_t width, int32_t height,
+                             int32_t views_per_step, double tiles_per_pair) {
+    if (!cfg || n_gauss <= 0 || n_cams <= 0 || width <= 0 || height <= 0 || cfg->tile_w <= 0 || cfg->tile_h <= 0 ||
+        cfg->sh_degree < 0 || cfg->sh_degree > 3)
+        return 0;
+    const double nv = (views_per_step <= 0 || views_per_step > n_cams) ? n_cams : views_per_step;
+    const double tpp = tiles_per_pair > 0.0 ? tiles_per_pair : 10.0;
+    const double G = (double)n_gauss;
+    const double P = G * (11 + 3 * (cfg->sh_degree + 1) * (cfg->sh_degree + 1));
+    const int tx = (width + cfg->tile_w - 1) / cfg->tile_w, ty = (height + cfg->tile_h - 1) / cfg->tile_h;
+    double S_view = 0.0, items_view = 0.0;
+    int max_items = 1;
+    for (int t = 0; t < tx * ty; ++t) {
+        const int vw = std::min(cfg->tile_w, width - (t % tx) * cfg->tile_w);
+        const int vh = std::min(cfg->tile_h, height - (t / tx) * cfg->tile_h);
+        const int k = samples_in_tile(*cfg, vw * vh);
+        S_view += k;
+        items_view += (k + 31) / 32;
+        max_items = std::max(max_items, (k + 31) / 32);
+    }
+    const double pairs = nv * G, entries = tpp * pairs, S = nv * S_view, items = nv * items_view;
+    // rec 96, rect 16, depth keys/values and their alternates 24, counts 8,
+    // cotangent slots 48, Gram blocks 160; scan and sort scratch ~2
+    const double per_pair = 96 + 16 + 24 + 8 + 48 + 160 + 2;
+    // keys, ids and their alternates 16, compact lists 4 per work item of a tile
+    const double per_entry = 16 + 4.0 * max_items + 1;
+    // offset 1, residual 12, FP32 and BF16 caches 12 + 4 + 6 + 2, stop index 4
+    const double per_sample = 41;
+    // tile offset, weight, range 16; compact lengths 4 per item; work items
+    // and their ordering buffers 36
+    const double per_view_tile = 16 + 4.0 * max_items;
+    const double per_item = 36;
+    const double fixed = 9 * 4 * P + 4.0 * kGaussF4 * 4 * G + (double)sizeof(CamDev) * n_cams +
+                         sizeof(double) * kMaxPartials + 65536;
+    const double var = pairs * per_pair + entries * per_entry + S * per_sample + nv * tx * ty * per_view_tile +
+                       items * per_item;
+    const double targets = (double)n_cams * height * width * 3 * sizeof(float);
+    return (int64_t)(fixed + targets + 1.25 * var);
+}
+
+int64_t lmrs_scene_device_bytes(const lmrs_scene* s) {
+    if (!s) return 0;
+    int64_t n = 0;
+    for (DevBuf* b : const_cast<lmrs_scene*>(s)->bufs()) n += (int64_t)b->cap;
+    return n;
+}
+
 }  // extern "C"
 
 // ===========================================================================
@@ -890,6 +957,7 @@ struct lmrs_batch {
     void* graph_key[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     std::vector<cudaEvent_t> ev_scene;
     cudaEvent_t ev_batch = nullptr;
+    std::vector<lmrs_status> scene_rc;  // per scene, of the last step
 };
 
 namespace {
@@ -1101,6 +1169,7 @@ lmrs_status lmrs_batch_lm_step(lmrs_batch* B, const int32_t* view_ids, const int
                                lmrs_step_stats* stats) {
     if (!B) return LMRS_ERR_INVALID_ARG;
     if (!view_ids || !n_views || !lm_steps) return bfail(B, LMRS_ERR_INVALID_ARG, "null argument");
+    B->scene_rc.assign(B->n, LMRS_ERR_NOT_PREPROCESSED);  // "not stepped" until the graph ran
     std::vector<long long> voff(B->n + 1, 0);
     for (int i = 0; i < B->n; ++i) {
         if (n_views[i] <= 0) return bfail(B, LMRS_ERR_INVALID_ARG, "scene without views");
@@ -1122,9 +1191,17 @@ lmrs_status lmrs_batch_lm_step(lmrs_batch* B, const int32_t* view_ids, const int
         for (int w = 0; w < B->nthreads; ++w) pool.emplace_back(work, w);
         for (auto& th : pool) th.join();
     }
+    lmrs_status first = LMRS_OK;
+    int first_i = -1;
     for (int i = 0; i < B->n; ++i)
-        if (rc[i] != LMRS_OK)
-            return bfail(B, rc[i], "scene " + std::to_string(i) + ": " + B->scenes[i]->err);
+        if (rc[i] != LMRS_OK) {
+            B->scene_rc[i] = rc[i];
+            if (first_i < 0) {
+                first = rc[i];
+                first_i = i;
+            }
+        }
+    if (first_i >= 0) return bfail(B, first, "scene " + std::to_string(first_i) + ": " + B->scenes[first_i]->err);
     // 2. tables, then the batched PCG loop and updates (one graph)
     for (int i = 0; i < B->n; ++i)
         if (cudaStreamWaitEvent(B->st, B->ev_scene[i], 0) != cudaSuccess)
@@ -1140,6 +1217,7 @@ lmrs_status lmrs_batch_lm_step(lmrs_batch* B, const int32_t* view_ids, const int
         if (cudaStreamWaitEvent(s->st, B->ev_batch, 0) != cudaSuccess) return bfail(B, LMRS_ERR_CUDA, "stream wait");
         s->preprocessed = s->rendered = s->have_D = s->ordered = false;
     }
+    std::fill(B->scene_rc.begin(), B->scene_rc.end(), LMRS_OK);
     if (!stats) return LMRS_OK;
     if (cudaStreamSynchronize(B->st) != cudaSuccess) return bfail(B, LMRS_ERR_CUDA, "synchronise");
     std::vector<double> hist((size_t)B->n * 2 * (kMaxBatchIters + 1));
@@ -1161,11 +1239,19 @@ lmrs_status lmrs_batch_lm_step(lmrs_batch* B, const int32_t* view_ids, const int
         stats[i].rz_final = rz[B->iters];
         stats[i].n_samples = s->S;
         stats[i].n_pairs = s->npairs;
-        if (h.numeric_error && out == LMRS_OK) out = bfail(B, LMRS_ERR_NUMERIC, "scene " + std::to_string(i));
+        if (h.numeric_error) {
+            B->scene_rc[i] = LMRS_ERR_NUMERIC;
+            if (out == LMRS_OK) out = bfail(B, LMRS_ERR_NUMERIC, "scene " + std::to_string(i));
+        }
     }
     return out;
 }
 
 const char* lmrs_batch_last_error(const lmrs_batch* B) { return B ? B->err.c_str() : "null batch"; }
+
+lmrs_status lmrs_batch_scene_status(const lmrs_batch* B, int32_t i) {
+    if (!B || i < 0 || i >= B->n) return LMRS_ERR_INVALID_ARG;
+    return i < (int)B->scene_rc.size() ? B->scene_rc[i] : LMRS_ERR_NOT_PREPROCESSED;
+}
 
 }  // extern "C"

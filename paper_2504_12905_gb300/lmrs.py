@@ -55,6 +55,24 @@ class StepStats(C.Structure):
                 ("rz_final", C.c_double), ("n_samples", C.c_int64), ("n_pairs", C.c_int64)]
 
 
+class ServerConfig(C.Structure):
+    _fields_ = [("budget_bytes", C.c_int64), ("max_active", C.c_int32), ("setup_threads", C.c_int32),
+                ("tiles_per_pair", C.c_double)]
+
+
+class JobInfo(C.Structure):
+    _fields_ = [("state", C.c_int32), ("status", C.c_int32), ("converged", C.c_int32), ("steps", C.c_int32),
+                ("loss", C.c_double), ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double),
+                ("footprint_est", C.c_int64), ("footprint_peak", C.c_int64)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("queued", C.c_int32), ("active", C.c_int32), ("finished", C.c_int64), ("bytes_in_use", C.c_int64),
+                ("bytes_peak", C.c_int64), ("iterations", C.c_int64)]
+
+
+JOB_QUEUED, JOB_RUNNING, JOB_DONE, JOB_FAILED = 0, 1, 2, 3
+
 _P = C.c_void_p
 _S = C.c_int
 _SIGS = {
@@ -90,6 +108,19 @@ _SIGS = {
     "lmrs_batch_last_error": (C.c_char_p, [_P]),
     "lmrs_autotune_tile": (_S, [C.POINTER(Config), C.c_int64, _P, _P, C.c_int32, _P, _P, C.c_int32, _P, C.c_int32,
                                 C.c_int32, _P, C.POINTER(C.c_int32), _P]),
+    "lmrs_batch_scene_status": (_S, [_P, C.c_int32]),
+    "lmrs_server_create": (_S, [C.POINTER(ServerConfig), C.POINTER(_P)]),
+    "lmrs_server_submit": (_S, [_P, C.POINTER(Config), C.c_int64, _P, _P, C.c_int32, _P, C.c_int32, C.c_double,
+                                C.c_int32, C.POINTER(C.c_int64)]),
+    "lmrs_server_poll": (_S, [_P, C.c_int64, C.POINTER(JobInfo)]),
+    "lmrs_server_wait": (_S, [_P, C.c_int64, C.c_double, C.POINTER(JobInfo)]),
+    "lmrs_server_result": (_S, [_P, C.c_int64, _P]),
+    "lmrs_server_forget": (_S, [_P, C.c_int64]),
+    "lmrs_server_get_stats": (_S, [_P, C.POINTER(ServerStats)]),
+    "lmrs_server_destroy": (_S, [_P]),
+    "lmrs_footprint_bytes": (C.c_int64, [C.POINTER(Config), C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                         C.c_double]),
+    "lmrs_scene_device_bytes": (C.c_int64, [_P]),
     "lmrs_synchronize": (_S, [_P]),
     "lmrs_status_str": (C.c_char_p, [_S]),
     "lmrs_last_error": (C.c_char_p, [_P]),
@@ -336,6 +367,77 @@ def lmrs_autotune_tile(cfg, n_gauss, params, cams, targets, views, shapes, reps=
                                     _ptr(targets), v.ctypes.data, len(v), sh.ctypes.data, len(sh), int(reps),
                                     _ptr(stream) if stream is not None else None, C.byref(best), ms.ctypes.data))
     return best.value, ms
+
+
+def lmrs_batch_scene_status(batch, i):
+    return int(lib().lmrs_batch_scene_status(batch, int(i)))
+
+
+def lmrs_server_create(budget_bytes, max_active=64, setup_threads=8, tiles_per_pair=0.0):
+    cfg = ServerConfig(int(budget_bytes), int(max_active), int(setup_threads), float(tiles_per_pair))
+    h = _P()
+    _check(lib().lmrs_server_create(C.byref(cfg), C.byref(h)))
+    return h.value
+
+
+def lmrs_server_submit(server, cfg, n_gauss, params_host, cams, targets_host, views_per_step=0, target_loss=0.0,
+                       max_steps=20):
+    """params_host [P] and targets_host [n_cams, H, W, 3]: float32 host arrays
+    (copied).  Returns the job id."""
+    p = np.ascontiguousarray(params_host, np.float32)
+    t = np.ascontiguousarray(targets_host, np.float32)
+    cam_arr = cams if isinstance(cams, C.Array) else cameras(cams)
+    jid = C.c_int64(0)
+    status = lib().lmrs_server_submit(server, C.byref(cfg), int(n_gauss), p.ctypes.data, C.cast(cam_arr, _P),
+                                      len(cam_arr), t.ctypes.data, int(views_per_step), float(target_loss),
+                                      int(max_steps), C.byref(jid))
+    if status != LMRS_OK:
+        raise LmrsError(status, "server submit")
+    return jid.value
+
+
+def lmrs_server_poll(server, job):
+    info = JobInfo()
+    _check(lib().lmrs_server_poll(server, int(job), C.byref(info)))
+    return info
+
+
+def lmrs_server_wait(server, job, timeout_s=60.0):
+    """Returns (status, JobInfo); status LMRS_ERR_TIMEOUT if not finished in time."""
+    info = JobInfo()
+    status = lib().lmrs_server_wait(server, int(job), float(timeout_s), C.byref(info))
+    if status not in (LMRS_OK, 6):
+        raise LmrsError(status, "server wait")
+    return status, info
+
+
+def lmrs_server_result(server, job, n_params):
+    out = np.empty(int(n_params), np.float32)
+    _check(lib().lmrs_server_result(server, int(job), out.ctypes.data))
+    return out
+
+
+def lmrs_server_forget(server, job):
+    _check(lib().lmrs_server_forget(server, int(job)))
+
+
+def lmrs_server_get_stats(server):
+    st = ServerStats()
+    _check(lib().lmrs_server_get_stats(server, C.byref(st)))
+    return st
+
+
+def lmrs_server_destroy(server):
+    _check(lib().lmrs_server_destroy(server))
+
+
+def lmrs_footprint_bytes(cfg, n_gauss, n_cams, width, height, views_per_step=0, tiles_per_pair=0.0):
+    return int(lib().lmrs_footprint_bytes(C.byref(cfg), int(n_gauss), int(n_cams), int(width), int(height),
+                                          int(views_per_step), float(tiles_per_pair)))
+
+
+def lmrs_scene_device_bytes(scene):
+    return int(lib().lmrs_scene_device_bytes(scene))
 
 
 def lmrs_synchronize(scene):

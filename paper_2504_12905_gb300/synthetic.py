@@ -258,6 +258,36 @@ def small_fit_scenes(seed=0x1A5E0003, n_scenes=64, g_lo=5_000, g_hi=50_000, v_lo
     return out
 
 
+def serving_requests(seed=0x1A5E0004, n_requests=100, rate=20.0, g_lo=2_000, g_hi=300_000, v_lo=8, v_hi=32,
+                     width=512, height=512, sh_degree=1):
+    """A stream of fit requests: Poisson arrivals (exponential gaps of mean
+    1/rate seconds), Gaussian counts log-uniform in [g_lo, g_hi], v_lo..v_hi
+    views of width x height on a Fibonacci hemisphere, means from 16 blobs.
+    Returns [(arrival time in seconds, Scene)]; the Scene holds the ground
+    truth of the fit."""
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    for i in range(n_requests):
+        t += float(rng.exponential(1.0 / rate))
+        G = int(round(math.exp(rng.uniform(math.log(g_lo), math.log(g_hi)))))
+        nv = int(rng.integers(v_lo, v_hi + 1))
+        sub = np.random.default_rng([seed, i])
+        params = draw_gaussians(sub, G, sh_degree, means=blob_means(sub, G, n_blobs=16))
+        cams = hemisphere_cameras(nv, 3.0, width, height)
+        out.append((t, Scene(G, sh_degree, params, cams, int(seed) * 1000 + i)))
+    return out
+
+
+def perturb_appearance(rng, params, n_gauss, sh_degree, sh_sigma=0.1, opacity_sigma=0.3):
+    """Start of a serving fit: SH coefficients + N(0, sh_sigma) and opacity
+    logits + N(0, opacity_sigma); geometry unchanged."""
+    off = group_offsets(n_gauss, sh_degree)
+    p = params.astype(np.float64).copy()
+    p[off["opacity"]:off["sh"]] += rng.normal(0.0, opacity_sigma, n_gauss)
+    p[off["sh"]:off["end"]] += rng.normal(0.0, sh_sigma, off["end"] - off["sh"])
+    return p.astype(np.float32)
+
+
 def view_subset(rng, n_cams, n_views):
     """Views of one LM step: uniform without replacement."""
     return np.sort(rng.choice(n_cams, size=n_views, replace=False)).astype(np.int32)

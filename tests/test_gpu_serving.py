@@ -1,0 +1,97 @@
+"""Fit server on the device: a job's result is the same alone and among
+other jobs, FIFO admission against the memory budget, the convergence rule
+and the rejection of bad submissions."""
+import numpy as np
+import pytest
+
+from paper_2504_12905_gb300 import synthetic as syn
+
+from helpers import normwise_rel
+
+pytestmark = pytest.mark.gpu
+
+WAIT_S = 180.0
+
+
+def _job(seed, G, n_cams, size=64):
+    rng = np.random.default_rng(seed)
+    params = syn.draw_gaussians(rng, G, 1, means=syn.blob_means(rng, G, n_blobs=4))
+    cams = syn.hemisphere_cameras(n_cams, 3.0, size, size)
+    tgt = syn.noise_targets(rng, n_cams, size, size)
+    return params, cams, tgt
+
+
+def _cfg(lmrs, seed):
+    return lmrs.lmrs_config_default(sh_degree=1, samples_per_tile=48, lambda_=0.1, damping_mode=0, cg_iters=4,
+                                    seed=seed)
+
+
+def _run(lmrs, jobs, budget=8 << 30, max_active=16, max_steps=4, target_loss=0.0):
+    srv = lmrs.lmrs_server_create(budget, max_active=max_active, setup_threads=4)
+    try:
+        ids = [lmrs.lmrs_server_submit(srv, _cfg(lmrs, 100 + k), p.size // 23, p, c, t, views_per_step=3,
+                                       target_loss=target_loss, max_steps=max_steps)
+               for k, (p, c, t) in jobs]
+        out = []
+        for jid, (k, (p, c, t)) in zip(ids, jobs):
+            status, info = lmrs.lmrs_server_wait(srv, jid, WAIT_S)
+            assert status == lmrs.LMRS_OK and info.state == lmrs.JOB_DONE, (k, info.state, info.status)
+            out.append((info, lmrs.lmrs_server_result(srv, jid, p.size)))
+        stats = lmrs.lmrs_server_get_stats(srv)
+    finally:
+        lmrs.lmrs_server_destroy(srv)
+    return out, stats
+
+
+def test_job_same_alone_and_in_mix():
+    from paper_2504_12905_gb300 import lmrs
+    a = (0, _job(1, 1500, 8))
+    others = [(1, _job(2, 600, 6)), (2, _job(3, 2500, 10)), (3, _job(4, 900, 5))]
+    (alone,), _ = _run(lmrs, [a])
+    mixed, stats = _run(lmrs, [others[0], a, others[1], others[2]])
+    info_a, res_a = mixed[1]
+    assert info_a.steps == alone[0].steps == 4
+    p0 = a[1][0]
+    assert normwise_rel(res_a - p0, alone[1] - p0) <= 1e-3  # the update agrees up to summation order
+    assert info_a.loss == pytest.approx(alone[0].loss, rel=1e-4)
+    assert stats.finished == 4 and stats.iterations >= 4
+    for info, res in mixed:
+        assert info.t_submit <= info.t_admit <= info.t_done and np.isfinite(res).all()
+
+
+def test_fifo_admission_under_budget():
+    from paper_2504_12905_gb300 import lmrs
+    jobs = [(k, _job(10 + k, 1200, 6)) for k in range(4)]
+    est = lmrs.lmrs_footprint_bytes(_cfg(lmrs, 0), 1200, 6, 64, 64, 3)
+    budget = int(1.5 * est)  # room for one job at a time
+    out, stats = _run(lmrs, jobs, budget=budget, max_steps=2)
+    for (i0, _), (i1, _) in zip(out, out[1:]):
+        assert i1.t_admit >= i0.t_done  # the next job waited for the previous one
+    assert stats.bytes_peak <= budget
+    for info, _ in out:
+        assert info.footprint_est == est and 0 < info.footprint_peak <= est
+
+
+def test_convergence_rule():
+    from paper_2504_12905_gb300 import lmrs
+    (info, _), = _run(lmrs, [(0, _job(20, 800, 5))], target_loss=1e9, max_steps=50)[0]
+    assert info.converged == 1 and info.steps == 1
+    (info, _), = _run(lmrs, [(0, _job(20, 800, 5))], target_loss=0.0, max_steps=3)[0]
+    assert info.converged == 0 and info.steps == 3
+
+
+def test_submit_rejections():
+    from paper_2504_12905_gb300 import lmrs
+    p, c, t = _job(30, 500, 4)
+    srv = lmrs.lmrs_server_create(1 << 20, max_active=4, setup_threads=1)  # 1 MiB: no job fits
+    try:
+        with pytest.raises(lmrs.LmrsError) as e:
+            lmrs.lmrs_server_submit(srv, _cfg(lmrs, 1), 500, p, c, t, views_per_step=2, max_steps=2)
+        assert e.value.status == 7
+        bad = _cfg(lmrs, 1)
+        bad.tile_w = 64  # 64 x 16 > 256 pixels
+        with pytest.raises(lmrs.LmrsError) as e:
+            lmrs.lmrs_server_submit(srv, bad, 500, p, c, t, views_per_step=2, max_steps=2)
+        assert e.value.status == 1
+    finally:
+        lmrs.lmrs_server_destroy(srv)
