@@ -163,6 +163,17 @@ void launch_sorted_counts(const Ctx& c, cudaStream_t st);
 // one (slot * T + tile, Gaussian) entry per overlapped tile, in depth order
 void launch_emit(const Ctx& c, cudaStream_t st);
 size_t radix_tmp_bytes(long long n);
+// Direct stable binning of the depth-sorted pairs into the tile lists
+// (c.ids, c.ranges) for views of at most kBinMaxTiles tiles: entry counts per
+// (slot, tile, chunk) into mat (bin_mat_elems) with the exact total in
+// *total, the exclusive scan of mat (its 32-bit total in *total32), then the
+// placement and the tile ranges.
+constexpr int kBinMaxTiles = 8192;
+size_t bin_mat_elems(const Ctx& c);
+size_t bin_scan_tmp_bytes(long long n);
+void launch_bin_count(const Ctx& c, unsigned* mat, unsigned long long* total, cudaStream_t st);
+void scan_bin_mat(unsigned* mat, long long n, unsigned* total32, void* tmp, cudaStream_t st);
+void launch_bin_place(const Ctx& c, const unsigned* mat, const unsigned* total32, cudaStream_t st);
 // Stable LSD radix sort of (keys, vals) on the low `bits` key bits.
 // Result ends in keys/vals (the alternate buffers are scratch).
 void radix_sort(unsigned long long* keys, unsigned int* vals, unsigned long long* keys_alt, unsigned int* vals_alt,

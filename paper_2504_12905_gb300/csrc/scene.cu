@@ -80,7 +80,7 @@ struct lmrs_scene {
     DevBuf keys, ids, keys_alt, ids_alt, ranges, scan_tmp, radix_tmp, total;
     DevBuf tile_off, off, wtile, work;
     DevBuf item_cost, work_sorted, okeys, ovals, okeys_alt, ovals_alt, otmp;
-    DevBuf cids, clen;
+    DevBuf cids, clen, binmat, bintmp;
     int max_items = 1;
     DevBuf resid, cacheC, cacheT, cacheCh, cacheTh, cacheN;
     DevBuf x, r, z, p, Ap, minv, D, b, stage_a, stage_b;
@@ -102,7 +102,7 @@ struct lmrs_scene {
         return {&params, &cams, &views, &gcache, &rec, &rect, &dkeys, &dvals, &dkeys_alt, &dvals_alt, &dtmp, &cnt,
                 &cot, &gram, &keys, &ids, &keys_alt, &ids_alt, &ranges, &scan_tmp, &radix_tmp, &total, &tile_off,
                 &off, &wtile, &work, &item_cost, &work_sorted, &okeys, &ovals, &okeys_alt, &ovals_alt, &otmp,
-                &cids, &clen, &resid, &cacheC, &cacheT, &cacheCh, &cacheTh, &cacheN, &x, &r, &z, &p, &Ap,
+                &cids, &clen, &binmat, &bintmp, &resid, &cacheC, &cacheT, &cacheCh, &cacheTh, &cacheN, &x, &r, &z, &p, &Ap,
                 &minv, &D, &b, &stage_a, &stage_b, &sc, &partials, &counter};
     }
 
@@ -514,7 +514,7 @@ lmrs_status lmrs_scene_create(const lmrs_config* cfg, int64_t n_gauss, const flo
     take(s->sc, sizeof(Scalars));
     take(s->partials, sizeof(double) * kMaxPartials);
     take(s->counter, sizeof(unsigned int) * 4);
-    take(s->total, sizeof(unsigned long long) * 2);
+    take(s->total, sizeof(unsigned long long) * 4);
     if (rc != LMRS_OK) {
         lmrs_scene_destroy(s);
         return rc;
@@ -594,14 +594,19 @@ lmrs_status lmrs_preprocess(lmrs_scene* s, const int32_t* view_ids, int32_t n_vi
     TRY(ensure(s, s->dvals, sizeof(unsigned int) * pairs));
     TRY(ensure(s, s->dvals_alt, sizeof(unsigned int) * pairs));
     TRY(ensure(s, s->dtmp, radix_tmp_bytes((long long)pairs)));
-    TRY(ensure(s, s->cnt, sizeof(unsigned long long) * pairs));
     TRY(ensure(s, s->cot, sizeof(float) * kCotF * pairs));
     TRY(ensure(s, s->ranges, sizeof(int2) * (size_t)s->nv * s->T));
-    TRY(ensure(s, s->scan_tmp, scan_u64_tmp_bytes((long long)pairs)));
+    // tile lists: direct binning, or entry emission + tile sort for views
+    // with more tiles than the binning's shared counters hold
+    const bool direct = s->T <= kBinMaxTiles;
+    if (!direct) {
+        TRY(ensure(s, s->cnt, sizeof(unsigned long long) * pairs));
+        TRY(ensure(s, s->scan_tmp, scan_u64_tmp_bytes((long long)pairs)));
+    }
     TRY(build_layout(s));
     CK(s, cudaMemcpyAsync(s->views.p, s->views_h.data(), sizeof(int) * n_views, cudaMemcpyHostToDevice, s->st));
     Ctx c = s->ctx();
-    CK(s, cudaMemsetAsync(s->total.p, 0, 2 * sizeof(unsigned long long), s->st));
+    CK(s, cudaMemsetAsync(s->total.p, 0, 4 * sizeof(unsigned long long), s->st));
     launch_sample(c, lm_step, s->cfg.seed, s->st);
     launch_prep_gauss(c, s->st);
     launch_prep_fwd(c, s->st);
@@ -610,8 +615,19 @@ lmrs_status lmrs_preprocess(lmrs_scene* s, const int32_t* view_ids, int32_t n_vi
     while ((1 << sbits) < s->nv) ++sbits;
     radix_sort(c.dkeys, c.dvals, s->dkeys_alt.as<unsigned long long>(), s->dvals_alt.as<unsigned int>(),
                (long long)pairs, 32 + sbits, s->dtmp.p, s->dtmp.cap, s->st);
-    launch_sorted_counts(c, s->st);
-    scan_u64(c.cnt, (long long)pairs, s->total.as<unsigned long long>(), s->scan_tmp.p, s->scan_tmp.cap, s->st);
+    // total[0]: entries, total[1]: visible pairs, total[2]: 32-bit scan total
+    unsigned* total32 = reinterpret_cast<unsigned*>(s->total.as<unsigned long long>() + 2);
+    size_t nmat = 0;
+    if (direct) {
+        nmat = bin_mat_elems(c);
+        TRY(ensure(s, s->binmat, sizeof(unsigned) * nmat));
+        TRY(ensure(s, s->bintmp, bin_scan_tmp_bytes((long long)nmat)));
+        launch_bin_count(c, s->binmat.as<unsigned>(), s->total.as<unsigned long long>(), s->st);
+        scan_bin_mat(s->binmat.as<unsigned>(), (long long)nmat, total32, s->bintmp.p, s->st);
+    } else {
+        launch_sorted_counts(c, s->st);
+        scan_u64(c.cnt, (long long)pairs, s->total.as<unsigned long long>(), s->scan_tmp.p, s->scan_tmp.cap, s->st);
+    }
     CHECK_LAUNCH(s);
     unsigned long long tot2[2] = {0ull, 0ull};
     CK(s, cudaMemcpyAsync(tot2, s->total.p, sizeof(tot2), cudaMemcpyDeviceToHost, s->st));
@@ -621,21 +637,26 @@ lmrs_status lmrs_preprocess(lmrs_scene* s, const int32_t* view_ids, int32_t n_vi
     if (total >= (1ull << 31)) return fail(s, LMRS_ERR_BUDGET, "more than 2^31 (view, tile, Gaussian) pairs");
     s->npairs = (long long)total;
     const size_t np = std::max<size_t>((size_t)total, 1);
-    TRY(ensure(s, s->keys, sizeof(unsigned int) * np));
-    TRY(ensure(s, s->keys_alt, sizeof(unsigned int) * np));
     TRY(ensure(s, s->ids, sizeof(unsigned int) * np));
-    TRY(ensure(s, s->ids_alt, sizeof(unsigned int) * np));
-    TRY(ensure(s, s->radix_tmp, radix_tmp_bytes((long long)np)));
     TRY(ensure(s, s->cids, sizeof(unsigned int) * np * (size_t)s->max_items));
-    c = s->ctx();
-    // level 2: entries in depth order, then a stable sort on the (slot, tile) bits
-    launch_emit(c, s->st);
-    int vbits = 0;
-    while ((1ll << vbits) < (long long)s->nv * s->T) ++vbits;
-    radix_sort32(c.keys, c.ids, s->keys_alt.as<unsigned int>(), s->ids_alt.as<unsigned int>(), s->npairs, vbits,
-                 s->radix_tmp.p, s->radix_tmp.cap, s->st);
-    CK(s, cudaMemsetAsync(s->ranges.p, 0, sizeof(int2) * (size_t)s->nv * s->T, s->st));
-    launch_ranges(c, s->st);
+    if (direct) {
+        c = s->ctx();
+        launch_bin_place(c, s->binmat.as<unsigned>(), total32, s->st);
+    } else {
+        TRY(ensure(s, s->keys, sizeof(unsigned int) * np));
+        TRY(ensure(s, s->keys_alt, sizeof(unsigned int) * np));
+        TRY(ensure(s, s->ids_alt, sizeof(unsigned int) * np));
+        TRY(ensure(s, s->radix_tmp, radix_tmp_bytes((long long)np)));
+        c = s->ctx();
+        // level 2: entries in depth order, then a stable sort on the (slot, tile) bits
+        launch_emit(c, s->st);
+        int vbits = 0;
+        while ((1ll << vbits) < (long long)s->nv * s->T) ++vbits;
+        radix_sort32(c.keys, c.ids, s->keys_alt.as<unsigned int>(), s->ids_alt.as<unsigned int>(), s->npairs, vbits,
+                     s->radix_tmp.p, s->radix_tmp.cap, s->st);
+        CK(s, cudaMemsetAsync(s->ranges.p, 0, sizeof(int2) * (size_t)s->nv * s->T, s->st));
+        launch_ranges(c, s->st);
+    }
     CHECK_LAUNCH(s);
     s->preprocessed = true;
     return LMRS_OK;

@@ -88,3 +88,26 @@ def group_errors(pair, gpu, ref):
         d = np.linalg.norm(r[k])
         out[k] = np.linalg.norm(g[k] - r[k]) / max(d, 1e-3 * tot, 1e-300)
     return out
+
+
+def flagged_contribution(pair, v):
+    """J^T W J v restricted to the samples the oracle flags as near one of the
+    per-pixel compositing decisions (alpha >= 1/255, T < 1e-4 of Eq. 4): an
+    FP32 evaluation may legitimately decide those differently, so their whole
+    contribution bounds the extra difference they can cause."""
+    _, _, flags = pair.orc.render_samples()
+    w = pair.orc.samples()["w"]
+    u = pair.orc.jvp(np.asarray(v, np.float64)) * (w * (flags != 0))[:, None]
+    return pair.orc.vjp(u)
+
+
+def assert_groups_close(pair, got, ref, tol, slack=None):
+    """Per parameter group: |got - ref| <= tol max(|ref|, 1e-3 |ref_total|)
+    + 2 |slack| (slack: a P-vector, e.g. flagged_contribution)."""
+    g, r = pair.groups(got), pair.groups(ref)
+    sl = pair.groups(slack) if slack is not None else None
+    tot = np.linalg.norm(ref)
+    for k in GROUPS:
+        err = np.linalg.norm(g[k] - r[k])
+        allow = tol * max(np.linalg.norm(r[k]), 1e-3 * tot) + (2.0 * np.linalg.norm(sl[k]) if sl else 0.0)
+        assert err <= allow, f"{k}: {err:.3e} > {allow:.3e}"
