@@ -18,7 +18,9 @@ constexpr int kRecF4 = 6;                   // float4 per (view, Gaussian) recor
 constexpr int kCotF = 12;                   // floats per (view, Gaussian) cotangent slot (9 used)
 constexpr int kGramF = 40;                  // floats per (view, Gaussian) Gram slot
 constexpr int kMaxPartials = 4096;          // block partials of the FP64 reductions
-constexpr int kGaussF4 = 9;                 // float4 planes of the per-Gaussian cache
+constexpr int kGaussF4 = 9;                  // float4 planes of the per-Gaussian cache
+// float4 planes of the per-pair Jacobian cache for SH degree 0..3
+__host__ __device__ constexpr int jac_f4(int deg) { return deg == 0 ? 10 : deg == 1 ? 13 : deg == 2 ? 14 : 16; }
 
 // Camera as the kernels read it.  R, t, fx, fy, cx, cy, limx, limy, znear are
 // the FP32 values the list decisions use.
@@ -68,6 +70,8 @@ struct Ctx {
     // per (slot, Gaussian) pair, index slot * G + g
     float4* gcache;         // per Gaussian, kGaussF4 planes of G float4 (view-independent 3D state)
     float4* rec;            // kRecF4 float4: primal (3) then tangent (3)
+    float4* pjac;           // per (view, Gaussian) pair: jac_f4(deg) planes of nv*G float4, the Jacobian
+                            // of the pair's 9 screen-space features w.r.t. the Gaussian's parameters
     int4* rect;             // inclusive tile rectangle, x0 > x1 when culled
     unsigned long long* dkeys;  // (slot << 32 | depth bits, or all ones when culled), sorted in place
     unsigned int* dvals;        // Gaussian index of each depth key

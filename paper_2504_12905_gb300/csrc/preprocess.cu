@@ -589,6 +589,87 @@ __global__ void k_sample(Ctx c, long long lm_step, unsigned long long seed) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Per-pair Jacobian cache.  Within one LM step the map from a Gaussian's
+// parameter tangent to the tangent of its 9 screen-space features in one view
+// is linear and fixed, so it is formed once per step (from the verified
+// tangent code on unit tangents) and the derivative kernels of every PCG
+// iteration read it instead of redoing the projection and SH derivatives.
+// Layout (floats; jac_f4(DEG) float4 planes of nv*G pairs):
+//   [0, 6)    d(mu_x, mu_y) / dX                     (row-major 2 x 3)
+//   [6, 36)   d(A, B, C) / d(X, log-scale, q)        (row-major 3 x 10)
+//   [36]      d o / d logit = o (1 - o)
+//   [37]      bit ch set: colour channel ch not clamped
+//   [38, 47)  d colour / dX through the view direction (row-major 3 x 3, DEG > 0)
+//   [47, 47 + K)  SH basis Y_k(view direction)       (DEG > 0; Y_0 only for DEG 0)
+// ---------------------------------------------------------------------------
+template <int DEG>
+struct Jac {
+    static constexpr int F4 = jac_f4(DEG);
+    static constexpr int N = 4 * F4;
+    static constexpr int kMu = 0, kCon = 6, kOp = 36, kMask = 37, kGx = 38, kY = 47;
+};
+
+template <int DEG>
+__device__ __forceinline__ void pair_jacobian(const Prim& P, const CamDev& cam, const float* sh, float* J) {
+    using L = Jac<DEG>;
+#pragma unroll
+    for (int k = 0; k < L::N; ++k) J[k] = 0.f;
+#pragma unroll
+    for (int col = 0; col < 10; ++col) {
+        GTan d;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            d.X[k] = col == k ? 1.f : 0.f;
+            d.ls[k] = col == 3 + k ? 1.f : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) d.q[k] = col == 6 + k ? 1.f : 0.f;
+        d.th = 0.f;
+        float out[9];
+        prim_tangent<DEG, false>(P, cam, d, sh, nullptr, out);
+        if (col < 3) {
+            J[L::kMu + col] = out[0];
+            J[L::kMu + 3 + col] = out[1];
+            if (DEG > 0) {
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) J[L::kGx + 3 * ch + col] = out[6 + ch];
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 3; ++r) J[L::kCon + 10 * r + col] = out[2 + r];
+    }
+    J[L::kOp] = P.o * (1.f - P.o);
+    unsigned bits = 0u;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch)
+        if (!P.clamped[ch]) bits |= 1u << ch;
+    J[L::kMask] = __uint_as_float(bits);
+    if (DEG > 0) {
+        float Y[Sh<DEG>::K];
+        sh_eval<DEG>(P.dir[0], P.dir[1], P.dir[2], Y);
+#pragma unroll
+        for (int k = 0; k < Sh<DEG>::K; ++k) J[L::kY + k] = Y[k];
+    }
+}
+
+template <int DEG>
+__device__ __forceinline__ void load_jac(const Ctx& c, long long pair, float* J) {
+    const long long np = (long long)c.nv * c.G;
+#pragma unroll
+    for (int q = 0; q < Jac<DEG>::F4; ++q) {
+        const float4 v = c.pjac[q * np + pair];
+        J[4 * q] = v.x; J[4 * q + 1] = v.y; J[4 * q + 2] = v.z; J[4 * q + 3] = v.w;
+    }
+}
+
+// Y_k of the pair (the constant Y_0 for DEG 0)
+template <int DEG>
+__device__ __forceinline__ float jac_Y(const float* J, int k) {
+    if (DEG == 0) return c_sh[0];
+    return J[Jac<DEG>::kY + k];
+}
+
 template <int DEG>
 __global__ void k_prep_fwd(Ctx c) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -620,6 +701,11 @@ __global__ void k_prep_fwd(Ctx c) {
     r[2] = make_float4(P.col[2], 0.f, 0.f, 0.f);
     c.rect[i] = rect;
     c.dkeys[i] = ((unsigned long long)slot << 32) | __float_as_uint(depth);
+    float J[Jac<DEG>::N];
+    pair_jacobian<DEG>(P, cam, sh, J);
+    const long long np = (long long)c.nv * c.G;
+#pragma unroll
+    for (int q = 0; q < Jac<DEG>::F4; ++q) c.pjac[q * np + i] = make_float4(J[4 * q], J[4 * q + 1], J[4 * q + 2], J[4 * q + 3]);
 }
 
 // Primal state of a visible pair for the derivative kernels.
@@ -649,23 +735,42 @@ __device__ __forceinline__ void load_geo_tangent(const float* v, int G, int g, G
 // clears the pair's cotangent slot.
 template <int DEG>
 __device__ __forceinline__ void prep_jvp_pair(const Ctx& c, const float* v, long long i) {
+    using L = Jac<DEG>;
     const int g = (int)(i / c.nv), slot = (int)(i - (long long)g * c.nv);
     const long long pair = (long long)slot * c.G + g;
     const int4 rc = c.rect[pair];
     if (rc.x > rc.y) return;
-    constexpr int K3 = 3 * Sh<DEG>::K;
+    constexpr int K = Sh<DEG>::K;
+    float J[L::N];
+    load_jac<DEG>(c, pair, J);
     GTan d;
     load_geo_tangent(v, c.G, g, d);
-    const float* dsh = v + 11ll * c.G + (long long)g * K3;
-    const float* sh = c.params + 11ll * c.G + (long long)g * K3;
-    float X[3];
-    load_mean(c.params, g, X);
-    Prim P;
-    load_gauss(c, g, P);
-    const CamDev& cam = c.cams[c.views[slot]];
-    pair_primal<DEG>(c, cam, X, sh, P);
+    const float* dsh = v + 11ll * c.G + (long long)g * 3 * K;
+    const float u[10] = {d.X[0], d.X[1], d.X[2], d.ls[0], d.ls[1], d.ls[2], d.q[0], d.q[1], d.q[2], d.q[3]};
     float o[9];
-    prim_tangent<DEG, true>(P, cam, d, sh, dsh, o);
+    o[0] = J[L::kMu] * d.X[0] + J[L::kMu + 1] * d.X[1] + J[L::kMu + 2] * d.X[2];
+    o[1] = J[L::kMu + 3] * d.X[0] + J[L::kMu + 4] * d.X[1] + J[L::kMu + 5] * d.X[2];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        float a = 0.f;
+#pragma unroll
+        for (int k = 0; k < 10; ++k) a += J[L::kCon + 10 * r + k] * u[k];
+        o[2 + r] = a;
+    }
+    o[5] = J[L::kOp] * d.th;
+    const unsigned bits = __float_as_uint(J[L::kMask]);
+    float v3[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float y = jac_Y<DEG>(J, k);
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) v3[ch] += y * dsh[3 * k + ch];
+    }
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        if (DEG > 0) v3[ch] += J[L::kGx + 3 * ch] * d.X[0] + J[L::kGx + 3 * ch + 1] * d.X[1] + J[L::kGx + 3 * ch + 2] * d.X[2];
+        o[6 + ch] = (bits >> ch) & 1u ? v3[ch] : 0.f;
+    }
     float4* r = c.rec + pair * kRecF4;
     r[3] = make_float4(o[0], o[1], o[2], o[3]);
     r[4] = make_float4(o[4], o[5], o[6], o[7]);
@@ -698,47 +803,64 @@ constexpr int kPrepBlock = 128;
 template <int DEG, bool kDot>
 __device__ __forceinline__ void prep_vjp_gauss(const Ctx& c, int g, float* out, const float* v, const float* D,
                                                Dot2& dot) {
-    constexpr int K3 = 3 * Sh<DEG>::K;
-    {
-        float X[3], sh[K3];  // held in registers across the view loop
-        load_mean(c.params, g, X);
-        load_sh<DEG>(c.params, c.G, g, sh);
-        Prim P;
-        load_gauss(c, g, P);
-        float gX[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, gth = 0.f;
-        float gsh[K3];
+    using L = Jac<DEG>;
+    constexpr int K = Sh<DEG>::K;
+    constexpr int K3 = 3 * K;
+    float gu[10];  // X, log-scale, q
 #pragma unroll
-        for (int k = 0; k < K3; ++k) gsh[k] = 0.f;
-        for (int slot = 0; slot < c.nv; ++slot) {
-            const long long i = (long long)slot * c.G + g;
-            const int4 rc = c.rect[i];
-            if (rc.x > rc.y) continue;
-            const CamDev& cam = c.cams[c.views[slot]];
-            pair_primal<DEG>(c, cam, X, sh, P);
-            const float4* ct = reinterpret_cast<const float4*>(c.cot + i * kCotF);
-            const float4 c0 = ct[0], c1 = ct[1], c2 = ct[2];
-            const float cot[9] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, c2.x};
-            prim_adjoint<DEG>(P, cam, cot, sh, gX, gls, gq, &gth, gsh);
+    for (int k = 0; k < 10; ++k) gu[k] = 0.f;
+    float gth = 0.f;
+    float gsh[K3];
+#pragma unroll
+    for (int k = 0; k < K3; ++k) gsh[k] = 0.f;
+    for (int slot = 0; slot < c.nv; ++slot) {
+        const long long i = (long long)slot * c.G + g;
+        const int4 rc = c.rect[i];
+        if (rc.x > rc.y) continue;
+        float J[L::N];
+        load_jac<DEG>(c, i, J);
+        const float4* ct = reinterpret_cast<const float4*>(c.cot + i * kCotF);
+        const float4 c0 = ct[0], c1 = ct[1], c2 = ct[2];
+        const float cot[9] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, c2.x};
+        const unsigned bits = __float_as_uint(J[L::kMask]);
+        float ccol[3];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) ccol[ch] = (bits >> ch) & 1u ? cot[6 + ch] : 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float a = J[L::kMu + k] * cot[0] + J[L::kMu + 3 + k] * cot[1];
+            if (DEG > 0) a += J[L::kGx + k] * ccol[0] + J[L::kGx + 3 + k] * ccol[1] + J[L::kGx + 6 + k] * ccol[2];
+            gu[k] += a;
         }
-        const long long G = c.G;
-        auto put = [&](long long idx, float val) {
-            if (v) {
-                const float damp = c.damping_mode == 1 ? c.lambda * D[idx] : c.lambda;
-                val += damp * v[idx];
-                if (kDot) dot.add(v[idx], val);
-            }
-            out[idx] = val;
-        };
 #pragma unroll
-        for (int k = 0; k < 3; ++k) put(3ll * g + k, gX[k]);
+        for (int k = 0; k < 10; ++k)
+            gu[k] += J[L::kCon + k] * cot[2] + J[L::kCon + 10 + k] * cot[3] + J[L::kCon + 20 + k] * cot[4];
+        gth += J[L::kOp] * cot[5];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) put(3 * G + 3ll * g + k, gls[k]);
+        for (int k = 0; k < K; ++k) {
+            const float y = jac_Y<DEG>(J, k);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) put(6 * G + 4ll * g + k, gq[k]);
-        put(10 * G + g, gth);
-#pragma unroll
-        for (int k = 0; k < K3; ++k) put(11 * G + (long long)g * K3 + k, gsh[k]);
+            for (int ch = 0; ch < 3; ++ch) gsh[3 * k + ch] += y * ccol[ch];
+        }
     }
+    const long long G = c.G;
+    auto put = [&](long long idx, float val) {
+        if (v) {
+            const float damp = c.damping_mode == 1 ? c.lambda * D[idx] : c.lambda;
+            val += damp * v[idx];
+            if (kDot) dot.add(v[idx], val);
+        }
+        out[idx] = val;
+    };
+#pragma unroll
+    for (int k = 0; k < 3; ++k) put(3ll * g + k, gu[k]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) put(3 * G + 3ll * g + k, gu[3 + k]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) put(6 * G + 4ll * g + k, gu[6 + k]);
+    put(10 * G + g, gth);
+#pragma unroll
+    for (int k = 0; k < K3; ++k) put(11 * G + (long long)g * K3 + k, gsh[k]);
 }
 
 template <int DEG, bool kDot>
@@ -805,15 +927,11 @@ __device__ __forceinline__ float gram_quad(const float* gm, const float a[9]) {
 
 template <int DEG>
 __global__ void __launch_bounds__(kPrepBlock) k_prep_diag(Ctx c, float* D) {
+    using L = Jac<DEG>;
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= c.G) return;
     constexpr int K = Sh<DEG>::K;
     constexpr int K3 = 3 * K;
-    float X[3];
-    load_mean(c.params, g, X);
-    const float* sh = c.params + 11ll * c.G + (long long)g * K3;
-    Prim P;
-    load_gauss(c, g, P);
     float dgeo[11];
 #pragma unroll
     for (int j = 0; j < 11; ++j) dgeo[j] = 0.f;
@@ -824,8 +942,8 @@ __global__ void __launch_bounds__(kPrepBlock) k_prep_diag(Ctx c, float* D) {
         const long long i = (long long)slot * c.G + g;
         const int4 rc = c.rect[i];
         if (rc.x > rc.y) continue;
-        const CamDev& cam = c.cams[c.views[slot]];
-        pair_primal<DEG>(c, cam, X, sh, P);
+        float J[L::N];
+        load_jac<DEG>(c, i, J);
         float gm[kGramF];
         const float4* gsrc = reinterpret_cast<const float4*>(c.gram + i * kGramF);
 #pragma unroll
@@ -833,27 +951,28 @@ __global__ void __launch_bounds__(kPrepBlock) k_prep_diag(Ctx c, float* D) {
             const float4 q = gsrc[k];
             gm[4 * k] = q.x; gm[4 * k + 1] = q.y; gm[4 * k + 2] = q.z; gm[4 * k + 3] = q.w;
         }
-        // geometric parameters: one unit tangent each
-#pragma unroll 1
+        // geometric parameter j: the feature tangent is column j of the Jacobian
+#pragma unroll
         for (int j = 0; j < 11; ++j) {
-            GTan d;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) { d.X[k] = j == k ? 1.f : 0.f; d.ls[k] = j == 3 + k ? 1.f : 0.f; }
-#pragma unroll
-            for (int k = 0; k < 4; ++k) d.q[k] = j == 6 + k ? 1.f : 0.f;
-            d.th = j == 10 ? 1.f : 0.f;
             float a[9];
-            prim_tangent<DEG, false>(P, cam, d, sh, nullptr, a);
+            a[0] = j < 3 ? J[L::kMu + j] : 0.f;
+            a[1] = j < 3 ? J[L::kMu + 3 + j] : 0.f;
+#pragma unroll
+            for (int r = 0; r < 3; ++r) a[2 + r] = j < 10 ? J[L::kCon + 10 * r + j] : 0.f;
+            a[5] = j == 10 ? J[L::kOp] : 0.f;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) a[6 + ch] = (DEG > 0 && j < 3) ? J[L::kGx + 3 * ch + j] : 0.f;
             dgeo[j] += gram_quad(gm, a);
         }
         // SH coefficient (k, ch) moves only colour ch, by Y_k
-        float Y[K];
-        sh_eval<DEG>(P.dir[0], P.dir[1], P.dir[2], Y);
+        const unsigned bits = __float_as_uint(J[L::kMask]);
 #pragma unroll
-        for (int k = 0; k < K; ++k)
+        for (int k = 0; k < K; ++k) {
+            const float y = jac_Y<DEG>(J, k);
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch)
-                if (!P.clamped[ch]) dsh[3 * k + ch] += gm[39] * Y[k] * Y[k];
+                if ((bits >> ch) & 1u) dsh[3 * k + ch] += gm[39] * y * y;
+        }
     }
     const long long G = c.G;
 #pragma unroll
@@ -866,8 +985,6 @@ __global__ void __launch_bounds__(kPrepBlock) k_prep_diag(Ctx c, float* D) {
 #pragma unroll
     for (int k = 0; k < K3; ++k) D[11 * G + (long long)g * K3 + k] = dsh[k];
 }
-
-
 
 // ---------------------------------------------------------------------------
 // Launchers (dispatch on the SH degree)

@@ -75,7 +75,7 @@ struct lmrs_scene {
     std::string err;
     const float* targets = nullptr;
     // device state
-    DevBuf params, cams, views, gcache;
+    DevBuf params, cams, views, gcache, pjac;
     DevBuf rec, rect, dkeys, dvals, dkeys_alt, dvals_alt, dtmp, cnt, cot, gram;
     DevBuf keys, ids, keys_alt, ids_alt, ranges, scan_tmp, radix_tmp, total;
     DevBuf tile_off, off, wtile, work;
@@ -99,7 +99,7 @@ struct lmrs_scene {
 
     // every device buffer the scene owns
     std::vector<DevBuf*> bufs() {
-        return {&params, &cams, &views, &gcache, &rec, &rect, &dkeys, &dvals, &dkeys_alt, &dvals_alt, &dtmp, &cnt,
+        return {&params, &cams, &views, &gcache, &pjac, &rec, &rect, &dkeys, &dvals, &dkeys_alt, &dvals_alt, &dtmp, &cnt,
                 &cot, &gram, &keys, &ids, &keys_alt, &ids_alt, &ranges, &scan_tmp, &radix_tmp, &total, &tile_off,
                 &off, &wtile, &work, &item_cost, &work_sorted, &okeys, &ovals, &okeys_alt, &ovals_alt, &otmp,
                 &cids, &clen, &binmat, &bintmp, &resid, &cacheC, &cacheT, &cacheCh, &cacheTh, &cacheN, &x, &r, &z, &p, &Ap,
@@ -121,6 +121,7 @@ struct lmrs_scene {
         c.targets = targets;
         c.gcache = gcache.as<float4>();
         c.rec = rec.as<float4>();
+        c.pjac = pjac.as<float4>();
         c.rect = rect.as<int4>();
         c.dkeys = dkeys.as<unsigned long long>();
         c.dvals = dvals.as<unsigned int>();
@@ -588,6 +589,7 @@ lmrs_status lmrs_preprocess(lmrs_scene* s, const int32_t* view_ids, int32_t n_vi
     const size_t pairs = (size_t)s->nv * s->G;
     TRY(ensure(s, s->views, sizeof(int) * n_views));
     TRY(ensure(s, s->rec, sizeof(float4) * kRecF4 * pairs));
+    TRY(ensure(s, s->pjac, sizeof(float4) * jac_f4(s->deg) * pairs));
     TRY(ensure(s, s->rect, sizeof(int4) * pairs));
     TRY(ensure(s, s->dkeys, sizeof(unsigned long long) * pairs));
     TRY(ensure(s, s->dkeys_alt, sizeof(unsigned long long) * pairs));
@@ -928,9 +930,10 @@ int64_t lmrs_footprint_bytes(const lmrs_config* cfg, int64_t n_gauss, int32_t n_
         max_items = std::max(max_items, (k + 31) / 32);
     }
     const double pairs = nv * G, entries = tpp * pairs, S = nv * S_view, items = nv * items_view;
-    // rec 96, rect 16, depth keys/values and their alternates 24, counts 8,
-    // cotangent slots 48, Gram blocks 160; scan and sort scratch ~2
-    const double per_pair = 96 + 16 + 24 + 8 + 48 + 160 + 2;
+    // rec 96, Jacobian cache, rect 16, depth keys/values and their
+    // alternates 24, counts 8, cotangent slots 48, Gram blocks 160; scan and
+    // sort scratch ~2
+    const double per_pair = 96 + 16.0 * jac_f4(cfg->sh_degree) + 16 + 24 + 8 + 48 + 160 + 2;
     // keys, ids and their alternates 16, compact lists 4 per work item of a tile
     const double per_entry = 16 + 4.0 * max_items + 1;
     // offset 1, residual 12, FP32 and BF16 caches 12 + 4 + 6 + 2, stop index 4
