@@ -333,6 +333,10 @@ lmrs_status lmrs_server_destroy(lmrs_server* srv);
  * headroom on the per-step parts. */
 int64_t lmrs_footprint_bytes(const lmrs_config* cfg, int64_t n_gauss, int32_t n_cams, int32_t width, int32_t height,
                              int32_t views_per_step, double tiles_per_pair);
+/* (sample, Gaussian) pairs composited before termination by the last
+ * lmrs_render (alpha >= 1/255 and T still >= 1e-4, Eq. 4): the evaluations
+ * each J v and J^T u application repeats.  -1 before a render. */
+int64_t lmrs_num_evaluations(lmrs_scene* scene);
 /* Device bytes the scene holds now. */
 int64_t lmrs_scene_device_bytes(const lmrs_scene* scene);
 

@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(kVecBlock) k_lm_update(Ctx c, long long lm_ste
 // they are used.  The history arrays start at zero.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kBatchBlock) kb_precond_init(BatchTables t) {
-    const int n = t.counts[2];
+    const int n = t.counts[1];
     for (int k = blockIdx.x; k < n; k += gridDim.x) {
         const int4 ch = t.vchunks[k];
         const Ctx& c = t.ctxs[ch.x];
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(kBatchBlock) kb_precond_init(BatchTables t) {
 }
 
 __global__ void __launch_bounds__(kBatchBlock) kb_direction(BatchTables t, int iter) {
-    const int n = t.counts[2];
+    const int n = t.counts[1];
     for (int k = blockIdx.x; k < n; k += gridDim.x) {
         const int4 ch = t.vchunks[k];
         const BatchVec& bv = t.vecs[ch.x];
@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(kBatchBlock) kb_direction(BatchTables t, int i
 }
 
 __global__ void __launch_bounds__(kBatchBlock) kb_update(BatchTables t, int iter) {
-    const int n = t.counts[2];
+    const int n = t.counts[1];
     for (int k = blockIdx.x; k < n; k += gridDim.x) {
         const int4 ch = t.vchunks[k];
         const Ctx& c = t.ctxs[ch.x];
@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(kBatchBlock) kb_max_dc(BatchTables t) {
 }
 
 __global__ void __launch_bounds__(kBatchBlock) kb_lm_update(BatchTables t) {
-    const int n = t.counts[2];
+    const int n = t.counts[1];
     for (int k = blockIdx.x; k < n; k += gridDim.x) {
         const int4 ch = t.vchunks[k];
         const Ctx& c = t.ctxs[ch.x];

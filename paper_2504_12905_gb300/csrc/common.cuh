@@ -14,7 +14,9 @@ constexpr int kMaxShCoeffs = 16;
 constexpr float kAlphaMin = 1.0f / 255.0f;  // skip threshold
 constexpr float kAlphaMax = 0.99f;          // alpha clamp
 constexpr float kTMin = 1e-4f;              // termination threshold
-constexpr int kRecF4 = 6;                   // float4 per (view, Gaussian) record
+constexpr int kRecF4 = 6;                   // float4 per staged (view, Gaussian) record: primal, tangent
+constexpr int kPrimF4 = 3;                  // float4 of a pair's primal 2D features
+constexpr int kTanF4 = 3;                   // float4 of a pair's 2D feature tangent
 constexpr int kCotF = 12;                   // floats per (view, Gaussian) cotangent slot (9 used)
 constexpr int kGramF = 40;                  // floats per (view, Gaussian) Gram slot
 constexpr int kMaxPartials = 4096;          // block partials of the FP64 reductions
@@ -50,6 +52,7 @@ struct Scalars {
     // LM step
     double loss_num;  // sum w |r|^2
     double loss_den;  // sum 3 w
+    unsigned long long n_eval;  // (sample, Gaussian) pairs composited before termination
     double eta;
     unsigned int max_dc_bits;  // bits of max |x_dc| (non-negative float)
     unsigned int pad1;
@@ -69,7 +72,8 @@ struct Ctx {
     const float* targets;   // [n_cams][H][W][3] or null
     // per (slot, Gaussian) pair, index slot * G + g
     float4* gcache;         // per Gaussian, kGaussF4 planes of G float4 (view-independent 3D state)
-    float4* rec;            // kRecF4 float4: primal (3) then tangent (3)
+    float4* rec;            // per pair kPrimF4 float4: mu_x, mu_y, A, B | C, o, r, g | b
+    float4* tan;            // per pair kTanF4 float4: the tangents of the same 9 features
     float4* pjac;           // per (view, Gaussian) pair: jac_f4(deg) planes of nv*G float4, the Jacobian
                             // of the pair's 9 screen-space features w.r.t. the Gaussian's parameters
     int4* rect;             // inclusive tile rectangle, x0 > x1 when culled
@@ -132,10 +136,9 @@ struct BatchTables {
     const Ctx* ctxs;
     const BatchVec* vecs;
     const int4* gchunks;  // Gaussians, <= kBatchBlock per chunk
-    const int4* pchunks;  // (Gaussian, view) pairs, Gaussian-major, <= kBatchBlock
     const int4* vchunks;  // P-vector entries, <= kVecChunk
     const int4* wchunks;  // raster work items, <= kBatchBlock / 32
-    const int* counts;    // [4]: number of g, p, v, w chunks
+    const int* counts;    // [3]: number of g, v, w chunks
 };
 
 // ---- launch count (every kernel launch goes through note_launch) --------

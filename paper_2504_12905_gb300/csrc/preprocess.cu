@@ -5,13 +5,16 @@
 //                   quaternion, R, M = R S, Sigma = M M^T, opacity), once per
 //                   LM step (Sec. 3, Eq. 3)
 //   k_prep_fwd      projection (Sec. 3, Eqs. 2-4): list decisions in FP32 with
-//                   a fixed operation order, 2D features, tile counts
-//   k_prep_jvp      forward-mode tangents of the 2D features (Alg. 3, the
+//                   a fixed operation order, 2D features, and the per-pair
+//                   Jacobian of the 9 features w.r.t. the Gaussian's
+//                   parameters (forward mode on unit tangents, Alg. 3)
+//   k_prep_jvp      tangents of the 2D features from the Jacobian cache (the
 //                   "preprocessing" half of the Jv kernel, App. A)
-//   k_prep_vjp      reverse mode from the per-pair 2D cotangents to the 3D
-//                   parameters (second launch of the J^T v kernel, App. A),
+//   k_prep_vjp      the transposed map from the per-pair 2D cotangents to the
+//                   3D parameters (second launch of the J^T v kernel, App. A),
 //                   plus the damping of Eq. 8 and p^T A p in FP64
-//   k_prep_diag     diag(J^T W J) from per-pair 9x9 Gram blocks (App. A "Diag")
+//   k_prep_diag     diag(J^T W J) from per-pair 9x9 Gram blocks and the
+//                   Jacobian columns (App. A "Diag")
 // Kernels are instantiated per SH degree (0..3) so coefficient arrays live
 // in registers.
 #include <cmath>
@@ -69,34 +72,6 @@ __device__ __forceinline__ void sh_eval(float x, float y, float z, float* Y) {
     Y[13] = c_sh[7] * x * (5.f * z * z - 1.f);
     Y[14] = c_sh[9] * z * (x * x - y * y);
     Y[15] = c_sh[5] * x * (x * x - 3.f * y * y);
-}
-
-// g = sum_{k>=1} w[k] grad Y_k(x, y, z)  (gradient in R^3 of the polynomial).
-template <int DEG>
-__device__ __forceinline__ void sh_weighted_grad(float x, float y, float z, const float* w, float g[3]) {
-    g[0] = g[1] = g[2] = 0.f;
-    if (DEG < 1) return;
-    const float k1 = c_sh[1];
-    g[1] += w[1] * k1;
-    g[2] += w[2] * k1;
-    g[0] += w[3] * k1;
-    if (DEG < 2) return;
-    const float k2 = c_sh[2], k20 = c_sh[3], k22 = c_sh[4];
-    g[0] += w[4] * k2 * y;  g[1] += w[4] * k2 * x;
-    g[1] += w[5] * k2 * z;  g[2] += w[5] * k2 * y;
-    g[2] += w[6] * 6.f * k20 * z;
-    g[0] += w[7] * k2 * z;  g[2] += w[7] * k2 * x;
-    g[0] += w[8] * 2.f * k22 * x;  g[1] -= w[8] * 2.f * k22 * y;
-    if (DEG < 3) return;
-    const float k33 = c_sh[5], k32a = c_sh[6], k31 = c_sh[7], k30 = c_sh[8], k32 = c_sh[9];
-    g[0] += w[9] * 6.f * k33 * x * y;
-    g[1] += w[9] * 3.f * k33 * (x * x - y * y);
-    g[0] += w[10] * k32a * y * z;  g[1] += w[10] * k32a * x * z;  g[2] += w[10] * k32a * x * y;
-    g[1] += w[11] * k31 * (5.f * z * z - 1.f);  g[2] += w[11] * 10.f * k31 * y * z;
-    g[2] += w[12] * k30 * (15.f * z * z - 3.f);
-    g[0] += w[13] * k31 * (5.f * z * z - 1.f);  g[2] += w[13] * 10.f * k31 * x * z;
-    g[0] += w[14] * 2.f * k32 * x * z;  g[1] -= w[14] * 2.f * k32 * y * z;  g[2] += w[14] * k32 * (x * x - y * y);
-    g[0] += w[15] * 3.f * k33 * (x * x - y * y);  g[1] -= w[15] * 6.f * k33 * x * y;
 }
 
 // gY[k] = grad Y_k(x, y, z) . d  (directional derivative of each basis function).
@@ -157,14 +132,6 @@ __device__ __forceinline__ float rd(float a, float b) { return __fdiv_rn(a, b); 
 __device__ __forceinline__ void load_mean(const float* p, int g, float X[3]) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) X[k] = p[3ll * g + k];
-}
-
-template <int DEG>
-__device__ __forceinline__ void load_sh(const float* p, int G, int g, float* sh) {
-    constexpr int K3 = 3 * Sh<DEG>::K;
-    const float* src = p + 11ll * G + (long long)g * K3;
-#pragma unroll
-    for (int i = 0; i < K3; ++i) sh[i] = src[i];
 }
 
 // View-independent 3D state in the fixed FP32 operation order of the list
@@ -445,115 +412,6 @@ __device__ __forceinline__ void prim_tangent(const Prim& P, const CamDev& cam, c
 }
 
 // ---------------------------------------------------------------------------
-// Reverse mode: cotangent of the 9 features -> cotangents of the 3D
-// parameters (accumulated into gX, gls, gq, gth, gsh).
-// ---------------------------------------------------------------------------
-template <int DEG>
-__device__ __forceinline__ void prim_adjoint(const Prim& P, const CamDev& cam, const float* cot, const float* sh,
-                                             float gX[3], float gls[3], float gq[4], float* gth, float* gsh) {
-    const float* W = cam.R;
-    // colour -> SH coefficients and view direction
-    constexpr int K = Sh<DEG>::K;
-    float ccol[3];
-#pragma unroll
-    for (int ch = 0; ch < 3; ++ch) ccol[ch] = P.clamped[ch] ? 0.f : cot[6 + ch];
-    float Y[K];
-    sh_eval<DEG>(P.dir[0], P.dir[1], P.dir[2], Y);
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) gsh[3 * k + ch] += ccol[ch] * Y[k];
-    if (DEG > 0) {
-        float wk[K];
-#pragma unroll
-        for (int k = 0; k < K; ++k) wk[k] = ccol[0] * sh[3 * k] + ccol[1] * sh[3 * k + 1] + ccol[2] * sh[3 * k + 2];
-        float gd[3];
-        sh_weighted_grad<DEG>(P.dir[0], P.dir[1], P.dir[2], wk, gd);
-        const float pd = P.dir[0] * gd[0] + P.dir[1] * gd[1] + P.dir[2] * gd[2];
-        const float idn = 1.f / P.dn;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) gX[k] += (gd[k] - P.dir[k] * pd) * idn;
-    }
-    // opacity
-    *gth += cot[5] * P.o * (1.f - P.o);
-    // conic -> 2D covariance (a, b, c)
-    const float idet = 1.f / P.det;
-    const float gdet = -(cot[2] * P.A + cot[3] * P.B + cot[4] * P.C) * idet;
-    const float ga = cot[4] * idet + gdet * P.c;
-    const float gb = -cot[3] * idet - 2.f * P.b * gdet;
-    const float gc = cot[2] * idet + gdet * P.a;
-    // 2D covariance -> T and Sigma:  a = T0 S T0^T, b = T0 S T1^T, c = T1 S T1^T
-    const float* T = P.T;
-    const float* V = P.V;
-    float gT[6];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        gT[k] = 2.f * ga * V[k] + gb * V[3 + k];
-        gT[3 + k] = gb * V[k] + 2.f * gc * V[3 + k];
-    }
-    float gS[9];  // full (non-symmetrised) cotangent of Sigma
-#pragma unroll
-    for (int m = 0; m < 3; ++m)
-#pragma unroll
-        for (int n = 0; n < 3; ++n) gS[3 * m + n] = ga * T[m] * T[n] + gb * T[m] * T[3 + n] + gc * T[3 + m] * T[3 + n];
-    // T = J W
-    float gj00 = 0.f, gj02 = 0.f, gj11 = 0.f, gj12 = 0.f;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        gj00 += gT[k] * W[k];
-        gj02 += gT[k] * W[6 + k];
-        gj11 += gT[3 + k] * W[3 + k];
-        gj12 += gT[3 + k] * W[6 + k];
-    }
-    const float it2 = 1.f / P.t[2];
-    float gt[3] = {0.f, 0.f, 0.f};
-    gt[2] += -(gj00 * P.j00 + gj02 * P.j02 + gj11 * P.j11 + gj12 * P.j12) * it2;
-    float gux = cot[0] * cam.fx, guy = cot[1] * cam.fy;
-    if (!P.clx) gux += -gj02 * cam.fx * it2;
-    if (!P.cly) guy += -gj12 * cam.fy * it2;
-    gt[0] += gux * it2;
-    gt[1] += guy * it2;
-    gt[2] += -(gux * P.ux + guy * P.uy) * it2;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) gX[k] += W[k] * gt[0] + W[3 + k] * gt[1] + W[6 + k] * gt[2];
-    // Sigma = M M^T -> gM = (gS + gS^T) M
-    float gM[9];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            float v = 0.f;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) v += (gS[3 * i + k] + gS[3 * k + i]) * P.M[3 * k + j];
-            gM[3 * i + j] = v;
-        }
-    // M = R diag(s)
-    float gR[9];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) gR[3 * i + j] = gM[3 * i + j] * P.s[j];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        const float gs = gM[j] * P.R[j] + gM[3 + j] * P.R[3 + j] + gM[6 + j] * P.R[6 + j];
-        gls[j] += gs * P.s[j];
-    }
-    // R(qh)
-    const float w = P.qh[0], x = P.qh[1], y = P.qh[2], z = P.qh[3];
-    const float gw = 2.f * (-z * gR[1] + y * gR[2] + z * gR[3] - x * gR[5] - y * gR[6] + x * gR[7]);
-    const float gx = 2.f * (y * gR[1] + z * gR[2] + y * gR[3] - w * gR[5] + z * gR[6] + w * gR[7]) - 4.f * x * (gR[4] + gR[8]);
-    const float gy = 2.f * (x * gR[1] + w * gR[2] + x * gR[3] + z * gR[5] - w * gR[6] + z * gR[7]) - 4.f * y * (gR[0] + gR[8]);
-    const float gz = 2.f * (-w * gR[1] + x * gR[2] + w * gR[3] + y * gR[5] + x * gR[6] + y * gR[7]) - 4.f * z * (gR[0] + gR[4]);
-    // qh = q / |q|
-    const float pr = w * gw + x * gx + y * gy + z * gz;
-    const float iqn = 1.f / P.qn;
-    gq[0] += (gw - w * pr) * iqn;
-    gq[1] += (gx - x * pr) * iqn;
-    gq[2] += (gy - y * pr) * iqn;
-    gq[3] += (gz - z * pr) * iqn;
-}
-
-// ---------------------------------------------------------------------------
 // Kernels
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned long long sm64_mix(unsigned long long z) {
@@ -695,7 +553,7 @@ __global__ void k_prep_fwd(Ctx c) {
     }
     const float* sh = c.params + 11ll * c.G + (long long)g * 3 * Sh<DEG>::K;
     prim_features<DEG>(X, sh, cam, P);
-    float4* r = c.rec + i * kRecF4;
+    float4* r = c.rec + i * kPrimF4;
     r[0] = make_float4(P.mux, P.muy, P.A, P.B);
     r[1] = make_float4(P.C, P.o, P.col[0], P.col[1]);
     r[2] = make_float4(P.col[2], 0.f, 0.f, 0.f);
@@ -706,14 +564,6 @@ __global__ void k_prep_fwd(Ctx c) {
     const long long np = (long long)c.nv * c.G;
 #pragma unroll
     for (int q = 0; q < Jac<DEG>::F4; ++q) c.pjac[q * np + i] = make_float4(J[4 * q], J[4 * q + 1], J[4 * q + 2], J[4 * q + 3]);
-}
-
-// Primal state of a visible pair for the derivative kernels.
-template <int DEG>
-__device__ __forceinline__ void pair_primal(const Ctx& c, const CamDev& cam, const float X[3], const float* sh,
-                                            Prim& P) {
-    prim_project(X, cam, c.tiles_x, c.tiles_y, c.tile_w, c.tile_h, P, nullptr, nullptr);
-    prim_features<DEG>(X, sh, cam, P);
 }
 
 // tangent of the 11 geometric parameters of Gaussian g
@@ -733,66 +583,78 @@ __device__ __forceinline__ void load_geo_tangent(const float* v, int G, int g, G
 // are the views of one Gaussian, so its parameters and tangent are loaded
 // once per warp through L1).  Writes the tangent half of the pair record and
 // clears the pair's cotangent slot.
+// Tangent half of the pair records of Gaussian g in views slot0, slot0 +
+// dslot, ... (visible ones), from the Jacobian cache, and cleared cotangent
+// slots.  The lanes of a warp take consecutive Gaussians, so every plane
+// load and record store is one contiguous run.
 template <int DEG>
-__device__ __forceinline__ void prep_jvp_pair(const Ctx& c, const float* v, long long i) {
+__device__ __forceinline__ void prep_jvp_gauss(const Ctx& c, const float* v, int g, int slot0, int dslot) {
     using L = Jac<DEG>;
-    const int g = (int)(i / c.nv), slot = (int)(i - (long long)g * c.nv);
-    const long long pair = (long long)slot * c.G + g;
-    const int4 rc = c.rect[pair];
-    if (rc.x > rc.y) return;
     constexpr int K = Sh<DEG>::K;
-    float J[L::N];
-    load_jac<DEG>(c, pair, J);
     GTan d;
     load_geo_tangent(v, c.G, g, d);
-    const float* dsh = v + 11ll * c.G + (long long)g * 3 * K;
     const float u[10] = {d.X[0], d.X[1], d.X[2], d.ls[0], d.ls[1], d.ls[2], d.q[0], d.q[1], d.q[2], d.q[3]};
-    float o[9];
-    o[0] = J[L::kMu] * d.X[0] + J[L::kMu + 1] * d.X[1] + J[L::kMu + 2] * d.X[2];
-    o[1] = J[L::kMu + 3] * d.X[0] + J[L::kMu + 4] * d.X[1] + J[L::kMu + 5] * d.X[2];
+    const float* dsh = v + 11ll * c.G + (long long)g * 3 * K;
+    for (int slot = slot0; slot < c.nv; slot += dslot) {
+        const long long pair = (long long)slot * c.G + g;
+        const int4 rc = c.rect[pair];
+        if (rc.x > rc.y) continue;
+        float J[L::N];
+        load_jac<DEG>(c, pair, J);
+        float o[9];
+        o[0] = J[L::kMu] * d.X[0] + J[L::kMu + 1] * d.X[1] + J[L::kMu + 2] * d.X[2];
+        o[1] = J[L::kMu + 3] * d.X[0] + J[L::kMu + 4] * d.X[1] + J[L::kMu + 5] * d.X[2];
 #pragma unroll
-    for (int r = 0; r < 3; ++r) {
-        float a = 0.f;
+        for (int r = 0; r < 3; ++r) {
+            float a = 0.f;
 #pragma unroll
-        for (int k = 0; k < 10; ++k) a += J[L::kCon + 10 * r + k] * u[k];
-        o[2 + r] = a;
+            for (int k = 0; k < 10; ++k) a += J[L::kCon + 10 * r + k] * u[k];
+            o[2 + r] = a;
+        }
+        o[5] = J[L::kOp] * d.th;
+        const unsigned bits = __float_as_uint(J[L::kMask]);
+        float v3[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const float y = jac_Y<DEG>(J, k);
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) v3[ch] += y * dsh[3 * k + ch];
+        }
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            if (DEG > 0)
+                v3[ch] += J[L::kGx + 3 * ch] * d.X[0] + J[L::kGx + 3 * ch + 1] * d.X[1] + J[L::kGx + 3 * ch + 2] * d.X[2];
+            o[6 + ch] = (bits >> ch) & 1u ? v3[ch] : 0.f;
+        }
+        float4* r = c.tan + pair * kTanF4;
+        r[0] = make_float4(o[0], o[1], o[2], o[3]);
+        r[1] = make_float4(o[4], o[5], o[6], o[7]);
+        r[2] = make_float4(o[8], 0.f, 0.f, 0.f);
+        float4* ct = reinterpret_cast<float4*>(c.cot + pair * kCotF);
+        ct[0] = ct[1] = ct[2] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    o[5] = J[L::kOp] * d.th;
-    const unsigned bits = __float_as_uint(J[L::kMask]);
-    float v3[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const float y = jac_Y<DEG>(J, k);
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) v3[ch] += y * dsh[3 * k + ch];
-    }
-#pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-        if (DEG > 0) v3[ch] += J[L::kGx + 3 * ch] * d.X[0] + J[L::kGx + 3 * ch + 1] * d.X[1] + J[L::kGx + 3 * ch + 2] * d.X[2];
-        o[6 + ch] = (bits >> ch) & 1u ? v3[ch] : 0.f;
-    }
-    float4* r = c.rec + pair * kRecF4;
-    r[3] = make_float4(o[0], o[1], o[2], o[3]);
-    r[4] = make_float4(o[4], o[5], o[6], o[7]);
-    r[5] = make_float4(o[8], 0.f, 0.f, 0.f);
-    float4* ct = reinterpret_cast<float4*>(c.cot + pair * kCotF);
-    ct[0] = ct[1] = ct[2] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
+
+// Blocks of 32 Gaussians (lanes) x kJvpWarps warps, warp w taking views w,
+// w + kJvpWarps, ...: several warps per Gaussian for latency hiding, the
+// tangent re-read by them from the same SM's L1.
+constexpr int kJvpWarps = 4;
 
 template <int DEG>
-__global__ void k_prep_jvp(Ctx c, const float* v) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < (long long)c.nv * c.G) prep_jvp_pair<DEG>(c, v, i);
+__global__ void __launch_bounds__(32 * kJvpWarps) k_prep_jvp(Ctx c, const float* v) {
+    const int g = blockIdx.x * 32 + (threadIdx.x & 31);
+    if (g < c.G) prep_jvp_gauss<DEG>(c, v, g, threadIdx.x >> 5, kJvpWarps);
 }
 
-// The same for every scene of a batch: chunks of pairs, tangent = the scene's p.
+// The same for every scene of a batch: Gaussian chunks, tangent = the scene's p.
 template <int DEG>
 __global__ void __launch_bounds__(kBatchBlock) kb_prep_jvp(BatchTables t) {
-    const int n = t.counts[1];
+    static_assert(kBatchBlock == 32 * kJvpWarps, "one lane per Gaussian, one warp per view class");
+    const int n = t.counts[0];
     for (int k = blockIdx.x; k < n; k += gridDim.x) {
-        const int4 ch = t.pchunks[k];
-        const long long i = (long long)ch.y + threadIdx.x;
-        if (i < ch.z) prep_jvp_pair<DEG>(t.ctxs[ch.x], t.vecs[ch.x].p, i);
+        const int4 ch = t.gchunks[k];
+        for (int g = ch.y + (int)(threadIdx.x & 31); g < ch.z; g += 32)
+            prep_jvp_gauss<DEG>(t.ctxs[ch.x], t.vecs[ch.x].p, g, threadIdx.x >> 5, kJvpWarps);
     }
 }
 
@@ -1005,8 +867,7 @@ static void prep_fwd_deg(const Ctx& c, cudaStream_t st) {
 }
 template <int DEG>
 static void prep_jvp_deg(const Ctx& c, const float* v, cudaStream_t st) {
-    const long long n = (long long)c.nv * c.G;
-    LMRS_LAUNCH_AS("k_prep_jvp", k_prep_jvp<DEG>, (unsigned)((n + 127) / 128), 128, 0, st, c, v);
+    LMRS_LAUNCH_AS("k_prep_jvp", k_prep_jvp<DEG>, (unsigned)((c.G + 31) / 32), 32 * kJvpWarps, 0, st, c, v);
 }
 template <int DEG>
 static void prep_vjp_deg(const Ctx& c, float* g, const float* v, const float* D, bool dot, cudaStream_t st) {

@@ -95,9 +95,9 @@ __device__ __forceinline__ int stage_batch(const Ctx& c, int slot, const unsigne
     const int k = b + lane;
     if (k < end) {
         const unsigned id = ids[k];
-        const float4* r = c.rec + ((long long)slot * c.G + id) * kRecF4;
+        const long long pr = (long long)slot * c.G + id;
 #pragma unroll
-        for (int q = 0; q < NF4; ++q) s_rec[lane][q] = r[q];
+        for (int q = 0; q < NF4; ++q) s_rec[lane][q] = q < kPrimF4 ? c.rec[pr * kPrimF4 + q] : c.tan[pr * kTanF4 + q - kPrimF4];
         s_id[lane] = id;
     }
     __syncwarp();
@@ -111,7 +111,8 @@ __device__ __forceinline__ int stage_batch(const Ctx& c, int slot, const unsigne
 template <bool kTan, bool kCompact>
 __device__ __forceinline__ void forward_pass(const Ctx& c, const Pix& p, List L, float4 (*s_rec)[kRecF4],
                                              unsigned* s_id, float C[3], float& T, float dC[3], int& ncons,
-                                             unsigned* out_ids = nullptr, int* out_len = nullptr) {
+                                             unsigned* out_ids = nullptr, int* out_len = nullptr,
+                                             int* n_comp = nullptr) {
     const int lane = threadIdx.x & 31;
     T = 1.f;
     float dT = 0.f;
@@ -153,6 +154,7 @@ __device__ __forceinline__ void forward_pass(const Ctx& c, const Pix& p, List L,
                         C[1] += r1.w * wgt;
                         C[2] += col2 * wgt;
                         T = Tn;
+                        if (n_comp) ++*n_comp;
                     }
                 }
                 if (any) ++kept;
@@ -285,8 +287,9 @@ __global__ void __launch_bounds__(kRasterBlock) k_fwd_samples(Ctx c) {
     float C[3], T, dC[3];
     int ncons;
     int* len_out = c.clen + (long long)p.vt * c.max_items + p.chunk;
+    int n_comp = 0;
     forward_pass<false, true>(c, p, tile_list(c, p), s_rec, s_id, C, T, dC, ncons,
-                              c.cids + compact_base(c, p, rg), len_out);
+                              c.cids + compact_base(c, p, rg), len_out, &n_comp);
     double num = 0.0, den = 0.0;
     if (p.active) {
         const long long si = p.si;
@@ -318,9 +321,13 @@ __global__ void __launch_bounds__(kRasterBlock) k_fwd_samples(Ctx c) {
     if ((threadIdx.x & 31) == 0 && c.item_cost) c.item_cost[item] = *len_out;
     num = warp_sum(num);
     den = warp_sum(den);
+    unsigned long long ne = p.active ? (unsigned long long)n_comp : 0ull;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) ne += __shfl_xor_sync(kFull, ne, o);
     if ((threadIdx.x & 31) == 0) {
         atomicAdd(&c.sc->loss_num, num);
         atomicAdd(&c.sc->loss_den, den);
+        atomicAdd(&c.sc->n_eval, ne);
     }
 }
 
@@ -373,7 +380,7 @@ __global__ void __launch_bounds__(kRasterBlock) kb_jtj(BatchTables t) {
     __shared__ float4 s_rec_all[kRasterWarps][32][kRecF4];
     __shared__ unsigned s_id_all[kRasterWarps][32];
     const int wid = threadIdx.x >> 5;
-    const int n = t.counts[3];
+    const int n = t.counts[2];
     for (int k = blockIdx.x; k < n; k += gridDim.x) {
         const int4 ch = t.wchunks[k];
         const int item = ch.y + wid;

@@ -76,7 +76,7 @@ struct lmrs_scene {
     const float* targets = nullptr;
     // device state
     DevBuf params, cams, views, gcache, pjac;
-    DevBuf rec, rect, dkeys, dvals, dkeys_alt, dvals_alt, dtmp, cnt, cot, gram;
+    DevBuf rec, tan, rect, dkeys, dvals, dkeys_alt, dvals_alt, dtmp, cnt, cot, gram;
     DevBuf keys, ids, keys_alt, ids_alt, ranges, scan_tmp, radix_tmp, total;
     DevBuf tile_off, off, wtile, work;
     DevBuf item_cost, work_sorted, okeys, ovals, okeys_alt, ovals_alt, otmp;
@@ -99,7 +99,7 @@ struct lmrs_scene {
 
     // every device buffer the scene owns
     std::vector<DevBuf*> bufs() {
-        return {&params, &cams, &views, &gcache, &pjac, &rec, &rect, &dkeys, &dvals, &dkeys_alt, &dvals_alt, &dtmp, &cnt,
+        return {&params, &cams, &views, &gcache, &pjac, &rec, &tan, &rect, &dkeys, &dvals, &dkeys_alt, &dvals_alt, &dtmp, &cnt,
                 &cot, &gram, &keys, &ids, &keys_alt, &ids_alt, &ranges, &scan_tmp, &radix_tmp, &total, &tile_off,
                 &off, &wtile, &work, &item_cost, &work_sorted, &okeys, &ovals, &okeys_alt, &ovals_alt, &otmp,
                 &cids, &clen, &binmat, &bintmp, &resid, &cacheC, &cacheT, &cacheCh, &cacheTh, &cacheN, &x, &r, &z, &p, &Ap,
@@ -121,6 +121,7 @@ struct lmrs_scene {
         c.targets = targets;
         c.gcache = gcache.as<float4>();
         c.rec = rec.as<float4>();
+        c.tan = tan.as<float4>();
         c.pjac = pjac.as<float4>();
         c.rect = rect.as<int4>();
         c.dkeys = dkeys.as<unsigned long long>();
@@ -588,7 +589,8 @@ lmrs_status lmrs_preprocess(lmrs_scene* s, const int32_t* view_ids, int32_t n_vi
     s->step = lm_step;
     const size_t pairs = (size_t)s->nv * s->G;
     TRY(ensure(s, s->views, sizeof(int) * n_views));
-    TRY(ensure(s, s->rec, sizeof(float4) * kRecF4 * pairs));
+    TRY(ensure(s, s->rec, sizeof(float4) * kPrimF4 * pairs));
+    TRY(ensure(s, s->tan, sizeof(float4) * kTanF4 * pairs));
     TRY(ensure(s, s->pjac, sizeof(float4) * jac_f4(s->deg) * pairs));
     TRY(ensure(s, s->rect, sizeof(int4) * pairs));
     TRY(ensure(s, s->dkeys, sizeof(unsigned long long) * pairs));
@@ -670,7 +672,7 @@ lmrs_status lmrs_render(lmrs_scene* s, float* images_dev, float* residuals_dev) 
     TRY(need_pre(s));
     s->ordered = false;  // the forward render indexes the work items in their natural order
     Ctx c = s->ctx();
-    CK(s, cudaMemsetAsync(&c.sc->loss_num, 0, 2 * sizeof(double), s->st));
+    CK(s, cudaMemsetAsync(&c.sc->loss_num, 0, offsetof(Scalars, eta) - offsetof(Scalars, loss_num), s->st));
     launch_raster_fwd_samples(c, s->st);
     if (images_dev) launch_raster_full(c, images_dev, s->st);
     launch_order_work(c, s->okeys.as<unsigned long long>(), s->ovals.as<unsigned int>(),
@@ -950,6 +952,17 @@ int64_t lmrs_footprint_bytes(const lmrs_config* cfg, int64_t n_gauss, int32_t n_
     return (int64_t)(fixed + targets + 1.25 * var);
 }
 
+int64_t lmrs_num_evaluations(lmrs_scene* s) {
+    if (check_scene(s) != LMRS_OK || !s->rendered) return -1;
+    unsigned long long n = 0;
+    if (cudaMemcpyAsync(&n, &s->ctx().sc->n_eval, sizeof(n), cudaMemcpyDeviceToHost, s->st) != cudaSuccess ||
+        cudaStreamSynchronize(s->st) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    return (int64_t)n;
+}
+
 int64_t lmrs_scene_device_bytes(const lmrs_scene* s) {
     if (!s) return 0;
     int64_t n = 0;
@@ -969,16 +982,16 @@ struct lmrs_batch {
     bool own_stream = false;
     std::string err;
     // device tables
-    DevBuf ctxs, vecs, gch, pch, vch, wch, counts, hist;
+    DevBuf ctxs, vecs, gch, vch, wch, counts, hist;
     // host copies (kept alive while the asynchronous uploads are staged)
     std::vector<Ctx> hctx;
     std::vector<BatchVec> hvec;
-    std::vector<int4> hg, hp, hv, hw;
-    int hcounts[4] = {0, 0, 0, 0};
+    std::vector<int4> hg, hv, hw;
+    int hcounts[3] = {0, 0, 0};
     // the captured CG loop
     cudaGraphExec_t exec = nullptr;
     long long graph_kernels = 0;
-    void* graph_key[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    void* graph_key[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     std::vector<cudaEvent_t> ev_scene;
     cudaEvent_t ev_batch = nullptr;
     std::vector<lmrs_status> scene_rc;  // per scene, of the last step
@@ -1011,7 +1024,6 @@ lmrs_status batch_tables(lmrs_batch* B, const int64_t* steps) {
     B->hctx.resize(B->n);
     B->hvec.resize(B->n);
     B->hg.clear();
-    B->hp.clear();
     B->hv.clear();
     B->hw.clear();
     double* hist = B->hist.as<double>();
@@ -1038,16 +1050,13 @@ lmrs_status batch_tables(lmrs_batch* B, const int64_t* steps) {
         v.color_bound = s->cfg.color_bound;
         v.warm_iters = s->cfg.warm_iters;
         add_chunks(B->hg, i, s->G, kBatchBlock);
-        add_chunks(B->hp, i, (long long)s->nv * s->G, kBatchBlock);
         add_chunks(B->hv, i, s->P, kVecChunk);
         add_chunks(B->hw, i, s->nwork, kBatchBlock / kWarp);
     }
     B->hcounts[0] = (int)B->hg.size();
-    B->hcounts[1] = (int)B->hp.size();
-    B->hcounts[2] = (int)B->hv.size();
-    B->hcounts[3] = (int)B->hw.size();
+    B->hcounts[1] = (int)B->hv.size();
+    B->hcounts[2] = (int)B->hw.size();
     cudaError_t ea = ensure_on(B->gch, sizeof(int4) * B->hg.size(), B->st);
-    if (ea == cudaSuccess) ea = ensure_on(B->pch, sizeof(int4) * B->hp.size(), B->st);
     if (ea == cudaSuccess) ea = ensure_on(B->vch, sizeof(int4) * B->hv.size(), B->st);
     if (ea == cudaSuccess) ea = ensure_on(B->wch, sizeof(int4) * std::max<size_t>(B->hw.size(), 1), B->st);
     if (ea != cudaSuccess) {
@@ -1060,7 +1069,6 @@ lmrs_status batch_tables(lmrs_batch* B, const int64_t* steps) {
     cudaError_t e = up(B->ctxs, B->hctx.data(), sizeof(Ctx) * B->n);
     if (e == cudaSuccess) e = up(B->vecs, B->hvec.data(), sizeof(BatchVec) * B->n);
     if (e == cudaSuccess) e = up(B->gch, B->hg.data(), sizeof(int4) * B->hg.size());
-    if (e == cudaSuccess) e = up(B->pch, B->hp.data(), sizeof(int4) * B->hp.size());
     if (e == cudaSuccess) e = up(B->vch, B->hv.data(), sizeof(int4) * B->hv.size());
     if (e == cudaSuccess) e = up(B->wch, B->hw.data(), sizeof(int4) * B->hw.size());
     if (e == cudaSuccess) e = up(B->counts, B->hcounts, sizeof(B->hcounts));
@@ -1075,7 +1083,6 @@ BatchTables batch_view(const lmrs_batch* B) {
     t.ctxs = B->ctxs.as<Ctx>();
     t.vecs = B->vecs.as<BatchVec>();
     t.gchunks = B->gch.as<int4>();
-    t.pchunks = B->pch.as<int4>();
     t.vchunks = B->vch.as<int4>();
     t.wchunks = B->wch.as<int4>();
     t.counts = B->counts.as<int>();
@@ -1085,8 +1092,8 @@ BatchTables batch_view(const lmrs_batch* B) {
 // Capture the PCG loop and the updates of all scenes as one graph (again
 // whenever a table buffer moved).
 lmrs_status batch_graph(lmrs_batch* B) {
-    void* key[6] = {B->ctxs.p, B->vecs.p, B->gch.p, B->pch.p, B->vch.p, B->wch.p};
-    if (B->exec && std::equal(key, key + 6, B->graph_key)) return LMRS_OK;
+    void* key[5] = {B->ctxs.p, B->vecs.p, B->gch.p, B->vch.p, B->wch.p};
+    if (B->exec && std::equal(key, key + 5, B->graph_key)) return LMRS_OK;
     if (B->exec) {
         cudaGraphExecDestroy(B->exec);
         B->exec = nullptr;
@@ -1120,7 +1127,7 @@ lmrs_status batch_graph(lmrs_batch* B) {
         B->exec = nullptr;
         return bfail(B, LMRS_ERR_CUDA, std::string("batch graph: ") + cudaGetErrorString(e));
     }
-    std::copy(key, key + 6, B->graph_key);
+    std::copy(key, key + 5, B->graph_key);
     return LMRS_OK;
 }
 
@@ -1157,7 +1164,7 @@ lmrs_status lmrs_batch_create(lmrs_scene* const* scenes, int32_t n_scenes, int32
     }
     if (rc == LMRS_OK && ensure_on(B->ctxs, sizeof(Ctx) * n_scenes, B->st) != cudaSuccess) rc = LMRS_ERR_OOM;
     if (rc == LMRS_OK && ensure_on(B->vecs, sizeof(BatchVec) * n_scenes, B->st) != cudaSuccess) rc = LMRS_ERR_OOM;
-    if (rc == LMRS_OK && ensure_on(B->counts, sizeof(int) * 4, B->st) != cudaSuccess) rc = LMRS_ERR_OOM;
+    if (rc == LMRS_OK && ensure_on(B->counts, sizeof(int) * 3, B->st) != cudaSuccess) rc = LMRS_ERR_OOM;
     if (rc == LMRS_OK && ensure_on(B->hist, sizeof(double) * n_scenes * 2 * (kMaxBatchIters + 1), B->st) != cudaSuccess) rc = LMRS_ERR_OOM;
     B->ev_scene.assign(n_scenes, nullptr);
     for (int i = 0; rc == LMRS_OK && i < n_scenes; ++i)
@@ -1180,7 +1187,7 @@ lmrs_status lmrs_batch_destroy(lmrs_batch* B) {
     for (auto e : B->ev_scene)
         if (e) cudaEventDestroy(e);
     if (B->ev_batch) cudaEventDestroy(B->ev_batch);
-    for (DevBuf* d : {&B->ctxs, &B->vecs, &B->gch, &B->pch, &B->vch, &B->wch, &B->counts, &B->hist})
+    for (DevBuf* d : {&B->ctxs, &B->vecs, &B->gch, &B->vch, &B->wch, &B->counts, &B->hist})
         release(*d, B->st);
     if (B->st) cudaStreamSynchronize(B->st);
     if (B->own_stream) cudaStreamDestroy(B->st);

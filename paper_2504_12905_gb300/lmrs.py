@@ -121,6 +121,7 @@ _SIGS = {
     "lmrs_footprint_bytes": (C.c_int64, [C.POINTER(Config), C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                          C.c_double]),
     "lmrs_scene_device_bytes": (C.c_int64, [_P]),
+    "lmrs_num_evaluations": (C.c_int64, [_P]),
     "lmrs_synchronize": (_S, [_P]),
     "lmrs_status_str": (C.c_char_p, [_S]),
     "lmrs_last_error": (C.c_char_p, [_P]),
@@ -434,6 +435,10 @@ def lmrs_server_destroy(server):
 def lmrs_footprint_bytes(cfg, n_gauss, n_cams, width, height, views_per_step=0, tiles_per_pair=0.0):
     return int(lib().lmrs_footprint_bytes(C.byref(cfg), int(n_gauss), int(n_cams), int(width), int(height),
                                           int(views_per_step), float(tiles_per_pair)))
+
+
+def lmrs_num_evaluations(scene):
+    return int(lib().lmrs_num_evaluations(scene))
 
 
 def lmrs_scene_device_bytes(scene):

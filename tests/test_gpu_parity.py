@@ -265,6 +265,25 @@ def test_edge_cases_empty_and_single():
     d = p1.zeros(p1.P)
     p1.lmrs.lmrs_jtj_diag(p1.gpu.h, d)
     assert_pvec_close(p1.host(d), p1.orc.diag(), OP_TOL, "diag, one Gaussian")
+    # composited (sample, Gaussian) pairs: for one Gaussian, the samples in
+    # its tile rectangle with alpha >= 1/255 (T stays above 1e-4), counted
+    # from the oracle's FP64 features; flagged samples may go either way
+    smp = p1.orc.samples()
+    _, _, flags = p1.orc.render_samples()
+    want = 0
+    for slot in range(2):
+        f = p1.orc.features(slot)[0]
+        _, _, rect = p1.orc.geom(slot)
+        m = smp["slot"] == slot
+        dx = f[0] - (smp["px"][m] + 0.5)
+        dy = f[1] - (smp["py"][m] + 0.5)
+        alpha = np.minimum(0.99, f[5] * np.exp(-0.5 * (f[2] * dx * dx + f[4] * dy * dy) - f[3] * dx * dy))
+        tx, ty = smp["px"][m] // 16, smp["py"][m] // 16
+        x0, x1, y0, y1 = rect[0]
+        inside = (tx >= x0) & (tx <= x1) & (ty >= y0) & (ty <= y1) if x0 <= x1 else np.zeros(m.sum(), bool)
+        want += int(((alpha >= 1.0 / 255.0) & inside).sum())
+    assert abs(p1.lmrs.lmrs_num_evaluations(p1.gpu.h) - want) <= int((flags != 0).sum())
+    assert pair.lmrs.lmrs_num_evaluations(pair.gpu.h) == 0
 
 
 def test_errors_are_status_codes():
