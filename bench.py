@@ -367,6 +367,20 @@ def run_ours(args, rank, world, local_rank):
             secondary[kname] = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak_hbm, "unit": "GB/s",
                                 "frac": round(ach / peak_hbm, 4), "peak_source": peak_kind,
                                 "algorithmic_bytes_per_launch": int(byt), "avg_launch_ms": round(tot / n_l, 4)}
+    # the whole operator application against the lower bound of the
+    # algorithmic model: t_min = max(Q / HBM, F / FP32, exponentials / SFU)
+    mhz = clock_info.get("sm_max_mhz") or 2070.0
+    Q = 16 * sizes["P"] + 144 * sizes["visible"] + 4 * sizes["pairs"] + 20 * sizes["samples"] + \
+        8 * sizes["view_tiles"]
+    F = JTJ_FLOPS_PER_EVAL * sizes["evaluations_mean"]
+    X = 2 * sizes["evaluations_mean"]
+    t_parts = {"hbm_ms": Q / (peak_hbm * 1e9) * 1e3, "fp32_ms": F / (fp32_peak_tflops(mhz) * 1e12) * 1e3,
+               "sfu_ms": X / (152 * 16 * mhz * 1e6) * 1e3}
+    t_min = max(t_parts.values())
+    matvec_bound = {"Q_bytes": int(Q), "F_flops": int(F), "exponentials": int(X),
+                    "t_min_ms": round(t_min, 4), **{k: round(v, 4) for k, v in t_parts.items()},
+                    "t_operator_ms": round(matvec_ms, 4), "frac": round(t_min / matvec_ms, 4),
+                    "hbm_frac_of_measured": round(Q / (matvec_ms / 1e3) / 1e9 / peak_hbm, 4)}
     step_ms = ms_max / args.steps
     kshare = {k: {"launches": n, "ms": round(t, 3), "share": round(t / max(ms, 1e-9), 4)}
               for k, (n, t) in sorted(ktimes.items(), key=lambda kv: -kv[1][1])}
@@ -385,7 +399,7 @@ def run_ours(args, rank, world, local_rank):
                    "lm_steps_per_s": round(1000.0 * args.steps / ms_max * world, 3),
                    "matvec_only_ms": round(matvec_ms, 4), "matvec_only_per_s": round(1000.0 / matvec_ms, 2),
                    "sizes_last_step": sizes, "loss_last_step": None if last is None else last.loss,
-                   "cache_bf16": bool(bf16), "bf16_cache_error": bf16_err},
+                   "cache_bf16": bool(bf16), "bf16_cache_error": bf16_err, "operator_bound": matvec_bound},
         "roofline": roof, "rooflines_hbm": secondary, "kernels": kshare, "e2e": e2e, "gpu_launches": launches,
         "clocks": clock_info,
     }
