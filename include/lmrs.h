@@ -250,6 +250,63 @@ const char* lmrs_batch_last_error(const lmrs_batch* batch);
  * before the batched loop). */
 lmrs_status lmrs_batch_scene_status(const lmrs_batch* batch, int32_t i);
 
+/* ---- View sampling (Sec. 4.3) and the fit loop ----------------------------
+ * Uniform views of step k: n_views camera indices drawn without replacement
+ * (partial Fisher-Yates driven by SplitMix64 keyed by (seed, k)), sorted;
+ * all cameras when n_views <= 0 or >= n_cams.  views: n_cams entries. */
+lmrs_status lmrs_uniform_views(int32_t n_cams, int32_t n_views, uint64_t seed, int64_t step, int32_t* views);
+
+/* K-means view sampler (Sec. 4.3): camera features [position, viewing
+ * direction], positions centred on their mean and scaled by the largest
+ * distance from it, the direction being the camera's +z axis in world
+ * space; Lloyd's algorithm with k-means++ initialisation (SplitMix64 keyed
+ * by seed), ties to the lower cluster index, at most 100 iterations;
+ * n_clusters = views per step (capped at n_cams).  Host only. */
+typedef struct lmrs_view_sampler lmrs_view_sampler;
+lmrs_status lmrs_view_sampler_create(const lmrs_camera* cams_host, int32_t n_cams, int32_t n_clusters, uint64_t seed,
+                                     lmrs_view_sampler** out);
+lmrs_status lmrs_view_sampler_destroy(lmrs_view_sampler* sampler);
+/* labels[n_cams] (or NULL), the cluster count and the Lloyd iterations run. */
+lmrs_status lmrs_view_sampler_labels(const lmrs_view_sampler* sampler, int32_t* labels, int32_t* n_clusters,
+                                     int32_t* iterations);
+/* One camera drawn uniformly from every cluster for step `step` (SplitMix64
+ * keyed by (seed, step, cluster)), sorted; views: n_clusters entries;
+ * *n_views receives the count (fewer only if a cluster came out empty). */
+lmrs_status lmrs_view_sampler_draw(const lmrs_view_sampler* sampler, int64_t step, int32_t* views, int32_t* n_views);
+
+/* Full-frame MSE of the current parameters against the targets over every
+ * camera (Eq. 7 without sampling; PSNR = -10 log10(mse) for colours in
+ * [0, 1]).  Renders the cameras 8 at a time; leaves the scene preprocessed
+ * for the last of them. */
+lmrs_status lmrs_eval_mse(lmrs_scene* scene, double* mse);
+
+/* An LM-RS fit (Alg. 1 repeated) with the schedules of Sec. 5: views per
+ * step and PCG iterations switch from *_first to *_later at switch_step
+ * (16 -> 32 views and 5 -> 8 iterations at step 50 in the paper's
+ * real-world runs), views drawn uniformly (view_mode 0) or by the K-means
+ * sampler with as many clusters as views (view_mode 1, Sec. 4.3), step k
+ * using LM step index k.  records: n_steps entries. */
+typedef struct {
+    int32_t n_steps;
+    int32_t views_first, views_later;
+    int32_t cg_first, cg_later;
+    int32_t switch_step;
+    int32_t view_mode;    /* 0 uniform, 1 K-means */
+    int32_t eval_every;   /* full-frame MSE every eval_every steps and after the last; 0: never */
+    uint64_t seed;        /* view draws */
+} lmrs_fit_config;
+
+typedef struct {
+    int32_t step, n_views, cg_iters;
+    double loss;      /* sampled loss of the step (before its update) */
+    double eta;
+    double mse_full;  /* after the step when evaluated, else -1 */
+    double psnr;      /* -10 log10(mse_full), else -1 */
+    double ms;        /* host wall time of the step (it synchronises) */
+} lmrs_fit_record;
+
+lmrs_status lmrs_fit(lmrs_scene* scene, const lmrs_fit_config* cfg, lmrs_fit_record* records);
+
 /* ---- Serving: a queue of fit jobs on one device --------------------------
  * The paper fits one scene at a time; the server keeps many fits resident
  * and steps them together with the batched LM step above.
@@ -266,10 +323,8 @@ lmrs_status lmrs_batch_scene_status(const lmrs_batch* batch, int32_t i);
  *     jobs whose sampled loss (Eq. 11 at the step's samples, before the
  *     update) is <= target_loss or that have run max_steps steps; the freed
  *     memory admits the next jobs (continuous batching).
- *   - the views of step k: views_per_step camera indices drawn without
- *     replacement (partial Fisher-Yates driven by SplitMix64 seeded with
- *     cfg.seed and k), or every camera when views_per_step <= 0 or >=
- *     n_cams.  A job's steps therefore do not depend on the other jobs: its
+ *   - the views of step k: lmrs_uniform_views(n_cams, views_per_step,
+ *     cfg.seed, k).  A job's steps therefore do not depend on the other jobs: its
  *     result alone and in any mix agree up to the summation order.
  * Jobs stay owned by the server; their records are kept until forgotten. */
 typedef struct lmrs_server lmrs_server;

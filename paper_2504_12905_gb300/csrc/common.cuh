@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <vector>
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -194,6 +195,9 @@ void launch_ranges(const Ctx& c, cudaStream_t st);
 void launch_raster_fwd_samples(const Ctx& c, cudaStream_t st);
 // Full frames of every slot into images [nv][H][W][3].
 void launch_raster_full(const Ctx& c, float* images, cudaStream_t st);
+void launch_frame_sqerr(const Ctx& c, const float* frames, double* out, cudaStream_t st);
+// host-side view draws (view_sampler.cu)
+void uniform_views(int n_cams, int n_views, uint64_t seed, int64_t step, std::vector<int32_t>& out);
 void launch_raster_jvp(const Ctx& c, float* u, cudaStream_t st);
 // Back-scatter of the per-sample cotangent (u, or w * residual when u is
 // null) into the cotangent slots; needs the caches.

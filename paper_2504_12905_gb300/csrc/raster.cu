@@ -540,6 +540,25 @@ void launch_order_work(const Ctx& c, unsigned long long* keys, unsigned int* val
 void launch_raster_fwd_samples(const Ctx& c, cudaStream_t st) {
     if (c.nwork > 0) LMRS_LAUNCH(k_fwd_samples, raster_grid(c), kRasterBlock, 0, st, c);
 }
+// Sum over the preprocessed views of |frame - target|^2 (full frames, slot
+// order), added into *out in FP64.
+__global__ void __launch_bounds__(256) k_frame_sqerr(Ctx c, const float* frames, double* out) {
+    const long long per = (long long)c.H * c.W * 3;
+    const long long n = (long long)c.nv * per;
+    double acc = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int slot = (int)(i / per);
+        const float d = frames[i] - c.targets[(long long)c.views[slot] * per + (i - (long long)slot * per)];
+        acc += (double)(d * d);
+    }
+    acc = block_sum<256>(acc);
+    if (threadIdx.x == 0) atomicAdd(out, acc);
+}
+
+void launch_frame_sqerr(const Ctx& c, const float* frames, double* out, cudaStream_t st) {
+    LMRS_LAUNCH(k_frame_sqerr, 152 * 8, 256, 0, st, c, frames, out);
+}
+
 void launch_raster_full(const Ctx& c, float* images, cudaStream_t st) {
     LMRS_LAUNCH(k_full, (unsigned)(c.nv * c.T), 256, 0, st, c, images);
 }

@@ -2,6 +2,7 @@
 // orchestration of the kernels of one LM step (Alg. 1).
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -71,6 +72,7 @@ struct lmrs_scene {
     int G = 0, deg = 0, K = 0, Pg = 0;
     long long P = 0;
     int n_cams = 0, W = 0, H = 0, tiles_x = 0, tiles_y = 0, T = 0;
+    std::vector<lmrs_camera> cams_h;  // host copy (view sampling)
     cudaStream_t st = nullptr;
     std::string err;
     const float* targets = nullptr;
@@ -84,7 +86,7 @@ struct lmrs_scene {
     int max_items = 1;
     DevBuf resid, cacheC, cacheT, cacheCh, cacheTh, cacheN;
     DevBuf x, r, z, p, Ap, minv, D, b, stage_a, stage_b;
-    DevBuf sc, partials, counter;
+    DevBuf sc, partials, counter, frames, sqerr;
     // host state of the current step
     std::vector<int> views_h;
     int nv = 0;
@@ -103,7 +105,7 @@ struct lmrs_scene {
                 &cot, &gram, &keys, &ids, &keys_alt, &ids_alt, &ranges, &scan_tmp, &radix_tmp, &total, &tile_off,
                 &off, &wtile, &work, &item_cost, &work_sorted, &okeys, &ovals, &okeys_alt, &ovals_alt, &otmp,
                 &cids, &clen, &binmat, &bintmp, &resid, &cacheC, &cacheT, &cacheCh, &cacheTh, &cacheN, &x, &r, &z, &p, &Ap,
-                &minv, &D, &b, &stage_a, &stage_b, &sc, &partials, &counter};
+                &minv, &D, &b, &stage_a, &stage_b, &sc, &partials, &counter, &frames, &sqerr};
     }
 
     Ctx ctx() const {
@@ -441,6 +443,9 @@ lmrs_status do_cg(lmrs_scene* s, const float* b, float* x, int iters) {
     return LMRS_OK;
 }
 
+lmrs_status lm_step_iters(lmrs_scene* s, const int32_t* view_ids, int32_t n_views, int64_t lm_step, int iters,
+                          lmrs_step_stats* st);
+
 lmrs_status read_scalars(lmrs_scene* s, Scalars* h) {
     CK(s, cudaMemcpyAsync(h, s->sc.p, sizeof(Scalars), cudaMemcpyDeviceToHost, s->st));
     CK(s, cudaStreamSynchronize(s->st));
@@ -521,6 +526,7 @@ lmrs_status lmrs_scene_create(const lmrs_config* cfg, int64_t n_gauss, const flo
         lmrs_scene_destroy(s);
         return rc;
     }
+    s->cams_h.assign(cams_host, cams_host + n_cams);
     std::vector<CamDev> cd(n_cams);
     for (int i = 0; i < n_cams; ++i) cd[i] = make_cam(cams_host[i]);
     // the stream-ordered allocations are complete before the synchronous
@@ -805,12 +811,22 @@ lmrs_status lmrs_step_size(lmrs_scene* s, const float* x, int64_t lm_step, doubl
 lmrs_status lmrs_lm_step(lmrs_scene* s, const int32_t* view_ids, int32_t n_views, int64_t lm_step,
                          lmrs_step_stats* st) {
     TRY(check_scene(s));
+    return lm_step_iters(s, view_ids, n_views, lm_step, s->cfg.cg_iters, st);
+}
+
+}  // extern "C"
+
+namespace {
+
+// One LM step (Alg. 1) with `iters` PCG iterations.
+lmrs_status lm_step_iters(lmrs_scene* s, const int32_t* view_ids, int32_t n_views, int64_t lm_step, int iters,
+                          lmrs_step_stats* st) {
     TimerScope ts_(s);
     TRY(lmrs_preprocess(s, view_ids, n_views, lm_step));
     TRY(lmrs_render(s, nullptr, nullptr));
     TRY(lmrs_rhs(s, s->b.as<float>()));
     TRY(do_jtj_diag(s));
-    TRY(do_cg(s, s->b.as<float>(), s->x.as<float>(), s->cfg.cg_iters));
+    TRY(do_cg(s, s->b.as<float>(), s->x.as<float>(), iters));
     Ctx c = s->ctx();
     CK(s, cudaMemsetAsync(&c.sc->max_dc_bits, 0, sizeof(unsigned int), s->st));
     launch_max_dc(c, s->x.as<float>(), s->st);
@@ -834,6 +850,88 @@ lmrs_status lmrs_lm_step(lmrs_scene* s, const int32_t* view_ids, int32_t n_views
         if (h.numeric_error) return fail(s, LMRS_ERR_NUMERIC, "non-finite or non-positive CG curvature");
     }
     return LMRS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lmrs_status lmrs_eval_mse(lmrs_scene* s, double* mse) {
+    TRY(check_scene(s));
+    if (!mse) return fail(s, LMRS_ERR_INVALID_ARG, "null output");
+    if (!s->targets) return fail(s, LMRS_ERR_INVALID_ARG, "the scene has no targets");
+    constexpr int kChunk = 8;
+    const size_t frame = (size_t)s->H * s->W * 3;
+    TRY(ensure(s, s->frames, sizeof(float) * frame * std::min(kChunk, s->n_cams)));
+    TRY(ensure(s, s->sqerr, sizeof(double)));
+    CK(s, cudaMemsetAsync(s->sqerr.p, 0, sizeof(double), s->st));
+    std::vector<int32_t> views;
+    for (int c0 = 0; c0 < s->n_cams; c0 += kChunk) {
+        views.clear();
+        for (int v = c0; v < std::min(s->n_cams, c0 + kChunk); ++v) views.push_back(v);
+        TRY(lmrs_preprocess(s, views.data(), (int32_t)views.size(), 0));
+        TRY(lmrs_render(s, s->frames.as<float>(), nullptr));
+        TimerScope ts_(s);
+        launch_frame_sqerr(s->ctx(), s->frames.as<float>(), s->sqerr.as<double>(), s->st);
+        CHECK_LAUNCH(s);
+    }
+    double sum = 0.0;
+    CK(s, cudaMemcpyAsync(&sum, s->sqerr.p, sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    CK(s, cudaStreamSynchronize(s->st));
+    *mse = sum / ((double)s->n_cams * (double)frame);
+    return LMRS_OK;
+}
+
+lmrs_status lmrs_fit(lmrs_scene* s, const lmrs_fit_config* f, lmrs_fit_record* rec) {
+    TRY(check_scene(s));
+    if (!f || !rec || f->n_steps <= 0 || f->views_first <= 0 || f->views_later <= 0 || f->cg_first < 0 ||
+        f->cg_later < 0 || (f->view_mode != 0 && f->view_mode != 1))
+        return fail(s, LMRS_ERR_INVALID_ARG, "bad fit configuration");
+    if (f->eval_every > 0 && !s->targets) return fail(s, LMRS_ERR_INVALID_ARG, "evaluation needs targets");
+    lmrs_view_sampler* smp = nullptr;
+    int smp_k = -1;
+    std::vector<int32_t> views(s->n_cams);
+    lmrs_status rc = LMRS_OK;
+    for (int k = 0; k < f->n_steps && rc == LMRS_OK; ++k) {
+        const bool early = k < f->switch_step;
+        const int nvk = std::min(s->n_cams, early ? f->views_first : f->views_later);
+        const int iters = early ? f->cg_first : f->cg_later;
+        int32_t nv = nvk;
+        if (f->view_mode == 1) {
+            if (smp_k != nvk) {
+                if (smp) lmrs_view_sampler_destroy(smp);
+                smp = nullptr;
+                rc = lmrs_view_sampler_create(s->cams_h.data(), s->n_cams, nvk, f->seed, &smp);
+                if (rc != LMRS_OK) break;
+                smp_k = nvk;
+            }
+            lmrs_view_sampler_draw(smp, k, views.data(), &nv);
+        } else {
+            lmrs_uniform_views(s->n_cams, nvk, f->seed, k, views.data());
+        }
+        const auto t0 = std::chrono::steady_clock::now();
+        lmrs_step_stats st;
+        rc = lm_step_iters(s, views.data(), nv, k, iters, &st);
+        const auto t1 = std::chrono::steady_clock::now();
+        if (rc != LMRS_OK) break;
+        lmrs_fit_record& r = rec[k];
+        r.step = k;
+        r.n_views = nv;
+        r.cg_iters = iters;
+        r.loss = st.loss;
+        r.eta = st.eta;
+        r.ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+        r.mse_full = -1.0;
+        r.psnr = -1.0;
+        if (f->eval_every > 0 && ((k + 1) % f->eval_every == 0 || k + 1 == f->n_steps)) {
+            double m = 0.0;
+            rc = lmrs_eval_mse(s, &m);
+            r.mse_full = m;
+            r.psnr = m > 0.0 ? -10.0 * std::log10(m) : INFINITY;
+        }
+    }
+    if (smp) lmrs_view_sampler_destroy(smp);
+    return rc;
 }
 
 lmrs_status lmrs_set_timing(lmrs_scene* s, int32_t enable) {

@@ -19,14 +19,6 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
-// SplitMix64 (Steele, Lea, Flood 2014): the step's view draw.
-inline uint64_t splitmix64_next(uint64_t& state) {
-    uint64_t z = (state += 0x9E3779B97F4A7C15ull);
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-
 struct Job {
     int64_t id = 0;
     lmrs_config cfg;
@@ -80,16 +72,7 @@ int64_t held_bytes(const Job* j) {
 }
 
 void views_of_step(const Job* j, int64_t step, std::vector<int32_t>& out) {
-    const int n = (int)j->cams.size();
-    const int k = (j->views_per_step <= 0 || j->views_per_step >= n) ? n : j->views_per_step;
-    std::vector<int32_t> perm(n);
-    for (int i = 0; i < n; ++i) perm[i] = i;
-    uint64_t state = j->cfg.seed ^ (0xD1B54A32D192ED03ull * (uint64_t)(step + 1));
-    for (int i = 0; i < k && k < n; ++i) {
-        const int r = i + (int)(splitmix64_next(state) % (uint64_t)(n - i));
-        std::swap(perm[i], perm[r]);
-    }
-    out.assign(perm.begin(), perm.begin() + k);
+    lmrs::uniform_views((int)j->cams.size(), j->views_per_step, j->cfg.seed, step, out);
 }
 
 // Device side of an admitted job; on failure the job is marked failed.

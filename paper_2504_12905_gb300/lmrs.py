@@ -73,6 +73,17 @@ class ServerStats(C.Structure):
 
 JOB_QUEUED, JOB_RUNNING, JOB_DONE, JOB_FAILED = 0, 1, 2, 3
 
+
+class FitConfig(C.Structure):
+    _fields_ = [("n_steps", C.c_int32), ("views_first", C.c_int32), ("views_later", C.c_int32),
+                ("cg_first", C.c_int32), ("cg_later", C.c_int32), ("switch_step", C.c_int32),
+                ("view_mode", C.c_int32), ("eval_every", C.c_int32), ("seed", C.c_uint64)]
+
+
+class FitRecord(C.Structure):
+    _fields_ = [("step", C.c_int32), ("n_views", C.c_int32), ("cg_iters", C.c_int32), ("loss", C.c_double),
+                ("eta", C.c_double), ("mse_full", C.c_double), ("psnr", C.c_double), ("ms", C.c_double)]
+
 _P = C.c_void_p
 _S = C.c_int
 _SIGS = {
@@ -122,6 +133,13 @@ _SIGS = {
                                          C.c_double]),
     "lmrs_scene_device_bytes": (C.c_int64, [_P]),
     "lmrs_num_evaluations": (C.c_int64, [_P]),
+    "lmrs_uniform_views": (_S, [C.c_int32, C.c_int32, C.c_uint64, C.c_int64, _P]),
+    "lmrs_view_sampler_create": (_S, [_P, C.c_int32, C.c_int32, C.c_uint64, C.POINTER(_P)]),
+    "lmrs_view_sampler_destroy": (_S, [_P]),
+    "lmrs_view_sampler_labels": (_S, [_P, _P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "lmrs_view_sampler_draw": (_S, [_P, C.c_int64, _P, C.POINTER(C.c_int32)]),
+    "lmrs_eval_mse": (_S, [_P, C.POINTER(C.c_double)]),
+    "lmrs_fit": (_S, [_P, C.POINTER(FitConfig), _P]),
     "lmrs_synchronize": (_S, [_P]),
     "lmrs_status_str": (C.c_char_p, [_S]),
     "lmrs_last_error": (C.c_char_p, [_P]),
@@ -443,6 +461,64 @@ def lmrs_num_evaluations(scene):
 
 def lmrs_scene_device_bytes(scene):
     return int(lib().lmrs_scene_device_bytes(scene))
+
+
+def lmrs_uniform_views(n_cams, n_views, seed, step):
+    out = np.empty(int(n_cams), np.int32)
+    _check(lib().lmrs_uniform_views(int(n_cams), int(n_views), C.c_uint64(seed), int(step), out.ctypes.data))
+    k = n_cams if (n_views <= 0 or n_views >= n_cams) else n_views
+    return out[:k].copy()
+
+
+class ViewSampler:
+    """K-means view sampler (Sec. 4.3)."""
+
+    def __init__(self, cams, n_clusters, seed=0):
+        self._arr = cams if isinstance(cams, C.Array) else cameras(cams)
+        h = _P()
+        _check(lib().lmrs_view_sampler_create(C.cast(self._arr, _P), len(self._arr), int(n_clusters),
+                                              C.c_uint64(seed), C.byref(h)))
+        self.h = h.value
+        self.n_cams = len(self._arr)
+
+    def labels(self):
+        out = np.empty(self.n_cams, np.int32)
+        k, it = C.c_int32(0), C.c_int32(0)
+        _check(lib().lmrs_view_sampler_labels(self.h, out.ctypes.data, C.byref(k), C.byref(it)))
+        return out, k.value, it.value
+
+    def draw(self, step):
+        out = np.empty(self.n_cams, np.int32)
+        n = C.c_int32(0)
+        _check(lib().lmrs_view_sampler_draw(self.h, int(step), out.ctypes.data, C.byref(n)))
+        return out[:n.value].copy()
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().lmrs_view_sampler_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def lmrs_eval_mse(scene):
+    m = C.c_double(0.0)
+    _check(lib().lmrs_eval_mse(scene, C.byref(m)), scene)
+    return m.value
+
+
+def lmrs_fit(scene, n_steps, views_first, views_later=None, cg_first=8, cg_later=None, switch_step=0,
+             view_mode=0, eval_every=0, seed=0):
+    cfg = FitConfig(int(n_steps), int(views_first), int(views_later or views_first), int(cg_first),
+                    int(cg_first if cg_later is None else cg_later), int(switch_step), int(view_mode),
+                    int(eval_every), int(seed))
+    recs = (FitRecord * int(n_steps))()
+    _check(lib().lmrs_fit(scene, C.byref(cfg), C.cast(recs, _P)), scene)
+    return list(recs)
 
 
 def lmrs_synchronize(scene):
