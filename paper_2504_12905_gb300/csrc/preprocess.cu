@@ -511,12 +511,25 @@ __device__ __forceinline__ void pair_jacobian(const Prim& P, const CamDev& cam, 
     }
 }
 
+// Blocked layout of the cache: pairs indexed slot * Gp + g (Gp = G rounded
+// up to 32), blocks of 32 consecutive pairs, each block holding its F4
+// planes one after the other ([block][q][32] float4).  The Jacobians of 32
+// consecutive Gaussians in one view are one contiguous run of F4 x 512 B.
+__device__ __forceinline__ long long jac_block(const Ctx& c, int slot, int g) {
+    return ((long long)slot * ((c.G + 31) & ~31) + g) >> 5;
+}
+
 template <int DEG>
-__device__ __forceinline__ void load_jac(const Ctx& c, long long pair, float* J) {
-    const long long np = (long long)c.nv * c.G;
+__device__ __forceinline__ long long jac_idx(const Ctx& c, int slot, int g, int q) {
+    return (jac_block(c, slot, g) * Jac<DEG>::F4 + q) * 32 + (g & 31);
+}
+
+template <int DEG>
+__device__ __forceinline__ void load_jac(const Ctx& c, int slot, int g, float* J) {
+    const float4* base = c.pjac + jac_block(c, slot, g) * Jac<DEG>::F4 * 32 + (g & 31);
 #pragma unroll
     for (int q = 0; q < Jac<DEG>::F4; ++q) {
-        const float4 v = c.pjac[q * np + pair];
+        const float4 v = base[q * 32];
         J[4 * q] = v.x; J[4 * q + 1] = v.y; J[4 * q + 2] = v.z; J[4 * q + 3] = v.w;
     }
 }
@@ -561,9 +574,9 @@ __global__ void k_prep_fwd(Ctx c) {
     c.dkeys[i] = ((unsigned long long)slot << 32) | __float_as_uint(depth);
     float J[Jac<DEG>::N];
     pair_jacobian<DEG>(P, cam, sh, J);
-    const long long np = (long long)c.nv * c.G;
 #pragma unroll
-    for (int q = 0; q < Jac<DEG>::F4; ++q) c.pjac[q * np + i] = make_float4(J[4 * q], J[4 * q + 1], J[4 * q + 2], J[4 * q + 3]);
+    for (int q = 0; q < Jac<DEG>::F4; ++q)
+        c.pjac[jac_idx<DEG>(c, slot, g, q)] = make_float4(J[4 * q], J[4 * q + 1], J[4 * q + 2], J[4 * q + 3]);
 }
 
 // tangent of the 11 geometric parameters of Gaussian g
@@ -600,7 +613,7 @@ __device__ __forceinline__ void prep_jvp_gauss(const Ctx& c, const float* v, int
         const int4 rc = c.rect[pair];
         if (rc.x > rc.y) continue;
         float J[L::N];
-        load_jac<DEG>(c, pair, J);
+        load_jac<DEG>(c, slot, g, J);
         float o[9];
         o[0] = J[L::kMu] * d.X[0] + J[L::kMu + 1] * d.X[1] + J[L::kMu + 2] * d.X[2];
         o[1] = J[L::kMu + 3] * d.X[0] + J[L::kMu + 4] * d.X[1] + J[L::kMu + 5] * d.X[2];
@@ -680,7 +693,7 @@ __device__ __forceinline__ void prep_vjp_gauss(const Ctx& c, int g, float* out, 
         const int4 rc = c.rect[i];
         if (rc.x > rc.y) continue;
         float J[L::N];
-        load_jac<DEG>(c, i, J);
+        load_jac<DEG>(c, slot, g, J);
         const float4* ct = reinterpret_cast<const float4*>(c.cot + i * kCotF);
         const float4 c0 = ct[0], c1 = ct[1], c2 = ct[2];
         const float cot[9] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, c2.x};
@@ -805,7 +818,7 @@ __global__ void __launch_bounds__(kPrepBlock) k_prep_diag(Ctx c, float* D) {
         const int4 rc = c.rect[i];
         if (rc.x > rc.y) continue;
         float J[L::N];
-        load_jac<DEG>(c, i, J);
+        load_jac<DEG>(c, slot, g, J);
         float gm[kGramF];
         const float4* gsrc = reinterpret_cast<const float4*>(c.gram + i * kGramF);
 #pragma unroll

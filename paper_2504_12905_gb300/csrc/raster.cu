@@ -214,9 +214,9 @@ __device__ __forceinline__ void backward_pass(const Ctx& c, const Pix& p, List L
     for (int b = L.b; b < warp_end; b += 32) {
         const int n = stage_batch<3>(c, p.slot, L.ids, b, warp_end, s_rec, s_id);
         for (int j = 0; j < n; ++j) {
-            float v[16];
+            float v[10];
 #pragma unroll
-            for (int q = 0; q < 16; ++q) v[q] = 0.f;
+            for (int q = 0; q < 10; ++q) v[q] = 0.f;
             bool contrib = false;
             if (b + j < lane_end) {
                 const float4 r0 = s_rec[j][0], r1 = s_rec[j][1];
@@ -231,7 +231,7 @@ __device__ __forceinline__ void backward_pass(const Ctx& c, const Pix& p, List L
                     const float ucol = ub[0] * r1.z + ub[1] * r1.w + ub[2] * col2;
                     const float wgt = alpha * T;
                     s += ucol * wgt;
-                    const float abar = T * ucol - (S_tot - s) / (1.f - alpha);
+                    const float abar = T * ucol - __fdividef(S_tot - s, 1.f - alpha);  // 1 - alpha >= 0.01
                     v[6] = ub[0] * wgt;
                     v[7] = ub[1] * wgt;
                     v[8] = ub[2] * wgt;
@@ -248,9 +248,8 @@ __device__ __forceinline__ void backward_pass(const Ctx& c, const Pix& p, List L
                 }
             }
             if (__any_sync(kFull, contrib)) {
-                warp_reduce_scatter<16>(v);
-                const int idx = lane >> 1;
-                if (!(lane & 1) && idx < 9) atomicAdd(cot_base + (long long)s_id[j] * kCotF + idx, v[0]);
+                const int idx = warp_reduce_scatter9(v);
+                if (!(lane & 1) && idx >= 0) atomicAdd(cot_base + (long long)s_id[j] * kCotF + idx, v[0]);
             }
         }
         __syncwarp();
@@ -431,11 +430,12 @@ __global__ void __launch_bounds__(kRasterBlock) k_gram(Ctx c) {
                     contrib = true;
                     const float col[3] = {r1.z, r1.w, s_rec[j][2].x};
                     const float q = alpha * T;
+                    const float inv = __fdividef(1.f, 1.f - alpha);  // 1 - alpha >= 0.01
                     float h[3];
 #pragma unroll
                     for (int ch = 0; ch < 3; ++ch) {
                         acc[ch] += col[ch] * q;
-                        h[ch] = T * col[ch] - (Cf[ch] - acc[ch]) / (1.f - alpha);
+                        h[ch] = T * col[ch] - (Cf[ch] - acc[ch]) * inv;
                     }
                     float e[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                     if (raw <= kAlphaMax) {

@@ -114,4 +114,34 @@ __device__ __forceinline__ void warp_reduce_scatter(float (&v)[N]) {
     }
 }
 
+// Warp sum of 9 values per lane, scattered over the lanes: the 9 values
+// (padded to 10) are halved over lane bits 16, 8, 4, 2 (5, 3, 2, 1
+// shuffles), then the two partial sums of each pair of lanes are added
+// across bit 1 -- 12 shuffles instead of 16 for the padded 16-value form.
+// Returns the index of the value whose sum this lane holds, -1 when it
+// holds padding (the even lanes 0, 2, 4, 8, 10, 16, 18, 20, 24 hold values
+// 0..8; odd lanes hold a copy of their even neighbour's).  v[9] must be 0.
+__device__ __forceinline__ int warp_reduce_scatter9(float (&v)[10]) {
+    const int lane = threadIdx.x & 31;
+    int base = 0, end = 9, n = 10;
+#pragma unroll
+    for (int m = 16; m >= 2; m >>= 1) {
+        const int half = (n + 1) / 2;
+        const bool up = (lane & m) != 0;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            if (i < half) {
+                const float lo = v[i];
+                const float hi = half + i < n ? v[half + i] : 0.f;
+                v[i] = (up ? hi : lo) + __shfl_xor_sync(kFull, up ? lo : hi, m);
+            }
+        }
+        if (up) base += half;
+        else end = min(end, base + half);
+        n = half;
+    }
+    v[0] += __shfl_xor_sync(kFull, v[0], 1);
+    return base < end ? base : -1;
+}
+
 }  // namespace lmrs

@@ -597,7 +597,8 @@ lmrs_status lmrs_preprocess(lmrs_scene* s, const int32_t* view_ids, int32_t n_vi
     TRY(ensure(s, s->views, sizeof(int) * n_views));
     TRY(ensure(s, s->rec, sizeof(float4) * kPrimF4 * pairs));
     TRY(ensure(s, s->tan, sizeof(float4) * kTanF4 * pairs));
-    TRY(ensure(s, s->pjac, sizeof(float4) * jac_f4(s->deg) * pairs));
+    // blocked by 32 pairs, each view's Gaussians padded to a multiple of 32
+    TRY(ensure(s, s->pjac, sizeof(float4) * jac_f4(s->deg) * (size_t)s->nv * (size_t)((s->G + 31) & ~31)));
     TRY(ensure(s, s->rect, sizeof(int4) * pairs));
     TRY(ensure(s, s->dkeys, sizeof(unsigned long long) * pairs));
     TRY(ensure(s, s->dkeys_alt, sizeof(unsigned long long) * pairs));
