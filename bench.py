@@ -43,7 +43,8 @@ WORKLOADS = {
                   cpu_views=1),
     "fit": dict(desc="LM-RS fits of the 200k-Gaussian scene seen from 96 views 1024x672: 100 LM steps, 16 -> 32 "
                      "views and 5 -> 8 PCG iterations at step 50 (Sec. 5), 32 samples per 16x16 tile, lambda 0.1; "
-                     "K-means view sampling (Sec. 4.3) against uniform; start = ground truth + N(0, 0.02)",
+                     "K-means view sampling (Sec. 4.3) against uniform, and the q_residual / q_Gaussian pixel "
+                     "distributions; start = ground truth + N(0, 0.02)",
                 n_views_total=96, n_steps=100, views=(16, 32), cg=(5, 8), switch=50, samples_per_tile=32, lam=0.1,
                 eval_every=10),
     "ksweep": dict(desc="samples per 16x16 tile K in {26, 32, 64, 128, 256} on the 200k-Gaussian scene (8 of 24 "
@@ -444,10 +445,13 @@ def run_fit(args, rank, world, local_rank):
     out = {}
     launches0 = lmrs.lmrs_launch_count()
     clocks.start()
-    for mode, name in ((1, "kmeans"), (0, "uniform")):
+    # (view draws, pixel distribution): K-means vs uniform views with uniform
+    # pixels, then K-means views with the two importance distributions
+    for mode, dist, name in ((1, 0, "kmeans"), (0, 0, "uniform"), (1, 1, "kmeans_q_residual"),
+                             (1, 2, "kmeans_q_gaussian")):
         scene = lmrs.Scene(torch.from_numpy(start).cuda(), sc.cams, G, deg, targets=targets,
                            samples_per_tile=wl["samples_per_tile"], lambda_=wl["lam"], damping_mode=0,
-                           cg_iters=wl["cg"][0], seed=0x5EED + rank)
+                           cg_iters=wl["cg"][0], seed=0x5EED + rank, sample_dist=dist)
         psnr0 = -10.0 * math.log10(lmrs.lmrs_eval_mse(scene.h))
         t0 = time.perf_counter()
         recs = lmrs.lmrs_fit(scene.h, n_steps=wl["n_steps"], views_first=wl["views"][0], views_later=wl["views"][1],

@@ -83,6 +83,13 @@ typedef struct {
     int32_t warm_iters;
     int32_t cache_bf16;       /* 1: per-sample render caches (final colour, transmittance) in BF16 */
     uint64_t seed;            /* key of the per-tile pixel sampler */
+    int32_t sample_dist;      /* residual sampling distribution within each tile (supplementary material):
+                                 0 uniform without replacement (the paper's choice);
+                                 1 q_residual, 2 q_Gaussian: K_t i.i.d. draws with probability proportional
+                                 to e^{|r_p|} (|r_p| the Euclidean norm of the pixel's RGB residual) or to
+                                 the number of Gaussians the pixel composites (uniform when a tile has none),
+                                 weight 1 / (K_t q(p)) per sample (weight_mode is then not used).  Modes 1
+                                 and 2 render every pixel of the step's views in lmrs_preprocess. */
 } lmrs_config;
 
 typedef struct {
@@ -427,6 +434,9 @@ int64_t lmrs_num_pairs(const lmrs_scene* scene);
 int64_t lmrs_num_visible(const lmrs_scene* scene); /* visible (view, Gaussian) pairs */
 lmrs_status lmrs_get_samples(lmrs_scene* scene, uint8_t* off_host, int32_t* tile_off_host);
 lmrs_status lmrs_get_tile_lists(lmrs_scene* scene, int32_t* ranges_host, int32_t* ids_host);
+/* Per-sample weights w_i (host, S floats): the tile weight of weight_mode for
+ * sample_dist 0, 1 / (K_t q(p_i)) otherwise. */
+lmrs_status lmrs_get_sample_weights(lmrs_scene* scene, float* w_host);
 
 /* Per-kernel device time, measured with CUDA events recorded on the scene's
  * stream around every launch while timing is enabled (off by default). */

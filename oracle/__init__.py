@@ -30,12 +30,12 @@ class _Config(C.Structure):
                 ("lambda_", C.c_double), ("damping_mode", C.c_int32), ("cg_iters", C.c_int32),
                 ("lr_warm", C.c_double), ("lr_cap", C.c_double), ("color_bound", C.c_double),
                 ("warm_iters", C.c_int32), ("seed", C.c_uint64),
-                ("margin_alpha", C.c_double), ("margin_T", C.c_double)]
+                ("margin_alpha", C.c_double), ("margin_T", C.c_double), ("sample_dist", C.c_int32)]
 
 
 DEFAULTS = dict(sh_degree=0, tile_w=16, tile_h=16, sample_frac=1.0, samples_per_tile=0, weight_mode=0,
                 lambda_=1e-2, damping_mode=1, cg_iters=10, lr_warm=0.05, lr_cap=0.2, color_bound=1.0,
-                warm_iters=10, seed=0x1A5E0000, margin_alpha=1e-4, margin_T=1e-3)
+                warm_iters=10, seed=0x1A5E0000, margin_alpha=1e-4, margin_T=1e-3, sample_dist=0)
 
 _P = C.c_void_p
 
@@ -60,6 +60,7 @@ def lib():
             "orc_begin_step": (C.c_int32, [_P, _P, C.c_int32, C.c_int64]),
             "orc_num_samples": (C.c_int64, [_P]),
             "orc_get_samples": (C.c_int32, [_P, _P, _P, _P, _P, _P, _P]),
+            "orc_get_sample_flags": (C.c_int32, [_P, _P]),
             "orc_num_pairs": (C.c_int64, [_P]),
             "orc_get_lists": (C.c_int32, [_P, _P, _P]),
             "orc_get_geom": (C.c_int32, [_P, C.c_int32, _P, _P, _P]),
@@ -67,6 +68,7 @@ def lib():
             "orc_render_samples": (C.c_int32, [_P, _P, _P, _P]),
             "orc_render_samples_subset": (C.c_int32, [_P, _P, C.c_int64, _P, _P]),
             "orc_render_full": (C.c_int32, [_P, C.c_int32, _P, _P]),
+            "orc_pixel_counts": (C.c_int32, [_P, C.c_int32, _P]),
             "orc_jvp": (C.c_int32, [_P, _P, _P]),
             "orc_jvp_subset": (C.c_int32, [_P, _P, _P, C.c_int64, _P]),
             "orc_vjp": (C.c_int32, [_P, _P, _P]),
@@ -177,6 +179,16 @@ class OracleScene:
         slot = np.empty(S, np.int32)
         lib().orc_get_samples(self._h, _ptr(off), _ptr(tile_off), _ptr(w), _ptr(px), _ptr(py), _ptr(slot))
         return dict(off=off, tile_off=tile_off, w=w, px=px, py=py, slot=slot)
+
+    def pixel_counts(self, slot):
+        out = np.empty((self.height, self.width), np.int32)
+        lib().orc_pixel_counts(self._h, int(slot), _ptr(out))
+        return out
+
+    def sample_flags(self):
+        out = np.empty(self.n_samples, np.uint8)
+        lib().orc_get_sample_flags(self._h, _ptr(out))
+        return out
 
     @property
     def tiles_x(self):

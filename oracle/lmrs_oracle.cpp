@@ -331,10 +331,10 @@ inline bool near_rel(double v, double thr, double m) { return std::fabs(v - thr)
 
 template <class S>
 void composite(double pcx, double pcy, const int32_t* ids, int len, const Feat<S>* F,
-               double ma, double mT, S C[3], int* consumed, int* flag) {
+               double ma, double mT, S C[3], int* consumed, int* flag, int* n_comp = nullptr) {
     S T = S(1.0);
     C[0] = C[1] = C[2] = S(0.0);
-    int used = len, fl = 0;
+    int used = len, fl = 0, nc = 0;
     for (int k = 0; k < len; ++k) {
         const Feat<S>& f = F[ids[k]];
         S dx = f.mu[0] - S(pcx), dy = f.mu[1] - S(pcy);
@@ -349,9 +349,11 @@ void composite(double pcx, double pcy, const int32_t* ids, int len, const Feat<S
         if (val(Tn) < kTMin) { used = k; break; }
         for (int ch = 0; ch < 3; ++ch) C[ch] = C[ch] + f.col[ch] * alpha * T;
         T = Tn;
+        ++nc;
     }
     if (consumed) *consumed = used;
     if (flag) *flag = fl;
+    if (n_comp) *n_comp = nc;
 }
 
 // Per-pixel derivatives of the three output channels with respect to the
@@ -472,6 +474,7 @@ struct orc_scene {
     std::vector<uint8_t> off;          // [S]
     std::vector<double> w;             // [S]
     std::vector<int32_t> spx, spy, sslot, stile;  // per sample
+    std::vector<uint8_t> sflag;                   // per sample: an importance draw near a decision
     std::vector<int64_t> ranges;       // [nv*T + 1]
     std::vector<int32_t> ids;          // [Pi]
     std::vector<GeoF> geo;             // [nv*G]
@@ -629,6 +632,100 @@ void make_samples(orc_scene* s) {
         }
 }
 
+// Importance sampling (the q_residual and q_Gaussian distributions of the
+// supplementary material, drawn per tile): every valid pixel of the tile is
+// rendered; its weight is e^{|r_p|} (|r_p| the Euclidean norm of the RGB
+// residual) or the number of Gaussians it composites (all zero: uniform);
+// K_t pixels are drawn independently by inverse CDF with the tile's
+// SplitMix64 outputs, u_i = (output i >> 11) 2^-53, pixel = the first whose
+// cumulative weight exceeds u_i x total; weight total / (K_t x its weight) =
+// 1 / (K_t q(p)), the Monte Carlo weight of the sampled-loss estimate.
+void make_samples_importance(orc_scene* s) {
+    const int nv = s->nv(), mode = s->cfg.sample_dist;
+    const size_t nt = (size_t)nv * s->T;
+    std::vector<std::vector<uint8_t>> offs(nt), fls(nt);
+    std::vector<std::vector<double>> ws(nt);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t vt = 0; vt < (int64_t)nt; ++vt) {
+        const int slot = (int)(vt / s->T), t = (int)(vt % s->T);
+        const int tx = t % s->tiles_x, ty = t / s->tiles_x;
+        const int vw = std::min(s->cfg.tile_w, s->W - tx * s->cfg.tile_w);
+        const int vh = std::min(s->cfg.tile_h, s->H - ty * s->cfg.tile_h);
+        const int n = vw * vh, k = samples_in_tile(s->cfg, n);
+        const int cam = s->views[slot];
+        int len;
+        const int32_t* ids = s->list(slot, t, &len);
+        std::vector<double> a(n), cdf(n);
+        bool any_flag = false;
+        for (int o = 0; o < n; ++o) {
+            int px, py, fl, nc;
+            pixel_of(s, t, o, &px, &py);
+            double C[3];
+            composite<double>(px + 0.5, py + 0.5, ids, len, s->feat.data() + (size_t)slot * s->G, s->cfg.margin_alpha,
+                              s->cfg.margin_T, C, nullptr, &fl, &nc);
+            any_flag = any_flag || fl != 0;
+            if (mode == 1) {
+                double r2 = 0.0;
+                for (int ch = 0; ch < 3; ++ch) {
+                    const double tg = s->targets.empty() ? 0.0
+                                                         : s->targets[(((size_t)cam * s->H + py) * s->W + px) * 3 + ch];
+                    r2 += (C[ch] - tg) * (C[ch] - tg);
+                }
+                a[o] = std::exp(std::sqrt(r2));
+            } else {
+                a[o] = (double)nc;
+            }
+        }
+        double run = 0.0;
+        for (int o = 0; o < n; ++o) cdf[o] = (run += a[o]);
+        const double total = run;
+        const bool uniform = !(total > 0.0);
+        uint64_t h = tile_seed(s->cfg.seed, s->step, cam, t);
+        for (int i = 0; i < k; ++i) {
+            const double u = (double)(sm64_next(h) >> 11) * (1.0 / 9007199254740992.0);
+            int sel;
+            double w;
+            bool near = false;
+            if (uniform) {
+                sel = std::min(n - 1, (int)std::floor(u * n));
+                w = (double)n / (double)k;
+            } else {
+                const double thr = u * total;
+                sel = n - 1;
+                for (int o = 0; o < n; ++o)
+                    if (cdf[o] > thr) {
+                        sel = o;
+                        break;
+                    }
+                const double m = 1e-5 * total;
+                near = std::fabs(cdf[sel] - thr) <= m || (sel > 0 && std::fabs(cdf[sel - 1] - thr) <= m);
+                w = total / ((double)k * a[sel]);
+            }
+            offs[vt].push_back((uint8_t)sel);
+            ws[vt].push_back(w);
+            fls[vt].push_back((uint8_t)((near || any_flag) ? 1 : 0));
+        }
+    }
+    s->off.clear(); s->w.clear(); s->spx.clear(); s->spy.clear(); s->sslot.clear(); s->stile.clear();
+    s->sflag.clear();
+    s->tile_off.assign(nt + 1, 0);
+    for (size_t vt = 0; vt < nt; ++vt) {
+        const int slot = (int)(vt / s->T), t = (int)(vt % s->T);
+        for (size_t i = 0; i < offs[vt].size(); ++i) {
+            int px, py;
+            pixel_of(s, t, offs[vt][i], &px, &py);
+            s->off.push_back(offs[vt][i]);
+            s->w.push_back(ws[vt][i]);
+            s->spx.push_back(px);
+            s->spy.push_back(py);
+            s->sslot.push_back(slot);
+            s->stile.push_back(t);
+            s->sflag.push_back(fls[vt][i]);
+        }
+        s->tile_off[vt + 1] = s->tile_off[vt] + (int32_t)offs[vt].size();
+    }
+}
+
 // Dual features of every visible pair for a tangent v.
 void dual_features(const orc_scene* s, const double* v, std::vector<Feat<Dual>>& fd) {
     int nv = s->nv();
@@ -712,6 +809,7 @@ orc_scene* orc_create(const orc_config* cfg, int32_t n_gauss, const float* param
     if (!cfg || n_gauss <= 0 || !params || !cams || n_cams <= 0) return nullptr;
     if (cfg->sh_degree < 0 || cfg->sh_degree > 3) return nullptr;
     if (cfg->tile_w <= 0 || cfg->tile_h <= 0 || cfg->tile_w * cfg->tile_h > 256) return nullptr;
+    if (cfg->sample_dist < 0 || cfg->sample_dist > 2) return nullptr;
     orc_scene* s = new orc_scene();
     s->cfg = *cfg;
     s->G = n_gauss;
@@ -757,6 +855,8 @@ int32_t orc_begin_step(orc_scene* s, const int32_t* view_ids, int32_t n_views, i
     make_samples(s);
     build_lists(s);
     compute_features(s);
+    if (s->cfg.sample_dist != 0) make_samples_importance(s);  // needs the lists and features
+    else s->sflag.assign(s->off.size(), 0);
     return 0;
 }
 
@@ -772,6 +872,11 @@ int32_t orc_get_samples(const orc_scene* s, uint8_t* off, int32_t* tile_off, dou
         if (slot) slot[i] = s->sslot[i];
     }
     if (tile_off) std::copy(s->tile_off.begin(), s->tile_off.end(), tile_off);
+    return 0;
+}
+
+int32_t orc_get_sample_flags(const orc_scene* s, uint8_t* flags) {
+    std::copy(s->sflag.begin(), s->sflag.end(), flags);
     return 0;
 }
 
@@ -855,6 +960,20 @@ int32_t orc_render_full(const orc_scene* s, int32_t slot, double* img, uint8_t* 
                               s->cfg.margin_alpha, s->cfg.margin_T, C, nullptr, &fl);
             for (int ch = 0; ch < 3; ++ch) img[((size_t)py * s->W + px) * 3 + ch] = C[ch];
             if (flags) flags[(size_t)py * s->W + px] = (uint8_t)fl;
+        }
+    return 0;
+}
+
+int32_t orc_pixel_counts(const orc_scene* s, int32_t slot, int32_t* counts) {
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int py = 0; py < s->H; ++py)
+        for (int px = 0; px < s->W; ++px) {
+            int t = (py / s->cfg.tile_h) * s->tiles_x + px / s->cfg.tile_w, len, nc;
+            const int32_t* ids = s->list(slot, t, &len);
+            double C[3];
+            composite<double>(px + 0.5, py + 0.5, ids, len, s->feat.data() + (size_t)slot * s->G,
+                              s->cfg.margin_alpha, s->cfg.margin_T, C, nullptr, nullptr, &nc);
+            counts[(size_t)py * s->W + px] = nc;
         }
     return 0;
 }

@@ -47,6 +47,7 @@ typedef struct {
     uint64_t seed;
     double  margin_alpha;     /* relative margin that flags an alpha test */
     double  margin_T;         /* relative margin that flags a termination test */
+    int32_t sample_dist;      /* 0 uniform without replacement; 1 q_residual; 2 q_Gaussian (i.i.d. per tile) */
 } orc_config;
 
 typedef struct orc_scene orc_scene;
@@ -65,6 +66,10 @@ int32_t orc_begin_step(orc_scene* s, const int32_t* view_ids, int32_t n_views, i
 int64_t orc_num_samples(const orc_scene* s);
 int32_t orc_get_samples(const orc_scene* s, uint8_t* off, int32_t* tile_off, double* w,
                         int32_t* px, int32_t* py, int32_t* slot);
+/* Per sample: 1 when an importance draw may legitimately go another way in
+ * a different precision (its threshold within a relative margin of a bin
+ * edge of the tile's cumulative weights, or a flagged pixel in its tile). */
+int32_t orc_get_sample_flags(const orc_scene* s, uint8_t* flags);
 int64_t orc_num_pairs(const orc_scene* s);
 int32_t orc_get_lists(const orc_scene* s, int32_t* ranges, int32_t* ids);
 int32_t orc_get_geom(const orc_scene* s, int32_t slot, int32_t* vis, float* depth, int32_t* rect);
@@ -74,6 +79,9 @@ int32_t orc_render_samples(const orc_scene* s, double* rgb, double* resid, uint8
 int32_t orc_render_samples_subset(const orc_scene* s, const int64_t* idx, int64_t n,
                                   double* rgb, uint8_t* flags);
 int32_t orc_render_full(const orc_scene* s, int32_t slot, double* img, uint8_t* flags);
+/* Number of Gaussians each pixel of the view composites (alpha >= 1/255
+ * before termination), H x W. */
+int32_t orc_pixel_counts(const orc_scene* s, int32_t slot, int32_t* counts);
 
 int32_t orc_jvp(const orc_scene* s, const double* v, double* u);
 int32_t orc_jvp_subset(const orc_scene* s, const double* v, const int64_t* idx, int64_t n, double* u);

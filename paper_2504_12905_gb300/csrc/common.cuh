@@ -93,6 +93,8 @@ struct Ctx {
     const int* tile_off;    // [nv * T + 1]
     unsigned char* off;     // [S]
     const float* wtile;     // [nv * T]
+    float* wsample;         // [S] per-sample weights (importance sampling), else null
+    int sample_dist;
     long long S;
     const int2* work;       // (slot * T + tile, first sample in tile) per warp item
     int nwork;
@@ -233,6 +235,24 @@ void launch_b_jtj(const BatchTables& t, int grid, cudaStream_t st);
 void launch_b_prep_vjp(const BatchTables& t, int deg, int iter, int grid, cudaStream_t st);
 void launch_b_update(const BatchTables& t, int iter, int grid, cudaStream_t st);
 void launch_b_lm_update(const BatchTables& t, int iters, int grid, cudaStream_t st);
+
+// ---- the per-tile SplitMix64 stream of the pixel sampler --------------------
+__device__ __forceinline__ unsigned long long sm64_mix(unsigned long long z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+// state of (seed, LM step, camera, tile); output i is sm64_mix(state + (i+1) gamma)
+__device__ __forceinline__ unsigned long long tile_stream(unsigned long long seed, long long lm_step, int cam,
+                                                          int tile) {
+    unsigned long long h = sm64_mix(seed ^ 0x5851F42D4C957F2Dull);
+    h = sm64_mix(h ^ (unsigned long long)lm_step);
+    h = sm64_mix(h ^ (unsigned long long)(unsigned int)cam);
+    return sm64_mix(h ^ (unsigned long long)(unsigned int)tile);
+}
+constexpr unsigned long long kSm64Gamma = 0x9E3779B97F4A7C15ull;
+
+void launch_importance(const Ctx& c, long long lm_step, unsigned long long seed, cudaStream_t st);
 
 // ---- device memory from the library's stream-ordered pool -----------------
 cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t st);

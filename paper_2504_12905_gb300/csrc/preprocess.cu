@@ -414,14 +414,6 @@ __device__ __forceinline__ void prim_tangent(const Prim& P, const CamDev& cam, c
 // ---------------------------------------------------------------------------
 // Kernels
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned long long sm64_mix(unsigned long long z) {
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-
-// One thread per (slot, tile): partial Fisher-Yates over the tile's valid
-// pixels driven by SplitMix64 keyed by (seed, LM step, camera id, tile id).
 __global__ void k_sample(Ctx c, long long lm_step, unsigned long long seed) {
     const int vt = blockIdx.x * blockDim.x + threadIdx.x;
     if (vt >= c.nv * c.T) return;
@@ -432,12 +424,9 @@ __global__ void k_sample(Ctx c, long long lm_step, unsigned long long seed) {
     const int b = c.tile_off[vt], k = c.tile_off[vt + 1] - b;
     unsigned char a[256];
     for (int i = 0; i < n; ++i) a[i] = (unsigned char)i;
-    unsigned long long h = sm64_mix(seed ^ 0x5851F42D4C957F2Dull);
-    h = sm64_mix(h ^ (unsigned long long)lm_step);
-    h = sm64_mix(h ^ (unsigned long long)(unsigned int)c.views[slot]);
-    h = sm64_mix(h ^ (unsigned long long)(unsigned int)tile);
+    unsigned long long h = tile_stream(seed, lm_step, c.views[slot], tile);
     for (int i = 0; i < k; ++i) {
-        h += 0x9E3779B97F4A7C15ull;
+        h += kSm64Gamma;
         const unsigned long long r = sm64_mix(h);
         const int j = i + (int)(r % (unsigned long long)(n - i));
         const unsigned char t = a[i];

@@ -55,7 +55,7 @@ __device__ __forceinline__ void setup_item(const Ctx& c, int item, Pix& p) {
     p.py = ty * c.tile_h + o / vw;
     p.pcx = p.px + 0.5f;
     p.pcy = p.py + 0.5f;
-    p.w = c.wtile[p.vt];
+    p.w = c.wsample ? (p.active ? c.wsample[p.si] : 0.f) : c.wtile[p.vt];
 }
 
 // The list a kernel walks: ids[b, e).
@@ -188,6 +188,7 @@ __device__ __forceinline__ void forward_pass(const Ctx& c, const Pix& p, List L,
             C[1] += r1.w * wgt;
             C[2] += col2 * wgt;
             T = Tn;
+            if (n_comp) ++*n_comp;
         }
         __syncwarp();
     }
@@ -512,6 +513,99 @@ __global__ void __launch_bounds__(256) k_full(Ctx c, float* images) {
         dst[1] = C[1];
         dst[2] = C[2];
     }
+}
+
+// Importance draws of the pixel sampler (modes 1, 2), one block per (view,
+// tile): every valid pixel is rendered and weighted -- e^{|r_p|}, |r_p| the
+// Euclidean norm of its RGB residual, or the number of Gaussians it
+// composites --, the weights are prefix-summed in FP64 in pixel order, and
+// draw i takes the first pixel whose cumulative weight exceeds u_i x total,
+// u_i = (output i of the tile's SplitMix64 stream >> 11) 2^-53; its weight
+// is total / (K_t x the pixel's weight) = 1 / (K_t q).  A tile whose total is
+// 0 is drawn uniformly with weight n_valid / K_t.
+__global__ void __launch_bounds__(256) k_importance(Ctx c, long long lm_step, unsigned long long seed) {
+    __shared__ float4 s_rec_all[8][32][kRecF4];
+    __shared__ unsigned s_id_all[8][32];
+    __shared__ double s_cdf[256];
+    __shared__ float s_a[256];
+    const int vt = blockIdx.x;
+    const int wid = threadIdx.x >> 5, o = threadIdx.x;
+    const int slot = vt / c.T, tile = vt - slot * c.T;
+    const int tx = tile % c.tiles_x, ty = tile / c.tiles_x;
+    const int vw = min(c.tile_w, c.W - tx * c.tile_w), vh = min(c.tile_h, c.H - ty * c.tile_h);
+    const int nvalid = vw * vh;
+    const int cam = c.views[slot];
+    float a = 0.f;
+    if (wid * 32 < nvalid) {
+        Pix p;
+        p.vt = vt;
+        p.slot = slot;
+        p.tile = tile;
+        p.chunk = 0;
+        p.active = o < nvalid;
+        p.si = 0;
+        p.px = tx * c.tile_w + (p.active ? o % vw : 0);
+        p.py = ty * c.tile_h + (p.active ? o / vw : 0);
+        p.pcx = p.px + 0.5f;
+        p.pcy = p.py + 0.5f;
+        p.w = 1.f;
+        float C[3], T, dC[3];
+        int ncons, ncomp = 0;
+        forward_pass<false, false>(c, p, tile_list(c, p), s_rec_all[wid], s_id_all[wid], C, T, dC, ncons, nullptr,
+                                   nullptr, &ncomp);
+        if (p.active) {
+            if (c.sample_dist == 1) {
+                float r2 = 0.f;
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) {
+                    const float tg = c.targets ? c.targets[(((long long)cam * c.H + p.py) * c.W + p.px) * 3 + ch] : 0.f;
+                    const float d = C[ch] - tg;
+                    r2 += d * d;
+                }
+                a = expf(sqrtf(r2));
+            } else {
+                a = (float)ncomp;
+            }
+        }
+    }
+    s_a[o] = a;
+    s_cdf[o] = (double)a;
+    __syncthreads();
+    for (int d = 1; d < 256; d <<= 1) {
+        const double v = o >= d ? s_cdf[o - d] : 0.0;
+        __syncthreads();
+        s_cdf[o] += v;
+        __syncthreads();
+    }
+    const double total = s_cdf[nvalid - 1];
+    const int b = c.tile_off[vt], K = c.tile_off[vt + 1] - b;
+    if (o < K) {
+        const unsigned long long r =
+            sm64_mix(tile_stream(seed, lm_step, cam, tile) + (unsigned long long)(o + 1) * kSm64Gamma);
+        const double u = (double)(r >> 11) * (1.0 / 9007199254740992.0);
+        int sel;
+        float w;
+        if (!(total > 0.0)) {
+            sel = min(nvalid - 1, (int)floor(u * nvalid));
+            w = (float)nvalid / (float)K;
+        } else {
+            const double thr = u * total;
+            int lo = 0, hi = nvalid - 1;  // the first index whose cumulative weight exceeds thr
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (s_cdf[mid] > thr) hi = mid;
+                else lo = mid + 1;
+            }
+            sel = lo;
+            w = (float)(total / ((double)K * (double)s_a[sel]));
+        }
+        c.off[b + o] = (unsigned char)sel;
+        c.wsample[b + o] = w;
+    }
+}
+
+void launch_importance(const Ctx& c, long long lm_step, unsigned long long seed, cudaStream_t st) {
+    LMRS_LAUNCH(k_importance, (unsigned)(c.nv * c.T), 256, 0, st, c, lm_step, seed);
 }
 
 static unsigned raster_grid(const Ctx& c) { return (unsigned)((c.nwork + kRasterWarps - 1) / kRasterWarps); }

@@ -80,7 +80,7 @@ struct lmrs_scene {
     DevBuf params, cams, views, gcache, pjac;
     DevBuf rec, tan, rect, dkeys, dvals, dkeys_alt, dvals_alt, dtmp, cnt, cot, gram;
     DevBuf keys, ids, keys_alt, ids_alt, ranges, scan_tmp, radix_tmp, total;
-    DevBuf tile_off, off, wtile, work;
+    DevBuf tile_off, off, wtile, wsample, work;
     DevBuf item_cost, work_sorted, okeys, ovals, okeys_alt, ovals_alt, otmp;
     DevBuf cids, clen, binmat, bintmp;
     int max_items = 1;
@@ -103,7 +103,7 @@ struct lmrs_scene {
     std::vector<DevBuf*> bufs() {
         return {&params, &cams, &views, &gcache, &pjac, &rec, &tan, &rect, &dkeys, &dvals, &dkeys_alt, &dvals_alt, &dtmp, &cnt,
                 &cot, &gram, &keys, &ids, &keys_alt, &ids_alt, &ranges, &scan_tmp, &radix_tmp, &total, &tile_off,
-                &off, &wtile, &work, &item_cost, &work_sorted, &okeys, &ovals, &okeys_alt, &ovals_alt, &otmp,
+                &off, &wtile, &wsample, &work, &item_cost, &work_sorted, &okeys, &ovals, &okeys_alt, &ovals_alt, &otmp,
                 &cids, &clen, &binmat, &bintmp, &resid, &cacheC, &cacheT, &cacheCh, &cacheTh, &cacheN, &x, &r, &z, &p, &Ap,
                 &minv, &D, &b, &stage_a, &stage_b, &sc, &partials, &counter, &frames, &sqerr};
     }
@@ -139,6 +139,8 @@ struct lmrs_scene {
         c.tile_off = tile_off.as<int>();
         c.off = off.as<unsigned char>();
         c.wtile = wtile.as<float>();
+        c.wsample = cfg.sample_dist != 0 ? wsample.as<float>() : nullptr;
+        c.sample_dist = cfg.sample_dist;
         c.S = S;
         c.work = ordered ? work_sorted.as<int2>() : work.as<int2>();
         c.item_cost = item_cost.as<int>();
@@ -361,6 +363,7 @@ lmrs_status build_layout(lmrs_scene* s) {
     TRY(ensure(s, s->wtile, sizeof(float) * nT));
     TRY(ensure(s, s->work, sizeof(int2) * std::max<size_t>(work.size(), 1)));
     TRY(ensure(s, s->off, (size_t)s->S));
+    if (s->cfg.sample_dist != 0) TRY(ensure(s, s->wsample, sizeof(float) * (size_t)s->S));
     TRY(ensure(s, s->resid, sizeof(float) * 3 * s->S));
     TRY(ensure(s, s->cacheC, sizeof(float) * 3 * s->S));
     TRY(ensure(s, s->cacheT, sizeof(float) * s->S));
@@ -487,7 +490,7 @@ lmrs_status lmrs_scene_create(const lmrs_config* cfg, int64_t n_gauss, const flo
     if (cfg->sh_degree < 0 || cfg->sh_degree > 3 || cfg->tile_w <= 0 || cfg->tile_h <= 0 ||
         cfg->tile_w * cfg->tile_h > 256 || !(cfg->sample_frac > 0.0) || cfg->cg_iters < 0 ||
         (cfg->damping_mode != 0 && cfg->damping_mode != 1) || (cfg->weight_mode != 0 && cfg->weight_mode != 1) ||
-        !(cfg->lambda >= 0.0))
+        !(cfg->lambda >= 0.0) || cfg->sample_dist < 0 || cfg->sample_dist > 2)
         return LMRS_ERR_INVALID_ARG;
     for (int i = 0; i < n_cams; ++i)
         if (cams_host[i].width != cams_host[0].width || cams_host[i].height != cams_host[0].height ||
@@ -618,7 +621,7 @@ lmrs_status lmrs_preprocess(lmrs_scene* s, const int32_t* view_ids, int32_t n_vi
     CK(s, cudaMemcpyAsync(s->views.p, s->views_h.data(), sizeof(int) * n_views, cudaMemcpyHostToDevice, s->st));
     Ctx c = s->ctx();
     CK(s, cudaMemsetAsync(s->total.p, 0, 4 * sizeof(unsigned long long), s->st));
-    launch_sample(c, lm_step, s->cfg.seed, s->st);
+    if (s->cfg.sample_dist == 0) launch_sample(c, lm_step, s->cfg.seed, s->st);  // importance draws follow the binning
     launch_prep_gauss(c, s->st);
     launch_prep_fwd(c, s->st);
     // level 1: (slot, depth, index) order of the pairs
@@ -668,6 +671,7 @@ lmrs_status lmrs_preprocess(lmrs_scene* s, const int32_t* view_ids, int32_t n_vi
         CK(s, cudaMemsetAsync(s->ranges.p, 0, sizeof(int2) * (size_t)s->nv * s->T, s->st));
         launch_ranges(c, s->st);
     }
+    if (s->cfg.sample_dist != 0) launch_importance(c, lm_step, s->cfg.seed, s->st);
     CHECK_LAUNCH(s);
     s->preprocessed = true;
     return LMRS_OK;
@@ -1037,8 +1041,9 @@ int64_t lmrs_footprint_bytes(const lmrs_config* cfg, int64_t n_gauss, int32_t n_
     const double per_pair = 96 + 16.0 * jac_f4(cfg->sh_degree) + 16 + 24 + 8 + 48 + 160 + 2;
     // keys, ids and their alternates 16, compact lists 4 per work item of a tile
     const double per_entry = 16 + 4.0 * max_items + 1;
-    // offset 1, residual 12, FP32 and BF16 caches 12 + 4 + 6 + 2, stop index 4
-    const double per_sample = 41;
+    // offset 1, residual 12, FP32 and BF16 caches 12 + 4 + 6 + 2, stop index 4,
+    // importance weight 4
+    const double per_sample = 41 + (cfg->sample_dist != 0 ? 4 : 0);
     // tile offset, weight, range 16; compact lengths 4 per item; work items
     // and their ordering buffers 36
     const double per_view_tile = 16 + 4.0 * max_items;
@@ -1049,6 +1054,23 @@ int64_t lmrs_footprint_bytes(const lmrs_config* cfg, int64_t n_gauss, int32_t n_
                        items * per_item;
     const double targets = (double)n_cams * height * width * 3 * sizeof(float);
     return (int64_t)(fixed + targets + 1.25 * var);
+}
+
+lmrs_status lmrs_get_sample_weights(lmrs_scene* s, float* w) {
+    TRY(check_scene(s));
+    TRY(need_pre(s));
+    if (!w) return fail(s, LMRS_ERR_INVALID_ARG, "null output");
+    if (s->cfg.sample_dist != 0) {
+        CK(s, cudaMemcpyAsync(w, s->wsample.p, sizeof(float) * s->S, cudaMemcpyDeviceToHost, s->st));
+        CK(s, cudaStreamSynchronize(s->st));
+        return LMRS_OK;
+    }
+    std::vector<float> wt((size_t)s->nv * s->T);
+    CK(s, cudaMemcpyAsync(wt.data(), s->wtile.p, sizeof(float) * wt.size(), cudaMemcpyDeviceToHost, s->st));
+    CK(s, cudaStreamSynchronize(s->st));
+    for (size_t vt = 0; vt < wt.size(); ++vt)
+        for (int i = s->tile_off_h[vt]; i < s->tile_off_h[vt + 1]; ++i) w[i] = wt[vt];
+    return LMRS_OK;
 }
 
 int64_t lmrs_num_evaluations(lmrs_scene* s) {

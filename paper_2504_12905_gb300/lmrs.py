@@ -38,7 +38,8 @@ class Config(C.Structure):
                 ("sample_frac", C.c_double), ("samples_per_tile", C.c_int32), ("weight_mode", C.c_int32),
                 ("lambda_", C.c_double), ("damping_mode", C.c_int32), ("cg_iters", C.c_int32),
                 ("lr_warm", C.c_double), ("lr_cap", C.c_double), ("color_bound", C.c_double),
-                ("warm_iters", C.c_int32), ("cache_bf16", C.c_int32), ("seed", C.c_uint64)]
+                ("warm_iters", C.c_int32), ("cache_bf16", C.c_int32), ("seed", C.c_uint64),
+                ("sample_dist", C.c_int32)]
 
 
 class CgStats(C.Structure):
@@ -111,6 +112,7 @@ _SIGS = {
     "lmrs_num_visible": (C.c_int64, [_P]),
     "lmrs_get_samples": (_S, [_P, _P, _P]),
     "lmrs_get_tile_lists": (_S, [_P, _P, _P]),
+    "lmrs_get_sample_weights": (_S, [_P, _P]),
     "lmrs_set_timing": (_S, [_P, C.c_int32]),
     "lmrs_get_timing": (_S, [_P, C.POINTER(KernelTime), C.c_int32, C.POINTER(C.c_int32)]),
     "lmrs_batch_create": (_S, [_P, C.c_int32, C.c_int32, _P, C.POINTER(_P)]),
@@ -327,6 +329,12 @@ def lmrs_get_tile_lists(scene, n_views, n_tiles):
     ids = np.empty(max(n, 1), np.int32)
     _check(lib().lmrs_get_tile_lists(scene, ranges.ctypes.data, ids.ctypes.data), scene)
     return ranges, ids[:n]
+
+
+def lmrs_get_sample_weights(scene, n_samples):
+    out = np.empty(int(n_samples), np.float32)
+    _check(lib().lmrs_get_sample_weights(scene, out.ctypes.data), scene)
+    return out
 
 
 def lmrs_set_timing(scene, enable=True):

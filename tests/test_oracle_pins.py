@@ -440,3 +440,74 @@ def test_sampler_full_tile_is_permutation_and_keyed():
         counts[oracle.sample_tile(1, 0, 0, t, 256, 32)] += 1
     expect = 4000 * 32 / 256
     assert np.abs(counts - expect).max() < 6 * math.sqrt(expect)
+
+
+# ---- importance distributions of the residual sampler (supplementary) ----
+
+def _importance_scene():
+    sc = syn.tiny_scene(seed=41, n_gauss=300, width=32, height=32)
+    tgt = syn.noise_targets(np.random.default_rng(2), len(sc.cams), 32, 32)
+    return sc, tgt
+
+
+@pytest.mark.parametrize("dist", [1, 2])
+def test_importance_estimate_is_unbiased(dist):
+    """E_q[sum_i w_i |r_i|^2] over the draws equals the loss over the pixels
+    q can draw (the Monte Carlo identity behind the weights): every pixel for
+    q_residual; for q_Gaussian the pixels some Gaussian composites, plus
+    every pixel of a tile that has none (drawn uniformly)."""
+    sc, tgt = _importance_scene()
+    o = oracle.OracleScene(sc.params, sc.cams, sc.n_gauss, 0, targets=tgt, samples_per_tile=8, sample_dist=dist)
+    views = [0, 2]
+    o.begin_step(views, 0)
+    full = 0.0
+    for slot, cam in enumerate(views):
+        r2 = ((o.render_full(slot)[0] - tgt[cam]) ** 2).sum(-1)
+        if dist == 2:
+            cnt = o.pixel_counts(slot)
+            for ty in range(2):
+                for tx in range(2):
+                    blk = (slice(16 * ty, 16 * ty + 16), slice(16 * tx, 16 * tx + 16))
+                    full += r2[blk][cnt[blk] > 0].sum() if (cnt[blk] > 0).any() else r2[blk].sum()
+        else:
+            full += r2.sum()
+    est = []
+    for step in range(300):
+        o.begin_step(views, step)
+        w = o.samples()["w"]
+        r = o.render_samples()[1]
+        est.append(float((w[:, None] * r ** 2).sum()))
+    est = np.array(est)
+    assert abs(est.mean() - full) <= 4.0 * est.std() / np.sqrt(len(est)) + 1e-9 * full
+
+
+def test_importance_residual_weights_match_their_pixels():
+    """q_residual: each draw's weight is total / (K e^{|r|}) of the drawn pixel."""
+    sc, tgt = _importance_scene()
+    o = oracle.OracleScene(sc.params, sc.cams, sc.n_gauss, 0, targets=tgt, samples_per_tile=8, sample_dist=1)
+    o.begin_step([1], 3)
+    smp = o.samples()
+    img = o.render_full(0)[0]
+    a = np.exp(np.sqrt(((img - tgt[1]) ** 2).sum(-1)))
+    tile = (smp["py"] // 16) * 2 + smp["px"] // 16
+    for t in range(4):
+        ys, xs = np.mgrid[(t // 2) * 16:(t // 2) * 16 + 16, (t % 2) * 16:(t % 2) * 16 + 16]
+        total = a[ys, xs].sum()
+        m = tile == t
+        np.testing.assert_allclose(smp["w"][m], total / (8 * a[smp["py"][m], smp["px"][m]]), rtol=1e-9)
+
+
+def test_importance_gaussian_draws_only_covered_pixels():
+    """q_Gaussian: a pixel no Gaussian composites is never drawn (unless the
+    whole tile is empty, where the draw is uniform)."""
+    sc, tgt = _importance_scene()
+    o = oracle.OracleScene(sc.params, sc.cams, sc.n_gauss, 0, targets=tgt, samples_per_tile=16, sample_dist=2)
+    o.begin_step([0], 5)
+    smp = o.samples()
+    covered = o.pixel_counts(0) > 0
+    tile = (smp["py"] // 16) * 2 + smp["px"] // 16
+    for t in range(4):
+        ys, xs = np.mgrid[(t // 2) * 16:(t // 2) * 16 + 16, (t % 2) * 16:(t % 2) * 16 + 16]
+        m = tile == t
+        if covered[ys, xs].any():
+            assert covered[smp["py"][m], smp["px"][m]].all()
