@@ -30,12 +30,14 @@ class _Config(C.Structure):
                 ("lambda_", C.c_double), ("damping_mode", C.c_int32), ("cg_iters", C.c_int32),
                 ("lr_warm", C.c_double), ("lr_cap", C.c_double), ("color_bound", C.c_double),
                 ("warm_iters", C.c_int32), ("seed", C.c_uint64),
-                ("margin_alpha", C.c_double), ("margin_T", C.c_double), ("sample_dist", C.c_int32)]
+                ("margin_alpha", C.c_double), ("margin_T", C.c_double), ("sample_dist", C.c_int32),
+                ("ssim_weight", C.c_double)]
 
 
 DEFAULTS = dict(sh_degree=0, tile_w=16, tile_h=16, sample_frac=1.0, samples_per_tile=0, weight_mode=0,
                 lambda_=1e-2, damping_mode=1, cg_iters=10, lr_warm=0.05, lr_cap=0.2, color_bound=1.0,
-                warm_iters=10, seed=0x1A5E0000, margin_alpha=1e-4, margin_T=1e-3, sample_dist=0)
+                warm_iters=10, seed=0x1A5E0000, margin_alpha=1e-4, margin_T=1e-3, sample_dist=0,
+                ssim_weight=0.0)
 
 _P = C.c_void_p
 
@@ -61,6 +63,7 @@ def lib():
             "orc_num_samples": (C.c_int64, [_P]),
             "orc_get_samples": (C.c_int32, [_P, _P, _P, _P, _P, _P, _P]),
             "orc_get_sample_flags": (C.c_int32, [_P, _P]),
+            "orc_get_ssim": (C.c_int32, [_P, _P, _P, _P]),
             "orc_num_pairs": (C.c_int64, [_P]),
             "orc_get_lists": (C.c_int32, [_P, _P, _P]),
             "orc_get_geom": (C.c_int32, [_P, C.c_int32, _P, _P, _P]),
@@ -87,6 +90,7 @@ def lib():
             "orc_tile_seed": (C.c_uint64, [C.c_uint64, C.c_int64, C.c_int32, C.c_int32]),
             "orc_sample_tile": (None, [C.c_uint64, C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _P]),
             "orc_num_threads": (C.c_int32, []),
+            "orc_ssim_pixel": (None, [_P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _P, _P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -189,6 +193,16 @@ class OracleScene:
         out = np.empty(self.n_samples, np.uint8)
         lib().orc_get_sample_flags(self._h, _ptr(out))
         return out
+
+    def ssim(self):
+        """Per sample and channel the SSIM residual s = 1 - SSIM and its
+        own-pixel derivative d (S x 3 each), and per sample the window flag."""
+        S = self.n_samples
+        sv = np.empty((S, 3))
+        dv = np.empty((S, 3))
+        fl = np.empty(S, np.uint8)
+        lib().orc_get_ssim(self._h, _ptr(sv), _ptr(dv), _ptr(fl))
+        return sv, dv, fl
 
     @property
     def tiles_x(self):
@@ -355,3 +369,14 @@ def sample_tile(seed, step, view, tile, n_valid, k):
 
 def num_threads():
     return int(lib().orc_num_threads())
+
+
+def ssim_pixel(X, Y, px, py):
+    """(s, d) of the three channels at pixel (px, py) of H x W x 3 images."""
+    X = np.ascontiguousarray(X, np.float64)
+    Y = np.ascontiguousarray(Y, np.float64)
+    H, W = X.shape[:2]
+    sv = np.empty(3)
+    dv = np.empty(3)
+    lib().orc_ssim_pixel(_ptr(X), _ptr(Y), H, W, int(px), int(py), _ptr(sv), _ptr(dv))
+    return sv, dv

@@ -475,6 +475,8 @@ struct orc_scene {
     std::vector<double> w;             // [S]
     std::vector<int32_t> spx, spy, sslot, stile;  // per sample
     std::vector<uint8_t> sflag;                   // per sample: an importance draw near a decision
+    std::vector<double> ssim_s, ssim_d;           // [S][3] SSIM residual and its own-pixel derivative
+    std::vector<uint8_t> ssim_flag;               // per sample: a flagged pixel inside its SSIM window
     std::vector<int64_t> ranges;       // [nv*T + 1]
     std::vector<int32_t> ids;          // [Pi]
     std::vector<GeoF> geo;             // [nv*G]
@@ -541,6 +543,14 @@ struct orc_scene {
                            f.col[0].d, f.col[1].d, f.col[2].d};
             for (int k = 0; k < 9; ++k) a[(size_t)k * Pg + j] = d[k];
         }
+    }
+    // weight of the (sample, channel) row in J^T W J: w_i for the colour
+    // residual plus ssim_weight * d^2 w_i for the SSIM residual of the same
+    // pixel and channel, whose Jacobian row is d times the colour's
+    double row_weight(int64_t i, int ch) const {
+        if (ssim_d.empty()) return w[i];
+        const double d = ssim_d[3 * i + ch];
+        return w[i] * (1.0 + cfg.ssim_weight * d * d);
     }
     int nv() const { return (int)views.size(); }
     int64_t S() const { return (int64_t)off.size(); }
@@ -797,6 +807,92 @@ void gaussian_cotangent(const orc_scene* s, int slot, int g, const double* ubar,
     });
 }
 
+// --------------------------------------------------------------------------
+// Diagonal SSIM term (supplementary material, "Results with SSIM loss").
+// SSIM per channel (Wang et al. 2004): local statistics under an 11 x 11
+// Gaussian window, sigma 1.5, weights normalised to sum 1, pixels outside the
+// image counting as 0; C1 = 0.01^2, C2 = 0.03^2 for a dynamic range of 1:
+//   SSIM = (2 mx my + C1)(2 cxy + C2) / ((mx^2 + my^2 + C1)(vx + vy + C2)).
+// The residual of the term is s = 1 - SSIM at every sampled pixel.  The
+// diagonal approximation keeps only the dependence of s on the pixel's own
+// colour X_i (Zhao et al. 2016 give dSSIM(p)/dX(q) for every q in the
+// window; here q = p): with g0 the centre weight, d mx = g0, d E[X^2] =
+// 2 g0 X_i, d E[XY] = g0 Y_i.
+// --------------------------------------------------------------------------
+constexpr int kSsimRad = 5;
+constexpr double kSsimSigma = 1.5, kSsimC1 = 0.01 * 0.01, kSsimC2 = 0.03 * 0.03;
+
+struct SsimWindow {
+    double g[2 * kSsimRad + 1][2 * kSsimRad + 1];
+    SsimWindow() {
+        double z = 0.0;
+        for (int a = -kSsimRad; a <= kSsimRad; ++a)
+            for (int b = -kSsimRad; b <= kSsimRad; ++b) {
+                g[a + kSsimRad][b + kSsimRad] = std::exp(-(a * a + b * b) / (2.0 * kSsimSigma * kSsimSigma));
+                z += g[a + kSsimRad][b + kSsimRad];
+            }
+        for (auto& row : g)
+            for (double& v : row) v /= z;
+    }
+};
+
+void ssim_pixel(const double* X, const double* Y, int H, int W, int px, int py, double s[3], double d[3]) {
+    static const SsimWindow win;
+    for (int ch = 0; ch < 3; ++ch) {
+        double mx = 0.0, my = 0.0, xx = 0.0, yy = 0.0, xy = 0.0;
+        for (int a = -kSsimRad; a <= kSsimRad; ++a)
+            for (int b = -kSsimRad; b <= kSsimRad; ++b) {
+                const int y = py + a, x = px + b;
+                if (y < 0 || y >= H || x < 0 || x >= W) continue;
+                const double g = win.g[a + kSsimRad][b + kSsimRad];
+                const double xv = X[((size_t)y * W + x) * 3 + ch], yv = Y[((size_t)y * W + x) * 3 + ch];
+                mx += g * xv;
+                my += g * yv;
+                xx += g * xv * xv;
+                yy += g * yv * yv;
+                xy += g * xv * yv;
+            }
+        const double vx = xx - mx * mx, vy = yy - my * my, cxy = xy - mx * my;
+        const double A1 = 2.0 * mx * my + kSsimC1, A2 = 2.0 * cxy + kSsimC2;
+        const double B1 = mx * mx + my * my + kSsimC1, B2 = vx + vy + kSsimC2;
+        const double ssim = (A1 * A2) / (B1 * B2);
+        const double g0 = win.g[kSsimRad][kSsimRad];
+        const double xi = X[((size_t)py * W + px) * 3 + ch], yi = Y[((size_t)py * W + px) * 3 + ch];
+        const double dA1 = 2.0 * g0 * my, dA2 = 2.0 * g0 * (yi - my);
+        const double dB1 = 2.0 * g0 * mx, dB2 = 2.0 * g0 * (xi - mx);
+        const double dssim = (dA1 * A2 + A1 * dA2) / (B1 * B2) - ssim * (dB1 * B2 + B1 * dB2) / (B1 * B2);
+        s[ch] = 1.0 - ssim;
+        d[ch] = -dssim;
+    }
+}
+
+// Full FP64 frames of the step's views, then s, d and the window flag of
+// every sample.
+void make_ssim(orc_scene* s) {
+    const int64_t S = s->S();
+    s->ssim_s.assign(3 * S, 0.0);
+    s->ssim_d.assign(3 * S, 0.0);
+    s->ssim_flag.assign(S, 0);
+    const size_t npx = (size_t)s->H * s->W;
+    std::vector<double> img(npx * 3), tgt(npx * 3);
+    std::vector<uint8_t> fl(npx);
+    for (int slot = 0; slot < s->nv(); ++slot) {
+        orc_render_full(s, slot, img.data(), fl.data());
+        const int cam = s->views[slot];
+        for (size_t k = 0; k < npx * 3; ++k) tgt[k] = s->targets.empty() ? 0.0 : s->targets[(size_t)cam * npx * 3 + k];
+#pragma omp parallel for schedule(dynamic, 64)
+        for (int64_t i = 0; i < S; ++i) {
+            if (s->sslot[i] != slot) continue;
+            ssim_pixel(img.data(), tgt.data(), s->H, s->W, s->spx[i], s->spy[i], &s->ssim_s[3 * i], &s->ssim_d[3 * i]);
+            uint8_t f = 0;
+            for (int y = std::max(0, s->spy[i] - kSsimRad); y <= std::min(s->H - 1, s->spy[i] + kSsimRad); ++y)
+                for (int x = std::max(0, s->spx[i] - kSsimRad); x <= std::min(s->W - 1, s->spx[i] + kSsimRad); ++x)
+                    f |= fl[(size_t)y * s->W + x];
+            s->ssim_flag[i] = f;
+        }
+    }
+}
+
 }  // namespace
 
 // ==========================================================================
@@ -809,7 +905,7 @@ orc_scene* orc_create(const orc_config* cfg, int32_t n_gauss, const float* param
     if (!cfg || n_gauss <= 0 || !params || !cams || n_cams <= 0) return nullptr;
     if (cfg->sh_degree < 0 || cfg->sh_degree > 3) return nullptr;
     if (cfg->tile_w <= 0 || cfg->tile_h <= 0 || cfg->tile_w * cfg->tile_h > 256) return nullptr;
-    if (cfg->sample_dist < 0 || cfg->sample_dist > 2) return nullptr;
+    if (cfg->sample_dist < 0 || cfg->sample_dist > 2 || !(cfg->ssim_weight >= 0.0)) return nullptr;
     orc_scene* s = new orc_scene();
     s->cfg = *cfg;
     s->G = n_gauss;
@@ -857,6 +953,12 @@ int32_t orc_begin_step(orc_scene* s, const int32_t* view_ids, int32_t n_views, i
     compute_features(s);
     if (s->cfg.sample_dist != 0) make_samples_importance(s);  // needs the lists and features
     else s->sflag.assign(s->off.size(), 0);
+    if (s->cfg.ssim_weight > 0.0) make_ssim(s);
+    else {
+        s->ssim_s.clear();
+        s->ssim_d.clear();
+        s->ssim_flag.clear();
+    }
     return 0;
 }
 
@@ -877,6 +979,18 @@ int32_t orc_get_samples(const orc_scene* s, uint8_t* off, int32_t* tile_off, dou
 
 int32_t orc_get_sample_flags(const orc_scene* s, uint8_t* flags) {
     std::copy(s->sflag.begin(), s->sflag.end(), flags);
+    return 0;
+}
+
+int32_t orc_get_ssim(const orc_scene* s, double* s_out, double* d_out, uint8_t* flags) {
+    const int64_t S = s->S();
+    const bool on = !s->ssim_s.empty();
+    for (int64_t k = 0; k < 3 * S; ++k) {
+        if (s_out) s_out[k] = on ? s->ssim_s[k] : 0.0;
+        if (d_out) d_out[k] = on ? s->ssim_d[k] : 0.0;
+    }
+    if (flags)
+        for (int64_t i = 0; i < S; ++i) flags[i] = on ? s->ssim_flag[i] : 0;
     return 0;
 }
 
@@ -1032,7 +1146,7 @@ int32_t orc_vjp_gauss(const orc_scene* s, const double* u, const int32_t* gids, 
     return 0;
 }
 
-// D_j = sum_i w_i J_ij^2, accumulated row by row: each (sample, channel) row
+// D_j = sum_i w_i J_ij^2 (w_i the row weight), accumulated row by row: each (sample, channel) row
 // of J restricted to one Gaussian is dC/dfeatures times the preprocessing
 // Jacobian (no Gram factorisation here).
 static void diag_local(const orc_scene* s, int slot, int g, double* out_local) {
@@ -1045,7 +1159,7 @@ static void diag_local(const orc_scene* s, int slot, int g, double* out_local) {
                 for (int j = 0; j < s->Pg; ++j) {
                     double Jij = 0.0;
                     for (int f = 0; f < 9; ++f) Jij += c.dC[ch][f] * a[(size_t)f * s->Pg + j];
-                    out_local[j] += s->w[i] * Jij * Jij;
+                    out_local[j] += s->row_weight(i, ch) * Jij * Jij;
                 }
         });
     });
@@ -1077,7 +1191,7 @@ int32_t orc_apply(const orc_scene* s, const double* v, const double* D, double* 
     std::vector<double> u((size_t)s->S() * 3);
     orc_jvp(s, v, u.data());
     for (int64_t i = 0; i < s->S(); ++i)
-        for (int ch = 0; ch < 3; ++ch) u[3 * i + ch] *= s->w[i];
+        for (int ch = 0; ch < 3; ++ch) u[3 * i + ch] *= s->row_weight(i, ch);
     orc_vjp(s, u.data(), out);
     for (int64_t j = 0; j < s->P(); ++j)
         out[j] += s->cfg.lambda * (s->cfg.damping_mode == 1 ? D[j] : 1.0) * v[j];
@@ -1089,7 +1203,7 @@ int32_t orc_apply_gauss(const orc_scene* s, const double* v, const double* D,
     std::vector<double> u((size_t)s->S() * 3);
     orc_jvp(s, v, u.data());
     for (int64_t i = 0; i < s->S(); ++i)
-        for (int ch = 0; ch < 3; ++ch) u[3 * i + ch] *= s->w[i];
+        for (int ch = 0; ch < 3; ++ch) u[3 * i + ch] *= s->row_weight(i, ch);
     orc_vjp_gauss(s, u.data(), gids, n, out);
     for (int k = 0; k < n; ++k)
         for (int j = 0; j < s->Pg; ++j) {
@@ -1099,12 +1213,17 @@ int32_t orc_apply_gauss(const orc_scene* s, const double* v, const double* D,
     return 0;
 }
 
-// b = J^T W r   (right-hand side of Eq. 8, Eq. 14 without the constant)
+// b = J^T W r   (right-hand side of Eq. 8, Eq. 14 without the constant);
+// with the SSIM term the stacked residual adds ssim_weight * d * s per row.
 int32_t orc_rhs(const orc_scene* s, double* b) {
     std::vector<double> r((size_t)s->S() * 3);
     orc_render_samples(s, nullptr, r.data(), nullptr);
+    const bool ssim = !s->ssim_s.empty();
     for (int64_t i = 0; i < s->S(); ++i)
-        for (int ch = 0; ch < 3; ++ch) r[3 * i + ch] *= s->w[i];
+        for (int ch = 0; ch < 3; ++ch) {
+            const double e = ssim ? s->cfg.ssim_weight * s->ssim_d[3 * i + ch] * s->ssim_s[3 * i + ch] : 0.0;
+            r[3 * i + ch] = s->w[i] * (r[3 * i + ch] + e);
+        }
     return orc_vjp(s, r.data(), b);
 }
 
@@ -1174,7 +1293,10 @@ int32_t orc_lm_step(orc_scene* s, const int32_t* view_ids, int32_t n_views, int6
     orc_render_samples(s, nullptr, r.data(), nullptr);
     double se = 0.0, sw = 0.0;
     for (int64_t i = 0; i < s->S(); ++i) {
-        for (int ch = 0; ch < 3; ++ch) se += s->w[i] * r[3 * i + ch] * r[3 * i + ch];
+        for (int ch = 0; ch < 3; ++ch) {
+            se += s->w[i] * r[3 * i + ch] * r[3 * i + ch];
+            if (!s->ssim_s.empty()) se += s->w[i] * s->cfg.ssim_weight * s->ssim_s[3 * i + ch] * s->ssim_s[3 * i + ch];
+        }
         sw += 3.0 * s->w[i];
     }
     std::vector<double> b(P), D(P), x(P);
@@ -1192,6 +1314,11 @@ int32_t orc_lm_step(orc_scene* s, const int32_t* view_ids, int32_t n_views, int6
 }
 
 void orc_sh_basis(int32_t deg, double x, double y, double z, double* Y) { sh_basis<double>(deg, x, y, z, Y); }
+
+void orc_ssim_pixel(const double* X, const double* Y, int32_t H, int32_t W, int32_t px, int32_t py, double* s,
+                    double* d) {
+    ssim_pixel(X, Y, H, W, px, py, s, d);
+}
 
 void orc_splitmix64(uint64_t state, int32_t n, uint64_t* out) {
     for (int i = 0; i < n; ++i) out[i] = sm64_next(state);

@@ -48,6 +48,7 @@ typedef struct {
     double  margin_alpha;     /* relative margin that flags an alpha test */
     double  margin_T;         /* relative margin that flags a termination test */
     int32_t sample_dist;      /* 0 uniform without replacement; 1 q_residual; 2 q_Gaussian (i.i.d. per tile) */
+    double  ssim_weight;      /* weight of the diagonal SSIM residual term (0: MSE only) */
 } orc_config;
 
 typedef struct orc_scene orc_scene;
@@ -70,6 +71,11 @@ int32_t orc_get_samples(const orc_scene* s, uint8_t* off, int32_t* tile_off, dou
  * a different precision (its threshold within a relative margin of a bin
  * edge of the tile's cumulative weights, or a flagged pixel in its tile). */
 int32_t orc_get_sample_flags(const orc_scene* s, uint8_t* flags);
+/* SSIM term of the step (ssim_weight > 0): per sample and channel the
+ * residual s = 1 - SSIM and its derivative d = ds/dX at the sample's own
+ * pixel (S x 3 each), and per sample 1 when its 11 x 11 window holds a
+ * full-frame pixel flagged near a compositing decision.  Zeros when off. */
+int32_t orc_get_ssim(const orc_scene* s, double* s_out, double* d_out, uint8_t* flags);
 int64_t orc_num_pairs(const orc_scene* s);
 int32_t orc_get_lists(const orc_scene* s, int32_t* ranges, int32_t* ids);
 int32_t orc_get_geom(const orc_scene* s, int32_t slot, int32_t* vis, float* depth, int32_t* rect);
@@ -109,6 +115,10 @@ uint64_t orc_tile_seed(uint64_t seed, int64_t lm_step, int32_t view_id, int32_t 
 void    orc_sample_tile(uint64_t seed, int64_t lm_step, int32_t view_id, int32_t tile_id,
                         int32_t n_valid, int32_t k, uint8_t* out);
 int32_t orc_num_threads(void);
+/* SSIM of the three channels of images X and Y (H x W x 3) at pixel (px, py):
+ * s = 1 - SSIM and d = ds/dX(px, py), every other pixel held fixed. */
+void    orc_ssim_pixel(const double* X, const double* Y, int32_t H, int32_t W, int32_t px, int32_t py,
+                       double* s, double* d);
 
 #ifdef __cplusplus
 }
