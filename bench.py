@@ -144,8 +144,9 @@ class ClockSampler:
 # tangents) 66, backward pass (the same primal, the colour cotangent, the 9
 # feature cotangents, their warp sum) 63.
 JTJ_FLOPS_PER_EVAL = 66 + 63
-# float4 planes of the per-pair Jacobian cache for SH degree 0..3
-JAC_F4 = {0: 10, 1: 13, 2: 14, 3: 16}
+# float4 planes of the per-pair Jacobian cache for SH degree 0..3 (the SH
+# basis values are recomputed from the view direction, not cached)
+JAC_F4 = {0: 10, 1: 12, 2: 12, 3: 12}
 
 
 def fp32_peak_tflops(sm_mhz):
@@ -159,14 +160,16 @@ def algorithmic_bytes(kernel, sizes):
     deg = sizes["sh_degree"]
     jac = 16 * JAC_F4[deg]
     pg = P // G
+    means = 12 * G if deg > 0 else 0  # the means, for the view direction of the SH basis
     if kernel == "k_prep_jvp":
         # rectangles of every pair; per visible pair the Jacobian, the 9-float
         # tangent written and the 9-float cotangent slot cleared; the tangent P-vector
-        return 16 * nv * G + Vis * (jac + 36 + 36) + 4 * P
+        return 16 * nv * G + Vis * (jac + 36 + 36) + 4 * P + means
     if kernel == "k_prep_vjp<dot>":
-        # rectangles; per visible pair the Jacobian and the cotangents; p, D
-        # read and Ap written
-        return 16 * nv * G + Vis * (jac + 36) + 3 * 4 * P
+        # rectangles; per visible pair the Jacobian and the cotangents; p read,
+        # Ap written, D read under diagonal damping
+        d_read = 4 * P if sizes.get("damping_mode", 0) == 1 else 0
+        return 16 * nv * G + Vis * (jac + 36) + 2 * 4 * P + d_read + means
     if kernel == "k_cg_update<true>":
         return 4 * P * 8  # p, Ap, M^-1, x, r read; x, r, z written
     if kernel == "k_cg_direction":
@@ -283,7 +286,8 @@ def run_ours(args, rank, world, local_rank):
         evals.append(lmrs.lmrs_num_evaluations(h))
     sizes = {"pairs": lmrs.lmrs_num_pairs(h), "visible": lmrs.lmrs_num_visible(h),
              "samples": lmrs.lmrs_num_samples(h), "view_tiles": nvs * scene.n_tiles, "P": scene.n_params,
-             "views": nvs, "G": G, "sh_degree": deg, "evaluations_mean": int(np.mean(evals))}
+             "views": nvs, "G": G, "sh_degree": deg, "evaluations_mean": int(np.mean(evals)),
+             "damping_mode": wl.get("damping_mode", 0)}
 
     # ---- (J^T W J + lambda diag(J^T W J)) v alone, at the current parameters
     cur = torch.empty(scene.n_params, dtype=torch.float32, device="cuda")
@@ -445,13 +449,14 @@ def run_fit(args, rank, world, local_rank):
     out = {}
     launches0 = lmrs.lmrs_launch_count()
     clocks.start()
-    # (view draws, pixel distribution): K-means vs uniform views with uniform
-    # pixels, then K-means views with the two importance distributions
-    for mode, dist, name in ((1, 0, "kmeans"), (0, 0, "uniform"), (1, 1, "kmeans_q_residual"),
-                             (1, 2, "kmeans_q_gaussian")):
+    # (view draws, pixel distribution, SSIM weight): K-means vs uniform views
+    # with uniform pixels, K-means views with the two importance
+    # distributions, and with the diagonal SSIM term at the paper's 0.2
+    for mode, dist, ssim, name in ((1, 0, 0.0, "kmeans"), (0, 0, 0.0, "uniform"), (1, 1, 0.0, "kmeans_q_residual"),
+                                   (1, 2, 0.0, "kmeans_q_gaussian"), (1, 0, 0.2, "kmeans_ssim")):
         scene = lmrs.Scene(torch.from_numpy(start).cuda(), sc.cams, G, deg, targets=targets,
                            samples_per_tile=wl["samples_per_tile"], lambda_=wl["lam"], damping_mode=0,
-                           cg_iters=wl["cg"][0], seed=0x5EED + rank, sample_dist=dist)
+                           cg_iters=wl["cg"][0], seed=0x5EED + rank, sample_dist=dist, ssim_weight=ssim)
         psnr0 = -10.0 * math.log10(lmrs.lmrs_eval_mse(scene.h))
         t0 = time.perf_counter()
         recs = lmrs.lmrs_fit(scene.h, n_steps=wl["n_steps"], views_first=wl["views"][0], views_later=wl["views"][1],

@@ -90,6 +90,15 @@ typedef struct {
                                  the number of Gaussians the pixel composites (uniform when a tile has none),
                                  weight 1 / (K_t q(p)) per sample (weight_mode is then not used).  Modes 1
                                  and 2 render every pixel of the step's views in lmrs_preprocess. */
+    double  ssim_weight;      /* weight of the diagonal SSIM term (supplementary material, "Results with SSIM
+                                 loss": 0.2 beside the MSE term's 1); 0 turns it off.  Per sampled pixel and
+                                 channel the residual s = 1 - SSIM (Wang et al. 2004: 11 x 11 Gaussian window,
+                                 sigma 1.5, pixels outside the image count as 0, C1 = 0.01^2, C2 = 0.03^2) is
+                                 added to the objective as ssim_weight * w * s^2, with the Jacobian of s kept
+                                 only through the pixel's own colour, d = ds/dC (the diagonal approximation):
+                                 J^T W J gains ssim_weight * w * d^2 per (sample, channel) row and J^T W r
+                                 gains ssim_weight * w * d * s.  lmrs_render then renders every pixel of the
+                                 step's views.  lmrs_jvp and lmrs_vjp stay the colour Jacobian's products. */
 } lmrs_config;
 
 typedef struct {
@@ -437,6 +446,10 @@ lmrs_status lmrs_get_tile_lists(lmrs_scene* scene, int32_t* ranges_host, int32_t
 /* Per-sample weights w_i (host, S floats): the tile weight of weight_mode for
  * sample_dist 0, 1 / (K_t q(p_i)) otherwise. */
 lmrs_status lmrs_get_sample_weights(lmrs_scene* scene, float* w_host);
+/* The SSIM term of the last lmrs_render (host, S x 3 floats each, NULL to
+ * skip): s = 1 - SSIM and d = ds/dC at each sample's own pixel.
+ * LMRS_ERR_INVALID_ARG when ssim_weight is 0. */
+lmrs_status lmrs_get_ssim(lmrs_scene* scene, float* s_host, float* d_host);
 
 /* Per-kernel device time, measured with CUDA events recorded on the scene's
  * stream around every launch while timing is enabled (off by default). */

@@ -19,11 +19,13 @@ constexpr int kRecF4 = 6;                   // float4 per staged (view, Gaussian
 constexpr int kPrimF4 = 3;                  // float4 of a pair's primal 2D features
 constexpr int kTanF4 = 3;                   // float4 of a pair's 2D feature tangent
 constexpr int kCotF = 12;                   // floats per (view, Gaussian) cotangent slot (9 used)
-constexpr int kGramF = 40;                  // floats per (view, Gaussian) Gram slot
+constexpr int kGramF = 44;                  // floats per (view, Gaussian) Gram slot (42 used)
 constexpr int kMaxPartials = 4096;          // block partials of the FP64 reductions
 constexpr int kGaussF4 = 9;                  // float4 planes of the per-Gaussian cache
-// float4 planes of the per-pair Jacobian cache for SH degree 0..3
-__host__ __device__ constexpr int jac_f4(int deg) { return deg == 0 ? 10 : deg == 1 ? 13 : deg == 2 ? 14 : 16; }
+// float4 planes of the per-pair Jacobian cache for SH degree 0..3: screen mean
+// 2x3, conic 3x10, opacity slope, clamp mask (38 floats), plus for degree >= 1
+// the colour-through-direction block 3x3 (47)
+__host__ __device__ constexpr int jac_f4(int deg) { return deg == 0 ? 10 : 12; }
 
 // Camera as the kernels read it.  R, t, fx, fy, cx, cy, limx, limy, znear are
 // the FP32 values the list decisions use.
@@ -95,6 +97,12 @@ struct Ctx {
     const float* wtile;     // [nv * T]
     float* wsample;         // [S] per-sample weights (importance sampling), else null
     int sample_dist;
+    // diagonal SSIM term (null when off): per (sample, channel) s = 1 - SSIM
+    // and d = ds/dC; rows of J^T W J weigh w (1 + ssim_weight d^2)
+    float* ssim_s;          // [S][3]
+    float* ssim_d;          // [S][3]
+    float ssim_weight;
+    const float* frames;    // [nv][H][W][3] full renders of the step's views (SSIM windows)
     long long S;
     const int2* work;       // (slot * T + tile, first sample in tile) per warp item
     int nwork;
@@ -197,6 +205,7 @@ void launch_ranges(const Ctx& c, cudaStream_t st);
 void launch_raster_fwd_samples(const Ctx& c, cudaStream_t st);
 // Full frames of every slot into images [nv][H][W][3].
 void launch_raster_full(const Ctx& c, float* images, cudaStream_t st);
+void launch_ssim(const Ctx& c, cudaStream_t st);
 void launch_frame_sqerr(const Ctx& c, const float* frames, double* out, cudaStream_t st);
 // host-side view draws (view_sampler.cu)
 void uniform_views(int n_cams, int n_views, uint64_t seed, int64_t step, std::vector<int32_t>& out);

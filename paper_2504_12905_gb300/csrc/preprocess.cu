@@ -454,7 +454,7 @@ template <int DEG>
 struct Jac {
     static constexpr int F4 = jac_f4(DEG);
     static constexpr int N = 4 * F4;
-    static constexpr int kMu = 0, kCon = 6, kOp = 36, kMask = 37, kGx = 38, kY = 47;
+    static constexpr int kMu = 0, kCon = 6, kOp = 36, kMask = 37, kGx = 38;
 };
 
 template <int DEG>
@@ -492,12 +492,6 @@ __device__ __forceinline__ void pair_jacobian(const Prim& P, const CamDev& cam, 
     for (int ch = 0; ch < 3; ++ch)
         if (!P.clamped[ch]) bits |= 1u << ch;
     J[L::kMask] = __uint_as_float(bits);
-    if (DEG > 0) {
-        float Y[Sh<DEG>::K];
-        sh_eval<DEG>(P.dir[0], P.dir[1], P.dir[2], Y);
-#pragma unroll
-        for (int k = 0; k < Sh<DEG>::K; ++k) J[L::kY + k] = Y[k];
-    }
 }
 
 // Blocked layout of the cache: pairs indexed slot * Gp + g (Gp = G rounded
@@ -523,11 +517,22 @@ __device__ __forceinline__ void load_jac(const Ctx& c, int slot, int g, float* J
     }
 }
 
-// Y_k of the pair (the constant Y_0 for DEG 0)
+// SH basis values Y_k of the pair's view direction, recomputed from the
+// Gaussian's mean X and the camera centre with the arithmetic of
+// prim_features (the cache does not hold them: at SH3 they would be a
+// quarter of its bytes).  DEG 0: the constant Y_0.
 template <int DEG>
-__device__ __forceinline__ float jac_Y(const float* J, int k) {
-    if (DEG == 0) return c_sh[0];
-    return J[Jac<DEG>::kY + k];
+__device__ __forceinline__ void pair_Y(const CamDev& cam, const float X[3], float* Y) {
+    if (DEG == 0) {
+        Y[0] = c_sh[0];
+        return;
+    }
+    float d[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) d[k] = X[k] - cam.centre[k];
+    const float dn = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    const float idn = 1.f / dn;
+    sh_eval<DEG>(d[0] * idn, d[1] * idn, d[2] * idn, Y);
 }
 
 template <int DEG>
@@ -589,20 +594,26 @@ __device__ __forceinline__ void load_geo_tangent(const float* v, int G, int g, G
 // dslot, ... (visible ones), from the Jacobian cache, and cleared cotangent
 // slots.  The lanes of a warp take consecutive Gaussians, so every plane
 // load and record store is one contiguous run.
+// dsh: the Gaussian's 3K SH tangent values (global memory, or a staged copy
+// in shared memory).
 template <int DEG>
-__device__ __forceinline__ void prep_jvp_gauss(const Ctx& c, const float* v, int g, int slot0, int dslot) {
+__device__ __forceinline__ void prep_jvp_gauss(const Ctx& c, const float* v, const float* dsh, int g, int slot0,
+                                               int dslot) {
     using L = Jac<DEG>;
     constexpr int K = Sh<DEG>::K;
     GTan d;
     load_geo_tangent(v, c.G, g, d);
     const float u[10] = {d.X[0], d.X[1], d.X[2], d.ls[0], d.ls[1], d.ls[2], d.q[0], d.q[1], d.q[2], d.q[3]};
-    const float* dsh = v + 11ll * c.G + (long long)g * 3 * K;
+    float X[3] = {0.f, 0.f, 0.f};
+    if (DEG > 0) load_mean(c.params, g, X);
     for (int slot = slot0; slot < c.nv; slot += dslot) {
         const long long pair = (long long)slot * c.G + g;
         const int4 rc = c.rect[pair];
         if (rc.x > rc.y) continue;
         float J[L::N];
         load_jac<DEG>(c, slot, g, J);
+        float Y[K];
+        pair_Y<DEG>(c.cams[c.views[slot]], X, Y);
         float o[9];
         o[0] = J[L::kMu] * d.X[0] + J[L::kMu + 1] * d.X[1] + J[L::kMu + 2] * d.X[2];
         o[1] = J[L::kMu + 3] * d.X[0] + J[L::kMu + 4] * d.X[1] + J[L::kMu + 5] * d.X[2];
@@ -618,9 +629,8 @@ __device__ __forceinline__ void prep_jvp_gauss(const Ctx& c, const float* v, int
         float v3[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            const float y = jac_Y<DEG>(J, k);
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) v3[ch] += y * dsh[3 * k + ch];
+            for (int ch = 0; ch < 3; ++ch) v3[ch] += Y[k] * dsh[3 * k + ch];
         }
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
@@ -638,14 +648,24 @@ __device__ __forceinline__ void prep_jvp_gauss(const Ctx& c, const float* v, int
 }
 
 // Blocks of 32 Gaussians (lanes) x kJvpWarps warps, warp w taking views w,
-// w + kJvpWarps, ...: several warps per Gaussian for latency hiding, the
-// tangent re-read by them from the same SM's L1.
+// w + kJvpWarps, ...: several warps per Gaussian for latency hiding.  The
+// block's 32 x 3K SH tangent values are one contiguous run of v: the block
+// stages them once, coalesced, into shared memory (row stride 3K + 1, odd,
+// so the lanes' reads of their own rows hit distinct banks).
 constexpr int kJvpWarps = 4;
 
 template <int DEG>
 __global__ void __launch_bounds__(32 * kJvpWarps) k_prep_jvp(Ctx c, const float* v) {
-    const int g = blockIdx.x * 32 + (threadIdx.x & 31);
-    if (g < c.G) prep_jvp_gauss<DEG>(c, v, g, threadIdx.x >> 5, kJvpWarps);
+    constexpr int K3 = 3 * Sh<DEG>::K;
+    __shared__ float s_dsh[32 * (K3 + 1)];
+    const int g0 = blockIdx.x * 32;
+    const int lane = threadIdx.x & 31;
+    const float* src = v + 11ll * c.G + (long long)g0 * K3;
+    const int n = min(32, c.G - g0) * K3;
+    for (int i = threadIdx.x; i < n; i += 32 * kJvpWarps) s_dsh[(i / K3) * (K3 + 1) + i % K3] = src[i];
+    __syncthreads();
+    const int g = g0 + lane;
+    if (g < c.G) prep_jvp_gauss<DEG>(c, v, s_dsh + lane * (K3 + 1), g, threadIdx.x >> 5, kJvpWarps);
 }
 
 // The same for every scene of a batch: Gaussian chunks, tangent = the scene's p.
@@ -656,17 +676,33 @@ __global__ void __launch_bounds__(kBatchBlock) kb_prep_jvp(BatchTables t) {
     for (int k = blockIdx.x; k < n; k += gridDim.x) {
         const int4 ch = t.gchunks[k];
         for (int g = ch.y + (int)(threadIdx.x & 31); g < ch.z; g += 32)
-            prep_jvp_gauss<DEG>(t.ctxs[ch.x], t.vecs[ch.x].p, g, threadIdx.x >> 5, kJvpWarps);
+            prep_jvp_gauss<DEG>(t.ctxs[ch.x], t.vecs[ch.x].p,
+                                t.vecs[ch.x].p + 11ll * t.ctxs[ch.x].G + (long long)g * 3 * Sh<DEG>::K, g,
+                                threadIdx.x >> 5, kJvpWarps);
     }
 }
 
 constexpr int kPrepBlock = 128;
 
+// out[idx] = val + the damping of v (when v is given), v^T out into dot.
+template <bool kDot>
+__device__ __forceinline__ void damp_put(const Ctx& c, float* out, const float* v, const float* D, long long idx,
+                                         float val, Dot2& dot) {
+    if (v) {
+        const float damp = c.damping_mode == 1 ? c.lambda * D[idx] : c.lambda;
+        val += damp * v[idx];
+        if (kDot) dot.add(v[idx], val);
+    }
+    out[idx] = val;
+}
+
 // J^T of Gaussian g's cotangent slots over its visible views, written to out
 // (+ lambda damping of v when v is given; v^T out accumulated into dot).
+// With sh_stage the 3K SH entries go to that shared-memory row instead, for
+// the caller to store coalesced.
 template <int DEG, bool kDot>
 __device__ __forceinline__ void prep_vjp_gauss(const Ctx& c, int g, float* out, const float* v, const float* D,
-                                               Dot2& dot) {
+                                               Dot2& dot, float* sh_stage = nullptr) {
     using L = Jac<DEG>;
     constexpr int K = Sh<DEG>::K;
     constexpr int K3 = 3 * K;
@@ -677,12 +713,16 @@ __device__ __forceinline__ void prep_vjp_gauss(const Ctx& c, int g, float* out, 
     float gsh[K3];
 #pragma unroll
     for (int k = 0; k < K3; ++k) gsh[k] = 0.f;
+    float X[3] = {0.f, 0.f, 0.f};
+    if (DEG > 0) load_mean(c.params, g, X);
     for (int slot = 0; slot < c.nv; ++slot) {
         const long long i = (long long)slot * c.G + g;
         const int4 rc = c.rect[i];
         if (rc.x > rc.y) continue;
         float J[L::N];
         load_jac<DEG>(c, slot, g, J);
+        float Y[K];
+        pair_Y<DEG>(c.cams[c.views[slot]], X, Y);
         const float4* ct = reinterpret_cast<const float4*>(c.cot + i * kCotF);
         const float4 c0 = ct[0], c1 = ct[1], c2 = ct[2];
         const float cot[9] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, c2.x};
@@ -702,36 +742,67 @@ __device__ __forceinline__ void prep_vjp_gauss(const Ctx& c, int g, float* out, 
         gth += J[L::kOp] * cot[5];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            const float y = jac_Y<DEG>(J, k);
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) gsh[3 * k + ch] += y * ccol[ch];
+            for (int ch = 0; ch < 3; ++ch) gsh[3 * k + ch] += Y[k] * ccol[ch];
         }
     }
     const long long G = c.G;
-    auto put = [&](long long idx, float val) {
-        if (v) {
-            const float damp = c.damping_mode == 1 ? c.lambda * D[idx] : c.lambda;
-            val += damp * v[idx];
-            if (kDot) dot.add(v[idx], val);
-        }
-        out[idx] = val;
-    };
 #pragma unroll
-    for (int k = 0; k < 3; ++k) put(3ll * g + k, gu[k]);
+    for (int k = 0; k < 3; ++k) damp_put<kDot>(c, out, v, D, 3ll * g + k, gu[k], dot);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) put(3 * G + 3ll * g + k, gu[3 + k]);
+    for (int k = 0; k < 3; ++k) damp_put<kDot>(c, out, v, D, 3 * G + 3ll * g + k, gu[3 + k], dot);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) put(6 * G + 4ll * g + k, gu[6 + k]);
-    put(10 * G + g, gth);
+    for (int k = 0; k < 4; ++k) damp_put<kDot>(c, out, v, D, 6 * G + 4ll * g + k, gu[6 + k], dot);
+    damp_put<kDot>(c, out, v, D, 10 * G + g, gth, dot);
+    if (sh_stage) {
 #pragma unroll
-    for (int k = 0; k < K3; ++k) put(11 * G + (long long)g * K3 + k, gsh[k]);
+        for (int k = 0; k < K3; ++k) sh_stage[k] = gsh[k];
+    } else {
+#pragma unroll
+        for (int k = 0; k < K3; ++k) damp_put<kDot>(c, out, v, D, 11 * G + (long long)g * K3 + k, gsh[k], dot);
+    }
 }
 
+// One warp per 32 consecutive Gaussians (grid-stride over warp groups).  The
+// SH entries of the 32 Gaussians are one contiguous run of out, v and D: each
+// lane stages its 3K entries in shared memory (row stride 3K + 1), then the
+// warp stores the run coalesced, with the damping and the dot product.
 template <int DEG, bool kDot>
 __global__ void __launch_bounds__(kPrepBlock) k_prep_vjp(Ctx c, float* out, const float* v, const float* D) {
+    constexpr int K3 = 3 * Sh<DEG>::K;
+    __shared__ float s_sh[kPrepBlock / 32][32 * (K3 + 1)];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float* stage = s_sh[wid];
     Dot2 dot;
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < c.G; g += gridDim.x * blockDim.x)
-        prep_vjp_gauss<DEG, kDot>(c, g, out, v, D, dot);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long gw = (long long)blockIdx.x * blockDim.x + wid * 32; gw < c.G; gw += stride) {
+        const int g = (int)gw + lane;
+        if (g < c.G) prep_vjp_gauss<DEG, kDot>(c, g, out, v, D, dot, stage + lane * (K3 + 1));
+        __syncwarp();
+        const int n = (int)min(32ll, (long long)c.G - gw) * K3;
+        const long long base = 11ll * c.G + gw * K3;
+        // the run's v and D first (out may alias neither, but the compiler
+        // cannot know: loaded after a store, each would be a round trip)
+        float vv[K3], dv[K3];
+#pragma unroll
+        for (int k = 0; k < K3; ++k) {
+            const int i = k * 32 + lane;
+            vv[k] = (v && i < n) ? v[base + i] : 0.f;
+            dv[k] = (v && c.damping_mode == 1 && i < n) ? D[base + i] : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < K3; ++k) {
+            const int i = k * 32 + lane;
+            if (i >= n) continue;
+            float val = stage[(i / K3) * (K3 + 1) + i % K3];
+            if (v) {
+                val += (c.damping_mode == 1 ? c.lambda * dv[k] : c.lambda) * vv[k];
+                if (kDot) dot.add(vv[k], val);
+            }
+            out[base + i] = val;
+        }
+        __syncwarp();
+    }
     if (kDot) {
         double tot;
         if (grid_sum_last<kPrepBlock>(dot.value(), c.partials, c.counter, &tot) && threadIdx.x == 0) {
@@ -768,9 +839,10 @@ __global__ void __launch_bounds__(kBatchBlock) kb_prep_vjp(BatchTables t, int it
 }
 
 // diag(J^T W J) for Gaussian g from the Gram blocks of its visible views.
-// Gram layout (40 floats): [0,21) upper triangle of the 6x6 geometric block
-// (mu_x, mu_y, A, B, C, o) row-major; [21,39) geometric x colour, index
-// 21 + 3 f + ch; [39] the colour diagonal (same for the three channels).
+// Gram layout (42 of kGramF floats): [0,21) upper triangle of the 6x6
+// geometric block (mu_x, mu_y, A, B, C, o) row-major; [21,39) geometric x
+// colour, index 21 + 3 f + ch; [39,42) the colour diagonal per channel (the
+// rows of one sample carry per-channel weights under the SSIM term).
 __device__ __forceinline__ float gram_quad(const float* gm, const float a[9]) {
     float v = 0.f;
     int idx = 0;
@@ -785,7 +857,7 @@ __device__ __forceinline__ float gram_quad(const float* gm, const float a[9]) {
     for (int f = 0; f < 6; ++f)
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) v += 2.f * gm[21 + 3 * f + ch] * a[f] * a[6 + ch];
-    v += gm[39] * (a[6] * a[6] + a[7] * a[7] + a[8] * a[8]);
+    v += gm[39] * a[6] * a[6] + gm[40] * a[7] * a[7] + gm[41] * a[8] * a[8];
     return v;
 }
 
@@ -802,12 +874,16 @@ __global__ void __launch_bounds__(kPrepBlock) k_prep_diag(Ctx c, float* D) {
     float dsh[K3];
 #pragma unroll
     for (int k = 0; k < K3; ++k) dsh[k] = 0.f;
+    float X[3] = {0.f, 0.f, 0.f};
+    if (DEG > 0) load_mean(c.params, g, X);
     for (int slot = 0; slot < c.nv; ++slot) {
         const long long i = (long long)slot * c.G + g;
         const int4 rc = c.rect[i];
         if (rc.x > rc.y) continue;
         float J[L::N];
         load_jac<DEG>(c, slot, g, J);
+        float Y[K];
+        pair_Y<DEG>(c.cams[c.views[slot]], X, Y);
         float gm[kGramF];
         const float4* gsrc = reinterpret_cast<const float4*>(c.gram + i * kGramF);
 #pragma unroll
@@ -832,10 +908,10 @@ __global__ void __launch_bounds__(kPrepBlock) k_prep_diag(Ctx c, float* D) {
         const unsigned bits = __float_as_uint(J[L::kMask]);
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            const float y = jac_Y<DEG>(J, k);
+            const float y = Y[k];
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch)
-                if ((bits >> ch) & 1u) dsh[3 * k + ch] += gm[39] * y * y;
+                if ((bits >> ch) & 1u) dsh[3 * k + ch] += gm[39 + ch] * y * y;
         }
     }
     const long long G = c.G;

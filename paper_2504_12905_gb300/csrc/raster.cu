@@ -17,6 +17,7 @@
 //   k_jtj          fused: JVP pass then VJP pass of w * (J v) per work item
 //   k_gram         per-pair Gram blocks of the per-sample feature gradients
 //                  (App. A, Diag kernel; completed by k_prep_diag)
+//   k_ssim         the diagonal SSIM term at every sample (from full frames)
 // k_vjp, k_jtj and k_gram walk the compact lists.  Back-scatter: per
 // Gaussian, the lanes' contributions are summed with a warp reduce-scatter
 // and one lane per value issues a single atomic add into the per-(view,
@@ -56,6 +57,14 @@ __device__ __forceinline__ void setup_item(const Ctx& c, int item, Pix& p) {
     p.pcx = p.px + 0.5f;
     p.pcy = p.py + 0.5f;
     p.w = c.wsample ? (p.active ? c.wsample[p.si] : 0.f) : c.wtile[p.vt];
+}
+
+// Weight of the sample's channel-ch row in J^T W J: w, times 1 + ssim_weight
+// d^2 with the SSIM term (its row is d times the colour's).
+__device__ __forceinline__ float row_weight(const Ctx& c, const Pix& p, int ch) {
+    if (!c.ssim_d || !p.active) return p.w;
+    const float d = c.ssim_d[3 * p.si + ch];
+    return p.w * fmaf(c.ssim_weight * d, d, 1.f);
 }
 
 // The list a kernel walks: ids[b, e).
@@ -349,7 +358,16 @@ __global__ void __launch_bounds__(kRasterBlock) k_vjp(Ctx c, const float* u) {
     if (p.active) {
         load_cache(c, p.si, Cf, ncons);
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) ub[ch] = u ? u[3 * p.si + ch] : p.w * c.resid[3 * p.si + ch];
+        for (int ch = 0; ch < 3; ++ch) {
+            if (u) {
+                ub[ch] = u[3 * p.si + ch];
+            } else {
+                // J^T W r, plus ssim_weight * w * d * s for the SSIM rows
+                float r = c.resid[3 * p.si + ch];
+                if (c.ssim_s) r = fmaf(c.ssim_weight * c.ssim_d[3 * p.si + ch], c.ssim_s[3 * p.si + ch], r);
+                ub[ch] = p.w * r;
+            }
+        }
     }
     backward_pass(c, p, compact_list(c, p), s_rec, s_id, ub, Cf, ncons);
 }
@@ -361,7 +379,7 @@ __device__ __forceinline__ void jtj_item(const Ctx& c, int item, float4 (*s_rec)
     float C[3], T, dC[3];
     int ncons;
     forward_pass<true, false>(c, p, L, s_rec, s_id, C, T, dC, ncons);
-    const float ub[3] = {p.w * dC[0], p.w * dC[1], p.w * dC[2]};
+    const float ub[3] = {row_weight(c, p, 0) * dC[0], row_weight(c, p, 1) * dC[1], row_weight(c, p, 2) * dC[2]};
     backward_pass(c, p, L, s_rec, s_id, ub, C, ncons);
 }
 
@@ -394,10 +412,11 @@ void launch_b_jtj(const BatchTables& t, int grid, cudaStream_t st) {
 }
 
 // Gram blocks: per contributing (sample, Gaussian), with e = d alpha /
-// d(mu_x, mu_y, A, B, C, o), h_ch = d C_ch / d alpha and q = alpha T:
-//   [0,21)   w (sum_ch h_ch^2) e e^T   (upper triangle, row-major)
-//   [21,39)  w q h_ch e_f              (index 21 + 3 f + ch)
-//   [39]     w q^2
+// d(mu_x, mu_y, A, B, C, o), h_ch = d C_ch / d alpha, q = alpha T and w_ch
+// the weight of the sample's channel-ch row:
+//   [0,21)   (sum_ch w_ch h_ch^2) e e^T   (upper triangle, row-major)
+//   [21,39)  w_ch q h_ch e_f              (index 21 + 3 f + ch)
+//   [39,42)  w_ch q^2
 __global__ void __launch_bounds__(kRasterBlock) k_gram(Ctx c) {
     LMRS_RASTER_PROLOGUE
     const List L = compact_list(c, p);
@@ -405,6 +424,7 @@ __global__ void __launch_bounds__(kRasterBlock) k_gram(Ctx c) {
     float Cf[3] = {0.f, 0.f, 0.f};
     int ncons = 0;
     if (p.active) load_cache(c, p.si, Cf, ncons);
+    const float wch[3] = {row_weight(c, p, 0), row_weight(c, p, 1), row_weight(c, p, 2)};
     const int lane_end = p.active ? L.b + ncons : L.b;
     int warp_end = lane_end;
 #pragma unroll
@@ -447,8 +467,8 @@ __global__ void __launch_bounds__(kRasterBlock) k_gram(Ctx c) {
                         e[4] = -0.5f * raw * dy * dy;
                         e[5] = gval;
                     }
-                    const float H2 = p.w * (h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
-                    float vals[40];
+                    const float H2 = wch[0] * h[0] * h[0] + wch[1] * h[1] * h[1] + wch[2] * h[2] * h[2];
+                    float vals[42];
                     int idx = 0;
 #pragma unroll
                     for (int f = 0; f < 6; ++f)
@@ -457,12 +477,13 @@ __global__ void __launch_bounds__(kRasterBlock) k_gram(Ctx c) {
 #pragma unroll
                     for (int f = 0; f < 6; ++f)
 #pragma unroll
-                        for (int ch = 0; ch < 3; ++ch) vals[21 + 3 * f + ch] = p.w * q * h[ch] * e[f];
-                    vals[39] = p.w * q * q;
+                        for (int ch = 0; ch < 3; ++ch) vals[21 + 3 * f + ch] = wch[ch] * q * h[ch] * e[f];
+#pragma unroll
+                    for (int ch = 0; ch < 3; ++ch) vals[39 + ch] = wch[ch] * q * q;
 #pragma unroll
                     for (int k = 0; k < 32; ++k) v[k] = vals[k];
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) v2[k] = vals[32 + k];
+                    for (int k = 0; k < 10; ++k) v2[k] = vals[32 + k];
                     T *= 1.f - alpha;
                 }
             }
@@ -472,7 +493,7 @@ __global__ void __launch_bounds__(kRasterBlock) k_gram(Ctx c) {
                 atomicAdd(dst + lane, v[0]);
                 warp_reduce_scatter<16>(v2);
                 const int idx = lane >> 1;
-                if (!(lane & 1) && idx < 8) atomicAdd(dst + 32 + idx, v2[0]);
+                if (!(lane & 1) && idx < 10) atomicAdd(dst + 32 + idx, v2[0]);
             }
         }
         __syncwarp();
@@ -513,6 +534,132 @@ __global__ void __launch_bounds__(256) k_full(Ctx c, float* images) {
         dst[1] = C[1];
         dst[2] = C[2];
     }
+}
+
+// Diagonal SSIM term at every sample (supplementary material: SSIM of
+// Wang et al. 2004 with an 11 x 11 Gaussian window, sigma 1.5, out-of-image
+// pixels counting as 0, C1 = 0.01^2, C2 = 0.03^2).  One warp per work item,
+// one sample per lane, over the full frame and the target.  Two passes over
+// the window: the means mx, my and dm = mean of X - Y, then the centred
+// second moments vx, vy, cxy and vd = Var(X - Y), so nothing is formed as
+// E[X^2] - mx^2.  With A1 = 2 mx my + C1, A2 = 2 cxy + C2, B1 = mx^2 + my^2 +
+// C1, B2 = vx + vy + C2, D1 = dm^2 = B1 - A1 and D2 = vd = B2 - A2:
+//   s = 1 - A1 A2 / (B1 B2) = (A1 D2 + B2 D1) / (B1 B2),
+// a sum of non-negative terms.  The derivative through the pixel's own
+// colour (g0 the centre weight: dA1 = 2 g0 my, dB1 = 2 g0 mx, dA2 =
+// 2 g0 (Y_i - my), dB2 = 2 g0 (X_i - mx)) is d = -N / (B1 B2) with
+//   N = dA1 A2 + A1 dA2 - (1 - s)(dB1 B2 + B1 dB2)
+//     = (dA1 - dB1) A2 - dB1 D2 + A1 (dA2 - dB2) - D1 dB2 + s (dB1 B2 + B1 dB2),
+// dA1 - dB1 = -2 g0 dm and dA2 - dB2 = -2 g0 ((X_i - Y_i) - dm) taken directly.
+constexpr int kSsimRad = 5;
+
+// s and d of one sample's three channels; returns sum_ch s^2.
+__device__ float ssim_sample(const Ctx& c, const Pix& p) {
+    // normalised 1D window; the 2D weights are the products g1[a] g1[b]
+    float g1[2 * kSsimRad + 1], z = 0.f;
+#pragma unroll
+    for (int k = 0; k <= 2 * kSsimRad; ++k) {
+        const float t = (float)(k - kSsimRad);
+        g1[k] = expf(-t * t * (1.f / 4.5f));
+        z += g1[k];
+    }
+#pragma unroll
+    for (int k = 0; k <= 2 * kSsimRad; ++k) g1[k] /= z;
+    const int cam = c.views[p.slot];
+    const float* X = c.frames + (long long)p.slot * c.H * c.W * 3;
+    const float* Y = c.targets ? c.targets + (long long)cam * c.H * c.W * 3 : nullptr;
+    float mx[3] = {0.f, 0.f, 0.f}, my[3] = {0.f, 0.f, 0.f}, dm[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a <= 2 * kSsimRad; ++a) {
+        const int y = p.py + a - kSsimRad;
+        if (y < 0 || y >= c.H) continue;
+        float rx[3] = {0.f, 0.f, 0.f}, ry[3] = {0.f, 0.f, 0.f}, rd[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int b = 0; b <= 2 * kSsimRad; ++b) {
+            const int x = p.px + b - kSsimRad;
+            if (x < 0 || x >= c.W) continue;
+            const long long o = ((long long)y * c.W + x) * 3;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                const float xv = X[o + ch], yv = Y ? Y[o + ch] : 0.f;
+                rx[ch] = fmaf(g1[b], xv, rx[ch]);
+                ry[ch] = fmaf(g1[b], yv, ry[ch]);
+                rd[ch] = fmaf(g1[b], xv - yv, rd[ch]);
+            }
+        }
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            mx[ch] = fmaf(g1[a], rx[ch], mx[ch]);
+            my[ch] = fmaf(g1[a], ry[ch], my[ch]);
+            dm[ch] = fmaf(g1[a], rd[ch], dm[ch]);
+        }
+    }
+    float vx[3] = {0.f, 0.f, 0.f}, vy[3] = {0.f, 0.f, 0.f}, cxy[3] = {0.f, 0.f, 0.f}, vd[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a <= 2 * kSsimRad; ++a) {
+        const int y = p.py + a - kSsimRad;
+        const bool yin = y >= 0 && y < c.H;
+        float rx[3] = {0.f, 0.f, 0.f}, ry[3] = {0.f, 0.f, 0.f}, rc[3] = {0.f, 0.f, 0.f}, rd[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int b = 0; b <= 2 * kSsimRad; ++b) {
+            const int x = p.px + b - kSsimRad;
+            const bool in = yin && x >= 0 && x < c.W;
+            const long long o = ((long long)y * c.W + x) * 3;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                const float xv = in ? X[o + ch] : 0.f;
+                const float yv = (in && Y) ? Y[o + ch] : 0.f;
+                const float ex = xv - mx[ch], ey = yv - my[ch], ed = (xv - yv) - dm[ch];
+                rx[ch] = fmaf(g1[b] * ex, ex, rx[ch]);
+                ry[ch] = fmaf(g1[b] * ey, ey, ry[ch]);
+                rc[ch] = fmaf(g1[b] * ex, ey, rc[ch]);
+                rd[ch] = fmaf(g1[b] * ed, ed, rd[ch]);
+            }
+        }
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            vx[ch] = fmaf(g1[a], rx[ch], vx[ch]);
+            vy[ch] = fmaf(g1[a], ry[ch], vy[ch]);
+            cxy[ch] = fmaf(g1[a], rc[ch], cxy[ch]);
+            vd[ch] = fmaf(g1[a], rd[ch], vd[ch]);
+        }
+    }
+    constexpr float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
+    const float g0 = g1[kSsimRad] * g1[kSsimRad];
+    const long long pix = ((long long)p.py * c.W + p.px) * 3;
+    float sq = 0.f;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        const float xi = X[pix + ch], yi = Y ? Y[pix + ch] : 0.f;
+        const float A1 = 2.f * mx[ch] * my[ch] + C1, A2 = 2.f * cxy[ch] + C2;
+        const float B1 = mx[ch] * mx[ch] + my[ch] * my[ch] + C1, B2 = vx[ch] + vy[ch] + C2;
+        const float D1 = dm[ch] * dm[ch], D2 = vd[ch];
+        const float BB = B1 * B2;
+        const float sv = (A1 * D2 + B2 * D1) / BB;
+        const float dB1 = 2.f * g0 * mx[ch], dB2 = 2.f * g0 * (xi - mx[ch]);
+        const float dA1mB1 = -2.f * g0 * dm[ch], dA2mB2 = -2.f * g0 * ((xi - yi) - dm[ch]);
+        const float N = dA1mB1 * A2 - dB1 * D2 + A1 * dA2mB2 - D1 * dB2 + sv * (dB1 * B2 + B1 * dB2);
+        c.ssim_s[3 * p.si + ch] = sv;
+        c.ssim_d[3 * p.si + ch] = -N / BB;
+        sq = fmaf(sv, sv, sq);
+    }
+    return sq;
+}
+
+__global__ void __launch_bounds__(kRasterBlock) k_ssim(Ctx c) {
+    const int wid = threadIdx.x >> 5;
+    const int item = blockIdx.x * kRasterWarps + wid;
+    if (item >= c.nwork) return;
+    Pix p;
+    setup_item(c, item, p);
+    // the term's share of the sampled loss: ssim_weight * w * sum_ch s^2
+    double part = p.active ? (double)c.ssim_weight * (double)p.w * (double)ssim_sample(c, p) : 0.0;
+    part = warp_sum(part);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&c.sc->loss_num, part);
+}
+
+void launch_ssim(const Ctx& c, cudaStream_t st) {
+    if (c.nwork > 0) LMRS_LAUNCH(k_ssim, (unsigned)((c.nwork + kRasterWarps - 1) / kRasterWarps), kRasterBlock, 0, st, c);
 }
 
 // Importance draws of the pixel sampler (modes 1, 2), one block per (view,

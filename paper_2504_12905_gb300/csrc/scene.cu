@@ -87,6 +87,7 @@ struct lmrs_scene {
     DevBuf resid, cacheC, cacheT, cacheCh, cacheTh, cacheN;
     DevBuf x, r, z, p, Ap, minv, D, b, stage_a, stage_b;
     DevBuf sc, partials, counter, frames, sqerr;
+    DevBuf ssim_s, ssim_d, sframes;  // the SSIM term: per-sample values, full frames of the step's views
     // host state of the current step
     std::vector<int> views_h;
     int nv = 0;
@@ -105,7 +106,7 @@ struct lmrs_scene {
                 &cot, &gram, &keys, &ids, &keys_alt, &ids_alt, &ranges, &scan_tmp, &radix_tmp, &total, &tile_off,
                 &off, &wtile, &wsample, &work, &item_cost, &work_sorted, &okeys, &ovals, &okeys_alt, &ovals_alt, &otmp,
                 &cids, &clen, &binmat, &bintmp, &resid, &cacheC, &cacheT, &cacheCh, &cacheTh, &cacheN, &x, &r, &z, &p, &Ap,
-                &minv, &D, &b, &stage_a, &stage_b, &sc, &partials, &counter, &frames, &sqerr};
+                &minv, &D, &b, &stage_a, &stage_b, &sc, &partials, &counter, &frames, &sqerr, &ssim_s, &ssim_d, &sframes};
     }
 
     Ctx ctx() const {
@@ -141,6 +142,11 @@ struct lmrs_scene {
         c.wtile = wtile.as<float>();
         c.wsample = cfg.sample_dist != 0 ? wsample.as<float>() : nullptr;
         c.sample_dist = cfg.sample_dist;
+        const bool ssim = cfg.ssim_weight > 0.0;
+        c.ssim_s = ssim ? ssim_s.as<float>() : nullptr;
+        c.ssim_d = ssim ? ssim_d.as<float>() : nullptr;
+        c.ssim_weight = (float)cfg.ssim_weight;
+        c.frames = sframes.as<float>();
         c.S = S;
         c.work = ordered ? work_sorted.as<int2>() : work.as<int2>();
         c.item_cost = item_cost.as<int>();
@@ -364,6 +370,10 @@ lmrs_status build_layout(lmrs_scene* s) {
     TRY(ensure(s, s->work, sizeof(int2) * std::max<size_t>(work.size(), 1)));
     TRY(ensure(s, s->off, (size_t)s->S));
     if (s->cfg.sample_dist != 0) TRY(ensure(s, s->wsample, sizeof(float) * (size_t)s->S));
+    if (s->cfg.ssim_weight > 0.0) {
+        TRY(ensure(s, s->ssim_s, sizeof(float) * 3 * s->S));
+        TRY(ensure(s, s->ssim_d, sizeof(float) * 3 * s->S));
+    }
     TRY(ensure(s, s->resid, sizeof(float) * 3 * s->S));
     TRY(ensure(s, s->cacheC, sizeof(float) * 3 * s->S));
     TRY(ensure(s, s->cacheT, sizeof(float) * s->S));
@@ -490,7 +500,8 @@ lmrs_status lmrs_scene_create(const lmrs_config* cfg, int64_t n_gauss, const flo
     if (cfg->sh_degree < 0 || cfg->sh_degree > 3 || cfg->tile_w <= 0 || cfg->tile_h <= 0 ||
         cfg->tile_w * cfg->tile_h > 256 || !(cfg->sample_frac > 0.0) || cfg->cg_iters < 0 ||
         (cfg->damping_mode != 0 && cfg->damping_mode != 1) || (cfg->weight_mode != 0 && cfg->weight_mode != 1) ||
-        !(cfg->lambda >= 0.0) || cfg->sample_dist < 0 || cfg->sample_dist > 2)
+        !(cfg->lambda >= 0.0) || cfg->sample_dist < 0 || cfg->sample_dist > 2 ||
+        !(cfg->ssim_weight >= 0.0 && cfg->ssim_weight < 1e30))
         return LMRS_ERR_INVALID_ARG;
     for (int i = 0; i < n_cams; ++i)
         if (cams_host[i].width != cams_host[0].width || cams_host[i].height != cams_host[0].height ||
@@ -677,15 +688,30 @@ lmrs_status lmrs_preprocess(lmrs_scene* s, const int32_t* view_ids, int32_t n_vi
     return LMRS_OK;
 }
 
-lmrs_status lmrs_render(lmrs_scene* s, float* images_dev, float* residuals_dev) {
-    TRY(check_scene(s));
+}  // extern "C"
+
+namespace {
+
+// The forward render of a step; with_ssim adds the SSIM term of the samples
+// (full frames of the step's views, then k_ssim).
+lmrs_status do_render(lmrs_scene* s, float* images_dev, float* residuals_dev, bool with_ssim) {
     TimerScope ts_(s);
     TRY(need_pre(s));
     s->ordered = false;  // the forward render indexes the work items in their natural order
+    const bool ssim = with_ssim && s->cfg.ssim_weight > 0.0;
+    const size_t frames = (size_t)s->nv * s->H * s->W * 3;
+    if (ssim) TRY(ensure(s, s->sframes, sizeof(float) * frames));
     Ctx c = s->ctx();
     CK(s, cudaMemsetAsync(&c.sc->loss_num, 0, offsetof(Scalars, eta) - offsetof(Scalars, loss_num), s->st));
     launch_raster_fwd_samples(c, s->st);
-    if (images_dev) launch_raster_full(c, images_dev, s->st);
+    if (ssim) {
+        launch_raster_full(c, s->sframes.as<float>(), s->st);
+        launch_ssim(c, s->st);
+        if (images_dev)
+            CK(s, cudaMemcpyAsync(images_dev, s->sframes.p, sizeof(float) * frames, cudaMemcpyDeviceToDevice, s->st));
+    } else if (images_dev) {
+        launch_raster_full(c, images_dev, s->st);
+    }
     launch_order_work(c, s->okeys.as<unsigned long long>(), s->ovals.as<unsigned int>(),
                       s->okeys_alt.as<unsigned long long>(), s->ovals_alt.as<unsigned int>(), s->otmp.p, s->otmp.cap,
                       s->work_sorted.as<int2>(), s->st);
@@ -695,6 +721,15 @@ lmrs_status lmrs_render(lmrs_scene* s, float* images_dev, float* residuals_dev) 
         CK(s, cudaMemcpyAsync(residuals_dev, s->resid.p, sizeof(float) * 3 * s->S, cudaMemcpyDeviceToDevice, s->st));
     s->rendered = true;
     return LMRS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lmrs_status lmrs_render(lmrs_scene* s, float* images_dev, float* residuals_dev) {
+    TRY(check_scene(s));
+    return do_render(s, images_dev, residuals_dev, true);
 }
 
 lmrs_status lmrs_jvp(lmrs_scene* s, const float* v, float* u) {
@@ -875,7 +910,7 @@ lmrs_status lmrs_eval_mse(lmrs_scene* s, double* mse) {
         views.clear();
         for (int v = c0; v < std::min(s->n_cams, c0 + kChunk); ++v) views.push_back(v);
         TRY(lmrs_preprocess(s, views.data(), (int32_t)views.size(), 0));
-        TRY(lmrs_render(s, s->frames.as<float>(), nullptr));
+        TRY(do_render(s, s->frames.as<float>(), nullptr, false));
         TimerScope ts_(s);
         launch_frame_sqerr(s->ctx(), s->frames.as<float>(), s->sqerr.as<double>(), s->st);
         CHECK_LAUNCH(s);
@@ -1036,14 +1071,14 @@ int64_t lmrs_footprint_bytes(const lmrs_config* cfg, int64_t n_gauss, int32_t n_
     }
     const double pairs = nv * G, entries = tpp * pairs, S = nv * S_view, items = nv * items_view;
     // rec 96, Jacobian cache, rect 16, depth keys/values and their
-    // alternates 24, counts 8, cotangent slots 48, Gram blocks 160; scan and
+    // alternates 24, counts 8, cotangent slots 48, Gram blocks 176; scan and
     // sort scratch ~2
-    const double per_pair = 96 + 16.0 * jac_f4(cfg->sh_degree) + 16 + 24 + 8 + 48 + 160 + 2;
+    const double per_pair = 96 + 16.0 * jac_f4(cfg->sh_degree) + 16 + 24 + 8 + 48 + 4.0 * kGramF + 2;
     // keys, ids and their alternates 16, compact lists 4 per work item of a tile
     const double per_entry = 16 + 4.0 * max_items + 1;
     // offset 1, residual 12, FP32 and BF16 caches 12 + 4 + 6 + 2, stop index 4,
-    // importance weight 4
-    const double per_sample = 41 + (cfg->sample_dist != 0 ? 4 : 0);
+    // importance weight 4, SSIM values 24
+    const double per_sample = 41 + (cfg->sample_dist != 0 ? 4 : 0) + (cfg->ssim_weight > 0.0 ? 24 : 0);
     // tile offset, weight, range 16; compact lengths 4 per item; work items
     // and their ordering buffers 36
     const double per_view_tile = 16 + 4.0 * max_items;
@@ -1053,7 +1088,19 @@ int64_t lmrs_footprint_bytes(const lmrs_config* cfg, int64_t n_gauss, int32_t n_
     const double var = pairs * per_pair + entries * per_entry + S * per_sample + nv * tx * ty * per_view_tile +
                        items * per_item;
     const double targets = (double)n_cams * height * width * 3 * sizeof(float);
-    return (int64_t)(fixed + targets + 1.25 * var);
+    // full frames of the step's views for the SSIM windows
+    const double frames = cfg->ssim_weight > 0.0 ? nv * height * width * 3 * sizeof(float) : 0.0;
+    return (int64_t)(fixed + targets + frames + 1.25 * var);
+}
+
+lmrs_status lmrs_get_ssim(lmrs_scene* s, float* s_host, float* d_host) {
+    TRY(check_scene(s));
+    if (!(s->cfg.ssim_weight > 0.0)) return fail(s, LMRS_ERR_INVALID_ARG, "the SSIM term is off");
+    TRY(need_render(s));
+    if (s_host) CK(s, cudaMemcpyAsync(s_host, s->ssim_s.p, sizeof(float) * 3 * s->S, cudaMemcpyDeviceToHost, s->st));
+    if (d_host) CK(s, cudaMemcpyAsync(d_host, s->ssim_d.p, sizeof(float) * 3 * s->S, cudaMemcpyDeviceToHost, s->st));
+    CK(s, cudaStreamSynchronize(s->st));
+    return LMRS_OK;
 }
 
 lmrs_status lmrs_get_sample_weights(lmrs_scene* s, float* w) {

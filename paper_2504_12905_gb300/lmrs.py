@@ -39,7 +39,7 @@ class Config(C.Structure):
                 ("lambda_", C.c_double), ("damping_mode", C.c_int32), ("cg_iters", C.c_int32),
                 ("lr_warm", C.c_double), ("lr_cap", C.c_double), ("color_bound", C.c_double),
                 ("warm_iters", C.c_int32), ("cache_bf16", C.c_int32), ("seed", C.c_uint64),
-                ("sample_dist", C.c_int32)]
+                ("sample_dist", C.c_int32), ("ssim_weight", C.c_double)]
 
 
 class CgStats(C.Structure):
@@ -113,6 +113,7 @@ _SIGS = {
     "lmrs_get_samples": (_S, [_P, _P, _P]),
     "lmrs_get_tile_lists": (_S, [_P, _P, _P]),
     "lmrs_get_sample_weights": (_S, [_P, _P]),
+    "lmrs_get_ssim": (_S, [_P, _P, _P]),
     "lmrs_set_timing": (_S, [_P, C.c_int32]),
     "lmrs_get_timing": (_S, [_P, C.POINTER(KernelTime), C.c_int32, C.POINTER(C.c_int32)]),
     "lmrs_batch_create": (_S, [_P, C.c_int32, C.c_int32, _P, C.POINTER(_P)]),
@@ -335,6 +336,14 @@ def lmrs_get_sample_weights(scene, n_samples):
     out = np.empty(int(n_samples), np.float32)
     _check(lib().lmrs_get_sample_weights(scene, out.ctypes.data), scene)
     return out
+
+
+def lmrs_get_ssim(scene, n_samples):
+    """(s, d), each n_samples x 3: the SSIM residual and its own-pixel derivative."""
+    s = np.empty((int(n_samples), 3), np.float32)
+    d = np.empty((int(n_samples), 3), np.float32)
+    _check(lib().lmrs_get_ssim(scene, s.ctypes.data, d.ctypes.data), scene)
+    return s, d
 
 
 def lmrs_set_timing(scene, enable=True):

@@ -27,10 +27,10 @@ def _scenes(n=5, seed=23):
     return out
 
 
-def _make(torch, lmrs, sc, tgt, stream):
+def _make(torch, lmrs, sc, tgt, stream, **extra):
     t = torch.from_numpy(tgt).cuda()
     s = lmrs.Scene(torch.from_numpy(sc.params).cuda(), sc.cams, sc.n_gauss, 0, targets=t, stream=stream,
-                   samples_per_tile=32, lambda_=0.1, damping_mode=0, cg_iters=8, seed=0x5EED)
+                   samples_per_tile=32, lambda_=0.1, damping_mode=0, cg_iters=8, seed=0x5EED, **extra)
     s._t = t
     return s
 
@@ -81,6 +81,30 @@ def test_batch_matches_solo_steps_and_oracle():
     a_norm = np.sqrt(max(e @ o.apply(e, D), 0.0)) / np.sqrt(x_ref @ o.apply(x_ref, D))
     assert a_norm <= 1e-3
     lmrs.lmrs_batch_destroy(b1)
+    lmrs.lmrs_batch_destroy(b)
+
+
+def test_batch_with_the_ssim_term_matches_solo():
+    import torch
+
+    from paper_2504_12905_gb300 import lmrs
+
+    scenes = _scenes(3, seed=31)
+    streams = [torch.cuda.Stream() for _ in scenes]
+    batch_sc = [_make(torch, lmrs, sc, tgt, streams[i].cuda_stream, ssim_weight=0.2)
+                for i, (sc, tgt) in enumerate(scenes)]
+    solo_sc = [_make(torch, lmrs, sc, tgt, None, ssim_weight=0.2) for sc, tgt in scenes]
+    b = lmrs.lmrs_batch_create([s.h for s in batch_sc], n_threads=2)
+    views = [list(range(len(sc.cams))) for sc, _ in scenes]
+    st_b = lmrs.lmrs_batch_lm_step(b, views, [3] * len(scenes))
+    for i, s in enumerate(solo_sc):
+        st = lmrs.lmrs_lm_step(s.h, views[i], 3)
+        xs = np.zeros(s.n_params, np.float32)
+        xb = np.zeros(s.n_params, np.float32)
+        lmrs.lmrs_get_solution(s.h, xs)
+        lmrs.lmrs_get_solution(batch_sc[i].h, xb)
+        assert normwise_rel(xb, xs) <= 1e-3, i
+        assert st_b[i].loss == pytest.approx(st.loss, rel=1e-6)
     lmrs.lmrs_batch_destroy(b)
 
 
