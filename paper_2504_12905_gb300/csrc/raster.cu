@@ -21,11 +21,20 @@
 // k_vjp, k_jtj and k_gram walk the compact lists.  Back-scatter: per
 // Gaussian, the lanes' contributions are summed with a warp reduce-scatter
 // and one lane per value issues a single atomic add into the per-(view,
-// Gaussian) slot.
+// Gaussian) slot; when at most four lanes contribute, they add their values
+// directly instead.
 #include "common.cuh"
 #include "reduce.cuh"
 
 namespace lmrs {
+
+// Back-scatter of one list entry: when at most this many lanes contribute,
+// each issues its own atomics and the warp reduce-scatter is skipped (the
+// reduce costs ~50 instructions; more contributors per address make the
+// atomics contend).  Measured on the 200k and 1.5M workloads: 4 and 8 equal,
+// 16 clearly slower.
+constexpr int kDirectMax = 4;      // 9 cotangents per contributing lane
+constexpr int kGramDirectMax = 4;  // 42 Gram entries per contributing lane
 
 constexpr int kRasterWarps = 4;
 constexpr int kRasterBlock = kRasterWarps * kWarp;
@@ -257,9 +266,18 @@ __device__ __forceinline__ void backward_pass(const Ctx& c, const Pix& p, List L
                     T *= 1.f - alpha;
                 }
             }
-            if (__any_sync(kFull, contrib)) {
-                const int idx = warp_reduce_scatter9(v);
-                if (!(lane & 1) && idx >= 0) atomicAdd(cot_base + (long long)s_id[j] * kCotF + idx, v[0]);
+            const unsigned ball = __ballot_sync(kFull, contrib);
+            if (ball) {
+                if (__popc(ball) <= kDirectMax) {
+                    if (contrib) {
+                        float* dst = cot_base + (long long)s_id[j] * kCotF;
+#pragma unroll
+                        for (int q = 0; q < 9; ++q) atomicAdd(dst + q, v[q]);
+                    }
+                } else {
+                    const int idx = warp_reduce_scatter9(v);
+                    if (!(lane & 1) && idx >= 0) atomicAdd(cot_base + (long long)s_id[j] * kCotF + idx, v[0]);
+                }
             }
         }
         __syncwarp();
@@ -487,13 +505,23 @@ __global__ void __launch_bounds__(kRasterBlock) k_gram(Ctx c) {
                     T *= 1.f - alpha;
                 }
             }
-            if (__any_sync(kFull, contrib)) {
+            const unsigned ball = __ballot_sync(kFull, contrib);
+            if (ball) {
                 float* dst = gbase + (long long)s_id[j] * kGramF;
-                warp_reduce_scatter<32>(v);
-                atomicAdd(dst + lane, v[0]);
-                warp_reduce_scatter<16>(v2);
-                const int idx = lane >> 1;
-                if (!(lane & 1) && idx < 10) atomicAdd(dst + 32 + idx, v2[0]);
+                if (__popc(ball) <= kGramDirectMax) {
+                    if (contrib) {
+#pragma unroll
+                        for (int k = 0; k < 32; ++k) atomicAdd(dst + k, v[k]);
+#pragma unroll
+                        for (int k = 0; k < 10; ++k) atomicAdd(dst + 32 + k, v2[k]);
+                    }
+                } else {
+                    warp_reduce_scatter<32>(v);
+                    atomicAdd(dst + lane, v[0]);
+                    warp_reduce_scatter<16>(v2);
+                    const int idx = lane >> 1;
+                    if (!(lane & 1) && idx < 10) atomicAdd(dst + 32 + idx, v2[0]);
+                }
             }
         }
         __syncwarp();
