@@ -717,15 +717,21 @@ __device__ __forceinline__ void prep_vjp_gauss(const Ctx& c, int g, float* out, 
     if (DEG > 0) load_mean(c.params, g, X);
     for (int slot = 0; slot < c.nv; ++slot) {
         const long long i = (long long)slot * c.G + g;
-        const int4 rc = c.rect[i];
-        if (rc.x > rc.y) continue;
+        // the cache and cotangent slots exist for culled pairs too: their
+        // loads go out with the rectangle's, and a culled pair's values are
+        // replaced by zeros (they are stale there)
         float J[L::N];
         load_jac<DEG>(c, slot, g, J);
-        float Y[K];
-        pair_Y<DEG>(c.cams[c.views[slot]], X, Y);
         const float4* ct = reinterpret_cast<const float4*>(c.cot + i * kCotF);
         const float4 c0 = ct[0], c1 = ct[1], c2 = ct[2];
-        const float cot[9] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, c2.x};
+        const int4 rc = c.rect[i];
+        const bool vis = rc.x <= rc.y;
+#pragma unroll
+        for (int k = 0; k < L::N; ++k) J[k] = vis ? J[k] : 0.f;
+        float Y[K];
+        pair_Y<DEG>(c.cams[c.views[slot]], X, Y);
+        const float cot[9] = {vis ? c0.x : 0.f, vis ? c0.y : 0.f, vis ? c0.z : 0.f, vis ? c0.w : 0.f, vis ? c1.x : 0.f,
+                              vis ? c1.y : 0.f, vis ? c1.z : 0.f, vis ? c1.w : 0.f, vis ? c2.x : 0.f};
         const unsigned bits = __float_as_uint(J[L::kMask]);
         float ccol[3];
 #pragma unroll
@@ -878,12 +884,10 @@ __global__ void __launch_bounds__(kPrepBlock) k_prep_diag(Ctx c, float* D) {
     if (DEG > 0) load_mean(c.params, g, X);
     for (int slot = 0; slot < c.nv; ++slot) {
         const long long i = (long long)slot * c.G + g;
-        const int4 rc = c.rect[i];
-        if (rc.x > rc.y) continue;
+        // loads before the visibility test, a culled pair's (stale) cache
+        // values replaced by zeros
         float J[L::N];
         load_jac<DEG>(c, slot, g, J);
-        float Y[K];
-        pair_Y<DEG>(c.cams[c.views[slot]], X, Y);
         float gm[kGramF];
         const float4* gsrc = reinterpret_cast<const float4*>(c.gram + i * kGramF);
 #pragma unroll
@@ -891,6 +895,14 @@ __global__ void __launch_bounds__(kPrepBlock) k_prep_diag(Ctx c, float* D) {
             const float4 q = gsrc[k];
             gm[4 * k] = q.x; gm[4 * k + 1] = q.y; gm[4 * k + 2] = q.z; gm[4 * k + 3] = q.w;
         }
+        const int4 rc = c.rect[i];
+        const bool vis = rc.x <= rc.y;
+#pragma unroll
+        for (int k = 0; k < L::N; ++k) J[k] = vis ? J[k] : 0.f;
+#pragma unroll
+        for (int k = 0; k < kGramF; ++k) gm[k] = vis ? gm[k] : 0.f;
+        float Y[K];
+        pair_Y<DEG>(c.cams[c.views[slot]], X, Y);
         // geometric parameter j: the feature tangent is column j of the Jacobian
 #pragma unroll
         for (int j = 0; j < 11; ++j) {
