@@ -377,152 +377,293 @@ void launch_ranges(const Ctx& c, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------------------
-// Direct stable binning (replaces the entry emission + tile sort when a
-// view has at most kBinMaxTiles tiles).  In the depth-sorted pair array slot
-// s occupies [s G, (s+1) G): its visible pairs by depth, then its culled ones
-// (empty rectangles).  A block takes a chunk of kBinChunk consecutive pairs
-// of one slot; warp w owns the w-th run of kBinRun pairs of the chunk and
-// handles them in order, the tiles of one pair spread over the lanes (a pair
-// touches each tile once, so the lanes never collide).
-//   count : entries per (slot, tile, chunk), tile-major in mat;
-//   scan  : exclusive prefix of mat = the output base of every (slot, tile,
-//           chunk), the start of every tile list and the total;
-//   place : per-warp counts per tile again, their prefix over the block's
-//           warps, then each warp walks its run once more and writes each
-//           entry's Gaussian index at base + warp prefix + running count.
-// Per tile the entries come out by chunk, then warp, then pair order: the
-// order of a stable sort on (slot, tile) of the depth-ordered entries.
+// Two-level stable binning of the depth-sorted pairs into the tile lists
+// (used while a view's rows and columns of tiles fit the shared-memory
+// counters; the entry emission + tile sort above covers the rest).  In the
+// depth-sorted pair array slot s occupies [s G, (s+1) G): its visible pairs
+// by depth, then its culled ones (empty rectangles).
+//   rows : each visible pair, in order, is placed into the list of every tile
+//          row its rectangle spans: counts per (slot, row, chunk of kBinChunk
+//          pairs), an exclusive scan, then the placement;
+//   tiles: one block per (slot, row) walks that row's list in order and places
+//          each pair into the row's tiles it spans: counts per tile, an
+//          exclusive scan (the tile lists' starts), then the placement in
+//          chunks of the block's warps.
+// A placement ranks a lane's pair among the warp's 32 pairs covering the same
+// bin with a ballot, warps are ranked by their order in the chunk and chunks
+// by the scan, so every list keeps the order it is read in: the tile lists
+// equal a stable sort on (slot, tile) of the depth-ordered entries.  The
+// lists a warp writes at a time are the rows of one view or the tiles of one
+// row, so its stores stay within a few dozen runs.
 // ---------------------------------------------------------------------------
 constexpr int kBinWarps = 8;
-constexpr int kBinRun = 256;
+constexpr int kBinRun = 256;                  // pairs per warp per chunk
 constexpr int kBinChunk = kBinWarps * kBinRun;
 constexpr int kBinBlock = kBinWarps * kWarp;
 
 int bin_chunks(const Ctx& c) { return (c.G + kBinChunk - 1) / kBinChunk; }
 
-size_t bin_place_smem(int T) { return (size_t)T * (sizeof(unsigned) + kBinWarps * sizeof(unsigned short)); }
+__device__ __forceinline__ int warp_min_i(int v) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v = min(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+__device__ __forceinline__ int warp_max_i(int v) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v = max(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
 
-// Calls f(tile, gaussian) for every tile of every pair of [b, e) of slot's
-// depth-ordered pairs, pairs in order, one __syncwarp between pairs.
-template <class F>
-__device__ __forceinline__ void for_run_tiles(const Ctx& c, int slot, long long b, long long e, F&& f) {
+// One round of a warp: lane l holds the l-th of 32 consecutive items, covering
+// the bins [lo, hi] (lo > hi: none).  For every bin of the union, m = the
+// lanes covering it; count(bin, m) runs on every lane (warp-uniform m), and
+// place(bin, rank) on each covering lane, rank = its position among them.
+template <class Count, class Place>
+__device__ __forceinline__ void rank_round(int lo, int hi, Count&& count, Place&& place) {
     const int lane = threadIdx.x & 31;
-    for (long long base = b; base < e; base += 32) {
-        const long long k = base + lane;
-        int4 rc = make_int4(1, 0, 1, 0);
-        unsigned g = 0u;
-        if (k < e) {
-            g = c.dvals[k];
-            rc = c.rect[(long long)slot * c.G + g];
-        }
-        const int n = (int)min(32ll, e - base);
-        for (int j = 0; j < n; ++j) {
-            const int x0 = __shfl_sync(kFull, rc.x, j), x1 = __shfl_sync(kFull, rc.y, j);
-            const int y0 = __shfl_sync(kFull, rc.z, j), y1 = __shfl_sync(kFull, rc.w, j);
-            const unsigned gj = __shfl_sync(kFull, g, j);
-            if (x0 <= x1) {
-                const int w = x1 - x0 + 1, area = w * (y1 - y0 + 1);
-                // row of q = floor((q + 0.5) / w): exact in FP32 for q < 2^22
-                const float inv_w = 1.f / (float)w;
-                for (int q = lane; q < area; q += 32) {
-                    const int qy = (int)(((float)q + 0.5f) * inv_w);
-                    f((y0 + qy) * c.tiles_x + x0 + (q - qy * w), gj);
-                }
-            }
-            __syncwarp();
-        }
+    const unsigned lt = (1u << lane) - 1u;
+    const int ulo = warp_min_i(lo <= hi ? lo : 0x7fffffff);
+    const int uhi = warp_max_i(lo <= hi ? hi : -1);
+    for (int bin = ulo; bin <= uhi; ++bin) {
+        const bool in = lo <= bin && bin <= hi;
+        const unsigned m = __ballot_sync(kFull, in);
+        if (m == 0u) continue;
+        if (in) place(bin, __popc(m & lt));
+        __syncwarp();
+        count(bin, m);
+        __syncwarp();
     }
 }
 
-__device__ __forceinline__ void bin_run(const Ctx& c, long long& b, long long& e) {
-    const long long s0 = (long long)blockIdx.y * c.G;
-    b = s0 + (long long)blockIdx.x * kBinChunk + (long long)(threadIdx.x >> 5) * kBinRun;
-    e = min(b + kBinRun, s0 + c.G);
+// Rectangle of the depth-ordered pair k of slot s (empty when culled or past e).
+__device__ __forceinline__ void pair_rect(const Ctx& c, long long s0, long long k, long long e, unsigned& g,
+                                          int4& rc) {
+    g = 0u;
+    rc = make_int4(1, 0, 1, 0);
+    if (k < e) {
+        g = c.dvals[k];
+        rc = c.rect[s0 + g];
+        if (rc.x > rc.y) rc = make_int4(1, 0, 1, 0);
+    }
 }
 
-__global__ void __launch_bounds__(kBinBlock) k_bin_count(Ctx c, int nchunk, unsigned* mat,
-                                                         unsigned long long* total) {
+// Row counts per (slot, row, chunk).
+__global__ void __launch_bounds__(kBinBlock) k_row_count(Ctx c, int nchunk, unsigned* mat) {
     extern __shared__ unsigned bin_smem[];
-    unsigned* s_cnt = bin_smem;  // [T]
-    for (int t = threadIdx.x; t < c.T; t += kBinBlock) s_cnt[t] = 0u;
+    unsigned* s_cnt = bin_smem;  // [tiles_y]
+    for (int r = threadIdx.x; r < c.tiles_y; r += kBinBlock) s_cnt[r] = 0u;
     __syncthreads();
-    long long b, e;
-    bin_run(c, b, e);
-    unsigned mine = 0u;
-    if (b < e)
-        for_run_tiles(c, (int)blockIdx.y, b, e, [&](int t, unsigned) {
-            atomicAdd(&s_cnt[t], 1u);
-            ++mine;
-        });
+    const int slot = blockIdx.y;
+    const long long s0 = (long long)slot * c.G;
+    const long long b = s0 + (long long)blockIdx.x * kBinChunk + (long long)(threadIdx.x >> 5) * kBinRun;
+    const long long e = min(b + kBinRun, s0 + c.G);
+    for (long long k = b + (threadIdx.x & 31); k < e; k += 32) {
+        const int4 rc = c.rect[s0 + c.dvals[k]];
+        if (rc.x <= rc.y)
+            for (int r = rc.z; r <= rc.w; ++r) atomicAdd(&s_cnt[r], 1u);
+    }
     __syncthreads();
-    const long long row = (long long)blockIdx.y * c.T;
-    for (int t = threadIdx.x; t < c.T; t += kBinBlock) mat[(row + t) * nchunk + blockIdx.x] = s_cnt[t];
-    // exact 64-bit total (the scan of mat is 32-bit)
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) mine += __shfl_xor_sync(kFull, mine, o);
-    if ((threadIdx.x & 31) == 0 && mine) atomicAdd(total, (unsigned long long)mine);
+    const long long row0 = (long long)slot * c.tiles_y;
+    for (int r = threadIdx.x; r < c.tiles_y; r += kBinBlock) mat[(row0 + r) * nchunk + blockIdx.x] = s_cnt[r];
 }
 
-__global__ void __launch_bounds__(kBinBlock) k_bin_place(Ctx c, int nchunk, const unsigned* mat) {
+// A row-list entry: the Gaussian index and its tile columns x0..x1.
+__device__ __forceinline__ unsigned long long row_entry(unsigned g, int x0, int x1) {
+    return (unsigned long long)g | ((unsigned long long)(unsigned)x0 << 32) | ((unsigned long long)(unsigned)x1 << 48);
+}
+__device__ __forceinline__ void row_entry_unpack(unsigned long long v, unsigned& g, int& x0, int& x1) {
+    g = (unsigned)v;
+    x0 = (int)((v >> 32) & 0xFFFFu);
+    x1 = (int)(v >> 48);
+}
+
+__global__ void __launch_bounds__(kBinBlock) k_row_place(Ctx c, int nchunk, const unsigned* mat,
+                                                         unsigned long long* rl) {
     extern __shared__ unsigned bin_smem[];
-    unsigned* s_base = bin_smem;                                                  // [T]
-    unsigned short* s_w = reinterpret_cast<unsigned short*>(bin_smem + c.T);     // [kBinWarps][T]
-    for (int t = threadIdx.x; t < kBinWarps * c.T; t += kBinBlock) s_w[t] = 0;
+    const int ny = c.tiles_y;
+    unsigned* s_base = bin_smem;                                             // [ny]
+    unsigned short* s_w = reinterpret_cast<unsigned short*>(bin_smem + ny);  // [kBinWarps][ny]
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < kBinWarps * ny; i += kBinBlock) s_w[i] = 0;
     __syncthreads();
-    long long b, e;
-    bin_run(c, b, e);
-    unsigned short* mine = s_w + (size_t)(threadIdx.x >> 5) * c.T;
-    if (b < e) for_run_tiles(c, (int)blockIdx.y, b, e, [&](int t, unsigned) { ++mine[t]; });
+    const int slot = blockIdx.y;
+    const long long s0 = (long long)slot * c.G;
+    const long long b = s0 + (long long)blockIdx.x * kBinChunk + (long long)wid * kBinRun;
+    const long long e = min(b + kBinRun, s0 + c.G);
+    unsigned short* mine = s_w + wid * ny;
+    // this warp's count per row
+    for (long long base = b; base < e; base += 32) {
+        unsigned g;
+        int4 rc;
+        pair_rect(c, s0, base + lane, e, g, rc);
+        rank_round(rc.z, rc.w, [&](int r, unsigned m) { if (lane == 0) mine[r] += (unsigned short)__popc(m); },
+                   [](int, int) {});
+    }
     __syncthreads();
-    const long long row = (long long)blockIdx.y * c.T;
-    for (int t = threadIdx.x; t < c.T; t += kBinBlock) {
+    // warps' offsets per row within the chunk, the chunk's base per row
+    const long long row0 = (long long)slot * ny;
+    for (int r = threadIdx.x; r < ny; r += kBinBlock) {
         unsigned run = 0u;
 #pragma unroll
         for (int w = 0; w < kBinWarps; ++w) {
-            const unsigned v = s_w[w * c.T + t];
-            s_w[w * c.T + t] = (unsigned short)run;
+            const unsigned v = s_w[w * ny + r];
+            s_w[w * ny + r] = (unsigned short)run;
             run += v;
         }
-        s_base[t] = mat[(row + t) * nchunk + blockIdx.x];
+        s_base[r] = mat[(row0 + r) * nchunk + blockIdx.x];
     }
     __syncthreads();
-    if (b < e)
-        for_run_tiles(c, (int)blockIdx.y, b, e, [&](int t, unsigned g) {
-            const unsigned pos = s_base[t] + mine[t];
-            ++mine[t];
-            c.ids[pos] = g;
-        });
+    for (long long base = b; base < e; base += 32) {
+        unsigned g;
+        int4 rc;
+        pair_rect(c, s0, base + lane, e, g, rc);
+        const unsigned long long v = row_entry(g, rc.x, rc.y);
+        rank_round(rc.z, rc.w, [&](int r, unsigned m) { if (lane == 0) mine[r] += (unsigned short)__popc(m); },
+                   [&](int r, int rank) { rl[s_base[r] + mine[r] + rank] = v; });
+    }
 }
 
-__global__ void k_bin_ranges(Ctx c, int nchunk, const unsigned* mat, const unsigned* total32) {
+// [begin, end) of the row list of (slot, row) index sr in rl.
+__device__ __forceinline__ void row_range(const Ctx& c, int nchunk, const unsigned* mat, const unsigned* total,
+                                          int sr, unsigned& b, unsigned& e) {
+    b = mat[(long long)sr * nchunk];
+    e = sr + 1 < c.nv * c.tiles_y ? mat[(long long)(sr + 1) * nchunk] : *total;
+}
+
+// Tile counts of one (slot, row) per block: a difference array over the
+// row's columns in shared memory (+1 at x0, -1 at x1 + 1 per entry), then its
+// prefix, written as cnt[slot * T + row * tiles_x + x].
+__global__ void __launch_bounds__(kBinBlock) k_tile_count(Ctx c, int nchunk, const unsigned* mat,
+                                                          const unsigned* rtotal, const unsigned long long* rl,
+                                                          unsigned* cnt) {
+    extern __shared__ unsigned bin_smem[];
+    const int nx = c.tiles_x;
+    int* s_d = reinterpret_cast<int*>(bin_smem);  // [nx + 1]
+    for (int x = threadIdx.x; x <= nx; x += kBinBlock) s_d[x] = 0;
+    __syncthreads();
+    const int sr = blockIdx.x, slot = sr / c.tiles_y, row = sr - slot * c.tiles_y;
+    unsigned b, e;
+    row_range(c, nchunk, mat, rtotal, sr, b, e);
+    for (unsigned k = b + threadIdx.x; k < e; k += kBinBlock) {
+        unsigned g;
+        int x0, x1;
+        row_entry_unpack(rl[k], g, x0, x1);
+        atomicAdd(&s_d[x0], 1);
+        atomicAdd(&s_d[x1 + 1], -1);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {  // prefix over the columns, 32 at a time
+        const int lane = threadIdx.x;
+        int carry = 0;
+        unsigned* o = cnt + (long long)slot * c.T + (long long)row * nx;
+        for (int x0 = 0; x0 < nx; x0 += 32) {
+            const int x = x0 + lane;
+            int v = x < nx ? s_d[x] : 0;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(kFull, v, off);
+                if (lane >= off) v += y;
+            }
+            if (x < nx) o[x] = (unsigned)(carry + v);
+            carry += __shfl_sync(kFull, v, 31);
+        }
+    }
+}
+
+// One block per (slot, row); warp w owns the row's columns x = w + kColWarps q
+// (q < kColsPerWarp, in groups of kColWarps * kColsPerWarp columns) and walks
+// the row list once per group, kColRounds rounds of 32 entries at a time (the
+// loads of a batch go out together): per owned column one ballot of the
+// entries covering it, each covering lane writing at the column's running
+// offset + its rank.  Every column's list is appended in order.
+constexpr int kColWarps = 16;
+constexpr int kColsPerWarp = 8;
+constexpr int kColRounds = 4;
+constexpr int kColBlock = kColWarps * kWarp;
+
+__global__ void __launch_bounds__(kColBlock) k_tile_place(Ctx c, int nchunk, const unsigned* mat,
+                                                          const unsigned* rtotal, const unsigned long long* rl,
+                                                          const unsigned* start) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int nx = c.tiles_x;
+    const int sr = blockIdx.x, slot = sr / c.tiles_y, row = sr - slot * c.tiles_y;
+    const long long t0 = (long long)slot * c.T + (long long)row * nx;
+    unsigned b, e;
+    row_range(c, nchunk, mat, rtotal, sr, b, e);
+    for (int x0g = 0; x0g < nx; x0g += kColWarps * kColsPerWarp) {
+        if (x0g + wid >= nx) continue;  // this warp owns no column of the group
+        unsigned off[kColsPerWarp];
+        int col[kColsPerWarp];
+#pragma unroll
+        for (int q = 0; q < kColsPerWarp; ++q) {
+            col[q] = x0g + wid + kColWarps * q;
+            off[q] = col[q] < nx ? start[t0 + col[q]] : 0u;
+        }
+        for (unsigned base = b; base < e; base += 32 * kColRounds) {
+            unsigned long long v[kColRounds];
+#pragma unroll
+            for (int r = 0; r < kColRounds; ++r) {
+                const unsigned k = base + 32 * r + lane;
+                v[r] = k < e ? rl[k] : row_entry(0u, 1, 0);
+            }
+#pragma unroll
+            for (int r = 0; r < kColRounds; ++r) {
+                unsigned g;
+                int x0, x1;
+                row_entry_unpack(v[r], g, x0, x1);
+#pragma unroll
+                for (int q = 0; q < kColsPerWarp; ++q) {
+                    const bool in = x0 <= col[q] && col[q] <= x1;
+                    const unsigned m = __ballot_sync(kFull, in);
+                    if (in) c.ids[off[q] + __popc(m & lt)] = g;
+                    off[q] += __popc(m);
+                }
+            }
+        }
+    }
+}
+
+__global__ void k_tile_ranges(Ctx c, const unsigned* start, const unsigned* total32) {
     const long long vt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nvt = (long long)c.nv * c.T;
     if (vt >= nvt) return;
-    const unsigned b = mat[vt * nchunk];
-    const unsigned e = vt + 1 < nvt ? mat[(vt + 1) * nchunk] : *total32;
+    const unsigned b = start[vt];
+    const unsigned e = vt + 1 < nvt ? start[vt + 1] : *total32;
     c.ranges[vt] = make_int2((int)b, (int)e);
 }
 
-size_t bin_mat_elems(const Ctx& c) { return (size_t)c.nv * c.T * bin_chunks(c); }
+static size_t row_place_smem(const Ctx& c) {
+    return (size_t)c.tiles_y * (sizeof(unsigned) + kBinWarps * sizeof(unsigned short));
+}
 
+bool bin_rows_fit(const Ctx& c) {
+    return row_place_smem(c) <= 200 * 1024 && (size_t)(c.tiles_x + 1) * sizeof(int) <= 200 * 1024 &&
+           c.tiles_x < 65536;
+}
+
+size_t bin_row_mat_elems(const Ctx& c) { return (size_t)c.nv * c.tiles_y * bin_chunks(c); }
 size_t bin_scan_tmp_bytes(long long n) { return scan_tmp_elems<unsigned int>(n) * sizeof(unsigned int); }
 
-void launch_bin_count(const Ctx& c, unsigned* mat, unsigned long long* total, cudaStream_t st) {
+void bin_rows(const Ctx& c, unsigned* mat, unsigned long long* rl, unsigned* rtotal, void* tmp, cudaStream_t st) {
     const dim3 grid(bin_chunks(c), c.nv);
-    LMRS_LAUNCH(k_bin_count, grid, kBinBlock, sizeof(unsigned) * c.T, st, c, bin_chunks(c), mat, total);
+    LMRS_LAUNCH(k_row_count, grid, kBinBlock, sizeof(unsigned) * c.tiles_y, st, c, bin_chunks(c), mat);
+    scan_rec<unsigned int>(mat, (long long)bin_row_mat_elems(c), rtotal, static_cast<unsigned*>(tmp), st);
+    const size_t smem = row_place_smem(c);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k_row_place, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    LMRS_LAUNCH(k_row_place, grid, kBinBlock, smem, st, c, bin_chunks(c), mat, rl);
 }
 
-void scan_bin_mat(unsigned* mat, long long n, unsigned* total32, void* tmp, cudaStream_t st) {
-    scan_rec<unsigned int>(mat, n, total32, static_cast<unsigned int*>(tmp), st);
-}
-
-void launch_bin_place(const Ctx& c, const unsigned* mat, const unsigned* total32, cudaStream_t st) {
-    const size_t smem = bin_place_smem(c.T);
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k_bin_place, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const dim3 grid(bin_chunks(c), c.nv);
-    LMRS_LAUNCH(k_bin_place, grid, kBinBlock, smem, st, c, bin_chunks(c), mat);
+void bin_tiles(const Ctx& c, const unsigned* mat, const unsigned* rtotal, const unsigned long long* rl, unsigned* cnt,
+               unsigned* etotal, void* tmp, cudaStream_t st) {
+    const unsigned rows = (unsigned)(c.nv * c.tiles_y);
+    const size_t smem = sizeof(int) * (c.tiles_x + 1);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k_tile_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    LMRS_LAUNCH(k_tile_count, rows, kBinBlock, smem, st, c, bin_chunks(c), mat, rtotal, rl, cnt);
     const long long nvt = (long long)c.nv * c.T;
-    LMRS_LAUNCH(k_bin_ranges, (unsigned)((nvt + 255) / 256), 256, 0, st, c, bin_chunks(c), mat, total32);
+    scan_rec<unsigned int>(cnt, nvt, etotal, static_cast<unsigned*>(tmp), st);
+    LMRS_LAUNCH(k_tile_place, rows, kColBlock, 0, st, c, bin_chunks(c), mat, rtotal, rl, cnt);
+    LMRS_LAUNCH(k_tile_ranges, (unsigned)((nvt + 255) / 256), 256, 0, st, c, cnt, etotal);
 }
 
 }  // namespace lmrs

@@ -84,6 +84,8 @@ struct Ctx {
     unsigned int* dvals;        // Gaussian index of each depth key
     unsigned long long* cnt;  // tiles touched per depth-sorted pair (then exclusive prefix)
     unsigned long long* n_visible;  // count of visible pairs
+    unsigned long long* n_entries;  // sum over visible pairs of the tiles they overlap
+    unsigned long long* n_rowent;   // sum over visible pairs of the tile rows they span
     float* cot;             // kCotF floats
     float* gram;            // kGramF floats
     // binning
@@ -181,17 +183,22 @@ void launch_sorted_counts(const Ctx& c, cudaStream_t st);
 // one (slot * T + tile, Gaussian) entry per overlapped tile, in depth order
 void launch_emit(const Ctx& c, cudaStream_t st);
 size_t radix_tmp_bytes(long long n);
-// Direct stable binning of the depth-sorted pairs into the tile lists
-// (c.ids, c.ranges) for views of at most kBinMaxTiles tiles: entry counts per
-// (slot, tile, chunk) into mat (bin_mat_elems) with the exact total in
-// *total, the exclusive scan of mat (its 32-bit total in *total32), then the
-// placement and the tile ranges.
-constexpr int kBinMaxTiles = 8192;
-size_t bin_mat_elems(const Ctx& c);
+// Two-level stable binning of the depth-sorted pairs into the tile lists
+// (c.ids, c.ranges), for views whose tile rows and columns fit the shared
+// counters (bin_rows_fit): bin_rows places every visible pair into the lists
+// of the tile rows it spans (rl, one entry per (pair, row): the Gaussian
+// index and the pair's tile columns packed in 64 bits; counts per
+// (slot, row, chunk) in mat, bin_row_mat_elems of them, scanned in place,
+// 32-bit total in *rtotal); bin_tiles places the row lists' pairs into the
+// tiles (per-tile counts in cnt, nv * T of them, scanned into the lists'
+// starts, total in *etotal) and writes the ranges.  tmp: scan scratch of
+// bin_scan_tmp_bytes(max(mat elements, nv * T)).
+bool bin_rows_fit(const Ctx& c);
+size_t bin_row_mat_elems(const Ctx& c);
 size_t bin_scan_tmp_bytes(long long n);
-void launch_bin_count(const Ctx& c, unsigned* mat, unsigned long long* total, cudaStream_t st);
-void scan_bin_mat(unsigned* mat, long long n, unsigned* total32, void* tmp, cudaStream_t st);
-void launch_bin_place(const Ctx& c, const unsigned* mat, const unsigned* total32, cudaStream_t st);
+void bin_rows(const Ctx& c, unsigned* mat, unsigned long long* rl, unsigned* rtotal, void* tmp, cudaStream_t st);
+void bin_tiles(const Ctx& c, const unsigned* mat, const unsigned* rtotal, const unsigned long long* rl, unsigned* cnt,
+               unsigned* etotal, void* tmp, cudaStream_t st);
 // Stable LSD radix sort of (keys, vals) on the low `bits` key bits.
 // Result ends in keys/vals (the alternate buffers are scratch).
 void radix_sort(unsigned long long* keys, unsigned int* vals, unsigned long long* keys_alt, unsigned int* vals_alt,

@@ -523,16 +523,16 @@ __device__ __forceinline__ void load_jac(const Ctx& c, int slot, int g, float* J
 // quarter of its bytes).  DEG 0: the constant Y_0.
 template <int DEG>
 __device__ __forceinline__ void pair_Y(const CamDev& cam, const float X[3], float* Y) {
-    if (DEG == 0) {
+    if constexpr (DEG == 0) {
         Y[0] = c_sh[0];
-        return;
-    }
-    float d[3];
+    } else {
+        float d[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) d[k] = X[k] - cam.centre[k];
-    const float dn = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-    const float idn = 1.f / dn;
-    sh_eval<DEG>(d[0] * idn, d[1] * idn, d[2] * idn, Y);
+        for (int k = 0; k < 3; ++k) d[k] = X[k] - cam.centre[k];
+        const float dn = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        const float idn = 1.f / dn;
+        sh_eval<DEG>(d[0] * idn, d[1] * idn, d[2] * idn, Y);
+    }
 }
 
 template <int DEG>
@@ -548,9 +548,18 @@ __global__ void k_prep_fwd(Ctx c) {
     int4 rect;
     float depth;
     const bool vis = prim_project(X, cam, c.tiles_x, c.tiles_y, c.tile_w, c.tile_h, P, &rect, &depth);
-    const unsigned ballot = __ballot_sync(__activemask(), vis);
-    if ((threadIdx.x & 31) == __ffs(__activemask()) - 1 && ballot)
+    // visible pairs, and the tiles and tile rows they cover (the sizes of the
+    // tile lists and of the binning's row lists)
+    const unsigned active = __activemask();
+    const unsigned ballot = __ballot_sync(active, vis);
+    const unsigned rows = vis ? (unsigned)(rect.w - rect.z + 1) : 0u;
+    const unsigned area = vis ? rows * (unsigned)(rect.y - rect.x + 1) : 0u;
+    const unsigned sum_rows = __reduce_add_sync(active, rows), sum_area = __reduce_add_sync(active, area);
+    if ((threadIdx.x & 31) == __ffs(active) - 1 && ballot) {
         atomicAdd(c.n_visible, (unsigned long long)__popc(ballot));
+        atomicAdd(c.n_entries, (unsigned long long)sum_area);
+        atomicAdd(c.n_rowent, (unsigned long long)sum_rows);
+    }
     // depth key in (slot, Gaussian) order: the stable depth sort keeps index order on ties
     c.dvals[i] = (unsigned int)g;
     if (!vis) {

@@ -82,7 +82,7 @@ struct lmrs_scene {
     DevBuf keys, ids, keys_alt, ids_alt, ranges, scan_tmp, radix_tmp, total;
     DevBuf tile_off, off, wtile, wsample, work;
     DevBuf item_cost, work_sorted, okeys, ovals, okeys_alt, ovals_alt, otmp;
-    DevBuf cids, clen, binmat, bintmp;
+    DevBuf cids, clen, binmat, bintmp, rowl, tcnt;
     int max_items = 1;
     DevBuf resid, cacheC, cacheT, cacheCh, cacheTh, cacheN;
     DevBuf x, r, z, p, Ap, minv, D, b, stage_a, stage_b;
@@ -105,7 +105,7 @@ struct lmrs_scene {
         return {&params, &cams, &views, &gcache, &pjac, &rec, &tan, &rect, &dkeys, &dvals, &dkeys_alt, &dvals_alt, &dtmp, &cnt,
                 &cot, &gram, &keys, &ids, &keys_alt, &ids_alt, &ranges, &scan_tmp, &radix_tmp, &total, &tile_off,
                 &off, &wtile, &wsample, &work, &item_cost, &work_sorted, &okeys, &ovals, &okeys_alt, &ovals_alt, &otmp,
-                &cids, &clen, &binmat, &bintmp, &resid, &cacheC, &cacheT, &cacheCh, &cacheTh, &cacheN, &x, &r, &z, &p, &Ap,
+                &cids, &clen, &binmat, &bintmp, &rowl, &tcnt, &resid, &cacheC, &cacheT, &cacheCh, &cacheTh, &cacheN, &x, &r, &z, &p, &Ap,
                 &minv, &D, &b, &stage_a, &stage_b, &sc, &partials, &counter, &frames, &sqerr, &ssim_s, &ssim_d, &sframes};
     }
 
@@ -130,7 +130,9 @@ struct lmrs_scene {
         c.dkeys = dkeys.as<unsigned long long>();
         c.dvals = dvals.as<unsigned int>();
         c.cnt = cnt.as<unsigned long long>();
+        c.n_entries = total.as<unsigned long long>();
         c.n_visible = total.as<unsigned long long>() + 1;
+        c.n_rowent = total.as<unsigned long long>() + 2;
         c.cot = cot.as<float>();
         c.gram = gram.as<float>();
         c.keys = keys.as<unsigned int>();
@@ -621,59 +623,61 @@ lmrs_status lmrs_preprocess(lmrs_scene* s, const int32_t* view_ids, int32_t n_vi
     TRY(ensure(s, s->dtmp, radix_tmp_bytes((long long)pairs)));
     TRY(ensure(s, s->cot, sizeof(float) * kCotF * pairs));
     TRY(ensure(s, s->ranges, sizeof(int2) * (size_t)s->nv * s->T));
-    // tile lists: direct binning, or entry emission + tile sort for views
-    // with more tiles than the binning's shared counters hold
-    const bool direct = s->T <= kBinMaxTiles;
-    if (!direct) {
-        TRY(ensure(s, s->cnt, sizeof(unsigned long long) * pairs));
-        TRY(ensure(s, s->scan_tmp, scan_u64_tmp_bytes((long long)pairs)));
-    }
     TRY(build_layout(s));
     CK(s, cudaMemcpyAsync(s->views.p, s->views_h.data(), sizeof(int) * n_views, cudaMemcpyHostToDevice, s->st));
     Ctx c = s->ctx();
+    // tile lists: two-level (rows, tiles) binning, or entry emission + tile
+    // sort for views whose tile rows or columns exceed the shared counters
+    const bool rows = bin_rows_fit(c);
+    if (!rows) {
+        TRY(ensure(s, s->cnt, sizeof(unsigned long long) * pairs));
+        TRY(ensure(s, s->scan_tmp, scan_u64_tmp_bytes((long long)pairs)));
+        c = s->ctx();
+    }
+    // total[0]: tile-list entries, [1]: visible pairs, [2]: row-list entries
+    // (all from the projection), [3]: the two 32-bit scan totals
     CK(s, cudaMemsetAsync(s->total.p, 0, 4 * sizeof(unsigned long long), s->st));
     if (s->cfg.sample_dist == 0) launch_sample(c, lm_step, s->cfg.seed, s->st);  // importance draws follow the binning
     launch_prep_gauss(c, s->st);
     launch_prep_fwd(c, s->st);
-    // level 1: (slot, depth, index) order of the pairs
+    // (slot, depth, index) order of the pairs
     int sbits = 0;
     while ((1 << sbits) < s->nv) ++sbits;
     radix_sort(c.dkeys, c.dvals, s->dkeys_alt.as<unsigned long long>(), s->dvals_alt.as<unsigned int>(),
                (long long)pairs, 32 + sbits, s->dtmp.p, s->dtmp.cap, s->st);
-    // total[0]: entries, total[1]: visible pairs, total[2]: 32-bit scan total
-    unsigned* total32 = reinterpret_cast<unsigned*>(s->total.as<unsigned long long>() + 2);
-    size_t nmat = 0;
-    if (direct) {
-        nmat = bin_mat_elems(c);
-        TRY(ensure(s, s->binmat, sizeof(unsigned) * nmat));
-        TRY(ensure(s, s->bintmp, bin_scan_tmp_bytes((long long)nmat)));
-        launch_bin_count(c, s->binmat.as<unsigned>(), s->total.as<unsigned long long>(), s->st);
-        scan_bin_mat(s->binmat.as<unsigned>(), (long long)nmat, total32, s->bintmp.p, s->st);
-    } else {
+    if (!rows) {
         launch_sorted_counts(c, s->st);
         scan_u64(c.cnt, (long long)pairs, s->total.as<unsigned long long>(), s->scan_tmp.p, s->scan_tmp.cap, s->st);
     }
     CHECK_LAUNCH(s);
-    unsigned long long tot2[2] = {0ull, 0ull};
-    CK(s, cudaMemcpyAsync(tot2, s->total.p, sizeof(tot2), cudaMemcpyDeviceToHost, s->st));
+    unsigned long long tot[3] = {0ull, 0ull, 0ull};
+    CK(s, cudaMemcpyAsync(tot, s->total.p, sizeof(tot), cudaMemcpyDeviceToHost, s->st));
     CK(s, cudaStreamSynchronize(s->st));
-    const unsigned long long total = tot2[0];
-    s->nvisible = (long long)tot2[1];
+    const unsigned long long total = tot[0];
+    s->nvisible = (long long)tot[1];
     if (total >= (1ull << 31)) return fail(s, LMRS_ERR_BUDGET, "more than 2^31 (view, tile, Gaussian) pairs");
     s->npairs = (long long)total;
     const size_t np = std::max<size_t>((size_t)total, 1);
     TRY(ensure(s, s->ids, sizeof(unsigned int) * np));
     TRY(ensure(s, s->cids, sizeof(unsigned int) * np * (size_t)s->max_items));
-    if (direct) {
+    if (rows) {
+        const size_t nmat = bin_row_mat_elems(c), nvt = (size_t)s->nv * s->T;
+        TRY(ensure(s, s->binmat, sizeof(unsigned) * nmat));
+        TRY(ensure(s, s->tcnt, sizeof(unsigned) * nvt));
+        TRY(ensure(s, s->rowl, sizeof(unsigned long long) * std::max<size_t>((size_t)tot[2], 1)));
+        TRY(ensure(s, s->bintmp, bin_scan_tmp_bytes((long long)std::max(nmat, nvt))));
         c = s->ctx();
-        launch_bin_place(c, s->binmat.as<unsigned>(), total32, s->st);
+        unsigned* total32 = reinterpret_cast<unsigned*>(s->total.as<unsigned long long>() + 3);
+        bin_rows(c, s->binmat.as<unsigned>(), s->rowl.as<unsigned long long>(), total32, s->bintmp.p, s->st);
+        bin_tiles(c, s->binmat.as<unsigned>(), total32, s->rowl.as<unsigned long long>(), s->tcnt.as<unsigned>(),
+                  total32 + 1, s->bintmp.p, s->st);
     } else {
         TRY(ensure(s, s->keys, sizeof(unsigned int) * np));
         TRY(ensure(s, s->keys_alt, sizeof(unsigned int) * np));
         TRY(ensure(s, s->ids_alt, sizeof(unsigned int) * np));
         TRY(ensure(s, s->radix_tmp, radix_tmp_bytes((long long)np)));
         c = s->ctx();
-        // level 2: entries in depth order, then a stable sort on the (slot, tile) bits
+        // entries in depth order, then a stable sort on the (slot, tile) bits
         launch_emit(c, s->st);
         int vbits = 0;
         while ((1ll << vbits) < (long long)s->nv * s->T) ++vbits;
@@ -1074,7 +1078,8 @@ int64_t lmrs_footprint_bytes(const lmrs_config* cfg, int64_t n_gauss, int32_t n_
     // alternates 24, counts 8, cotangent slots 48, Gram blocks 176; scan and
     // sort scratch ~2
     const double per_pair = 96 + 16.0 * jac_f4(cfg->sh_degree) + 16 + 24 + 8 + 48 + 4.0 * kGramF + 2;
-    // keys, ids and their alternates 16, compact lists 4 per work item of a tile
+    // ids and the binning's row lists 8 (the emission path: keys, ids and their
+    // alternates 16, the bound taken), compact lists 4 per work item of a tile
     const double per_entry = 16 + 4.0 * max_items + 1;
     // offset 1, residual 12, FP32 and BF16 caches 12 + 4 + 6 + 2, stop index 4,
     // importance weight 4, SSIM values 24

@@ -36,13 +36,21 @@ def _ragged(sh_degree=1, frac=0.1, **cfg):
 
 
 def _tiles2(width, height):
-    """2x2 tiles: 8100 tiles per view (direct binning at its largest shared
-    footprint) or 8500 (above the direct binning's limit: emission + tile
-    sort)."""
+    """2x2 tiles: 8100 or 8500 tiles per view (90 x 90 and 100 x 85 tiles),
+    through the row-then-tile binning."""
     rng = np.random.default_rng(29)
     sc = syn.tiny_scene(seed=7, n_gauss=1500, width=width, height=height, sh_degree=1)
     tgt = syn.noise_targets(rng, len(sc.cams), height, width)
     return Pair(sc, tgt, sample_frac=0.5, tile_w=2, tile_h=2), [2, 0]
+
+
+def _strip():
+    """An 8600 x 2 view of 1x1 tiles: 8600 tile columns exceed the binning's
+    shared counters, so the entry emission + tile sort builds the lists."""
+    rng = np.random.default_rng(31)
+    sc = syn.tiny_scene(seed=7, n_gauss=1500, width=8600, height=2, sh_degree=0)
+    tgt = syn.noise_targets(rng, len(sc.cams), 2, 8600)
+    return Pair(sc, tgt, sample_frac=1.0, tile_w=1, tile_h=1), [0, 2]
 
 
 CASES = {
@@ -53,7 +61,8 @@ CASES = {
     "ragged_tile32x8": lambda: _ragged(1, 0.3, tile_w=32, tile_h=8),
     "ragged_tile8x32_spt": lambda: _ragged(0, 1.0, tile_w=8, tile_h=32, samples_per_tile=40, weight_mode=1),
     "tiles2x2_direct_8100": lambda: _tiles2(180, 180),
-    "tiles2x2_sorted_8500": lambda: _tiles2(200, 170),
+    "tiles2x2_8500": lambda: _tiles2(200, 170),
+    "strip_emit_8600": lambda: _strip(),
 }
 
 
