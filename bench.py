@@ -199,6 +199,62 @@ def profiled_traffic(kernel, workload):
     return d["dram_bytes_per_launch"]
 
 
+class Replicas:
+    """The ranks of a torchrun launch as independent replicas: the operator is
+    a sum over views with no exchange step worth sharding on one node, so every
+    rank runs its own fit.  A barrier around each timed region and the maximum
+    of a rank-local time are the only traffic between ranks (NCCL on the GPU
+    box; the tests use gloo on CPU)."""
+
+    def __init__(self, rank, world, local_rank, backend="nccl"):
+        self.rank, self.world = rank, world
+        self.dist = None
+        self.device = None
+        if world > 1:
+            import torch
+            import torch.distributed as dist
+            if backend == "nccl":
+                self.device = torch.device("cuda", local_rank)
+                dist.init_process_group(backend, device_id=self.device)
+            else:
+                dist.init_process_group(backend)
+            self.dist = dist
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def max(self, x):
+        """The maximum of a rank-local value over the ranks."""
+        if self.dist is None:
+            return float(x)
+        import torch
+        t = torch.tensor([float(x)], dtype=torch.float64, device=self.device if self.device is not None else "cpu")
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, x):
+        """The sum of a rank-local count over the ranks."""
+        if self.dist is None:
+            return float(x)
+        import torch
+        t = torch.tensor([float(x)], dtype=torch.float64, device=self.device if self.device is not None else "cpu")
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.barrier()
+            self.dist.destroy_process_group()
+            self.dist = None
+
+
+def job_rate(units_per_rank, world, ms_max):
+    """Whole-job throughput: the units all ranks processed (the same number on
+    every rank) over the slowest rank's time."""
+    return world * units_per_rank / (ms_max / 1000.0)
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -206,10 +262,7 @@ def run_ours(args, rank, world, local_rank):
     from paper_2504_12905_gb300 import synthetic as syn
 
     torch.cuda.set_device(local_rank)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    ranks = Replicas(rank, world, local_rank)
     wl = WORKLOADS[args.workload]
     sc = make_scene(args.workload, seed_offset=rank)
     G, deg = sc.n_gauss, sc.sh_degree
@@ -240,8 +293,7 @@ def run_ours(args, rank, world, local_rank):
 
     def barrier():
         torch.cuda.synchronize()
-        if dist is not None:
-            dist.barrier()
+        ranks.barrier()
 
     # ---- warm-up -------------------------------------------------------
     for k in range(args.warmup):
@@ -268,13 +320,9 @@ def run_ours(args, rank, world, local_rank):
     lmrs.lmrs_set_timing(h, False)
     ktimes = lmrs.lmrs_get_timing(h)
     ms = e0.elapsed_time(e1)
-    ms_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
+    ms_max = ranks.max(ms)
     matvecs = world * args.steps * wl["cg_iters"]
-    value = matvecs / (ms_max / 1000.0)
+    value = job_rate(args.steps * wl["cg_iters"], world, ms_max)
 
     # sizes of the last step for the byte model, and the composited
     # evaluations per operator application averaged over the timed steps'
@@ -338,11 +386,7 @@ def run_ours(args, rank, world, local_rank):
         lmrs.lmrs_lm_step(h, views[k], k, stats=False)
         lmrs.lmrs_get_params(h, p_host)          # device -> host, synchronises
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = ranks.max(time.perf_counter() - t0)
     e2e = {"value": matvecs / e2e_s, "unit": "matvec/s", "h2d_bytes_per_step": 4 * scene.n_params,
            "d2h_bytes_per_step": 4 * scene.n_params}
 
@@ -415,9 +459,7 @@ def run_ours(args, rank, world, local_rank):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(sc, views[n_steps - 1], n_steps - 1, wl, budget_s=args.cpu_seconds)
-    if dist is not None:
-        dist.barrier()
-        dist.destroy_process_group()
+    ranks.close()
     scene.close()
     return result
 
@@ -596,10 +638,7 @@ def run_batched(args, rank, world, local_rank):
     from paper_2504_12905_gb300 import synthetic as syn
 
     torch.cuda.set_device(local_rank)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    ranks = Replicas(rank, world, local_rank)
     wl = WORKLOADS["batched"]
     scenes = syn.small_fit_scenes(seed=0x1A5E0003 + rank)
     n_sc = len(scenes)
@@ -636,8 +675,7 @@ def run_batched(args, rank, world, local_rank):
 
     def barrier():
         torch.cuda.synchronize()
-        if dist is not None:
-            dist.barrier()
+        ranks.barrier()
 
     n_steps = args.warmup + args.steps
     vis_dev = os.environ.get("CUDA_VISIBLE_DEVICES", "")
@@ -709,14 +747,7 @@ def run_batched(args, rank, world, local_rank):
     for s in bsc:
         s.close()
 
-    def world_max(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    ms_b, ms_s, e2e_s = world_max(ms_b), world_max(ms_s), world_max(e2e_s)
+    ms_b, ms_s, e2e_s = ranks.max(ms_b), ranks.max(ms_s), ranks.max(e2e_s)
     fits = world * n_sc * args.steps / wl["fit_steps"]
     P_tot = sum(sc.n_params for sc in scenes)
     result = {
@@ -748,9 +779,7 @@ def run_batched(args, rank, world, local_rank):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline_batched(scenes, starts, targets, views, cfg, wl, args.cpu_seconds)
-    if dist is not None:
-        dist.barrier()
-        dist.destroy_process_group()
+    ranks.close()
     return result
 
 
@@ -795,10 +824,7 @@ def run_serving(args, rank, world, local_rank):
     from paper_2504_12905_gb300 import synthetic as syn
 
     torch.cuda.set_device(local_rank)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    ranks = Replicas(rank, world, local_rank)
     wl = WORKLOADS["serving"]
     n_req = args.requests or wl["requests"]
     reqs = syn.serving_requests(seed=0x1A5E0004 + rank, n_requests=n_req + args.warmup, rate=wl["rate"])
@@ -815,8 +841,7 @@ def run_serving(args, rank, world, local_rank):
 
     def barrier():
         torch.cuda.synchronize()
-        if dist is not None:
-            dist.barrier()
+        ranks.barrier()
 
     # ---- server arm ---------------------------------------------------------
     srv = lmrs.lmrs_server_create(wl["budget_bytes"], max_active=wl["max_active"], setup_threads=8)
@@ -881,8 +906,10 @@ def run_serving(args, rank, world, local_rank):
     barrier()
 
     n = len(jobs)
-    fits_srv = world * len(ok) / span_srv
-    fits_plain = world * n / wall_plain
+    # whole-job rates over the slowest rank's span (every rank serves its own stream)
+    span_srv_max, wall_plain_max = ranks.max(span_srv), ranks.max(wall_plain)
+    fits_srv = ranks.sum(len(ok)) / span_srv_max
+    fits_plain = job_rate(n, world, wall_plain_max * 1000.0)
     h2d = int(np.mean([j["targets"].nbytes + j["start"].nbytes for j in jobs]))
     d2h = int(np.mean([j["start"].nbytes for j in jobs]))
     est = np.array([i.footprint_est for i in ok], np.float64)
@@ -925,9 +952,7 @@ def run_serving(args, rank, world, local_rank):
             "value": round(1.0 / (spf * t), 6), "unit": "fits/s", "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"one FP64 LM step on each of the first {m} requests ({dt:.1f} s); fits/s = 1 / "
                       f"({spf:.1f} steps per fit, the server's mean, x mean seconds per step)"}
-    if dist is not None:
-        dist.barrier()
-        dist.destroy_process_group()
+    ranks.close()
     return result
 
 
