@@ -1,0 +1,124 @@
+"""Parity at the full size of the benchmarked 200k-Gaussian workload (SH3, 8
+of 24 views of 1024x672, 10% of every tile sampled, the benchmark's seed,
+damping and first view set), on outputs the oracle computes one by one: the
+whole sample set and tile lists bit for bit, the residuals and J v of 4096
+random samples, and the damped operator, diag(J^T W J) and J^T W r of the
+parameters of 256 random Gaussians.  Targets are seeded noise (the shared
+input generator), so no oracle input comes from the CUDA path."""
+import numpy as np
+import pytest
+
+from paper_2504_12905_gb300 import synthetic as syn
+
+from gpu_common import Pair
+
+pytestmark = pytest.mark.gpu
+
+PIX_TOL = 1e-5
+OP_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def full():
+    sc = syn.moderate_scene()  # the benchmark's scene (same default seed)
+    tgt = syn.noise_targets(np.random.default_rng(5), len(sc.cams), sc.height, sc.width)
+    pair = Pair(sc, tgt, sample_frac=0.1, lambda_=0.1, damping_mode=0, cg_iters=8, seed=0x5EED)
+    views = syn.view_subset(np.random.default_rng(77), len(sc.cams), 8)  # the first benchmarked view set
+    pair.begin(list(views), step=3)
+    pair.lmrs.lmrs_render(pair.gpu.h)
+    rng = np.random.default_rng(2)
+    pair.sample_idx = np.sort(rng.choice(pair.S, 4096, replace=False)).astype(np.int64)
+    pair.gids = np.sort(rng.choice(sc.n_gauss, 256, replace=False)).astype(np.int32)
+    _, _, flags = pair.orc.render_samples()
+    pair.flags = flags != 0
+    yield pair
+    pair.gpu.close()
+
+
+def _param_index(G, K3, g, j):
+    if j < 3:
+        return 3 * g + j
+    if j < 6:
+        return 3 * G + 3 * g + j - 3
+    if j < 10:
+        return 6 * G + 4 * g + j - 6
+    if j == 10:
+        return 10 * G + g
+    return 11 * G + K3 * g + j - 11
+
+
+def _blocks(pair, vec):
+    """The gids' parameter blocks of a P-vector, (n, Pg)."""
+    G = pair.scene.n_gauss
+    K3 = 3 * (pair.scene.sh_degree + 1) ** 2
+    Pg = 11 + K3
+    idx = np.array([[_param_index(G, K3, int(g), j) for j in range(Pg)] for g in pair.gids])
+    return vec[idx]
+
+
+def test_samples_and_tile_lists_bit_exact(full):
+    off, tile_off = full.lmrs.lmrs_get_samples(full.gpu.h, full.gpu.n_views, full.gpu.n_tiles)
+    ref = full.orc.samples()
+    np.testing.assert_array_equal(tile_off, ref["tile_off"])
+    np.testing.assert_array_equal(off, ref["off"])
+    ranges, ids = full.lmrs.lmrs_get_tile_lists(full.gpu.h, full.gpu.n_views, full.gpu.n_tiles)
+    r_ref, ids_ref = full.orc.lists()
+    assert len(ids) == len(ids_ref) > 10_000_000
+    np.testing.assert_array_equal(ids, ids_ref)
+    len_gpu, len_ref = ranges[:, 1] - ranges[:, 0], r_ref[:, 1] - r_ref[:, 0]
+    np.testing.assert_array_equal(len_gpu, len_ref)
+
+
+def test_sampled_residuals_and_jvp(full):
+    resid = full.zeros(full.S * 3)
+    full.lmrs.lmrs_render(full.gpu.h, None, resid)
+    r = full.host(resid).reshape(-1, 3)[full.sample_idx]
+    rgb_ref, fl = full.orc.render_samples_subset(full.sample_idx)
+    keep = fl == 0
+    # a sample is flagged when any of its alpha or termination tests lies
+    # within the oracle's relative margin of the threshold; at this size a
+    # sample makes a few hundred alpha tests, so ~1.5% are flagged
+    assert keep.mean() > 0.97
+    # residual = colour - target: the device's colour at the sampled pixels
+    smp = full.orc.samples()
+    cams = np.asarray(full.views)[smp["slot"][full.sample_idx]]
+    targets = full.targets_np[cams, smp["py"][full.sample_idx], smp["px"][full.sample_idx]].astype(np.float64)
+    np.testing.assert_allclose((r + targets)[keep], rgb_ref[keep], atol=PIX_TOL, rtol=0)
+    v = np.random.default_rng(3).standard_normal(full.P).astype(np.float32)
+    u = full.zeros(full.S * 3)
+    full.lmrs.lmrs_jvp(full.gpu.h, full.cuda(v), u)
+    u_got = full.host(u).reshape(-1, 3)[full.sample_idx]
+    u_ref = full.orc.jvp_subset(v.astype(np.float64), full.sample_idx)
+    err = np.linalg.norm(u_got[keep] - u_ref[keep]) / np.linalg.norm(u_ref[keep])
+    assert err <= OP_TOL, err
+
+
+def test_operator_diag_rhs_of_sampled_gaussians(full):
+    full.lmrs.lmrs_jtj_diag(full.gpu.h)
+    d = full.zeros(full.P)
+    full.lmrs.lmrs_jtj_diag(full.gpu.h, d)
+    D_got = _blocks(full, full.host(d))
+    D_ref = full.orc.diag_gauss(full.gids)
+    err = np.linalg.norm(D_got - D_ref) / np.linalg.norm(D_ref)
+    assert err <= OP_TOL, f"diag {err:.2e}"
+    v = np.random.default_rng(4).standard_normal(full.P).astype(np.float32)
+    v64 = v.astype(np.float64)
+    out = full.zeros(full.P)
+    full.lmrs.lmrs_jtjv(full.gpu.h, full.cuda(v), out)
+    got = _blocks(full, full.host(out))
+    ref = full.orc.apply_gauss(v64, np.zeros(full.P), full.gids)  # lambda I damping
+    # the samples the oracle flags near a compositing decision may go the
+    # other way in FP32: their whole contribution bounds the extra difference
+    w = full.orc.samples()["w"]
+    u_flag = full.orc.jvp(v64) * (w * full.flags)[:, None]
+    slack = np.linalg.norm(full.orc.vjp_gauss(u_flag, full.gids))
+    err = np.linalg.norm(got - ref)
+    assert err <= OP_TOL * np.linalg.norm(ref) + 3.0 * slack, (err, slack, np.linalg.norm(ref))
+    assert slack <= 0.05 * np.linalg.norm(ref)
+    b = full.zeros(full.P)
+    full.lmrs.lmrs_rhs(full.gpu.h, b)
+    b_got = _blocks(full, full.host(b))
+    _, r_all, _ = full.orc.render_samples()
+    b_ref = full.orc.vjp_gauss(r_all * w[:, None], full.gids)
+    slack_b = np.linalg.norm(full.orc.vjp_gauss(r_all * (w * full.flags)[:, None], full.gids))
+    assert np.linalg.norm(b_got - b_ref) <= OP_TOL * np.linalg.norm(b_ref) + 3.0 * slack_b
