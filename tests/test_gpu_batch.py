@@ -140,3 +140,50 @@ def test_autotune_tile_times_every_shape():
     np.testing.assert_array_equal(params.cpu().numpy(), sc.params)  # the caller's parameters are untouched
     with pytest.raises(lmrs.LmrsError):
         lmrs.lmrs_autotune_tile(cfg, sc.n_gauss, params, sc.cams, t, views, [(32, 16)], reps=1)
+
+
+def test_full_batch_of_64_scenes_against_oracle_on_sampled_scenes():
+    """The benchmarked batch at full size (64 scenes of 5k-50k Gaussians,
+    4-16 views of 256x256, 32 samples per tile, the benchmark's seeds and
+    tile shape; seeded noise targets): one batched LM step of all 64 scenes,
+    then the solutions of the smallest, the median and the largest scene
+    against the oracle's LM step, in the A-norm, and their losses."""
+    import torch
+
+    from paper_2504_12905_gb300 import lmrs
+
+    scenes = syn.small_fit_scenes()
+    prng = np.random.default_rng(4321)
+    starts = [syn.perturb(prng, sc.params) for sc in scenes]
+    trng = np.random.default_rng(6)
+    tgts = [syn.noise_targets(trng, len(sc.cams), sc.height, sc.width) for sc in scenes]
+    cfg = dict(samples_per_tile=32, lambda_=0.1, damping_mode=0, cg_iters=8, seed=0x5EED, tile_w=16, tile_h=16)
+    streams = [torch.cuda.Stream() for _ in scenes]
+    gpu = []
+    for i, sc in enumerate(scenes):
+        t = torch.from_numpy(tgts[i]).cuda()
+        s = lmrs.Scene(torch.from_numpy(starts[i]).cuda(), sc.cams, sc.n_gauss, 0, targets=t,
+                       stream=streams[i].cuda_stream, **cfg)
+        s._t = t
+        gpu.append(s)
+    b = lmrs.lmrs_batch_create([s.h for s in gpu], n_threads=4)
+    views = [list(range(len(sc.cams))) for sc in scenes]
+    st = lmrs.lmrs_batch_lm_step(b, views, [10] * len(scenes))
+    order = np.argsort([sc.n_gauss for sc in scenes])
+    for i in (int(order[0]), int(order[len(order) // 2]), int(order[-1])):
+        sc = scenes[i]
+        x = np.zeros(gpu[i].n_params, np.float32)
+        lmrs.lmrs_get_solution(gpu[i].h, x)
+        o = oracle.OracleScene(starts[i], sc.cams, sc.n_gauss, 0, targets=tgts[i], **cfg)
+        o.begin_step(views[i], 10)
+        D = o.diag()
+        x_ref, st_ref = o.lm_step(views[i], 10)
+        o.set_params(starts[i].astype(np.float64))
+        o.begin_step(views[i], 10)
+        e = x.astype(np.float64) - x_ref
+        a_norm = np.sqrt(max(e @ o.apply(e, D), 0.0)) / np.sqrt(x_ref @ o.apply(x_ref, D))
+        assert a_norm <= 1e-3, (i, sc.n_gauss, a_norm)
+        assert st[i].loss == pytest.approx(st_ref[0], rel=1e-5)
+    lmrs.lmrs_batch_destroy(b)
+    for s in gpu:
+        s.close()
