@@ -95,3 +95,57 @@ def test_submit_rejections():
         assert e.value.status == 1
     finally:
         lmrs.lmrs_server_destroy(srv)
+
+
+def test_benchmark_stream_jobs_same_alone_and_in_mix():
+    """At the benchmark's sizes: the first 8 requests of its stream (2k-300k
+    Gaussians, 8-32 views of 512x512, SH1, every view each step, 32 samples
+    per tile, 8 PCG iterations; seeded noise targets and the benchmark's
+    start perturbation) served together for 3 LM steps each, then the
+    largest of them alone, twice: same steps, same loss, and an update that
+    differs from the solo run's no more than two solo runs differ from each
+    other (the back-scatter's atomic additions make the summation order, and
+    so the last bits, vary from run to run; three steps of 8 PCG iterations
+    carry that into the update of a 2.6M-parameter job)."""
+    from paper_2504_12905_gb300 import lmrs
+    reqs = syn.serving_requests()[:8]
+    prng = np.random.default_rng(99)
+    trng = np.random.default_rng(7)
+    jobs = []
+    for k, (_, sc) in enumerate(reqs):
+        start = syn.perturb_appearance(prng, sc.params, sc.n_gauss, sc.sh_degree)
+        tgt = syn.noise_targets(trng, len(sc.cams), sc.height, sc.width)
+        jobs.append((k, sc, start, tgt))
+
+    def cfg(k):
+        return lmrs.lmrs_config_default(sh_degree=1, samples_per_tile=32, lambda_=0.1, damping_mode=0, cg_iters=8,
+                                        seed=0x5EED + k)
+
+    def serve(subset):
+        srv = lmrs.lmrs_server_create(120 << 30, max_active=64, setup_threads=4)
+        try:
+            ids = [lmrs.lmrs_server_submit(srv, cfg(k), sc.n_gauss, start, sc.cams, tgt, 0, 0.0, 3)
+                   for k, sc, start, tgt in subset]
+            out = {}
+            for jid, (k, sc, start, _) in zip(ids, subset):
+                status, info = lmrs.lmrs_server_wait(srv, jid, 600.0)
+                assert status == lmrs.LMRS_OK and info.state == lmrs.JOB_DONE, (k, info.state, info.status)
+                out[k] = (info, lmrs.lmrs_server_result(srv, jid, start.size))
+        finally:
+            lmrs.lmrs_server_destroy(srv)
+        return out
+
+    mixed = serve(jobs)
+    big = max(jobs, key=lambda j: j[1].n_gauss)
+    alone, again = serve([big]), serve([big])
+    k = big[0]
+    assert big[1].n_gauss > 100_000
+    (info_m, res_m), (info_a, res_a), (info_b, res_b) = mixed[k], alone[k], again[k]
+    assert info_m.steps == info_a.steps == info_b.steps == 3
+    assert info_m.loss == pytest.approx(info_a.loss, rel=1e-4)
+    p0 = big[2]
+    run_to_run = normwise_rel(res_b - p0, res_a - p0)
+    mix_to_run = normwise_rel(res_m - p0, res_a - p0)
+    assert mix_to_run <= 3.0 * run_to_run + 1e-4 and mix_to_run <= 5e-3, (mix_to_run, run_to_run)
+    for info, res in mixed.values():
+        assert info.steps == 3 and np.isfinite(res).all()
