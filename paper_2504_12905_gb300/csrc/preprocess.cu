@@ -923,7 +923,10 @@ __global__ void __launch_bounds__(kPrepBlock) k_prep_diag(Ctx c, float* D) {
             a[5] = j == 10 ? J[L::kOp] : 0.f;
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) a[6 + ch] = (DEG > 0 && j < 3) ? J[L::kGx + 3 * ch + j] : 0.f;
-            dgeo[j] += gram_quad(gm, a);
+            // exactly a sum of squares (the Gram block is a sum of outer
+            // products); in FP32 a rank-deficient block (a pair hit by one
+            // sample) can round the form below zero
+            dgeo[j] += fmaxf(gram_quad(gm, a), 0.f);
         }
         // SH coefficient (k, ch) moves only colour ch, by Y_k
         const unsigned bits = __float_as_uint(J[L::kMask]);

@@ -57,6 +57,15 @@ CASES = {
     "tiny": lambda: _tiny(0, lambda_=1e-2),
     "ragged_sh1_frac": lambda: _ragged(1, 0.1, weight_mode=1),
     "ragged_sh3": lambda: _ragged(3, 0.25),
+    "ragged_sh2": lambda: _ragged(2, 0.3),
+    # one sample per tile: every work item has a single live lane.  70
+    # samples for 34,500 parameters leave half of the 8,917 touched diagonal
+    # entries below 1e-6 of the largest; under lambda diag(J^T W J) damping
+    # (which also scales the Jacobi preconditioner) the oracle's own 10-step
+    # CG moves by ~10% in the A-norm when D is perturbed at FP32 rounding of
+    # its largest entry, so the solves compare under lambda I damping (the
+    # operator test still runs both modes)
+    "ragged_k1": lambda: _ragged(1, 1.0, samples_per_tile=1, damping_mode=0),
     # non-square tiles of the autotuner's candidate set
     "ragged_tile32x8": lambda: _ragged(1, 0.3, tile_w=32, tile_h=8),
     "ragged_tile8x32_spt": lambda: _ragged(0, 1.0, tile_w=8, tile_h=32, samples_per_tile=40, weight_mode=1),
@@ -177,15 +186,19 @@ def test_jtjv(case, damping_mode):
 
 def assert_solution_close(pair, x, x_ref, D_ref, tol=CG_TOL):
     """CG iterates agree in the energy norm |e|_A / |x|_A (the norm CG
-    minimises) and in the 2-norm over the well-determined parameters
-    (D_j >= 1e-6 max D).  Parameters with a near-null Jacobian column get
-    x_j ~ b_j / ((1 + lambda) D_j) under diagonal damping, where the FP32
-    and FP64 diagonals legitimately differ in relative terms."""
+    minimises) and in the 2-norm over the well-determined parameters: all of
+    them under lambda I damping (A >= lambda I), those with D_j >= 1e-6 max D
+    under diagonal damping.  There, parameters with a near-null Jacobian
+    column get x_j ~ b_j / ((1 + lambda) D_j), where the FP32 and FP64
+    diagonals legitimately differ in relative terms."""
     e = x - x_ref
     a_norm = np.sqrt(max(e @ pair.orc.apply(e, D_ref), 0.0)) / np.sqrt(x_ref @ pair.orc.apply(x_ref, D_ref))
     assert a_norm <= tol, f"A-norm rel error {a_norm:.3e}"
-    well = D_ref >= 1e-6 * D_ref.max()
-    assert well.sum() >= 0.5 * (D_ref > 0).sum()
+    if pair.cfg["damping_mode"] == 1:
+        well = D_ref >= 1e-6 * D_ref.max()
+        assert well.sum() >= 0.5 * (D_ref > 0).sum()
+    else:
+        well = np.ones(D_ref.size, bool)
     assert normwise_rel(x[well], x_ref[well]) <= tol
     return a_norm
 
@@ -227,7 +240,10 @@ def test_lm_step_and_step_size(case):
         pair.lmrs.lmrs_get_params(pair.gpu.h, p1)
         well = D_ref >= 1e-6 * D_ref.max()
         # beta_1 = beta_0 - eta x; compared on the well-determined entries
-        np.testing.assert_allclose(p1 - p0, -st.eta * x, rtol=1e-5, atol=1e-6 * np.abs(x).max() * st.eta + 1e-7)
+        # the device forms p - (float)eta * x in FP32: (float)eta, the product
+        # and the subtraction each round once (unit roundoff 2^-24)
+        upd = -st.eta * x
+        assert np.all(np.abs((p1 - p0) - upd) <= 1.01 * 2.0 ** -24 * (np.abs(p1) + 2.0 * np.abs(upd)))
         assert normwise_rel((p1 - p0)[well], -st_ref[1] * x_ref[well]) <= CG_TOL
         assert pair.lmrs.lmrs_step_size(pair.gpu.h, pair.cuda(x), step) == pytest.approx(eta_gpu_rule, rel=1e-12)
         pair.gpu.close()
