@@ -436,7 +436,13 @@ lmrs_status lmrs_autotune_tile(const lmrs_config* cfg, int64_t n_gauss, const fl
 /* Introspection (host memory; synchronising).  Sample layout: off[S] is the
  * offset of each sample inside the valid part of its tile (row-major over
  * min(tile_w, remaining width) columns), tile_off[n_views*T + 1] the prefix
- * over tiles.  Tile lists: ranges[n_views*T][2] = [begin, end) into ids[]. */
+ * over tiles.  Tile lists: ranges[n_views*T][2] = [begin, end) into ids[];
+ * a Gaussian's list covers the tiles of its 3-sigma rectangle where its
+ * alpha can reach 1/255 at a pixel (the ellipse q <= 2 ln(255 o) + 0.02 met
+ * by a pixel-centre column within the tile row), so a tile left out changes
+ * no pixel.  lmrs_num_pairs is the number of list entries (ids[]); it waits
+ * for the preprocessing on the scene's stream; -1 before preprocessing or
+ * when that read fails. */
 int64_t lmrs_num_params(const lmrs_scene* scene);
 int64_t lmrs_num_samples(const lmrs_scene* scene);
 int64_t lmrs_num_pairs(const lmrs_scene* scene);

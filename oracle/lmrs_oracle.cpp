@@ -145,21 +145,43 @@ CamF cam_float(const orc_camera& c) {
 }
 
 // --------------------------------------------------------------------------
-// FP32 list decisions (visibility, depth key, tile rectangle).  Every
-// operation is a single IEEE binary32 operation in the written order (the
-// build disables contraction); the scale exponential is the binary32 rounding
-// of the double exponential.  The CUDA side follows the same sequence.
+// FP32 list decisions (visibility, depth key, tile rectangle, and the tile
+// columns each row of the rectangle keeps).  Every operation is a single IEEE
+// binary32 operation in the written order (the build disables contraction);
+// the scale exponential and the ellipse level are binary32 roundings of
+// double expressions.  The CUDA side follows the same sequence.
 // --------------------------------------------------------------------------
 struct GeoF {
     int vis;
     float depth;
     int x0, x1, y0, y1;  // inclusive tile rectangle
+    // the ellipse {d : d^T Sigma2^-1 d <= tau} around the 2D mean (mux, muy),
+    // tau = 2 ln(255 o) + kTauSlack: every pixel whose alpha reaches 1/255
+    // lies inside it.  Given the offset dy from muy, its points have
+    // (dx - kx dy)^2 <= pq - qq dy^2 (the conditional form of the 2D
+    // Gaussian); |dy| <= ey; the rightmost point has dy = dys, the leftmost
+    // dy = -dys.  ey < 0: no pixel reaches 1/255.
+    float mux, muy, kx, dys, pq, qq, ey;
 };
 
-GeoF geom_f32(const float* X, const float* ls, const float* q, const CamF& c,
+// Slack on the ellipse's level: the lists keep every tile some pixel of which
+// reaches alpha >= 1/255 by a margin far above the FP32 rounding of the
+// renderer's alpha (a factor e^-0.01 on the threshold).
+constexpr double kTauSlack = 0.02;
+
+// Level tau of the 1/255 ellipse: alpha = o exp(-q/2) >= 1/255 iff
+// q <= 2 ln(255 o); o = sigmoid(logit), in double, rounded once to binary32.
+float ellipse_level(float logit) {
+    const double o = 1.0 / (1.0 + std::exp(-(double)logit));
+    return (float)(2.0 * std::log(255.0 * o) + kTauSlack);
+}
+
+GeoF geom_f32(const float* X, const float* ls, const float* q, float logit, const CamF& c,
               int tiles_x, int tiles_y, int tw, int th) {
     GeoF g;
     g.vis = 0; g.depth = 0.f; g.x0 = g.x1 = g.y0 = g.y1 = 0;
+    g.mux = g.muy = g.kx = g.dys = g.pq = g.qq = 0.f;
+    g.ey = -1.f;
     const float* R = c.R;
     float t0 = ((R[0] * X[0] + R[1] * X[1]) + R[2] * X[2]) + c.t[0];
     float t1 = ((R[3] * X[0] + R[4] * X[1]) + R[5] * X[2]) + c.t[1];
@@ -227,7 +249,47 @@ GeoF geom_f32(const float* X, const float* ls, const float* q, const CamF& c,
     g.x1 = (int)std::fmin(fx1, (float)(tiles_x - 1));
     g.y0 = (int)std::fmax(fy0, 0.f);
     g.y1 = (int)std::fmin(fy1, (float)(tiles_y - 1));
+    g.mux = mux;
+    g.muy = muy;
+    const float tau = ellipse_level(logit);
+    if (tau > 0.f) {
+        const float sv = det / cc;  // variance of dx given dy
+        g.kx = b / cc;
+        g.pq = sv * tau;
+        g.qq = sv / cc;
+        g.ey = std::sqrt(tau * cc);
+        g.dys = b * std::sqrt(tau / a);
+    }
     return g;
+}
+
+// Tile columns [*sx0, *sx1] of tile row ty that the Gaussian's list covers:
+// those of its rectangle holding a pixel-centre column that meets the
+// ellipse inside the row's band of pixel-centre rows [yA, yB] (the band taken
+// as an interval, so the test can only keep more).  The ellipse cut by the
+// band is convex, so the columns it meets form one interval: from the
+// leftmost point x_l(dl) to the rightmost x_r(dr), where the unconstrained
+// extreme offsets -dys / dys are clamped into the band (x_r is concave in dy,
+// x_l convex).  False: no tile of this row.
+bool row_span(const GeoF& q, int ty, int tw, int th, int W, int H, int* sx0, int* sx1) {
+    const float yA = (float)(ty * th) + 0.5f;
+    const float yB = (float)std::min(ty * th + th, H) - 0.5f;
+    const float lo = std::fmax(yA - q.muy, -q.ey);
+    const float hi = std::fmin(yB - q.muy, q.ey);
+    if (!(lo <= hi)) return false;
+    const float dr = std::fmin(std::fmax(q.dys, lo), hi);
+    const float dl = std::fmin(std::fmax(-q.dys, lo), hi);
+    const float hr = std::sqrt(std::fmax(q.pq - q.qq * (dr * dr), 0.f));
+    const float hl = std::sqrt(std::fmax(q.pq - q.qq * (dl * dl), 0.f));
+    const float xr = q.mux + (q.kx * dr + hr);
+    const float xl = q.mux + (q.kx * dl - hl);
+    // pixel columns px whose centre px + 1/2 lies in [xl, xr]
+    const float fl = std::fmax(std::ceil(xl - 0.5f), 0.f);
+    const float fh = std::fmin(std::floor(xr - 0.5f), (float)(W - 1));
+    if (!(fl <= fh)) return false;
+    *sx0 = std::max((int)fl / tw, q.x0);
+    *sx1 = std::min((int)fh / tw, q.x1);
+    return *sx0 <= *sx1;
 }
 
 uint32_t float_bits(float f) {
@@ -590,7 +652,8 @@ void build_lists(orc_scene* s) {
     for (int64_t i = 0; i < (int64_t)nv * G; ++i) {
         int slot = (int)(i / G), g = (int)(i % G);
         s->geo[i] = geom_f32(&pf[3 * (size_t)g], &pf[3 * (size_t)G + 3 * g], &pf[6 * (size_t)G + 4 * g],
-                             s->camf[s->views[slot]], s->tiles_x, s->tiles_y, s->cfg.tile_w, s->cfg.tile_h);
+                             pf[10 * (size_t)G + g], s->camf[s->views[slot]], s->tiles_x, s->tiles_y, s->cfg.tile_w,
+                             s->cfg.tile_h);
     }
     // per (slot, tile): sort entries by (depth bits, Gaussian index)
     std::vector<std::vector<std::pair<uint64_t, int32_t>>> bins((size_t)nv * s->T);
@@ -599,9 +662,12 @@ void build_lists(orc_scene* s) {
             const GeoF& q = s->geo[(size_t)slot * G + g];
             if (!q.vis) continue;
             uint64_t key = ((uint64_t)float_bits(q.depth) << 32) | (uint32_t)g;
-            for (int ty = q.y0; ty <= q.y1; ++ty)
-                for (int tx = q.x0; tx <= q.x1; ++tx)
+            for (int ty = q.y0; ty <= q.y1; ++ty) {
+                int sx0, sx1;
+                if (!row_span(q, ty, s->cfg.tile_w, s->cfg.tile_h, s->W, s->H, &sx0, &sx1)) continue;
+                for (int tx = sx0; tx <= sx1; ++tx)
                     bins[(size_t)slot * s->T + ty * s->tiles_x + tx].push_back({key, g});
+            }
         }
     s->ranges.assign((size_t)nv * s->T + 1, 0);
     for (size_t b = 0; b < bins.size(); ++b) s->ranges[b + 1] = s->ranges[b] + (int64_t)bins[b].size();

@@ -13,8 +13,13 @@
  *   parameters: group-major SoA, [means Gx3 | log-scales Gx3 | quats Gx4
  *     (w,x,y,z) | opacity logits G | SH Gx(d+1)^2x3]; s = exp(log-scale),
  *     q normalised, o = sigmoid(logit), colour = SH(dir) + 0.5 clamped at 0.
- *   decisions that choose integers (visibility, depth key, tile rectangle)
- *     are taken in FP32 with a fixed operation order; everything else is FP64.
+ *   decisions that choose integers (visibility, depth key, tile rectangle,
+ *     the tile columns kept per row of the rectangle) are taken in FP32 with
+ *     a fixed operation order; everything else is FP64.
+ *   a Gaussian's tile list entries are the tiles of its rectangle some
+ *     pixel-centre column of which meets the ellipse where alpha reaches
+ *     1/255 (level 2 ln(255 o) + 0.02) within the tile row's band: a tile it
+ *     leaves out has alpha < 1/255 at every pixel, so no pixel changes.
  *   per-pixel skip / clamp / termination tests are taken in FP64 and a pixel
  *     whose test lies within a relative margin of its threshold is flagged.
  */

@@ -307,45 +307,58 @@ void radix_sort32(unsigned int* keys, unsigned int* vals, unsigned int* keys_alt
 // ---------------------------------------------------------------------------
 // Level 2: tile counts of the depth-sorted pairs and entry emission.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned long long rect_area(int4 rc) {
-    return rc.x > rc.y ? 0ull : (unsigned long long)(rc.y - rc.x + 1) * (unsigned long long)(rc.w - rc.z + 1);
+// Tiles the list of pair i covers: the row spans of its rectangle.
+__device__ __forceinline__ unsigned long long list_tiles(const Ctx& c, long long i) {
+    const int4 rc = c.rect[i];
+    if (rc.x > rc.y) return 0ull;
+    const float4 e0 = c.ell[2 * i], e1 = c.ell[2 * i + 1];
+    unsigned long long n = 0ull;
+    for (int ty = rc.z; ty <= rc.w; ++ty) {
+        int x0, x1;
+        if (row_span(e0, e1, ty, rc, c.tile_w, c.tile_h, c.W, c.H, x0, x1)) n += (unsigned long long)(x1 - x0 + 1);
+    }
+    return n;
 }
 
 __global__ void k_sorted_counts(Ctx c) {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= (long long)c.nv * c.G) return;
     const long long slot = (long long)(c.dkeys[k] >> 32);
-    c.cnt[k] = rect_area(c.rect[slot * c.G + c.dvals[k]]);
+    c.cnt[k] = list_tiles(c, slot * c.G + c.dvals[k]);
 }
 
 // Entries (view-tile key, Gaussian) of the depth-sorted pairs.  Each warp
 // takes 32 consecutive pairs and writes them one pair at a time with all
-// lanes, so the stores are contiguous and large rectangles do not serialise
-// on one thread.
+// lanes, row by row of its rectangle, so the stores are contiguous and large
+// rectangles do not serialise on one thread.
 __global__ void k_emit(Ctx c) {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     unsigned slot = 0u, g = 0u;
-    int4 rc = make_int4(1, 0, 1, 0);
     unsigned long long o = 0ull;
     if (k < (long long)c.nv * c.G) {
         slot = (unsigned)(c.dkeys[k] >> 32);
         g = c.dvals[k];
-        rc = c.rect[(long long)slot * c.G + g];
         o = c.cnt[k];
     }
     for (int j = 0; j < 32; ++j) {
-        const int x0 = __shfl_sync(0xffffffffu, rc.x, j), x1 = __shfl_sync(0xffffffffu, rc.y, j);
-        const int y0 = __shfl_sync(0xffffffffu, rc.z, j), y1 = __shfl_sync(0xffffffffu, rc.w, j);
-        const unsigned long long oj = __shfl_sync(0xffffffffu, o, j);
+        if (k - lane + j >= (long long)c.nv * c.G) break;  // warp-uniform
         const unsigned gj = __shfl_sync(0xffffffffu, g, j);
-        const unsigned base = __shfl_sync(0xffffffffu, slot, j) * (unsigned)c.T;
-        if (x0 > x1) continue;
-        const int w = x1 - x0 + 1, area = w * (y1 - y0 + 1);
-        for (int e = lane; e < area; e += 32) {
-            const int ty = y0 + e / w, tx = x0 + e - (e / w) * w;
-            c.keys[oj + e] = base + (unsigned)(ty * c.tiles_x + tx);
-            c.ids[oj + e] = gj;
+        const unsigned sj = __shfl_sync(0xffffffffu, slot, j);
+        unsigned long long oj = __shfl_sync(0xffffffffu, o, j);
+        const long long i = (long long)sj * c.G + gj;
+        const int4 rc = c.rect[i];
+        if (rc.x > rc.y) continue;
+        const float4 e0 = c.ell[2 * i], e1 = c.ell[2 * i + 1];
+        const unsigned base = sj * (unsigned)c.T;
+        for (int ty = rc.z; ty <= rc.w; ++ty) {
+            int x0, x1;
+            if (!row_span(e0, e1, ty, rc, c.tile_w, c.tile_h, c.W, c.H, x0, x1)) continue;
+            for (int tx = x0 + lane; tx <= x1; tx += 32) {
+                c.keys[oj + (tx - x0)] = base + (unsigned)(ty * c.tiles_x + tx);
+                c.ids[oj + (tx - x0)] = gj;
+            }
+            oj += (unsigned long long)(x1 - x0 + 1);
         }
     }
 }
@@ -383,8 +396,10 @@ void launch_ranges(const Ctx& c, cudaStream_t st) {
 // depth-sorted pair array slot s occupies [s G, (s+1) G): its visible pairs
 // by depth, then its culled ones (empty rectangles).
 //   rows : each visible pair, in order, is placed into the list of every tile
-//          row its rectangle spans: counts per (slot, row, chunk of kBinChunk
-//          pairs), an exclusive scan, then the placement;
+//          row of its rectangle whose band meets its ellipse (band_meets),
+//          with that row's tile columns (row_span, possibly none): counts
+//          per (slot, row, chunk of kBinChunk pairs), an exclusive scan, then
+//          the placement;
 //   tiles: one block per (slot, row) walks that row's list in order and places
 //          each pair into the row's tiles it spans: counts per tile, an
 //          exclusive scan (the tile lists' starts), then the placement in
@@ -414,18 +429,19 @@ __device__ __forceinline__ int warp_max_i(int v) {
     return v;
 }
 
-// One round of a warp: lane l holds the l-th of 32 consecutive items, covering
-// the bins [lo, hi] (lo > hi: none).  For every bin of the union, m = the
-// lanes covering it; count(bin, m) runs on every lane (warp-uniform m), and
-// place(bin, rank) on each covering lane, rank = its position among them.
-template <class Count, class Place>
-__device__ __forceinline__ void rank_round(int lo, int hi, Count&& count, Place&& place) {
+// One round of a warp: lane l holds the l-th of 32 consecutive items, which
+// may cover the bins [lo, hi] (lo > hi: none); covers(bin) decides each.  For
+// every bin of the union, m = the lanes covering it; count(bin, m) runs on
+// every lane (warp-uniform m), and place(bin, rank) on each covering lane,
+// rank = its position among them.
+template <class Covers, class Count, class Place>
+__device__ __forceinline__ void rank_round(int lo, int hi, Covers&& covers, Count&& count, Place&& place) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int ulo = warp_min_i(lo <= hi ? lo : 0x7fffffff);
     const int uhi = warp_max_i(lo <= hi ? hi : -1);
     for (int bin = ulo; bin <= uhi; ++bin) {
-        const bool in = lo <= bin && bin <= hi;
+        const bool in = lo <= bin && bin <= hi && covers(bin);
         const unsigned m = __ballot_sync(kFull, in);
         if (m == 0u) continue;
         if (in) place(bin, __popc(m & lt));
@@ -435,16 +451,32 @@ __device__ __forceinline__ void rank_round(int lo, int hi, Count&& count, Place&
     }
 }
 
-// Rectangle of the depth-ordered pair k of slot s (empty when culled or past e).
+// Rectangle and row-span ellipse of the depth-ordered pair k of slot s
+// (empty when culled or past e).
 __device__ __forceinline__ void pair_rect(const Ctx& c, long long s0, long long k, long long e, unsigned& g,
-                                          int4& rc) {
+                                          int4& rc, float4& e0, float4& e1) {
     g = 0u;
     rc = make_int4(1, 0, 1, 0);
+    e0 = e1 = make_float4(0.f, 0.f, 0.f, 0.f);
     if (k < e) {
         g = c.dvals[k];
         rc = c.rect[s0 + g];
-        if (rc.x > rc.y) rc = make_int4(1, 0, 1, 0);
+        if (rc.x > rc.y) {
+            rc = make_int4(1, 0, 1, 0);
+        } else {
+            e0 = c.ell[2 * (s0 + g)];
+            e1 = c.ell[2 * (s0 + g) + 1];
+        }
     }
+}
+
+// The rows of rc whose band meets the pair's ellipse: contiguous, since
+// band_meets is monotone from both ends; lo > hi when there are none.
+__device__ __forceinline__ void band_rows(const Ctx& c, int4 rc, float4 e0, float4 e1, int& lo, int& hi) {
+    lo = rc.z;
+    hi = rc.w;
+    while (lo <= hi && !band_meets(e0, e1, lo, c.tile_h, c.H)) ++lo;
+    while (hi >= lo && !band_meets(e0, e1, hi, c.tile_h, c.H)) --hi;
 }
 
 // Row counts per (slot, row, chunk).
@@ -458,9 +490,12 @@ __global__ void __launch_bounds__(kBinBlock) k_row_count(Ctx c, int nchunk, unsi
     const long long b = s0 + (long long)blockIdx.x * kBinChunk + (long long)(threadIdx.x >> 5) * kBinRun;
     const long long e = min(b + kBinRun, s0 + c.G);
     for (long long k = b + (threadIdx.x & 31); k < e; k += 32) {
-        const int4 rc = c.rect[s0 + c.dvals[k]];
-        if (rc.x <= rc.y)
-            for (int r = rc.z; r <= rc.w; ++r) atomicAdd(&s_cnt[r], 1u);
+        const long long i = s0 + c.dvals[k];
+        const int4 rc = c.rect[i];
+        if (rc.x > rc.y) continue;
+        int lo, hi;
+        band_rows(c, rc, c.ell[2 * i], c.ell[2 * i + 1], lo, hi);
+        for (int r = lo; r <= hi; ++r) atomicAdd(&s_cnt[r], 1u);
     }
     __syncthreads();
     const long long row0 = (long long)slot * c.tiles_y;
@@ -477,12 +512,18 @@ __device__ __forceinline__ void row_entry_unpack(unsigned long long v, unsigned&
     x1 = (int)(v >> 48);
 }
 
+// Placement in windows of kRowWin rows: the ballots of a window fix every
+// (pair, row) entry's slot, then each lane computes the tile columns of its
+// own rows once (row_span) and writes their entries.
+constexpr int kRowWin = 32;
+
 __global__ void __launch_bounds__(kBinBlock) k_row_place(Ctx c, int nchunk, const unsigned* mat,
                                                          unsigned long long* rl) {
     extern __shared__ unsigned bin_smem[];
     const int ny = c.tiles_y;
     unsigned* s_base = bin_smem;                                             // [ny]
     unsigned short* s_w = reinterpret_cast<unsigned short*>(bin_smem + ny);  // [kBinWarps][ny]
+    unsigned* s_dst = bin_smem + ny + (kBinWarps * ny + 1) / 2;              // [kBinWarps][kRowWin][32]
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < kBinWarps * ny; i += kBinBlock) s_w[i] = 0;
     __syncthreads();
@@ -491,13 +532,17 @@ __global__ void __launch_bounds__(kBinBlock) k_row_place(Ctx c, int nchunk, cons
     const long long b = s0 + (long long)blockIdx.x * kBinChunk + (long long)wid * kBinRun;
     const long long e = min(b + kBinRun, s0 + c.G);
     unsigned short* mine = s_w + wid * ny;
+    const auto all = [](int) { return true; };
+    const auto count = [&](int r, unsigned m) { if (lane == 0) mine[r] += (unsigned short)__popc(m); };
     // this warp's count per row
     for (long long base = b; base < e; base += 32) {
         unsigned g;
         int4 rc;
-        pair_rect(c, s0, base + lane, e, g, rc);
-        rank_round(rc.z, rc.w, [&](int r, unsigned m) { if (lane == 0) mine[r] += (unsigned short)__popc(m); },
-                   [](int, int) {});
+        float4 e0, e1;
+        pair_rect(c, s0, base + lane, e, g, rc, e0, e1);
+        int lo, hi;
+        band_rows(c, rc, e0, e1, lo, hi);
+        rank_round(lo, hi, all, count, [](int, int) {});
     }
     __syncthreads();
     // warps' offsets per row within the chunk, the chunk's base per row
@@ -513,13 +558,28 @@ __global__ void __launch_bounds__(kBinBlock) k_row_place(Ctx c, int nchunk, cons
         s_base[r] = mat[(row0 + r) * nchunk + blockIdx.x];
     }
     __syncthreads();
+    unsigned* dst = s_dst + wid * kRowWin * 32;
     for (long long base = b; base < e; base += 32) {
         unsigned g;
         int4 rc;
-        pair_rect(c, s0, base + lane, e, g, rc);
-        const unsigned long long v = row_entry(g, rc.x, rc.y);
-        rank_round(rc.z, rc.w, [&](int r, unsigned m) { if (lane == 0) mine[r] += (unsigned short)__popc(m); },
-                   [&](int r, int rank) { rl[s_base[r] + mine[r] + rank] = v; });
+        float4 e0, e1;
+        pair_rect(c, s0, base + lane, e, g, rc, e0, e1);
+        int lo, hi;
+        band_rows(c, rc, e0, e1, lo, hi);
+        const int ulo = warp_min_i(lo <= hi ? lo : 0x7fffffff);
+        const int uhi = warp_max_i(lo <= hi ? hi : -1);
+        for (int w0 = ulo; w0 <= uhi; w0 += kRowWin) {
+            const int wl = max(lo, w0), wh = min(hi, w0 + kRowWin - 1);
+            rank_round(wl, wh, all, count,
+                       [&](int r, int rank) { dst[(r - w0) * 32 + lane] = s_base[r] + mine[r] + rank; });
+            __syncwarp();
+            for (int r = wl; r <= wh; ++r) {
+                int x0, x1;  // no tile in this row: an empty entry the tile stage skips
+                if (!row_span(e0, e1, r, rc, c.tile_w, c.tile_h, c.W, c.H, x0, x1)) x0 = 1, x1 = 0;
+                rl[dst[(r - w0) * 32 + lane]] = row_entry(g, x0, x1);
+            }
+            __syncwarp();
+        }
     }
 }
 
@@ -548,6 +608,7 @@ __global__ void __launch_bounds__(kBinBlock) k_tile_count(Ctx c, int nchunk, con
         unsigned g;
         int x0, x1;
         row_entry_unpack(rl[k], g, x0, x1);
+        if (x0 > x1) continue;
         atomicAdd(&s_d[x0], 1);
         atomicAdd(&s_d[x1 + 1], -1);
     }
@@ -631,10 +692,12 @@ __global__ void k_tile_ranges(Ctx c, const unsigned* start, const unsigned* tota
     const unsigned b = start[vt];
     const unsigned e = vt + 1 < nvt ? start[vt + 1] : *total32;
     c.ranges[vt] = make_int2((int)b, (int)e);
+    if (vt == 0) c.sc->n_list = *total32;
 }
 
 static size_t row_place_smem(const Ctx& c) {
-    return (size_t)c.tiles_y * (sizeof(unsigned) + kBinWarps * sizeof(unsigned short));
+    const size_t w16 = ((size_t)kBinWarps * c.tiles_y + 1) / 2;  // s_w in 32-bit words
+    return ((size_t)c.tiles_y + w16 + (size_t)kBinWarps * kRowWin * 32) * sizeof(unsigned);
 }
 
 bool bin_rows_fit(const Ctx& c) {

@@ -59,6 +59,9 @@ struct Scalars {
     double eta;
     unsigned int max_dc_bits;  // bits of max |x_dc| (non-negative float)
     unsigned int pad1;
+    // preprocessing
+    unsigned int n_list;  // tile-list entries of the step (written by the binning)
+    unsigned int pad2;
 };
 
 // Everything a kernel needs to know about the scene and the current step.
@@ -80,12 +83,14 @@ struct Ctx {
     float4* pjac;           // per (view, Gaussian) pair: jac_f4(deg) planes of nv*G float4, the Jacobian
                             // of the pair's 9 screen-space features w.r.t. the Gaussian's parameters
     int4* rect;             // inclusive tile rectangle, x0 > x1 when culled
+    float4* ell;            // per pair 2 float4: the alpha >= 1/255 ellipse that picks each rectangle
+                            // row's tile columns (row_span)
     unsigned long long* dkeys;  // (slot << 32 | depth bits, or all ones when culled), sorted in place
     unsigned int* dvals;        // Gaussian index of each depth key
     unsigned long long* cnt;  // tiles touched per depth-sorted pair (then exclusive prefix)
     unsigned long long* n_visible;  // count of visible pairs
-    unsigned long long* n_entries;  // sum over visible pairs of the tiles they overlap
-    unsigned long long* n_rowent;   // sum over visible pairs of the tile rows they span
+    unsigned long long* n_entries;  // bound on the tile-list entries: band rows x rectangle width
+    unsigned long long* n_rowent;   // sum over visible pairs of the rectangle rows band_meets keeps
     float* cot;             // kCotF floats
     float* gram;            // kGramF floats
     // binning
@@ -253,6 +258,54 @@ void launch_b_update(const BatchTables& t, int iter, int grid, cudaStream_t st);
 void launch_b_lm_update(const BatchTables& t, int iters, int grid, cudaStream_t st);
 
 // ---- the per-tile SplitMix64 stream of the pixel sampler --------------------
+// Tile columns [x0, x1] that the list of a pair covers in tile row ty of its
+// rectangle rc.  The ellipse {d : d^T Sigma2^-1 d <= tau} around the 2D mean,
+// tau = 2 ln(255 o) + 0.02, holds every pixel where alpha reaches 1/255 (by a
+// factor e^-0.01 on the threshold, far above FP32 rounding), so a tile it
+// misses changes no pixel.  e0 = (mux, muy, kx, dys), e1 = (pq, qq, ey, -):
+// given the offset dy from muy the ellipse holds dx with (dx - kx dy)^2 <=
+// pq - qq dy^2, |dy| <= ey (< 0: empty), and its rightmost / leftmost points
+// lie at dy = dys / -dys.  Its cut by the row's band of pixel-centre rows
+// [yA, yB] (taken as an interval) is convex, so the pixel-centre columns it
+// meets run from x_l(dl) to x_r(dr), the extreme offsets clamped into the
+// band (x_r is concave in dy, x_l convex).  Every operation is rounded on
+// its own, in a fixed order, so the lists are reproducible bit for bit.
+__device__ __forceinline__ bool row_span(float4 e0, float4 e1, int ty, int4 rc, int tw, int th, int W, int H,
+                                         int& x0, int& x1) {
+    const float yA = __fadd_rn((float)(ty * th), 0.5f);
+    const float yB = __fsub_rn((float)min(ty * th + th, H), 0.5f);
+    const float lo = fmaxf(__fsub_rn(yA, e0.y), -e1.z);
+    const float hi = fminf(__fsub_rn(yB, e0.y), e1.z);
+    if (!(lo <= hi)) return false;  // the band misses the ellipse's rows (band_meets)
+    const float dr = fminf(fmaxf(e0.w, lo), hi);
+    const float dl = fminf(fmaxf(-e0.w, lo), hi);
+    const float hr = __fsqrt_rn(fmaxf(__fsub_rn(e1.x, __fmul_rn(e1.y, __fmul_rn(dr, dr))), 0.f));
+    const float hl = __fsqrt_rn(fmaxf(__fsub_rn(e1.x, __fmul_rn(e1.y, __fmul_rn(dl, dl))), 0.f));
+    const float xr = __fadd_rn(e0.x, __fadd_rn(__fmul_rn(e0.z, dr), hr));
+    const float xl = __fadd_rn(e0.x, __fsub_rn(__fmul_rn(e0.z, dl), hl));
+    // pixel columns px whose centre px + 1/2 lies in [xl, xr]
+    const float fl = fmaxf(ceilf(__fsub_rn(xl, 0.5f)), 0.f);
+    const float fh = fminf(floorf(__fsub_rn(xr, 0.5f)), (float)(W - 1));
+    if (!(fl <= fh)) return false;
+    // their tile columns (a shift for power-of-two tile widths)
+    const int il = (int)fl, ih = (int)fh;
+    const bool pow2 = (tw & (tw - 1)) == 0;
+    const int sh = __ffs(tw) - 1;
+    x0 = max(pow2 ? il >> sh : il / tw, rc.x);
+    x1 = min(pow2 ? ih >> sh : ih / tw, rc.y);
+    return x0 <= x1;
+}
+
+// The first test of row_span alone: whether tile row ty's band meets the
+// ellipse's rows |dy| <= ey.  Monotone in ty from both ends, so the rows that
+// pass are contiguous; row_span can still find no tile in one of them (no
+// pixel-centre column inside, or outside the rectangle's columns).
+__device__ __forceinline__ bool band_meets(float4 e0, float4 e1, int ty, int th, int H) {
+    const float yA = __fadd_rn((float)(ty * th), 0.5f);
+    const float yB = __fsub_rn((float)min(ty * th + th, H), 0.5f);
+    return fmaxf(__fsub_rn(yA, e0.y), -e1.z) <= fminf(__fsub_rn(yB, e0.y), e1.z);
+}
+
 __device__ __forceinline__ unsigned long long sm64_mix(unsigned long long z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;

@@ -109,6 +109,7 @@ struct Prim {
     float s[3], qn, qh[4];
     float R[9], M[9], S[9];
     float o;
+    float tau;  // level of the alpha >= 1/255 ellipse (row_span)
     bool valid;
     // per (view, Gaussian)
     float t[3];
@@ -174,6 +175,10 @@ __global__ void k_prep_gauss(Ctx c) {
         for (int j = i; j < 3; ++j)
             S[k++] = ra(ra(rm(m[3 * i], m[3 * j]), rm(m[3 * i + 1], m[3 * j + 1])), rm(m[3 * i + 2], m[3 * j + 2]));
     const float o = 1.f / (1.f + expf(-p[10 * G + g]));
+    // alpha = o exp(-q / 2) >= 1/255 iff q <= 2 ln(255 o); with a slack of
+    // 0.02, in double, rounded once
+    const double od = 1.0 / (1.0 + exp(-(double)p[10 * G + g]));
+    const float tau = (float)__dadd_rn(__dmul_rn(2.0, log(255.0 * od)), 0.02);
     float4* gc = c.gcache;
     gc[0 * G + g] = make_float4(s[0], s[1], s[2], qn);
     gc[1 * G + g] = make_float4(w, x, y, z);
@@ -183,7 +188,7 @@ __global__ void k_prep_gauss(Ctx c) {
     gc[5 * G + g] = make_float4(m[3], m[4], m[5], m[6]);
     gc[6 * G + g] = make_float4(m[7], m[8], S[0], S[1]);
     gc[7 * G + g] = make_float4(S[2], S[3], S[4], S[5]);
-    gc[8 * G + g] = make_float4(o, valid ? 1.f : 0.f, 0.f, 0.f);
+    gc[8 * G + g] = make_float4(o, valid ? 1.f : 0.f, tau, 0.f);
 }
 
 __device__ __forceinline__ void load_gauss(const Ctx& c, int g, Prim& P) {
@@ -209,13 +214,16 @@ __device__ __forceinline__ void load_gauss(const Ctx& c, int g, Prim& P) {
     v = gc[8 * G + g];
     P.o = v.x;
     P.valid = v.y != 0.f;
+    P.tau = v.z;
 }
 
 // Per-(view, Gaussian) projection with the list decisions, continuing the
-// fixed FP32 operation order of k_prep_gauss (so visibility, depth key and
-// tile rectangle are reproducible bit for bit).  Returns false when culled.
+// fixed FP32 operation order of k_prep_gauss (so visibility, depth key, tile
+// rectangle and the ellipse that picks each row's tiles are reproducible bit
+// for bit).  Returns false when culled.
 __device__ __forceinline__ bool prim_project(const float X[3], const CamDev& cam, int tiles_x, int tiles_y, int tw,
-                                             int th, Prim& P, int4* rect_out, float* depth_out) {
+                                             int th, Prim& P, int4* rect_out, float* depth_out,
+                                             float4* ell_out = nullptr) {
     const float* R = cam.R;
     P.t[0] = ra(ra(ra(rm(R[0], X[0]), rm(R[1], X[1])), rm(R[2], X[2])), cam.t[0]);
     P.t[1] = ra(ra(ra(rm(R[3], X[0]), rm(R[4], X[1])), rm(R[5], X[2])), cam.t[1]);
@@ -264,6 +272,21 @@ __device__ __forceinline__ bool prim_project(const float X[3], const CamDev& cam
         rect_out->z = (int)fmaxf(fy0, 0.f);
         rect_out->w = (int)fminf(fy1, (float)(tiles_y - 1));
         *depth_out = P.t[2];
+        if (ell_out) {
+            // (dx - kx dy)^2 <= pq - qq dy^2 with kx = b / c, pq = (det / c) tau,
+            // qq = det / c^2; |dy| <= sqrt(tau c); extreme points at dy = +-b sqrt(tau / a)
+            float kx = 0.f, dys = 0.f, pq = 0.f, qq = 0.f, ey = -1.f;
+            if (P.tau > 0.f) {
+                const float sv = rd(P.det, P.c);
+                kx = rd(P.b, P.c);
+                pq = rm(sv, P.tau);
+                qq = rd(sv, P.c);
+                ey = __fsqrt_rn(rm(P.tau, P.c));
+                dys = rm(P.b, __fsqrt_rn(rd(P.tau, P.a)));
+            }
+            ell_out[0] = make_float4(P.mux, P.muy, kx, dys);
+            ell_out[1] = make_float4(pq, qq, ey, 0.f);
+        }
     }
     return true;
 }
@@ -547,12 +570,16 @@ __global__ void k_prep_fwd(Ctx c) {
     load_gauss(c, g, P);
     int4 rect;
     float depth;
-    const bool vis = prim_project(X, cam, c.tiles_x, c.tiles_y, c.tile_w, c.tile_h, P, &rect, &depth);
-    // visible pairs, and the tiles and tile rows they cover (the sizes of the
-    // tile lists and of the binning's row lists)
+    float4 ell[2];
+    const bool vis = prim_project(X, cam, c.tiles_x, c.tiles_y, c.tile_w, c.tile_h, P, &rect, &depth, ell);
+    // visible pairs, the binning's row-list entries (the rectangle rows whose
+    // band meets the ellipse), and a bound on the tile-list entries (those
+    // rows times the rectangle's width; the binning counts the exact number)
     const unsigned active = __activemask();
     const unsigned ballot = __ballot_sync(active, vis);
-    const unsigned rows = vis ? (unsigned)(rect.w - rect.z + 1) : 0u;
+    unsigned rows = 0u;
+    if (vis)
+        for (int ty = rect.z; ty <= rect.w; ++ty) rows += band_meets(ell[0], ell[1], ty, c.tile_h, c.H) ? 1u : 0u;
     const unsigned area = vis ? rows * (unsigned)(rect.y - rect.x + 1) : 0u;
     const unsigned sum_rows = __reduce_add_sync(active, rows), sum_area = __reduce_add_sync(active, area);
     if ((threadIdx.x & 31) == __ffs(active) - 1 && ballot) {
@@ -574,6 +601,8 @@ __global__ void k_prep_fwd(Ctx c) {
     r[1] = make_float4(P.C, P.o, P.col[0], P.col[1]);
     r[2] = make_float4(P.col[2], 0.f, 0.f, 0.f);
     c.rect[i] = rect;
+    c.ell[2 * i] = ell[0];
+    c.ell[2 * i + 1] = ell[1];
     c.dkeys[i] = ((unsigned long long)slot << 32) | __float_as_uint(depth);
     float J[Jac<DEG>::N];
     pair_jacobian<DEG>(P, cam, sh, J);

@@ -78,7 +78,7 @@ struct lmrs_scene {
     const float* targets = nullptr;
     // device state
     DevBuf params, cams, views, gcache, pjac;
-    DevBuf rec, tan, rect, dkeys, dvals, dkeys_alt, dvals_alt, dtmp, cnt, cot, gram;
+    DevBuf rec, tan, rect, ell, dkeys, dvals, dkeys_alt, dvals_alt, dtmp, cnt, cot, gram;
     DevBuf keys, ids, keys_alt, ids_alt, ranges, scan_tmp, radix_tmp, total;
     DevBuf tile_off, off, wtile, wsample, work;
     DevBuf item_cost, work_sorted, okeys, ovals, okeys_alt, ovals_alt, otmp;
@@ -102,7 +102,7 @@ struct lmrs_scene {
 
     // every device buffer the scene owns
     std::vector<DevBuf*> bufs() {
-        return {&params, &cams, &views, &gcache, &pjac, &rec, &tan, &rect, &dkeys, &dvals, &dkeys_alt, &dvals_alt, &dtmp, &cnt,
+        return {&params, &cams, &views, &gcache, &pjac, &rec, &tan, &rect, &ell, &dkeys, &dvals, &dkeys_alt, &dvals_alt, &dtmp, &cnt,
                 &cot, &gram, &keys, &ids, &keys_alt, &ids_alt, &ranges, &scan_tmp, &radix_tmp, &total, &tile_off,
                 &off, &wtile, &wsample, &work, &item_cost, &work_sorted, &okeys, &ovals, &okeys_alt, &ovals_alt, &otmp,
                 &cids, &clen, &binmat, &bintmp, &rowl, &tcnt, &resid, &cacheC, &cacheT, &cacheCh, &cacheTh, &cacheN, &x, &r, &z, &p, &Ap,
@@ -127,6 +127,7 @@ struct lmrs_scene {
         c.tan = tan.as<float4>();
         c.pjac = pjac.as<float4>();
         c.rect = rect.as<int4>();
+        c.ell = ell.as<float4>();
         c.dkeys = dkeys.as<unsigned long long>();
         c.dvals = dvals.as<unsigned int>();
         c.cnt = cnt.as<unsigned long long>();
@@ -461,6 +462,21 @@ lmrs_status do_cg(lmrs_scene* s, const float* b, float* x, int iters) {
 lmrs_status lm_step_iters(lmrs_scene* s, const int32_t* view_ids, int32_t n_views, int64_t lm_step, int iters,
                           lmrs_step_stats* st);
 
+// Tile-list entries of the preprocessed step: known on the host after the
+// emission path, read from the scalars (one small copy) after the binning
+// path; -1 when the copy fails.
+long long pairs_exact(lmrs_scene* s) {
+    if (s->npairs < 0) {
+        unsigned int n = 0u;
+        if (cudaMemcpyAsync(&n, &s->sc.as<Scalars>()->n_list, sizeof(n), cudaMemcpyDeviceToHost, s->st) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(s->st) != cudaSuccess)
+            return -1;
+        s->npairs = (long long)n;
+    }
+    return s->npairs;
+}
+
 lmrs_status read_scalars(lmrs_scene* s, Scalars* h) {
     CK(s, cudaMemcpyAsync(h, s->sc.p, sizeof(Scalars), cudaMemcpyDeviceToHost, s->st));
     CK(s, cudaStreamSynchronize(s->st));
@@ -616,6 +632,7 @@ lmrs_status lmrs_preprocess(lmrs_scene* s, const int32_t* view_ids, int32_t n_vi
     // blocked by 32 pairs, each view's Gaussians padded to a multiple of 32
     TRY(ensure(s, s->pjac, sizeof(float4) * jac_f4(s->deg) * (size_t)s->nv * (size_t)((s->G + 31) & ~31)));
     TRY(ensure(s, s->rect, sizeof(int4) * pairs));
+    TRY(ensure(s, s->ell, 2 * sizeof(float4) * pairs));
     TRY(ensure(s, s->dkeys, sizeof(unsigned long long) * pairs));
     TRY(ensure(s, s->dkeys_alt, sizeof(unsigned long long) * pairs));
     TRY(ensure(s, s->dvals, sizeof(unsigned int) * pairs));
@@ -653,10 +670,12 @@ lmrs_status lmrs_preprocess(lmrs_scene* s, const int32_t* view_ids, int32_t n_vi
     unsigned long long tot[3] = {0ull, 0ull, 0ull};
     CK(s, cudaMemcpyAsync(tot, s->total.p, sizeof(tot), cudaMemcpyDeviceToHost, s->st));
     CK(s, cudaStreamSynchronize(s->st));
+    // the emission path counted the entries exactly; the binning path has a
+    // bound here and writes the exact number to the scalars (pairs_exact)
     const unsigned long long total = tot[0];
     s->nvisible = (long long)tot[1];
     if (total >= (1ull << 31)) return fail(s, LMRS_ERR_BUDGET, "more than 2^31 (view, tile, Gaussian) pairs");
-    s->npairs = (long long)total;
+    s->npairs = rows ? -1 : (long long)total;
     const size_t np = std::max<size_t>((size_t)total, 1);
     TRY(ensure(s, s->ids, sizeof(unsigned int) * np));
     TRY(ensure(s, s->cids, sizeof(unsigned int) * np * (size_t)s->max_items));
@@ -890,7 +909,7 @@ lmrs_status lm_step_iters(lmrs_scene* s, const int32_t* view_ids, int32_t n_view
         st->rz0 = h.rz0;
         st->rz_final = h.rz;
         st->n_samples = s->S;
-        st->n_pairs = s->npairs;
+        st->n_pairs = s->npairs >= 0 ? s->npairs : (int64_t)h.n_list;
         if (h.numeric_error) return fail(s, LMRS_ERR_NUMERIC, "non-finite or non-positive CG curvature");
     }
     return LMRS_OK;
@@ -1015,7 +1034,9 @@ lmrs_status lmrs_get_timing(lmrs_scene* s, lmrs_kernel_time* out, int32_t max_en
 
 int64_t lmrs_num_params(const lmrs_scene* s) { return s ? s->P : -1; }
 int64_t lmrs_num_samples(const lmrs_scene* s) { return s && s->layout_nv >= 0 ? s->S : -1; }
-int64_t lmrs_num_pairs(const lmrs_scene* s) { return s && s->preprocessed ? s->npairs : -1; }
+int64_t lmrs_num_pairs(const lmrs_scene* s) {
+    return s && s->preprocessed ? pairs_exact(const_cast<lmrs_scene*>(s)) : -1;
+}
 int64_t lmrs_num_visible(const lmrs_scene* s) { return s && s->preprocessed ? s->nvisible : -1; }
 
 lmrs_status lmrs_get_samples(lmrs_scene* s, uint8_t* off, int32_t* tile_off) {
@@ -1032,8 +1053,9 @@ lmrs_status lmrs_get_tile_lists(lmrs_scene* s, int32_t* ranges, int32_t* ids) {
     TRY(need_pre(s));
     if (ranges)
         CK(s, cudaMemcpyAsync(ranges, s->ranges.p, sizeof(int2) * (size_t)s->nv * s->T, cudaMemcpyDeviceToHost, s->st));
-    if (ids && s->npairs > 0)
-        CK(s, cudaMemcpyAsync(ids, s->ids.p, sizeof(unsigned int) * s->npairs, cudaMemcpyDeviceToHost, s->st));
+    const long long n = pairs_exact(s);
+    if (n < 0) return fail(s, LMRS_ERR_CUDA, "reading the tile-list size");
+    if (ids && n > 0) CK(s, cudaMemcpyAsync(ids, s->ids.p, sizeof(unsigned int) * n, cudaMemcpyDeviceToHost, s->st));
     CK(s, cudaStreamSynchronize(s->st));
     return LMRS_OK;
 }
@@ -1074,10 +1096,10 @@ int64_t lmrs_footprint_bytes(const lmrs_config* cfg, int64_t n_gauss, int32_t n_
         max_items = std::max(max_items, (k + 31) / 32);
     }
     const double pairs = nv * G, entries = tpp * pairs, S = nv * S_view, items = nv * items_view;
-    // rec 96, Jacobian cache, rect 16, depth keys/values and their
-    // alternates 24, counts 8, cotangent slots 48, Gram blocks 176; scan and
-    // sort scratch ~2
-    const double per_pair = 96 + 16.0 * jac_f4(cfg->sh_degree) + 16 + 24 + 8 + 48 + 4.0 * kGramF + 2;
+    // rec 96, Jacobian cache, rect 16, row-span ellipse 32, depth keys/values
+    // and their alternates 24, counts 8, cotangent slots 48, Gram blocks 176;
+    // scan and sort scratch ~2
+    const double per_pair = 96 + 16.0 * jac_f4(cfg->sh_degree) + 16 + 32 + 24 + 8 + 48 + 4.0 * kGramF + 2;
     // ids and the binning's row lists 8 (the emission path: keys, ids and their
     // alternates 16, the bound taken), compact lists 4 per work item of a tile
     const double per_entry = 16 + 4.0 * max_items + 1;
@@ -1442,7 +1464,7 @@ lmrs_status lmrs_batch_lm_step(lmrs_batch* B, const int32_t* view_ids, const int
         stats[i].rz0 = rz[0];
         stats[i].rz_final = rz[B->iters];
         stats[i].n_samples = s->S;
-        stats[i].n_pairs = s->npairs;
+        stats[i].n_pairs = s->npairs >= 0 ? s->npairs : (int64_t)h.n_list;
         if (h.numeric_error) {
             B->scene_rc[i] = LMRS_ERR_NUMERIC;
             if (out == LMRS_OK) out = bfail(B, LMRS_ERR_NUMERIC, "scene " + std::to_string(i));

@@ -357,21 +357,95 @@ def test_lm_step_descends():
 # Binning and sampling (integer work)
 # ---------------------------------------------------------------------------
 
-def test_tile_lists_equal_brute_force():
-    sc = syn.tiny_scene(n_gauss=300)
-    osc = oracle.OracleScene(sc.params, sc.cams, sc.n_gauss, 0)
+def _ellipse_scene():
+    """300 large anisotropic Gaussians on a ragged 100 x 70 view, 8 of them
+    too faint (o < 1/255) to reach the alpha threshold anywhere."""
+    rng = np.random.default_rng(41)
+    G = 300
+    means = rng.uniform(-0.6, 0.6, (G, 3))
+    ls = rng.normal(-2.6, 0.5, (G, 3))
+    q = rng.standard_normal((G, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    opac = rng.normal(0.0, 1.5, G)
+    opac[:8] = -7.0
+    sh = np.zeros((G, 1, 3))
+    sh[:, 0, :] = rng.uniform(-0.8, 0.8, (G, 3))
+    cams = syn.ring_cameras(3, 3.0, 100, 70, elev_deg=20.0)
+    return syn.Scene(G, 0, syn.pack_params(means, ls, q, opac, sh), cams, 41)
+
+
+def _min_level(f, tx, ty, tw, th, W, H):
+    """Smallest d^T Sigma2^-1 d over the tile's pixel-centre columns and its
+    band of pixel-centre rows taken as an interval, in FP64: per column the
+    quadratic in dy is minimised at its vertex clamped into the band."""
+    mux, muy, A, B, C = f[0], f[1], f[2], f[3], f[4]
+    lo = ty * th + 0.5 - muy
+    hi = min(ty * th + th, H) - 0.5 - muy
+    dx = np.arange(tx * tw, min(tx * tw + tw, W)) + 0.5 - mux
+    dy = np.clip(-B * dx / C, lo, hi)
+    return float((A * dx * dx + 2.0 * B * dx * dy + C * dy * dy).min())
+
+
+@pytest.mark.parametrize("tw,th", [(16, 16), (8, 32)])
+def test_tile_lists_are_the_tiles_the_alpha_ellipse_reaches(tw, th):
+    """A Gaussian's list covers the tiles of its 3-sigma rectangle where the
+    ellipse alpha >= 1/255 (level 2 ln(255 o), plus a slack of 0.02) meets a
+    pixel-centre column within the tile row's band, sorted by (depth,
+    index).  Checked against the FP64 features by a separate formulation
+    (per column, the vertex of the quadratic in dy), leaving out tiles within
+    a rounding margin of the level; every tile left out has alpha < 1/255 at
+    all of its pixels, so the culling changes no pixel."""
+    sc = _ellipse_scene()
+    W, H = 100, 70
+    osc = oracle.OracleScene(sc.params, sc.cams, sc.n_gauss, 0, tile_w=tw, tile_h=th)
     osc.begin_step([2, 0])
     ranges, ids = osc.lists()
-    T = osc.n_tiles
+    T, ntx = osc.n_tiles, osc.tiles_x
+    dropped = kept = decided = 0
     for slot in range(2):
         vis, depth, rect = osc.geom(slot)
+        f = osc.features(slot)
+        lists = [list(ids[ranges[slot * T + t, 0]:ranges[slot * T + t, 1]]) for t in range(T)]
         for t in range(T):
-            tx, ty = t % osc.tiles_x, t // osc.tiles_x
-            inside = [g for g in range(sc.n_gauss) if vis[g] and rect[g, 0] <= tx <= rect[g, 1]
-                      and rect[g, 2] <= ty <= rect[g, 3]]
-            expect = sorted(inside, key=lambda g: (float(depth[g]), g))
-            b, e = ranges[slot * T + t]
-            assert list(ids[b:e]) == expect
+            tx, ty = t % ntx, t // ntx
+            cand = [g for g in range(sc.n_gauss) if vis[g] and rect[g, 0] <= tx <= rect[g, 1]
+                    and rect[g, 2] <= ty <= rect[g, 3]]
+            order = sorted(cand, key=lambda g: (float(depth[g]), g))
+            got = lists[t]
+            # a subsequence of the rectangle's depth order
+            pos = [order.index(g) for g in got]
+            assert pos == sorted(pos) and len(set(got)) == len(got)
+            for g in order:
+                tau = 2.0 * math.log(255.0 * f[g, 5]) + 0.02
+                inside = g in got
+                kept += inside
+                dropped += not inside
+                if tau <= 0.0:
+                    assert not inside
+                    continue
+                m = _min_level(f[g], tx, ty, tw, th, W, H)
+                if abs(m - tau) > 2e-3 * max(tau, 1.0) + 1e-3:
+                    assert inside == (m < tau), (slot, t, g, m, tau)
+                    decided += 1
+                if not inside:
+                    px = np.arange(tx * tw, min(tx * tw + tw, W)) + 0.5 - f[g, 0]
+                    py = np.arange(ty * th, min(ty * th + th, H)) + 0.5 - f[g, 1]
+                    dx, dy = np.meshgrid(px, py)
+                    q = f[g, 2] * dx * dx + 2.0 * f[g, 3] * dx * dy + f[g, 4] * dy * dy
+                    assert f[g, 5] * np.exp(-0.5 * q).max() < 1.0 / 255.0
+    # the test decides nearly every entry, and the ellipse drops a good share
+    assert decided >= 0.99 * (kept + dropped - 8 * 2 * 4)
+    assert dropped >= 0.1 * (kept + dropped) and kept > 500
+
+
+def test_faint_gaussians_have_no_entries():
+    sc = _ellipse_scene()
+    osc = oracle.OracleScene(sc.params, sc.cams, sc.n_gauss, 0)
+    osc.begin_step([0, 1])
+    vis, _, _ = osc.geom(0)
+    _, ids = osc.lists()
+    assert vis[:8].any()  # visible, but alpha < 1/255 everywhere
+    assert not np.isin(ids, np.arange(8)).any()
 
 
 def test_fp32_rectangles_agree_with_fp64_geometry():
