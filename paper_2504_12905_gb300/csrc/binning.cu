@@ -654,6 +654,8 @@ __global__ void __launch_bounds__(kColBlock) k_tile_place(Ctx c, int nchunk, con
     row_range(c, nchunk, mat, rtotal, sr, b, e);
     for (int x0g = 0; x0g < nx; x0g += kColWarps * kColsPerWarp) {
         if (x0g + wid >= nx) continue;  // this warp owns no column of the group
+        // its columns inside the row: the ballots of the others are skipped
+        const int nq = min(kColsPerWarp, (nx - 1 - x0g - wid) / kColWarps + 1);
         unsigned off[kColsPerWarp];
         int col[kColsPerWarp];
 #pragma unroll
@@ -675,6 +677,7 @@ __global__ void __launch_bounds__(kColBlock) k_tile_place(Ctx c, int nchunk, con
                 row_entry_unpack(v[r], g, x0, x1);
 #pragma unroll
                 for (int q = 0; q < kColsPerWarp; ++q) {
+                    if (q >= nq) break;  // warp-uniform
                     const bool in = x0 <= col[q] && col[q] <= x1;
                     const unsigned m = __ballot_sync(kFull, in);
                     if (in) c.ids[off[q] + __popc(m & lt)] = g;
