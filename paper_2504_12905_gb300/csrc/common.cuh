@@ -228,6 +228,8 @@ void launch_raster_vjp(const Ctx& c, const float* u, cudaStream_t st);
 // Fused J^T W J: JVP pass then VJP pass per warp item.
 void launch_raster_jtj(const Ctx& c, cudaStream_t st);
 void launch_raster_gram(const Ctx& c, cudaStream_t st);
+// k_gram that also back-scatters the right-hand side's cotangents into c.cot
+void launch_raster_gram_rhs(const Ctx& c, cudaStream_t st);
 // Longest-first order of the work items by the traversal lengths the forward
 // render recorded: sorted[k] = work[order[k]].  Scratch: keys/vals and their
 // alternates (nwork each) and radix_tmp_bytes(nwork).

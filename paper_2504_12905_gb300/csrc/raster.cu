@@ -435,6 +435,11 @@ void launch_b_jtj(const BatchTables& t, int grid, cudaStream_t st) {
 //   [0,21)   (sum_ch w_ch h_ch^2) e e^T   (upper triangle, row-major)
 //   [21,39)  w_ch q h_ch e_f              (index 21 + 3 f + ch)
 //   [39,42)  w_ch q^2
+// With kRhs the same walk also back-scatters the right-hand side J^T W r
+// (plus the SSIM rows' ssim_weight w d s): for the cotangent ub of the
+// sample's colour, d<ub, C>/d alpha = ub . h, so the 9 feature cotangents
+// are (ub . h) e and ub q -- those of k_vjp, without a second walk.
+template <bool kRhs>
 __global__ void __launch_bounds__(kRasterBlock) k_gram(Ctx c) {
     LMRS_RASTER_PROLOGUE
     const List L = compact_list(c, p);
@@ -443,6 +448,15 @@ __global__ void __launch_bounds__(kRasterBlock) k_gram(Ctx c) {
     int ncons = 0;
     if (p.active) load_cache(c, p.si, Cf, ncons);
     const float wch[3] = {row_weight(c, p, 0), row_weight(c, p, 1), row_weight(c, p, 2)};
+    float ub[3] = {0.f, 0.f, 0.f};
+    if (kRhs && p.active)
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            float r = c.resid[3 * p.si + ch];
+            if (c.ssim_s) r = fmaf(c.ssim_weight * c.ssim_d[3 * p.si + ch], c.ssim_s[3 * p.si + ch], r);
+            ub[ch] = p.w * r;
+        }
+    float* cot_base = c.cot + (long long)p.slot * c.G * kCotF;
     const int lane_end = p.active ? L.b + ncons : L.b;
     int warp_end = lane_end;
 #pragma unroll
@@ -452,11 +466,13 @@ __global__ void __launch_bounds__(kRasterBlock) k_gram(Ctx c) {
     for (int b = L.b; b < warp_end; b += 32) {
         const int n = stage_batch<3>(c, p.slot, L.ids, b, warp_end, s_rec, s_id);
         for (int j = 0; j < n; ++j) {
-            float v[32], v2[16];
+            float v[32], v2[16], vr[10];
 #pragma unroll
             for (int q = 0; q < 32; ++q) v[q] = 0.f;
 #pragma unroll
             for (int q = 0; q < 16; ++q) v2[q] = 0.f;
+#pragma unroll
+            for (int q = 0; q < 10; ++q) vr[q] = 0.f;
             bool contrib = false;
             if (b + j < lane_end) {
                 const float4 r0 = s_rec[j][0], r1 = s_rec[j][1];
@@ -502,6 +518,13 @@ __global__ void __launch_bounds__(kRasterBlock) k_gram(Ctx c) {
                     for (int k = 0; k < 32; ++k) v[k] = vals[k];
 #pragma unroll
                     for (int k = 0; k < 10; ++k) v2[k] = vals[32 + k];
+                    if (kRhs) {
+                        const float abar = ub[0] * h[0] + ub[1] * h[1] + ub[2] * h[2];
+#pragma unroll
+                        for (int f = 0; f < 6; ++f) vr[f] = abar * e[f];
+#pragma unroll
+                        for (int ch = 0; ch < 3; ++ch) vr[6 + ch] = ub[ch] * q;
+                    }
                     T *= 1.f - alpha;
                 }
             }
@@ -521,6 +544,17 @@ __global__ void __launch_bounds__(kRasterBlock) k_gram(Ctx c) {
                     warp_reduce_scatter<16>(v2);
                     const int idx = lane >> 1;
                     if (!(lane & 1) && idx < 10) atomicAdd(dst + 32 + idx, v2[0]);
+                }
+                if (kRhs) {
+                    float* cdst = cot_base + (long long)s_id[j] * kCotF;
+                    if (__popc(ball) <= kDirectMax) {
+                        if (contrib)
+#pragma unroll
+                            for (int q = 0; q < 9; ++q) atomicAdd(cdst + q, vr[q]);
+                    } else {
+                        const int ci = warp_reduce_scatter9(vr);
+                        if (!(lane & 1) && ci >= 0) atomicAdd(cdst + ci, vr[0]);
+                    }
                 }
             }
         }
@@ -841,7 +875,10 @@ void launch_raster_jtj(const Ctx& c, cudaStream_t st) {
     if (c.nwork > 0) LMRS_LAUNCH(k_jtj, raster_grid(c), kRasterBlock, 0, st, c);
 }
 void launch_raster_gram(const Ctx& c, cudaStream_t st) {
-    if (c.nwork > 0) LMRS_LAUNCH(k_gram, raster_grid(c), kRasterBlock, 0, st, c);
+    if (c.nwork > 0) LMRS_LAUNCH_AS("k_gram", k_gram<false>, raster_grid(c), kRasterBlock, 0, st, c);
+}
+void launch_raster_gram_rhs(const Ctx& c, cudaStream_t st) {
+    if (c.nwork > 0) LMRS_LAUNCH_AS("k_gram<rhs>", k_gram<true>, raster_grid(c), kRasterBlock, 0, st, c);
 }
 
 }  // namespace lmrs

@@ -427,6 +427,24 @@ lmrs_status do_jtj_diag(lmrs_scene* s) {
     return LMRS_OK;
 }
 
+// Right-hand side J^T W r -> b and diag(J^T W J) -> D of an LM step in one
+// walk of the compact lists (k_gram<rhs>), then their parameter-level
+// kernels: the same results as lmrs_rhs followed by do_jtj_diag.
+lmrs_status do_rhs_diag(lmrs_scene* s, float* b) {
+    TRY(need_render(s));
+    const size_t pairs = (size_t)s->nv * s->G;
+    TRY(ensure(s, s->gram, sizeof(float) * kGramF * pairs));
+    CK(s, cudaMemsetAsync(s->gram.p, 0, sizeof(float) * kGramF * pairs, s->st));
+    CK(s, cudaMemsetAsync(s->cot.p, 0, sizeof(float) * kCotF * pairs, s->st));
+    Ctx c = s->ctx();
+    launch_raster_gram_rhs(c, s->st);
+    launch_prep_diag(c, s->D.as<float>(), s->st);
+    launch_prep_vjp(c, b, nullptr, nullptr, false, s->st);
+    CHECK_LAUNCH(s);
+    s->have_D = true;
+    return LMRS_OK;
+}
+
 // (J^T W J + lambda damp) v -> out, device pointers.
 lmrs_status do_jtjv(lmrs_scene* s, const float* v, float* out) {
     Ctx c = s->ctx();
@@ -887,8 +905,7 @@ lmrs_status lm_step_iters(lmrs_scene* s, const int32_t* view_ids, int32_t n_view
     TimerScope ts_(s);
     TRY(lmrs_preprocess(s, view_ids, n_views, lm_step));
     TRY(lmrs_render(s, nullptr, nullptr));
-    TRY(lmrs_rhs(s, s->b.as<float>()));
-    TRY(do_jtj_diag(s));
+    TRY(do_rhs_diag(s, s->b.as<float>()));
     TRY(do_cg(s, s->b.as<float>(), s->x.as<float>(), iters));
     Ctx c = s->ctx();
     CK(s, cudaMemsetAsync(&c.sc->max_dc_bits, 0, sizeof(unsigned int), s->st));
@@ -1209,9 +1226,8 @@ void add_chunks(std::vector<int4>& out, int scene, long long n, int step) {
 lmrs_status scene_setup(lmrs_scene* s, const int32_t* views, int nv, long long step) {
     TRY(lmrs_preprocess(s, views, nv, step));
     TRY(lmrs_render(s, nullptr, nullptr));
-    TRY(lmrs_rhs(s, s->b.as<float>()));
     TimerScope ts_(s);
-    TRY(do_jtj_diag(s));
+    TRY(do_rhs_diag(s, s->b.as<float>()));
     return LMRS_OK;
 }
 

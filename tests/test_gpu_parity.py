@@ -231,6 +231,10 @@ def test_lm_step_and_step_size(case):
         pair.orc.set_params(p0)  # the operator at the pre-step point
         pair.orc.begin_step(case.views, step)
         assert_solution_close(pair, x.astype(np.float64), x_ref, D_ref)
+        # the step forms J^T W r and diag(J^T W J) in one walk of the lists:
+        # r0^T z0 = sum b^2 / M pins both at the operator bar
+        _, cg_ref = pair.orc.cg(pair.orc.rhs(), D_ref, 1)
+        assert abs(st.rz0 - cg_ref[0]) <= OP_TOL * abs(cg_ref[0])
         # the step size is exact given x (Sec. 4.5, App. D)
         eta_gpu_rule = pair.orc.step_size(x.astype(np.float64), step)
         assert st.eta == pytest.approx(eta_gpu_rule, rel=1e-12)
