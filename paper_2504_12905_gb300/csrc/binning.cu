@@ -631,14 +631,16 @@ __global__ void __launch_bounds__(kBinBlock) k_tile_count(Ctx c, int nchunk, con
     }
 }
 
-// One block per (slot, row); warp w owns the row's columns x = w + kColWarps q
-// (q < kColsPerWarp, in groups of kColWarps * kColsPerWarp columns) and walks
-// the row list once per group, kColRounds rounds of 32 entries at a time (the
-// loads of a batch go out together): per owned column one ballot of the
-// entries covering it, each covering lane writing at the column's running
-// offset + its rank.  Every column's list is appended in order.
-constexpr int kColWarps = 16;
-constexpr int kColsPerWarp = 8;
+// One block per (slot, row, group of kColGroup columns); warp w owns the
+// group's columns x = x0g + w + kColWarps q (q < kColsPerWarp) and walks the
+// row list once, kColRounds rounds of 32 entries at a time (the loads of a
+// batch go out together): per owned column one ballot of the entries
+// covering it, each covering lane writing at the column's running offset +
+// its rank.  Every column's list is appended in order.  Splitting a row over
+// column groups spreads its work over several SMs.
+constexpr int kColWarps = 8;
+constexpr int kColsPerWarp = 4;
+constexpr int kColGroup = kColWarps * kColsPerWarp;
 constexpr int kColRounds = 4;
 constexpr int kColBlock = kColWarps * kWarp;
 
@@ -649,40 +651,39 @@ __global__ void __launch_bounds__(kColBlock) k_tile_place(Ctx c, int nchunk, con
     const unsigned lt = (1u << lane) - 1u;
     const int nx = c.tiles_x;
     const int sr = blockIdx.x, slot = sr / c.tiles_y, row = sr - slot * c.tiles_y;
+    const int x0g = blockIdx.y * kColGroup;
+    if (x0g + wid >= nx) return;  // this warp owns no column of the row
     const long long t0 = (long long)slot * c.T + (long long)row * nx;
     unsigned b, e;
     row_range(c, nchunk, mat, rtotal, sr, b, e);
-    for (int x0g = 0; x0g < nx; x0g += kColWarps * kColsPerWarp) {
-        if (x0g + wid >= nx) continue;  // this warp owns no column of the group
-        // its columns inside the row: the ballots of the others are skipped
-        const int nq = min(kColsPerWarp, (nx - 1 - x0g - wid) / kColWarps + 1);
-        unsigned off[kColsPerWarp];
-        int col[kColsPerWarp];
+    // its columns inside the row: the ballots of the others are skipped
+    const int nq = min(kColsPerWarp, (nx - 1 - x0g - wid) / kColWarps + 1);
+    unsigned off[kColsPerWarp];
+    int col[kColsPerWarp];
 #pragma unroll
-        for (int q = 0; q < kColsPerWarp; ++q) {
-            col[q] = x0g + wid + kColWarps * q;
-            off[q] = col[q] < nx ? start[t0 + col[q]] : 0u;
+    for (int q = 0; q < kColsPerWarp; ++q) {
+        col[q] = x0g + wid + kColWarps * q;
+        off[q] = q < nq ? start[t0 + col[q]] : 0u;
+    }
+    for (unsigned base = b; base < e; base += 32 * kColRounds) {
+        unsigned long long v[kColRounds];
+#pragma unroll
+        for (int r = 0; r < kColRounds; ++r) {
+            const unsigned k = base + 32 * r + lane;
+            v[r] = k < e ? rl[k] : row_entry(0u, 1, 0);
         }
-        for (unsigned base = b; base < e; base += 32 * kColRounds) {
-            unsigned long long v[kColRounds];
 #pragma unroll
-            for (int r = 0; r < kColRounds; ++r) {
-                const unsigned k = base + 32 * r + lane;
-                v[r] = k < e ? rl[k] : row_entry(0u, 1, 0);
-            }
+        for (int r = 0; r < kColRounds; ++r) {
+            unsigned g;
+            int x0, x1;
+            row_entry_unpack(v[r], g, x0, x1);
 #pragma unroll
-            for (int r = 0; r < kColRounds; ++r) {
-                unsigned g;
-                int x0, x1;
-                row_entry_unpack(v[r], g, x0, x1);
-#pragma unroll
-                for (int q = 0; q < kColsPerWarp; ++q) {
-                    if (q >= nq) break;  // warp-uniform
-                    const bool in = x0 <= col[q] && col[q] <= x1;
-                    const unsigned m = __ballot_sync(kFull, in);
-                    if (in) c.ids[off[q] + __popc(m & lt)] = g;
-                    off[q] += __popc(m);
-                }
+            for (int q = 0; q < kColsPerWarp; ++q) {
+                if (q >= nq) break;  // warp-uniform
+                const bool in = x0 <= col[q] && col[q] <= x1;
+                const unsigned m = __ballot_sync(kFull, in);
+                if (in) c.ids[off[q] + __popc(m & lt)] = g;
+                off[q] += __popc(m);
             }
         }
     }
@@ -728,7 +729,8 @@ void bin_tiles(const Ctx& c, const unsigned* mat, const unsigned* rtotal, const 
     LMRS_LAUNCH(k_tile_count, rows, kBinBlock, smem, st, c, bin_chunks(c), mat, rtotal, rl, cnt);
     const long long nvt = (long long)c.nv * c.T;
     scan_rec<unsigned int>(cnt, nvt, etotal, static_cast<unsigned*>(tmp), st);
-    LMRS_LAUNCH(k_tile_place, rows, kColBlock, 0, st, c, bin_chunks(c), mat, rtotal, rl, cnt);
+    const dim3 pgrid(rows, (unsigned)((c.tiles_x + kColGroup - 1) / kColGroup));
+    LMRS_LAUNCH(k_tile_place, pgrid, kColBlock, 0, st, c, bin_chunks(c), mat, rtotal, rl, cnt);
     LMRS_LAUNCH(k_tile_ranges, (unsigned)((nvt + 255) / 256), 256, 0, st, c, cnt, etotal);
 }
 
