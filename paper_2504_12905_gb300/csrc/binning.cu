@@ -641,7 +641,7 @@ __global__ void __launch_bounds__(kBinBlock) k_tile_count(Ctx c, int nchunk, con
 constexpr int kColWarps = 8;
 constexpr int kColsPerWarp = 4;
 constexpr int kColGroup = kColWarps * kColsPerWarp;
-constexpr int kColRounds = 4;
+constexpr int kColRounds = 8;
 constexpr int kColBlock = kColWarps * kWarp;
 
 __global__ void __launch_bounds__(kColBlock) k_tile_place(Ctx c, int nchunk, const unsigned* mat,
