@@ -400,10 +400,10 @@ void launch_ranges(const Ctx& c, cudaStream_t st) {
 //          with that row's tile columns (row_span, possibly none): counts
 //          per (slot, row, chunk of kBinChunk pairs), an exclusive scan, then
 //          the placement;
-//   tiles: one block per (slot, row) walks that row's list in order and places
-//          each pair into the row's tiles it spans: counts per tile, an
-//          exclusive scan (the tile lists' starts), then the placement in
-//          chunks of the block's warps.
+//   tiles: one block per (slot, row) counts that row's list per tile, an
+//          exclusive scan gives the tile lists' starts, then one block per
+//          (slot, row, group of 32 tile columns) walks the row list in order
+//          and places each pair into the group's tiles it spans.
 // A placement ranks a lane's pair among the warp's 32 pairs covering the same
 // bin with a ballot, warps are ranked by their order in the chunk and chunks
 // by the scan, so every list keeps the order it is read in: the tile lists
@@ -429,19 +429,18 @@ __device__ __forceinline__ int warp_max_i(int v) {
     return v;
 }
 
-// One round of a warp: lane l holds the l-th of 32 consecutive items, which
-// may cover the bins [lo, hi] (lo > hi: none); covers(bin) decides each.  For
-// every bin of the union, m = the lanes covering it; count(bin, m) runs on
-// every lane (warp-uniform m), and place(bin, rank) on each covering lane,
-// rank = its position among them.
-template <class Covers, class Count, class Place>
-__device__ __forceinline__ void rank_round(int lo, int hi, Covers&& covers, Count&& count, Place&& place) {
+// One round of a warp: lane l holds the l-th of 32 consecutive items, covering
+// the bins [lo, hi] (lo > hi: none).  For every bin of the union, m = the
+// lanes covering it; count(bin, m) runs on every lane (warp-uniform m), and
+// place(bin, rank) on each covering lane, rank = its position among them.
+template <class Count, class Place>
+__device__ __forceinline__ void rank_round(int lo, int hi, Count&& count, Place&& place) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int ulo = warp_min_i(lo <= hi ? lo : 0x7fffffff);
     const int uhi = warp_max_i(lo <= hi ? hi : -1);
     for (int bin = ulo; bin <= uhi; ++bin) {
-        const bool in = lo <= bin && bin <= hi && covers(bin);
+        const bool in = lo <= bin && bin <= hi;
         const unsigned m = __ballot_sync(kFull, in);
         if (m == 0u) continue;
         if (in) place(bin, __popc(m & lt));
@@ -532,7 +531,6 @@ __global__ void __launch_bounds__(kBinBlock) k_row_place(Ctx c, int nchunk, cons
     const long long b = s0 + (long long)blockIdx.x * kBinChunk + (long long)wid * kBinRun;
     const long long e = min(b + kBinRun, s0 + c.G);
     unsigned short* mine = s_w + wid * ny;
-    const auto all = [](int) { return true; };
     const auto count = [&](int r, unsigned m) { if (lane == 0) mine[r] += (unsigned short)__popc(m); };
     // this warp's count per row
     for (long long base = b; base < e; base += 32) {
@@ -542,7 +540,7 @@ __global__ void __launch_bounds__(kBinBlock) k_row_place(Ctx c, int nchunk, cons
         pair_rect(c, s0, base + lane, e, g, rc, e0, e1);
         int lo, hi;
         band_rows(c, rc, e0, e1, lo, hi);
-        rank_round(lo, hi, all, count, [](int, int) {});
+        rank_round(lo, hi, count, [](int, int) {});
     }
     __syncthreads();
     // warps' offsets per row within the chunk, the chunk's base per row
@@ -570,7 +568,7 @@ __global__ void __launch_bounds__(kBinBlock) k_row_place(Ctx c, int nchunk, cons
         const int uhi = warp_max_i(lo <= hi ? hi : -1);
         for (int w0 = ulo; w0 <= uhi; w0 += kRowWin) {
             const int wl = max(lo, w0), wh = min(hi, w0 + kRowWin - 1);
-            rank_round(wl, wh, all, count,
+            rank_round(wl, wh, count,
                        [&](int r, int rank) { dst[(r - w0) * 32 + lane] = s_base[r] + mine[r] + rank; });
             __syncwarp();
             for (int r = wl; r <= wh; ++r) {
