@@ -44,12 +44,16 @@ def _tiles2(width, height):
     return Pair(sc, tgt, sample_frac=0.5, tile_w=2, tile_h=2), [2, 0]
 
 
-def _strip():
-    """An 8600 x 2 view of 1x1 tiles: 8600 tile columns exceed the binning's
-    shared counters, so the entry emission + tile sort builds the lists."""
-    rng = np.random.default_rng(31)
-    sc = syn.tiny_scene(seed=7, n_gauss=1500, width=8600, height=2, sh_degree=0)
-    tgt = syn.noise_targets(rng, len(sc.cams), 2, 8600)
+def _strip(width, height, seed):
+    """A width x height view of 1x1 tiles, every pixel sampled; the 60 degree
+    field of view spans the long side."""
+    rng = np.random.default_rng(seed)
+    sc = syn.tiny_scene(seed=7, n_gauss=1500, width=width, height=height, sh_degree=0)
+    if height > width:
+        f = height / (2.0 * np.tan(np.radians(30.0)))
+        sc.cams["fx"] = f
+        sc.cams["fy"] = f
+    tgt = syn.noise_targets(rng, len(sc.cams), height, width)
     return Pair(sc, tgt, sample_frac=1.0, tile_w=1, tile_h=1), [0, 2]
 
 
@@ -71,7 +75,12 @@ CASES = {
     "ragged_tile8x32_spt": lambda: _ragged(0, 1.0, tile_w=8, tile_h=32, samples_per_tile=40, weight_mode=1),
     "tiles2x2_direct_8100": lambda: _tiles2(180, 180),
     "tiles2x2_8500": lambda: _tiles2(200, 170),
-    "strip_emit_8600": lambda: _strip(),
+    # 8,600 tile columns: 269 column groups of the two-level binning
+    "strip_wide_8600": lambda: _strip(8600, 2, 31),
+    # 8,700 tile rows: the row placement's shared counters would pass 200 KB,
+    # so the entry emission + tile sort builds the lists (217,724 entries in
+    # 26,462 tiles, up to 18 in one)
+    "strip_tall_emit_8700": lambda: _strip(2, 8700, 37),
 }
 
 
@@ -80,6 +89,21 @@ def case(request):
     pair, views = CASES[request.param]()
     pair.begin(views, step=2)
     return pair
+
+
+@pytest.mark.parametrize("name,emits", [("tiny", False), ("strip_wide_8600", False), ("strip_tall_emit_8700", True)])
+def test_list_builder_of_the_case(name, emits):
+    """Which of the two list builders a case runs, from the launches of its
+    preprocessing: the two-level binning (k_tile_place) or the entry
+    emission + tile sort (k_emit)."""
+    pair, views = CASES[name]()
+    pair.lmrs.lmrs_set_timing(pair.gpu.h, True)
+    pair.gpu.preprocess(views, 2)
+    names = set(pair.lmrs.lmrs_get_timing(pair.gpu.h))
+    pair.lmrs.lmrs_set_timing(pair.gpu.h, False)
+    pair.gpu.close()
+    assert ("k_emit" in names) == emits, sorted(names)
+    assert ("k_tile_place" in names) == (not emits), sorted(names)
 
 
 def test_samples_bit_exact(case):
