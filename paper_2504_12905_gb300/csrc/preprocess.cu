@@ -13,13 +13,14 @@
 //   k_prep_vjp      the transposed map from the per-pair 2D cotangents to the
 //                   3D parameters (second launch of the J^T v kernel, App. A),
 //                   plus the damping of Eq. 8 and p^T A p in FP64
-//   k_prep_diag     diag(J^T W J) from per-pair 9x9 Gram blocks and the
-//                   Jacobian columns (App. A "Diag")
+//   k_prep_diag     diag(J^T W J): the per-pair row sums of k_diag summed over
+//                   the views (App. A "Diag")
 // Kernels are instantiated per SH degree (0..3) so coefficient arrays live
 // in registers.
 #include <cmath>
 
 #include "common.cuh"
+#include "jac.cuh"
 #include "reduce.cuh"
 
 namespace lmrs {
@@ -44,11 +45,6 @@ void set_sh_constants() {
     };
     cudaMemcpyToSymbol(c_sh, h, sizeof(h));
 }
-
-template <int DEG>
-struct Sh {
-    static constexpr int K = (DEG + 1) * (DEG + 1);
-};
 
 // Basis values, index l^2 + l + m.
 template <int DEG>
@@ -460,26 +456,10 @@ __global__ void k_sample(Ctx c, long long lm_step, unsigned long long seed) {
 }
 
 // ---------------------------------------------------------------------------
-// Per-pair Jacobian cache.  Within one LM step the map from a Gaussian's
-// parameter tangent to the tangent of its 9 screen-space features in one view
-// is linear and fixed, so it is formed once per step (from the verified
-// tangent code on unit tangents) and the derivative kernels of every PCG
-// iteration read it instead of redoing the projection and SH derivatives.
-// Layout (floats; jac_f4(DEG) float4 planes of nv*G pairs):
-//   [0, 6)    d(mu_x, mu_y) / dX                     (row-major 2 x 3)
-//   [6, 36)   d(A, B, C) / d(X, log-scale, q)        (row-major 3 x 10)
-//   [36]      d o / d logit = o (1 - o)
-//   [37]      bit ch set: colour channel ch not clamped
-//   [38, 47)  d colour / dX through the view direction (row-major 3 x 3, DEG > 0)
-//   [47, 47 + K)  SH basis Y_k(view direction)       (DEG > 0; Y_0 only for DEG 0)
+// Per-pair Jacobian cache (layout in jac.cuh), formed from the verified
+// tangent code on unit tangents: column j is the tangent of the 9 features
+// along geometric parameter j.
 // ---------------------------------------------------------------------------
-template <int DEG>
-struct Jac {
-    static constexpr int F4 = jac_f4(DEG);
-    static constexpr int N = 4 * F4;
-    static constexpr int kMu = 0, kCon = 6, kOp = 36, kMask = 37, kGx = 38;
-};
-
 template <int DEG>
 __device__ __forceinline__ void pair_jacobian(const Prim& P, const CamDev& cam, const float* sh, float* J) {
     using L = Jac<DEG>;
@@ -515,29 +495,6 @@ __device__ __forceinline__ void pair_jacobian(const Prim& P, const CamDev& cam, 
     for (int ch = 0; ch < 3; ++ch)
         if (!P.clamped[ch]) bits |= 1u << ch;
     J[L::kMask] = __uint_as_float(bits);
-}
-
-// Blocked layout of the cache: pairs indexed slot * Gp + g (Gp = G rounded
-// up to 32), blocks of 32 consecutive pairs, each block holding its F4
-// planes one after the other ([block][q][32] float4).  The Jacobians of 32
-// consecutive Gaussians in one view are one contiguous run of F4 x 512 B.
-__device__ __forceinline__ long long jac_block(const Ctx& c, int slot, int g) {
-    return ((long long)slot * ((c.G + 31) & ~31) + g) >> 5;
-}
-
-template <int DEG>
-__device__ __forceinline__ long long jac_idx(const Ctx& c, int slot, int g, int q) {
-    return (jac_block(c, slot, g) * Jac<DEG>::F4 + q) * 32 + (g & 31);
-}
-
-template <int DEG>
-__device__ __forceinline__ void load_jac(const Ctx& c, int slot, int g, float* J) {
-    const float4* base = c.pjac + jac_block(c, slot, g) * Jac<DEG>::F4 * 32 + (g & 31);
-#pragma unroll
-    for (int q = 0; q < Jac<DEG>::F4; ++q) {
-        const float4 v = base[q * 32];
-        J[4 * q] = v.x; J[4 * q + 1] = v.y; J[4 * q + 2] = v.z; J[4 * q + 3] = v.w;
-    }
 }
 
 // SH basis values Y_k of the pair's view direction, recomputed from the
@@ -882,29 +839,10 @@ __global__ void __launch_bounds__(kBatchBlock) kb_prep_vjp(BatchTables t, int it
     }
 }
 
-// diag(J^T W J) for Gaussian g from the Gram blocks of its visible views.
-// Gram layout (42 of kGramF floats): [0,21) upper triangle of the 6x6
-// geometric block (mu_x, mu_y, A, B, C, o) row-major; [21,39) geometric x
-// colour, index 21 + 3 f + ch; [39,42) the colour diagonal per channel (the
-// rows of one sample carry per-channel weights under the SSIM term).
-__device__ __forceinline__ float gram_quad(const float* gm, const float a[9]) {
-    float v = 0.f;
-    int idx = 0;
-#pragma unroll
-    for (int f = 0; f < 6; ++f)
-#pragma unroll
-        for (int h = f; h < 6; ++h) {
-            const float m = gm[idx++];
-            v += (f == h ? 1.f : 2.f) * m * a[f] * a[h];
-        }
-#pragma unroll
-    for (int f = 0; f < 6; ++f)
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) v += 2.f * gm[21 + 3 * f + ch] * a[f] * a[6 + ch];
-    v += gm[39] * a[6] * a[6] + gm[40] * a[7] * a[7] + gm[41] * a[8] * a[8];
-    return v;
-}
-
+// diag(J^T W J) for Gaussian g: the sum over its visible views of the
+// pair slots k_diag filled (the 11 geometric entries directly; SH
+// coefficient (k, ch) moves only colour ch, by Y_k, so its entry is
+// Y_k^2 sum w_ch q^2 where channel ch is not clamped).
 template <int DEG>
 __global__ void __launch_bounds__(kPrepBlock) k_prep_diag(Ctx c, float* D) {
     using L = Jac<DEG>;
@@ -922,49 +860,26 @@ __global__ void __launch_bounds__(kPrepBlock) k_prep_diag(Ctx c, float* D) {
     if (DEG > 0) load_mean(c.params, g, X);
     for (int slot = 0; slot < c.nv; ++slot) {
         const long long i = (long long)slot * c.G + g;
-        // loads before the visibility test, a culled pair's (stale) cache
-        // values replaced by zeros
-        float J[L::N];
-        load_jac<DEG>(c, slot, g, J);
-        float gm[kGramF];
-        const float4* gsrc = reinterpret_cast<const float4*>(c.gram + i * kGramF);
-#pragma unroll
-        for (int k = 0; k < kGramF / 4; ++k) {
-            const float4 q = gsrc[k];
-            gm[4 * k] = q.x; gm[4 * k + 1] = q.y; gm[4 * k + 2] = q.z; gm[4 * k + 3] = q.w;
-        }
+        // loads before the visibility test; a culled pair's (stale) slot and
+        // mask are replaced by zeros
+        const float4* src = reinterpret_cast<const float4*>(c.dslot + i * kDiagF);
+        const float4 s0 = src[0], s1 = src[1], s2 = src[2], s3 = src[3];
+        static_assert(L::kMask % 4 == 1, "the clamp mask is the .y of its plane");
+        const float maskf = c.pjac[jac_idx<DEG>(c, slot, g, L::kMask / 4)].y;
         const int4 rc = c.rect[i];
         const bool vis = rc.x <= rc.y;
+        const float v[14] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w, s2.x, s2.y, s2.z, s2.w, s3.x, s3.y};
 #pragma unroll
-        for (int k = 0; k < L::N; ++k) J[k] = vis ? J[k] : 0.f;
-#pragma unroll
-        for (int k = 0; k < kGramF; ++k) gm[k] = vis ? gm[k] : 0.f;
+        for (int j = 0; j < 11; ++j) dgeo[j] += vis ? v[j] : 0.f;
+        const unsigned bits = vis ? __float_as_uint(maskf) : 0u;
         float Y[K];
         pair_Y<DEG>(c.cams[c.views[slot]], X, Y);
-        // geometric parameter j: the feature tangent is column j of the Jacobian
-#pragma unroll
-        for (int j = 0; j < 11; ++j) {
-            float a[9];
-            a[0] = j < 3 ? J[L::kMu + j] : 0.f;
-            a[1] = j < 3 ? J[L::kMu + 3 + j] : 0.f;
-#pragma unroll
-            for (int r = 0; r < 3; ++r) a[2 + r] = j < 10 ? J[L::kCon + 10 * r + j] : 0.f;
-            a[5] = j == 10 ? J[L::kOp] : 0.f;
-#pragma unroll
-            for (int ch = 0; ch < 3; ++ch) a[6 + ch] = (DEG > 0 && j < 3) ? J[L::kGx + 3 * ch + j] : 0.f;
-            // exactly a sum of squares (the Gram block is a sum of outer
-            // products); in FP32 a rank-deficient block (a pair hit by one
-            // sample) can round the form below zero
-            dgeo[j] += fmaxf(gram_quad(gm, a), 0.f);
-        }
-        // SH coefficient (k, ch) moves only colour ch, by Y_k
-        const unsigned bits = __float_as_uint(J[L::kMask]);
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            const float y = Y[k];
+            const float y2 = Y[k] * Y[k];
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch)
-                if ((bits >> ch) & 1u) dsh[3 * k + ch] += gm[39 + ch] * y * y;
+                if ((bits >> ch) & 1u) dsh[3 * k + ch] = fmaf(y2, v[11 + ch], dsh[3 * k + ch]);
         }
     }
     const long long G = c.G;

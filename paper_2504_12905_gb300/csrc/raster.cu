@@ -15,26 +15,20 @@
 //                  kernel, first launch) using the cached final colour and
 //                  stopping position
 //   k_jtj          fused: JVP pass then VJP pass of w * (J v) per work item
-//   k_gram         per-pair Gram blocks of the per-sample feature gradients
-//                  (App. A, Diag kernel; completed by k_prep_diag)
+//   k_diag         diag(J^T W J) row by row into per-pair slots (App. A, Diag
+//                  kernel; completed by k_prep_diag), optionally with the
+//                  right-hand side's back-scatter in the same walk
 //   k_ssim         the diagonal SSIM term at every sample (from full frames)
-// k_vjp, k_jtj and k_gram walk the compact lists.  Back-scatter: per
-// Gaussian, the lanes' contributions are summed with a warp reduce-scatter
-// and one lane per value issues a single atomic add into the per-(view,
-// Gaussian) slot; when at most four lanes contribute, they add their values
-// directly instead.
+// k_vjp, k_jtj and k_diag walk the compact lists.  Back-scatter: the lanes
+// first write per-(entry, sample) values to shared memory in list order, then
+// the lanes take the entries and sum over the samples, so each (work item,
+// list entry) adds its cotangents with a few vector atomics and no warp
+// reduction (backward_pass).
 #include "common.cuh"
+#include "jac.cuh"
 #include "reduce.cuh"
 
 namespace lmrs {
-
-// Back-scatter of one list entry: when at most this many lanes contribute,
-// each issues its own atomics and the warp reduce-scatter is skipped (the
-// reduce costs ~50 instructions; more contributors per address make the
-// atomics contend).  Measured on the 200k and 1.5M workloads: 4 and 8 equal,
-// 16 clearly slower.
-constexpr int kDirectMax = 4;      // 9 cotangents per contributing lane
-constexpr int kGramDirectMax = 4;  // 42 Gram entries per contributing lane
 
 constexpr int kRasterWarps = 4;
 constexpr int kRasterBlock = kRasterWarps * kWarp;
@@ -106,9 +100,10 @@ __device__ __forceinline__ List tile_list(const Ctx& c, const Pix& p) {
     return L;
 }
 
-template <int NF4>
+template <int NF4, int W>
 __device__ __forceinline__ int stage_batch(const Ctx& c, int slot, const unsigned* ids, int b, int end,
-                                           float4 (*s_rec)[kRecF4], unsigned* s_id) {
+                                           float4 (*s_rec)[W], unsigned* s_id) {
+    static_assert(NF4 <= W, "staged row too narrow");
     const int lane = threadIdx.x & 31;
     const int k = b + lane;
     if (k < end) {
@@ -220,8 +215,44 @@ __device__ __forceinline__ void forward_pass(const Ctx& c, const Pix& p, List L,
 // cotangents of every contributing Gaussian (reverse mode through Eq. 4 with
 // the final colour Cf known: dC/dalpha_n = T_n c_n - (Cf - C_<=n)/(1 - alpha_n)).
 // Lane stops after its first ncons entries of the list.
-__device__ __forceinline__ void backward_pass(const Ctx& c, const Pix& p, List L, float4 (*s_rec)[kRecF4],
-                                              unsigned* s_id, const float ub[3], const float Cf[3], int ncons) {
+//
+// Two phases per kBwdE staged entries, so that no warp reduction is needed:
+//   A  lane = sample, in list order: alpha, T and the running sum give, per
+//      entry, pbar = <ub, dC/dalpha> raw (0 where alpha is clamped: alpha
+//      then does not move with the features) and wgt = alpha T, written to
+//      pw[entry][lane];
+//   B  lane = (entry e, half hh of the samples): the lane sums its entry's
+//      moments over its samples (dx = mu_x - pixel x, dy likewise)
+//        Mx = sum pbar dx, My = sum pbar dy, Mxx = sum pbar dx^2,
+//        Mxy = sum pbar dx dy, Myy = sum pbar dy^2, M5 = sum pbar,
+//        Mc_ch = sum ub_ch wgt,
+//      the two halves are added with one shuffle per moment, and with the
+//      entry's conic (A, B, C) and opacity o the cotangents are
+//        mu: -(A Mx + B My), -(B Mx + C My);  conic: -Mxx/2, -Mxy, -Myy/2;
+//        o: M5 / o (pbar / o = <ub, dC/dalpha> e^power);  colour: Mc,
+//      added with two 4-wide and one scalar atomic.
+constexpr int kBwdE = 16;  // entries per phase; lanes e and e + 16 share entry e
+
+struct BwdSmem {
+    float2 pw[kBwdE][33];  // (pbar, wgt) per (entry, sample); row stride 33 keeps phase B's column reads conflict-free
+    float4 pix[32];        // per sample: pixel centre x, y, ub_0, ub_1
+    float ub2[32];
+};
+
+// One staged batch per warp, plus the back-scatter's exchange area.
+struct WarpSmem {
+    float4 rec[32][kRecF4];
+    unsigned id[32];
+    BwdSmem bw;
+};
+
+__device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float c, float d) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
+                 : "memory");
+}
+
+__device__ __forceinline__ void backward_pass(const Ctx& c, const Pix& p, List L, WarpSmem& sm, const float ub[3],
+                                              const float Cf[3], int ncons) {
     const int lane = threadIdx.x & 31;
     const float S_tot = ub[0] * Cf[0] + ub[1] * Cf[1] + ub[2] * Cf[2];
     float s = 0.f, T = 1.f;
@@ -229,58 +260,76 @@ __device__ __forceinline__ void backward_pass(const Ctx& c, const Pix& p, List L
     int warp_end = lane_end;
 #pragma unroll
     for (int m = 16; m >= 1; m >>= 1) warp_end = max(warp_end, __shfl_xor_sync(kFull, warp_end, m));
+    // the live samples are lanes [0, nact)
+    const int nact = __popc(__ballot_sync(kFull, p.active));
+    sm.bw.pix[lane] = make_float4(p.pcx, p.pcy, ub[0], ub[1]);
+    sm.bw.ub2[lane] = ub[2];
     float* cot_base = c.cot + (long long)p.slot * c.G * kCotF;
+    const int e = lane & (kBwdE - 1), hh = lane >> 4;
     for (int b = L.b; b < warp_end; b += 32) {
-        const int n = stage_batch<3>(c, p.slot, L.ids, b, warp_end, s_rec, s_id);
-        for (int j = 0; j < n; ++j) {
-            float v[10];
-#pragma unroll
-            for (int q = 0; q < 10; ++q) v[q] = 0.f;
-            bool contrib = false;
-            if (b + j < lane_end) {
-                const float4 r0 = s_rec[j][0], r1 = s_rec[j][1];
-                const float dx = r0.x - p.pcx, dy = r0.y - p.pcy;
-                const float power = -0.5f * (r0.z * dx * dx + r1.x * dy * dy) - r0.w * dx * dy;
-                const float gval = __expf(power);
-                const float raw = r1.y * gval;
-                const float alpha = fminf(kAlphaMax, raw);
-                if (alpha >= kAlphaMin) {
-                    contrib = true;
-                    const float col2 = s_rec[j][2].x;
-                    const float ucol = ub[0] * r1.z + ub[1] * r1.w + ub[2] * col2;
-                    const float wgt = alpha * T;
-                    s += ucol * wgt;
-                    const float abar = T * ucol - __fdividef(S_tot - s, 1.f - alpha);  // 1 - alpha >= 0.01
-                    v[6] = ub[0] * wgt;
-                    v[7] = ub[1] * wgt;
-                    v[8] = ub[2] * wgt;
-                    if (raw <= kAlphaMax) {
-                        const float pbar = abar * raw;
-                        v[0] = -pbar * (r0.z * dx + r0.w * dy);
-                        v[1] = -pbar * (r0.w * dx + r1.x * dy);
-                        v[2] = -0.5f * pbar * dx * dx;
-                        v[3] = -pbar * dx * dy;
-                        v[4] = -0.5f * pbar * dy * dy;
-                        v[5] = abar * gval;
+        const int n = stage_batch<3>(c, p.slot, L.ids, b, warp_end, sm.rec, sm.id);
+        for (int h0 = 0; h0 < n; h0 += kBwdE) {
+            const int m = min(kBwdE, n - h0);
+            // phase A
+            for (int jj = 0; jj < m; ++jj) {
+                const int j = h0 + jj;
+                float pb = 0.f, wt = 0.f;
+                if (b + j < lane_end) {
+                    const float4 r0 = sm.rec[j][0], r1 = sm.rec[j][1];
+                    const float dx = r0.x - p.pcx, dy = r0.y - p.pcy;
+                    const float power = -0.5f * (r0.z * dx * dx + r1.x * dy * dy) - r0.w * dx * dy;
+                    const float gval = __expf(power);
+                    const float raw = r1.y * gval;
+                    const float alpha = fminf(kAlphaMax, raw);
+                    if (alpha >= kAlphaMin) {
+                        const float col2 = sm.rec[j][2].x;
+                        const float ucol = ub[0] * r1.z + ub[1] * r1.w + ub[2] * col2;
+                        wt = alpha * T;
+                        s += ucol * wt;
+                        const float abar = T * ucol - __fdividef(S_tot - s, 1.f - alpha);  // 1 - alpha >= 0.01
+                        pb = raw <= kAlphaMax ? abar * raw : 0.f;
+                        T *= 1.f - alpha;
                     }
-                    T *= 1.f - alpha;
+                }
+                sm.bw.pw[jj][lane] = make_float2(pb, wt);
+            }
+            __syncwarp();
+            // phase B
+            float M[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            float M5 = 0.f;
+            const int j = h0 + e;
+            if (e < m) {
+                const float mx = sm.rec[j][0].x, my = sm.rec[j][0].y;
+                for (int i = hh; i < nact; i += 2) {
+                    const float2 q = sm.bw.pw[e][i];
+                    const float4 px = sm.bw.pix[i];
+                    const float u2 = sm.bw.ub2[i];
+                    const float dx = mx - px.x, dy = my - px.y;
+                    const float pdx = q.x * dx, pdy = q.x * dy;
+                    M[0] += pdx;
+                    M[1] += pdy;
+                    M[2] = fmaf(pdx, dx, M[2]);
+                    M[3] = fmaf(pdx, dy, M[3]);
+                    M[4] = fmaf(pdy, dy, M[4]);
+                    M5 += q.x;
+                    M[6] = fmaf(px.z, q.y, M[6]);
+                    M[7] = fmaf(px.w, q.y, M[7]);
+                    M[8] = fmaf(u2, q.y, M[8]);
                 }
             }
-            const unsigned ball = __ballot_sync(kFull, contrib);
-            if (ball) {
-                if (__popc(ball) <= kDirectMax) {
-                    if (contrib) {
-                        float* dst = cot_base + (long long)s_id[j] * kCotF;
 #pragma unroll
-                        for (int q = 0; q < 9; ++q) atomicAdd(dst + q, v[q]);
-                    }
-                } else {
-                    const int idx = warp_reduce_scatter9(v);
-                    if (!(lane & 1) && idx >= 0) atomicAdd(cot_base + (long long)s_id[j] * kCotF + idx, v[0]);
-                }
+            for (int k = 0; k < 9; ++k)
+                if (k != 5) M[k] += __shfl_xor_sync(kFull, M[k], 16);
+            M5 += __shfl_xor_sync(kFull, M5, 16);
+            if (hh == 0 && e < m) {
+                const float4 r0 = sm.rec[j][0], r1 = sm.rec[j][1];
+                float* dst = cot_base + (long long)sm.id[j] * kCotF;
+                red_add_v4(dst, -(r0.z * M[0] + r0.w * M[1]), -(r0.w * M[0] + r1.x * M[1]), -0.5f * M[2], -M[3]);
+                red_add_v4(dst + 4, -0.5f * M[4], __fdividef(M5, r1.y), M[6], M[7]);
+                atomicAdd(dst + 8, M[8]);
             }
+            __syncwarp();
         }
-        __syncwarp();
     }
 }
 
@@ -355,6 +404,7 @@ __global__ void __launch_bounds__(kRasterBlock) k_fwd_samples(Ctx c) {
         atomicAdd(&c.sc->loss_num, num);
         atomicAdd(&c.sc->loss_den, den);
         atomicAdd(&c.sc->n_eval, ne);
+        atomicAdd(&c.sc->n_walk, (unsigned long long)*len_out);
     }
 }
 
@@ -370,7 +420,12 @@ __global__ void __launch_bounds__(kRasterBlock) k_jvp(Ctx c, float* u) {
 }
 
 __global__ void __launch_bounds__(kRasterBlock) k_vjp(Ctx c, const float* u) {
-    LMRS_RASTER_PROLOGUE
+    __shared__ WarpSmem s_warp[kRasterWarps];
+    const int wid = threadIdx.x >> 5;
+    const int item = blockIdx.x * kRasterWarps + wid;
+    if (item >= c.nwork) return;
+    Pix p;
+    setup_item(c, item, p);
     float ub[3] = {0.f, 0.f, 0.f}, Cf[3] = {0.f, 0.f, 0.f};
     int ncons = 0;
     if (p.active) {
@@ -387,40 +442,39 @@ __global__ void __launch_bounds__(kRasterBlock) k_vjp(Ctx c, const float* u) {
             }
         }
     }
-    backward_pass(c, p, compact_list(c, p), s_rec, s_id, ub, Cf, ncons);
+    backward_pass(c, p, compact_list(c, p), s_warp[wid], ub, Cf, ncons);
 }
 
-__device__ __forceinline__ void jtj_item(const Ctx& c, int item, float4 (*s_rec)[kRecF4], unsigned* s_id) {
+__device__ __forceinline__ void jtj_item(const Ctx& c, int item, WarpSmem& sm) {
     Pix p;
     setup_item(c, item, p);
     const List L = compact_list(c, p);
     float C[3], T, dC[3];
     int ncons;
-    forward_pass<true, false>(c, p, L, s_rec, s_id, C, T, dC, ncons);
+    forward_pass<true, false>(c, p, L, sm.rec, sm.id, C, T, dC, ncons);
     const float ub[3] = {row_weight(c, p, 0) * dC[0], row_weight(c, p, 1) * dC[1], row_weight(c, p, 2) * dC[2]};
-    backward_pass(c, p, L, s_rec, s_id, ub, C, ncons);
+    __syncwarp();
+    backward_pass(c, p, L, sm, ub, C, ncons);
 }
 
 __global__ void __launch_bounds__(kRasterBlock) k_jtj(Ctx c) {
-    __shared__ float4 s_rec_all[kRasterWarps][32][kRecF4];
-    __shared__ unsigned s_id_all[kRasterWarps][32];
+    __shared__ WarpSmem s_warp[kRasterWarps];
     const int wid = threadIdx.x >> 5;
     const int item = blockIdx.x * kRasterWarps + wid;
-    if (item < c.nwork) jtj_item(c, item, s_rec_all[wid], s_id_all[wid]);
+    if (item < c.nwork) jtj_item(c, item, s_warp[wid]);
 }
 
 // The same for every scene of a batch: chunks of at most kRasterWarps work
 // items of one scene, one item per warp.
 __global__ void __launch_bounds__(kRasterBlock) kb_jtj(BatchTables t) {
     static_assert(kRasterBlock == kBatchBlock, "one warp per work item of a chunk");
-    __shared__ float4 s_rec_all[kRasterWarps][32][kRecF4];
-    __shared__ unsigned s_id_all[kRasterWarps][32];
+    __shared__ WarpSmem s_warp[kRasterWarps];
     const int wid = threadIdx.x >> 5;
     const int n = t.counts[2];
     for (int k = blockIdx.x; k < n; k += gridDim.x) {
         const int4 ch = t.wchunks[k];
         const int item = ch.y + wid;
-        if (item < ch.z) jtj_item(t.ctxs[ch.x], item, s_rec_all[wid], s_id_all[wid]);
+        if (item < ch.z) jtj_item(t.ctxs[ch.x], item, s_warp[wid]);
         __syncwarp();
     }
 }
@@ -429,25 +483,49 @@ void launch_b_jtj(const BatchTables& t, int grid, cudaStream_t st) {
     LMRS_LAUNCH(kb_jtj, grid, kRasterBlock, 0, st, t);
 }
 
-// Gram blocks: per contributing (sample, Gaussian), with e = d alpha /
-// d(mu_x, mu_y, A, B, C, o), h_ch = d C_ch / d alpha, q = alpha T and w_ch
-// the weight of the sample's channel-ch row:
-//   [0,21)   (sum_ch w_ch h_ch^2) e e^T   (upper triangle, row-major)
-//   [21,39)  w_ch q h_ch e_f              (index 21 + 3 f + ch)
-//   [39,42)  w_ch q^2
-// With kRhs the same walk also back-scatters the right-hand side J^T W r
-// (plus the SSIM rows' ssim_weight w d s): for the cotangent ub of the
-// sample's colour, d<ub, C>/d alpha = ub . h, so the 9 feature cotangents
-// are (ub . h) e and ub q -- those of k_vjp, without a second walk.
-template <bool kRhs>
-__global__ void __launch_bounds__(kRasterBlock) k_gram(Ctx c) {
-    LMRS_RASTER_PROLOGUE
+// diag(J^T W J) row by row (App. A, Diag kernel), optionally with the right-
+// hand side J^T W r in the same walk.  Per contributing (sample, Gaussian)
+// and channel, the row of J restricted to the Gaussian's geometric parameter
+// k is
+//   hr_ch (et . a_k) + q acol_ch,k
+// with q = alpha T, h_ch = dC_ch/dalpha, hr_ch = h_ch raw (0 where alpha is
+// clamped), et = d power / d(mu_x, mu_y, A, B, C) (= -(A dx + B dy),
+// -(B dx + C dy), -dx^2/2, -dx dy, -dy^2/2), a_k column k of the pair's
+// Jacobian cache and acol its colour-through-direction part (DEG > 0).  Its
+// square, weighted by the channel's row weight w_ch, is added to the pair's
+// slot: every term is non-negative, so each entry of D keeps its own relative
+// accuracy however small it is next to the rest of its Gaussian's block.
+// Slot (kDiagF floats): [0, 10) the 10 parameters X, log-scale, q; [10] the
+// opacity logit, (1 - o)^2 sum_ch w_ch hr_ch^2 (dalpha/dlogit = raw (1 - o));
+// [11, 14) sum w_ch q^2 per channel, which k_prep_diag turns into the SH
+// entries (colour ch moves by Y_k per unit of coefficient (k, ch)).
+// Two phases per kBwdE staged entries as in backward_pass: A (lane = sample)
+// writes (q, hr_0, hr_1, hr_2); B (lane = (entry, half of the samples)) sums
+// the rows over the samples with the entry's Jacobian in registers, and the
+// halves are added with one shuffle per value.
+struct DiagSmem {
+    float4 rec[32][kPrimF4];
+    unsigned id[32];
+    float4 qh[kBwdE][33];  // (q, hr_0, hr_1, hr_2) per (entry, sample)
+    float4 pix0[32];       // pixel centre x, y, w_0, w_1
+    float4 pix1[32];       // w_2, ub_0, ub_1, ub_2 (right-hand side cotangent)
+};
+
+template <int DEG, bool kRhs>
+__global__ void __launch_bounds__(kRasterBlock) k_diag(Ctx c) {
+    using LJ = Jac<DEG>;
+    __shared__ DiagSmem s_warp[kRasterWarps];
+    const int wid = threadIdx.x >> 5;
+    const int item = blockIdx.x * kRasterWarps + wid;
+    if (item >= c.nwork) return;
+    DiagSmem& sm = s_warp[wid];
+    Pix p;
+    setup_item(c, item, p);
     const List L = compact_list(c, p);
     const int lane = threadIdx.x & 31;
     float Cf[3] = {0.f, 0.f, 0.f};
     int ncons = 0;
     if (p.active) load_cache(c, p.si, Cf, ncons);
-    const float wch[3] = {row_weight(c, p, 0), row_weight(c, p, 1), row_weight(c, p, 2)};
     float ub[3] = {0.f, 0.f, 0.f};
     if (kRhs && p.active)
 #pragma unroll
@@ -456,109 +534,134 @@ __global__ void __launch_bounds__(kRasterBlock) k_gram(Ctx c) {
             if (c.ssim_s) r = fmaf(c.ssim_weight * c.ssim_d[3 * p.si + ch], c.ssim_s[3 * p.si + ch], r);
             ub[ch] = p.w * r;
         }
-    float* cot_base = c.cot + (long long)p.slot * c.G * kCotF;
+    sm.pix0[lane] = make_float4(p.pcx, p.pcy, row_weight(c, p, 0), row_weight(c, p, 1));
+    sm.pix1[lane] = make_float4(row_weight(c, p, 2), ub[0], ub[1], ub[2]);
+    const int nact = __popc(__ballot_sync(kFull, p.active));
     const int lane_end = p.active ? L.b + ncons : L.b;
     int warp_end = lane_end;
 #pragma unroll
     for (int m = 16; m >= 1; m >>= 1) warp_end = max(warp_end, __shfl_xor_sync(kFull, warp_end, m));
     float acc[3] = {0.f, 0.f, 0.f}, T = 1.f;
-    float* gbase = c.gram + (long long)p.slot * c.G * kGramF;
+    float* dbase = c.dslot + (long long)p.slot * c.G * kDiagF;
+    float* cbase = c.cot + (long long)p.slot * c.G * kCotF;
+    const int e = lane & (kBwdE - 1), hh = lane >> 4;
     for (int b = L.b; b < warp_end; b += 32) {
-        const int n = stage_batch<3>(c, p.slot, L.ids, b, warp_end, s_rec, s_id);
-        for (int j = 0; j < n; ++j) {
-            float v[32], v2[16], vr[10];
+        const int n = stage_batch<3>(c, p.slot, L.ids, b, warp_end, sm.rec, sm.id);
+        for (int h0 = 0; h0 < n; h0 += kBwdE) {
+            const int m = min(kBwdE, n - h0);
+            // phase A
+            for (int jj = 0; jj < m; ++jj) {
+                const int j = h0 + jj;
+                float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (b + j < lane_end) {
+                    const float4 r0 = sm.rec[j][0], r1 = sm.rec[j][1];
+                    const float dx = r0.x - p.pcx, dy = r0.y - p.pcy;
+                    const float power = -0.5f * (r0.z * dx * dx + r1.x * dy * dy) - r0.w * dx * dy;
+                    const float gval = __expf(power);
+                    const float raw = r1.y * gval;
+                    const float alpha = fminf(kAlphaMax, raw);
+                    if (alpha >= kAlphaMin) {
+                        const float col[3] = {r1.z, r1.w, sm.rec[j][2].x};
+                        const float q = alpha * T;
+                        const float inv = __fdividef(1.f, 1.f - alpha);  // 1 - alpha >= 0.01
+                        const float rr = raw <= kAlphaMax ? raw : 0.f;
+                        float hr[3];
 #pragma unroll
-            for (int q = 0; q < 32; ++q) v[q] = 0.f;
-#pragma unroll
-            for (int q = 0; q < 16; ++q) v2[q] = 0.f;
-#pragma unroll
-            for (int q = 0; q < 10; ++q) vr[q] = 0.f;
-            bool contrib = false;
-            if (b + j < lane_end) {
-                const float4 r0 = s_rec[j][0], r1 = s_rec[j][1];
-                const float dx = r0.x - p.pcx, dy = r0.y - p.pcy;
-                const float power = -0.5f * (r0.z * dx * dx + r1.x * dy * dy) - r0.w * dx * dy;
-                const float gval = __expf(power);
-                const float raw = r1.y * gval;
-                const float alpha = fminf(kAlphaMax, raw);
-                if (alpha >= kAlphaMin) {
-                    contrib = true;
-                    const float col[3] = {r1.z, r1.w, s_rec[j][2].x};
-                    const float q = alpha * T;
-                    const float inv = __fdividef(1.f, 1.f - alpha);  // 1 - alpha >= 0.01
-                    float h[3];
-#pragma unroll
-                    for (int ch = 0; ch < 3; ++ch) {
-                        acc[ch] += col[ch] * q;
-                        h[ch] = T * col[ch] - (Cf[ch] - acc[ch]) * inv;
+                        for (int ch = 0; ch < 3; ++ch) {
+                            acc[ch] += col[ch] * q;
+                            hr[ch] = rr * (T * col[ch] - (Cf[ch] - acc[ch]) * inv);
+                        }
+                        out = make_float4(q, hr[0], hr[1], hr[2]);
+                        T *= 1.f - alpha;
                     }
-                    float e[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                    if (raw <= kAlphaMax) {
-                        e[0] = -raw * (r0.z * dx + r0.w * dy);
-                        e[1] = -raw * (r0.w * dx + r1.x * dy);
-                        e[2] = -0.5f * raw * dx * dx;
-                        e[3] = -raw * dx * dy;
-                        e[4] = -0.5f * raw * dy * dy;
-                        e[5] = gval;
+                }
+                sm.qh[jj][lane] = out;
+            }
+            __syncwarp();
+            // phase B
+            float D[14], M[9];
+#pragma unroll
+            for (int k = 0; k < 14; ++k) D[k] = 0.f;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) M[k] = 0.f;
+            const int j = h0 + e;
+            if (e < m) {
+                float J[LJ::N];
+                load_jac<DEG>(c, p.slot, (int)sm.id[j], J);
+                const float4 r0 = sm.rec[j][0], r1 = sm.rec[j][1];
+                const unsigned bits = __float_as_uint(J[LJ::kMask]);
+                float acol[3][3];
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch)
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) acol[ch][k] = (DEG > 0 && ((bits >> ch) & 1u)) ? J[LJ::kGx + 3 * ch + k] : 0.f;
+                for (int i = hh; i < nact; i += 2) {
+                    const float4 qh = sm.qh[e][i];
+                    const float4 x0 = sm.pix0[i], x1 = sm.pix1[i];
+                    const float dx = r0.x - x0.x, dy = r0.y - x0.y;
+                    const float et0 = -(r0.z * dx + r0.w * dy), et1 = -(r0.w * dx + r1.x * dy);
+                    const float et2 = -0.5f * dx * dx, et3 = -dx * dy, et4 = -0.5f * dy * dy;
+                    const float W = x0.z * qh.y * qh.y + x0.w * qh.z * qh.z + x1.x * qh.w * qh.w;
+#pragma unroll
+                    for (int k = 3; k < 10; ++k) {
+                        const float ea = et2 * J[LJ::kCon + k] + et3 * J[LJ::kCon + 10 + k] + et4 * J[LJ::kCon + 20 + k];
+                        D[k] = fmaf(W * ea, ea, D[k]);
                     }
-                    const float H2 = wch[0] * h[0] * h[0] + wch[1] * h[1] * h[1] + wch[2] * h[2] * h[2];
-                    float vals[42];
-                    int idx = 0;
 #pragma unroll
-                    for (int f = 0; f < 6; ++f)
-#pragma unroll
-                        for (int g = f; g < 6; ++g) vals[idx++] = H2 * e[f] * e[g];
-#pragma unroll
-                    for (int f = 0; f < 6; ++f)
-#pragma unroll
-                        for (int ch = 0; ch < 3; ++ch) vals[21 + 3 * f + ch] = wch[ch] * q * h[ch] * e[f];
-#pragma unroll
-                    for (int ch = 0; ch < 3; ++ch) vals[39 + ch] = wch[ch] * q * q;
-#pragma unroll
-                    for (int k = 0; k < 32; ++k) v[k] = vals[k];
-#pragma unroll
-                    for (int k = 0; k < 10; ++k) v2[k] = vals[32 + k];
+                    for (int k = 0; k < 3; ++k) {
+                        const float ea = et0 * J[LJ::kMu + k] + et1 * J[LJ::kMu + 3 + k] + et2 * J[LJ::kCon + k] +
+                                         et3 * J[LJ::kCon + 10 + k] + et4 * J[LJ::kCon + 20 + k];
+                        if constexpr (DEG == 0) {
+                            D[k] = fmaf(W * ea, ea, D[k]);
+                        } else {
+                            const float t0 = fmaf(qh.y, ea, qh.x * acol[0][k]);
+                            const float t1 = fmaf(qh.z, ea, qh.x * acol[1][k]);
+                            const float t2 = fmaf(qh.w, ea, qh.x * acol[2][k]);
+                            D[k] = fmaf(x0.z * t0, t0, fmaf(x0.w * t1, t1, fmaf(x1.x * t2, t2, D[k])));
+                        }
+                    }
+                    D[10] += W;
+                    const float q2 = qh.x * qh.x;
+                    D[11] = fmaf(x0.z, q2, D[11]);
+                    D[12] = fmaf(x0.w, q2, D[12]);
+                    D[13] = fmaf(x1.x, q2, D[13]);
                     if (kRhs) {
-                        const float abar = ub[0] * h[0] + ub[1] * h[1] + ub[2] * h[2];
-#pragma unroll
-                        for (int f = 0; f < 6; ++f) vr[f] = abar * e[f];
-#pragma unroll
-                        for (int ch = 0; ch < 3; ++ch) vr[6 + ch] = ub[ch] * q;
+                        const float pb = x1.y * qh.y + x1.z * qh.z + x1.w * qh.w;
+                        const float pdx = pb * dx, pdy = pb * dy;
+                        M[0] += pdx;
+                        M[1] += pdy;
+                        M[2] = fmaf(pdx, dx, M[2]);
+                        M[3] = fmaf(pdx, dy, M[3]);
+                        M[4] = fmaf(pdy, dy, M[4]);
+                        M[5] += pb;
+                        M[6] = fmaf(x1.y, qh.x, M[6]);
+                        M[7] = fmaf(x1.z, qh.x, M[7]);
+                        M[8] = fmaf(x1.w, qh.x, M[8]);
                     }
-                    T *= 1.f - alpha;
                 }
             }
-            const unsigned ball = __ballot_sync(kFull, contrib);
-            if (ball) {
-                float* dst = gbase + (long long)s_id[j] * kGramF;
-                if (__popc(ball) <= kGramDirectMax) {
-                    if (contrib) {
 #pragma unroll
-                        for (int k = 0; k < 32; ++k) atomicAdd(dst + k, v[k]);
+            for (int k = 0; k < 14; ++k) D[k] += __shfl_xor_sync(kFull, D[k], 16);
+            if (kRhs)
 #pragma unroll
-                        for (int k = 0; k < 10; ++k) atomicAdd(dst + 32 + k, v2[k]);
-                    }
-                } else {
-                    warp_reduce_scatter<32>(v);
-                    atomicAdd(dst + lane, v[0]);
-                    warp_reduce_scatter<16>(v2);
-                    const int idx = lane >> 1;
-                    if (!(lane & 1) && idx < 10) atomicAdd(dst + 32 + idx, v2[0]);
-                }
+                for (int k = 0; k < 9; ++k) M[k] += __shfl_xor_sync(kFull, M[k], 16);
+            if (hh == 0 && e < m) {
+                const float4 r0 = sm.rec[j][0], r1 = sm.rec[j][1];
+                const float om = 1.f - r1.y;
+                float* dst = dbase + (long long)sm.id[j] * kDiagF;
+                red_add_v4(dst, D[0], D[1], D[2], D[3]);
+                red_add_v4(dst + 4, D[4], D[5], D[6], D[7]);
+                red_add_v4(dst + 8, D[8], D[9], om * om * D[10], D[11]);
+                red_add_v4(dst + 12, D[12], D[13], 0.f, 0.f);
                 if (kRhs) {
-                    float* cdst = cot_base + (long long)s_id[j] * kCotF;
-                    if (__popc(ball) <= kDirectMax) {
-                        if (contrib)
-#pragma unroll
-                            for (int q = 0; q < 9; ++q) atomicAdd(cdst + q, vr[q]);
-                    } else {
-                        const int ci = warp_reduce_scatter9(vr);
-                        if (!(lane & 1) && ci >= 0) atomicAdd(cdst + ci, vr[0]);
-                    }
+                    float* cdst = cbase + (long long)sm.id[j] * kCotF;
+                    red_add_v4(cdst, -(r0.z * M[0] + r0.w * M[1]), -(r0.w * M[0] + r1.x * M[1]), -0.5f * M[2], -M[3]);
+                    red_add_v4(cdst + 4, -0.5f * M[4], __fdividef(M[5], r1.y), M[6], M[7]);
+                    atomicAdd(cdst + 8, M[8]);
                 }
             }
+            __syncwarp();
         }
-        __syncwarp();
     }
 }
 
@@ -874,11 +977,22 @@ void launch_raster_vjp(const Ctx& c, const float* u, cudaStream_t st) {
 void launch_raster_jtj(const Ctx& c, cudaStream_t st) {
     if (c.nwork > 0) LMRS_LAUNCH(k_jtj, raster_grid(c), kRasterBlock, 0, st, c);
 }
-void launch_raster_gram(const Ctx& c, cudaStream_t st) {
-    if (c.nwork > 0) LMRS_LAUNCH_AS("k_gram", k_gram<false>, raster_grid(c), kRasterBlock, 0, st, c);
+template <bool kRhs>
+static void diag_deg(const Ctx& c, cudaStream_t st) {
+    const unsigned grid = raster_grid(c);
+    const char* name = kRhs ? "k_diag<rhs>" : "k_diag";
+    switch (c.deg) {
+        case 0: LMRS_LAUNCH_AS(name, (k_diag<0, kRhs>), grid, kRasterBlock, 0, st, c); break;
+        case 1: LMRS_LAUNCH_AS(name, (k_diag<1, kRhs>), grid, kRasterBlock, 0, st, c); break;
+        case 2: LMRS_LAUNCH_AS(name, (k_diag<2, kRhs>), grid, kRasterBlock, 0, st, c); break;
+        default: LMRS_LAUNCH_AS(name, (k_diag<3, kRhs>), grid, kRasterBlock, 0, st, c); break;
+    }
 }
-void launch_raster_gram_rhs(const Ctx& c, cudaStream_t st) {
-    if (c.nwork > 0) LMRS_LAUNCH_AS("k_gram<rhs>", k_gram<true>, raster_grid(c), kRasterBlock, 0, st, c);
+void launch_raster_diag(const Ctx& c, cudaStream_t st) {
+    if (c.nwork > 0) diag_deg<false>(c, st);
+}
+void launch_raster_diag_rhs(const Ctx& c, cudaStream_t st) {
+    if (c.nwork > 0) diag_deg<true>(c, st);
 }
 
 }  // namespace lmrs

@@ -78,7 +78,7 @@ struct lmrs_scene {
     const float* targets = nullptr;
     // device state
     DevBuf params, cams, views, gcache, pjac;
-    DevBuf rec, tan, rect, ell, dkeys, dvals, dkeys_alt, dvals_alt, dtmp, cnt, cot, gram;
+    DevBuf rec, tan, rect, ell, dkeys, dvals, dkeys_alt, dvals_alt, dtmp, cnt, cot, dslot;
     DevBuf keys, ids, keys_alt, ids_alt, ranges, scan_tmp, radix_tmp, total;
     DevBuf tile_off, off, wtile, wsample, work;
     DevBuf item_cost, work_sorted, okeys, ovals, okeys_alt, ovals_alt, otmp;
@@ -103,7 +103,7 @@ struct lmrs_scene {
     // every device buffer the scene owns
     std::vector<DevBuf*> bufs() {
         return {&params, &cams, &views, &gcache, &pjac, &rec, &tan, &rect, &ell, &dkeys, &dvals, &dkeys_alt, &dvals_alt, &dtmp, &cnt,
-                &cot, &gram, &keys, &ids, &keys_alt, &ids_alt, &ranges, &scan_tmp, &radix_tmp, &total, &tile_off,
+                &cot, &dslot, &keys, &ids, &keys_alt, &ids_alt, &ranges, &scan_tmp, &radix_tmp, &total, &tile_off,
                 &off, &wtile, &wsample, &work, &item_cost, &work_sorted, &okeys, &ovals, &okeys_alt, &ovals_alt, &otmp,
                 &cids, &clen, &binmat, &bintmp, &rowl, &tcnt, &resid, &cacheC, &cacheT, &cacheCh, &cacheTh, &cacheN, &x, &r, &z, &p, &Ap,
                 &minv, &D, &b, &stage_a, &stage_b, &sc, &partials, &counter, &frames, &sqerr, &ssim_s, &ssim_d, &sframes};
@@ -135,7 +135,7 @@ struct lmrs_scene {
         c.n_visible = total.as<unsigned long long>() + 1;
         c.n_rowent = total.as<unsigned long long>() + 2;
         c.cot = cot.as<float>();
-        c.gram = gram.as<float>();
+        c.dslot = dslot.as<float>();
         c.keys = keys.as<unsigned int>();
         c.ids = ids.as<unsigned int>();
         c.npairs = npairs;
@@ -417,10 +417,10 @@ lmrs_status need_render(lmrs_scene* s) {
 
 lmrs_status do_jtj_diag(lmrs_scene* s) {
     const size_t pairs = (size_t)s->nv * s->G;
-    TRY(ensure(s, s->gram, sizeof(float) * kGramF * pairs));
-    CK(s, cudaMemsetAsync(s->gram.p, 0, sizeof(float) * kGramF * pairs, s->st));
+    TRY(ensure(s, s->dslot, sizeof(float) * kDiagF * pairs));
+    CK(s, cudaMemsetAsync(s->dslot.p, 0, sizeof(float) * kDiagF * pairs, s->st));
     Ctx c = s->ctx();
-    launch_raster_gram(c, s->st);
+    launch_raster_diag(c, s->st);
     launch_prep_diag(c, s->D.as<float>(), s->st);
     CHECK_LAUNCH(s);
     s->have_D = true;
@@ -428,16 +428,16 @@ lmrs_status do_jtj_diag(lmrs_scene* s) {
 }
 
 // Right-hand side J^T W r -> b and diag(J^T W J) -> D of an LM step in one
-// walk of the compact lists (k_gram<rhs>), then their parameter-level
+// walk of the compact lists (k_diag<rhs>), then their parameter-level
 // kernels: the same results as lmrs_rhs followed by do_jtj_diag.
 lmrs_status do_rhs_diag(lmrs_scene* s, float* b) {
     TRY(need_render(s));
     const size_t pairs = (size_t)s->nv * s->G;
-    TRY(ensure(s, s->gram, sizeof(float) * kGramF * pairs));
-    CK(s, cudaMemsetAsync(s->gram.p, 0, sizeof(float) * kGramF * pairs, s->st));
+    TRY(ensure(s, s->dslot, sizeof(float) * kDiagF * pairs));
+    CK(s, cudaMemsetAsync(s->dslot.p, 0, sizeof(float) * kDiagF * pairs, s->st));
     CK(s, cudaMemsetAsync(s->cot.p, 0, sizeof(float) * kCotF * pairs, s->st));
     Ctx c = s->ctx();
-    launch_raster_gram_rhs(c, s->st);
+    launch_raster_diag_rhs(c, s->st);
     launch_prep_diag(c, s->D.as<float>(), s->st);
     launch_prep_vjp(c, b, nullptr, nullptr, false, s->st);
     CHECK_LAUNCH(s);
@@ -1114,9 +1114,9 @@ int64_t lmrs_footprint_bytes(const lmrs_config* cfg, int64_t n_gauss, int32_t n_
     }
     const double pairs = nv * G, entries = tpp * pairs, S = nv * S_view, items = nv * items_view;
     // rec 96, Jacobian cache, rect 16, row-span ellipse 32, depth keys/values
-    // and their alternates 24, counts 8, cotangent slots 48, Gram blocks 176;
+    // and their alternates 24, counts 8, cotangent slots 48, diagonal slots 64;
     // scan and sort scratch ~2
-    const double per_pair = 96 + 16.0 * jac_f4(cfg->sh_degree) + 16 + 32 + 24 + 8 + 48 + 4.0 * kGramF + 2;
+    const double per_pair = 96 + 16.0 * jac_f4(cfg->sh_degree) + 16 + 32 + 24 + 8 + 48 + 4.0 * kDiagF + 2;
     // ids and the binning's row lists 8 (the emission path: keys, ids and their
     // alternates 16, the bound taken), compact lists 4 per work item of a tile
     const double per_entry = 16 + 4.0 * max_items + 1;
@@ -1168,6 +1168,17 @@ int64_t lmrs_num_evaluations(lmrs_scene* s) {
     if (check_scene(s) != LMRS_OK || !s->rendered) return -1;
     unsigned long long n = 0;
     if (cudaMemcpyAsync(&n, &s->ctx().sc->n_eval, sizeof(n), cudaMemcpyDeviceToHost, s->st) != cudaSuccess ||
+        cudaStreamSynchronize(s->st) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    return (int64_t)n;
+}
+
+int64_t lmrs_num_walked_entries(lmrs_scene* s) {
+    if (check_scene(s) != LMRS_OK || !s->rendered) return -1;
+    unsigned long long n = 0;
+    if (cudaMemcpyAsync(&n, &s->ctx().sc->n_walk, sizeof(n), cudaMemcpyDeviceToHost, s->st) != cudaSuccess ||
         cudaStreamSynchronize(s->st) != cudaSuccess) {
         cudaGetLastError();
         return -1;
