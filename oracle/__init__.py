@@ -31,13 +31,13 @@ class _Config(C.Structure):
                 ("lr_warm", C.c_double), ("lr_cap", C.c_double), ("color_bound", C.c_double),
                 ("warm_iters", C.c_int32), ("seed", C.c_uint64),
                 ("margin_alpha", C.c_double), ("margin_T", C.c_double), ("sample_dist", C.c_int32),
-                ("ssim_weight", C.c_double)]
+                ("ssim_weight", C.c_double), ("list_mode", C.c_int32)]
 
 
 DEFAULTS = dict(sh_degree=0, tile_w=16, tile_h=16, sample_frac=1.0, samples_per_tile=0, weight_mode=0,
                 lambda_=1e-2, damping_mode=1, cg_iters=10, lr_warm=0.05, lr_cap=0.2, color_bound=1.0,
                 warm_iters=10, seed=0x1A5E0000, margin_alpha=1e-4, margin_T=1e-3, sample_dist=0,
-                ssim_weight=0.0)
+                ssim_weight=0.0, list_mode=0)
 
 _P = C.c_void_p
 
@@ -77,6 +77,7 @@ def lib():
             "orc_vjp": (C.c_int32, [_P, _P, _P]),
             "orc_vjp_gauss": (C.c_int32, [_P, _P, _P, C.c_int32, _P]),
             "orc_diag": (C.c_int32, [_P, _P]),
+            "orc_diag_magnitude": (C.c_int32, [_P, _P]),
             "orc_diag_gauss": (C.c_int32, [_P, _P, C.c_int32, _P]),
             "orc_apply": (C.c_int32, [_P, _P, _P, _P]),
             "orc_apply_gauss": (C.c_int32, [_P, _P, _P, _P, C.c_int32, _P]),
@@ -289,6 +290,13 @@ class OracleScene:
         D = np.empty(self.n_params)
         lib().orc_diag(self._h, _ptr(D))
         return D
+
+    def diag_magnitude(self):
+        """Per entry of diag(J^T W J): the sum over rows of w (sum_f |dC/df
+        a_fj|)^2, against which an FP32 evaluation of the entry rounds."""
+        M = np.empty(self.n_params)
+        lib().orc_diag_magnitude(self._h, _ptr(M))
+        return M
 
     def diag_gauss(self, gids):
         gids = np.ascontiguousarray(gids, dtype=np.int32)

@@ -663,8 +663,9 @@ void build_lists(orc_scene* s) {
             if (!q.vis) continue;
             uint64_t key = ((uint64_t)float_bits(q.depth) << 32) | (uint32_t)g;
             for (int ty = q.y0; ty <= q.y1; ++ty) {
-                int sx0, sx1;
-                if (!row_span(q, ty, s->cfg.tile_w, s->cfg.tile_h, s->W, s->H, &sx0, &sx1)) continue;
+                int sx0 = q.x0, sx1 = q.x1;
+                if (s->cfg.list_mode == 0 && !row_span(q, ty, s->cfg.tile_w, s->cfg.tile_h, s->W, s->H, &sx0, &sx1))
+                    continue;
                 for (int tx = sx0; tx <= sx1; ++tx)
                     bins[(size_t)slot * s->T + ty * s->tiles_x + tx].push_back({key, g});
             }
@@ -1229,6 +1230,37 @@ static void diag_local(const orc_scene* s, int slot, int g, double* out_local) {
                 }
         });
     });
+}
+
+// Magnitude of the same rows: sum over (sample, channel) of w (sum_f
+// |dC_ch/dfeature_f a[f][j]|)^2, the scale against which a floating-point
+// evaluation of each row's chain rule rounds (an FP32 evaluation of D_j has
+// an error of order u sqrt(D_j M_j) by Cauchy-Schwarz, u = 2^-24).
+static void diag_mag_local(const orc_scene* s, int slot, int g, double* out_local) {
+    std::vector<double> a;
+    s->prep_jacobian(slot, g, a);
+    samples_of_gaussian(s, slot, g, [&](int64_t i) {
+        for_each_contribution(s, i, [&](int, const Contrib& c) {
+            if (c.id != g) return;
+            for (int ch = 0; ch < 3; ++ch)
+                for (int j = 0; j < s->Pg; ++j) {
+                    double m = 0.0;
+                    for (int f = 0; f < 9; ++f) m += std::fabs(c.dC[ch][f] * a[(size_t)f * s->Pg + j]);
+                    out_local[j] += s->row_weight(i, ch) * m * m;
+                }
+        });
+    });
+}
+
+int32_t orc_diag_magnitude(const orc_scene* s, double* M) {
+    std::fill(M, M + s->P(), 0.0);
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int g = 0; g < s->G; ++g) {
+        std::vector<double> loc(s->Pg, 0.0);
+        for (int slot = 0; slot < s->nv(); ++slot) diag_mag_local(s, slot, g, loc.data());
+        for (int j = 0; j < s->Pg; ++j) M[s->pindex(g, j)] = loc[j];
+    }
+    return 0;
 }
 
 int32_t orc_diag(const orc_scene* s, double* D) {

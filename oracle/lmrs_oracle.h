@@ -54,6 +54,8 @@ typedef struct {
     double  margin_T;         /* relative margin that flags a termination test */
     int32_t sample_dist;      /* 0 uniform without replacement; 1 q_residual; 2 q_Gaussian (i.i.d. per tile) */
     double  ssim_weight;      /* weight of the diagonal SSIM residual term (0: MSE only) */
+    int32_t list_mode;        /* 0: per tile row, the tiles the alpha >= 1/255 ellipse reaches;
+                                 1: every tile of the 3-sigma rectangle (the 3DGS lists, Sec. 3) */
 } orc_config;
 
 typedef struct orc_scene orc_scene;
@@ -99,6 +101,9 @@ int32_t orc_jvp_subset(const orc_scene* s, const double* v, const int64_t* idx, 
 int32_t orc_vjp(const orc_scene* s, const double* u, double* g);
 int32_t orc_vjp_gauss(const orc_scene* s, const double* u, const int32_t* gids, int32_t n, double* out);
 int32_t orc_diag(const orc_scene* s, double* D);
+/* Per entry j: sum over the rows (sample, channel) of w (sum_f |dC/df a_fj|)^2,
+ * the magnitude of the terms of D_j's chain rule. */
+int32_t orc_diag_magnitude(const orc_scene* s, double* M);
 int32_t orc_diag_gauss(const orc_scene* s, const int32_t* gids, int32_t n, double* out);
 int32_t orc_apply(const orc_scene* s, const double* v, const double* D, double* out);
 int32_t orc_apply_gauss(const orc_scene* s, const double* v, const double* D,

@@ -438,6 +438,56 @@ def test_tile_lists_are_the_tiles_the_alpha_ellipse_reaches(tw, th):
     assert dropped >= 0.1 * (kept + dropped) and kept > 500
 
 
+def _list_scenes():
+    rng = np.random.default_rng(5)
+    tiny = syn.tiny_scene()
+    ragged = syn.tiny_scene(seed=99, n_gauss=1500, width=100, height=70, sh_degree=1)
+    ell = _ellipse_scene()
+    return {
+        "tiny": (tiny, syn.noise_targets(rng, 4, 64, 64), [0, 1, 2, 3], dict(lambda_=1e-2)),
+        "ragged_sh1_10pct": (ragged, syn.noise_targets(rng, 4, 70, 100), [3, 1],
+                             dict(sample_frac=0.1, weight_mode=1, lambda_=0.1)),
+        "ellipse_8x32": (ell, syn.noise_targets(rng, 3, 70, 100), [2, 0],
+                         dict(tile_w=8, tile_h=32, lambda_=0.1)),
+    }
+
+
+@pytest.mark.parametrize("name", ["tiny", "ragged_sh1_10pct", "ellipse_8x32"])
+def test_ellipse_lists_change_no_result(name):
+    """The tile lists that follow the alpha >= 1/255 ellipse against the
+    3-sigma rectangles of 3DGS (Sec. 3 defers the lists to it): every
+    ellipse list is a subsequence of its rectangle list, and full frames,
+    sampled renders and their flags, J v, J^T u, diag(J^T W J), J^T W r and
+    the damped operator come out bit for bit the same.  An ellipse that
+    missed a pixel with alpha >= 1/255 would change them."""
+    sc, tgt, views, cfg = _list_scenes()[name]
+    osc = {m: oracle.OracleScene(sc.params, sc.cams, sc.n_gauss, sc.sh_degree, targets=tgt, list_mode=m, **cfg)
+           for m in (0, 1)}
+    for o in osc.values():
+        o.begin_step(views, 3)
+    (r0, i0), (r1, i1) = osc[0].lists(), osc[1].lists()
+    for t in range(len(r0)):
+        a, b = list(i0[r0[t, 0]:r0[t, 1]]), list(i1[r1[t, 0]:r1[t, 1]])
+        it = iter(b)
+        assert all(g in it for g in a), t  # subsequence, same order
+    assert len(i0) < 0.9 * len(i1)
+    for slot in range(len(views)):
+        (im0, f0), (im1, f1) = osc[0].render_full(slot), osc[1].render_full(slot)
+        np.testing.assert_array_equal(im0, im1)
+        np.testing.assert_array_equal(f0, f1)
+    for a, b in zip(osc[0].render_samples(), osc[1].render_samples()):
+        np.testing.assert_array_equal(a, b)
+    rng = np.random.default_rng(8)
+    v = rng.standard_normal(osc[0].n_params)
+    u = rng.standard_normal((osc[0].n_samples, 3))
+    np.testing.assert_array_equal(osc[0].jvp(v), osc[1].jvp(v))
+    np.testing.assert_array_equal(osc[0].vjp(u), osc[1].vjp(u))
+    D0, D1 = osc[0].diag(), osc[1].diag()
+    np.testing.assert_array_equal(D0, D1)
+    np.testing.assert_array_equal(osc[0].rhs(), osc[1].rhs())
+    np.testing.assert_array_equal(osc[0].apply(v, D0), osc[1].apply(v, D1))
+
+
 def test_faint_gaussians_have_no_entries():
     sc = _ellipse_scene()
     osc = oracle.OracleScene(sc.params, sc.cams, sc.n_gauss, 0)
