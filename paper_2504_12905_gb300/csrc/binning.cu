@@ -1,14 +1,19 @@
 // Tile binning with a hand-written stable LSD radix sort.
 //
-// Two levels, so the long (view, tile, Gaussian) list is sorted on the tile
-// bits only:
-//   1. the (view, Gaussian) pairs are sorted by (view, FP32 depth bits); they
-//      are emitted in Gaussian-index order and every pass is stable, so equal
-//      depths keep the lower index first;
-//   2. each visible pair, in that order, emits one entry per overlapped tile;
-//   3. the entries are stable-sorted by (view, tile).
-// The result is ordered by (view, tile, depth, Gaussian index), the list
-// order of the rendering equation (Sec. 3: Gaussians sorted by depth).
+// The (view, Gaussian) pairs are first sorted by (view, FP32 depth bits);
+// they are emitted in Gaussian-index order and every pass is stable, so equal
+// depths keep the lower index first.  The tile lists are then built from the
+// depth-ordered pairs, by one of two builders:
+//   * the two-level placement (the main path, while a view's rows and columns
+//     of tiles fit the shared-memory counters): each pair goes into the lists
+//     of the tile rows its ellipse reaches, then each row entry into the
+//     tiles of its span (see the section "Two-level stable binning" below);
+//   * the fallback for wider or taller tile grids: each visible pair emits one
+//     entry per tile it covers, and the entries are stable-sorted by (view,
+//     tile).
+// Either way the result is ordered by (view, tile, depth, Gaussian index),
+// the list order of the rendering equation (Sec. 3: Gaussians sorted by
+// depth).
 #include <algorithm>
 
 #include "common.cuh"

@@ -51,6 +51,12 @@ class KernelTime(C.Structure):
     _fields_ = [("name", C.c_char * 64), ("launches", C.c_int64), ("total_ms", C.c_double)]
 
 
+class Peaks(C.Structure):
+    _fields_ = [("sm_count", C.c_int32), ("sm_clock_max_mhz", C.c_double), ("fp32_tflops", C.c_double),
+                ("fp64_tflops", C.c_double), ("ex2_gops", C.c_double), ("atomic_scattered_gops", C.c_double),
+                ("red_v4_scattered_gops", C.c_double), ("atomic_same_address_gops", C.c_double)]
+
+
 class StepStats(C.Structure):
     _fields_ = [("loss", C.c_double), ("eta", C.c_double), ("max_dc", C.c_double), ("rz0", C.c_double),
                 ("rz_final", C.c_double), ("n_samples", C.c_int64), ("n_pairs", C.c_int64)]
@@ -136,6 +142,7 @@ _SIGS = {
                                          C.c_double]),
     "lmrs_scene_device_bytes": (C.c_int64, [_P]),
     "lmrs_num_evaluations": (C.c_int64, [_P]),
+    "lmrs_num_walked_entries": (C.c_int64, [_P]),
     "lmrs_uniform_views": (_S, [C.c_int32, C.c_int32, C.c_uint64, C.c_int64, _P]),
     "lmrs_view_sampler_create": (_S, [_P, C.c_int32, C.c_int32, C.c_uint64, C.POINTER(_P)]),
     "lmrs_view_sampler_destroy": (_S, [_P]),
@@ -147,6 +154,7 @@ _SIGS = {
     "lmrs_status_str": (C.c_char_p, [_S]),
     "lmrs_last_error": (C.c_char_p, [_P]),
     "lmrs_launch_count": (C.c_int64, []),
+    "lmrs_measure_peaks": (_S, [_P, C.POINTER(Peaks)]),
 }
 EXPORTS = tuple(_SIGS)
 
@@ -177,6 +185,8 @@ def _ptr(x):
         return None
     if isinstance(x, int):
         return x
+    if hasattr(x, "cuda_stream"):  # a torch.cuda.Stream: its cudaStream_t handle
+        return x.cuda_stream
     if hasattr(x, "data_ptr"):
         return x.data_ptr()
     if isinstance(x, np.ndarray):
@@ -476,6 +486,10 @@ def lmrs_num_evaluations(scene):
     return int(lib().lmrs_num_evaluations(scene))
 
 
+def lmrs_num_walked_entries(scene):
+    return int(lib().lmrs_num_walked_entries(scene))
+
+
 def lmrs_scene_device_bytes(scene):
     return int(lib().lmrs_scene_device_bytes(scene))
 
@@ -553,6 +567,13 @@ def lmrs_last_error(scene):
 
 def lmrs_launch_count():
     return int(lib().lmrs_launch_count())
+
+
+def lmrs_measure_peaks(stream=None):
+    """Measured peak rates of the current device as a dict (see include/lmrs.h)."""
+    pk = Peaks()
+    _check(lib().lmrs_measure_peaks(_ptr(stream), C.byref(pk)))
+    return {name: getattr(pk, name) for name, _ in Peaks._fields_}
 
 
 class Scene:

@@ -40,6 +40,11 @@ def test_noalloc_step_size_matches_scene_entry_point():
             assert got == pytest.approx(ref, rel=1e-12, abs=0.0), (call, step, got, ref)
         m = float(np.abs(x[dc0:].reshape(G, K3)[:, :3]).max())
         assert got == pytest.approx(min(0.2, 1.0 / m), rel=1e-12)
+        # the same call on a stream of the caller's (a torch stream)
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        got_s = lmrs.lmrs_step_size_noalloc(xd, G, deg, 12, stream=side, **cfg)
+        assert got_s == pytest.approx(ref, rel=1e-12, abs=0.0), (call, got_s, ref)
     scene.close()
 
 
