@@ -55,11 +55,12 @@ WORKLOADS = {
                     samples_per_tile=32, cg_iters=8, lam=0.1, damping_mode=0, fit_steps=20,
                     tile_shapes=((16, 16), (32, 8), (8, 32))),
     "serving": dict(desc="fit requests with Poisson arrivals (mean 20/s): 2k-300k Gaussians (log-uniform), SH1, "
-                         "8-32 views 512x512, all views every step, 32 samples per 256-pixel tile, 8 CG iters; each "
-                         "fit runs until its sampled loss is within 0.1 dB of its ground truth's (at most 60 steps); "
-                         "120 GB admission budget",
+                         "8-32 views 512x512, all views every step, 32 samples per 256-pixel tile, 8 CG iters, "
+                         "lambda*I damping; each fit runs until its full-frame PSNR over every camera is within "
+                         "0.1 dB of its ground truth's (at most 60 steps); 120 GB admission budget",
                     samples_per_tile=32, cg_iters=8, lam=0.1, damping_mode=0, rate=20.0, requests=100,
-                    max_steps=60, noise_sigma=0.02, psnr_slack_db=0.1, budget_bytes=120 << 30, max_active=64),
+                    max_steps=60, noise_sigma=0.02, psnr_slack_db=0.1, budget_bytes=120 << 30, max_active=16,
+                    policy=1, full_frame_gate=1.25),
 }
 
 
@@ -149,9 +150,11 @@ JTJ_FLOPS_PER_EVAL = 66 + 63
 JAC_F4 = {0: 10, 1: 12, 2: 12, 3: 12}
 
 
-def fp32_peak_tflops(sm_mhz):
-    """152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x clock."""
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+def unit_peaks():
+    """FP32, FP64, 2^x and atomic rates of this GPU, measured by the
+    library's microbenchmarks (lmrs_measure_peaks), with its SM count."""
+    from paper_2504_12905_gb300 import lmrs
+    return lmrs.lmrs_measure_peaks()
 
 
 def algorithmic_bytes(kernel, sizes):
@@ -163,8 +166,9 @@ def algorithmic_bytes(kernel, sizes):
     means = 12 * G if deg > 0 else 0  # the means, for the view direction of the SH basis
     if kernel == "k_prep_jvp":
         # rectangles of every pair; per visible pair the Jacobian, the 9-float
-        # tangent written and the 9-float cotangent slot cleared; the tangent P-vector
-        return 16 * nv * G + Vis * (jac + 36 + 36) + 4 * P + means
+        # tangent written and the 9-float cotangent slot cleared; the PCG
+        # direction p <- z + beta p formed in the same pass (z, p read; p written)
+        return 16 * nv * G + Vis * (jac + 36 + 36) + 12 * P + means
     if kernel == "k_prep_vjp<dot>":
         # rectangles; per visible pair the Jacobian and the cotangents; p read,
         # Ap written, D read under diagonal damping
@@ -172,8 +176,6 @@ def algorithmic_bytes(kernel, sizes):
         return 16 * nv * G + Vis * (jac + 36) + 2 * 4 * P + d_read + means
     if kernel == "k_cg_update<true>":
         return 4 * P * 8  # p, Ap, M^-1, x, r read; x, r, z written
-    if kernel == "k_cg_direction":
-        return 4 * P * 3  # z, p read; p written
     return None
 
 
@@ -295,6 +297,9 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         ranks.barrier()
 
+    # ---- peak rates of the units the raster kernels use (not timed) -----
+    peaks = unit_peaks()
+
     # ---- warm-up -------------------------------------------------------
     for k in range(args.warmup):
         lmrs.lmrs_lm_step(h, views[k], k, stats=False)
@@ -333,14 +338,16 @@ def run_ours(args, rank, world, local_rank):
     # sizes of the last step for the byte model, and the composited
     # evaluations per operator application averaged over the timed steps'
     # view sets (at the final parameters)
-    evals = []
+    evals, walked = [], []
     for k in range(args.warmup, n_steps):
         lmrs.lmrs_preprocess(h, views[k], k)
         lmrs.lmrs_render(h)
         evals.append(lmrs.lmrs_num_evaluations(h))
+        walked.append(lmrs.lmrs_num_walked_entries(h))
     sizes = {"pairs": lmrs.lmrs_num_pairs(h), "visible": lmrs.lmrs_num_visible(h),
              "samples": lmrs.lmrs_num_samples(h), "view_tiles": nvs * scene.n_tiles, "P": scene.n_params,
              "views": nvs, "G": G, "sh_degree": deg, "evaluations_mean": int(np.mean(evals)),
+             "walked_entries_mean": int(np.mean(walked)),
              "damping_mode": wl.get("damping_mode", 0)}
 
     # ---- (J^T W J + lambda diag(J^T W J)) v alone, at the current parameters
@@ -398,20 +405,23 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- roofline of the dominant kernel ------------------------------
     # k_jtj is bound by FP32 / integer instruction issue (ALU), not by HBM:
-    # algorithmic FLOPs = composited evaluations x FLOPs per evaluation
+    # algorithmic FLOPs = composited evaluations x FLOPs per evaluation,
+    # against the FP32 FMA rate measured on this GPU
     peak_hbm, peak_kind = load_peaks()
     roof = None
+    peak32 = peaks["fp32_tflops"]
+    src32 = (f"measured: lmrs_measure_peaks FP32 FMA chains on {peaks['sm_count']} SMs "
+             f"(nominal {peaks['sm_count']} x 128 lanes x 2 x {peaks['sm_clock_max_mhz']:.0f} MHz = "
+             f"{peaks['sm_count'] * 256 * peaks['sm_clock_max_mhz'] * 1e-6:.1f})")
     if "k_jtj" in ktimes:
         n_l, tot = ktimes["k_jtj"]
         avg_s = tot / n_l / 1000.0
         flops = JTJ_FLOPS_PER_EVAL * sizes["evaluations_mean"]
-        mhz = clock_info.get("sm_max_mhz") or 2070.0
-        peak = fp32_peak_tflops(mhz)
         ach = flops / avg_s / 1e12
-        roof = {"kernel": "k_jtj", "bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 2),
-                "unit": "TFLOP/s", "frac": round(ach / peak, 4),
+        roof = {"kernel": "k_jtj", "bound": "alu", "achieved": round(ach, 3), "peak": round(peak32, 2),
+                "unit": "TFLOP/s", "frac": round(ach / peak32, 4),
                 "traffic": profiled_traffic("k_jtj", args.workload),
-                "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz",
+                "peak_source": src32,
                 "algorithmic_flops_per_launch": int(flops), "avg_launch_ms": round(tot / n_l, 4),
                 "hbm_frac_of_measured": None}
         tr = roof["traffic"]
@@ -419,7 +429,7 @@ def run_ours(args, rank, world, local_rank):
             roof["hbm_frac_of_measured"] = round(tr / avg_s / 1e9 / peak_hbm, 4)
     # the HBM-bound kernels of the PCG loop, against the measured copy bandwidth
     secondary = {}
-    for kname in ("k_prep_jvp", "k_prep_vjp<dot>", "k_cg_update<true>", "k_cg_direction"):
+    for kname in ("k_prep_jvp", "k_prep_vjp<dot>", "k_cg_update<true>"):
         if kname in ktimes:
             n_l, tot = ktimes[kname]
             byt = algorithmic_bytes(kname, sizes)
@@ -428,16 +438,20 @@ def run_ours(args, rank, world, local_rank):
                                 "frac": round(ach / peak_hbm, 4), "peak_source": peak_kind,
                                 "algorithmic_bytes_per_launch": int(byt), "avg_launch_ms": round(tot / n_l, 4)}
     # the whole operator application against the lower bound of the
-    # algorithmic model: t_min = max(Q / HBM, F / FP32, exponentials / SFU)
-    mhz = clock_info.get("sm_max_mhz") or 2070.0
+    # algorithmic model: t_min = max(Q / HBM, F / FP32, exponentials / SFU,
+    # atomics / L2 atomic rate), every rate measured on this GPU; the
+    # back-scatter issues, per walked (work item, list entry), two 4-wide
+    # and one scalar atomic add
     Q = 16 * sizes["P"] + 144 * sizes["visible"] + 4 * sizes["pairs"] + 20 * sizes["samples"] + \
         8 * sizes["view_tiles"]
     F = JTJ_FLOPS_PER_EVAL * sizes["evaluations_mean"]
     X = 2 * sizes["evaluations_mean"]
-    t_parts = {"hbm_ms": Q / (peak_hbm * 1e9) * 1e3, "fp32_ms": F / (fp32_peak_tflops(mhz) * 1e12) * 1e3,
-               "sfu_ms": X / (152 * 16 * mhz * 1e6) * 1e3}
+    Wk = sizes["walked_entries_mean"]
+    t_parts = {"hbm_ms": Q / (peak_hbm * 1e9) * 1e3, "fp32_ms": F / (peak32 * 1e12) * 1e3,
+               "sfu_ms": X / (peaks["ex2_gops"] * 1e9) * 1e3,
+               "atomic_ms": (2 * Wk / peaks["red_v4_scattered_gops"] + Wk / peaks["atomic_scattered_gops"]) * 1e-9 * 1e3}
     t_min = max(t_parts.values())
-    matvec_bound = {"Q_bytes": int(Q), "F_flops": int(F), "exponentials": int(X),
+    matvec_bound = {"Q_bytes": int(Q), "F_flops": int(F), "exponentials": int(X), "walked_entries": int(Wk),
                     "t_min_ms": round(t_min, 4), **{k: round(v, 4) for k, v in t_parts.items()},
                     "t_operator_ms": round(matvec_ms, 4), "frac": round(t_min / matvec_ms, 4),
                     "hbm_frac_of_measured": round(Q / (matvec_ms / 1e3) / 1e9 / peak_hbm, 4)}
@@ -459,7 +473,8 @@ def run_ours(args, rank, world, local_rank):
                    "lm_steps_per_s": round(1000.0 * args.steps / ms_max * world, 3),
                    "matvec_only_ms": round(matvec_ms, 4), "matvec_only_per_s": round(1000.0 / matvec_ms, 2),
                    "sizes_last_step": sizes, "loss_last_step": None if last is None else last.loss,
-                   "cache_bf16": bool(bf16), "bf16_cache_error": bf16_err, "operator_bound": matvec_bound},
+                   "cache_bf16": bool(bf16), "bf16_cache_error": bf16_err, "operator_bound": matvec_bound,
+                   "unit_peaks": {k: (round(v, 3) if isinstance(v, float) else v) for k, v in peaks.items()}},
         "roofline": roof, "rooflines_hbm": secondary, "kernels": kshare, "e2e": e2e, "gpu_launches": launches,
         "clocks": clock_info,
     }
@@ -831,7 +846,11 @@ def run_serving(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     ranks = Replicas(rank, world, local_rank)
-    wl = WORKLOADS["serving"]
+    wl = dict(WORKLOADS["serving"])
+    if args.max_active > 0:
+        wl["max_active"] = args.max_active
+    if args.policy >= 0:
+        wl["policy"] = args.policy
     n_req = args.requests or wl["requests"]
     reqs = syn.serving_requests(seed=0x1A5E0004 + rank, n_requests=n_req + args.warmup, rate=wl["rate"])
     jobs = _serving_inputs(lmrs, torch, syn, reqs, wl, rank)
@@ -850,7 +869,8 @@ def run_serving(args, rank, world, local_rank):
         ranks.barrier()
 
     # ---- server arm ---------------------------------------------------------
-    srv = lmrs.lmrs_server_create(wl["budget_bytes"], max_active=wl["max_active"], setup_threads=8)
+    srv = lmrs.lmrs_server_create(wl["budget_bytes"], max_active=wl["max_active"], setup_threads=8,
+                                  policy=wl["policy"], stop_full_frame=1, full_frame_gate=wl["full_frame_gate"])
     wid = [lmrs.lmrs_server_submit(srv, cfg_of(k, j["sc"]), j["sc"].n_gauss, j["start"], j["sc"].cams, j["targets"],
                                    0, j["stop_loss"], wl["max_steps"]) for k, j in enumerate(warm)]
     for w in wid:
@@ -898,7 +918,9 @@ def run_serving(args, rank, world, local_rank):
         conv = False
         for step in range(wl["max_steps"]):
             st = lmrs.lmrs_lm_step(scene.h, views, step)
-            if st.loss <= j["stop_loss"]:
+            # the server's rule: full-frame MSE after the step, checked once
+            # the sampled loss is within the gate
+            if st.loss <= wl["full_frame_gate"] * j["stop_loss"] and lmrs.lmrs_eval_mse(scene.h) <= j["stop_loss"]:
                 conv = True
                 break
         out = np.empty(scene.n_params, np.float32)
@@ -941,6 +963,11 @@ def run_serving(args, rank, world, local_rank):
                              "latency_s": {"p50": _pct(lat_plain, 50), "p99": _pct(lat_plain, 99)},
                              "converged": conv_plain, "steps_mean": round(float(np.mean(steps_plain)), 2)},
                    "server_over_plain": round(fits_srv / fits_plain, 3),
+                   "offered_load_over_plain_capacity": round(wl["rate"] / fits_plain, 2),
+                   "policy": "least estimated work first" if wl["policy"] == 1 else "FIFO",
+                   "stop_rule": (f"full-frame MSE over every camera <= the ground truth's MSE x 10^(0.1/10), "
+                                 f"checked when the sampled loss is within {wl['full_frame_gate']}x of it; "
+                                 f"both arms"),
                    "parallelism": f"replicas x{world}", "l2": "no flush: per-step working set > 129 MB",
                    "wall_s": {"server": round(wall_srv, 2), "plain": round(wall_plain, 2)}},
         "roofline": None,
@@ -1102,6 +1129,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--requests", type=int, default=0, help="serving workload: number of timed requests")
+    ap.add_argument("--max-active", type=int, default=0, help="serving workload: resident jobs at most (0: default)")
+    ap.add_argument("--policy", type=int, default=-1, help="serving workload: 0 FIFO, 1 least work first")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

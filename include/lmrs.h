@@ -225,7 +225,10 @@ lmrs_status lmrs_step_size_noalloc(const float* x_dev, int64_t n_gauss, int32_t 
  * cfg.cg_iters iterations, step size, and the update beta <- beta - eta x
  * (the descent reading of Eq. 8 with r = render - target).  st may be NULL
  * (then nothing synchronises).  The solution x stays readable through
- * lmrs_get_solution. */
+ * lmrs_get_solution.  When the solve meets a non-finite r^T z or p^T A p, or
+ * p^T A p <= 0 (non-finite parameters or targets, for example), the update
+ * is skipped on the device (the parameters stay as they were, eta = 0) and,
+ * with st given, the call returns LMRS_ERR_NUMERIC; the scene stays usable. */
 lmrs_status lmrs_lm_step(lmrs_scene* scene, const int32_t* view_ids_host, int32_t n_views,
                          int64_t lm_step, lmrs_step_stats* st);
 lmrs_status lmrs_get_solution(lmrs_scene* scene, float* x_dst);
@@ -261,7 +264,8 @@ lmrs_status lmrs_batch_lm_step(lmrs_batch* batch, const int32_t* view_ids, const
 const char* lmrs_batch_last_error(const lmrs_batch* batch);
 /* Outcome of the last lmrs_batch_lm_step for scene i: LMRS_OK (stepped),
  * the scene's own error (its setup failed; LMRS_ERR_NUMERIC when its CG hit
- * p^T A p <= 0, detected only when stats were requested), or
+ * a non-finite or non-positive p^T A p, detected only when stats were
+ * requested; that scene's parameters are left unchanged), or
  * LMRS_ERR_NOT_PREPROCESSED (not stepped because another scene failed
  * before the batched loop). */
 lmrs_status lmrs_batch_scene_status(const lmrs_batch* batch, int32_t i);
@@ -328,17 +332,25 @@ lmrs_status lmrs_fit(lmrs_scene* scene, const lmrs_fit_config* cfg, lmrs_fit_rec
  * and steps them together with the batched LM step above.
  *   - lmrs_server_submit copies a job (parameters, cameras, targets: host
  *     memory) and queues it; it does not wait for the device.
- *   - a scheduler thread admits queued jobs in FIFO order while fewer than
- *     max_active jobs are resident and the device bytes of the resident jobs
- *     (for each, the larger of its admission estimate and what it holds)
- *     plus the next job's estimate (lmrs_footprint_bytes) stay within
- *     budget_bytes.  An admitted job's parameters, CG vectors, raster
- *     caches and targets stay on the device until it finishes.
+ *   - a scheduler thread admits queued jobs while fewer than max_active
+ *     jobs are resident and the device bytes of the resident jobs (for
+ *     each, the larger of its admission estimate and what it holds) plus
+ *     the next job's estimate (lmrs_footprint_bytes) stay within
+ *     budget_bytes.  The next job is the oldest (policy 0, FIFO) or the one
+ *     with the least estimated work, Gaussians x views per step x max_steps,
+ *     oldest first among equals (policy 1).  An admitted job's parameters,
+ *     CG vectors, raster caches and targets stay on the device until it
+ *     finishes.
  *   - every scheduler iteration runs one LM step of each resident job (one
  *     batch per group of equal SH degree and cg_iters), then retires the
- *     jobs whose sampled loss (Eq. 11 at the step's samples, before the
- *     update) is <= target_loss or that have run max_steps steps; the freed
- *     memory admits the next jobs (continuous batching).
+ *     jobs that reached target_loss or have run max_steps steps; the freed
+ *     memory admits the next jobs (continuous batching).  A job reaches its
+ *     target when its sampled loss (Eq. 11 at the step's samples, before the
+ *     update) is <= target_loss (stop_full_frame 0), or, with
+ *     stop_full_frame 1, when the full-frame MSE of its updated parameters
+ *     over every camera (lmrs_eval_mse) is <= target_loss; that is evaluated
+ *     after the steps whose sampled loss is <= full_frame_gate x
+ *     target_loss.
  *   - the views of step k: lmrs_uniform_views(n_cams, views_per_step,
  *     cfg.seed, k).  A job's steps therefore do not depend on the other jobs: its
  *     result alone and in any mix agree up to the summation order.
@@ -349,6 +361,9 @@ typedef struct {
     int32_t max_active;     /* resident jobs at most (1..1024) */
     int32_t setup_threads;  /* host threads for the per-scene step setup (>= 1) */
     double tiles_per_pair;  /* footprint model: tile entries per visible (view, Gaussian) pair; <= 0: 10 */
+    int32_t policy;         /* admission order: 0 FIFO, 1 least estimated work first */
+    int32_t stop_full_frame;  /* 1: the target is the full-frame MSE (see above) */
+    double full_frame_gate;   /* sampled loss / target_loss at or below which the full frames are checked; <= 0: 1.25 */
 } lmrs_server_config;
 
 typedef enum { LMRS_JOB_QUEUED = 0, LMRS_JOB_RUNNING = 1, LMRS_JOB_DONE = 2, LMRS_JOB_FAILED = 3 } lmrs_job_state;
@@ -359,6 +374,7 @@ typedef struct {
     int32_t converged;       /* 1: target_loss reached; 0: stopped at max_steps (or not finished) */
     int32_t steps;           /* LM steps run so far */
     double loss;             /* sampled loss of the last step */
+    double full_mse;         /* full-frame MSE at the last check (stop_full_frame), -1 if none */
     double t_submit;         /* seconds since the server was created */
     double t_admit;          /* -1 while queued */
     double t_done;           /* -1 until finished */
@@ -408,6 +424,11 @@ int64_t lmrs_footprint_bytes(const lmrs_config* cfg, int64_t n_gauss, int32_t n_
  * lmrs_render (alpha >= 1/255 and T still >= 1e-4, Eq. 4): the evaluations
  * each J v and J^T u application repeats.  -1 before a render. */
 int64_t lmrs_num_evaluations(lmrs_scene* scene);
+/* List entries the derivative kernels walk per application: the sum over
+ * work items (up to 32 samples of one tile) of their compact lists, the
+ * entries at which some sample of the item has alpha >= 1/255 before it
+ * stops, from the last lmrs_render.  -1 before a render. */
+int64_t lmrs_num_walked_entries(lmrs_scene* scene);
 /* Device bytes the scene holds now. */
 int64_t lmrs_scene_device_bytes(const lmrs_scene* scene);
 
@@ -478,6 +499,33 @@ const char* lmrs_last_error(const lmrs_scene* scene);
 
 /* Number of kernels this library has launched in the process so far. */
 int64_t lmrs_launch_count(void);
+
+/* ---- Peak rates of the current device ------------------------------------
+ * Measured by microbenchmarks of this library (the paper has no
+ * counterpart: they are the denominators of the raster kernels' roofline,
+ * App. A's Jv / J^T v kernels being FP32-, exponential- and atomic-bound).
+ * Each kernel runs once untimed and once timed with CUDA events on
+ * cuda_stream (NULL = legacy stream):
+ *   fp32_tflops / fp64_tflops : fused multiply-adds (2 FLOP each), 8
+ *                               independent chains per thread, 64 warps per SM;
+ *   ex2_gops                  : 2^x on the special-function unit
+ *                               (ex2.approx, as __expf issues it);
+ *   atomic_scattered_gops     : float atomic adds, every lane a different
+ *                               64-byte slot of a 64 MB buffer (L2-resident);
+ *   red_v4_scattered_gops     : the same with 4-wide vector adds (ops, each
+ *                               adding 4 floats);
+ *   atomic_same_address_gops  : the 32 lanes of a warp on one address.
+ * sm_count and sm_clock_max_mhz are the device attributes.  The call
+ * allocates and frees a 64 MB scratch buffer and two small output arrays
+ * with cudaMalloc, takes a few tens of milliseconds and synchronises.
+ * Errors: LMRS_ERR_INVALID_ARG (out NULL), LMRS_ERR_OOM, LMRS_ERR_CUDA. */
+typedef struct {
+    int32_t sm_count;
+    double sm_clock_max_mhz;
+    double fp32_tflops, fp64_tflops, ex2_gops;
+    double atomic_scattered_gops, red_v4_scattered_gops, atomic_same_address_gops;
+} lmrs_peaks;
+lmrs_status lmrs_measure_peaks(void* cuda_stream, lmrs_peaks* out);
 
 #ifdef __cplusplus
 }

@@ -78,6 +78,10 @@ def lib():
             "orc_vjp_gauss": (C.c_int32, [_P, _P, _P, C.c_int32, _P]),
             "orc_diag": (C.c_int32, [_P, _P]),
             "orc_diag_magnitude": (C.c_int32, [_P, _P]),
+            "orc_set_flips": (C.c_int32, [_P, _P, _P, C.c_int64]),
+            "orc_clear_flips": (C.c_int32, [_P]),
+            "orc_near_counts": (C.c_int32, [_P, _P, C.c_int64, _P]),
+            "orc_sample_outcomes": (C.c_int32, [_P, _P, _P, C.c_int64, C.c_int32, _P, _P, _P]),
             "orc_diag_gauss": (C.c_int32, [_P, _P, C.c_int32, _P]),
             "orc_apply": (C.c_int32, [_P, _P, _P, _P]),
             "orc_apply_gauss": (C.c_int32, [_P, _P, _P, _P, C.c_int32, _P]),
@@ -290,6 +294,37 @@ class OracleScene:
         D = np.empty(self.n_params)
         lib().orc_diag(self._h, _ptr(D))
         return D
+
+    def set_flips(self, idx, masks):
+        """Bit k of masks[j] inverts the k-th near decision of sample idx[j]
+        (clamp, skip, termination per entry, in list order)."""
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+        masks = np.ascontiguousarray(masks, dtype=np.uint32)
+        assert idx.shape == masks.shape
+        if lib().orc_set_flips(self._h, _ptr(idx), _ptr(masks), len(idx)) != 0:
+            raise ValueError("sample index out of range")
+
+    def clear_flips(self):
+        lib().orc_clear_flips(self._h)
+
+    def near_counts(self, idx):
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+        out = np.zeros(len(idx), np.int32)
+        lib().orc_near_counts(self._h, _ptr(idx), len(idx), _ptr(out))
+        return out
+
+    def sample_outcomes(self, v, idx, max_bits=4):
+        """(n_near [n], rgb [n, 2^max_bits, 3], u [n, 2^max_bits, 3]): the
+        colour and J v of each sample under every mask of its near decisions
+        (NaN beyond 2^min(n_near, max_bits))."""
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+        M = 1 << max_bits
+        nn = np.zeros(len(idx), np.int32)
+        rgb = np.empty((len(idx), M, 3))
+        u = np.empty((len(idx), M, 3))
+        lib().orc_sample_outcomes(self._h, _ptr(v), _ptr(idx), len(idx), int(max_bits), _ptr(nn), _ptr(rgb), _ptr(u))
+        return nn, rgb, u
 
     def diag_magnitude(self):
         """Per entry of diag(J^T W J): the sum over rows of w (sum_f |dC/df

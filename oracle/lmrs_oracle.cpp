@@ -391,24 +391,50 @@ void preprocess(const Gauss<S>& g, int deg, const CamD& c, Feat<S>& f) {
 // --------------------------------------------------------------------------
 inline bool near_rel(double v, double thr, double m) { return std::fabs(v - thr) <= m * thr; }
 
+// A decision on a value within a relative margin of its threshold is "near":
+// an implementation in other precision may take it the other way, and both
+// outcomes are correct.  flip: bit k inverts the k-th near decision met along
+// the list (the alpha clamp, the alpha skip and the termination test, in that
+// order per entry), so the oracle can follow the outcome another
+// implementation took; *n_near receives the number of near decisions met.
+struct Decisions {
+    uint32_t flip;
+    int k = 0;
+    explicit Decisions(uint32_t f) : flip(f) {}
+    // the outcome of a test whose plain result is `plain`, near its threshold or not
+    bool take(bool plain, bool near) {
+        if (!near) return plain;
+        const bool inv = k < 32 && ((flip >> k) & 1u);
+        ++k;
+        return inv ? !plain : plain;
+    }
+};
+
 template <class S>
 void composite(double pcx, double pcy, const int32_t* ids, int len, const Feat<S>* F,
-               double ma, double mT, S C[3], int* consumed, int* flag, int* n_comp = nullptr) {
+               double ma, double mT, S C[3], int* consumed, int* flag, int* n_comp = nullptr, uint32_t flip = 0u,
+               int* n_near = nullptr) {
     S T = S(1.0);
     C[0] = C[1] = C[2] = S(0.0);
     int used = len, fl = 0, nc = 0;
+    Decisions dec(flip);
     for (int k = 0; k < len; ++k) {
         const Feat<S>& f = F[ids[k]];
         S dx = f.mu[0] - S(pcx), dy = f.mu[1] - S(pcy);
         S power = S(-0.5) * (f.con[0] * dx * dx + f.con[2] * dy * dy) - f.con[1] * dx * dy;
         S alpha = f.o * exp(power);
-        if (near_rel(val(alpha), kAlphaMin, ma)) fl |= 1;
-        if (near_rel(val(alpha), kAlphaMax, ma)) fl |= 2;
-        if (val(alpha) > kAlphaMax) alpha = S(kAlphaMax);
-        if (val(alpha) < kAlphaMin) continue;
+        const double av = val(alpha);
+        const bool nmax = near_rel(av, kAlphaMax, ma), nmin = near_rel(av, kAlphaMin, ma);
+        if (nmin) fl |= 1;
+        if (nmax) fl |= 2;
+        const bool clamp = dec.take(av > kAlphaMax, nmax);
+        const bool skip = dec.take(av < kAlphaMin, nmin);
+        if (clamp) alpha = S(kAlphaMax);
+        if (skip) continue;
         S Tn = T * (S(1.0) - alpha);
-        if (near_rel(val(Tn), kTMin, mT)) fl |= 4;
-        if (val(Tn) < kTMin) { used = k; break; }
+        const bool nT = near_rel(val(Tn), kTMin, mT);
+        if (nT) fl |= 4;
+        if (dec.take(val(Tn) < kTMin, nT)) { used = k; break; }
         for (int ch = 0; ch < 3; ++ch) C[ch] = C[ch] + f.col[ch] * alpha * T;
         T = Tn;
         ++nc;
@@ -416,6 +442,7 @@ void composite(double pcx, double pcy, const int32_t* ids, int len, const Feat<S
     if (consumed) *consumed = used;
     if (flag) *flag = fl;
     if (n_comp) *n_comp = nc;
+    if (n_near) *n_near = dec.k;
 }
 
 // Per-pixel derivatives of the three output channels with respect to the
@@ -428,21 +455,24 @@ struct Contrib {
 };
 
 void pixel_feature_jacobian(double pcx, double pcy, const int32_t* ids, int len, const Feat<double>* F,
-                            std::vector<Contrib>& out, double Cfinal[3]) {
+                            std::vector<Contrib>& out, double Cfinal[3], double ma, double mT, uint32_t flip) {
     struct Rec { int id; double alpha, T, g, dx, dy; bool aclamp; };
     std::vector<Rec> recs;
     double T = 1.0, C[3] = {0.0, 0.0, 0.0};
+    Decisions dec(flip);
     for (int k = 0; k < len; ++k) {
         const Feat<double>& f = F[ids[k]];
         double dx = f.mu[0] - pcx, dy = f.mu[1] - pcy;
         double power = -0.5 * (f.con[0] * dx * dx + f.con[2] * dy * dy) - f.con[1] * dx * dy;
         double g = std::exp(power);
         double alpha = f.o * g;
-        bool aclamp = false;
-        if (alpha > kAlphaMax) { alpha = kAlphaMax; aclamp = true; }
-        if (alpha < kAlphaMin) continue;
+        // the same decisions, in the same order, as composite()
+        const bool aclamp = dec.take(alpha > kAlphaMax, near_rel(alpha, kAlphaMax, ma));
+        const bool skip = dec.take(alpha < kAlphaMin, near_rel(alpha, kAlphaMin, ma));
+        if (aclamp) alpha = kAlphaMax;
+        if (skip) continue;
         double Tn = T * (1.0 - alpha);
-        if (Tn < kTMin) break;
+        if (dec.take(Tn < kTMin, near_rel(Tn, kTMin, mT))) break;
         for (int ch = 0; ch < 3; ++ch) C[ch] += f.col[ch] * alpha * T;
         recs.push_back(Rec{ids[k], alpha, T, g, dx, dy, aclamp});
         T = Tn;
@@ -537,6 +567,7 @@ struct orc_scene {
     std::vector<double> w;             // [S]
     std::vector<int32_t> spx, spy, sslot, stile;  // per sample
     std::vector<uint8_t> sflag;                   // per sample: an importance draw near a decision
+    std::vector<uint32_t> flip;                   // per sample: near decisions taken the other way (Decisions)
     std::vector<double> ssim_s, ssim_d;           // [S][3] SSIM residual and its own-pixel derivative
     std::vector<uint8_t> ssim_flag;               // per sample: a flagged pixel inside its SSIM window
     std::vector<int64_t> ranges;       // [nv*T + 1]
@@ -822,7 +853,7 @@ void jvp_sample(const orc_scene* s, const std::vector<Feat<Dual>>& fd, int64_t i
     const int32_t* ids = s->list(slot, s->stile[i], &len);
     Dual C[3];
     composite<Dual>(s->spx[i] + 0.5, s->spy[i] + 0.5, ids, len, fd.data() + (size_t)slot * s->G,
-                    s->cfg.margin_alpha, s->cfg.margin_T, C, nullptr, nullptr);
+                    s->cfg.margin_alpha, s->cfg.margin_T, C, nullptr, nullptr, nullptr, s->flip[i]);
     for (int ch = 0; ch < 3; ++ch) u[ch] = C[ch].d;
 }
 
@@ -834,7 +865,8 @@ void for_each_contribution(const orc_scene* s, int64_t i, Fn fn) {
     const int32_t* ids = s->list(slot, s->stile[i], &len);
     std::vector<Contrib> cs;
     double Cf[3];
-    pixel_feature_jacobian(s->spx[i] + 0.5, s->spy[i] + 0.5, ids, len, s->feat.data() + (size_t)slot * s->G, cs, Cf);
+    pixel_feature_jacobian(s->spx[i] + 0.5, s->spy[i] + 0.5, ids, len, s->feat.data() + (size_t)slot * s->G, cs, Cf,
+                           s->cfg.margin_alpha, s->cfg.margin_T, s->flip[i]);
     for (const Contrib& c : cs) fn(slot, c);
 }
 
@@ -1020,6 +1052,7 @@ int32_t orc_begin_step(orc_scene* s, const int32_t* view_ids, int32_t n_views, i
     compute_features(s);
     if (s->cfg.sample_dist != 0) make_samples_importance(s);  // needs the lists and features
     else s->sflag.assign(s->off.size(), 0);
+    s->flip.assign(s->off.size(), 0u);
     if (s->cfg.ssim_weight > 0.0) make_ssim(s);
     else {
         s->ssim_s.clear();
@@ -1094,14 +1127,76 @@ int32_t orc_get_features(const orc_scene* s, int32_t slot, double* feat) {
     return 0;
 }
 
-static void render_one(const orc_scene* s, int64_t i, double* rgb, uint8_t* flag) {
+static void render_one(const orc_scene* s, int64_t i, double* rgb, uint8_t* flag, int* n_near = nullptr) {
     int slot = s->sslot[i], len, fl;
     const int32_t* ids = s->list(slot, s->stile[i], &len);
     double C[3];
     composite<double>(s->spx[i] + 0.5, s->spy[i] + 0.5, ids, len, s->feat.data() + (size_t)slot * s->G,
-                      s->cfg.margin_alpha, s->cfg.margin_T, C, nullptr, &fl);
+                      s->cfg.margin_alpha, s->cfg.margin_T, C, nullptr, &fl, nullptr, s->flip[i], n_near);
     for (int ch = 0; ch < 3; ++ch) rgb[ch] = C[ch];
     if (flag) *flag = (uint8_t)fl;
+}
+
+int32_t orc_set_flips(orc_scene* s, const int64_t* idx, const uint32_t* masks, int64_t n) {
+    for (int64_t k = 0; k < n; ++k) {
+        if (idx[k] < 0 || idx[k] >= s->S()) return 1;
+        s->flip[idx[k]] = masks[k];
+    }
+    return 0;
+}
+
+int32_t orc_clear_flips(orc_scene* s) {
+    std::fill(s->flip.begin(), s->flip.end(), 0u);
+    return 0;
+}
+
+int32_t orc_sample_outcomes(const orc_scene* s, const double* v, const int64_t* idx, int64_t n, int32_t max_bits,
+                            int32_t* n_near, double* rgb, double* u) {
+    if (max_bits < 0 || max_bits > 8) return 1;
+    const int64_t M = (int64_t)1 << max_bits;
+    std::vector<Feat<Dual>> fd;
+    dual_features(s, v, fd);
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t k = 0; k < n; ++k) {
+        const int64_t i = idx[k];
+        int slot = s->sslot[i], len, nn = 0;
+        const int32_t* ids = s->list(slot, s->stile[i], &len);
+        const double pcx = s->spx[i] + 0.5, pcy = s->spy[i] + 0.5;
+        double C[3];
+        composite<double>(pcx, pcy, ids, len, s->feat.data() + (size_t)slot * s->G, s->cfg.margin_alpha,
+                          s->cfg.margin_T, C, nullptr, nullptr, nullptr, 0u, &nn);
+        n_near[k] = nn;
+        const int64_t mk = (int64_t)1 << std::min(nn, (int)max_bits);
+        for (int64_t m = 0; m < M; ++m) {
+            double* r = rgb + 3 * (k * M + m);
+            double* d = u + 3 * (k * M + m);
+            if (m >= mk) {
+                for (int ch = 0; ch < 3; ++ch) r[ch] = d[ch] = std::nan("");
+                continue;
+            }
+            composite<double>(pcx, pcy, ids, len, s->feat.data() + (size_t)slot * s->G, s->cfg.margin_alpha,
+                              s->cfg.margin_T, C, nullptr, nullptr, nullptr, (uint32_t)m);
+            Dual Cd[3];
+            composite<Dual>(pcx, pcy, ids, len, fd.data() + (size_t)slot * s->G, s->cfg.margin_alpha,
+                            s->cfg.margin_T, Cd, nullptr, nullptr, nullptr, (uint32_t)m);
+            for (int ch = 0; ch < 3; ++ch) {
+                r[ch] = C[ch];
+                d[ch] = Cd[ch].d;
+            }
+        }
+    }
+    return 0;
+}
+
+int32_t orc_near_counts(const orc_scene* s, const int64_t* idx, int64_t n, int32_t* counts) {
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t k = 0; k < n; ++k) {
+        double c[3];
+        int nn = 0;
+        render_one(s, idx[k], c, nullptr, &nn);
+        counts[k] = nn;
+    }
+    return 0;
 }
 
 int32_t orc_render_samples(const orc_scene* s, double* rgb, double* resid, uint8_t* flags) {

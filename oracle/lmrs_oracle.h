@@ -88,6 +88,24 @@ int32_t orc_get_lists(const orc_scene* s, int32_t* ranges, int32_t* ids);
 int32_t orc_get_geom(const orc_scene* s, int32_t slot, int32_t* vis, float* depth, int32_t* rect);
 int32_t orc_get_features(const orc_scene* s, int32_t slot, double* feat);
 
+/* Per-sample outcomes of near decisions (reset by orc_begin_step).  A test on
+ * a value within a relative margin of its threshold (margin_alpha for the
+ * alpha skip at 1/255 and the clamp at 0.99, margin_T for the termination at
+ * 1e-4) is "near": an FP32 evaluation may take it either way.  Bit k of a
+ * sample's mask inverts the k-th near decision met along its list (per
+ * entry: clamp, skip, termination), in every sample-level computation
+ * (render, J v, J^T u, diag, right-hand side, operator).  orc_near_counts
+ * gives the number of near decisions each sample meets under its mask. */
+int32_t orc_set_flips(orc_scene* s, const int64_t* idx, const uint32_t* masks, int64_t n);
+int32_t orc_clear_flips(orc_scene* s);
+int32_t orc_near_counts(const orc_scene* s, const int64_t* idx, int64_t n, int32_t* counts);
+/* Every outcome of the near decisions of samples idx[0..n): n_near[k] as in
+ * orc_near_counts (masks ignored); for m < 2^min(n_near[k], max_bits) the
+ * colour (rgb) and J v (u, tangent v) of sample idx[k] with mask m at
+ * [(k 2^max_bits + m) 3 + ch], NaN for the other m.  max_bits <= 8. */
+int32_t orc_sample_outcomes(const orc_scene* s, const double* v, const int64_t* idx, int64_t n, int32_t max_bits,
+                            int32_t* n_near, double* rgb, double* u);
+
 int32_t orc_render_samples(const orc_scene* s, double* rgb, double* resid, uint8_t* flags);
 int32_t orc_render_samples_subset(const orc_scene* s, const int64_t* idx, int64_t n,
                                   double* rgb, uint8_t* flags);

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB_NAME = "liblmrs.so"
 SOURCES = ["scene.cu", "preprocess.cu", "binning.cu", "raster.cu", "cg.cu", "noalloc.cu", "autotune.cu",
-           "server.cu", "view_sampler.cu"]
+           "server.cu", "view_sampler.cu", "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -139,25 +139,6 @@ __global__ void __launch_bounds__(kVecBlock) k_cg_update(Ctx c, int iter, const 
     }
 }
 
-// p = z + beta p (beta = r_{i+1}^T z_{i+1} / r_i^T z_i, 0 before the first
-// iteration so that p_0 = z_0).
-__global__ void __launch_bounds__(kVecBlock) k_cg_direction(Ctx c, const float* z, float* p) {
-    const float beta = (float)c.sc->beta;
-    const Span s = span(c.P, true);
-    const float4* z4 = reinterpret_cast<const float4*>(z);
-    float4* p4 = reinterpret_cast<float4*>(p);
-    for (long long j = s.first; j < s.n4; j += s.stride) {
-        const float4 a = z4[j];
-        float4 b = p4[j];
-        b.x = a.x + beta * b.x;
-        b.y = a.y + beta * b.y;
-        b.z = a.z + beta * b.z;
-        b.w = a.w + beta * b.w;
-        p4[j] = b;
-    }
-    for (long long j = s.lo + s.first; j < s.hi; j += s.stride) p[j] = z[j] + beta * p[j];
-}
-
 // max |x| over the SH degree-0 entries (the colour parameters of Sec. 4.5).
 __global__ void __launch_bounds__(kVecBlock) k_max_dc(Ctx c, const float* x) {
     float m = 0.f;
@@ -178,12 +159,15 @@ __device__ __forceinline__ double step_size(long long lm_step, double lr_warm, d
     return fmin(lr_cap, color_bound / m);
 }
 
-// beta <- beta - eta x
+// beta <- beta - eta x; a solve that met a non-finite or non-positive
+// curvature (numeric_error) leaves the parameters as they were, eta = 0
 __global__ void __launch_bounds__(kVecBlock) k_lm_update(Ctx c, long long lm_step, double lr_warm, double lr_cap,
                                                         double color_bound, int warm_iters, const float* x,
                                                         float* params) {
-    const double eta = step_size(lm_step, lr_warm, lr_cap, color_bound, warm_iters, c.sc->max_dc_bits);
+    const bool failed = c.sc->numeric_error != 0u;
+    const double eta = failed ? 0.0 : step_size(lm_step, lr_warm, lr_cap, color_bound, warm_iters, c.sc->max_dc_bits);
     if (blockIdx.x == 0 && threadIdx.x == 0) c.sc->eta = eta;
+    if (failed) return;
     const float e = (float)eta;
     for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < c.P; j += (long long)gridDim.x * blockDim.x)
         params[j] -= e * x[j];
@@ -287,9 +271,11 @@ __global__ void __launch_bounds__(kBatchBlock) kb_lm_update(BatchTables t) {
         const int4 ch = t.vchunks[k];
         const Ctx& c = t.ctxs[ch.x];
         const BatchVec& bv = t.vecs[ch.x];
-        const double eta = step_size(bv.lm_step, bv.lr_warm, bv.lr_cap, bv.color_bound, bv.warm_iters,
-                                     c.sc->max_dc_bits);
+        const bool failed = c.sc->numeric_error != 0u;
+        const double eta = failed ? 0.0 : step_size(bv.lm_step, bv.lr_warm, bv.lr_cap, bv.color_bound,
+                                                    bv.warm_iters, c.sc->max_dc_bits);
         if (ch.y == 0 && threadIdx.x == 0) c.sc->eta = eta;
+        if (failed) continue;  // the scene's parameters stay as they were
         const float e = (float)eta;
         for (long long j = ch.y + threadIdx.x; j < ch.z; j += kBatchBlock) bv.params[j] -= e * bv.x[j];
     }
@@ -323,9 +309,6 @@ void launch_cg_update(const Ctx& c, int iter, const float* p, const float* Ap, c
     const bool vec = aligned16(p) && aligned16(Ap) && aligned16(minv) && aligned16(x) && aligned16(r) && aligned16(z);
     if (vec) LMRS_LAUNCH(k_cg_update<true>, vec_grid(c.P / 4 + 1), kVecBlock, 0, st, c, iter, p, Ap, minv, x, r, z);
     else LMRS_LAUNCH(k_cg_update<false>, vec_grid(c.P), kVecBlock, 0, st, c, iter, p, Ap, minv, x, r, z);
-}
-void launch_cg_direction(const Ctx& c, const float* z, float* p, cudaStream_t st) {
-    LMRS_LAUNCH(k_cg_direction, vec_grid(c.P / 4 + 1), kVecBlock, 0, st, c, z, p);
 }
 void launch_max_dc(const Ctx& c, const float* x, cudaStream_t st) {
     LMRS_LAUNCH(k_max_dc, vec_grid(c.G), kVecBlock, 0, st, c, x);

@@ -19,7 +19,7 @@ constexpr int kRecF4 = 6;                   // float4 per staged (view, Gaussian
 constexpr int kPrimF4 = 3;                  // float4 of a pair's primal 2D features
 constexpr int kTanF4 = 3;                   // float4 of a pair's 2D feature tangent
 constexpr int kCotF = 12;                   // floats per (view, Gaussian) cotangent slot (9 used)
-constexpr int kGramF = 44;                  // floats per (view, Gaussian) Gram slot (42 used)
+constexpr int kDiagF = 16;                  // floats per (view, Gaussian) slot of diag(J^T W J) rows (14 used)
 constexpr int kMaxPartials = 4096;          // block partials of the FP64 reductions
 constexpr int kGaussF4 = 9;                  // float4 planes of the per-Gaussian cache
 // float4 planes of the per-pair Jacobian cache for SH degree 0..3: screen mean
@@ -56,6 +56,7 @@ struct Scalars {
     double loss_num;  // sum w |r|^2
     double loss_den;  // sum 3 w
     unsigned long long n_eval;  // (sample, Gaussian) pairs composited before termination
+    unsigned long long n_walk;  // compact-list entries over all work items (walked by the derivative kernels)
     double eta;
     unsigned int max_dc_bits;  // bits of max |x_dc| (non-negative float)
     unsigned int pad1;
@@ -92,7 +93,7 @@ struct Ctx {
     unsigned long long* n_entries;  // bound on the tile-list entries: band rows x rectangle width
     unsigned long long* n_rowent;   // sum over visible pairs of the rectangle rows band_meets keeps
     float* cot;             // kCotF floats
-    float* gram;            // kGramF floats
+    float* dslot;           // kDiagF floats: the pair's share of diag(J^T W J) (k_diag)
     // binning
     unsigned int* keys;     // slot * T + tile of each list entry
     unsigned int* ids;
@@ -172,6 +173,9 @@ void launch_prep_fwd(const Ctx& c, cudaStream_t st);
 // tangent features of v (P floats) for every visible pair; clears the
 // pairs' cotangent slots
 void launch_prep_jvp(const Ctx& c, const float* v, cudaStream_t st);
+// the same for the PCG direction p <- z + beta p (beta from the device
+// scalars), formed and written back to p in the same pass
+void launch_prep_jvp_direction(const Ctx& c, const float* z, float* p, cudaStream_t st);
 // g = J^T u chained from the cotangent slots (+ lambda damping of v if v).
 // With dot, pAp = v^T g in FP64 and alpha = rz / pAp on the device.
 void launch_prep_vjp(const Ctx& c, float* g, const float* v, const float* D, bool dot, cudaStream_t st);
@@ -227,9 +231,10 @@ void launch_raster_jvp(const Ctx& c, float* u, cudaStream_t st);
 void launch_raster_vjp(const Ctx& c, const float* u, cudaStream_t st);
 // Fused J^T W J: JVP pass then VJP pass per warp item.
 void launch_raster_jtj(const Ctx& c, cudaStream_t st);
-void launch_raster_gram(const Ctx& c, cudaStream_t st);
-// k_gram that also back-scatters the right-hand side's cotangents into c.cot
-void launch_raster_gram_rhs(const Ctx& c, cudaStream_t st);
+// Per-pair rows of diag(J^T W J) into c.dslot (cleared by the caller).
+void launch_raster_diag(const Ctx& c, cudaStream_t st);
+// k_diag that also back-scatters the right-hand side's cotangents into c.cot
+void launch_raster_diag_rhs(const Ctx& c, cudaStream_t st);
 // Longest-first order of the work items by the traversal lengths the forward
 // render recorded: sorted[k] = work[order[k]].  Scratch: keys/vals and their
 // alternates (nwork each) and radix_tmp_bytes(nwork).
@@ -242,8 +247,6 @@ void launch_cg_init(const Ctx& c, const float* b, const float* minv, float* x, f
                     cudaStream_t st);
 void launch_cg_update(const Ctx& c, int iter, const float* p, const float* Ap, const float* minv, float* x, float* r,
                       float* z, cudaStream_t st);
-// p = z + beta p with beta from the device scalars (Alg. 1, last loop line)
-void launch_cg_direction(const Ctx& c, const float* z, float* p, cudaStream_t st);
 void launch_max_dc(const Ctx& c, const float* x, cudaStream_t st);
 void launch_lm_update(const Ctx& c, long long lm_step, double lr_warm, double lr_cap, double color_bound,
                       int warm_iters, const float* x, float* params, cudaStream_t st);

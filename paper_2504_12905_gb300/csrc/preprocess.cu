@@ -592,12 +592,10 @@ __device__ __forceinline__ void load_geo_tangent(const float* v, int G, int g, G
 // dsh: the Gaussian's 3K SH tangent values (global memory, or a staged copy
 // in shared memory).
 template <int DEG>
-__device__ __forceinline__ void prep_jvp_gauss(const Ctx& c, const float* v, const float* dsh, int g, int slot0,
+__device__ __forceinline__ void prep_jvp_gauss(const Ctx& c, const GTan& d, const float* dsh, int g, int slot0,
                                                int dslot) {
     using L = Jac<DEG>;
     constexpr int K = Sh<DEG>::K;
-    GTan d;
-    load_geo_tangent(v, c.G, g, d);
     const float u[10] = {d.X[0], d.X[1], d.X[2], d.ls[0], d.ls[1], d.ls[2], d.q[0], d.q[1], d.q[2], d.q[3]};
     float X[3] = {0.f, 0.f, 0.f};
     if (DEG > 0) load_mean(c.params, g, X);
@@ -644,23 +642,106 @@ __device__ __forceinline__ void prep_jvp_gauss(const Ctx& c, const float* v, con
 
 // Blocks of 32 Gaussians (lanes) x kJvpWarps warps, warp w taking views w,
 // w + kJvpWarps, ...: several warps per Gaussian for latency hiding.  The
-// block's 32 x 3K SH tangent values are one contiguous run of v: the block
-// stages them once, coalesced, into shared memory (row stride 3K + 1, odd,
-// so the lanes' reads of their own rows hit distinct banks).
+// block's tangent values are contiguous runs of the P-vector (32 x 3K SH
+// values; 3, 3, 4 and 1 geometric values per Gaussian in the four geometric
+// groups): the block stages them once, coalesced, into shared memory (row
+// strides 3K + 1 and 11, odd, so the lanes' reads of their own rows hit
+// distinct banks).  With z given, the staged tangent is the PCG direction
+// p <- z + beta p (Alg. 1, beta from the device scalars), written back to p
+// by the thread that read it; otherwise it is v = p as given.
 constexpr int kJvpWarps = 4;
 
+// Position in the P-vector, and in the staging area, of the i-th of the
+// 11 ng geometric values of Gaussians g0 .. g0 + ng - 1 (their runs in the
+// means, log-scale, quaternion and opacity groups, in that order).
+__device__ __forceinline__ void geo_slot(long long G, int g0, int ng, int i, long long& idx, int& at) {
+    int row, k;
+    if (i < 3 * ng) {
+        idx = 3ll * g0 + i, row = i / 3, k = i % 3;
+    } else if (i < 6 * ng) {
+        const int o = i - 3 * ng;
+        idx = 3 * G + 3ll * g0 + o, row = o / 3, k = 3 + o % 3;
+    } else if (i < 10 * ng) {
+        const int o = i - 6 * ng;
+        idx = 6 * G + 4ll * g0 + o, row = o / 4, k = 6 + o % 4;
+    } else {
+        const int o = i - 10 * ng;
+        idx = 10 * G + g0 + o, row = o, k = 10;
+    }
+    at = row * 11 + k;
+}
+
 template <int DEG>
-__global__ void __launch_bounds__(32 * kJvpWarps) k_prep_jvp(Ctx c, const float* v) {
+__global__ void __launch_bounds__(32 * kJvpWarps) k_prep_jvp(Ctx c, const float* __restrict__ z, float* p) {
     constexpr int K3 = 3 * Sh<DEG>::K;
+    constexpr int kThreads = 32 * kJvpWarps;
+    constexpr int kShPer = (32 * K3 + kThreads - 1) / kThreads;  // SH values per thread
+    constexpr int kGeoPer = (32 * 11 + kThreads - 1) / kThreads;
     __shared__ float s_dsh[32 * (K3 + 1)];
+    __shared__ float s_geo[32 * 11];
     const int g0 = blockIdx.x * 32;
     const int lane = threadIdx.x & 31;
-    const float* src = v + 11ll * c.G + (long long)g0 * K3;
-    const int n = min(32, c.G - g0) * K3;
-    for (int i = threadIdx.x; i < n; i += 32 * kJvpWarps) s_dsh[(i / K3) * (K3 + 1) + i % K3] = src[i];
+    const int ng = min(32, c.G - g0);
+    const float beta = z ? (float)c.sc->beta : 0.f;
+    const long long G = c.G;
+    const long long sh0 = 11 * G + (long long)g0 * K3;
+    const int nsh = ng * K3, ngeo = 11 * ng;
+    // every load of the thread first, then the direction and the stores
+    float vs[kShPer], vg[kGeoPer], zs[kShPer], zg[kGeoPer];
+    long long gidx[kGeoPer];
+    int gat[kGeoPer];
+#pragma unroll
+    for (int k = 0; k < kShPer; ++k) {
+        const int i = threadIdx.x + k * kThreads;
+        vs[k] = i < nsh ? p[sh0 + i] : 0.f;
+        zs[k] = (z && i < nsh) ? z[sh0 + i] : 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < kGeoPer; ++k) {
+        const int i = threadIdx.x + k * kThreads;
+        gidx[k] = 0;
+        gat[k] = 0;
+        if (i < ngeo) geo_slot(G, g0, ng, i, gidx[k], gat[k]);
+        vg[k] = i < ngeo ? p[gidx[k]] : 0.f;
+        zg[k] = (z && i < ngeo) ? z[gidx[k]] : 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < kShPer; ++k) {
+        const int i = threadIdx.x + k * kThreads;
+        if (i >= nsh) continue;
+        float val = vs[k];
+        if (z) {
+            val = zs[k] + beta * val;
+            p[sh0 + i] = val;
+        }
+        s_dsh[(i / K3) * (K3 + 1) + i % K3] = val;
+    }
+#pragma unroll
+    for (int k = 0; k < kGeoPer; ++k) {
+        const int i = threadIdx.x + k * kThreads;
+        if (i >= ngeo) continue;
+        float val = vg[k];
+        if (z) {
+            val = zg[k] + beta * val;
+            p[gidx[k]] = val;
+        }
+        s_geo[gat[k]] = val;
+    }
     __syncthreads();
     const int g = g0 + lane;
-    if (g < c.G) prep_jvp_gauss<DEG>(c, v, s_dsh + lane * (K3 + 1), g, threadIdx.x >> 5, kJvpWarps);
+    if (g < c.G) {
+        const float* sg = s_geo + lane * 11;
+        GTan d;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            d.X[k] = sg[k];
+            d.ls[k] = sg[3 + k];
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) d.q[k] = sg[6 + k];
+        d.th = sg[10];
+        prep_jvp_gauss<DEG>(c, d, s_dsh + lane * (K3 + 1), g, threadIdx.x >> 5, kJvpWarps);
+    }
 }
 
 // The same for every scene of a batch: Gaussian chunks, tangent = the scene's p.
@@ -670,10 +751,13 @@ __global__ void __launch_bounds__(kBatchBlock) kb_prep_jvp(BatchTables t) {
     const int n = t.counts[0];
     for (int k = blockIdx.x; k < n; k += gridDim.x) {
         const int4 ch = t.gchunks[k];
-        for (int g = ch.y + (int)(threadIdx.x & 31); g < ch.z; g += 32)
-            prep_jvp_gauss<DEG>(t.ctxs[ch.x], t.vecs[ch.x].p,
-                                t.vecs[ch.x].p + 11ll * t.ctxs[ch.x].G + (long long)g * 3 * Sh<DEG>::K, g,
-                                threadIdx.x >> 5, kJvpWarps);
+        for (int g = ch.y + (int)(threadIdx.x & 31); g < ch.z; g += 32) {
+            const Ctx& c = t.ctxs[ch.x];
+            const float* v = t.vecs[ch.x].p;
+            GTan d;
+            load_geo_tangent(v, c.G, g, d);
+            prep_jvp_gauss<DEG>(c, d, v + 11ll * c.G + (long long)g * 3 * Sh<DEG>::K, g, threadIdx.x >> 5, kJvpWarps);
+        }
     }
 }
 
@@ -912,8 +996,8 @@ static void prep_fwd_deg(const Ctx& c, cudaStream_t st) {
     LMRS_LAUNCH_AS("k_prep_fwd", k_prep_fwd<DEG>, (unsigned)((n + 127) / 128), 128, 0, st, c);
 }
 template <int DEG>
-static void prep_jvp_deg(const Ctx& c, const float* v, cudaStream_t st) {
-    LMRS_LAUNCH_AS("k_prep_jvp", k_prep_jvp<DEG>, (unsigned)((c.G + 31) / 32), 32 * kJvpWarps, 0, st, c, v);
+static void prep_jvp_deg(const Ctx& c, const float* z, float* p, cudaStream_t st) {
+    LMRS_LAUNCH_AS("k_prep_jvp", k_prep_jvp<DEG>, (unsigned)((c.G + 31) / 32), 32 * kJvpWarps, 0, st, c, z, p);
 }
 template <int DEG>
 static void prep_vjp_deg(const Ctx& c, float* g, const float* v, const float* D, bool dot, cudaStream_t st) {
@@ -940,11 +1024,22 @@ void launch_prep_fwd(const Ctx& c, cudaStream_t st) {
 }
 
 void launch_prep_jvp(const Ctx& c, const float* v, cudaStream_t st) {
+    // read only: k_prep_jvp writes p only when z is given
+    float* p = const_cast<float*>(v);
     switch (c.deg) {
-        case 0: prep_jvp_deg<0>(c, v, st); break;
-        case 1: prep_jvp_deg<1>(c, v, st); break;
-        case 2: prep_jvp_deg<2>(c, v, st); break;
-        default: prep_jvp_deg<3>(c, v, st); break;
+        case 0: prep_jvp_deg<0>(c, nullptr, p, st); break;
+        case 1: prep_jvp_deg<1>(c, nullptr, p, st); break;
+        case 2: prep_jvp_deg<2>(c, nullptr, p, st); break;
+        default: prep_jvp_deg<3>(c, nullptr, p, st); break;
+    }
+}
+
+void launch_prep_jvp_direction(const Ctx& c, const float* z, float* p, cudaStream_t st) {
+    switch (c.deg) {
+        case 0: prep_jvp_deg<0>(c, z, p, st); break;
+        case 1: prep_jvp_deg<1>(c, z, p, st); break;
+        case 2: prep_jvp_deg<2>(c, z, p, st); break;
+        default: prep_jvp_deg<3>(c, z, p, st); break;
     }
 }
 

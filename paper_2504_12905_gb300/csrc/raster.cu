@@ -273,24 +273,24 @@ __device__ __forceinline__ void backward_pass(const Ctx& c, const Pix& p, List L
             // phase A
             for (int jj = 0; jj < m; ++jj) {
                 const int j = h0 + jj;
-                float pb = 0.f, wt = 0.f;
-                if (b + j < lane_end) {
-                    const float4 r0 = sm.rec[j][0], r1 = sm.rec[j][1];
-                    const float dx = r0.x - p.pcx, dy = r0.y - p.pcy;
-                    const float power = -0.5f * (r0.z * dx * dx + r1.x * dy * dy) - r0.w * dx * dy;
-                    const float gval = __expf(power);
-                    const float raw = r1.y * gval;
-                    const float alpha = fminf(kAlphaMax, raw);
-                    if (alpha >= kAlphaMin) {
-                        const float col2 = sm.rec[j][2].x;
-                        const float ucol = ub[0] * r1.z + ub[1] * r1.w + ub[2] * col2;
-                        wt = alpha * T;
-                        s += ucol * wt;
-                        const float abar = T * ucol - __fdividef(S_tot - s, 1.f - alpha);  // 1 - alpha >= 0.01
-                        pb = raw <= kAlphaMax ? abar * raw : 0.f;
-                        T *= 1.f - alpha;
-                    }
-                }
+                const float4 r0 = sm.rec[j][0], r1 = sm.rec[j][1];
+                const float col2 = sm.rec[j][2].x;
+                const float dx = r0.x - p.pcx, dy = r0.y - p.pcy;
+                const float power = -0.5f * (r0.z * dx * dx + r1.x * dy * dy) - r0.w * dx * dy;
+                const float gval = __expf(power);
+                const float raw = r1.y * gval;
+                float alpha = fminf(kAlphaMax, raw);
+                // branch-free: an entry the lane does not composite (past its
+                // stop, or alpha < 1/255) takes alpha = 0, which leaves T and s
+                // unchanged and gives pb = wt = 0
+                const bool on = (b + j < lane_end) && alpha >= kAlphaMin;
+                alpha = on ? alpha : 0.f;
+                const float ucol = ub[0] * r1.z + ub[1] * r1.w + ub[2] * col2;
+                const float wt = alpha * T;
+                s += ucol * wt;
+                const float abar = T * ucol - __fdividef(S_tot - s, 1.f - alpha);  // 1 - alpha >= 0.01
+                const float pb = (on && raw <= kAlphaMax) ? abar * raw : 0.f;
+                T *= 1.f - alpha;
                 sm.bw.pw[jj][lane] = make_float2(pb, wt);
             }
             __syncwarp();
@@ -552,30 +552,28 @@ __global__ void __launch_bounds__(kRasterBlock) k_diag(Ctx c) {
             // phase A
             for (int jj = 0; jj < m; ++jj) {
                 const int j = h0 + jj;
-                float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (b + j < lane_end) {
-                    const float4 r0 = sm.rec[j][0], r1 = sm.rec[j][1];
-                    const float dx = r0.x - p.pcx, dy = r0.y - p.pcy;
-                    const float power = -0.5f * (r0.z * dx * dx + r1.x * dy * dy) - r0.w * dx * dy;
-                    const float gval = __expf(power);
-                    const float raw = r1.y * gval;
-                    const float alpha = fminf(kAlphaMax, raw);
-                    if (alpha >= kAlphaMin) {
-                        const float col[3] = {r1.z, r1.w, sm.rec[j][2].x};
-                        const float q = alpha * T;
-                        const float inv = __fdividef(1.f, 1.f - alpha);  // 1 - alpha >= 0.01
-                        const float rr = raw <= kAlphaMax ? raw : 0.f;
-                        float hr[3];
+                const float4 r0 = sm.rec[j][0], r1 = sm.rec[j][1];
+                const float col[3] = {r1.z, r1.w, sm.rec[j][2].x};
+                const float dx = r0.x - p.pcx, dy = r0.y - p.pcy;
+                const float power = -0.5f * (r0.z * dx * dx + r1.x * dy * dy) - r0.w * dx * dy;
+                const float gval = __expf(power);
+                const float raw = r1.y * gval;
+                float alpha = fminf(kAlphaMax, raw);
+                // branch-free as in backward_pass: alpha = 0 where the lane
+                // does not composite the entry, so q = hr = 0 there
+                const bool on = (b + j < lane_end) && alpha >= kAlphaMin;
+                alpha = on ? alpha : 0.f;
+                const float q = alpha * T;
+                const float inv = __fdividef(1.f, 1.f - alpha);  // 1 - alpha >= 0.01
+                const float rr = (on && raw <= kAlphaMax) ? raw : 0.f;
+                float hr[3];
 #pragma unroll
-                        for (int ch = 0; ch < 3; ++ch) {
-                            acc[ch] += col[ch] * q;
-                            hr[ch] = rr * (T * col[ch] - (Cf[ch] - acc[ch]) * inv);
-                        }
-                        out = make_float4(q, hr[0], hr[1], hr[2]);
-                        T *= 1.f - alpha;
-                    }
+                for (int ch = 0; ch < 3; ++ch) {
+                    acc[ch] += col[ch] * q;
+                    hr[ch] = rr * (T * col[ch] - (Cf[ch] - acc[ch]) * inv);
                 }
-                sm.qh[jj][lane] = out;
+                sm.qh[jj][lane] = make_float4(q, hr[0], hr[1], hr[2]);
+                T *= 1.f - alpha;
             }
             __syncwarp();
             // phase B

@@ -467,8 +467,7 @@ lmrs_status do_cg(lmrs_scene* s, const float* b, float* x, int iters) {
     launch_precond(c, D, minv, s->st);
     launch_cg_init(c, b, minv, x, r, z, p, s->st);
     for (int it = 0; it < iters; ++it) {
-        launch_cg_direction(c, z, p, s->st);             // p = z + beta p
-        launch_prep_jvp(c, p, s->st);                    // tangent features of p
+        launch_prep_jvp_direction(c, z, p, s->st);       // p = z + beta p, tangent features of p
         launch_raster_jtj(c, s->st);                     // J^T W J p into the cotangent slots
         launch_prep_vjp(c, Ap, p, D, true, s->st);       // Ap (+ damping), p^T A p, alpha
         launch_cg_update(c, it, p, Ap, minv, x, r, z, s->st);  // x, r, z, beta

@@ -126,7 +126,12 @@ void finish(lmrs_server* S, Job* j, lmrs_status status, bool converged) {
     S->cv_done.notify_all();
 }
 
-// Admits queued jobs (FIFO) while the budget and the slot count allow.
+double work_estimate(const Job* j) {
+    const int views = j->views_per_step > 0 ? std::min<int>(j->views_per_step, (int)j->cams.size()) : (int)j->cams.size();
+    return (double)j->G * views * j->max_steps;
+}
+
+// Admits queued jobs (policy order) while the budget and the slot count allow.
 void admit(lmrs_server* S) {
     for (;;) {
         Job* j = nullptr;
@@ -135,9 +140,17 @@ void admit(lmrs_server* S) {
             if (S->queue.empty() || (int)S->active.size() >= S->cfg.max_active) return;
             int64_t used = 0;
             for (const Job* a : S->active) used += std::max<int64_t>(a->info.footprint_est, held_bytes(a));
-            Job* head = S->queue.front();
+            auto pick = S->queue.begin();
+            if (S->cfg.policy == 1) {
+                // least estimated work (Gaussians x views per step x max_steps); the
+                // queue is in arrival order, so ties go to the oldest
+                pick = std::min_element(S->queue.begin(), S->queue.end(), [](const Job* a, const Job* b) {
+                    return work_estimate(a) < work_estimate(b);
+                });
+            }
+            Job* head = *pick;
             if (!S->active.empty() && used + head->info.footprint_est > S->cfg.budget_bytes) return;
-            S->queue.pop_front();
+            S->queue.erase(pick);
             j = head;
         }
         const lmrs_status rc = bring_up(j);
@@ -235,14 +248,21 @@ void scheduler(lmrs_server* S) {
                     continue;
                 }
                 const int64_t held = held_bytes(j);
+                bool reached = st[i].loss <= j->target_loss;
+                double full = -1.0;
+                if (S->cfg.stop_full_frame) {
+                    reached = false;
+                    if (st[i].loss <= S->cfg.full_frame_gate * j->target_loss && lmrs_eval_mse(j->scene, &full) == LMRS_OK)
+                        reached = full <= j->target_loss;
+                }
                 std::lock_guard<std::mutex> lk(S->mu);
                 j->info.steps += 1;
                 j->info.loss = st[i].loss;
+                if (full >= 0.0) j->info.full_mse = full;
                 j->info.footprint_peak = std::max(j->info.footprint_peak, held);
-                const bool done = st[i].loss <= j->target_loss || j->info.steps >= j->max_steps;
-                if (done) {
+                if (reached || j->info.steps >= j->max_steps) {
                     retire.push_back(j);
-                    conv.push_back(st[i].loss <= j->target_loss);
+                    conv.push_back(reached);
                 }
             }
         }
@@ -300,11 +320,13 @@ extern "C" {
 
 lmrs_status lmrs_server_create(const lmrs_server_config* cfg, lmrs_server** out) {
     if (!cfg || !out || cfg->budget_bytes <= 0 || cfg->max_active < 1 || cfg->max_active > 1024 ||
-        cfg->setup_threads < 1)
+        cfg->setup_threads < 1 || cfg->policy < 0 || cfg->policy > 1 || cfg->stop_full_frame < 0 ||
+        cfg->stop_full_frame > 1)
         return LMRS_ERR_INVALID_ARG;
     lmrs_server* S = new lmrs_server();
     S->cfg = *cfg;
     if (!(S->cfg.tiles_per_pair > 0.0)) S->cfg.tiles_per_pair = 10.0;
+    if (!(S->cfg.full_frame_gate > 0.0)) S->cfg.full_frame_gate = 1.25;
     if (cudaGetDevice(&S->device) != cudaSuccess) {
         cudaGetLastError();
         delete S;
@@ -342,6 +364,7 @@ lmrs_status lmrs_server_submit(lmrs_server* S, const lmrs_config* cfg, int64_t n
     j->info.state = LMRS_JOB_QUEUED;
     j->info.t_admit = -1.0;
     j->info.t_done = -1.0;
+    j->info.full_mse = -1.0;
     j->info.footprint_est = lmrs_footprint_bytes(cfg, n_gauss, n_cams, cams_host[0].width, cams_host[0].height,
                                                  views_per_step, S->cfg.tiles_per_pair);
     if (j->info.footprint_est > S->cfg.budget_bytes) return LMRS_ERR_BUDGET;

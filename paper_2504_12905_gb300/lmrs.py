@@ -64,12 +64,14 @@ class StepStats(C.Structure):
 
 class ServerConfig(C.Structure):
     _fields_ = [("budget_bytes", C.c_int64), ("max_active", C.c_int32), ("setup_threads", C.c_int32),
-                ("tiles_per_pair", C.c_double)]
+                ("tiles_per_pair", C.c_double), ("policy", C.c_int32), ("stop_full_frame", C.c_int32),
+                ("full_frame_gate", C.c_double)]
 
 
 class JobInfo(C.Structure):
     _fields_ = [("state", C.c_int32), ("status", C.c_int32), ("converged", C.c_int32), ("steps", C.c_int32),
-                ("loss", C.c_double), ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double),
+                ("loss", C.c_double), ("full_mse", C.c_double), ("t_submit", C.c_double), ("t_admit", C.c_double),
+                ("t_done", C.c_double),
                 ("footprint_est", C.c_int64), ("footprint_peak", C.c_int64)]
 
 
@@ -419,8 +421,10 @@ def lmrs_batch_scene_status(batch, i):
     return int(lib().lmrs_batch_scene_status(batch, int(i)))
 
 
-def lmrs_server_create(budget_bytes, max_active=64, setup_threads=8, tiles_per_pair=0.0):
-    cfg = ServerConfig(int(budget_bytes), int(max_active), int(setup_threads), float(tiles_per_pair))
+def lmrs_server_create(budget_bytes, max_active=64, setup_threads=8, tiles_per_pair=0.0, policy=0,
+                       stop_full_frame=0, full_frame_gate=0.0):
+    cfg = ServerConfig(int(budget_bytes), int(max_active), int(setup_threads), float(tiles_per_pair), int(policy),
+                       int(stop_full_frame), float(full_frame_gate))
     h = _P()
     _check(lib().lmrs_server_create(C.byref(cfg), C.byref(h)))
     return h.value

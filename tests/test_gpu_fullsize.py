@@ -38,7 +38,12 @@ def full(request):
     pair = Pair(sc, tgt, sample_frac=frac, lambda_=0.1, damping_mode=0, cg_iters=8, seed=0x5EED)
     views = syn.view_subset(np.random.default_rng(77), len(sc.cams), nviews)  # the first benchmarked view set
     pair.begin(list(views), step=3)
-    pair.lmrs.lmrs_render(pair.gpu.h)
+    # the oracle follows the device's outcome at its flagged samples
+    # (gpu_common.adopt_device_decisions): every comparison below is exact
+    flagged, flipped, worst = pair.adopt()
+    print(f"{request.param}: {flagged} of {pair.S} samples flagged, {flipped} taken the other way, "
+          f"worst score {worst:.3f}")
+    assert worst <= 1.0
     rng = np.random.default_rng(2)
     pair.sample_idx = np.sort(rng.choice(pair.S, 4096, replace=False)).astype(np.int64)
     pair.gids = np.sort(rng.choice(sc.n_gauss, 256, replace=False)).astype(np.int32)
@@ -87,22 +92,23 @@ def test_sampled_residuals_and_jvp(full):
     full.lmrs.lmrs_render(full.gpu.h, None, resid)
     r = full.host(resid).reshape(-1, 3)[full.sample_idx]
     rgb_ref, fl = full.orc.render_samples_subset(full.sample_idx)
-    keep = fl == 0
     # a sample is flagged when any of its alpha or termination tests lies
     # within the oracle's relative margin of the threshold; at these sizes a
-    # sample makes hundreds of alpha tests, so ~1.5-2% are flagged
-    assert keep.mean() > 0.97
+    # sample makes hundreds of alpha tests, so ~1.5-2% are flagged (compared
+    # too: the oracle takes the device's outcome there)
+    assert (fl == 0).mean() > 0.97
     # residual = colour - target: the device's colour at the sampled pixels
     smp = full.orc.samples()
     cams = np.asarray(full.views)[smp["slot"][full.sample_idx]]
     targets = full.targets_np[cams, smp["py"][full.sample_idx], smp["px"][full.sample_idx]].astype(np.float64)
-    np.testing.assert_allclose((r + targets)[keep], rgb_ref[keep], atol=PIX_TOL, rtol=0)
+    np.testing.assert_allclose(r + targets, rgb_ref, atol=PIX_TOL, rtol=0)
     v = np.random.default_rng(3).standard_normal(full.P).astype(np.float32)
     u = full.zeros(full.S * 3)
     full.lmrs.lmrs_jvp(full.gpu.h, full.cuda(v), u)
     u_got = full.host(u).reshape(-1, 3)[full.sample_idx]
     u_ref = full.orc.jvp_subset(v.astype(np.float64), full.sample_idx)
-    err = np.linalg.norm(u_got[keep] - u_ref[keep]) / np.linalg.norm(u_ref[keep])
+    err = np.linalg.norm(u_got - u_ref) / np.linalg.norm(u_ref)
+    print(f"J v of 4096 samples: {err:.3e}")
     assert err <= OP_TOL, err
 
 
@@ -120,33 +126,39 @@ def test_operator_diag_rhs_of_sampled_gaussians(full):
     full.lmrs.lmrs_jtjv(full.gpu.h, full.cuda(v), out)
     got = _blocks(full, full.host(out))
     ref = full.orc.apply_gauss(v64, np.zeros(full.P), full.gids)  # lambda I damping
-    # the samples the oracle flags near a compositing decision may go the
-    # other way in FP32: their whole contribution bounds the extra difference
-    w = full.orc.samples()["w"]
-    u_flag = full.orc.jvp(v64) * (w * full.flags)[:, None]
-    slack = np.linalg.norm(full.orc.vjp_gauss(u_flag, full.gids))
-    err = np.linalg.norm(got - ref)
-    assert err <= OP_TOL * np.linalg.norm(ref) + 3.0 * slack, (err, slack, np.linalg.norm(ref))
-    assert slack <= 0.05 * np.linalg.norm(ref)
+    err_op = np.linalg.norm(got - ref) / np.linalg.norm(ref)
     b = full.zeros(full.P)
     full.lmrs.lmrs_rhs(full.gpu.h, b)
     b_got = _blocks(full, full.host(b))
+    b_ref = _rhs_gauss(full)
+    err_b = np.linalg.norm(b_got - b_ref) / np.linalg.norm(b_ref)
+    print(f"256 Gaussians: diag {err:.3e}, operator {err_op:.3e}, right-hand side {err_b:.3e}")
+    assert err_op <= OP_TOL and err_b <= OP_TOL
+
+
+def _rhs_gauss(full):
+    """J^T W r restricted to the sampled Gaussians' blocks (oracle)."""
     _, r_all, _ = full.orc.render_samples()
-    b_ref = full.orc.vjp_gauss(r_all * w[:, None], full.gids)
-    slack_b = np.linalg.norm(full.orc.vjp_gauss(r_all * (w * full.flags)[:, None], full.gids))
-    assert np.linalg.norm(b_got - b_ref) <= OP_TOL * np.linalg.norm(b_ref) + 3.0 * slack_b
+    w = full.orc.samples()["w"]
+    return full.orc.vjp_gauss(r_all * w[:, None], full.gids)
 
 
 def test_bf16_cache_mode_against_the_oracle(full):
-    """The benchmark's BF16-cache mode (final colour and transmittance of
-    every sample stored in BF16) on the same inputs: its damped operator on
-    the sampled Gaussians against the FP64 oracle.  BF16 keeps 8 bits of the
-    cached colour, which enters the back-scatter through the suffix
-    (C_final - C_<=n) / (1 - alpha_n); measured 7e-7 normwise on the sampled
-    Gaussians (2.3e-5 over the whole P-vector against the FP32 caches, in
-    bench.py), held at 5e-4."""
-    if full.scene.n_gauss < 1_000_000:
-        pytest.skip("the BF16-cache mode is the 1.5M-Gaussian workload's")
+    """BF16 per-sample caches (the final colour of every sample stored in
+    BF16, cache_bf16=1) against the FP64 oracle, on the paths that read the
+    cache: J^T W r (lmrs_rhs) and diag(J^T W J) (lmrs_jtj_diag) of the sampled
+    Gaussians, and the solution of one LM step against the same step with
+    FP32 caches, in the A-norm of the device's damped operator (the oracle's
+    PCG over the whole parameter vector is beyond this size).  The cache
+    enters through the suffix (C_final - C_<=n) / (1 - alpha_n) of the alpha
+    cotangent: BF16 keeps 8 significant bits of C_final, so the suffix of a
+    late entry carries an absolute error of about 2^-9 C_final, the same sign
+    at every entry of a sample.  The damped operator of the PCG loop
+    recomputes the colour and does not read it.  Measured on the 200k
+    workload: J^T W r 9.1e-3, diag 5.7e-4, solution 7.4e-2 (the 8 PCG
+    iterations amplify the right-hand side's error); held at about twice
+    that.  The FP32 caches (the default, 12 bytes per sample) meet the 1e-4
+    bars above."""
     torch = full.torch
     cfg = dict(full.cfg, cache_bf16=1)
     gpu16 = full.lmrs.Scene(torch.from_numpy(full.scene.params).cuda(), full.scene.cams, full.scene.n_gauss,
@@ -154,13 +166,32 @@ def test_bf16_cache_mode_against_the_oracle(full):
     try:
         gpu16.preprocess(full.views, 3)
         full.lmrs.lmrs_render(gpu16.h)
-        v = np.random.default_rng(4).standard_normal(full.P).astype(np.float32)
-        out = full.zeros(full.P)
-        full.lmrs.lmrs_jtjv(gpu16.h, full.cuda(v), out)
-        got = _blocks(full, full.host(out))
-        ref = full.orc.apply_gauss(v.astype(np.float64), np.zeros(full.P), full.gids)
-        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
-        print(f"BF16-cache operator vs FP64 oracle, 256 Gaussians: {err:.3e}")
-        assert err <= 5e-4
+        b = full.zeros(full.P)
+        full.lmrs.lmrs_rhs(gpu16.h, b)
+        b_ref = _rhs_gauss(full)
+        err_b = np.linalg.norm(_blocks(full, full.host(b)) - b_ref) / np.linalg.norm(b_ref)
+        d = full.zeros(full.P)
+        full.lmrs.lmrs_jtj_diag(gpu16.h, d)
+        D_ref = full.orc.diag_gauss(full.gids)
+        err_d = np.linalg.norm(_blocks(full, full.host(d)) - D_ref) / np.linalg.norm(D_ref)
+        # one LM step (solve only: its parameters are not used again) in both cache modes
+        xs = []
+        for cache in (0, 1):
+            sc = full.lmrs.Scene(torch.from_numpy(full.scene.params).cuda(), full.scene.cams, full.scene.n_gauss,
+                                 full.scene.sh_degree, targets=full.targets, **dict(full.cfg, cache_bf16=cache))
+            full.lmrs.lmrs_lm_step(sc.h, full.views, 3)
+            x = full.zeros(full.P)
+            full.lmrs.lmrs_get_solution(sc.h, x)
+            xs.append(x)
+            sc.close()
+        e = xs[1] - xs[0]
+        Ae, Ax = full.zeros(full.P), full.zeros(full.P)
+        full.lmrs.lmrs_jtj_diag(full.gpu.h)
+        full.lmrs.lmrs_jtjv(full.gpu.h, e, Ae)
+        full.lmrs.lmrs_jtjv(full.gpu.h, xs[0], Ax)
+        err_x = float(torch.sqrt(torch.clamp(e @ Ae, min=0.0) / (xs[0] @ Ax)))
+        print(f"BF16 caches vs FP64 oracle, 256 Gaussians: J^T W r {err_b:.3e}, diag {err_d:.3e}; "
+              f"LM-step solution vs FP32 caches, A-norm {err_x:.3e}")
+        assert err_b <= 2e-2 and err_d <= 2e-3 and err_x <= 0.15
     finally:
         gpu16.close()

@@ -10,8 +10,7 @@ import pytest
 
 from paper_2504_12905_gb300 import synthetic as syn
 
-from gpu_common import (GROUPS, Pair, assert_groups_close, assert_pvec_close, flagged_contribution, group_errors,
-                        oracle_targets)
+from gpu_common import GROUPS, Pair, assert_groups_close, assert_pvec_close, group_errors, oracle_targets
 from helpers import normwise_rel, small_scene
 
 pytestmark = pytest.mark.gpu
@@ -63,12 +62,15 @@ CASES = {
     "ragged_sh3": lambda: _ragged(3, 0.25),
     "ragged_sh2": lambda: _ragged(2, 0.3),
     # one sample per tile: every work item has a single live lane.  70
-    # samples for 34,500 parameters leave half of the 8,917 touched diagonal
-    # entries below 1e-6 of the largest; under lambda diag(J^T W J) damping
-    # (which also scales the Jacobi preconditioner) the oracle's own 10-step
-    # CG moves by ~10% in the A-norm when D is perturbed at FP32 rounding of
-    # its largest entry, so the solves compare under lambda I damping (the
-    # operator test still runs both modes)
+    # samples for 34,500 parameters: under lambda diag(J^T W J) damping the
+    # system is singular to working precision in the directions of the 22
+    # diagonal entries FP32 cannot resolve (D_j < 1e-6 of the magnitude of
+    # their terms, 8,710 positive).  Measured with the oracle's own 10-step
+    # PCG: fed the device's right-hand side (2.5e-6 from its own, normwise)
+    # it moves by 0.84 in the A-norm; fed the device's diagonal on those 22
+    # entries alone, by 92% in the 2-norm; on the other 8,688 entries, by
+    # 2e-6.  So this case compares its solves and LM steps under lambda I
+    # damping; its operator test runs both modes
     "ragged_k1": lambda: _ragged(1, 1.0, samples_per_tile=1, damping_mode=0),
     # non-square tiles of the autotuner's candidate set
     "ragged_tile32x8": lambda: _ragged(1, 0.3, tile_w=32, tile_h=8),
@@ -88,6 +90,11 @@ CASES = {
 def case(request):
     pair, views = CASES[request.param]()
     pair.begin(views, step=2)
+    # at the samples the oracle flags near a compositing decision, the
+    # oracle follows the outcome the device took (gpu_common.adopt_device_decisions)
+    flagged, flipped, worst = pair.adopt()
+    print(f"{request.param}: {flagged} flagged samples, {flipped} taken the other way, worst score {worst:.3f}")
+    assert worst <= 1.0
     return pair
 
 
@@ -132,9 +139,9 @@ def test_render_and_residuals(case):
     case.lmrs.lmrs_render(case.gpu.h, images, resid)
     rgb, r_ref, flags = case.orc.render_samples()
     r = case.host(resid).reshape(-1, 3)
-    keep = flags == 0
-    assert keep.mean() > 0.995
-    np.testing.assert_allclose(r[keep], r_ref[keep], atol=PIX_TOL, rtol=0)
+    assert (flags == 0).mean() > 0.995
+    # every sample, the flagged ones with the outcome the device took
+    np.testing.assert_allclose(r, r_ref, atol=PIX_TOL, rtol=0)
     img = case.host(images).reshape(case.gpu.n_views, case.scene.height, case.scene.width, 3)
     for slot in range(case.gpu.n_views):
         ref, fl = case.orc.render_full(slot)
@@ -149,10 +156,8 @@ def test_jvp(case):
     u = case.zeros(case.S * 3)
     case.lmrs.lmrs_jvp(case.gpu.h, case.cuda(v), u)
     u_ref = case.orc.jvp(v.astype(np.float64))
-    _, _, flags = case.orc.render_samples()
-    keep = flags == 0
     got = case.host(u).reshape(-1, 3)
-    assert normwise_rel(got[keep], u_ref[keep]) <= OP_TOL
+    assert normwise_rel(got, u_ref) <= OP_TOL
 
 
 def test_vjp_and_rhs(case):
@@ -191,7 +196,7 @@ def test_jtjv(case, damping_mode):
     cfg.setdefault("lambda_", 0.1)
     pair = Pair(case.scene, case.targets_np, **cfg)
     pair.begin(case.views, step=2)
-    pair.lmrs.lmrs_render(pair.gpu.h)
+    assert pair.adopt()[2] <= 1.0
     pair.lmrs.lmrs_jtj_diag(pair.gpu.h)
     D_ref = pair.orc.diag()
     rng = np.random.default_rng(4)
@@ -201,7 +206,7 @@ def test_jtjv(case, damping_mode):
     ref = pair.orc.apply(v.astype(np.float64), D_ref)
     got = pair.host(out)
     assert_pvec_close(got, ref, OP_TOL, "(J^T W J + lambda D) v")
-    assert_groups_close(pair, got, ref, OP_TOL, flagged_contribution(pair, v))
+    assert_groups_close(pair, got, ref, OP_TOL)
     # host buffers through the same entry point
     out_h = np.zeros(pair.P, np.float32)
     pair.lmrs.lmrs_jtjv(pair.gpu.h, np.ascontiguousarray(v), out_h)
@@ -210,20 +215,24 @@ def test_jtjv(case, damping_mode):
 
 def assert_solution_close(pair, x, x_ref, D_ref, tol=CG_TOL):
     """CG iterates agree in the energy norm |e|_A / |x|_A (the norm CG
-    minimises) and in the 2-norm over the well-determined parameters: all of
-    them under lambda I damping (A >= lambda I), those with D_j >= 1e-6 max D
-    under diagonal damping.  There, parameters with a near-null Jacobian
-    column get x_j ~ b_j / ((1 + lambda) D_j), where the FP32 and FP64
-    diagonals legitimately differ in relative terms."""
+    minimises) and in the 2-norm over the parameters whose diagonal entry
+    FP32 can resolve: all of them under lambda I damping (A >= lambda I);
+    under diagonal damping those with D_j >= 1e-5 M_j, M_j = sum over rows of
+    w (sum_f |dC/df a_fj|)^2 (the oracle's diag_magnitude).  An FP32
+    evaluation of the entry's chain rule errs by about u sqrt(D_j M_j) times
+    the chain's length, so below that ratio D_j, and with it x_j ~ b_j /
+    ((1 + lambda) D_j), carries no FP32 information."""
     e = x - x_ref
     a_norm = np.sqrt(max(e @ pair.orc.apply(e, D_ref), 0.0)) / np.sqrt(x_ref @ pair.orc.apply(x_ref, D_ref))
     assert a_norm <= tol, f"A-norm rel error {a_norm:.3e}"
     if pair.cfg["damping_mode"] == 1:
-        well = D_ref >= 1e-6 * D_ref.max()
-        assert well.sum() >= 0.5 * (D_ref > 0).sum()
+        well = D_ref >= 1e-5 * pair.orc.diag_magnitude()
+        assert well.mean() >= 0.99, well.mean()
     else:
         well = np.ones(D_ref.size, bool)
-    assert normwise_rel(x[well], x_ref[well]) <= tol
+    err = normwise_rel(x[well], x_ref[well])
+    print(f"solution: A-norm {a_norm:.2e}, 2-norm over {well.sum()} of {well.size} entries {err:.2e}")
+    assert err <= tol
     return a_norm
 
 
@@ -266,8 +275,10 @@ def test_lm_step_and_step_size(case):
         assert st.loss == pytest.approx(st_ref[0], rel=1e-5)
         p1 = np.zeros(pair.P, np.float32)
         pair.lmrs.lmrs_get_params(pair.gpu.h, p1)
-        well = D_ref >= 1e-6 * D_ref.max()
-        # beta_1 = beta_0 - eta x; compared on the well-determined entries
+        well = (D_ref >= 1e-5 * pair.orc.diag_magnitude()) if pair.cfg["damping_mode"] == 1 else \
+            np.ones(pair.P, bool)
+        # beta_1 = beta_0 - eta x; compared on the entries FP32 resolves (as
+        # in assert_solution_close)
         # the device forms p - (float)eta * x in FP32: (float)eta, the product
         # and the subtraction each round once (unit roundoff 2^-24)
         upd = -st.eta * x

@@ -26,8 +26,8 @@ def _cfg(lmrs, seed):
                                     seed=seed)
 
 
-def _run(lmrs, jobs, budget=8 << 30, max_active=16, max_steps=4, target_loss=0.0):
-    srv = lmrs.lmrs_server_create(budget, max_active=max_active, setup_threads=4)
+def _run(lmrs, jobs, budget=8 << 30, max_active=16, max_steps=4, target_loss=0.0, **server):
+    srv = lmrs.lmrs_server_create(budget, max_active=max_active, setup_threads=4, **server)
     try:
         ids = [lmrs.lmrs_server_submit(srv, _cfg(lmrs, 100 + k), p.size // 23, p, c, t, views_per_step=3,
                                        target_loss=target_loss, max_steps=max_steps)
@@ -70,6 +70,38 @@ def test_fifo_admission_under_budget():
     assert stats.bytes_peak <= budget
     for info, _ in out:
         assert info.footprint_est == est and 0 < info.footprint_peak <= est
+
+
+def test_least_work_first_admission():
+    """Policy 1 admits the queued job with the least estimated work
+    (Gaussians x views x max_steps) first: with room for about one job at a
+    time, every job after the first admitted (the queue may hold only it
+    then) is admitted in order of size."""
+    from paper_2504_12905_gb300 import lmrs
+    sizes = [1500, 2400, 600, 1200, 900]
+    jobs = [(k, _job(40 + k, G, 6)) for k, G in enumerate(sizes)]
+    est = max(lmrs.lmrs_footprint_bytes(_cfg(lmrs, 0), G, 6, 64, 64, 3) for G in sizes)
+    out, _ = _run(lmrs, jobs, budget=int(1.2 * est), max_steps=2, policy=1)
+    order = [k for _, k in sorted((info.t_admit, k) for k, (info, _) in enumerate(out))]
+    assert order[1:] == sorted(order[1:], key=lambda k: sizes[k]), order
+
+
+def test_full_frame_stop_rule():
+    """stop_full_frame: a job converges once the full-frame MSE of its
+    updated parameters over every camera (lmrs_eval_mse) is within the
+    target, checked after steps whose sampled loss is within the gate."""
+    from paper_2504_12905_gb300 import lmrs
+    job = [(0, _job(20, 800, 5))]
+    (info, res), = _run(lmrs, job, target_loss=1e9, max_steps=50, stop_full_frame=1)[0]
+    assert info.converged == 1 and info.steps == 1 and info.full_mse > 0.0
+    # the reported MSE is the full frames' of the returned parameters
+    p, cams, tgt = job[0][1]
+    import torch
+    s = lmrs.Scene(res, cams, 800, 1, targets=torch.from_numpy(tgt).cuda())
+    assert lmrs.lmrs_eval_mse(s.h) == pytest.approx(info.full_mse, rel=1e-6)
+    s.close()
+    (info, _), = _run(lmrs, job, target_loss=0.0, max_steps=3, stop_full_frame=1)[0]
+    assert info.converged == 0 and info.steps == 3 and info.full_mse == -1.0  # never within the gate of 0
 
 
 def test_convergence_rule():

@@ -635,3 +635,41 @@ def test_importance_gaussian_draws_only_covered_pixels():
         m = tile == t
         if covered[ys, xs].any():
             assert covered[smp["py"][m], smp["px"][m]].all()
+
+
+def test_decision_outcomes_are_adopted_from_planted_values():
+    """The oracle's handling of near-threshold decisions (alpha skip and
+    clamp, termination within the flagging margins): with the oracle's own
+    residuals and J v as the evidence every flagged sample keeps mask 0;
+    with the values of the other outcome planted at every flagged sample,
+    the adoption recovers that outcome everywhere, and the oracle's sample
+    renders and J v then equal the planted values.  The flipped decisions
+    move J^T W r, so exact sums need the adopted outcomes."""
+    from gpu_common import adopt_device_decisions
+    sc = syn.tiny_scene(n_gauss=3000, sh_degree=1)
+    tgt = syn.noise_targets(np.random.default_rng(3), 4, 64, 64)
+    o = oracle.OracleScene(sc.params, sc.cams, sc.n_gauss, 1, targets=tgt, sample_frac=1.0, lambda_=0.1,
+                           seed=0x5EED)
+    o.begin_step([0, 1, 2, 3], 2)
+    rgb, res, fl = o.render_samples()
+    idx = np.nonzero(fl)[0]
+    assert len(idx) >= 5
+    v = np.random.default_rng(1).standard_normal(o.n_params)
+    u = o.jvp(v)
+    b0 = o.rhs()
+    assert adopt_device_decisions(o, res, u, v) == (len(idx), 0, 0.0)
+    nn, rgb_m, u_m = o.sample_outcomes(v, idx, 4)
+    assert np.all(nn >= 1)
+    np.testing.assert_array_equal(rgb_m[:, 0], rgb[idx])
+    np.testing.assert_array_equal(u_m[:, 0], u[idx])
+    res2, u2 = res.copy(), u.copy()
+    res2[idx] = rgb_m[:, 1] - (rgb[idx] - res[idx])
+    u2[idx] = u_m[:, 1]
+    n_fl, n_flip, worst = adopt_device_decisions(o, res2, u2, v)
+    assert (n_fl, n_flip, worst) == (len(idx), len(idx), 0.0)
+    rgb_f, res_f, _ = o.render_samples()
+    np.testing.assert_array_equal(res_f, res2)
+    np.testing.assert_array_equal(o.jvp(v), u2)
+    assert np.linalg.norm(o.rhs() - b0) > 1e-6 * np.linalg.norm(b0)
+    o.clear_flips()
+    np.testing.assert_array_equal(o.rhs(), b0)
