@@ -59,7 +59,7 @@ WORKLOADS = {
                          "lambda*I damping; each fit runs until its full-frame PSNR over every camera is within "
                          "0.1 dB of its ground truth's (at most 60 steps); 120 GB admission budget",
                     samples_per_tile=32, cg_iters=8, lam=0.1, damping_mode=0, rate=20.0, requests=100,
-                    max_steps=60, noise_sigma=0.02, psnr_slack_db=0.1, budget_bytes=120 << 30, max_active=16,
+                    max_steps=60, noise_sigma=0.02, psnr_slack_db=0.1, budget_bytes=120 << 30, max_active=8,
                     policy=1, full_frame_gate=1.25),
 }
 

@@ -341,8 +341,12 @@ lmrs_status lmrs_fit(lmrs_scene* scene, const lmrs_fit_config* cfg, lmrs_fit_rec
  *     oldest first among equals (policy 1).  An admitted job's parameters,
  *     CG vectors, raster caches and targets stay on the device until it
  *     finishes.
- *   - every scheduler iteration runs one LM step of each resident job (one
- *     batch per group of equal SH degree and cg_iters), then retires the
+ *   - every scheduler iteration runs one LM step of each resident job: the
+ *     jobs with fewer than solo_min_samples sampled pixels per step in one
+ *     batch per group of equal SH degree and cg_iters (lmrs_batch_lm_step),
+ *     the others each with lmrs_lm_step on its own stream from a host thread
+ *     (up to setup_threads at a time), so their kernels overlap on the
+ *     device; then it retires the
  *     jobs that reached target_loss or have run max_steps steps; the freed
  *     memory admits the next jobs (continuous batching).  A job reaches its
  *     target when its sampled loss (Eq. 11 at the step's samples, before the
@@ -364,6 +368,7 @@ typedef struct {
     int32_t policy;         /* admission order: 0 FIFO, 1 least estimated work first */
     int32_t stop_full_frame;  /* 1: the target is the full-frame MSE (see above) */
     double full_frame_gate;   /* sampled loss / target_loss at or below which the full frames are checked; <= 0: 1.25 */
+    int64_t solo_min_samples; /* sampled pixels per step from which a job steps on its own stream; <= 0: 131072 */
 } lmrs_server_config;
 
 typedef enum { LMRS_JOB_QUEUED = 0, LMRS_JOB_RUNNING = 1, LMRS_JOB_DONE = 2, LMRS_JOB_FAILED = 3 } lmrs_job_state;

@@ -3,6 +3,7 @@
 // every resident job per scheduler iteration through lmrs_batch_lm_step).
 // Host code over the public C-ABI plus the library's memory pool.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -54,7 +55,8 @@ struct lmrs_server {
     std::thread thread;
     // batches of the current resident set, per (SH degree, cg_iters) group
     struct Group {
-        std::vector<Job*> members;
+        std::vector<Job*> members;  // batched members first (n_batched of them), then the solo ones
+        size_t n_batched = 0;
         lmrs_batch* batch = nullptr;
     };
     std::vector<Group> groups;
@@ -126,6 +128,15 @@ void finish(lmrs_server* S, Job* j, lmrs_status status, bool converged) {
     S->cv_done.notify_all();
 }
 
+int64_t samples_per_step(const Job* j) {
+    const int views = j->views_per_step > 0 ? std::min<int>(j->views_per_step, (int)j->cams.size()) : (int)j->cams.size();
+    const double px = (double)j->cams[0].width * j->cams[0].height;
+    const double frac = j->cfg.samples_per_tile > 0
+                            ? std::min(1.0, (double)j->cfg.samples_per_tile / (j->cfg.tile_w * j->cfg.tile_h))
+                            : std::min(1.0, j->cfg.sample_frac);
+    return (int64_t)(px * frac * views);
+}
+
 double work_estimate(const Job* j) {
     const int views = j->views_per_step > 0 ? std::min<int>(j->views_per_step, (int)j->cams.size()) : (int)j->cams.size();
     return (double)j->G * views * j->max_steps;
@@ -181,52 +192,92 @@ void rebuild_groups(lmrs_server* S) {
         it->members.push_back(j);
     }
     for (auto& g : S->groups) {
+        // small jobs batched (they do not fill the device alone), large ones solo
+        std::stable_partition(g.members.begin(), g.members.end(),
+                              [&](const Job* j) { return samples_per_step(j) < S->cfg.solo_min_samples; });
+        g.n_batched = (size_t)std::count_if(g.members.begin(), g.members.end(), [&](const Job* j) {
+            return samples_per_step(j) < S->cfg.solo_min_samples;
+        });
+        if (g.n_batched < 2) g.n_batched = 0;  // one small job steps on its own
         std::vector<lmrs_scene*> sc;
-        for (Job* j : g.members) sc.push_back(j->scene);
-        if (lmrs_batch_create(sc.data(), (int32_t)sc.size(), S->cfg.setup_threads, nullptr, &g.batch) != LMRS_OK)
+        for (size_t i = 0; i < g.n_batched; ++i) sc.push_back(g.members[i]->scene);
+        if (!sc.empty() &&
+            lmrs_batch_create(sc.data(), (int32_t)sc.size(), S->cfg.setup_threads, nullptr, &g.batch) != LMRS_OK)
             g.batch = nullptr;
     }
     S->groups_dirty = false;
 }
 
-// One LM step of every member; per-job status in rc.
-void step_group(lmrs_server::Group& g, std::vector<lmrs_status>& rc, std::vector<lmrs_step_stats>& st) {
+// Outcome of one step of one job.
+struct StepOut {
+    lmrs_status rc = LMRS_OK;
+    lmrs_step_stats st{};
+    bool reached = false;
+    double full = -1.0;
+};
+
+// Whether the job reached its target after the step (the sampled loss, or
+// the full-frame MSE once the sampled loss is within the gate).
+void check_target(const lmrs_server* S, Job* j, StepOut& o) {
+    if (o.rc != LMRS_OK) return;
+    o.reached = o.st.loss <= j->target_loss;
+    if (S->cfg.stop_full_frame) {
+        o.reached = false;
+        if (o.st.loss <= S->cfg.full_frame_gate * j->target_loss && lmrs_eval_mse(j->scene, &o.full) == LMRS_OK)
+            o.reached = o.full <= j->target_loss;
+    }
+}
+
+// One LM step of every member of the group and its target check: the
+// batched members through the group's batch (a member the batch did not step
+// steps alone), the solo members concurrently, each on its own stream from a
+// host thread.
+void step_group(lmrs_server* S, lmrs_server::Group& g, std::vector<StepOut>& out) {
     const size_t n = g.members.size();
-    rc.assign(n, LMRS_OK);
-    st.assign(n, lmrs_step_stats{});
-    std::vector<int32_t> flat, nv(n), v;
-    std::vector<int64_t> steps(n);
-    for (size_t i = 0; i < n; ++i) {
-        Job* j = g.members[i];
-        views_of_step(j, j->info.steps, v);
-        flat.insert(flat.end(), v.begin(), v.end());
-        nv[i] = (int32_t)v.size();
-        steps[i] = j->info.steps;
-    }
-    if (g.batch) {
-        if (lmrs_batch_lm_step(g.batch, flat.data(), nv.data(), steps.data(), st.data()) == LMRS_OK) return;
-        // members that failed are reported; the others either stepped or
-        // were not stepped (then they step alone below)
-        size_t off = 0;
-        for (size_t i = 0; i < n; ++i) {
-            rc[i] = lmrs_batch_scene_status(g.batch, (int32_t)i);
-            if (rc[i] == LMRS_ERR_NOT_PREPROCESSED)
-                rc[i] = lmrs_lm_step(g.members[i]->scene, flat.data() + off, nv[i], steps[i], &st[i]);
-            off += nv[i];
+    out.assign(n, StepOut{});
+    std::vector<std::vector<int32_t>> views(n);
+    for (size_t i = 0; i < n; ++i) views_of_step(g.members[i], g.members[i]->info.steps, views[i]);
+    std::vector<size_t> alone;  // members stepped one by one
+    if (g.n_batched > 0 && g.batch) {
+        std::vector<int32_t> flat, nv(g.n_batched);
+        std::vector<int64_t> steps(g.n_batched);
+        std::vector<lmrs_step_stats> st(g.n_batched);
+        for (size_t i = 0; i < g.n_batched; ++i) {
+            flat.insert(flat.end(), views[i].begin(), views[i].end());
+            nv[i] = (int32_t)views[i].size();
+            steps[i] = g.members[i]->info.steps;
         }
-        return;
+        const bool ok = lmrs_batch_lm_step(g.batch, flat.data(), nv.data(), steps.data(), st.data()) == LMRS_OK;
+        for (size_t i = 0; i < g.n_batched; ++i) {
+            out[i].st = st[i];
+            out[i].rc = ok ? LMRS_OK : lmrs_batch_scene_status(g.batch, (int32_t)i);
+            if (out[i].rc == LMRS_ERR_NOT_PREPROCESSED) alone.push_back(i);  // not stepped: alone below
+            else check_target(S, g.members[i], out[i]);
+        }
+    } else {
+        for (size_t i = 0; i < g.n_batched; ++i) alone.push_back(i);
     }
-    size_t off = 0;
-    for (size_t i = 0; i < n; ++i) {
-        rc[i] = lmrs_lm_step(g.members[i]->scene, flat.data() + off, nv[i], steps[i], &st[i]);
-        off += nv[i];
-    }
+    for (size_t i = g.n_batched; i < n; ++i) alone.push_back(i);
+    std::atomic<size_t> next{0};
+    auto work = [&] {
+        cudaSetDevice(S->device);
+        for (size_t k = next++; k < alone.size(); k = next++) {
+            const size_t i = alone[k];
+            Job* j = g.members[i];
+            out[i].rc = lmrs_lm_step(j->scene, views[i].data(), (int32_t)views[i].size(), j->info.steps, &out[i].st);
+            check_target(S, j, out[i]);
+        }
+    };
+    const size_t nt = std::min<size_t>(alone.size(), (size_t)S->cfg.setup_threads);
+    std::vector<std::thread> pool;
+    for (size_t t = 1; t < nt; ++t) pool.emplace_back(work);
+    if (nt > 0) work();
+    for (auto& t : pool) t.join();
 }
 
 void scheduler(lmrs_server* S) {
     cudaSetDevice(S->device);
-    std::vector<lmrs_status> rc;
-    std::vector<lmrs_step_stats> st;
+    std::vector<StepOut> out;
     for (;;) {
         {
             std::unique_lock<std::mutex> lk(S->mu);
@@ -240,29 +291,22 @@ void scheduler(lmrs_server* S) {
         std::vector<std::pair<Job*, lmrs_status>> failed;
         std::vector<bool> conv;
         for (auto& g : S->groups) {
-            step_group(g, rc, st);
+            step_group(S, g, out);
             for (size_t i = 0; i < g.members.size(); ++i) {
                 Job* j = g.members[i];
-                if (rc[i] != LMRS_OK) {
-                    failed.push_back({j, rc[i]});
+                if (out[i].rc != LMRS_OK) {
+                    failed.push_back({j, out[i].rc});
                     continue;
                 }
                 const int64_t held = held_bytes(j);
-                bool reached = st[i].loss <= j->target_loss;
-                double full = -1.0;
-                if (S->cfg.stop_full_frame) {
-                    reached = false;
-                    if (st[i].loss <= S->cfg.full_frame_gate * j->target_loss && lmrs_eval_mse(j->scene, &full) == LMRS_OK)
-                        reached = full <= j->target_loss;
-                }
                 std::lock_guard<std::mutex> lk(S->mu);
                 j->info.steps += 1;
-                j->info.loss = st[i].loss;
-                if (full >= 0.0) j->info.full_mse = full;
+                j->info.loss = out[i].st.loss;
+                if (out[i].full >= 0.0) j->info.full_mse = out[i].full;
                 j->info.footprint_peak = std::max(j->info.footprint_peak, held);
-                if (reached || j->info.steps >= j->max_steps) {
+                if (out[i].reached || j->info.steps >= j->max_steps) {
                     retire.push_back(j);
-                    conv.push_back(reached);
+                    conv.push_back(out[i].reached);
                 }
             }
         }
@@ -327,6 +371,7 @@ lmrs_status lmrs_server_create(const lmrs_server_config* cfg, lmrs_server** out)
     S->cfg = *cfg;
     if (!(S->cfg.tiles_per_pair > 0.0)) S->cfg.tiles_per_pair = 10.0;
     if (!(S->cfg.full_frame_gate > 0.0)) S->cfg.full_frame_gate = 1.25;
+    if (S->cfg.solo_min_samples <= 0) S->cfg.solo_min_samples = 131072;
     if (cudaGetDevice(&S->device) != cudaSuccess) {
         cudaGetLastError();
         delete S;

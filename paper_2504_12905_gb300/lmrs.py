@@ -65,7 +65,7 @@ class StepStats(C.Structure):
 class ServerConfig(C.Structure):
     _fields_ = [("budget_bytes", C.c_int64), ("max_active", C.c_int32), ("setup_threads", C.c_int32),
                 ("tiles_per_pair", C.c_double), ("policy", C.c_int32), ("stop_full_frame", C.c_int32),
-                ("full_frame_gate", C.c_double)]
+                ("full_frame_gate", C.c_double), ("solo_min_samples", C.c_int64)]
 
 
 class JobInfo(C.Structure):
@@ -422,9 +422,9 @@ def lmrs_batch_scene_status(batch, i):
 
 
 def lmrs_server_create(budget_bytes, max_active=64, setup_threads=8, tiles_per_pair=0.0, policy=0,
-                       stop_full_frame=0, full_frame_gate=0.0):
+                       stop_full_frame=0, full_frame_gate=0.0, solo_min_samples=0):
     cfg = ServerConfig(int(budget_bytes), int(max_active), int(setup_threads), float(tiles_per_pair), int(policy),
-                       int(stop_full_frame), float(full_frame_gate))
+                       int(stop_full_frame), float(full_frame_gate), int(solo_min_samples))
     h = _P()
     _check(lib().lmrs_server_create(C.byref(cfg), C.byref(h)))
     return h.value
