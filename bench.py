@@ -33,12 +33,14 @@ sys.path.insert(0, ROOT)
 METRIC = "JᵀJv matvecs/s at 200k Gaussians (%HBM peak); fits/s & p99 fit latency vs plain"
 
 WORKLOADS = {
-    "moderate": dict(desc="200k Gaussians, SH3, 8 of 24 views 1024x672, 10% per-tile sampling, 8 CG iters",
+    "moderate": dict(desc="LM steps with lambda*I damping (Eq. 8); 200k Gaussians, SH3, 8 of 24 views 1024x672, "
+                          "10% per-tile sampling, 8 CG iters",
                      views_per_step=8, sample_frac=0.1, cg_iters=8, lam=0.1, damping_mode=0),
-    "tiny": dict(desc="1k Gaussians, SH0, 4 views 64x64, all pixels, 10 CG iters",
+    "tiny": dict(desc="LM steps with lambda*I damping (Eq. 8); 1k Gaussians, SH0, 4 views 64x64, all pixels, "
+                      "10 CG iters",
                  views_per_step=4, sample_frac=1.0, cg_iters=10, lam=1e-2, damping_mode=0),
-    "large": dict(desc="1.5M Gaussians, SH3, 12 of 100 views 1297x840 (360 deg orbit, +-15 deg jitter), 25% "
-                       "per-tile sampling, BF16 per-sample caches, 8 CG iters",
+    "large": dict(desc="LM steps with lambda*I damping (Eq. 8); 1.5M Gaussians, SH3, 12 of 100 views 1297x840 "
+                       "(360 deg orbit, +-15 deg jitter), 25% per-tile sampling, BF16 per-sample caches, 8 CG iters",
                   views_per_step=12, sample_frac=0.25, cg_iters=8, lam=0.1, damping_mode=0, cache_bf16=1,
                   cpu_views=1),
     "fit": dict(desc="LM-RS fits of the 200k-Gaussian scene seen from 96 views 1024x672: 100 LM steps, 16 -> 32 "
@@ -707,6 +709,7 @@ def run_batched(args, rank, world, local_rank):
     bstream = torch.cuda.Stream()
     bsc = [make(i, streams[i].cuda_stream) for i in range(n_sc)]
     batch = lmrs.lmrs_batch_create([s.h for s in bsc], n_threads=8, stream=bstream.cuda_stream)
+    lmrs.lmrs_batch_set_persistent(batch, 1 if args.pcg_launch == "persistent" else 0)
     for k in range(args.warmup):
         lmrs.lmrs_batch_lm_step(batch, views, [k] * n_sc, stats=False)
     barrier()
@@ -783,6 +786,8 @@ def run_batched(args, rank, world, local_rank):
                    "step": "one LM step of all 64 scenes", "parallelism": f"replicas x{world}",
                    "l2": "no flush: per-step working set of all scenes > 129 MB",
                    "tile_shape": f"{tw}x{th}",
+                   "pcg_launch": ("one persistent cooperative launch per LM step (grid barriers between phases)"
+                                  if args.pcg_launch == "persistent" else "CUDA graph of per-phase launches"),
                    "autotune_ms_per_step": {f"{a}x{b}": round(float(m), 4) for (a, b), m in zip(shapes, tune_ms)},
                    "sequential_fits_per_s": round(fits / (ms_s / 1000.0), 3),
                    "sequential_ms_per_step": round(ms_s / args.steps, 3),
@@ -1131,6 +1136,9 @@ def main():
     ap.add_argument("--requests", type=int, default=0, help="serving workload: number of timed requests")
     ap.add_argument("--max-active", type=int, default=0, help="serving workload: resident jobs at most (0: default)")
     ap.add_argument("--policy", type=int, default=-1, help="serving workload: 0 FIFO, 1 least work first")
+    ap.add_argument("--pcg-launch", choices=["persistent", "graph"], default="persistent",
+                    help="batched workload: the PCG of all scenes in one persistent launch per LM step "
+                         "(default), or a CUDA graph of per-phase launches")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -212,8 +212,8 @@ lmrs_status lmrs_step_size(lmrs_scene* scene, const float* x_dev, int64_t lm_ste
  *   *eta_host  : the step size (host); the call synchronises the stream.
  * Scratch: a 16,512-byte static device array that every GPU loading the
  * library holds until the process exits.  The first call on a device looks
- * up its address (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture.  All calls on a device share the
+ * up its address (cudaGetSymbolAddress) with that device current.  All
+ * calls on a device share the
  * array, so calls that overlap on the GPU race; each call clears the words
  * that must start at zero.  Errors: LMRS_ERR_INVALID_ARG for null pointers,
  * n_gauss <= 0 or sh_degree outside 0..3; LMRS_ERR_CUDA if a CUDA call fails. */
@@ -240,12 +240,14 @@ lmrs_status lmrs_get_solution(lmrs_scene* scene, float* x_dst);
  *   1. each scene's per-step setup (sampling, binning, render, J^T W r,
  *      diag) runs on its own stream, n_threads scenes at a time on host
  *      threads (give the scenes distinct streams for overlap);
- *   2. the PCG iterations of all scenes run as one launch per phase
- *      (direction, preprocess-JVP, fused raster, preprocess-VJP + p^T A p,
- *      vector update) over segment tables, with per-scene FP64 scalars;
- *      the whole loop is a CUDA graph captured at the first step and
- *      replayed (re-captured when the tables outgrow their buffers);
- *   3. the per-scene step sizes and updates run in two more launches.
+ *   2. the PCG iterations of all scenes run over segment tables, with
+ *      per-scene FP64 scalars, phase by phase (direction, preprocess-JVP,
+ *      fused raster, preprocess-VJP + p^T A p, vector update): by default
+ *      in one persistent cooperative launch with grid barriers between the
+ *      phases, else as one launch per phase, the whole loop a CUDA graph
+ *      captured at the first step and replayed (re-captured when the
+ *      tables outgrow their buffers) -- see lmrs_batch_set_persistent;
+ *   3. the per-scene step sizes and updates run as two more phases.
  * Each scene's result equals its own lmrs_lm_step up to the summation
  * order of the inner products.  The scenes stay owned by the caller, must
  * outlive the batch and must not be used by other calls during a step.
@@ -269,6 +271,24 @@ const char* lmrs_batch_last_error(const lmrs_batch* batch);
  * LMRS_ERR_NOT_PREPROCESSED (not stepped because another scene failed
  * before the batched loop). */
 lmrs_status lmrs_batch_scene_status(const lmrs_batch* batch, int32_t i);
+/* The launch form of step 2 and 3 above: 1 (the default), one persistent
+ * cooperative launch that runs every phase of every PCG iteration and the
+ * updates for all scenes, a grid-wide barrier between phases; 0, the CUDA
+ * graph of per-phase launches.  Each barrier's wait is bounded (2 s by
+ * %globaltimer); a barrier that cannot complete ends the launch, and
+ * lmrs_batch_lm_step with stats then returns LMRS_ERR_TIMEOUT.  Where the
+ * device refuses a cooperative launch of the grid (too large, or not
+ * supported) the batch switches to the graph form for good.  Both forms
+ * give the same result up to the summation order of the atomics.
+ * Errors: LMRS_ERR_INVALID_ARG for a null batch or on outside {0, 1}. */
+lmrs_status lmrs_batch_set_persistent(lmrs_batch* batch, int32_t on);
+/* Self-test of that grid barrier, for the host side of failure detection:
+ * one cooperative launch whose barrier expects `missing` more blocks than it
+ * has.  missing = 0 passes (LMRS_OK); missing > 0 can never complete, so
+ * every block's wait runs out after timeout_s (<= 10) and the call returns
+ * LMRS_ERR_TIMEOUT with the device still usable.  Synchronises cuda_stream
+ * (NULL = legacy stream).  The paper has no counterpart. */
+lmrs_status lmrs_grid_barrier_selftest(int32_t missing, double timeout_s, void* cuda_stream);
 
 /* ---- View sampling (Sec. 4.3) and the fit loop ----------------------------
  * Uniform views of step k: n_views camera indices drawn without replacement
@@ -419,10 +439,14 @@ lmrs_status lmrs_server_destroy(lmrs_server* srv);
 
 /* Footprint model of the admission test: device bytes of a scene during an
  * LM step with views_per_step views (all when <= 0): 9 P-vectors, the
- * per-Gaussian cache, 352 B per (view, Gaussian) pair, the tile entries
- * (tiles_per_pair per pair, keys, ids, their sort buffers and the compact
- * lists), 41 B per sample, the per-tile tables, the targets, and 25%
- * headroom on the per-step parts. */
+ * per-Gaussian cache, 290 B per (view, Gaussian) pair plus its Jacobian
+ * cache (10 planes of 16 B for SH degree 0, 12 otherwise), the tile entries
+ * (tiles_per_pair per pair: ids, the binning's row lists and the compact
+ * lists), 41 B per sample (+4 with importance sampling, +24 with the SSIM
+ * term), the per-tile tables, the targets, and 25% headroom on the per-step
+ * parts.  It is an estimate, not a bound: a scene whose Gaussians cover more
+ * tiles than tiles_per_pair holds more, and the server then counts what the
+ * job holds. */
 int64_t lmrs_footprint_bytes(const lmrs_config* cfg, int64_t n_gauss, int32_t n_cams, int32_t width, int32_t height,
                              int32_t views_per_step, double tiles_per_pair);
 /* (sample, Gaussian) pairs composited before termination by the last

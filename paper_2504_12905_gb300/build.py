@@ -18,8 +18,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB_NAME = "liblmrs.so"
-SOURCES = ["scene.cu", "preprocess.cu", "binning.cu", "raster.cu", "cg.cu", "noalloc.cu", "autotune.cu",
-           "server.cu", "view_sampler.cu", "peaks.cu"]
+# hotpath.cu includes preprocess.cu, raster.cu and cg.cu (one translation unit)
+SOURCES = ["scene.cu", "hotpath.cu", "binning.cu", "noalloc.cu", "autotune.cu", "server.cu", "view_sampler.cu",
+           "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

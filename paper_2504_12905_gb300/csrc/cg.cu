@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(kVecBlock) k_lm_update(Ctx c, long long lm_ste
 // so alpha_i = rz[i] / pAp[i] and beta_i = rz[i+1] / rz[i] are formed where
 // they are used.  The history arrays start at zero.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kBatchBlock) kb_precond_init(BatchTables t) {
+__device__ __forceinline__ void b_precond_init(const BatchTables& t) {
     const int n = t.counts[1];
     for (int k = blockIdx.x; k < n; k += gridDim.x) {
         const int4 ch = t.vchunks[k];
@@ -210,8 +210,10 @@ __global__ void __launch_bounds__(kBatchBlock) kb_precond_init(BatchTables t) {
         if (threadIdx.x == 0) atomicAdd(&bv.rz[0], tot);
     }
 }
+__global__ void __launch_bounds__(kBatchBlock) kb_precond_init(BatchTables t) { b_precond_init(t); }
 
-__global__ void __launch_bounds__(kBatchBlock) kb_direction(BatchTables t, int iter) {
+
+__device__ __forceinline__ void b_direction(const BatchTables& t, int iter) {
     const int n = t.counts[1];
     for (int k = blockIdx.x; k < n; k += gridDim.x) {
         const int4 ch = t.vchunks[k];
@@ -221,8 +223,10 @@ __global__ void __launch_bounds__(kBatchBlock) kb_direction(BatchTables t, int i
         for (long long j = ch.y + threadIdx.x; j < ch.z; j += kBatchBlock) bv.p[j] = bv.z[j] + beta * bv.p[j];
     }
 }
+__global__ void __launch_bounds__(kBatchBlock) kb_direction(BatchTables t, int iter) { b_direction(t, iter); }
 
-__global__ void __launch_bounds__(kBatchBlock) kb_update(BatchTables t, int iter) {
+
+__device__ __forceinline__ void b_update(const BatchTables& t, int iter) {
     const int n = t.counts[1];
     for (int k = blockIdx.x; k < n; k += gridDim.x) {
         const int4 ch = t.vchunks[k];
@@ -247,8 +251,10 @@ __global__ void __launch_bounds__(kBatchBlock) kb_update(BatchTables t, int iter
         if (threadIdx.x == 0) atomicAdd(&bv.rz[iter + 1], tot);
     }
 }
+__global__ void __launch_bounds__(kBatchBlock) kb_update(BatchTables t, int iter) { b_update(t, iter); }
 
-__global__ void __launch_bounds__(kBatchBlock) kb_max_dc(BatchTables t) {
+
+__device__ __forceinline__ void b_max_dc(const BatchTables& t) {
     const int n = t.counts[0];
     for (int k = blockIdx.x; k < n; k += gridDim.x) {
         const int4 ch = t.gchunks[k];
@@ -264,8 +270,10 @@ __global__ void __launch_bounds__(kBatchBlock) kb_max_dc(BatchTables t) {
         if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(&c.sc->max_dc_bits, __float_as_uint(m));
     }
 }
+__global__ void __launch_bounds__(kBatchBlock) kb_max_dc(BatchTables t) { b_max_dc(t); }
 
-__global__ void __launch_bounds__(kBatchBlock) kb_lm_update(BatchTables t) {
+
+__device__ __forceinline__ void b_lm_update(const BatchTables& t) {
     const int n = t.counts[1];
     for (int k = blockIdx.x; k < n; k += gridDim.x) {
         const int4 ch = t.vchunks[k];
@@ -280,6 +288,8 @@ __global__ void __launch_bounds__(kBatchBlock) kb_lm_update(BatchTables t) {
         for (long long j = ch.y + threadIdx.x; j < ch.z; j += kBatchBlock) bv.params[j] -= e * bv.x[j];
     }
 }
+__global__ void __launch_bounds__(kBatchBlock) kb_lm_update(BatchTables t) { b_lm_update(t); }
+
 
 void launch_b_precond_init(const BatchTables& t, int grid, cudaStream_t st) {
     LMRS_LAUNCH(kb_precond_init, grid, kBatchBlock, 0, st, t);

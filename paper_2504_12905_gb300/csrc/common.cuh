@@ -79,10 +79,11 @@ struct Ctx {
     const float* targets;   // [n_cams][H][W][3] or null
     // per (slot, Gaussian) pair, index slot * G + g
     float4* gcache;         // per Gaussian, kGaussF4 planes of G float4 (view-independent 3D state)
-    float4* rec;            // per pair kPrimF4 float4: mu_x, mu_y, A, B | C, o, r, g | b
-    float4* tan;            // per pair kTanF4 float4: the tangents of the same 9 features
+    float4* rec;            // per pair kPrimF4 float4: mu_x, mu_y, A, B | C, o, r, g | b, A', B', C' with
+                            // (A', B', C') = -log2(e) (A / 2, B, C / 2): e^power = 2^(dx (A' dx + B' dy) + C' dy^2)
+    float4* tan;            // per pair kTanF4 float4: the tangents of the 9 features of pjac
     float4* pjac;           // per (view, Gaussian) pair: jac_f4(deg) planes of nv*G float4, the Jacobian
-                            // of the pair's 9 screen-space features w.r.t. the Gaussian's parameters
+                            // of the pair's 9 screen-space features (jac.cuh) w.r.t. its parameters
     int4* rect;             // inclusive tile rectangle, x0 > x1 when culled
     float4* ell;            // per pair 2 float4: the alpha >= 1/255 ellipse that picks each rectangle
                             // row's tile columns (row_span)
@@ -92,7 +93,7 @@ struct Ctx {
     unsigned long long* n_visible;  // count of visible pairs
     unsigned long long* n_entries;  // bound on the tile-list entries: band rows x rectangle width
     unsigned long long* n_rowent;   // sum over visible pairs of the rectangle rows band_meets keeps
-    float* cot;             // kCotF floats
+    float* cot;             // kCotF floats: cotangents of the 9 features of pjac
     float* dslot;           // kDiagF floats: the pair's share of diag(J^T W J) (k_diag)
     // binning
     unsigned int* keys;     // slot * T + tile of each list entry
@@ -261,6 +262,13 @@ void launch_b_jtj(const BatchTables& t, int grid, cudaStream_t st);
 void launch_b_prep_vjp(const BatchTables& t, int deg, int iter, int grid, cudaStream_t st);
 void launch_b_update(const BatchTables& t, int iter, int grid, cudaStream_t st);
 void launch_b_lm_update(const BatchTables& t, int iters, int grid, cudaStream_t st);
+// All of the above in one persistent cooperative launch (grid barriers between
+// the phases, each waiting at most timeout_s); bar: grid_bar_bytes() of device
+// memory, zeroed by the launcher.  grid_bar_error: the error word of a host
+// copy of those bytes (1: a barrier's wait ran out).
+size_t grid_bar_bytes();
+cudaError_t launch_b_pcg(const BatchTables& t, int deg, int iters, void* bar, double timeout_s, cudaStream_t st);
+int grid_bar_error(const void* bar_host_copy);
 
 // ---- the per-tile SplitMix64 stream of the pixel sampler --------------------
 // Tile columns [x0, x1] that the list of a pair covers in tile row ty of its

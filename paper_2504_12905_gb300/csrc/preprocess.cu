@@ -457,8 +457,9 @@ __global__ void k_sample(Ctx c, long long lm_step, unsigned long long seed) {
 
 // ---------------------------------------------------------------------------
 // Per-pair Jacobian cache (layout in jac.cuh), formed from the verified
-// tangent code on unit tangents: column j is the tangent of the 9 features
-// along geometric parameter j.
+// tangent code on unit tangents: column j is the tangent of the mean, conic,
+// opacity and colour along geometric parameter j, turned into the tangents
+// of the exponent's coefficients e_1..e_5 with the pair's conic.
 // ---------------------------------------------------------------------------
 template <int DEG>
 __device__ __forceinline__ void pair_jacobian(const Prim& P, const CamDev& cam, const float* sh, float* J) {
@@ -479,15 +480,16 @@ __device__ __forceinline__ void pair_jacobian(const Prim& P, const CamDev& cam, 
         float out[9];
         prim_tangent<DEG, false>(P, cam, d, sh, nullptr, out);
         if (col < 3) {
-            J[L::kMu + col] = out[0];
-            J[L::kMu + 3 + col] = out[1];
+            J[L::kMu + col] = -(P.A * out[0] + P.B * out[1]);
+            J[L::kMu + 3 + col] = -(P.B * out[0] + P.C * out[1]);
             if (DEG > 0) {
 #pragma unroll
                 for (int ch = 0; ch < 3; ++ch) J[L::kGx + 3 * ch + col] = out[6 + ch];
             }
         }
-#pragma unroll
-        for (int r = 0; r < 3; ++r) J[L::kCon + 10 * r + col] = out[2 + r];
+        J[L::kCon + col] = -0.5f * out[2];
+        J[L::kCon + 10 + col] = -out[3];
+        J[L::kCon + 20 + col] = -0.5f * out[4];
     }
     J[L::kOp] = P.o * (1.f - P.o);
     unsigned bits = 0u;
@@ -556,7 +558,9 @@ __global__ void k_prep_fwd(Ctx c) {
     float4* r = c.rec + i * kPrimF4;
     r[0] = make_float4(P.mux, P.muy, P.A, P.B);
     r[1] = make_float4(P.C, P.o, P.col[0], P.col[1]);
-    r[2] = make_float4(P.col[2], 0.f, 0.f, 0.f);
+    // the conic scaled for the rasterizer's 2^x (the primal record's spare slots)
+    const float L2E = 1.4426950408889634f;
+    r[2] = make_float4(P.col[2], -0.5f * L2E * P.A, -L2E * P.B, -0.5f * L2E * P.C);
     c.rect[i] = rect;
     c.ell[2 * i] = ell[0];
     c.ell[2 * i + 1] = ell[1];
@@ -746,7 +750,7 @@ __global__ void __launch_bounds__(32 * kJvpWarps) k_prep_jvp(Ctx c, const float*
 
 // The same for every scene of a batch: Gaussian chunks, tangent = the scene's p.
 template <int DEG>
-__global__ void __launch_bounds__(kBatchBlock) kb_prep_jvp(BatchTables t) {
+__device__ __forceinline__ void b_prep_jvp(const BatchTables& t) {
     static_assert(kBatchBlock == 32 * kJvpWarps, "one lane per Gaussian, one warp per view class");
     const int n = t.counts[0];
     for (int k = blockIdx.x; k < n; k += gridDim.x) {
@@ -760,6 +764,9 @@ __global__ void __launch_bounds__(kBatchBlock) kb_prep_jvp(BatchTables t) {
         }
     }
 }
+template <int DEG>
+__global__ void __launch_bounds__(kBatchBlock) kb_prep_jvp(BatchTables t) { b_prep_jvp<DEG>(t); }
+
 
 constexpr int kPrepBlock = 128;
 
@@ -775,26 +782,22 @@ __device__ __forceinline__ void damp_put(const Ctx& c, float* out, const float* 
     out[idx] = val;
 }
 
-// J^T of Gaussian g's cotangent slots over its visible views, written to out
-// (+ lambda damping of v when v is given; v^T out accumulated into dot).
-// With sh_stage the 3K SH entries go to that shared-memory row instead, for
-// the caller to store coalesced.
-template <int DEG, bool kDot>
-__device__ __forceinline__ void prep_vjp_gauss(const Ctx& c, int g, float* out, const float* v, const float* D,
-                                               Dot2& dot, float* sh_stage = nullptr) {
+// J^T of Gaussian g's cotangent slots over its visible views slot0, slot0 +
+// dslot, ...: gu (X, log-scale, q), gth (opacity logit), gsh (3K SH values).
+template <int DEG>
+__device__ __forceinline__ void vjp_views(const Ctx& c, int g, int slot0, int dslot, float gu[10], float& gth,
+                                          float* gsh) {
     using L = Jac<DEG>;
     constexpr int K = Sh<DEG>::K;
     constexpr int K3 = 3 * K;
-    float gu[10];  // X, log-scale, q
 #pragma unroll
     for (int k = 0; k < 10; ++k) gu[k] = 0.f;
-    float gth = 0.f;
-    float gsh[K3];
+    gth = 0.f;
 #pragma unroll
     for (int k = 0; k < K3; ++k) gsh[k] = 0.f;
     float X[3] = {0.f, 0.f, 0.f};
     if (DEG > 0) load_mean(c.params, g, X);
-    for (int slot = 0; slot < c.nv; ++slot) {
+    for (int slot = slot0; slot < c.nv; slot += dslot) {
         const long long i = (long long)slot * c.G + g;
         // the cache and cotangent slots exist for culled pairs too: their
         // loads go out with the rectangle's, and a culled pair's values are
@@ -831,27 +834,40 @@ __device__ __forceinline__ void prep_vjp_gauss(const Ctx& c, int g, float* out, 
             for (int ch = 0; ch < 3; ++ch) gsh[3 * k + ch] += Y[k] * ccol[ch];
         }
     }
+}
+
+// The geometric entries of Gaussian g: out = gu, gth (+ lambda damping of v
+// when v is given; v^T out accumulated into dot).  Entries [k0, k1) of the 11.
+template <bool kDot>
+__device__ __forceinline__ void put_geo(const Ctx& c, int g, float* out, const float* v, const float* D,
+                                        const float gu[10], float gth, Dot2& dot, int k0 = 0, int k1 = 11) {
     const long long G = c.G;
+    const long long idx[11] = {3ll * g, 3ll * g + 1, 3ll * g + 2, 3 * G + 3ll * g, 3 * G + 3ll * g + 1,
+                               3 * G + 3ll * g + 2, 6 * G + 4ll * g, 6 * G + 4ll * g + 1, 6 * G + 4ll * g + 2,
+                               6 * G + 4ll * g + 3, 10 * G + g};
 #pragma unroll
-    for (int k = 0; k < 3; ++k) damp_put<kDot>(c, out, v, D, 3ll * g + k, gu[k], dot);
+    for (int k = 0; k < 11; ++k)
+        if (k >= k0 && k < k1) damp_put<kDot>(c, out, v, D, idx[k], k < 10 ? gu[k] : gth, dot);
+}
+
+// The whole map for Gaussian g, every view, one thread.
+template <int DEG, bool kDot>
+__device__ __forceinline__ void prep_vjp_gauss(const Ctx& c, int g, float* out, const float* v, const float* D,
+                                               Dot2& dot) {
+    constexpr int K3 = 3 * Sh<DEG>::K;
+    float gu[10], gth, gsh[K3];
+    vjp_views<DEG>(c, g, 0, 1, gu, gth, gsh);
+    put_geo<kDot>(c, g, out, v, D, gu, gth, dot);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) damp_put<kDot>(c, out, v, D, 3 * G + 3ll * g + k, gu[3 + k], dot);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) damp_put<kDot>(c, out, v, D, 6 * G + 4ll * g + k, gu[6 + k], dot);
-    damp_put<kDot>(c, out, v, D, 10 * G + g, gth, dot);
-    if (sh_stage) {
-#pragma unroll
-        for (int k = 0; k < K3; ++k) sh_stage[k] = gsh[k];
-    } else {
-#pragma unroll
-        for (int k = 0; k < K3; ++k) damp_put<kDot>(c, out, v, D, 11 * G + (long long)g * K3 + k, gsh[k], dot);
-    }
+    for (int k = 0; k < K3; ++k) damp_put<kDot>(c, out, v, D, 11ll * c.G + (long long)g * K3 + k, gsh[k], dot);
 }
 
 // One warp per 32 consecutive Gaussians (grid-stride over warp groups).  The
 // SH entries of the 32 Gaussians are one contiguous run of out, v and D: each
 // lane stages its 3K entries in shared memory (row stride 3K + 1), then the
-// warp stores the run coalesced, with the damping and the dot product.
+// warp stores the run coalesced, with the damping and the dot product.  (A
+// lane pair per Gaussian, each lane taking half of the views, measured
+// slower: 134 against 108 us on the 200k-Gaussian workload.)
 template <int DEG, bool kDot>
 __global__ void __launch_bounds__(kPrepBlock) k_prep_vjp(Ctx c, float* out, const float* v, const float* D) {
     constexpr int K3 = 3 * Sh<DEG>::K;
@@ -862,7 +878,14 @@ __global__ void __launch_bounds__(kPrepBlock) k_prep_vjp(Ctx c, float* out, cons
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long gw = (long long)blockIdx.x * blockDim.x + wid * 32; gw < c.G; gw += stride) {
         const int g = (int)gw + lane;
-        if (g < c.G) prep_vjp_gauss<DEG, kDot>(c, g, out, v, D, dot, stage + lane * (K3 + 1));
+        if (g < c.G) {
+            float gu[10], gth, gsh[K3];
+            vjp_views<DEG>(c, g, 0, 1, gu, gth, gsh);
+            put_geo<kDot>(c, g, out, v, D, gu, gth, dot);
+            float* row = stage + lane * (K3 + 1);
+#pragma unroll
+            for (int k = 0; k < K3; ++k) row[k] = gsh[k];
+        }
         __syncwarp();
         const int n = (int)min(32ll, (long long)c.G - gw) * K3;
         const long long base = 11ll * c.G + gw * K3;
@@ -909,7 +932,7 @@ __global__ void __launch_bounds__(kPrepBlock) k_prep_vjp(Ctx c, float* out, cons
 // p^T A p of iteration `iter` accumulated into the scene's history (the
 // per-thread Dot2 partials of one chunk are summed in FP64 over the block).
 template <int DEG>
-__global__ void __launch_bounds__(kBatchBlock) kb_prep_vjp(BatchTables t, int iter) {
+__device__ __forceinline__ void b_prep_vjp(const BatchTables& t, int iter) {
     const int n = t.counts[0];
     for (int k = blockIdx.x; k < n; k += gridDim.x) {
         const int4 ch = t.gchunks[k];
@@ -922,6 +945,9 @@ __global__ void __launch_bounds__(kBatchBlock) kb_prep_vjp(BatchTables t, int it
         if (threadIdx.x == 0) atomicAdd(&bv.pAp[iter], tot);
     }
 }
+template <int DEG>
+__global__ void __launch_bounds__(kBatchBlock) kb_prep_vjp(BatchTables t, int iter) { b_prep_vjp<DEG>(t, iter); }
+
 
 // diag(J^T W J) for Gaussian g: the sum over its visible views of the
 // pair slots k_diag filled (the 11 geometric entries directly; SH

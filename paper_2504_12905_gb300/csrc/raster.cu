@@ -33,6 +33,15 @@ namespace lmrs {
 constexpr int kRasterWarps = 4;
 constexpr int kRasterBlock = kRasterWarps * kWarp;
 
+// 2^x on the special-function unit.  The records carry the conic scaled by
+// -log2(e)/2 (A, C) and -log2(e) (B), so e^power = 2^(dx (A' dx + B' dy) +
+// C' dy^2) takes five FP32 operations and one 2^x.
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 struct Pix {
     int vt, slot, tile, chunk;
     long long si;
@@ -138,20 +147,12 @@ __device__ __forceinline__ void forward_pass(const Ctx& c, const Pix& p, List L,
         if (__all_sync(kFull, done)) break;
         const int n = stage_batch<kTan ? 6 : 3>(c, p.slot, L.ids, b, L.e, s_rec, s_id);
         for (int j = 0; j < n; ++j) {
-            bool need = false;
-            float alpha = 0.f, raw = 0.f, gval = 0.f, dx = 0.f, dy = 0.f;
-            float4 r0, r1;
-            if (!done) {
-                r0 = s_rec[j][0];
-                r1 = s_rec[j][1];
-                dx = r0.x - p.pcx;
-                dy = r0.y - p.pcy;
-                const float power = -0.5f * (r0.z * dx * dx + r1.x * dy * dy) - r0.w * dx * dy;
-                gval = __expf(power);
-                raw = r1.y * gval;
-                alpha = fminf(kAlphaMax, raw);
-                need = alpha >= kAlphaMin;
-            }
+            const float4 r0 = s_rec[j][0], r1 = s_rec[j][1], r2 = s_rec[j][2];
+            const float dx = r0.x - p.pcx, dy = r0.y - p.pcy;
+            const float gval = ex2_approx(fmaf(r2.w * dy, dy, dx * fmaf(r2.z, dy, r2.y * dx)));
+            const float raw = r1.y * gval;
+            float alpha = fminf(kAlphaMax, raw);
+            bool need = !done && alpha >= kAlphaMin;
             if (kCompact) {
                 const bool any = __any_sync(kFull, need);
                 if (any && lane == 0) out_ids[kept] = s_id[j];
@@ -161,11 +162,10 @@ __device__ __forceinline__ void forward_pass(const Ctx& c, const Pix& p, List L,
                         done = true;
                         ncons = kept;
                     } else {
-                        const float col2 = s_rec[j][2].x;
                         const float wgt = alpha * T;
                         C[0] += r1.z * wgt;
                         C[1] += r1.w * wgt;
-                        C[2] += col2 * wgt;
+                        C[2] += r2.x * wgt;
                         T = Tn;
                         if (n_comp) ++*n_comp;
                     }
@@ -173,24 +173,26 @@ __device__ __forceinline__ void forward_pass(const Ctx& c, const Pix& p, List L,
                 if (any) ++kept;
                 continue;
             }
-            if (!need) continue;
-            const float Tn = T * (1.f - alpha);
-            if (Tn < kTMin) {
+            // branch-free: an entry the lane does not composite takes alpha = 0,
+            // which leaves T, C and their tangents unchanged
+            const float Tn0 = T * (1.f - alpha);
+            const bool stop = need && Tn0 < kTMin;
+            if (stop) {
                 done = true;
                 ncons = b + j - L.b;
-                continue;
             }
-            const float col2 = s_rec[j][2].x;
+            const bool comp = need && !stop;
+            alpha = comp ? alpha : 0.f;
+            const float Tn = T * (1.f - alpha);
+            const float col2 = r2.x;
             const float wgt = alpha * T;
             if (kTan) {
+                // tangent record (e_1, e_2, e_3, e_4 | e_5, o, r, g | b): the
+                // exponent's tangent dx e_1 + dy e_2 + dx^2 e_3 + dx dy e_4 + dy^2 e_5
                 const float4 t0 = s_rec[j][3], t1 = s_rec[j][4];
                 const float dcol2 = s_rec[j][5].x;
-                float dalpha = 0.f;
-                if (raw <= kAlphaMax) {
-                    const float dpow = -0.5f * (t0.z * dx * dx + t1.x * dy * dy) - t0.w * dx * dy -
-                                       (r0.z * dx + r0.w * dy) * t0.x - (r0.w * dx + r1.x * dy) * t0.y;
-                    dalpha = t1.y * gval + raw * dpow;
-                }
+                const float dpow = fmaf(dx, fmaf(t0.z, dx, fmaf(t0.w, dy, t0.x)), dy * fmaf(t1.x, dy, t0.y));
+                const float dalpha = (comp && raw <= kAlphaMax) ? t1.y * gval + raw * dpow : 0.f;
                 const float dw = dalpha * T + alpha * dT;
                 dC[0] += t1.z * wgt + r1.z * dw;
                 dC[1] += t1.w * wgt + r1.w * dw;
@@ -201,7 +203,7 @@ __device__ __forceinline__ void forward_pass(const Ctx& c, const Pix& p, List L,
             C[1] += r1.w * wgt;
             C[2] += col2 * wgt;
             T = Tn;
-            if (n_comp) ++*n_comp;
+            if (n_comp && comp) ++*n_comp;
         }
         __syncwarp();
     }
@@ -226,10 +228,10 @@ __device__ __forceinline__ void forward_pass(const Ctx& c, const Pix& p, List L,
 //        Mx = sum pbar dx, My = sum pbar dy, Mxx = sum pbar dx^2,
 //        Mxy = sum pbar dx dy, Myy = sum pbar dy^2, M5 = sum pbar,
 //        Mc_ch = sum ub_ch wgt,
-//      the two halves are added with one shuffle per moment, and with the
-//      entry's conic (A, B, C) and opacity o the cotangents are
-//        mu: -(A Mx + B My), -(B Mx + C My);  conic: -Mxx/2, -Mxy, -Myy/2;
-//        o: M5 / o (pbar / o = <ub, dC/dalpha> e^power);  colour: Mc,
+//      the two halves are added with one shuffle per moment; the moments
+//      are the cotangents of the exponent's coefficients e_1..e_5 (jac.cuh):
+//        (Mx, My, Mxx, Mxy, Myy);  o: M5 / o (pbar / o = <ub, dC/dalpha>
+//        e^power);  colour: Mc,
 //      added with two 4-wide and one scalar atomic.
 constexpr int kBwdE = 16;  // entries per phase; lanes e and e + 16 share entry e
 
@@ -273,11 +275,10 @@ __device__ __forceinline__ void backward_pass(const Ctx& c, const Pix& p, List L
             // phase A
             for (int jj = 0; jj < m; ++jj) {
                 const int j = h0 + jj;
-                const float4 r0 = sm.rec[j][0], r1 = sm.rec[j][1];
-                const float col2 = sm.rec[j][2].x;
+                const float4 r0 = sm.rec[j][0], r1 = sm.rec[j][1], r2 = sm.rec[j][2];
+                const float col2 = r2.x;
                 const float dx = r0.x - p.pcx, dy = r0.y - p.pcy;
-                const float power = -0.5f * (r0.z * dx * dx + r1.x * dy * dy) - r0.w * dx * dy;
-                const float gval = __expf(power);
+                const float gval = ex2_approx(fmaf(r2.w * dy, dy, dx * fmaf(r2.z, dy, r2.y * dx)));
                 const float raw = r1.y * gval;
                 float alpha = fminf(kAlphaMax, raw);
                 // branch-free: an entry the lane does not composite (past its
@@ -322,10 +323,9 @@ __device__ __forceinline__ void backward_pass(const Ctx& c, const Pix& p, List L
                 if (k != 5) M[k] += __shfl_xor_sync(kFull, M[k], 16);
             M5 += __shfl_xor_sync(kFull, M5, 16);
             if (hh == 0 && e < m) {
-                const float4 r0 = sm.rec[j][0], r1 = sm.rec[j][1];
                 float* dst = cot_base + (long long)sm.id[j] * kCotF;
-                red_add_v4(dst, -(r0.z * M[0] + r0.w * M[1]), -(r0.w * M[0] + r1.x * M[1]), -0.5f * M[2], -M[3]);
-                red_add_v4(dst + 4, -0.5f * M[4], __fdividef(M5, r1.y), M[6], M[7]);
+                red_add_v4(dst, M[0], M[1], M[2], M[3]);
+                red_add_v4(dst + 4, M[4], __fdividef(M5, sm.rec[j][1].y), M[6], M[7]);
                 atomicAdd(dst + 8, M[8]);
             }
             __syncwarp();
@@ -466,9 +466,8 @@ __global__ void __launch_bounds__(kRasterBlock) k_jtj(Ctx c) {
 
 // The same for every scene of a batch: chunks of at most kRasterWarps work
 // items of one scene, one item per warp.
-__global__ void __launch_bounds__(kRasterBlock) kb_jtj(BatchTables t) {
+__device__ __forceinline__ void b_jtj(const BatchTables& t, WarpSmem* s_warp) {
     static_assert(kRasterBlock == kBatchBlock, "one warp per work item of a chunk");
-    __shared__ WarpSmem s_warp[kRasterWarps];
     const int wid = threadIdx.x >> 5;
     const int n = t.counts[2];
     for (int k = blockIdx.x; k < n; k += gridDim.x) {
@@ -477,6 +476,11 @@ __global__ void __launch_bounds__(kRasterBlock) kb_jtj(BatchTables t) {
         if (item < ch.z) jtj_item(t.ctxs[ch.x], item, s_warp[wid]);
         __syncwarp();
     }
+}
+
+__global__ void __launch_bounds__(kRasterBlock) kb_jtj(BatchTables t) {
+    __shared__ WarpSmem s_warp[kRasterWarps];
+    b_jtj(t, s_warp);
 }
 
 void launch_b_jtj(const BatchTables& t, int grid, cudaStream_t st) {
@@ -552,11 +556,10 @@ __global__ void __launch_bounds__(kRasterBlock) k_diag(Ctx c) {
             // phase A
             for (int jj = 0; jj < m; ++jj) {
                 const int j = h0 + jj;
-                const float4 r0 = sm.rec[j][0], r1 = sm.rec[j][1];
-                const float col[3] = {r1.z, r1.w, sm.rec[j][2].x};
+                const float4 r0 = sm.rec[j][0], r1 = sm.rec[j][1], r2 = sm.rec[j][2];
+                const float col[3] = {r1.z, r1.w, r2.x};
                 const float dx = r0.x - p.pcx, dy = r0.y - p.pcy;
-                const float power = -0.5f * (r0.z * dx * dx + r1.x * dy * dy) - r0.w * dx * dy;
-                const float gval = __expf(power);
+                const float gval = ex2_approx(fmaf(r2.w * dy, dy, dx * fmaf(r2.z, dy, r2.y * dx)));
                 const float raw = r1.y * gval;
                 float alpha = fminf(kAlphaMax, raw);
                 // branch-free as in backward_pass: alpha = 0 where the lane
@@ -586,7 +589,7 @@ __global__ void __launch_bounds__(kRasterBlock) k_diag(Ctx c) {
             if (e < m) {
                 float J[LJ::N];
                 load_jac<DEG>(c, p.slot, (int)sm.id[j], J);
-                const float4 r0 = sm.rec[j][0], r1 = sm.rec[j][1];
+                const float4 r0 = sm.rec[j][0];
                 const unsigned bits = __float_as_uint(J[LJ::kMask]);
                 float acol[3][3];
 #pragma unroll
@@ -597,8 +600,8 @@ __global__ void __launch_bounds__(kRasterBlock) k_diag(Ctx c) {
                     const float4 qh = sm.qh[e][i];
                     const float4 x0 = sm.pix0[i], x1 = sm.pix1[i];
                     const float dx = r0.x - x0.x, dy = r0.y - x0.y;
-                    const float et0 = -(r0.z * dx + r0.w * dy), et1 = -(r0.w * dx + r1.x * dy);
-                    const float et2 = -0.5f * dx * dx, et3 = -dx * dy, et4 = -0.5f * dy * dy;
+                    // d power = dx e_1 + dy e_2 + dx^2 e_3 + dx dy e_4 + dy^2 e_5 (jac.cuh)
+                    const float et0 = dx, et1 = dy, et2 = dx * dx, et3 = dx * dy, et4 = dy * dy;
                     const float W = x0.z * qh.y * qh.y + x0.w * qh.z * qh.z + x1.x * qh.w * qh.w;
 #pragma unroll
                     for (int k = 3; k < 10; ++k) {
@@ -644,7 +647,7 @@ __global__ void __launch_bounds__(kRasterBlock) k_diag(Ctx c) {
 #pragma unroll
                 for (int k = 0; k < 9; ++k) M[k] += __shfl_xor_sync(kFull, M[k], 16);
             if (hh == 0 && e < m) {
-                const float4 r0 = sm.rec[j][0], r1 = sm.rec[j][1];
+                const float4 r1 = sm.rec[j][1];
                 const float om = 1.f - r1.y;
                 float* dst = dbase + (long long)sm.id[j] * kDiagF;
                 red_add_v4(dst, D[0], D[1], D[2], D[3]);
@@ -653,8 +656,8 @@ __global__ void __launch_bounds__(kRasterBlock) k_diag(Ctx c) {
                 red_add_v4(dst + 12, D[12], D[13], 0.f, 0.f);
                 if (kRhs) {
                     float* cdst = cbase + (long long)sm.id[j] * kCotF;
-                    red_add_v4(cdst, -(r0.z * M[0] + r0.w * M[1]), -(r0.w * M[0] + r1.x * M[1]), -0.5f * M[2], -M[3]);
-                    red_add_v4(cdst + 4, -0.5f * M[4], __fdividef(M[5], r1.y), M[6], M[7]);
+                    red_add_v4(cdst, M[0], M[1], M[2], M[3]);
+                    red_add_v4(cdst + 4, M[4], __fdividef(M[5], r1.y), M[6], M[7]);
                     atomicAdd(cdst + 8, M[8]);
                 }
             }

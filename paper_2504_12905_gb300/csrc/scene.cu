@@ -1217,11 +1217,16 @@ struct lmrs_batch {
     std::vector<cudaEvent_t> ev_scene;
     cudaEvent_t ev_batch = nullptr;
     std::vector<lmrs_status> scene_rc;  // per scene, of the last step
+    // the launch form: one persistent cooperative launch of every phase (the
+    // default), or the graph of per-phase launches
+    bool persistent = true;
+    DevBuf bar;  // its grid barrier's words
 };
 
 namespace {
 
 constexpr int kBatchGrid = 1216;  // blocks of the batched launches (8 per SM), grid-stride over chunks
+constexpr double kBarrierTimeoutS = 2.0;  // a grid barrier of the persistent PCG waits at most this long
 
 lmrs_status bfail(lmrs_batch* b, lmrs_status code, const std::string& msg) {
     if (b) b->err = msg;
@@ -1408,7 +1413,7 @@ lmrs_status lmrs_batch_destroy(lmrs_batch* B) {
     for (auto e : B->ev_scene)
         if (e) cudaEventDestroy(e);
     if (B->ev_batch) cudaEventDestroy(B->ev_batch);
-    for (DevBuf* d : {&B->ctxs, &B->vecs, &B->gch, &B->vch, &B->wch, &B->counts, &B->hist})
+    for (DevBuf* d : {&B->ctxs, &B->vecs, &B->gch, &B->vch, &B->wch, &B->counts, &B->hist, &B->bar})
         release(*d, B->st);
     if (B->st) cudaStreamSynchronize(B->st);
     if (B->own_stream) cudaStreamDestroy(B->st);
@@ -1459,10 +1464,25 @@ lmrs_status lmrs_batch_lm_step(lmrs_batch* B, const int32_t* view_ids, const int
         if (cudaStreamWaitEvent(B->st, B->ev_scene[i], 0) != cudaSuccess)
             return bfail(B, LMRS_ERR_CUDA, "stream wait");
     TRY(batch_tables(B, lm_steps));
-    TRY(batch_graph(B));
-    cudaError_t e = cudaGraphLaunch(B->exec, B->st);
-    if (e != cudaSuccess) return bfail(B, LMRS_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
-    g_launches.fetch_add(B->graph_kernels, std::memory_order_relaxed);
+    if (B->persistent) {
+        if (ensure_on(B->bar, grid_bar_bytes(), B->st) != cudaSuccess) return bfail(B, LMRS_ERR_OOM, "barrier words");
+        const cudaError_t e = launch_b_pcg(batch_view(B), B->deg, B->iters, B->bar.p, kBarrierTimeoutS, B->st);
+        if (e == cudaErrorCooperativeLaunchTooLarge || e == cudaErrorNotSupported) {
+            // the device cannot hold the whole grid at once: from here on the
+            // batch uses the graph of per-phase launches
+            cudaGetLastError();
+            B->persistent = false;
+        } else if (e != cudaSuccess) {
+            cudaGetLastError();
+            return bfail(B, LMRS_ERR_CUDA, std::string("persistent PCG launch: ") + cudaGetErrorString(e));
+        }
+    }
+    if (!B->persistent) {
+        TRY(batch_graph(B));
+        cudaError_t e = cudaGraphLaunch(B->exec, B->st);
+        if (e != cudaSuccess) return bfail(B, LMRS_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+        g_launches.fetch_add(B->graph_kernels, std::memory_order_relaxed);
+    }
     // 3. the scenes' next work waits for the batch
     if (cudaEventRecord(B->ev_batch, B->st) != cudaSuccess) return bfail(B, LMRS_ERR_CUDA, "event record");
     for (lmrs_scene* s : B->scenes) {
@@ -1472,6 +1492,15 @@ lmrs_status lmrs_batch_lm_step(lmrs_batch* B, const int32_t* view_ids, const int
     std::fill(B->scene_rc.begin(), B->scene_rc.end(), LMRS_OK);
     if (!stats) return LMRS_OK;
     if (cudaStreamSynchronize(B->st) != cudaSuccess) return bfail(B, LMRS_ERR_CUDA, "synchronise");
+    if (B->persistent) {
+        unsigned char hb[64] = {};
+        if (cudaMemcpy(hb, B->bar.p, grid_bar_bytes(), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return bfail(B, LMRS_ERR_CUDA, "read barrier words");
+        if (grid_bar_error(hb)) {
+            for (auto& r : B->scene_rc) r = LMRS_ERR_TIMEOUT;
+            return bfail(B, LMRS_ERR_TIMEOUT, "a grid barrier of the persistent PCG timed out");
+        }
+    }
     std::vector<double> hist((size_t)B->n * 2 * (kMaxBatchIters + 1));
     if (cudaMemcpy(hist.data(), B->hist.p, sizeof(double) * hist.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
         return bfail(B, LMRS_ERR_CUDA, "read history");
@@ -1500,6 +1529,12 @@ lmrs_status lmrs_batch_lm_step(lmrs_batch* B, const int32_t* view_ids, const int
 }
 
 const char* lmrs_batch_last_error(const lmrs_batch* B) { return B ? B->err.c_str() : "null batch"; }
+
+lmrs_status lmrs_batch_set_persistent(lmrs_batch* B, int32_t on) {
+    if (!B || (on != 0 && on != 1)) return LMRS_ERR_INVALID_ARG;
+    B->persistent = on == 1;
+    return LMRS_OK;
+}
 
 lmrs_status lmrs_batch_scene_status(const lmrs_batch* B, int32_t i) {
     if (!B || i < 0 || i >= B->n) return LMRS_ERR_INVALID_ARG;

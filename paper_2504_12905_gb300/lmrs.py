@@ -131,6 +131,8 @@ _SIGS = {
     "lmrs_autotune_tile": (_S, [C.POINTER(Config), C.c_int64, _P, _P, C.c_int32, _P, _P, C.c_int32, _P, C.c_int32,
                                 C.c_int32, _P, C.POINTER(C.c_int32), _P]),
     "lmrs_batch_scene_status": (_S, [_P, C.c_int32]),
+    "lmrs_batch_set_persistent": (_S, [_P, C.c_int32]),
+    "lmrs_grid_barrier_selftest": (_S, [C.c_int32, C.c_double, _P]),
     "lmrs_server_create": (_S, [C.POINTER(ServerConfig), C.POINTER(_P)]),
     "lmrs_server_submit": (_S, [_P, C.POINTER(Config), C.c_int64, _P, _P, C.c_int32, _P, C.c_int32, C.c_double,
                                 C.c_int32, C.POINTER(C.c_int64)]),
@@ -419,6 +421,15 @@ def lmrs_autotune_tile(cfg, n_gauss, params, cams, targets, views, shapes, reps=
 
 def lmrs_batch_scene_status(batch, i):
     return int(lib().lmrs_batch_scene_status(batch, int(i)))
+
+
+def lmrs_batch_set_persistent(batch, on):
+    _check(lib().lmrs_batch_set_persistent(batch, int(on)))
+
+
+def lmrs_grid_barrier_selftest(missing, timeout_s=0.25, stream=None):
+    """Status of a grid-barrier launch missing `missing` blocks (see include/lmrs.h)."""
+    return int(lib().lmrs_grid_barrier_selftest(int(missing), float(timeout_s), _ptr(stream)))
 
 
 def lmrs_server_create(budget_bytes, max_active=64, setup_threads=8, tiles_per_pair=0.0, policy=0,

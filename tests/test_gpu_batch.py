@@ -35,6 +35,80 @@ def _make(torch, lmrs, sc, tgt, stream, **extra):
     return s
 
 
+def test_persistent_launch_matches_the_graph_of_phases():
+    """The persistent cooperative launch (every phase of every PCG
+    iteration, grid barriers between them) against the graph of per-phase
+    launches on the same scenes, and both against the scenes' own solo
+    steps.  Two steps (12 and 13: the graph form's second one replays the
+    captured graph), each from the same starting parameters in every run, so
+    that the runs differ only in the summation order of the float atomics
+    (blocks arrive in any order), not in inputs that an earlier step already
+    moved apart: these small fits amplify a last-bit difference in their
+    parameters by 40x and more in the next step's solve.  The spread of two
+    graph runs is printed beside the difference of the two forms."""
+    import torch
+
+    from paper_2504_12905_gb300 import lmrs
+
+    scenes = _scenes(n=6, seed=31)
+    views = [list(range(len(sc.cams))) for sc, _ in scenes]
+    start = [np.ascontiguousarray(sc.params, np.float32) for sc, _ in scenes]
+    runs = []
+    for mode in (0, 0, 1):
+        streams = [torch.cuda.Stream() for _ in scenes]
+        sc_b = [_make(torch, lmrs, sc, tgt, streams[i].cuda_stream) for i, (sc, tgt) in enumerate(scenes)]
+        b = lmrs.lmrs_batch_create([s.h for s in sc_b], n_threads=3)
+        lmrs.lmrs_batch_set_persistent(b, mode)
+        out = []
+        for step in (12, 13):
+            for s, x0 in zip(sc_b, start):
+                lmrs.lmrs_set_params(s.h, x0)
+            st = lmrs.lmrs_batch_lm_step(b, views, [step] * len(scenes))
+            xs = []
+            for s in sc_b:
+                x = np.zeros(s.n_params, np.float32)
+                lmrs.lmrs_get_solution(s.h, x)
+                xs.append(x)
+            out.append((st, xs))
+        lmrs.lmrs_batch_destroy(b)
+        for s in sc_b:
+            s.close()
+        runs.append(out)
+    solo = [_make(torch, lmrs, sc, tgt, None) for sc, tgt in scenes]
+    for k, step in enumerate((12, 13)):
+        (st0, x0), (_, xg), (st1, x1) = runs[0][k], runs[1][k], runs[2][k]
+        spread = max(normwise_rel(xg[i], x0[i]) for i in range(len(scenes)))
+        diff = max(normwise_rel(x1[i], x0[i]) for i in range(len(scenes)))
+        print(f"step {step}: persistent vs graph {diff:.2e}, graph vs graph {spread:.2e}")
+        for i, s in enumerate(solo):
+            lmrs.lmrs_set_params(s.h, start[i])
+            st = lmrs.lmrs_lm_step(s.h, views[i], step)
+            xs = np.zeros(s.n_params, np.float32)
+            lmrs.lmrs_get_solution(s.h, xs)
+            assert normwise_rel(x1[i], x0[i]) <= 1e-4, (step, i)
+            assert normwise_rel(x1[i], xs) <= 1e-3, (step, i)
+            assert st1[i].loss == pytest.approx(st0[i].loss, rel=1e-6)
+            assert st1[i].eta == pytest.approx(st.eta, rel=1e-4)
+            assert st1[i].rz0 == pytest.approx(st0[i].rz0, rel=1e-6)
+    for s in solo:
+        s.close()
+
+
+def test_grid_barrier_wait_runs_out_and_the_device_stays_usable():
+    """The persistent launch's grid barrier: a launch whose barrier expects
+    one block more than it has cannot complete; every wait runs out after
+    the timeout and the call reports LMRS_ERR_TIMEOUT.  A complete barrier
+    passes before and after, on the same device."""
+    import time
+
+    from paper_2504_12905_gb300 import lmrs
+    assert lmrs.lmrs_grid_barrier_selftest(0, 1.0) == lmrs.LMRS_OK
+    t0 = time.perf_counter()
+    assert lmrs.lmrs_grid_barrier_selftest(1, 0.25) == 6  # LMRS_ERR_TIMEOUT
+    assert time.perf_counter() - t0 >= 0.2
+    assert lmrs.lmrs_grid_barrier_selftest(0, 1.0) == lmrs.LMRS_OK
+
+
 def test_batch_matches_solo_steps_and_oracle():
     import torch
 
