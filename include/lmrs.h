@@ -99,12 +99,6 @@ typedef struct {
                                  J^T W J gains ssim_weight * w * d^2 per (sample, channel) row and J^T W r
                                  gains ssim_weight * w * d * s.  lmrs_render then renders every pixel of the
                                  step's views.  lmrs_jvp and lmrs_vjp stay the colour Jacobian's products. */
-    int32_t view_split;       /* the operator (J^T W J + damping) v is a sum over the step's views: with
-                                 view_split != 0 its preprocessing-JVP and raster run in two view groups,
-                                 the second group's on a helper stream beside the first group's raster, so
-                                 that memory-bound and instruction-bound kernels overlap.  > 0: views in the
-                                 first group (at most n_views - 1); -1: ceil(n_views / 4); 0: one group.
-                                 The result is the same up to the summation order of the atomics. */
 } lmrs_config;
 
 typedef struct {

@@ -177,9 +177,6 @@ void launch_prep_jvp(const Ctx& c, const float* v, cudaStream_t st);
 // the same for the PCG direction p <- z + beta p (beta from the device
 // scalars), formed and written back to p in the same pass
 void launch_prep_jvp_direction(const Ctx& c, const float* z, float* p, cudaStream_t st);
-// The same over the view slots [slot_begin, slot_end) only (z, when given:
-// the direction, formed for every Gaussian).
-void launch_prep_jvp_views(const Ctx& c, const float* z, float* p, int slot_begin, int slot_end, cudaStream_t st);
 // g = J^T u chained from the cotangent slots (+ lambda damping of v if v).
 // With dot, pAp = v^T g in FP64 and alpha = rz / pAp on the device.
 void launch_prep_vjp(const Ctx& c, float* g, const float* v, const float* D, bool dot, cudaStream_t st);
@@ -240,13 +237,10 @@ void launch_raster_diag(const Ctx& c, cudaStream_t st);
 // k_diag that also back-scatters the right-hand side's cotangents into c.cot
 void launch_raster_diag_rhs(const Ctx& c, cudaStream_t st);
 // Longest-first order of the work items by the traversal lengths the forward
-// render recorded: sorted[k] = work[order[k]]; with 0 < n_first < nwork, the
-// first n_first items (natural order) and the rest are ordered apart, the
-// first group first.  Scratch: keys/vals and their alternates (nwork each)
-// and radix_tmp_bytes(nwork).
-void launch_order_work(const Ctx& c, int n_first, unsigned long long* keys, unsigned int* vals,
-                       unsigned long long* keys_alt, unsigned int* vals_alt, void* tmp, size_t tmp_bytes, int2* sorted,
-                       cudaStream_t st);
+// render recorded: sorted[k] = work[order[k]].  Scratch: keys/vals and their
+// alternates (nwork each) and radix_tmp_bytes(nwork).
+void launch_order_work(const Ctx& c, unsigned long long* keys, unsigned int* vals, unsigned long long* keys_alt,
+                       unsigned int* vals_alt, void* tmp, size_t tmp_bytes, int2* sorted, cudaStream_t st);
 
 // ---- cg.cu ----------------------------------------------------------------
 void launch_precond(const Ctx& c, const float* D, float* minv, cudaStream_t st);

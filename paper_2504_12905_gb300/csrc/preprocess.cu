@@ -597,13 +597,13 @@ __device__ __forceinline__ void load_geo_tangent(const float* v, int G, int g, G
 // in shared memory).
 template <int DEG>
 __device__ __forceinline__ void prep_jvp_gauss(const Ctx& c, const GTan& d, const float* dsh, int g, int slot0,
-                                               int dslot, int slot_end) {
+                                               int dslot) {
     using L = Jac<DEG>;
     constexpr int K = Sh<DEG>::K;
     const float u[10] = {d.X[0], d.X[1], d.X[2], d.ls[0], d.ls[1], d.ls[2], d.q[0], d.q[1], d.q[2], d.q[3]};
     float X[3] = {0.f, 0.f, 0.f};
     if (DEG > 0) load_mean(c.params, g, X);
-    for (int slot = slot0; slot < slot_end; slot += dslot) {
+    for (int slot = slot0; slot < c.nv; slot += dslot) {
         const long long pair = (long long)slot * c.G + g;
         const int4 rc = c.rect[pair];
         if (rc.x > rc.y) continue;
@@ -652,9 +652,7 @@ __device__ __forceinline__ void prep_jvp_gauss(const Ctx& c, const GTan& d, cons
 // strides 3K + 1 and 11, odd, so the lanes' reads of their own rows hit
 // distinct banks).  With z given, the staged tangent is the PCG direction
 // p <- z + beta p (Alg. 1, beta from the device scalars), written back to p
-// by the thread that read it; otherwise it is v = p as given.  The launch
-// covers the view slots [slot_begin, slot_end) (the direction, when z is
-// given, is formed for every Gaussian whatever the range).
+// by the thread that read it; otherwise it is v = p as given.
 constexpr int kJvpWarps = 4;
 
 // Position in the P-vector, and in the staging area, of the i-th of the
@@ -678,8 +676,7 @@ __device__ __forceinline__ void geo_slot(long long G, int g0, int ng, int i, lon
 }
 
 template <int DEG>
-__global__ void __launch_bounds__(32 * kJvpWarps) k_prep_jvp(Ctx c, const float* __restrict__ z, float* p,
-                                                              int slot_begin, int slot_end) {
+__global__ void __launch_bounds__(32 * kJvpWarps) k_prep_jvp(Ctx c, const float* __restrict__ z, float* p) {
     constexpr int K3 = 3 * Sh<DEG>::K;
     constexpr int kThreads = 32 * kJvpWarps;
     constexpr int kShPer = (32 * K3 + kThreads - 1) / kThreads;  // SH values per thread
@@ -747,7 +744,7 @@ __global__ void __launch_bounds__(32 * kJvpWarps) k_prep_jvp(Ctx c, const float*
 #pragma unroll
         for (int k = 0; k < 4; ++k) d.q[k] = sg[6 + k];
         d.th = sg[10];
-        prep_jvp_gauss<DEG>(c, d, s_dsh + lane * (K3 + 1), g, slot_begin + (threadIdx.x >> 5), kJvpWarps, slot_end);
+        prep_jvp_gauss<DEG>(c, d, s_dsh + lane * (K3 + 1), g, threadIdx.x >> 5, kJvpWarps);
     }
 }
 
@@ -763,8 +760,7 @@ __device__ __forceinline__ void b_prep_jvp(const BatchTables& t) {
             const float* v = t.vecs[ch.x].p;
             GTan d;
             load_geo_tangent(v, c.G, g, d);
-            prep_jvp_gauss<DEG>(c, d, v + 11ll * c.G + (long long)g * 3 * Sh<DEG>::K, g, threadIdx.x >> 5, kJvpWarps,
-                                c.nv);
+            prep_jvp_gauss<DEG>(c, d, v + 11ll * c.G + (long long)g * 3 * Sh<DEG>::K, g, threadIdx.x >> 5, kJvpWarps);
         }
     }
 }
@@ -1026,9 +1022,8 @@ static void prep_fwd_deg(const Ctx& c, cudaStream_t st) {
     LMRS_LAUNCH_AS("k_prep_fwd", k_prep_fwd<DEG>, (unsigned)((n + 127) / 128), 128, 0, st, c);
 }
 template <int DEG>
-static void prep_jvp_deg(const Ctx& c, const float* z, float* p, int s0, int s1, cudaStream_t st) {
-    LMRS_LAUNCH_AS("k_prep_jvp", k_prep_jvp<DEG>, (unsigned)((c.G + 31) / 32), 32 * kJvpWarps, 0, st, c, z, p, s0,
-                   s1);
+static void prep_jvp_deg(const Ctx& c, const float* z, float* p, cudaStream_t st) {
+    LMRS_LAUNCH_AS("k_prep_jvp", k_prep_jvp<DEG>, (unsigned)((c.G + 31) / 32), 32 * kJvpWarps, 0, st, c, z, p);
 }
 template <int DEG>
 static void prep_vjp_deg(const Ctx& c, float* g, const float* v, const float* D, bool dot, cudaStream_t st) {
@@ -1054,22 +1049,24 @@ void launch_prep_fwd(const Ctx& c, cudaStream_t st) {
     }
 }
 
-void launch_prep_jvp_views(const Ctx& c, const float* z, float* p, int slot_begin, int slot_end, cudaStream_t st) {
+void launch_prep_jvp(const Ctx& c, const float* v, cudaStream_t st) {
+    // read only: k_prep_jvp writes p only when z is given
+    float* p = const_cast<float*>(v);
     switch (c.deg) {
-        case 0: prep_jvp_deg<0>(c, z, p, slot_begin, slot_end, st); break;
-        case 1: prep_jvp_deg<1>(c, z, p, slot_begin, slot_end, st); break;
-        case 2: prep_jvp_deg<2>(c, z, p, slot_begin, slot_end, st); break;
-        default: prep_jvp_deg<3>(c, z, p, slot_begin, slot_end, st); break;
+        case 0: prep_jvp_deg<0>(c, nullptr, p, st); break;
+        case 1: prep_jvp_deg<1>(c, nullptr, p, st); break;
+        case 2: prep_jvp_deg<2>(c, nullptr, p, st); break;
+        default: prep_jvp_deg<3>(c, nullptr, p, st); break;
     }
 }
 
-void launch_prep_jvp(const Ctx& c, const float* v, cudaStream_t st) {
-    // read only: k_prep_jvp writes p only when z is given
-    launch_prep_jvp_views(c, nullptr, const_cast<float*>(v), 0, c.nv, st);
-}
-
 void launch_prep_jvp_direction(const Ctx& c, const float* z, float* p, cudaStream_t st) {
-    launch_prep_jvp_views(c, z, p, 0, c.nv, st);
+    switch (c.deg) {
+        case 0: prep_jvp_deg<0>(c, z, p, st); break;
+        case 1: prep_jvp_deg<1>(c, z, p, st); break;
+        case 2: prep_jvp_deg<2>(c, z, p, st); break;
+        default: prep_jvp_deg<3>(c, z, p, st); break;
+    }
 }
 
 void launch_prep_vjp(const Ctx& c, float* g, const float* v, const float* D, bool dot, cudaStream_t st) {

@@ -923,12 +923,10 @@ void launch_importance(const Ctx& c, long long lm_step, unsigned long long seed,
 
 static unsigned raster_grid(const Ctx& c) { return (unsigned)((c.nwork + kRasterWarps - 1) / kRasterWarps); }
 
-// Ascending key = descending cost; the items from n_first on (the second view
-// group: the natural order is slot-major) sort after the first n_first.
-__global__ void k_order_keys(const int* cost, int n, int n_first, unsigned long long* keys, unsigned int* vals) {
+__global__ void k_order_keys(const int* cost, int n, unsigned long long* keys, unsigned int* vals) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
-    keys[k] = (k >= n_first ? 1ull << 32 : 0ull) | (0xFFFFFFFFull - (unsigned long long)(unsigned int)cost[k]);
+    keys[k] = 0xFFFFFFFFull - (unsigned long long)(unsigned int)cost[k];  // ascending key = descending cost
     vals[k] = (unsigned int)k;
 }
 
@@ -937,14 +935,12 @@ __global__ void k_gather_work(const int2* work, const unsigned int* order, int n
     if (k < n) sorted[k] = work[order[k]];
 }
 
-void launch_order_work(const Ctx& c, int n_first, unsigned long long* keys, unsigned int* vals,
-                       unsigned long long* keys_alt, unsigned int* vals_alt, void* tmp, size_t tmp_bytes, int2* sorted,
-                       cudaStream_t st) {
+void launch_order_work(const Ctx& c, unsigned long long* keys, unsigned int* vals, unsigned long long* keys_alt,
+                       unsigned int* vals_alt, void* tmp, size_t tmp_bytes, int2* sorted, cudaStream_t st) {
     if (c.nwork <= 0) return;
     const unsigned grid = (unsigned)((c.nwork + 255) / 256);
-    const bool split = n_first > 0 && n_first < c.nwork;
-    LMRS_LAUNCH(k_order_keys, grid, 256, 0, st, c.item_cost, c.nwork, split ? n_first : c.nwork, keys, vals);
-    radix_sort(keys, vals, keys_alt, vals_alt, c.nwork, split ? 33 : 32, tmp, tmp_bytes, st);
+    LMRS_LAUNCH(k_order_keys, grid, 256, 0, st, c.item_cost, c.nwork, keys, vals);
+    radix_sort(keys, vals, keys_alt, vals_alt, c.nwork, 32, tmp, tmp_bytes, st);
     LMRS_LAUNCH(k_gather_work, grid, 256, 0, st, c.work, vals, c.nwork, sorted);
 }
 

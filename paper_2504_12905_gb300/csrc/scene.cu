@@ -74,10 +74,6 @@ struct lmrs_scene {
     int n_cams = 0, W = 0, H = 0, tiles_x = 0, tiles_y = 0, T = 0;
     std::vector<lmrs_camera> cams_h;  // host copy (view sampling)
     cudaStream_t st = nullptr;
-    // the view-split operator (cfg.view_split): a helper stream and the
-    // events that fork it from st and join it back
-    cudaStream_t st2 = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::string err;
     const float* targets = nullptr;
     // device state
@@ -97,7 +93,6 @@ struct lmrs_scene {
     int nv = 0;
     long long step = 0, S = 0, npairs = 0, nvisible = 0;
     int nwork = 0;
-    int nsplit = 0, nwork_a = 0;  // views of the first group (0: one group) and its work items
     int layout_nv = -1;
     std::vector<int> tile_off_h;
     bool preprocessed = false, rendered = false, have_D = false;
@@ -358,13 +353,8 @@ lmrs_status build_layout(lmrs_scene* s) {
     std::vector<int> toff(nT + 1, 0);
     std::vector<float> w(nT);
     std::vector<int2> work;
-    // the view groups of the operator: the first nsplit slots, then the rest
-    const int vs = s->cfg.view_split;
-    s->nsplit = (!s->st2 || s->nv < 2) ? 0 : vs > 0 ? std::min(vs, s->nv - 1) : (s->nv + 3) / 4;
-    s->nwork_a = 0;
     for (int slot = 0; slot < s->nv; ++slot)
         for (int t = 0; t < s->T; ++t) {
-            if (t == 0 && slot == s->nsplit) s->nwork_a = (int)work.size();
             const int tx = t % s->tiles_x, ty = t / s->tiles_x;
             const int vw = std::min(s->cfg.tile_w, s->W - tx * s->cfg.tile_w);
             const int vh = std::min(s->cfg.tile_h, s->H - ty * s->cfg.tile_h);
@@ -455,42 +445,11 @@ lmrs_status do_rhs_diag(lmrs_scene* s, float* b) {
     return LMRS_OK;
 }
 
-// The preprocessing-JVP of p (with z given: the PCG direction p <- z + beta p
-// first) and the fused raster, into the cotangent slots.  With view groups
-// (cfg.view_split), the first group's views run on st; the second group's
-// preprocessing waits for the first's (it reads the p that one writes) and
-// runs with its raster on the helper stream, beside the first group's
-// raster, so the memory-bound preprocessing overlaps the issue-bound raster;
-// st waits for the helper before the transposed map.  The natural and the
-// longest-first work orders both list the first group's items first.
-lmrs_status operator_pass(lmrs_scene* s, const Ctx& c, const float* z, float* p) {
-    const int h = s->nsplit;
-    if (h <= 0 || h >= s->nv) {
-        if (z) launch_prep_jvp_direction(c, z, p, s->st);
-        else launch_prep_jvp(c, p, s->st);
-        launch_raster_jtj(c, s->st);
-        return LMRS_OK;
-    }
-    launch_prep_jvp_views(c, z, p, 0, h, s->st);
-    CK(s, cudaEventRecord(s->ev_fork, s->st));
-    CK(s, cudaStreamWaitEvent(s->st2, s->ev_fork, 0));
-    launch_prep_jvp_views(c, nullptr, p, h, s->nv, s->st2);
-    Ctx cb = c;
-    cb.work = c.work + s->nwork_a;
-    cb.nwork = c.nwork - s->nwork_a;
-    launch_raster_jtj(cb, s->st2);
-    CK(s, cudaEventRecord(s->ev_join, s->st2));
-    Ctx ca = c;
-    ca.nwork = s->nwork_a;
-    launch_raster_jtj(ca, s->st);
-    CK(s, cudaStreamWaitEvent(s->st, s->ev_join, 0));
-    return LMRS_OK;
-}
-
 // (J^T W J + lambda damp) v -> out, device pointers.
 lmrs_status do_jtjv(lmrs_scene* s, const float* v, float* out) {
     Ctx c = s->ctx();
-    TRY(operator_pass(s, c, nullptr, const_cast<float*>(v)));
+    launch_prep_jvp(c, v, s->st);
+    launch_raster_jtj(c, s->st);
     launch_prep_vjp(c, out, v, s->D.as<float>(), false, s->st);
     CHECK_LAUNCH(s);
     return LMRS_OK;
@@ -508,7 +467,8 @@ lmrs_status do_cg(lmrs_scene* s, const float* b, float* x, int iters) {
     launch_precond(c, D, minv, s->st);
     launch_cg_init(c, b, minv, x, r, z, p, s->st);
     for (int it = 0; it < iters; ++it) {
-        TRY(operator_pass(s, c, z, p));                  // p = z + beta p; J^T W J p into the cotangent slots
+        launch_prep_jvp_direction(c, z, p, s->st);       // p = z + beta p, tangent features of p
+        launch_raster_jtj(c, s->st);                     // J^T W J p into the cotangent slots
         launch_prep_vjp(c, Ap, p, D, true, s->st);       // Ap (+ damping), p^T A p, alpha
         launch_cg_update(c, it, p, Ap, minv, x, r, z, s->st);  // x, r, z, beta
     }
@@ -576,7 +536,7 @@ lmrs_status lmrs_scene_create(const lmrs_config* cfg, int64_t n_gauss, const flo
         cfg->tile_w * cfg->tile_h > 256 || !(cfg->sample_frac > 0.0) || cfg->cg_iters < 0 ||
         (cfg->damping_mode != 0 && cfg->damping_mode != 1) || (cfg->weight_mode != 0 && cfg->weight_mode != 1) ||
         !(cfg->lambda >= 0.0) || cfg->sample_dist < 0 || cfg->sample_dist > 2 ||
-        !(cfg->ssim_weight >= 0.0 && cfg->ssim_weight < 1e30) || cfg->view_split < -1)
+        !(cfg->ssim_weight >= 0.0 && cfg->ssim_weight < 1e30))
         return LMRS_ERR_INVALID_ARG;
     for (int i = 0; i < n_cams; ++i)
         if (cams_host[i].width != cams_host[0].width || cams_host[i].height != cams_host[0].height ||
@@ -611,19 +571,6 @@ lmrs_status lmrs_scene_create(const lmrs_config* cfg, int64_t n_gauss, const flo
     take(s->partials, sizeof(double) * kMaxPartials);
     take(s->counter, sizeof(unsigned int) * 4);
     take(s->total, sizeof(unsigned long long) * 4);
-    if (rc == LMRS_OK && cfg->view_split != 0) {
-        // the helper stream at the highest priority, so that the second view
-        // group's blocks are dispatched as soon as the first group's raster
-        // frees a slot
-        int lo = 0, hi = 0;
-        if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess ||
-            cudaStreamCreateWithPriority(&s->st2, cudaStreamNonBlocking, hi) != cudaSuccess ||
-            cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming) != cudaSuccess) {
-            cudaGetLastError();
-            rc = LMRS_ERR_CUDA;
-        }
-    }
     if (rc != LMRS_OK) {
         lmrs_scene_destroy(s);
         return rc;
@@ -651,13 +598,9 @@ lmrs_status lmrs_scene_create(const lmrs_config* cfg, int64_t n_gauss, const flo
 lmrs_status lmrs_scene_destroy(lmrs_scene* s) {
     if (!s) return LMRS_ERR_INVALID_ARG;
     if (s->st) cudaStreamSynchronize(s->st);
-    if (s->st2) cudaStreamSynchronize(s->st2);
     for (DevBuf* b : s->bufs())
         release(*b, s->st);
     cudaStreamSynchronize(s->st);
-    if (s->st2) cudaStreamDestroy(s->st2);
-    if (s->ev_fork) cudaEventDestroy(s->ev_fork);
-    if (s->ev_join) cudaEventDestroy(s->ev_join);
     trim_pool();
     delete s;
     return LMRS_OK;
@@ -809,7 +752,7 @@ lmrs_status do_render(lmrs_scene* s, float* images_dev, float* residuals_dev, bo
     } else if (images_dev) {
         launch_raster_full(c, images_dev, s->st);
     }
-    launch_order_work(c, s->nsplit > 0 ? s->nwork_a : 0, s->okeys.as<unsigned long long>(), s->ovals.as<unsigned int>(),
+    launch_order_work(c, s->okeys.as<unsigned long long>(), s->ovals.as<unsigned int>(),
                       s->okeys_alt.as<unsigned long long>(), s->ovals_alt.as<unsigned int>(), s->otmp.p, s->otmp.cap,
                       s->work_sorted.as<int2>(), s->st);
     CHECK_LAUNCH(s);

@@ -39,7 +39,7 @@ class Config(C.Structure):
                 ("lambda_", C.c_double), ("damping_mode", C.c_int32), ("cg_iters", C.c_int32),
                 ("lr_warm", C.c_double), ("lr_cap", C.c_double), ("color_bound", C.c_double),
                 ("warm_iters", C.c_int32), ("cache_bf16", C.c_int32), ("seed", C.c_uint64),
-                ("sample_dist", C.c_int32), ("ssim_weight", C.c_double), ("view_split", C.c_int32)]
+                ("sample_dist", C.c_int32), ("ssim_weight", C.c_double)]
 
 
 class CgStats(C.Structure):

@@ -43,8 +43,7 @@ class Pair:
         self.targets = None if targets is None else torch.from_numpy(targets).cuda()
         self.gpu = lmrs.Scene(torch.from_numpy(scene.params).cuda(), scene.cams, scene.n_gauss, scene.sh_degree,
                               targets=self.targets, **cfg)
-        # device-only settings: the BF16 caches and the operator's view groups
-        ocfg = {("lambda_" if k == "lambda" else k): v for k, v in cfg.items() if k not in ("cache_bf16", "view_split")}
+        ocfg = {("lambda_" if k == "lambda" else k): v for k, v in cfg.items() if k != "cache_bf16"}
         self.orc = oracle.OracleScene(scene.params, scene.cams, scene.n_gauss, scene.sh_degree, targets=targets, **ocfg)
         self.P = self.gpu.n_params
         assert self.P == self.orc.n_params
