@@ -593,9 +593,22 @@ __device__ __forceinline__ void row_range(const Ctx& c, int nchunk, const unsign
     e = sr + 1 < c.nv * c.tiles_y ? mat[(long long)(sr + 1) * nchunk] : *total;
 }
 
-// Tile counts of one (slot, row) per block: a difference array over the
-// row's columns in shared memory (+1 at x0, -1 at x1 + 1 per entry), then its
-// prefix, written as cnt[slot * T + row * tiles_x + x].
+// A row list is placed in kRowSegs segments of its entries (in order), so
+// that a dense row's work spreads over several blocks; every (tile, segment)
+// has its own count and start, and a tile's list is its segments' runs one
+// after the other, in row-list order.
+constexpr int kRowSegs = 8;
+
+__device__ __forceinline__ void seg_range(unsigned b, unsigned e, int seg, unsigned& sb, unsigned& se) {
+    const unsigned long long n = e - b;
+    sb = b + (unsigned)(n * (unsigned long long)seg / kRowSegs);
+    se = b + (unsigned)(n * (unsigned long long)(seg + 1) / kRowSegs);
+}
+
+// Tile counts of one (slot, row, segment) per block: a difference array over
+// the row's columns in shared memory (+1 at x0, -1 at x1 + 1 per entry), then
+// its prefix, written as cnt[(slot * T + row * tiles_x + x) * kRowSegs + seg]
+// (the scan over that order gives every segment's start in its tile's list).
 __global__ void __launch_bounds__(kBinBlock) k_tile_count(Ctx c, int nchunk, const unsigned* mat,
                                                           const unsigned* rtotal, const unsigned long long* rl,
                                                           unsigned* cnt) {
@@ -604,9 +617,10 @@ __global__ void __launch_bounds__(kBinBlock) k_tile_count(Ctx c, int nchunk, con
     int* s_d = reinterpret_cast<int*>(bin_smem);  // [nx + 1]
     for (int x = threadIdx.x; x <= nx; x += kBinBlock) s_d[x] = 0;
     __syncthreads();
-    const int sr = blockIdx.x, slot = sr / c.tiles_y, row = sr - slot * c.tiles_y;
-    unsigned b, e;
-    row_range(c, nchunk, mat, rtotal, sr, b, e);
+    const int sr = blockIdx.x, slot = sr / c.tiles_y, row = sr - slot * c.tiles_y, seg = blockIdx.y;
+    unsigned rb, re, b, e;
+    row_range(c, nchunk, mat, rtotal, sr, rb, re);
+    seg_range(rb, re, seg, b, e);
     for (unsigned k = b + threadIdx.x; k < e; k += kBinBlock) {
         unsigned g;
         int x0, x1;
@@ -619,7 +633,7 @@ __global__ void __launch_bounds__(kBinBlock) k_tile_count(Ctx c, int nchunk, con
     if (threadIdx.x < 32) {  // prefix over the columns, 32 at a time
         const int lane = threadIdx.x;
         int carry = 0;
-        unsigned* o = cnt + (long long)slot * c.T + (long long)row * nx;
+        unsigned* o = cnt + ((long long)slot * c.T + (long long)row * nx) * kRowSegs;
         for (int x0 = 0; x0 < nx; x0 += 32) {
             const int x = x0 + lane;
             int v = x < nx ? s_d[x] : 0;
@@ -628,19 +642,20 @@ __global__ void __launch_bounds__(kBinBlock) k_tile_count(Ctx c, int nchunk, con
                 const int y = __shfl_up_sync(kFull, v, off);
                 if (lane >= off) v += y;
             }
-            if (x < nx) o[x] = (unsigned)(carry + v);
+            if (x < nx) o[(long long)x * kRowSegs + seg] = (unsigned)(carry + v);
             carry += __shfl_sync(kFull, v, 31);
         }
     }
 }
 
-// One block per (slot, row, group of kColGroup columns); warp w owns the
-// group's columns x = x0g + w + kColWarps q (q < kColsPerWarp) and walks the
-// row list once, kColRounds rounds of 32 entries at a time (the loads of a
-// batch go out together): per owned column one ballot of the entries
-// covering it, each covering lane writing at the column's running offset +
-// its rank.  Every column's list is appended in order.  Splitting a row over
-// column groups spreads its work over several SMs.
+// One block per (slot, row, group of kColGroup columns, segment); warp w owns
+// the group's columns x = x0g + w + kColWarps q (q < kColsPerWarp) and walks
+// the segment of the row list once, kColRounds rounds of 32 entries at a
+// time (the loads of a batch go out together): per owned column one ballot
+// of the entries covering it, each covering lane writing at the (column,
+// segment)'s running offset + its rank.  Every column's list is appended in
+// order.  Splitting a row over column groups and segments spreads its work
+// over several SMs.
 constexpr int kColWarps = 8;
 constexpr int kColsPerWarp = 4;
 constexpr int kColGroup = kColWarps * kColsPerWarp;
@@ -653,12 +668,13 @@ __global__ void __launch_bounds__(kColBlock) k_tile_place(Ctx c, int nchunk, con
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     const int nx = c.tiles_x;
-    const int sr = blockIdx.x, slot = sr / c.tiles_y, row = sr - slot * c.tiles_y;
+    const int sr = blockIdx.x, slot = sr / c.tiles_y, row = sr - slot * c.tiles_y, seg = blockIdx.z;
     const int x0g = blockIdx.y * kColGroup;
     if (x0g + wid >= nx) return;  // this warp owns no column of the row
     const long long t0 = (long long)slot * c.T + (long long)row * nx;
-    unsigned b, e;
-    row_range(c, nchunk, mat, rtotal, sr, b, e);
+    unsigned rb, re, b, e;
+    row_range(c, nchunk, mat, rtotal, sr, rb, re);
+    seg_range(rb, re, seg, b, e);
     // its columns inside the row: the ballots of the others are skipped
     const int nq = min(kColsPerWarp, (nx - 1 - x0g - wid) / kColWarps + 1);
     unsigned off[kColsPerWarp];
@@ -666,7 +682,7 @@ __global__ void __launch_bounds__(kColBlock) k_tile_place(Ctx c, int nchunk, con
 #pragma unroll
     for (int q = 0; q < kColsPerWarp; ++q) {
         col[q] = x0g + wid + kColWarps * q;
-        off[q] = q < nq ? start[t0 + col[q]] : 0u;
+        off[q] = q < nq ? start[(t0 + col[q]) * kRowSegs + seg] : 0u;
     }
     for (unsigned base = b; base < e; base += 32 * kColRounds) {
         unsigned long long v[kColRounds];
@@ -696,8 +712,8 @@ __global__ void k_tile_ranges(Ctx c, const unsigned* start, const unsigned* tota
     const long long vt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nvt = (long long)c.nv * c.T;
     if (vt >= nvt) return;
-    const unsigned b = start[vt];
-    const unsigned e = vt + 1 < nvt ? start[vt + 1] : *total32;
+    const unsigned b = start[vt * kRowSegs];
+    const unsigned e = vt + 1 < nvt ? start[(vt + 1) * kRowSegs] : *total32;
     c.ranges[vt] = make_int2((int)b, (int)e);
     if (vt == 0) c.sc->n_list = *total32;
 }
@@ -713,6 +729,7 @@ bool bin_rows_fit(const Ctx& c) {
 }
 
 size_t bin_row_mat_elems(const Ctx& c) { return (size_t)c.nv * c.tiles_y * bin_chunks(c); }
+size_t bin_tile_count_elems(const Ctx& c) { return (size_t)c.nv * c.T * kRowSegs; }
 size_t bin_scan_tmp_bytes(long long n) { return scan_tmp_elems<unsigned int>(n) * sizeof(unsigned int); }
 
 void bin_rows(const Ctx& c, unsigned* mat, unsigned long long* rl, unsigned* rtotal, void* tmp, cudaStream_t st) {
@@ -729,10 +746,10 @@ void bin_tiles(const Ctx& c, const unsigned* mat, const unsigned* rtotal, const 
     const unsigned rows = (unsigned)(c.nv * c.tiles_y);
     const size_t smem = sizeof(int) * (c.tiles_x + 1);
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_tile_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    LMRS_LAUNCH(k_tile_count, rows, kBinBlock, smem, st, c, bin_chunks(c), mat, rtotal, rl, cnt);
+    LMRS_LAUNCH(k_tile_count, dim3(rows, kRowSegs), kBinBlock, smem, st, c, bin_chunks(c), mat, rtotal, rl, cnt);
     const long long nvt = (long long)c.nv * c.T;
-    scan_rec<unsigned int>(cnt, nvt, etotal, static_cast<unsigned*>(tmp), st);
-    const dim3 pgrid(rows, (unsigned)((c.tiles_x + kColGroup - 1) / kColGroup));
+    scan_rec<unsigned int>(cnt, nvt * kRowSegs, etotal, static_cast<unsigned*>(tmp), st);
+    const dim3 pgrid(rows, (unsigned)((c.tiles_x + kColGroup - 1) / kColGroup), kRowSegs);
     LMRS_LAUNCH(k_tile_place, pgrid, kColBlock, 0, st, c, bin_chunks(c), mat, rtotal, rl, cnt);
     LMRS_LAUNCH(k_tile_ranges, (unsigned)((nvt + 255) / 256), 256, 0, st, c, cnt, etotal);
 }

@@ -200,11 +200,13 @@ size_t radix_tmp_bytes(long long n);
 // index and the pair's tile columns packed in 64 bits; counts per
 // (slot, row, chunk) in mat, bin_row_mat_elems of them, scanned in place,
 // 32-bit total in *rtotal); bin_tiles places the row lists' pairs into the
-// tiles (per-tile counts in cnt, nv * T of them, scanned into the lists'
-// starts, total in *etotal) and writes the ranges.  tmp: scan scratch of
-// bin_scan_tmp_bytes(max(mat elements, nv * T)).
+// tiles (counts per (tile, segment of its row list) in cnt,
+// bin_tile_count_elems of them, scanned into the runs' starts, total in
+// *etotal) and writes the ranges.  tmp: scan scratch of
+// bin_scan_tmp_bytes(max(mat elements, tile-count elements)).
 bool bin_rows_fit(const Ctx& c);
 size_t bin_row_mat_elems(const Ctx& c);
+size_t bin_tile_count_elems(const Ctx& c);
 size_t bin_scan_tmp_bytes(long long n);
 void bin_rows(const Ctx& c, unsigned* mat, unsigned long long* rl, unsigned* rtotal, void* tmp, cudaStream_t st);
 void bin_tiles(const Ctx& c, const unsigned* mat, const unsigned* rtotal, const unsigned long long* rl, unsigned* cnt,

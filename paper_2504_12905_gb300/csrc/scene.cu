@@ -697,7 +697,7 @@ lmrs_status lmrs_preprocess(lmrs_scene* s, const int32_t* view_ids, int32_t n_vi
     TRY(ensure(s, s->ids, sizeof(unsigned int) * np));
     TRY(ensure(s, s->cids, sizeof(unsigned int) * np * (size_t)s->max_items));
     if (rows) {
-        const size_t nmat = bin_row_mat_elems(c), nvt = (size_t)s->nv * s->T;
+        const size_t nmat = bin_row_mat_elems(c), nvt = bin_tile_count_elems(c);
         TRY(ensure(s, s->binmat, sizeof(unsigned) * nmat));
         TRY(ensure(s, s->tcnt, sizeof(unsigned) * nvt));
         TRY(ensure(s, s->rowl, sizeof(unsigned long long) * std::max<size_t>((size_t)tot[2], 1)));
@@ -1122,9 +1122,10 @@ int64_t lmrs_footprint_bytes(const lmrs_config* cfg, int64_t n_gauss, int32_t n_
     // offset 1, residual 12, FP32 and BF16 caches 12 + 4 + 6 + 2, stop index 4,
     // importance weight 4, SSIM values 24
     const double per_sample = 41 + (cfg->sample_dist != 0 ? 4 : 0) + (cfg->ssim_weight > 0.0 ? 24 : 0);
-    // tile offset, weight, range 16; compact lengths 4 per item; work items
-    // and their ordering buffers 36
-    const double per_view_tile = 16 + 4.0 * max_items;
+    // tile offset, weight, range 16; the binning's counts per (tile, row-list
+    // segment) 16; compact lengths 4 per item; work items and their ordering
+    // buffers 36
+    const double per_view_tile = 32 + 4.0 * max_items;
     const double per_item = 36;
     const double fixed = 9 * 4 * P + 4.0 * kGaussF4 * 4 * G + (double)sizeof(CamDev) * n_cams +
                          sizeof(double) * kMaxPartials + 65536;
