@@ -23,13 +23,14 @@ struct Sh {
 //   d power = dx e_1 + dy e_2 + dx^2 e_3 + dx dy e_4 + dy^2 e_5
 // with e_1 = -(A dmu_x + B dmu_y), e_2 = -(B dmu_x + C dmu_y), e_3 = -dA / 2,
 // e_4 = -dB, e_5 = -dC / 2 (dmu, dA, ... the tangents of the mean and conic);
-// then the opacity o and the colour (r, g, b).  So the tangent of the exponent
-// at a pixel takes five operations, and the cotangents of e_1..e_5 are the
-// plain moments (sum pbar dx, sum pbar dy, sum pbar dx^2, ...) of the
+// then log(o) and the colour (r, g, b).  So the tangent of the exponent at a
+// pixel takes five operations, alpha = o e^power moves by alpha (d power +
+// d log o), and the cotangents of e_1..e_5 and log(o) are the plain moments
+// (sum pbar dx, sum pbar dy, sum pbar dx^2, ..., sum pbar) of the
 // back-scatter.  Layout (floats; jac_f4(DEG) float4 planes per pair):
 //   [0, 6)    d(e_1, e_2) / dX                       (row-major 2 x 3)
 //   [6, 36)   d(e_3, e_4, e_5) / d(X, log-scale, q)  (row-major 3 x 10)
-//   [36]      d o / d logit = o (1 - o)
+//   [36]      d log(o) / d logit = 1 - o
 //   [37]      bit ch set: colour channel ch not clamped
 //   [38, 47)  d colour / dX through the view direction (row-major 3 x 3, DEG > 0)
 template <int DEG>

@@ -491,7 +491,7 @@ __device__ __forceinline__ void pair_jacobian(const Prim& P, const CamDev& cam, 
         J[L::kCon + 10 + col] = -out[3];
         J[L::kCon + 20 + col] = -0.5f * out[4];
     }
-    J[L::kOp] = P.o * (1.f - P.o);
+    J[L::kOp] = 1.f - P.o;  // d log(o) / d logit
     unsigned bits = 0u;
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch)
@@ -621,7 +621,7 @@ __device__ __forceinline__ void prep_jvp_gauss(const Ctx& c, const GTan& d, cons
             for (int k = 0; k < 10; ++k) a += J[L::kCon + 10 * r + k] * u[k];
             o[2 + r] = a;
         }
-        o[5] = J[L::kOp] * d.th;
+        o[5] = J[L::kOp] * d.th;  // tangent of log(o)
         const unsigned bits = __float_as_uint(J[L::kMask]);
         float v3[3] = {0.f, 0.f, 0.f};
 #pragma unroll

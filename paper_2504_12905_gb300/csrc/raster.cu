@@ -187,12 +187,13 @@ __device__ __forceinline__ void forward_pass(const Ctx& c, const Pix& p, List L,
             const float col2 = r2.x;
             const float wgt = alpha * T;
             if (kTan) {
-                // tangent record (e_1, e_2, e_3, e_4 | e_5, o, r, g | b): the
-                // exponent's tangent dx e_1 + dy e_2 + dx^2 e_3 + dx dy e_4 + dy^2 e_5
+                // tangent record (e_1, e_2, e_3, e_4 | e_5, log o, r, g | b):
+                // alpha moves by raw (dx e_1 + dy e_2 + dx^2 e_3 + dx dy e_4 +
+                // dy^2 e_5 + d log o) where it is not clamped
                 const float4 t0 = s_rec[j][3], t1 = s_rec[j][4];
                 const float dcol2 = s_rec[j][5].x;
-                const float dpow = fmaf(dx, fmaf(t0.z, dx, fmaf(t0.w, dy, t0.x)), dy * fmaf(t1.x, dy, t0.y));
-                const float dalpha = (comp && raw <= kAlphaMax) ? t1.y * gval + raw * dpow : 0.f;
+                const float dlin = fmaf(dx, fmaf(t0.z, dx, fmaf(t0.w, dy, t0.x)), fmaf(dy, fmaf(t1.x, dy, t0.y), t1.y));
+                const float dalpha = (comp && raw <= kAlphaMax) ? raw * dlin : 0.f;
                 const float dw = dalpha * T + alpha * dT;
                 dC[0] += t1.z * wgt + r1.z * dw;
                 dC[1] += t1.w * wgt + r1.w * dw;
@@ -230,8 +231,8 @@ __device__ __forceinline__ void forward_pass(const Ctx& c, const Pix& p, List L,
 //        Mc_ch = sum ub_ch wgt,
 //      the two halves are added with one shuffle per moment; the moments
 //      are the cotangents of the exponent's coefficients e_1..e_5 (jac.cuh):
-//        (Mx, My, Mxx, Mxy, Myy);  o: M5 / o (pbar / o = <ub, dC/dalpha>
-//        e^power);  colour: Mc,
+//        (Mx, My, Mxx, Mxy, Myy);  log o: M5 (alpha = o e^power, so
+//        d alpha / d log o = raw);  colour: Mc,
 //      added with two 4-wide and one scalar atomic.
 constexpr int kBwdE = 16;  // entries per phase; lanes e and e + 16 share entry e
 
@@ -325,7 +326,7 @@ __device__ __forceinline__ void backward_pass(const Ctx& c, const Pix& p, List L
             if (hh == 0 && e < m) {
                 float* dst = cot_base + (long long)sm.id[j] * kCotF;
                 red_add_v4(dst, M[0], M[1], M[2], M[3]);
-                red_add_v4(dst + 4, M[4], __fdividef(M5, sm.rec[j][1].y), M[6], M[7]);
+                red_add_v4(dst + 4, M[4], M5, M[6], M[7]);
                 atomicAdd(dst + 8, M[8]);
             }
             __syncwarp();
@@ -445,16 +446,80 @@ __global__ void __launch_bounds__(kRasterBlock) k_vjp(Ctx c, const float* u) {
     backward_pass(c, p, compact_list(c, p), s_warp[wid], ub, Cf, ncons);
 }
 
+// The JVP pass of k_jtj (Alg. 3 over the compact list).  Within an LM step
+// the primal is fixed, so each lane's stopping position (lane_end, from the
+// forward render's cache) replaces the termination test, and the final
+// colour comes from the cache: the pass carries T and the tangents only.
+// With kColour it also accumulates the primal colour C, for the BF16 cache
+// mode, whose cached colour is too coarse for the back-scatter's suffix
+// Cf - C_<=n.  alpha >= 1/255 is tested on raw: the clamp at 0.99 is above
+// the threshold, so the decision is the same.
+template <bool kColour>
+__device__ __forceinline__ void jvp_pass(const Ctx& c, const Pix& p, List L, int lane_end, int warp_end,
+                                         float4 (*s_rec)[kRecF4], unsigned* s_id, float C[3], float dC[3]) {
+    float T = 1.f, dT = 0.f;
+    C[0] = C[1] = C[2] = 0.f;
+    dC[0] = dC[1] = dC[2] = 0.f;
+    for (int b = L.b; b < warp_end; b += 32) {
+        const int n = stage_batch<6>(c, p.slot, L.ids, b, warp_end, s_rec, s_id);
+        const int rem = lane_end - b;
+        for (int j = 0; j < n; ++j) {
+            const float4 r0 = s_rec[j][0], r1 = s_rec[j][1], r2 = s_rec[j][2];
+            const float dx = r0.x - p.pcx, dy = r0.y - p.pcy;
+            const float raw = r1.y * ex2_approx(fmaf(r2.w * dy, dy, dx * fmaf(r2.z, dy, r2.y * dx)));
+            // alpha = 0 where the lane does not composite the entry: T, C and
+            // the tangents stay as they are
+            const bool on = j < rem && raw >= kAlphaMin;
+            const float alpha = on ? fminf(kAlphaMax, raw) : 0.f;
+            const float4 t0 = s_rec[j][3], t1 = s_rec[j][4];
+            const float dcol2 = s_rec[j][5].x;
+            const float dlin = fmaf(dx, fmaf(t0.z, dx, fmaf(t0.w, dy, t0.x)), fmaf(dy, fmaf(t1.x, dy, t0.y), t1.y));
+            const float dalpha = (on && raw <= kAlphaMax) ? raw * dlin : 0.f;
+            const float wgt = alpha * T;
+            const float dw = fmaf(dalpha, T, alpha * dT);
+            dC[0] += t1.z * wgt + r1.z * dw;
+            dC[1] += t1.w * wgt + r1.w * dw;
+            dC[2] += dcol2 * wgt + r2.x * dw;
+            if (kColour) {
+                C[0] += r1.z * wgt;
+                C[1] += r1.w * wgt;
+                C[2] += r2.x * wgt;
+            }
+            const float om = 1.f - alpha;
+            dT = dT * om - T * dalpha;
+            T *= om;
+        }
+        __syncwarp();
+    }
+}
+
 __device__ __forceinline__ void jtj_item(const Ctx& c, int item, WarpSmem& sm) {
     Pix p;
     setup_item(c, item, p);
     const List L = compact_list(c, p);
-    float C[3], T, dC[3];
-    int ncons;
-    forward_pass<true, false>(c, p, L, sm.rec, sm.id, C, T, dC, ncons);
+    float Cf[3] = {0.f, 0.f, 0.f}, C[3], dC[3];
+    int ncons = 0;
+    if (p.active) {
+        ncons = c.cacheN[p.si];
+        if (!c.cache_bf16) {
+            Cf[0] = c.cacheC[3 * p.si];
+            Cf[1] = c.cacheC[3 * p.si + 1];
+            Cf[2] = c.cacheC[3 * p.si + 2];
+        }
+    }
+    const int lane_end = p.active ? L.b + ncons : L.b;
+    int warp_end = lane_end;
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) warp_end = max(warp_end, __shfl_xor_sync(kFull, warp_end, m));
+    if (c.cache_bf16) {
+        jvp_pass<true>(c, p, L, lane_end, warp_end, sm.rec, sm.id, C, dC);
+        Cf[0] = C[0], Cf[1] = C[1], Cf[2] = C[2];
+    } else {
+        jvp_pass<false>(c, p, L, lane_end, warp_end, sm.rec, sm.id, C, dC);
+    }
     const float ub[3] = {row_weight(c, p, 0) * dC[0], row_weight(c, p, 1) * dC[1], row_weight(c, p, 2) * dC[2]};
     __syncwarp();
-    backward_pass(c, p, L, sm, ub, C, ncons);
+    backward_pass(c, p, L, sm, ub, Cf, ncons);
 }
 
 __global__ void __launch_bounds__(kRasterBlock) k_jtj(Ctx c) {
@@ -657,7 +722,7 @@ __global__ void __launch_bounds__(kRasterBlock) k_diag(Ctx c) {
                 if (kRhs) {
                     float* cdst = cbase + (long long)sm.id[j] * kCotF;
                     red_add_v4(cdst, M[0], M[1], M[2], M[3]);
-                    red_add_v4(cdst + 4, M[4], __fdividef(M[5], r1.y), M[6], M[7]);
+                    red_add_v4(cdst + 4, M[4], M[5], M[6], M[7]);
                     atomicAdd(cdst + 8, M[8]);
                 }
             }
