@@ -79,7 +79,7 @@ struct Ctx {
     const float* targets;   // [n_cams][H][W][3] or null
     // per (slot, Gaussian) pair, index slot * G + g
     float4* gcache;         // per Gaussian, kGaussF4 planes of G float4 (view-independent 3D state)
-    float4* rec;            // per pair kPrimF4 float4: mu_x, mu_y, A, B | C, o, r, g | b, A', B', C' with
+    float4* rec;            // per pair kPrimF4 float4: mu_x, mu_y, A, B | C, o, r, g | b, B', A', C' with
                             // (A', B', C') = -log2(e) (A / 2, B, C / 2): e^power = 2^(dx (A' dx + B' dy) + C' dy^2)
     float4* tan;            // per pair kTanF4 float4: the tangents of the 9 features of pjac
     float4* pjac;           // per (view, Gaussian) pair: jac_f4(deg) planes of nv*G float4, the Jacobian

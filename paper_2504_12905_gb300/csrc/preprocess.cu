@@ -315,83 +315,107 @@ __device__ __forceinline__ void prim_features(const float X[3], const float* sh,
 }
 
 // ---------------------------------------------------------------------------
-// Forward-mode tangent of the 9 features (mu_x, mu_y, A, B, C, o, r, g, b)
-// along (dX, dls, dq, dth, dsh); kSh = false means a zero SH tangent.
+// Forward-mode tangent of the features (mu_x, mu_y, A, B, C) and of the colour
+// through the view direction, along a tangent with one non-zero parameter
+// group: kTanMean (dX), kTanScale (d log-scale) or kTanRot (dq), as the
+// Jacobian cache's columns need.  The terms the other groups would add are
+// exactly zero and are not formed (IEEE arithmetic cannot drop a product with
+// a zero factor by itself).  out[5] (opacity) is 0; the colour out[6..8] is
+// formed for the mean group only (the other columns do not move it).
 // ---------------------------------------------------------------------------
 struct GTan {
     float X[3], ls[3], q[4], th;
 };
 
-template <int DEG, bool kSh>
+constexpr int kTanMean = 1, kTanScale = 2, kTanRot = 4;
+
+template <int DEG, int kGroup>
 __device__ __forceinline__ void prim_tangent(const Prim& P, const CamDev& cam, const GTan& d, const float* sh,
-                                             const float* dsh, float out[9]) {
+                                             float out[9]) {
+    constexpr bool kX = kGroup == kTanMean, kS = kGroup == kTanScale, kQ = kGroup == kTanRot;
+    static_assert(kX || kS || kQ, "one parameter group");
     const float* W = cam.R;
-    float dt[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) dt[k] = W[3 * k] * d.X[0] + W[3 * k + 1] * d.X[1] + W[3 * k + 2] * d.X[2];
-    float ds[3];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) ds[j] = P.s[j] * d.ls[j];
-    // normalised quaternion: dqh = (dq - qh (qh . dq)) / |q|
-    const float* qh = P.qh;
-    const float proj = qh[0] * d.q[0] + qh[1] * d.q[1] + qh[2] * d.q[2] + qh[3] * d.q[3];
-    const float iqn = 1.f / P.qn;
-    const float dw = (d.q[0] - qh[0] * proj) * iqn, dx = (d.q[1] - qh[1] * proj) * iqn;
-    const float dy = (d.q[2] - qh[2] * proj) * iqn, dz = (d.q[3] - qh[3] * proj) * iqn;
-    const float w = qh[0], x = qh[1], y = qh[2], z = qh[3];
-    float dR[9];
-    dR[0] = -4.f * (y * dy + z * dz);
-    dR[1] = 2.f * (dx * y + x * dy - dw * z - w * dz);
-    dR[2] = 2.f * (dx * z + x * dz + dw * y + w * dy);
-    dR[3] = 2.f * (dx * y + x * dy + dw * z + w * dz);
-    dR[4] = -4.f * (x * dx + z * dz);
-    dR[5] = 2.f * (dy * z + y * dz - dw * x - w * dx);
-    dR[6] = 2.f * (dx * z + x * dz - dw * y - w * dy);
-    dR[7] = 2.f * (dy * z + y * dz + dw * x + w * dx);
-    dR[8] = -4.f * (x * dx + y * dy);
-    float dM[9];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) dM[3 * i + j] = dR[3 * i + j] * P.s[j] + P.R[3 * i + j] * ds[j];
-    // dSigma = dM M^T + M dM^T
-    float dS[9];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            float v = 0.f;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) v += dM[3 * i + k] * P.M[3 * j + k] + P.M[3 * i + k] * dM[3 * j + k];
-            dS[3 * i + j] = v;
-        }
-    const float it2 = 1.f / P.t[2];
-    const float dux = (dt[0] - P.ux * dt[2]) * it2;
-    const float duy = (dt[1] - P.uy * dt[2]) * it2;
-    const float dcux = P.clx ? 0.f : dux, dcuy = P.cly ? 0.f : duy;
-    const float dj00 = -P.j00 * dt[2] * it2;
-    const float dj02 = -cam.fx * dcux * it2 - P.j02 * dt[2] * it2;
-    const float dj11 = -P.j11 * dt[2] * it2;
-    const float dj12 = -cam.fy * dcuy * it2 - P.j12 * dt[2] * it2;
-    float dT[6];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        dT[k] = dj00 * W[k] + dj02 * W[6 + k];
-        dT[3 + k] = dj11 * W[3 + k] + dj12 * W[6 + k];
-    }
-    // d(T Sigma T^T) = dT V^T + V dT^T + T dSigma T^T  with V = T Sigma
-    float TdS[6];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int k = 0; k < 3; ++k)
-            TdS[3 * i + k] = P.T[3 * i] * dS[k] + P.T[3 * i + 1] * dS[3 + k] + P.T[3 * i + 2] * dS[6 + k];
     const float* V = P.V;
     const float* T = P.T;
-    const float da = 2.f * (dT[0] * V[0] + dT[1] * V[1] + dT[2] * V[2]) + TdS[0] * T[0] + TdS[1] * T[1] + TdS[2] * T[2];
-    const float db = dT[0] * V[3] + dT[1] * V[4] + dT[2] * V[5] + V[0] * dT[3] + V[1] * dT[4] + V[2] * dT[5] +
-                     TdS[0] * T[3] + TdS[1] * T[4] + TdS[2] * T[5];
-    const float dc = 2.f * (dT[3] * V[3] + dT[4] * V[4] + dT[5] * V[5]) + TdS[3] * T[3] + TdS[4] * T[4] + TdS[5] * T[5];
+    float da, db, dc, dux = 0.f, duy = 0.f;
+    if constexpr (kX) {
+        float dt[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) dt[k] = W[3 * k] * d.X[0] + W[3 * k + 1] * d.X[1] + W[3 * k + 2] * d.X[2];
+        const float it2 = 1.f / P.t[2];
+        dux = (dt[0] - P.ux * dt[2]) * it2;
+        duy = (dt[1] - P.uy * dt[2]) * it2;
+        const float dcux = P.clx ? 0.f : dux, dcuy = P.cly ? 0.f : duy;
+        const float dj00 = -P.j00 * dt[2] * it2;
+        const float dj02 = -cam.fx * dcux * it2 - P.j02 * dt[2] * it2;
+        const float dj11 = -P.j11 * dt[2] * it2;
+        const float dj12 = -cam.fy * dcuy * it2 - P.j12 * dt[2] * it2;
+        float dT[6];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            dT[k] = dj00 * W[k] + dj02 * W[6 + k];
+            dT[3 + k] = dj11 * W[3 + k] + dj12 * W[6 + k];
+        }
+        // d(T Sigma T^T) = dT V^T + V dT^T  with V = T Sigma
+        da = 2.f * (dT[0] * V[0] + dT[1] * V[1] + dT[2] * V[2]);
+        db = dT[0] * V[3] + dT[1] * V[4] + dT[2] * V[5] + V[0] * dT[3] + V[1] * dT[4] + V[2] * dT[5];
+        dc = 2.f * (dT[3] * V[3] + dT[4] * V[4] + dT[5] * V[5]);
+    } else {
+        // dM = d(R S): R dS with dS = S d log-scale, or dR S with dR from the
+        // normalised quaternion's tangent dqh = (dq - qh (qh . dq)) / |q|
+        float dM[9];
+        if constexpr (kS) {
+            float ds[3];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) ds[j] = P.s[j] * d.ls[j];
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) dM[3 * i + j] = P.R[3 * i + j] * ds[j];
+        } else {
+            const float* qh = P.qh;
+            const float proj = qh[0] * d.q[0] + qh[1] * d.q[1] + qh[2] * d.q[2] + qh[3] * d.q[3];
+            const float iqn = 1.f / P.qn;
+            const float dw = (d.q[0] - qh[0] * proj) * iqn, dx = (d.q[1] - qh[1] * proj) * iqn;
+            const float dy = (d.q[2] - qh[2] * proj) * iqn, dz = (d.q[3] - qh[3] * proj) * iqn;
+            const float w = qh[0], x = qh[1], y = qh[2], z = qh[3];
+            float dR[9];
+            dR[0] = -4.f * (y * dy + z * dz);
+            dR[1] = 2.f * (dx * y + x * dy - dw * z - w * dz);
+            dR[2] = 2.f * (dx * z + x * dz + dw * y + w * dy);
+            dR[3] = 2.f * (dx * y + x * dy + dw * z + w * dz);
+            dR[4] = -4.f * (x * dx + z * dz);
+            dR[5] = 2.f * (dy * z + y * dz - dw * x - w * dx);
+            dR[6] = 2.f * (dx * z + x * dz - dw * y - w * dy);
+            dR[7] = 2.f * (dy * z + y * dz + dw * x + w * dx);
+            dR[8] = -4.f * (x * dx + y * dy);
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) dM[3 * i + j] = dR[3 * i + j] * P.s[j];
+        }
+        // dSigma = dM M^T + M dM^T
+        float dS[9];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                float v = 0.f;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) v += dM[3 * i + k] * P.M[3 * j + k] + P.M[3 * i + k] * dM[3 * j + k];
+                dS[3 * i + j] = v;
+            }
+        // d(T Sigma T^T) = T dSigma T^T
+        float TdS[6];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                TdS[3 * i + k] = T[3 * i] * dS[k] + T[3 * i + 1] * dS[3 + k] + T[3 * i + 2] * dS[6 + k];
+        da = TdS[0] * T[0] + TdS[1] * T[1] + TdS[2] * T[2];
+        db = TdS[0] * T[3] + TdS[1] * T[4] + TdS[2] * T[5];
+        dc = TdS[3] * T[3] + TdS[4] * T[4] + TdS[5] * T[5];
+    }
     const float ddet = da * P.c + P.a * dc - 2.f * P.b * db;
     const float idet = 1.f / P.det;
     out[0] = cam.fx * dux;
@@ -399,13 +423,12 @@ __device__ __forceinline__ void prim_tangent(const Prim& P, const CamDev& cam, c
     out[2] = (dc - P.A * ddet) * idet;
     out[3] = (-db - P.B * ddet) * idet;
     out[4] = (da - P.C * ddet) * idet;
-    out[5] = P.o * (1.f - P.o) * d.th;
-    // colour: SH coefficients and the view direction (through the mean);
-    // dc_ch = sum_k dsh_k,ch Y_k + sh_k,ch (grad Y_k . ddir), coefficients
-    // streamed from memory
+    out[5] = 0.f;
+    // colour through the view direction (mean group only):
+    // dc_ch = sum_k sh_k,ch (grad Y_k . ddir), coefficients streamed from memory
     constexpr int K = Sh<DEG>::K;
     float v3[3] = {0.f, 0.f, 0.f};
-    if (DEG > 0) {
+    if constexpr (DEG > 0 && kX) {
         const float idn = 1.f / P.dn;
         const float pd = P.dir[0] * d.X[0] + P.dir[1] * d.X[1] + P.dir[2] * d.X[2];
         float ddir[3];
@@ -417,14 +440,6 @@ __device__ __forceinline__ void prim_tangent(const Prim& P, const CamDev& cam, c
         for (int k = 1; k < K; ++k)
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) v3[ch] += sh[3 * k + ch] * gY[k];
-    }
-    if (kSh) {
-        float Y[K];
-        sh_eval<DEG>(P.dir[0], P.dir[1], P.dir[2], Y);
-#pragma unroll
-        for (int k = 0; k < K; ++k)
-#pragma unroll
-            for (int ch = 0; ch < 3; ++ch) v3[ch] += dsh[3 * k + ch] * Y[k];
     }
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) out[6 + ch] = P.clamped[ch] ? 0.f : v3[ch];
@@ -478,7 +493,12 @@ __device__ __forceinline__ void pair_jacobian(const Prim& P, const CamDev& cam, 
         for (int k = 0; k < 4; ++k) d.q[k] = col == 6 + k ? 1.f : 0.f;
         d.th = 0.f;
         float out[9];
-        prim_tangent<DEG, false>(P, cam, d, sh, nullptr, out);
+        if (col < 3)
+            prim_tangent<DEG, kTanMean>(P, cam, d, sh, out);
+        else if (col < 6)
+            prim_tangent<DEG, kTanScale>(P, cam, d, sh, out);
+        else
+            prim_tangent<DEG, kTanRot>(P, cam, d, sh, out);
         if (col < 3) {
             J[L::kMu + col] = -(P.A * out[0] + P.B * out[1]);
             J[L::kMu + 3 + col] = -(P.B * out[0] + P.C * out[1]);
@@ -560,7 +580,7 @@ __global__ void k_prep_fwd(Ctx c) {
     r[1] = make_float4(P.C, P.o, P.col[0], P.col[1]);
     // the conic scaled for the rasterizer's 2^x (the primal record's spare slots)
     const float L2E = 1.4426950408889634f;
-    r[2] = make_float4(P.col[2], -0.5f * L2E * P.A, -L2E * P.B, -0.5f * L2E * P.C);
+    r[2] = make_float4(P.col[2], -L2E * P.B, -0.5f * L2E * P.A, -0.5f * L2E * P.C);
     c.rect[i] = rect;
     c.ell[2 * i] = ell[0];
     c.ell[2 * i + 1] = ell[1];

@@ -42,11 +42,19 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
+// e^power at offset d = mu - pixel centre from the third float4 of a pair's
+// record, (b, B', A', C'): (A' dx, C' dy) is one paired multiply.
+__device__ __forceinline__ float gauss_ex2(float4 r2, float2 d) {
+    const float2 ac = __fmul2_rn(make_float2(r2.z, r2.w), d);
+    return ex2_approx(fmaf(ac.y, d.y, d.x * fmaf(r2.y, d.y, ac.x)));
+}
+
 struct Pix {
     int vt, slot, tile, chunk;
     long long si;
     bool active;
     float pcx, pcy;
+    float2 npc;  // -(pcx, pcy)
     int px, py;
     float w;
 };
@@ -68,6 +76,7 @@ __device__ __forceinline__ void setup_item(const Ctx& c, int item, Pix& p) {
     p.py = ty * c.tile_h + o / vw;
     p.pcx = p.px + 0.5f;
     p.pcy = p.py + 0.5f;
+    p.npc = make_float2(-p.pcx, -p.pcy);
     p.w = c.wsample ? (p.active ? c.wsample[p.si] : 0.f) : c.wtile[p.vt];
 }
 
@@ -120,7 +129,7 @@ __device__ __forceinline__ int stage_batch(const Ctx& c, int slot, const unsigne
         const long long pr = (long long)slot * c.G + id;
 #pragma unroll
         for (int q = 0; q < NF4; ++q) s_rec[lane][q] = q < kPrimF4 ? c.rec[pr * kPrimF4 + q] : c.tan[pr * kTanF4 + q - kPrimF4];
-        s_id[lane] = id;
+        if (s_id) s_id[lane] = id;
     }
     __syncwarp();
     return min(32, end - b);
@@ -148,8 +157,9 @@ __device__ __forceinline__ void forward_pass(const Ctx& c, const Pix& p, List L,
         const int n = stage_batch<kTan ? 6 : 3>(c, p.slot, L.ids, b, L.e, s_rec, s_id);
         for (int j = 0; j < n; ++j) {
             const float4 r0 = s_rec[j][0], r1 = s_rec[j][1], r2 = s_rec[j][2];
-            const float dx = r0.x - p.pcx, dy = r0.y - p.pcy;
-            const float gval = ex2_approx(fmaf(r2.w * dy, dy, dx * fmaf(r2.z, dy, r2.y * dx)));
+            const float2 d = __fadd2_rn(make_float2(r0.x, r0.y), p.npc);
+            const float dx = d.x, dy = d.y;
+            const float gval = gauss_ex2(r2, d);
             const float raw = r1.y * gval;
             float alpha = fminf(kAlphaMax, raw);
             bool need = !done && alpha >= kAlphaMin;
@@ -237,17 +247,21 @@ __device__ __forceinline__ void forward_pass(const Ctx& c, const Pix& p, List L,
 constexpr int kBwdE = 16;  // entries per phase; lanes e and e + 16 share entry e
 
 struct BwdSmem {
-    float2 pw[kBwdE][33];  // (pbar, wgt) per (entry, sample); row stride 33 keeps phase B's column reads conflict-free
-    float4 pix[32];        // per sample: pixel centre x, y, ub_0, ub_1
-    float ub2[32];
+    // pbar and wgt per (entry, sample), planar; row stride 34 (even, for the
+    // sample-pair loads, and 2 mod 32) keeps phase B's reads conflict-free
+    float pb[kBwdE][34], wt[kBwdE][34];
+    float npx[32], npy[32];  // per sample: minus the pixel centre
+    float u0[32], u1[32], u2[32];
 };
 
-// One staged batch per warp, plus the back-scatter's exchange area.
+// One staged batch per warp, plus the back-scatter's exchange area.  The
+// batch's Gaussian ids are read back from the list where they are needed.
 struct WarpSmem {
     float4 rec[32][kRecF4];
-    unsigned id[32];
     BwdSmem bw;
 };
+
+__device__ __forceinline__ float2 ld2(const float* a) { return *reinterpret_cast<const float2*>(a); }
 
 __device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float c, float d) {
     asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
@@ -265,12 +279,15 @@ __device__ __forceinline__ void backward_pass(const Ctx& c, const Pix& p, List L
     for (int m = 16; m >= 1; m >>= 1) warp_end = max(warp_end, __shfl_xor_sync(kFull, warp_end, m));
     // the live samples are lanes [0, nact)
     const int nact = __popc(__ballot_sync(kFull, p.active));
-    sm.bw.pix[lane] = make_float4(p.pcx, p.pcy, ub[0], ub[1]);
-    sm.bw.ub2[lane] = ub[2];
+    sm.bw.npx[lane] = -p.pcx;
+    sm.bw.npy[lane] = -p.pcy;
+    sm.bw.u0[lane] = ub[0];
+    sm.bw.u1[lane] = ub[1];
+    sm.bw.u2[lane] = ub[2];
     float* cot_base = c.cot + (long long)p.slot * c.G * kCotF;
     const int e = lane & (kBwdE - 1), hh = lane >> 4;
     for (int b = L.b; b < warp_end; b += 32) {
-        const int n = stage_batch<3>(c, p.slot, L.ids, b, warp_end, sm.rec, sm.id);
+        const int n = stage_batch<3>(c, p.slot, L.ids, b, warp_end, sm.rec, nullptr);
         for (int h0 = 0; h0 < n; h0 += kBwdE) {
             const int m = min(kBwdE, n - h0);
             // phase A
@@ -278,8 +295,7 @@ __device__ __forceinline__ void backward_pass(const Ctx& c, const Pix& p, List L
                 const int j = h0 + jj;
                 const float4 r0 = sm.rec[j][0], r1 = sm.rec[j][1], r2 = sm.rec[j][2];
                 const float col2 = r2.x;
-                const float dx = r0.x - p.pcx, dy = r0.y - p.pcy;
-                const float gval = ex2_approx(fmaf(r2.w * dy, dy, dx * fmaf(r2.z, dy, r2.y * dx)));
+                const float gval = gauss_ex2(r2, __fadd2_rn(make_float2(r0.x, r0.y), p.npc));
                 const float raw = r1.y * gval;
                 float alpha = fminf(kAlphaMax, raw);
                 // branch-free: an entry the lane does not composite (past its
@@ -293,41 +309,49 @@ __device__ __forceinline__ void backward_pass(const Ctx& c, const Pix& p, List L
                 const float abar = T * ucol - __fdividef(S_tot - s, 1.f - alpha);  // 1 - alpha >= 0.01
                 const float pb = (on && raw <= kAlphaMax) ? abar * raw : 0.f;
                 T *= 1.f - alpha;
-                sm.bw.pw[jj][lane] = make_float2(pb, wt);
+                sm.bw.pb[jj][lane] = pb;
+                sm.bw.wt[jj][lane] = wt;
             }
             __syncwarp();
-            // phase B
-            float M[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            float M5 = 0.f;
+            // phase B, in paired FP32 operations (f32x2: two lanes of
+            // arithmetic per issued instruction, each rounded as alone) over
+            // sample pairs (i, i + 1): samples past the live ones hold
+            // pbar = wgt = 0 (phase A writes every lane), so the pairs run to
+            // an even count; the two lanes of an entry take alternate pairs
+            float2 M[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) M[k] = make_float2(0.f, 0.f);
             const int j = h0 + e;
             if (e < m) {
-                const float mx = sm.rec[j][0].x, my = sm.rec[j][0].y;
-                for (int i = hh; i < nact; i += 2) {
-                    const float2 q = sm.bw.pw[e][i];
-                    const float4 px = sm.bw.pix[i];
-                    const float u2 = sm.bw.ub2[i];
-                    const float dx = mx - px.x, dy = my - px.y;
-                    const float pdx = q.x * dx, pdy = q.x * dy;
-                    M[0] += pdx;
-                    M[1] += pdy;
-                    M[2] = fmaf(pdx, dx, M[2]);
-                    M[3] = fmaf(pdx, dy, M[3]);
-                    M[4] = fmaf(pdy, dy, M[4]);
-                    M5 += q.x;
-                    M[6] = fmaf(px.z, q.y, M[6]);
-                    M[7] = fmaf(px.w, q.y, M[7]);
-                    M[8] = fmaf(u2, q.y, M[8]);
+                const float2 mx = make_float2(sm.rec[j][0].x, sm.rec[j][0].x);
+                const float2 my = make_float2(sm.rec[j][0].y, sm.rec[j][0].y);
+                for (int i = 2 * hh; i < nact; i += 4) {
+                    const float2 q = ld2(&sm.bw.pb[e][i]), w = ld2(&sm.bw.wt[e][i]);
+                    const float2 dx = __fadd2_rn(mx, ld2(&sm.bw.npx[i]));
+                    const float2 dy = __fadd2_rn(my, ld2(&sm.bw.npy[i]));
+                    const float2 pdx = __fmul2_rn(q, dx), pdy = __fmul2_rn(q, dy);
+                    M[0] = __fadd2_rn(M[0], pdx);
+                    M[1] = __fadd2_rn(M[1], pdy);
+                    M[2] = __ffma2_rn(pdx, dx, M[2]);
+                    M[3] = __ffma2_rn(pdx, dy, M[3]);
+                    M[4] = __ffma2_rn(pdy, dy, M[4]);
+                    M[5] = __fadd2_rn(M[5], q);
+                    M[6] = __ffma2_rn(ld2(&sm.bw.u0[i]), w, M[6]);
+                    M[7] = __ffma2_rn(ld2(&sm.bw.u1[i]), w, M[7]);
+                    M[8] = __ffma2_rn(ld2(&sm.bw.u2[i]), w, M[8]);
                 }
             }
+            float Ms[9];
 #pragma unroll
-            for (int k = 0; k < 9; ++k)
-                if (k != 5) M[k] += __shfl_xor_sync(kFull, M[k], 16);
-            M5 += __shfl_xor_sync(kFull, M5, 16);
+            for (int k = 0; k < 9; ++k) {
+                Ms[k] = M[k].x + M[k].y;
+                Ms[k] += __shfl_xor_sync(kFull, Ms[k], 16);
+            }
             if (hh == 0 && e < m) {
-                float* dst = cot_base + (long long)sm.id[j] * kCotF;
-                red_add_v4(dst, M[0], M[1], M[2], M[3]);
-                red_add_v4(dst + 4, M[4], M5, M[6], M[7]);
-                atomicAdd(dst + 8, M[8]);
+                float* dst = cot_base + (long long)L.ids[b + j] * kCotF;
+                red_add_v4(dst, Ms[0], Ms[1], Ms[2], Ms[3]);
+                red_add_v4(dst + 4, Ms[4], Ms[5], Ms[6], Ms[7]);
+                atomicAdd(dst + 8, Ms[8]);
             }
             __syncwarp();
         }
@@ -454,36 +478,64 @@ __global__ void __launch_bounds__(kRasterBlock) k_vjp(Ctx c, const float* u) {
 // mode, whose cached colour is too coarse for the back-scatter's suffix
 // Cf - C_<=n.  alpha >= 1/255 is tested on raw: the clamp at 0.99 is above
 // the threshold, so the decision is the same.
+//
+// Its own staged layout, five float4 per entry, puts each channel's colour
+// tangent beside its colour, so that dC_ch = sum dc_ch wgt + c_ch dw is one
+// paired FMA per channel into (sum dc_ch wgt, sum c_ch dw):
+//   (mu_x, mu_y, A', C') (dr, r, dg, g) (db, b, B', o) (e_1..e_4) (e_5, d log o, -, -)
+constexpr int kJvpF4 = 5;
+static_assert(kJvpF4 <= kRecF4, "staged row too narrow");
+
+__device__ __forceinline__ void stage_jvp(const Ctx& c, int slot, const unsigned* ids, int b, int end,
+                                          float4 (*s)[kRecF4]) {
+    const int lane = threadIdx.x & 31;
+    const int k = b + lane;
+    if (k < end) {
+        const long long pr = (long long)slot * c.G + ids[k];
+        const float4 a0 = c.rec[pr * kPrimF4], a1 = c.rec[pr * kPrimF4 + 1], a2 = c.rec[pr * kPrimF4 + 2];
+        const float4 t0 = c.tan[pr * kTanF4], t1 = c.tan[pr * kTanF4 + 1];
+        const float tb = reinterpret_cast<const float*>(c.tan + pr * kTanF4 + 2)[0];
+        s[lane][0] = make_float4(a0.x, a0.y, a2.z, a2.w);
+        s[lane][1] = make_float4(t1.z, a1.z, t1.w, a1.w);
+        s[lane][2] = make_float4(tb, a2.x, a2.y, a1.y);
+        s[lane][3] = t0;
+        s[lane][4] = make_float4(t1.x, t1.y, 0.f, 0.f);
+    }
+    __syncwarp();
+}
+
 template <bool kColour>
 __device__ __forceinline__ void jvp_pass(const Ctx& c, const Pix& p, List L, int lane_end, int warp_end,
-                                         float4 (*s_rec)[kRecF4], unsigned* s_id, float C[3], float dC[3]) {
+                                         float4 (*s_rec)[kRecF4], float C[3], float dC[3]) {
     float T = 1.f, dT = 0.f;
     C[0] = C[1] = C[2] = 0.f;
-    dC[0] = dC[1] = dC[2] = 0.f;
+    float2 dCp[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
     for (int b = L.b; b < warp_end; b += 32) {
-        const int n = stage_batch<6>(c, p.slot, L.ids, b, warp_end, s_rec, s_id);
+        stage_jvp(c, p.slot, L.ids, b, warp_end, s_rec);
+        const int n = min(32, warp_end - b);
         const int rem = lane_end - b;
         for (int j = 0; j < n; ++j) {
-            const float4 r0 = s_rec[j][0], r1 = s_rec[j][1], r2 = s_rec[j][2];
-            const float dx = r0.x - p.pcx, dy = r0.y - p.pcy;
-            const float raw = r1.y * ex2_approx(fmaf(r2.w * dy, dy, dx * fmaf(r2.z, dy, r2.y * dx)));
+            const float4 s0 = s_rec[j][0], s1 = s_rec[j][1], s2 = s_rec[j][2];
+            const float2 d = __fadd2_rn(make_float2(s0.x, s0.y), p.npc);
+            const float2 ac = __fmul2_rn(make_float2(s0.z, s0.w), d);
+            const float raw = s2.w * ex2_approx(fmaf(ac.y, d.y, d.x * fmaf(s2.z, d.y, ac.x)));
             // alpha = 0 where the lane does not composite the entry: T, C and
             // the tangents stay as they are
             const bool on = j < rem && raw >= kAlphaMin;
             const float alpha = on ? fminf(kAlphaMax, raw) : 0.f;
-            const float4 t0 = s_rec[j][3], t1 = s_rec[j][4];
-            const float dcol2 = s_rec[j][5].x;
+            const float4 t0 = s_rec[j][3];
+            const float2 t1 = make_float2(s_rec[j][4].x, s_rec[j][4].y);
+            const float dx = d.x, dy = d.y;
             const float dlin = fmaf(dx, fmaf(t0.z, dx, fmaf(t0.w, dy, t0.x)), fmaf(dy, fmaf(t1.x, dy, t0.y), t1.y));
             const float dalpha = (on && raw <= kAlphaMax) ? raw * dlin : 0.f;
-            const float wgt = alpha * T;
-            const float dw = fmaf(dalpha, T, alpha * dT);
-            dC[0] += t1.z * wgt + r1.z * dw;
-            dC[1] += t1.w * wgt + r1.w * dw;
-            dC[2] += dcol2 * wgt + r2.x * dw;
+            const float2 wd = make_float2(alpha * T, fmaf(dalpha, T, alpha * dT));  // (wgt, dw)
+            dCp[0] = __ffma2_rn(make_float2(s1.x, s1.y), wd, dCp[0]);
+            dCp[1] = __ffma2_rn(make_float2(s1.z, s1.w), wd, dCp[1]);
+            dCp[2] = __ffma2_rn(make_float2(s2.x, s2.y), wd, dCp[2]);
             if (kColour) {
-                C[0] += r1.z * wgt;
-                C[1] += r1.w * wgt;
-                C[2] += r2.x * wgt;
+                C[0] = fmaf(s1.y, wd.x, C[0]);
+                C[1] = fmaf(s1.w, wd.x, C[1]);
+                C[2] = fmaf(s2.y, wd.x, C[2]);
             }
             const float om = 1.f - alpha;
             dT = dT * om - T * dalpha;
@@ -491,6 +543,8 @@ __device__ __forceinline__ void jvp_pass(const Ctx& c, const Pix& p, List L, int
         }
         __syncwarp();
     }
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) dC[ch] = dCp[ch].x + dCp[ch].y;
 }
 
 __device__ __forceinline__ void jtj_item(const Ctx& c, int item, WarpSmem& sm) {
@@ -512,10 +566,10 @@ __device__ __forceinline__ void jtj_item(const Ctx& c, int item, WarpSmem& sm) {
 #pragma unroll
     for (int m = 16; m >= 1; m >>= 1) warp_end = max(warp_end, __shfl_xor_sync(kFull, warp_end, m));
     if (c.cache_bf16) {
-        jvp_pass<true>(c, p, L, lane_end, warp_end, sm.rec, sm.id, C, dC);
+        jvp_pass<true>(c, p, L, lane_end, warp_end, sm.rec, C, dC);
         Cf[0] = C[0], Cf[1] = C[1], Cf[2] = C[2];
     } else {
-        jvp_pass<false>(c, p, L, lane_end, warp_end, sm.rec, sm.id, C, dC);
+        jvp_pass<false>(c, p, L, lane_end, warp_end, sm.rec, C, dC);
     }
     const float ub[3] = {row_weight(c, p, 0) * dC[0], row_weight(c, p, 1) * dC[1], row_weight(c, p, 2) * dC[2]};
     __syncwarp();
@@ -623,8 +677,7 @@ __global__ void __launch_bounds__(kRasterBlock) k_diag(Ctx c) {
                 const int j = h0 + jj;
                 const float4 r0 = sm.rec[j][0], r1 = sm.rec[j][1], r2 = sm.rec[j][2];
                 const float col[3] = {r1.z, r1.w, r2.x};
-                const float dx = r0.x - p.pcx, dy = r0.y - p.pcy;
-                const float gval = ex2_approx(fmaf(r2.w * dy, dy, dx * fmaf(r2.z, dy, r2.y * dx)));
+                const float gval = gauss_ex2(r2, __fadd2_rn(make_float2(r0.x, r0.y), p.npc));
                 const float raw = r1.y * gval;
                 float alpha = fminf(kAlphaMax, raw);
                 // branch-free as in backward_pass: alpha = 0 where the lane
@@ -755,6 +808,7 @@ __global__ void __launch_bounds__(256) k_full(Ctx c, float* images) {
     p.py = ty * c.tile_h + (p.active ? o / vw : 0);
     p.pcx = p.px + 0.5f;
     p.pcy = p.py + 0.5f;
+    p.npc = make_float2(-p.pcx, -p.pcy);
     p.w = 1.f;
     float C[3], T, dC[3];
     int ncons;
@@ -926,6 +980,7 @@ __global__ void __launch_bounds__(256) k_importance(Ctx c, long long lm_step, un
         p.py = ty * c.tile_h + (p.active ? o / vw : 0);
         p.pcx = p.px + 0.5f;
         p.pcy = p.py + 0.5f;
+        p.npc = make_float2(-p.pcx, -p.pcy);
         p.w = 1.f;
         float C[3], T, dC[3];
         int ncons, ncomp = 0;
@@ -988,10 +1043,16 @@ void launch_importance(const Ctx& c, long long lm_step, unsigned long long seed,
 
 static unsigned raster_grid(const Ctx& c) { return (unsigned)((c.nwork + kRasterWarps - 1) / kRasterWarps); }
 
+// Longest-first order of the work items (load balance only): 16-bit keys,
+// ascending key = descending cost; items of 65,535 or more list entries tie
+// and keep their index order.
+constexpr int kOrderBits = 16;
+
 __global__ void k_order_keys(const int* cost, int n, unsigned long long* keys, unsigned int* vals) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
-    keys[k] = 0xFFFFFFFFull - (unsigned long long)(unsigned int)cost[k];  // ascending key = descending cost
+    const unsigned cmax = (1u << kOrderBits) - 1u;
+    keys[k] = cmax - min((unsigned)max(cost[k], 0), cmax);
     vals[k] = (unsigned int)k;
 }
 
@@ -1005,7 +1066,7 @@ void launch_order_work(const Ctx& c, unsigned long long* keys, unsigned int* val
     if (c.nwork <= 0) return;
     const unsigned grid = (unsigned)((c.nwork + 255) / 256);
     LMRS_LAUNCH(k_order_keys, grid, 256, 0, st, c.item_cost, c.nwork, keys, vals);
-    radix_sort(keys, vals, keys_alt, vals_alt, c.nwork, 32, tmp, tmp_bytes, st);
+    radix_sort(keys, vals, keys_alt, vals_alt, c.nwork, kOrderBits, tmp, tmp_bytes, st);
     LMRS_LAUNCH(k_gather_work, grid, 256, 0, st, c.work, vals, c.nwork, sorted);
 }
 
