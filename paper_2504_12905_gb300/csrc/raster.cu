@@ -118,13 +118,13 @@ __device__ __forceinline__ List tile_list(const Ctx& c, const Pix& p) {
     return L;
 }
 
-template <int NF4, int W>
+template <int NF4, int W, int R = 32>
 __device__ __forceinline__ int stage_batch(const Ctx& c, int slot, const unsigned* ids, int b, int end,
                                            float4 (*s_rec)[W], unsigned* s_id) {
     static_assert(NF4 <= W, "staged row too narrow");
     const int lane = threadIdx.x & 31;
     const int k = b + lane;
-    if (k < end) {
+    if (lane < R && k < end) {
         const unsigned id = ids[k];
         const long long pr = (long long)slot * c.G + id;
 #pragma unroll
@@ -132,7 +132,7 @@ __device__ __forceinline__ int stage_batch(const Ctx& c, int slot, const unsigne
         if (s_id) s_id[lane] = id;
     }
     __syncwarp();
-    return min(32, end - b);
+    return min(R, end - b);
 }
 
 // Front-to-back pass.  With kTan also the tangent of the colour (Alg. 3).
@@ -256,8 +256,10 @@ struct BwdSmem {
 
 // One staged batch per warp, plus the back-scatter's exchange area.  The
 // batch's Gaussian ids are read back from the list where they are needed.
+constexpr int kJtjRows = 16;  // list entries staged at a time by k_jtj and k_vjp
+constexpr int kJtjF4 = 5;     // float4 per staged row (the JVP pass's layout)
 struct WarpSmem {
-    float4 rec[32][kRecF4];
+    float4 rec[kJtjRows][kJtjF4];
     BwdSmem bw;
 };
 
@@ -286,8 +288,8 @@ __device__ __forceinline__ void backward_pass(const Ctx& c, const Pix& p, List L
     sm.bw.u2[lane] = ub[2];
     float* cot_base = c.cot + (long long)p.slot * c.G * kCotF;
     const int e = lane & (kBwdE - 1), hh = lane >> 4;
-    for (int b = L.b; b < warp_end; b += 32) {
-        const int n = stage_batch<3>(c, p.slot, L.ids, b, warp_end, sm.rec, nullptr);
+    for (int b = L.b; b < warp_end; b += kJtjRows) {
+        const int n = stage_batch<3, kJtjF4, kJtjRows>(c, p.slot, L.ids, b, warp_end, sm.rec, nullptr);
         for (int h0 = 0; h0 < n; h0 += kBwdE) {
             const int m = min(kBwdE, n - h0);
             // phase A
@@ -483,14 +485,12 @@ __global__ void __launch_bounds__(kRasterBlock) k_vjp(Ctx c, const float* u) {
 // tangent beside its colour, so that dC_ch = sum dc_ch wgt + c_ch dw is one
 // paired FMA per channel into (sum dc_ch wgt, sum c_ch dw):
 //   (mu_x, mu_y, A', C') (dr, r, dg, g) (db, b, B', o) (e_1..e_4) (e_5, d log o, -, -)
-constexpr int kJvpF4 = 5;
-static_assert(kJvpF4 <= kRecF4, "staged row too narrow");
 
 __device__ __forceinline__ void stage_jvp(const Ctx& c, int slot, const unsigned* ids, int b, int end,
-                                          float4 (*s)[kRecF4]) {
+                                          float4 (*s)[kJtjF4]) {
     const int lane = threadIdx.x & 31;
     const int k = b + lane;
-    if (k < end) {
+    if (lane < kJtjRows && k < end) {
         const long long pr = (long long)slot * c.G + ids[k];
         const float4 a0 = c.rec[pr * kPrimF4], a1 = c.rec[pr * kPrimF4 + 1], a2 = c.rec[pr * kPrimF4 + 2];
         const float4 t0 = c.tan[pr * kTanF4], t1 = c.tan[pr * kTanF4 + 1];
@@ -506,13 +506,13 @@ __device__ __forceinline__ void stage_jvp(const Ctx& c, int slot, const unsigned
 
 template <bool kColour>
 __device__ __forceinline__ void jvp_pass(const Ctx& c, const Pix& p, List L, int lane_end, int warp_end,
-                                         float4 (*s_rec)[kRecF4], float C[3], float dC[3]) {
+                                         float4 (*s_rec)[kJtjF4], float C[3], float dC[3]) {
     float T = 1.f, dT = 0.f;
     C[0] = C[1] = C[2] = 0.f;
     float2 dCp[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-    for (int b = L.b; b < warp_end; b += 32) {
+    for (int b = L.b; b < warp_end; b += kJtjRows) {
         stage_jvp(c, p.slot, L.ids, b, warp_end, s_rec);
-        const int n = min(32, warp_end - b);
+        const int n = min(kJtjRows, warp_end - b);
         const int rem = lane_end - b;
         for (int j = 0; j < n; ++j) {
             const float4 s0 = s_rec[j][0], s1 = s_rec[j][1], s2 = s_rec[j][2];
@@ -576,7 +576,7 @@ __device__ __forceinline__ void jtj_item(const Ctx& c, int item, WarpSmem& sm) {
     backward_pass(c, p, L, sm, ub, Cf, ncons);
 }
 
-__global__ void __launch_bounds__(kRasterBlock) k_jtj(Ctx c) {
+__global__ void __launch_bounds__(kRasterBlock, 8) k_jtj(Ctx c) {
     __shared__ WarpSmem s_warp[kRasterWarps];
     const int wid = threadIdx.x >> 5;
     const int item = blockIdx.x * kRasterWarps + wid;
