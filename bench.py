@@ -370,7 +370,8 @@ def run_ours(args, rank, world, local_rank):
                     damping_mode=1, cg_iters=wl["cg_iters"], seed=0x5EED + rank, cache_bf16=bf16)
     lmrs.lmrs_preprocess(op.h, views[n_steps - 1], n_steps - 1)
     lmrs.lmrs_render(op.h)
-    lmrs.lmrs_jtj_diag(op.h)
+    d_op = torch.empty(scene.n_params, dtype=torch.float32, device="cuda")
+    lmrs.lmrs_jtj_diag(op.h, d_op)
     v = torch.randn(scene.n_params, device="cuda")
     out = torch.empty_like(v)
     for _ in range(3):
@@ -386,21 +387,35 @@ def run_ours(args, rank, world, local_rank):
     matvec_ms = m0.elapsed_time(m1) / reps
     bf16_err = None
     if bf16:
-        # the same operator with FP32 caches: the error the BF16 caches add
+        # The same quantities with FP32 caches (which match the FP64 oracle to
+        # about 1e-6 on the 200k-Gaussian workload): the error the BF16 caches
+        # add.  The cached final colour is read by the right-hand side's
+        # back-scatter and by the diagonal; the operator recomputes the colour
+        # in BF16 mode and differs only through D.
         op32 = lmrs.Scene(cur, sc.cams, G, deg, targets=targets, sample_frac=wl["sample_frac"], lambda_=wl["lam"],
                           damping_mode=1, cg_iters=wl["cg_iters"], seed=0x5EED + rank, cache_bf16=0)
         lmrs.lmrs_preprocess(op32.h, views[n_steps - 1], n_steps - 1)
         lmrs.lmrs_render(op32.h)
-        lmrs.lmrs_jtj_diag(op32.h)
+        d32 = torch.empty_like(d_op)
+        lmrs.lmrs_jtj_diag(op32.h, d32)
         out32 = torch.empty_like(v)
         lmrs.lmrs_jtjv(op32.h, v, out32)
+        b16, b32 = torch.empty_like(v), torch.empty_like(v)
+        lmrs.lmrs_rhs(op.h, b16)
+        lmrs.lmrs_rhs(op32.h, b32)
         torch.cuda.synchronize()
-        bf16_err = {"normwise_rel_vs_fp32_caches": float(((out - out32).norm() / out32.norm()).item()),
-                    "what": "(J^T W J + lambda diag) v with BF16 vs FP32 final-colour/transmittance caches"}
+
+        def rel(a, b):
+            return float(((a - b).norm() / b.norm()).item())
+
+        bf16_err = {"rhs": rel(b16, b32), "diag": rel(d_op, d32), "operator": rel(out, out32),
+                    "what": "normwise relative difference of J^T W r, diag(J^T W J) and the lambda*diag operator "
+                            "with BF16 vs FP32 final-colour/transmittance caches (the operator sees the cache "
+                            "only through D)"}
         op32.close()
-        del out32
+        del out32, d32, b16, b32
     op.close()
-    del cur
+    del cur, d_op
 
     # ---- end to end through the C-ABI with host buffers ---------------
     p_host = torch.empty(scene.n_params, dtype=torch.float32).pin_memory()
