@@ -529,6 +529,23 @@ const char* lmrs_last_error(const lmrs_scene* scene);
 /* Number of kernels this library has launched in the process so far. */
 int64_t lmrs_launch_count(void);
 
+/* ---- Bounds-checked builds ----------------------------------------------
+ * The paper has no counterpart: these stand in for a memory checker on GPUs
+ * where none can be run.  A library built with LMRS_DEBUG defined (build.py
+ * build(debug=True), into _build_debug/) checks the indexes the rasterisers
+ * take from the lists before each access: a Gaussian id of a staged list
+ * entry (< G), a compact-list write (< the tile list's length) and the id of
+ * every back-scattered entry.  A failed check sets its bit in the scene's
+ * debug word and the access uses index 0 instead, so it stays in bounds.
+ * Release builds compile the checks away.
+ *   lmrs_debug_build: 1 in an LMRS_DEBUG build, else 0.
+ *   lmrs_debug_status: the scene's debug word (host, *bits_host; bit 0 a
+ *     staged id, bit 1 a compact-list write, bit 2 a back-scattered id),
+ *     then cleared; waits for the scene's stream.  Always 0 in release
+ *     builds.  LMRS_ERR_INVALID_ARG for a null argument. */
+int32_t lmrs_debug_build(void);
+lmrs_status lmrs_debug_status(lmrs_scene* scene, uint32_t* bits_host);
+
 /* ---- Peak rates of the current device ------------------------------------
  * Measured by microbenchmarks of this library (the paper has no
  * counterpart: they are the denominators of the raster kernels' roofline,

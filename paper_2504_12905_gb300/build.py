@@ -17,6 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
+# the bounds-checked build (LMRS_DEBUG, see include/lmrs.h), beside the release one
+OUT_DIR_DEBUG = os.path.join(HERE, "_build_debug")
 LIB_NAME = "liblmrs.so"
 # hotpath.cu includes preprocess.cu, raster.cu and cg.cu (one translation unit)
 SOURCES = ["scene.cu", "hotpath.cu", "binning.cu", "noalloc.cu", "autotune.cu", "server.cu", "view_sampler.cu",
@@ -31,8 +33,8 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build liblmrs")
 
 
-def library_path() -> str:
-    return os.path.join(OUT_DIR, LIB_NAME)
+def library_path(debug: bool = False) -> str:
+    return os.path.join(OUT_DIR_DEBUG if debug else OUT_DIR, LIB_NAME)
 
 
 def _flags(extra=()):
@@ -45,16 +47,21 @@ def _stamp_inputs():
     return max(os.path.getmtime(f) for f in files)
 
 
-def build(verbose: bool = False, force: bool = False, extra_flags=()) -> str:
-    os.makedirs(OUT_DIR, exist_ok=True)
-    out = library_path()
+def build(verbose: bool = False, force: bool = False, extra_flags=(), debug: bool = False) -> str:
+    """Builds the library (debug: the bounds-checked LMRS_DEBUG build into
+    _build_debug/) unless it is newer than every source; returns its path."""
+    out_dir = OUT_DIR_DEBUG if debug else OUT_DIR
+    if debug:
+        extra_flags = tuple(extra_flags) + ("-DLMRS_DEBUG",)
+    os.makedirs(out_dir, exist_ok=True)
+    out = library_path(debug)
     if not force and os.path.exists(out) and os.path.getmtime(out) >= _stamp_inputs():
         return out
     nv = nvcc()
     objs = []
 
     def compile_one(src):
-        obj = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
+        obj = os.path.join(out_dir, src.replace(".cu", ".o"))
         cmd = [nv, "-c", os.path.join(CSRC, src), "-o", obj] + _flags(extra_flags)
         if verbose:
             print(" ".join(cmd), file=sys.stderr)

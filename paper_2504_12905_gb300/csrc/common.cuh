@@ -62,8 +62,26 @@ struct Scalars {
     unsigned int pad1;
     // preprocessing
     unsigned int n_list;  // tile-list entries of the step (written by the binning)
-    unsigned int pad2;
+    unsigned int debug_err;  // LMRS_DEBUG builds: bit k set by a failed check k (lmrs_debug_status)
 };
+
+// Index checks of LMRS_DEBUG builds: an index outside [0, n) sets bit `bit`
+// of the scene's debug word and is replaced by 0, so that the access it
+// guards stays in bounds.  Release builds compile the check away.
+#ifdef LMRS_DEBUG
+#define LMRS_DCHECK_INDEX(c, idx, n, bit)                                                 \
+    do {                                                                                  \
+        if ((unsigned long long)(idx) >= (unsigned long long)(n)) {                       \
+            atomicOr(&(c).sc->debug_err, 1u << (bit));                                    \
+            (idx) = 0;                                                                    \
+        }                                                                                 \
+    } while (0)
+#else
+#define LMRS_DCHECK_INDEX(c, idx, n, bit) \
+    do {                                  \
+    } while (0)
+#endif
+enum { kCheckStagedId = 0, kCheckCompactWrite = 1, kCheckScatterId = 2 };
 
 // Everything a kernel needs to know about the scene and the current step.
 struct Ctx {

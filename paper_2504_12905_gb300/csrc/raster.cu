@@ -125,7 +125,8 @@ __device__ __forceinline__ int stage_batch(const Ctx& c, int slot, const unsigne
     const int lane = threadIdx.x & 31;
     const int k = b + lane;
     if (lane < R && k < end) {
-        const unsigned id = ids[k];
+        unsigned id = ids[k];
+        LMRS_DCHECK_INDEX(c, id, c.G, kCheckStagedId);
         const long long pr = (long long)slot * c.G + id;
 #pragma unroll
         for (int q = 0; q < NF4; ++q) s_rec[lane][q] = q < kPrimF4 ? c.rec[pr * kPrimF4 + q] : c.tan[pr * kTanF4 + q - kPrimF4];
@@ -165,7 +166,11 @@ __device__ __forceinline__ void forward_pass(const Ctx& c, const Pix& p, List L,
             bool need = !done && alpha >= kAlphaMin;
             if (kCompact) {
                 const bool any = __any_sync(kFull, need);
-                if (any && lane == 0) out_ids[kept] = s_id[j];
+                if (any && lane == 0) {
+                    int slot_k = kept;
+                    LMRS_DCHECK_INDEX(c, slot_k, L.e - L.b, kCheckCompactWrite);
+                    out_ids[slot_k] = s_id[j];
+                }
                 if (need) {
                     const float Tn = T * (1.f - alpha);
                     if (Tn < kTMin) {
@@ -350,7 +355,9 @@ __device__ __forceinline__ void backward_pass(const Ctx& c, const Pix& p, List L
                 Ms[k] += __shfl_xor_sync(kFull, Ms[k], 16);
             }
             if (hh == 0 && e < m) {
-                float* dst = cot_base + (long long)L.ids[b + j] * kCotF;
+                unsigned id = L.ids[b + j];
+                LMRS_DCHECK_INDEX(c, id, c.G, kCheckScatterId);
+                float* dst = cot_base + (long long)id * kCotF;
                 red_add_v4(dst, Ms[0], Ms[1], Ms[2], Ms[3]);
                 red_add_v4(dst + 4, Ms[4], Ms[5], Ms[6], Ms[7]);
                 atomicAdd(dst + 8, Ms[8]);
@@ -491,7 +498,9 @@ __device__ __forceinline__ void stage_jvp(const Ctx& c, int slot, const unsigned
     const int lane = threadIdx.x & 31;
     const int k = b + lane;
     if (lane < kJtjRows && k < end) {
-        const long long pr = (long long)slot * c.G + ids[k];
+        unsigned id = ids[k];
+        LMRS_DCHECK_INDEX(c, id, c.G, kCheckStagedId);
+        const long long pr = (long long)slot * c.G + id;
         const float4 a0 = c.rec[pr * kPrimF4], a1 = c.rec[pr * kPrimF4 + 1], a2 = c.rec[pr * kPrimF4 + 2];
         const float4 t0 = c.tan[pr * kTanF4], t1 = c.tan[pr * kTanF4 + 1];
         const float tb = reinterpret_cast<const float*>(c.tan + pr * kTanF4 + 2)[0];
@@ -767,13 +776,15 @@ __global__ void __launch_bounds__(kRasterBlock) k_diag(Ctx c) {
             if (hh == 0 && e < m) {
                 const float4 r1 = sm.rec[j][1];
                 const float om = 1.f - r1.y;
-                float* dst = dbase + (long long)sm.id[j] * kDiagF;
+                unsigned id = sm.id[j];
+                LMRS_DCHECK_INDEX(c, id, c.G, kCheckScatterId);
+                float* dst = dbase + (long long)id * kDiagF;
                 red_add_v4(dst, D[0], D[1], D[2], D[3]);
                 red_add_v4(dst + 4, D[4], D[5], D[6], D[7]);
                 red_add_v4(dst + 8, D[8], D[9], om * om * D[10], D[11]);
                 red_add_v4(dst + 12, D[12], D[13], 0.f, 0.f);
                 if (kRhs) {
-                    float* cdst = cbase + (long long)sm.id[j] * kCotF;
+                    float* cdst = cbase + (long long)id * kCotF;
                     red_add_v4(cdst, M[0], M[1], M[2], M[3]);
                     red_add_v4(cdst + 4, M[4], M[5], M[6], M[7]);
                     atomicAdd(cdst + 8, M[8]);

@@ -11,6 +11,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 
 namespace lmrs {
@@ -898,14 +900,37 @@ lmrs_status lmrs_lm_step(lmrs_scene* s, const int32_t* view_ids, int32_t n_views
 
 namespace {
 
+// A named range on the host timeline of a profiler (NVTX; without a tool
+// attached the calls return at once), closed when it goes out of scope.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 // One LM step (Alg. 1) with `iters` PCG iterations.
 lmrs_status lm_step_iters(lmrs_scene* s, const int32_t* view_ids, int32_t n_views, int64_t lm_step, int iters,
                           lmrs_step_stats* st) {
     TimerScope ts_(s);
-    TRY(lmrs_preprocess(s, view_ids, n_views, lm_step));
-    TRY(lmrs_render(s, nullptr, nullptr));
-    TRY(do_rhs_diag(s, s->b.as<float>()));
-    TRY(do_cg(s, s->b.as<float>(), s->x.as<float>(), iters));
+    NvtxRange step_("lmrs_lm_step");
+    {
+        NvtxRange r_("preprocess");
+        TRY(lmrs_preprocess(s, view_ids, n_views, lm_step));
+    }
+    {
+        NvtxRange r_("render");
+        TRY(lmrs_render(s, nullptr, nullptr));
+    }
+    {
+        NvtxRange r_("rhs_diag");
+        TRY(do_rhs_diag(s, s->b.as<float>()));
+    }
+    {
+        NvtxRange r_("pcg");
+        TRY(do_cg(s, s->b.as<float>(), s->x.as<float>(), iters));
+    }
+    NvtxRange u_("update");
     Ctx c = s->ctx();
     CK(s, cudaMemsetAsync(&c.sc->max_dc_bits, 0, sizeof(unsigned int), s->st));
     launch_max_dc(c, s->x.as<float>(), s->st);
@@ -1090,6 +1115,24 @@ const char* lmrs_status_str(lmrs_status st) {
 const char* lmrs_last_error(const lmrs_scene* s) { return s ? s->err.c_str() : "null scene"; }
 
 int64_t lmrs_launch_count(void) { return lmrs::g_launches.load(std::memory_order_relaxed); }
+
+int32_t lmrs_debug_build(void) {
+#ifdef LMRS_DEBUG
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+lmrs_status lmrs_debug_status(lmrs_scene* s, uint32_t* bits) {
+    TRY(check_scene(s));
+    if (!bits) return fail(s, LMRS_ERR_INVALID_ARG, "null argument");
+    unsigned int* w = &s->sc.as<Scalars>()->debug_err;
+    CK(s, cudaMemcpyAsync(bits, w, sizeof(unsigned int), cudaMemcpyDeviceToHost, s->st));
+    CK(s, cudaMemsetAsync(w, 0, sizeof(unsigned int), s->st));
+    CK(s, cudaStreamSynchronize(s->st));
+    return LMRS_OK;
+}
 
 int64_t lmrs_footprint_bytes(const lmrs_config* cfg, int64_t n_gauss, int32_t n_cams, int32_t width, int32_t height,
                              int32_t views_per_step, double tiles_per_pair) {
@@ -1427,6 +1470,7 @@ lmrs_status lmrs_batch_lm_step(lmrs_batch* B, const int32_t* view_ids, const int
                                lmrs_step_stats* stats) {
     if (!B) return LMRS_ERR_INVALID_ARG;
     if (!view_ids || !n_views || !lm_steps) return bfail(B, LMRS_ERR_INVALID_ARG, "null argument");
+    NvtxRange step_("lmrs_batch_lm_step");
     B->scene_rc.assign(B->n, LMRS_ERR_NOT_PREPROCESSED);  // "not stepped" until the graph ran
     std::vector<long long> voff(B->n + 1, 0);
     for (int i = 0; i < B->n; ++i) {

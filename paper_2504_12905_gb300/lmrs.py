@@ -159,12 +159,16 @@ _SIGS = {
     "lmrs_last_error": (C.c_char_p, [_P]),
     "lmrs_launch_count": (C.c_int64, []),
     "lmrs_measure_peaks": (_S, [_P, C.POINTER(Peaks)]),
+    "lmrs_debug_build": (C.c_int32, []),
+    "lmrs_debug_status": (_S, [_P, C.POINTER(C.c_uint32)]),
 }
 EXPORTS = tuple(_SIGS)
 
 
 def library_path() -> str:
-    return _build.library_path()
+    """The release library, or the bounds-checked LMRS_DEBUG build when the
+    environment sets LMRS_DEBUG_LIBRARY=1 (include/lmrs.h)."""
+    return _build.library_path(debug=os.environ.get("LMRS_DEBUG_LIBRARY") == "1")
 
 
 def lib():
@@ -582,6 +586,17 @@ def lmrs_last_error(scene):
 
 def lmrs_launch_count():
     return int(lib().lmrs_launch_count())
+
+
+def lmrs_debug_build():
+    return int(lib().lmrs_debug_build())
+
+
+def lmrs_debug_status(scene):
+    """The scene's debug word (0: every check passed), then cleared."""
+    bits = C.c_uint32()
+    _check(lib().lmrs_debug_status(scene, C.byref(bits)), scene)
+    return int(bits.value)
 
 
 def lmrs_measure_peaks(stream=None):
