@@ -649,34 +649,42 @@ __global__ void __launch_bounds__(kBinBlock) k_tile_count(Ctx c, int nchunk, con
 }
 
 // One block per (slot, row, group of kColGroup columns, segment); warp w owns
-// the group's columns x = x0g + w + kColWarps q (q < kColsPerWarp) and walks
-// the segment of the row list once, kColRounds rounds of 32 entries at a
-// time (the loads of a batch go out together): per owned column one ballot
-// of the entries covering it, each covering lane writing at the (column,
-// segment)'s running offset + its rank.  Every column's list is appended in
-// order.  Splitting a row over column groups and segments spreads its work
-// over several SMs.
+// the group's columns x = x0g + w + kColWarps q (q < kColsPerWarp).  The
+// block walks the segment of the row list kPlaceRound entries at a time:
+// the warps load consecutive runs of them and keep, in order, the entries
+// whose span meets the group (a ballot and a block-wide prefix of the
+// warps' counts place them in shared memory); then every warp walks the
+// kept entries 32 at a time, and per owned column one ballot of the entries
+// covering it, each covering lane writing at the (column, segment)'s
+// running offset + its rank.  Every column's list is appended in order.
+// Splitting a row over column groups and segments spreads its work over
+// several SMs; the keep step spares the column ballots the entries of the
+// row that lie in other groups.
 constexpr int kColWarps = 8;
 constexpr int kColsPerWarp = 4;
 constexpr int kColGroup = kColWarps * kColsPerWarp;
-constexpr int kColRounds = 8;
+constexpr int kColRounds = 4;  // 32-entry loads per warp per round
 constexpr int kColBlock = kColWarps * kWarp;
+constexpr int kPlaceRound = kColBlock * kColRounds;  // entries the block walks per round
 
 __global__ void __launch_bounds__(kColBlock) k_tile_place(Ctx c, int nchunk, const unsigned* mat,
                                                           const unsigned* rtotal, const unsigned long long* rl,
                                                           const unsigned* start) {
+    __shared__ unsigned long long s_keep[kPlaceRound];
+    __shared__ int s_wcnt[kColWarps];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     const int nx = c.tiles_x;
     const int sr = blockIdx.x, slot = sr / c.tiles_y, row = sr - slot * c.tiles_y, seg = blockIdx.z;
     const int x0g = blockIdx.y * kColGroup;
-    if (x0g + wid >= nx) return;  // this warp owns no column of the row
+    const int x1g = min(x0g + kColGroup, nx) - 1;  // the group's last column
     const long long t0 = (long long)slot * c.T + (long long)row * nx;
     unsigned rb, re, b, e;
     row_range(c, nchunk, mat, rtotal, sr, rb, re);
     seg_range(rb, re, seg, b, e);
-    // its columns inside the row: the ballots of the others are skipped
-    const int nq = min(kColsPerWarp, (nx - 1 - x0g - wid) / kColWarps + 1);
+    // its columns inside the row (none for some warps of the last group):
+    // the ballots of the others are skipped
+    const int nq = x0g + wid < nx ? min(kColsPerWarp, (nx - 1 - x0g - wid) / kColWarps + 1) : 0;
     unsigned off[kColsPerWarp];
     int col[kColsPerWarp];
 #pragma unroll
@@ -684,11 +692,14 @@ __global__ void __launch_bounds__(kColBlock) k_tile_place(Ctx c, int nchunk, con
         col[q] = x0g + wid + kColWarps * q;
         off[q] = q < nq ? start[(t0 + col[q]) * kRowSegs + seg] : 0u;
     }
-    for (unsigned base = b; base < e; base += 32 * kColRounds) {
+    for (unsigned base = b; base < e; base += kPlaceRound) {
+        // keep, in order, the round's entries whose span meets the group
         unsigned long long v[kColRounds];
+        unsigned m[kColRounds];
+        int cnt = 0;
 #pragma unroll
         for (int r = 0; r < kColRounds; ++r) {
-            const unsigned k = base + 32 * r + lane;
+            const unsigned k = base + (unsigned)(wid * kColRounds + r) * 32u + lane;
             v[r] = k < e ? rl[k] : row_entry(0u, 1, 0);
         }
 #pragma unroll
@@ -696,15 +707,40 @@ __global__ void __launch_bounds__(kColBlock) k_tile_place(Ctx c, int nchunk, con
             unsigned g;
             int x0, x1;
             row_entry_unpack(v[r], g, x0, x1);
+            m[r] = __ballot_sync(kFull, x0 <= x1 && x0 <= x1g && x1 >= x0g);
+            cnt += __popc(m[r]);
+        }
+        if (lane == 0) s_wcnt[wid] = cnt;
+        __syncthreads();
+        int run = 0, n = 0;
+#pragma unroll
+        for (int w = 0; w < kColWarps; ++w) {
+            const int t = s_wcnt[w];
+            run += w < wid ? t : 0;
+            n += t;
+        }
+#pragma unroll
+        for (int r = 0; r < kColRounds; ++r) {
+            if ((m[r] >> lane) & 1u) s_keep[run + __popc(m[r] & lt)] = v[r];
+            run += __popc(m[r]);
+        }
+        __syncthreads();
+        // the kept entries, 32 at a time: per owned column one ballot
+        for (int j = 0; j < n; j += 32) {
+            const int i = j + lane;
+            unsigned g;
+            int x0, x1;
+            row_entry_unpack(i < n ? s_keep[i] : row_entry(0u, 1, 0), g, x0, x1);
 #pragma unroll
             for (int q = 0; q < kColsPerWarp; ++q) {
                 if (q >= nq) break;  // warp-uniform
                 const bool in = x0 <= col[q] && col[q] <= x1;
-                const unsigned m = __ballot_sync(kFull, in);
-                if (in) c.ids[off[q] + __popc(m & lt)] = g;
-                off[q] += __popc(m);
+                const unsigned mq = __ballot_sync(kFull, in);
+                if (in) c.ids[off[q] + __popc(mq & lt)] = g;
+                off[q] += __popc(mq);
             }
         }
+        __syncthreads();  // s_keep and s_wcnt are rewritten by the next round
     }
 }
 
