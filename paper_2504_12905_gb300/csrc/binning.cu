@@ -405,10 +405,11 @@ void launch_ranges(const Ctx& c, cudaStream_t st) {
 //          with that row's tile columns (row_span, possibly none): counts
 //          per (slot, row, chunk of kBinChunk pairs), an exclusive scan, then
 //          the placement;
-//   tiles: one block per (slot, row) counts that row's list per tile, an
-//          exclusive scan gives the tile lists' starts, then one block per
-//          (slot, row, group of 32 tile columns) walks the row list in order
-//          and places each pair into the group's tiles it spans.
+//   tiles: one block per (slot, row, segment of its row list) counts that
+//          row's list per tile, an exclusive scan gives the tile lists'
+//          starts, then one block per (slot, row, group of kColGroup tile
+//          columns, segment) walks the segment in order and places each pair
+//          whose span meets the group into the group's tiles it spans.
 // A placement ranks a lane's pair among the warp's 32 pairs covering the same
 // bin with a ballot, warps are ranked by their order in the chunk and chunks
 // by the scan, so every list keeps the order it is read in: the tile lists
@@ -661,7 +662,7 @@ __global__ void __launch_bounds__(kBinBlock) k_tile_count(Ctx c, int nchunk, con
 // several SMs; the keep step spares the column ballots the entries of the
 // row that lie in other groups.
 constexpr int kColWarps = 8;
-constexpr int kColsPerWarp = 4;
+constexpr int kColsPerWarp = 2;
 constexpr int kColGroup = kColWarps * kColsPerWarp;
 constexpr int kColRounds = 4;  // 32-entry loads per warp per round
 constexpr int kColBlock = kColWarps * kWarp;

@@ -1166,9 +1166,9 @@ int64_t lmrs_footprint_bytes(const lmrs_config* cfg, int64_t n_gauss, int32_t n_
     // importance weight 4, SSIM values 24
     const double per_sample = 41 + (cfg->sample_dist != 0 ? 4 : 0) + (cfg->ssim_weight > 0.0 ? 24 : 0);
     // tile offset, weight, range 16; the binning's counts per (tile, row-list
-    // segment) 16; compact lengths 4 per item; work items and their ordering
-    // buffers 36
-    const double per_view_tile = 32 + 4.0 * max_items;
+    // segment) 32 (8 segments); compact lengths 4 per item; work items and
+    // their ordering buffers 36
+    const double per_view_tile = 48 + 4.0 * max_items;
     const double per_item = 36;
     const double fixed = 9 * 4 * P + 4.0 * kGaussF4 * 4 * G + (double)sizeof(CamDev) * n_cams +
                          sizeof(double) * kMaxPartials + 65536;
