@@ -79,3 +79,35 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(lmrs, "library_path", lambda: str(tmp_path / "nope.so"))
     with pytest.raises(RuntimeError, match="no fallback"):
         lmrs.lib()
+
+
+def test_release_build_reports_no_debug_checks(lib):
+    L, _ = lib
+    L.lmrs_debug_build.restype = C.c_int32
+    assert L.lmrs_debug_build() == 0
+
+
+def test_debug_library_is_selected_by_the_environment(monkeypatch):
+    """LMRS_DEBUG_LIBRARY=1 points the binding at the bounds-checked build,
+    which lives beside the release build; nothing else does."""
+    from paper_2504_12905_gb300 import lmrs
+    monkeypatch.delenv("LMRS_DEBUG_LIBRARY", raising=False)
+    release = lmrs.library_path()
+    monkeypatch.setenv("LMRS_DEBUG_LIBRARY", "1")
+    debug = lmrs.library_path()
+    monkeypatch.setenv("LMRS_DEBUG_LIBRARY", "0")
+    assert lmrs.library_path() == release
+    assert release == lbuild.library_path() and debug == lbuild.library_path(debug=True)
+    assert os.path.dirname(release) != os.path.dirname(debug)
+    assert os.path.basename(release) == os.path.basename(debug)
+
+
+def test_debug_build_compiles_and_reports_itself():
+    """The bounds-checked build compiles for sm_103a with LMRS_DEBUG defined
+    and exports the same entry points."""
+    path = lbuild.build(debug=True)
+    L = C.CDLL(path)
+    L.lmrs_debug_build.restype = C.c_int32
+    assert L.lmrs_debug_build() == 1
+    for n in _declared():
+        assert hasattr(L, n), f"{n} not exported by {path}"
