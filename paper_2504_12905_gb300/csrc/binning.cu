@@ -484,12 +484,16 @@ __device__ __forceinline__ void band_rows(const Ctx& c, int4 rc, float4 e0, floa
     while (hi >= lo && !band_meets(e0, e1, hi, c.tile_h, c.H)) --hi;
 }
 
-// Row counts per (slot, row, chunk).
+// Row counts per (slot, row, chunk, warp of the chunk): mat[((slot * tiles_y
+// + row) * nchunk + chunk) * kBinWarps + warp], so that the scan over mat
+// gives every warp of the placement its start in each row list.
 __global__ void __launch_bounds__(kBinBlock) k_row_count(Ctx c, int nchunk, unsigned* mat) {
     extern __shared__ unsigned bin_smem[];
-    unsigned* s_cnt = bin_smem;  // [tiles_y]
-    for (int r = threadIdx.x; r < c.tiles_y; r += kBinBlock) s_cnt[r] = 0u;
+    const int ny = c.tiles_y;
+    unsigned* s_cnt = bin_smem;  // [kBinWarps][tiles_y]
+    for (int i = threadIdx.x; i < kBinWarps * ny; i += kBinBlock) s_cnt[i] = 0u;
     __syncthreads();
+    unsigned* mine = s_cnt + (threadIdx.x >> 5) * ny;
     const int slot = blockIdx.y;
     const long long s0 = (long long)slot * c.G;
     const long long b = s0 + (long long)blockIdx.x * kBinChunk + (long long)(threadIdx.x >> 5) * kBinRun;
@@ -500,11 +504,14 @@ __global__ void __launch_bounds__(kBinBlock) k_row_count(Ctx c, int nchunk, unsi
         if (rc.x > rc.y) continue;
         int lo, hi;
         band_rows(c, rc, c.ell[2 * i], c.ell[2 * i + 1], lo, hi);
-        for (int r = lo; r <= hi; ++r) atomicAdd(&s_cnt[r], 1u);
+        for (int r = lo; r <= hi; ++r) atomicAdd(&mine[r], 1u);
     }
     __syncthreads();
-    const long long row0 = (long long)slot * c.tiles_y;
-    for (int r = threadIdx.x; r < c.tiles_y; r += kBinBlock) mat[(row0 + r) * nchunk + blockIdx.x] = s_cnt[r];
+    const long long row0 = (long long)slot * ny;
+    for (int i = threadIdx.x; i < kBinWarps * ny; i += kBinBlock) {
+        const int w = i / ny, r = i - w * ny;
+        mat[((row0 + r) * nchunk + blockIdx.x) * kBinWarps + w] = s_cnt[i];
+    }
 }
 
 // A row-list entry: the Gaussian index and its tile columns x0..x1.
@@ -518,50 +525,31 @@ __device__ __forceinline__ void row_entry_unpack(unsigned long long v, unsigned&
 }
 
 // Placement in windows of kRowWin rows: the ballots of a window fix every
-// (pair, row) entry's slot, then each lane computes the tile columns of its
-// own rows once (row_span) and writes their entries.
+// (pair, row) entry's slot (the warp's start in the row from the scanned
+// counts, plus the entries it placed there before, plus the lane's rank),
+// then each lane computes the tile columns of its own rows once (row_span)
+// and writes their entries.
 constexpr int kRowWin = 32;
 
 __global__ void __launch_bounds__(kBinBlock) k_row_place(Ctx c, int nchunk, const unsigned* mat,
                                                          unsigned long long* rl) {
     extern __shared__ unsigned bin_smem[];
     const int ny = c.tiles_y;
-    unsigned* s_base = bin_smem;                                             // [ny]
-    unsigned short* s_w = reinterpret_cast<unsigned short*>(bin_smem + ny);  // [kBinWarps][ny]
-    unsigned* s_dst = bin_smem + ny + (kBinWarps * ny + 1) / 2;              // [kBinWarps][kRowWin][32]
+    unsigned* s_pos = bin_smem;                   // [kBinWarps][ny]: each warp's next slot per row
+    unsigned* s_dst = bin_smem + kBinWarps * ny;  // [kBinWarps][kRowWin][32]
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < kBinWarps * ny; i += kBinBlock) s_w[i] = 0;
-    __syncthreads();
     const int slot = blockIdx.y;
+    const long long row0 = (long long)slot * ny;
+    for (int i = threadIdx.x; i < kBinWarps * ny; i += kBinBlock) {
+        const int w = i / ny, r = i - w * ny;
+        s_pos[i] = mat[((row0 + r) * nchunk + blockIdx.x) * kBinWarps + w];
+    }
+    __syncthreads();
     const long long s0 = (long long)slot * c.G;
     const long long b = s0 + (long long)blockIdx.x * kBinChunk + (long long)wid * kBinRun;
     const long long e = min(b + kBinRun, s0 + c.G);
-    unsigned short* mine = s_w + wid * ny;
-    const auto count = [&](int r, unsigned m) { if (lane == 0) mine[r] += (unsigned short)__popc(m); };
-    // this warp's count per row
-    for (long long base = b; base < e; base += 32) {
-        unsigned g;
-        int4 rc;
-        float4 e0, e1;
-        pair_rect(c, s0, base + lane, e, g, rc, e0, e1);
-        int lo, hi;
-        band_rows(c, rc, e0, e1, lo, hi);
-        rank_round(lo, hi, count, [](int, int) {});
-    }
-    __syncthreads();
-    // warps' offsets per row within the chunk, the chunk's base per row
-    const long long row0 = (long long)slot * ny;
-    for (int r = threadIdx.x; r < ny; r += kBinBlock) {
-        unsigned run = 0u;
-#pragma unroll
-        for (int w = 0; w < kBinWarps; ++w) {
-            const unsigned v = s_w[w * ny + r];
-            s_w[w * ny + r] = (unsigned short)run;
-            run += v;
-        }
-        s_base[r] = mat[(row0 + r) * nchunk + blockIdx.x];
-    }
-    __syncthreads();
+    unsigned* mine = s_pos + wid * ny;
+    const auto count = [&](int r, unsigned m) { if (lane == 0) mine[r] += (unsigned)__popc(m); };
     unsigned* dst = s_dst + wid * kRowWin * 32;
     for (long long base = b; base < e; base += 32) {
         unsigned g;
@@ -574,8 +562,7 @@ __global__ void __launch_bounds__(kBinBlock) k_row_place(Ctx c, int nchunk, cons
         const int uhi = warp_max_i(lo <= hi ? hi : -1);
         for (int w0 = ulo; w0 <= uhi; w0 += kRowWin) {
             const int wl = max(lo, w0), wh = min(hi, w0 + kRowWin - 1);
-            rank_round(wl, wh, count,
-                       [&](int r, int rank) { dst[(r - w0) * 32 + lane] = s_base[r] + mine[r] + rank; });
+            rank_round(wl, wh, count, [&](int r, int rank) { dst[(r - w0) * 32 + lane] = mine[r] + rank; });
             __syncwarp();
             for (int r = wl; r <= wh; ++r) {
                 int x0, x1;  // no tile in this row: an empty entry the tile stage skips
@@ -590,8 +577,8 @@ __global__ void __launch_bounds__(kBinBlock) k_row_place(Ctx c, int nchunk, cons
 // [begin, end) of the row list of (slot, row) index sr in rl.
 __device__ __forceinline__ void row_range(const Ctx& c, int nchunk, const unsigned* mat, const unsigned* total,
                                           int sr, unsigned& b, unsigned& e) {
-    b = mat[(long long)sr * nchunk];
-    e = sr + 1 < c.nv * c.tiles_y ? mat[(long long)(sr + 1) * nchunk] : *total;
+    b = mat[(long long)sr * nchunk * kBinWarps];
+    e = sr + 1 < c.nv * c.tiles_y ? mat[(long long)(sr + 1) * nchunk * kBinWarps] : *total;
 }
 
 // A row list is placed in kRowSegs segments of its entries (in order), so
@@ -756,8 +743,7 @@ __global__ void k_tile_ranges(Ctx c, const unsigned* start, const unsigned* tota
 }
 
 static size_t row_place_smem(const Ctx& c) {
-    const size_t w16 = ((size_t)kBinWarps * c.tiles_y + 1) / 2;  // s_w in 32-bit words
-    return ((size_t)c.tiles_y + w16 + (size_t)kBinWarps * kRowWin * 32) * sizeof(unsigned);
+    return ((size_t)kBinWarps * c.tiles_y + (size_t)kBinWarps * kRowWin * 32) * sizeof(unsigned);
 }
 
 bool bin_rows_fit(const Ctx& c) {
@@ -765,13 +751,15 @@ bool bin_rows_fit(const Ctx& c) {
            c.tiles_x < 65536;
 }
 
-size_t bin_row_mat_elems(const Ctx& c) { return (size_t)c.nv * c.tiles_y * bin_chunks(c); }
+size_t bin_row_mat_elems(const Ctx& c) { return (size_t)c.nv * c.tiles_y * bin_chunks(c) * kBinWarps; }
 size_t bin_tile_count_elems(const Ctx& c) { return (size_t)c.nv * c.T * kRowSegs; }
 size_t bin_scan_tmp_bytes(long long n) { return scan_tmp_elems<unsigned int>(n) * sizeof(unsigned int); }
 
 void bin_rows(const Ctx& c, unsigned* mat, unsigned long long* rl, unsigned* rtotal, void* tmp, cudaStream_t st) {
     const dim3 grid(bin_chunks(c), c.nv);
-    LMRS_LAUNCH(k_row_count, grid, kBinBlock, sizeof(unsigned) * c.tiles_y, st, c, bin_chunks(c), mat);
+    const size_t csmem = sizeof(unsigned) * kBinWarps * c.tiles_y;
+    if (csmem > 48 * 1024) cudaFuncSetAttribute(k_row_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem);
+    LMRS_LAUNCH(k_row_count, grid, kBinBlock, csmem, st, c, bin_chunks(c), mat);
     scan_rec<unsigned int>(mat, (long long)bin_row_mat_elems(c), rtotal, static_cast<unsigned*>(tmp), st);
     const size_t smem = row_place_smem(c);
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_row_place, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
