@@ -72,6 +72,7 @@ def lib():
             "orc_render_samples_subset": (C.c_int32, [_P, _P, C.c_int64, _P, _P]),
             "orc_render_full": (C.c_int32, [_P, C.c_int32, _P, _P]),
             "orc_pixel_counts": (C.c_int32, [_P, C.c_int32, _P]),
+            "orc_render_full_f32": (C.c_int32, [_P, C.c_int32, _P]),
             "orc_jvp": (C.c_int32, [_P, _P, _P]),
             "orc_jvp_subset": (C.c_int32, [_P, _P, _P, C.c_int64, _P]),
             "orc_vjp": (C.c_int32, [_P, _P, _P]),
@@ -188,6 +189,13 @@ class OracleScene:
         slot = np.empty(S, np.int32)
         lib().orc_get_samples(self._h, _ptr(off), _ptr(tile_off), _ptr(w), _ptr(px), _ptr(py), _ptr(slot))
         return dict(off=off, tile_off=tile_off, w=w, px=px, py=py, slot=slot)
+
+    def render_full_f32(self, slot):
+        """The view's frame with the preprocessing and compositing in
+        binary32 over the same lists (FP32 rounding against the FP64 frame)."""
+        img = np.empty((self.height, self.width, 3))
+        lib().orc_render_full_f32(self._h, slot, _ptr(img))
+        return img
 
     def pixel_counts(self, slot):
         out = np.empty((self.height, self.width), np.int32)

@@ -40,6 +40,7 @@ inline Dual operator/(Dual a, Dual b) { return Dual(a.v / b.v, (a.d * b.v - a.v 
 inline Dual exp(Dual a) { double e = std::exp(a.v); return Dual(e, e * a.d); }
 inline Dual sqrt(Dual a) { double r = std::sqrt(a.v); return Dual(r, a.d / (2.0 * r)); }
 inline double val(double x) { return x; }
+inline double val(float x) { return x; }
 inline double val(const Dual& x) { return x.v; }
 inline double tan_of(double) { return 0.0; }
 inline double tan_of(const Dual& x) { return x.d; }
@@ -1236,6 +1237,36 @@ int32_t orc_render_full(const orc_scene* s, int32_t slot, double* img, uint8_t* 
                               s->cfg.margin_alpha, s->cfg.margin_T, C, nullptr, &fl);
             for (int ch = 0; ch < 3; ++ch) img[((size_t)py * s->W + px) * 3 + ch] = C[ch];
             if (flags) flags[(size_t)py * s->W + px] = (uint8_t)fl;
+        }
+    return 0;
+}
+
+// The same frame with the preprocessing and the compositing in binary32
+// (Feat<float>, composite<float>: every operation rounded to float, the
+// decisions taken on the float values) over the same lists: what FP32
+// arithmetic alone does to a pixel, against the FP64 frame.  Not a model of
+// any particular FP32 implementation's operation order.
+int32_t orc_render_full_f32(const orc_scene* s, int32_t slot, double* img) {
+    std::vector<Feat<float>> ff((size_t)s->G);
+    for (int g = 0; g < s->G; ++g) {
+        const Gauss<double> gd = s->gauss(g);
+        Gauss<float> gf;
+        for (int k = 0; k < 3; ++k) gf.X[k] = (float)gd.X[k], gf.ls[k] = (float)gd.ls[k];
+        for (int k = 0; k < 4; ++k) gf.q[k] = (float)gd.q[k];
+        gf.th = (float)gd.th;
+        for (int k = 0; k < 16; ++k)
+            for (int ch = 0; ch < 3; ++ch) gf.sh[k][ch] = (float)gd.sh[k][ch];
+        preprocess<float>(gf, s->deg, s->camd[s->views[slot]], ff[g]);
+    }
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int py = 0; py < s->H; ++py)
+        for (int px = 0; px < s->W; ++px) {
+            int t = (py / s->cfg.tile_h) * s->tiles_x + px / s->cfg.tile_w, len, fl;
+            const int32_t* ids = s->list(slot, t, &len);
+            float C[3];
+            composite<float>(px + 0.5, py + 0.5, ids, len, ff.data(), s->cfg.margin_alpha, s->cfg.margin_T, C,
+                             nullptr, &fl);
+            for (int ch = 0; ch < 3; ++ch) img[((size_t)py * s->W + px) * 3 + ch] = C[ch];
         }
     return 0;
 }

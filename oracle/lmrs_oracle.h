@@ -113,6 +113,11 @@ int32_t orc_render_full(const orc_scene* s, int32_t slot, double* img, uint8_t* 
 /* Number of Gaussians each pixel of the view composites (alpha >= 1/255
  * before termination), H x W. */
 int32_t orc_pixel_counts(const orc_scene* s, int32_t slot, int32_t* counts);
+/* The view's full frame (H x W x 3) with the preprocessing and compositing
+ * evaluated in binary32 over the same lists (test infrastructure: the FP32
+ * rounding error of a pixel against the FP64 frame, as a function of how
+ * many Gaussians it composites). */
+int32_t orc_render_full_f32(const orc_scene* s, int32_t slot, double* img);
 
 int32_t orc_jvp(const orc_scene* s, const double* v, double* u);
 int32_t orc_jvp_subset(const orc_scene* s, const double* v, const int64_t* idx, int64_t n, double* u);
