@@ -363,3 +363,35 @@ def test_errors_are_status_codes():
     with pytest.raises(lmrs.LmrsError) as e:
         lmrs.lmrs_vjp(pair.gpu.h, pair.zeros(pair.S * 3), pair.zeros(pair.P))
     assert e.value.status == 4  # render first
+
+
+def test_squeezed_strip_within_the_fp32_floor():
+    """The 2 x 8700 strip with the 60 degree field of view across its width
+    (focal length 1.7 px: every Gaussian sub-pixel, 1,498 in the deepest
+    list).  There FP32 arithmetic alone misses the 1e-5 pixel bar (the
+    oracle's binary32 evaluation errs by up to 5.5e-5, tests/test_oracle_fp32.py),
+    so the device's frames are held to twice that floor, measured per view
+    from the oracle's own FP32 frame, at every pixel the oracle does not flag;
+    its tile lists are still bit for bit the oracle's."""
+    sc = syn.tiny_scene(seed=7, n_gauss=1500, width=2, height=8700, sh_degree=0)
+    tgt = syn.noise_targets(np.random.default_rng(37), len(sc.cams), 8700, 2)
+    pair = Pair(sc, tgt, sample_frac=1.0, tile_w=1, tile_h=1)
+    views = [0, 2]
+    pair.begin(views, step=2)
+    ranges, ids = pair.lmrs.lmrs_get_tile_lists(pair.gpu.h, pair.gpu.n_views, pair.gpu.n_tiles)
+    r_ref, ids_ref = pair.orc.lists()
+    np.testing.assert_array_equal(ids, ids_ref)
+    images = pair.zeros(pair.gpu.n_views * 8700 * 2 * 3)
+    pair.lmrs.lmrs_render(pair.gpu.h, images, None)
+    img = pair.host(images).reshape(pair.gpu.n_views, 8700, 2, 3)
+    worst = []
+    for slot in range(pair.gpu.n_views):
+        ref, fl = pair.orc.render_full(slot)
+        floor = float(np.abs(pair.orc.render_full_f32(slot) - ref)[fl == 0].max())
+        k = fl == 0
+        err = float(np.abs(img[slot][k] - ref[k]).max())
+        worst.append((err, floor))
+        assert floor > 1e-5  # the case is the one FP32 cannot render to 1e-5
+        assert err <= 2.0 * floor, (slot, err, floor)
+    print("device error, FP32 floor per view:", worst)
+    pair.gpu.close()
