@@ -65,10 +65,13 @@ __device__ bool grid_barrier(GridBar* b, unsigned expected, unsigned long long t
 // iteration kb_direction, kb_prep_jvp, kb_jtj, kb_prep_vjp, kb_update, then
 // kb_max_dc and kb_lm_update), each a grid-stride loop over its chunk table,
 // separated by grid barriers.  The per-scene FP64 scalars are those of the
-// per-phase form, so both give the same result.
+// per-phase form, so both give the same result.  The kernel waits mostly on
+// memory (ncu on the SH0 batch: long-scoreboard stalls first, 31% of DRAM
+// throughput at 5 blocks per SM), so at SH0 it is held to 80 registers for 6
+// resident blocks per SM (44 B of spills); the SH >= 1 forms keep 3.
 template <int DEG>
-__global__ void __launch_bounds__(kBatchBlock) kb_pcg(BatchTables t, int iters, GridBar* bar,
-                                                      unsigned long long timeout_ns) {
+__global__ void __launch_bounds__(kBatchBlock, DEG == 0 ? 6 : 3)
+    kb_pcg(BatchTables t, int iters, GridBar* bar, unsigned long long timeout_ns) {
     __shared__ WarpSmem s_warp[kRasterWarps];
     const unsigned int n = gridDim.x;
     b_precond_init(t);
