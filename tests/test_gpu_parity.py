@@ -77,7 +77,7 @@ CASES = {
     "ragged_tile8x32_spt": lambda: _ragged(0, 1.0, tile_w=8, tile_h=32, samples_per_tile=40, weight_mode=1),
     "tiles2x2_direct_8100": lambda: _tiles2(180, 180),
     "tiles2x2_8500": lambda: _tiles2(200, 170),
-    # 8,600 tile columns: 269 column groups of the two-level binning
+    # 8,600 tile columns: 538 column groups of 16 in the two-level binning
     "strip_wide_8600": lambda: _strip(8600, 2, 31),
     # 8,700 tile rows: the row placement's shared counters would pass 200 KB,
     # so the entry emission + tile sort builds the lists (217,724 entries in
